@@ -1,0 +1,251 @@
+"""Pins for the oracle's solvers: duality, two independent relaxation solvers,
+the exact box ridge against a library routine, brute force against the
+branch-and-bound, the orthonormal special case and the BnB invariants."""
+import numpy as np
+import pytest
+from scipy.optimize import lsq_linear
+
+import datagen
+from oracle import relax, admm, pgd, ub, brute, bnb
+
+
+def _small(seed=0, n=60, p=12, rho=0.3, k=3, snr=5.0):
+    return datagen.make_instance(n, p, rho, k, snr, seed)
+
+
+def _params(inst, lam2=0.01, frac=0.05, mfac=1.5):
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2, mfac)
+    lam0 = frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    return lam0, lam2, M
+
+
+# ---------------------------------------------------------------- duality
+
+
+@pytest.mark.parametrize("mfac", [1.5, 0.3])   # both regimes of Eq. psi
+def test_weak_duality_random_r(mfac):
+    inst = _small(1)
+    lam0, lam2, M = _params(inst, mfac=mfac)
+    rng = np.random.default_rng(0)
+    X, y = inst.X, inst.y
+    for _ in range(200):
+        fix = datagen.random_fixings(inst.p, 1, rng, 5)[0]
+        r = y * rng.uniform(-1, 2) + rng.normal(0, 1, inst.n)
+        beta = rng.uniform(-M, M, inst.p)
+        beta[fix == relax.F0] = 0.0
+        d = relax.dual_value(X, y, r, fix, lam0, lam2, M)
+        pval = relax.primal_value(X, y, beta, fix, lam0, lam2, M)
+        assert d <= pval + 1e-12
+
+
+@pytest.mark.parametrize("mfac", [1.5, 0.3])
+def test_admm_matches_second_solver_and_strong_duality(mfac):
+    inst = _small(2)
+    lam0, lam2, M = _params(inst, mfac=mfac)
+    rng = np.random.default_rng(4)
+    data = admm.AdmmData(inst.X, inst.y, 1.0)
+    for _ in range(4):
+        fix = datagen.random_fixings(inst.p, 1, rng, 4)[0]
+        a = admm.solve_node(data, fix, lam0, lam2, M, tol=1e-12, max_iter=200000)
+        b, fb = pgd.solve_node(inst.X, inst.y, fix, lam0, lam2, M)
+        # strong duality at the ADMM optimum (Proposition 1.2, 1.3)
+        assert a.primal - a.dual <= 1e-9 * max(1.0, abs(a.primal))
+        # two independent algorithms reach the same relaxation value
+        assert a.primal == pytest.approx(fb, rel=1e-9, abs=1e-10)
+        # and the dual bound never exceeds the relaxation optimum
+        assert a.dual <= fb + 1e-10
+
+
+def test_woodbury_reading():
+    """b-update inverse: (1/rho)(I - X^T (X X^T + rho I)^{-1} X) is the inverse of
+    X^T X + rho I; the printed coefficient 1/rho^2 on the second term is not."""
+    rng = np.random.default_rng(5)
+    n, p, rho = 7, 19, 2.5
+    X = rng.normal(size=(n, p))
+    A = X.T @ X + rho * np.eye(p)
+    inner = np.linalg.inv(X @ X.T + rho * np.eye(n))
+    good = (np.eye(p) - X.T @ inner @ X) / rho
+    printed = np.eye(p) / rho - X.T @ inner @ X / rho**2
+    assert np.max(np.abs(good @ A - np.eye(p))) < 1e-12
+    assert np.max(np.abs(printed @ A - np.eye(p))) > 1e-2
+
+
+def test_admm_iteration_identity_u_equals_xb():
+    """With the exact b-update, X b = (X X^T + rho I)^{-1} X w (push-through identity)."""
+    inst = _small(3)
+    rho = 0.7
+    data = admm.AdmmData(inst.X, inst.y, rho)
+    rng = np.random.default_rng(6)
+    w = rng.normal(size=inst.p)
+    b = data.D @ w
+    U = np.linalg.solve(inst.X @ inst.X.T + rho * np.eye(inst.n), inst.X @ w)
+    assert np.max(np.abs(inst.X @ b - U)) < 1e-10
+
+
+# ---------------------------------------------------------------- upper bound
+
+
+@pytest.mark.parametrize("M", [10.0, 0.4, 0.15])   # box loose, binding, strongly binding
+def test_box_ridge_matches_library(M):
+    inst = _small(7, n=80, p=14, k=5)
+    X, y, lam2 = inst.X, inst.y, 0.02
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        S = np.sort(rng.choice(inst.p, size=int(rng.integers(1, 9)), replace=False))
+        b = ub.box_ridge(X, y, S, lam2, M)
+        A = np.vstack([X[:, S], np.sqrt(2 * lam2) * np.eye(len(S))])
+        rhs = np.concatenate([y, np.zeros(len(S))])
+        ref = lsq_linear(A, rhs, bounds=(-M, M), tol=1e-15, lsmr_tol=1e-15, max_iter=10000).x
+        assert ub.kkt_residual(X, y, S, lam2, M, b) < 1e-10
+        assert ub.u_value(X, y, S, lam2, b) <= ub.u_value(X, y, S, lam2, ref) + 1e-12
+        np.testing.assert_allclose(b, ref, atol=1e-7)
+        f = ub.fista_backtracking(X, y, S, lam2, M)
+        assert ub.u_value(X, y, S, lam2, f) == pytest.approx(ub.u_value(X, y, S, lam2, b), rel=1e-10)
+
+
+# ---------------------------------------------------------------- optimum
+
+
+def test_brute_force_two_features_by_hand():
+    """p = 2: enumerate the four supports by explicit formulas."""
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(10, 2))
+    y = rng.normal(size=10)
+    lam0, lam2, M = 0.3, 0.05, 100.0
+
+    def ridge_val(cols):
+        if not cols:
+            return 0.5 * y @ y
+        A = X[:, cols]
+        b = np.linalg.solve(A.T @ A + 2 * lam2 * np.eye(len(cols)), A.T @ y)
+        r = y - A @ b
+        return 0.5 * r @ r + lam2 * b @ b + lam0 * len(cols)
+
+    vals = {(): ridge_val([]), (0,): ridge_val([0]), (1,): ridge_val([1]), (0, 1): ridge_val([0, 1])}
+    best = min(vals, key=vals.get)
+    res = brute.solve(X, y, lam0, lam2, M)
+    assert res.support == best
+    assert res.objective == pytest.approx(vals[best], rel=1e-12)
+
+
+@pytest.mark.parametrize("frac", [0.5, 0.05, 0.005])
+def test_bnb_matches_brute_force_p16(frac):
+    inst = datagen.config_instance("c1_p16", 0)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    res = bnb.solve(inst.X, inst.y, lam0, lam2, M, gap=1e-9)
+    assert tuple(np.nonzero(res.beta)[0]) == br.support
+    assert res.ub == pytest.approx(br.objective, rel=1e-9)
+    # invariants: LB <= opt <= UB along the whole run
+    for _, U, L in res.history:
+        assert L <= br.objective * (1 + 1e-9) + 1e-12
+        assert U >= br.objective * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("K", [1, 4])
+def test_bnb_batched_selection_same_optimum(K):
+    inst = datagen.config_instance("c1_p16", 1)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = 0.02 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    res = bnb.solve(inst.X, inst.y, lam0, lam2, M, gap=1e-9, K=K)
+    assert tuple(np.nonzero(res.beta)[0]) == br.support
+
+
+def test_bnb_exact_with_loose_node_solves():
+    """Prop. 1.1: the dual bound holds for every r, so stopping ADMM early weakens
+    bounds but never loses the optimum.  Every node whose fixings keep the optimal
+    support feasible must report a bound below the optimum."""
+    inst = datagen.config_instance("c1_p16", 2)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = 0.02 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    res = bnb.solve(inst.X, inst.y, lam0, lam2, M, gap=1e-9, node_tol=1e-2, max_admm_iter=20)
+    assert tuple(np.nonzero(res.beta)[0]) == br.support
+    for _, U, L in res.history:
+        assert L <= br.objective * (1 + 1e-12)
+    opt = np.zeros(inst.p, dtype=bool)
+    opt[list(br.support)] = True
+    checked = 0
+    for fix, lbp, d in res.node_log:
+        if np.all(~opt[fix == relax.F0]) and np.all(opt[fix == relax.F1]):
+            assert d <= br.objective * (1 + 1e-12)
+            checked += 1
+    assert checked >= 1
+
+
+def test_orthonormal_design_closed_form():
+    """X^T X = I: the problem separates per coordinate (a textbook case)."""
+    rng = np.random.default_rng(10)
+    n, p = 40, 10
+    Q, _ = np.linalg.qr(rng.normal(size=(n, p)))
+    X = Q
+    y = X @ rng.normal(0, 1, p) * 0.8 + 0.1 * rng.normal(size=n)
+    lam0, lam2, M = 0.08, 0.05, 1.2
+    c = X.T @ y
+    # MIP optimum: beta_j = clip(c_j / (1 + 2 lam2), +-M) if its gain beats lam0
+    bj = np.clip(c / (1 + 2 * lam2), -M, M)
+    gain = c * bj - (0.5 + lam2) * bj * bj
+    keep = gain > lam0
+    opt = 0.5 * y @ y - np.sum(np.where(keep, gain - lam0, 0.0))
+    res = bnb.solve(X, y, lam0, lam2, M, gap=1e-10)
+    assert res.ub == pytest.approx(opt, rel=1e-10)
+    assert set(np.nonzero(res.beta)[0]) == set(np.nonzero(keep)[0])
+    # root relaxation: separable, min 1/2 (b - c_j)^2 + psi(b) solved coordinate-wise
+    # by the prox at rho = 1; checked against the independent second solver
+    fix = np.full(p, relax.FREE, dtype=np.int8)
+    bstar = relax.prox(c, fix, lam0, lam2, M, 1.0)
+    root = 0.5 * y @ y - 0.5 * c @ c + np.sum(0.5 * (bstar - c) ** 2 + relax.psi(bstar, fix, lam0, lam2, M))
+    _, fb = pgd.solve_node(X, y, fix, lam0, lam2, M)
+    assert root == pytest.approx(fb, rel=1e-10)
+
+
+def test_lambda0_zero_relaxation_is_box_ridge():
+    inst = _small(11)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2, 0.8)
+    fix = np.full(inst.p, relax.FREE, dtype=np.int8)
+    a = admm.solve_node(admm.AdmmData(inst.X, inst.y, 1.0), fix, 0.0, lam2, M, tol=1e-12, max_iter=100000)
+    obj, _ = ub.support_objective(inst.X, inst.y, np.arange(inst.p), 0.0, lam2, M)
+    assert a.dual == pytest.approx(obj, rel=1e-9)
+
+
+def test_leaf_relaxation_equals_support_value():
+    inst = _small(12)
+    lam0, lam2, M = _params(inst)
+    rng = np.random.default_rng(13)
+    fix = (rng.random(inst.p) < 0.4).astype(np.int8)  # every coordinate fixed
+    a = admm.solve_node(admm.AdmmData(inst.X, inst.y, 1.0), fix, lam0, lam2, M, tol=1e-12, max_iter=100000)
+    S = np.nonzero(fix == relax.F1)[0]
+    b = ub.box_ridge(inst.X, inst.y, S, lam2, M)
+    leaf = ub.u_value(inst.X, inst.y, S, lam2, b) + lam0 * len(S)
+    assert a.dual == pytest.approx(leaf, rel=1e-9)
+
+
+def test_child_relaxations_dominate_parent():
+    inst = _small(14)
+    lam0, lam2, M = _params(inst, frac=0.02)
+    fix = np.full(inst.p, relax.FREE, dtype=np.int8)
+    _, parent = pgd.solve_node(inst.X, inst.y, fix, lam0, lam2, M)
+    for j in (0, 3, 7):
+        for v in (relax.F0, relax.F1):
+            child = fix.copy()
+            child[j] = v
+            _, cv = pgd.solve_node(inst.X, inst.y, child, lam0, lam2, M)
+            assert cv >= parent - 1e-10
+
+
+def test_datagen_toeplitz_recipe():
+    rng = np.random.default_rng(0)
+    X = datagen.toeplitz_design(4000, 6, 0.6, rng)
+    assert X.flags.f_contiguous
+    np.testing.assert_array_equal(X, X.astype(np.float32).astype(np.float64))
+    np.testing.assert_allclose(np.linalg.norm(X, axis=0), 1.0, atol=1e-6)
+    C = np.corrcoef(X, rowvar=False)
+    for lag in range(1, 4):
+        assert np.mean(np.diag(C, lag)) == pytest.approx(0.6 ** lag, abs=0.04)
+    assert list(datagen.true_support(50, 5)) == [0, 10, 20, 30, 40]
