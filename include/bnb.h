@@ -1,0 +1,181 @@
+/*
+ * bnb.h -- C ABI of the B300 (sm_103a) l0-l2 branch-and-bound library.
+ *
+ * Problem (Eq. original, Eq. perspective of arxiv 2602.04551):
+ *     min_beta 1/2 ||y - X beta||^2 + lambda0 ||beta||_0 + lambda2 ||beta||^2,
+ *     |beta_i| <= M  (big-M of the perspective formulation, Section 2.1).
+ *
+ * Conventions
+ *   - Every function returns an int status: BNB_OK (0) or a negative BNB_E*
+ *     code.  No function aborts or exits.  bnb_last_error() gives a message.
+ *   - X is column-major: element (i, j) (sample i, feature j) at X[i + j*n].
+ *   - Node fixings are int8 rows of length p: -1 free, 0 fixed to zero
+ *     (z_i = 0, the set F0), 1 fixed to one (z_i = 1, the set F1).
+ *   - Batched node arrays are node-major: row k of a K x p array is node k.
+ *   - Host-pointer entry points copy inputs in and results out (the copies are
+ *     part of the call); *_device entry points take device pointers on the
+ *     handle's device and stream.  Output buffers are owned by the caller.
+ *   - A handle owns all device memory it allocates; it is not thread-safe.
+ *     Distinct handles are independent and may run on different streams.
+ *   - Objective values follow Eq. original; every lower bound returned is an
+ *     FP64 dual bound of Proposition 1 evaluated on the caller's data, so it
+ *     is valid whatever the precision of the ADMM iterations.
+ */
+#ifndef BNB_H
+#define BNB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BNB_OK 0
+#define BNB_EINVAL (-1)   /* bad argument (sizes, lambdas, M, options) */
+#define BNB_ENOMEM (-2)   /* device allocation failed */
+#define BNB_ECUDA (-3)    /* a CUDA call failed (message in bnb_last_error) */
+#define BNB_ETIMEOUT (-4) /* time limit reached inside a call */
+#define BNB_EQUEUE (-5)   /* node pool capacity reached */
+#define BNB_ENODEV (-6)   /* no CUDA device / not an sm_103 device */
+
+/* ADMM arithmetic of the node solves (certificates and polish are FP64 always) */
+#define BNB_PREC_FP64 0   /* plain FP64 everywhere: the comparator path */
+#define BNB_PREC_FP32 1   /* FP32 state and contractions */
+#define BNB_PREC_BF16 2   /* BF16 X on tcgen05 tensor cores, FP32 accumulate/state */
+
+/* bnb_solve status */
+#define BNB_STATUS_OPTIMAL 0     /* open-node set exhausted: UB is optimal */
+#define BNB_STATUS_GAP 1         /* (UB - LB) / UB <= requested gap */
+#define BNB_STATUS_TIME_LIMIT 2
+#define BNB_STATUS_QUEUE_FULL 3
+#define BNB_STATUS_NODE_LIMIT 4
+
+typedef struct bnb_handle bnb_handle;
+
+typedef struct {
+  double M;              /* big-M bound, > 0 (required: no default) */
+  double rho;            /* ADMM penalty (Eq. ADMM2), default 1.0 */
+  double node_tol;       /* relative primal-dual gap to stop a node solve, default 1e-4 */
+  int max_admm_iter;     /* ADMM iteration cap per node visit, default 400 */
+  int check_every;       /* ADMM iterations between stop tests (one "round"), default 10 */
+  int batch_K;           /* node slots solved together, default 512 */
+  int precision;         /* BNB_PREC_*, default BNB_PREC_FP32 */
+  int use_graphs;        /* capture each round in a CUDA graph, default 1 */
+  double time_limit_s;   /* bnb_solve wall-clock limit, default 3600 */
+  long long max_nodes;   /* bnb_solve node limit, default 1e9 */
+  long long queue_capacity; /* open-node pool capacity, default 1<<20 */
+  long long warm_capacity;  /* warm-start store entries (parent beta, v), default auto */
+  int support_max;       /* largest candidate support for the upper bound, default 200 */
+  int ub_max_iter;       /* projected-gradient iterations per candidate, default 200 */
+  int device;            /* CUDA device ordinal, default 0 */
+  void* stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle */
+} bnb_options;
+
+/* Fill *opt with defaults (M is set to 0: the caller must set it). */
+int bnb_options_default(bnb_options* opt);
+
+/*
+ * Create a solve handle (setup, §8 row R0): copies X (n x p, column-major,
+ * FP64 host array) and y (n) to the device, keeps X in FP64 (certificates,
+ * polish) and in the ADMM precision, forms c = X^T y and the inverse of
+ * G = X X^T + rho I (b-update of Eq. b_update via the Woodbury identity,
+ * Section 3.1.2, with the 1/rho coefficient).  lambda0 >= 0, lambda2 > 0.
+ * On success *out owns all device memory; release it with bnb_destroy.
+ */
+int bnb_create(const double* X_colmajor, const double* y, int n, int p,
+               double lambda0, double lambda2, const bnb_options* opt,
+               bnb_handle** out);
+
+/* Same as bnb_create with X and y already on the device (FP64, column-major).
+ * The data are copied; the caller's buffers may be freed after the call. */
+int bnb_create_device(const double* dX_colmajor, const double* dy, int n, int p,
+                      double lambda0, double lambda2, const bnb_options* opt,
+                      bnb_handle** out);
+
+/*
+ * Batched node relaxation (Sections 3.1-3.2; Eqs. batched_b_update ..
+ * batched_v_update; dual bound of Proposition 1).
+ *   K            number of nodes, 1 <= K <= opt.batch_K
+ *   fix          K x p int8 fixings (host)
+ *   warm_beta    K x p FP32 warm start for beta, or NULL (zeros)
+ *   warm_v       K x p FP32 warm start for the ADMM dual v, or NULL (zeros)
+ *   max_iter     ADMM iterations cap (<= 0: opt.max_admm_iter)
+ * Outputs (host, any may be NULL except lb):
+ *   lb           K certified FP64 lower bounds D(r), r = y - X b
+ *   beta_out     K x p final beta
+ *   v_out        K x p final v
+ *   z_out        K x p relaxed z (Appendix A.1 recovery)
+ *   branch_idx   K most-fractional free index (-1: no free index)
+ *   node_gap     K FP32-estimated relative primal-dual gap at exit
+ *   iters        K ADMM iterations run
+ */
+int bnb_relax_batch(bnb_handle* h, int K, const int8_t* fix, const float* warm_beta,
+                    const float* warm_v, int max_iter, double* lb, float* beta_out,
+                    float* v_out, float* z_out, int* branch_idx, double* node_gap, int* iters);
+
+/* Device-pointer form of bnb_relax_batch (all pointers on the handle's device;
+ * runs asynchronously on the handle's stream; outputs valid after a sync). */
+int bnb_relax_batch_device(bnb_handle* h, int K, const int8_t* fix, const float* warm_beta,
+                           const float* warm_v, int max_iter, double* lb, float* beta_out,
+                           float* v_out, float* z_out, int* branch_idx, double* node_gap,
+                           int* iters);
+
+/*
+ * FP64 dual bound of Proposition 1 for caller-supplied residuals:
+ *   lb[k] = -1/2 ||r_k||^2 + y^T r_k - sum_i nu_i(|X_i^T r_k|)   (Eqs. dual, nudef)
+ * with the fixings of row k.  r is K x n FP64 (host), node-major.
+ */
+int bnb_dual_bound(bnb_handle* h, int K, const int8_t* fix, const double* r, double* lb);
+
+/*
+ * Batched upper bound (Sections 3.3-3.4, Eq. upperboundbeta): for each of K
+ * supports (K x p uint8 mask, host), projected gradient with t/(t+3)
+ * extrapolation and Armijo backtracking in the ADMM precision, then an FP64
+ * re-solve of the box ridge on the support (exact active set).  Returns
+ *   ub[k]        FP64 objective of Eq. original at the FP64 solution (lambda0
+ *                counted once per nonzero)
+ *   beta_out     K x p FP64 solutions (or NULL)
+ * Supports larger than opt.support_max return ub = +inf.
+ */
+int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, double* ub, double* beta_out);
+
+/*
+ * Full branch-and-bound (Algorithm 1 with a device-resident node pool,
+ * continuous slot refill, best-first selection, branching on the most
+ * fractional z_i, pruning when LB >= UB (1 - rel_gap)).
+ *   beta_out   p FP64 incumbent (host, may be NULL)
+ *   ub, lb     final global bounds
+ *   nodes      nodes solved
+ *   status     BNB_STATUS_*
+ */
+int bnb_solve(bnb_handle* h, double rel_gap, double* beta_out, double* ub, double* lb,
+              long long* nodes, int* status);
+
+typedef struct {
+  long long nodes;          /* nodes solved (retired with an FP64 certificate) */
+  long long rounds;         /* device rounds run */
+  long long admm_iters;     /* ADMM batch iterations run */
+  long long slot_iters;     /* sum over nodes of ADMM iterations */
+  long long pruned;         /* nodes closed by their bound */
+  long long ub_polished;    /* FP64 polishes of candidate incumbents */
+  long long pool_peak;      /* largest open-node count */
+  int max_depth;
+  double solve_seconds;     /* wall time of the last bnb_solve */
+  double setup_seconds;     /* wall time of bnb_create */
+  double final_ub, final_lb;
+} bnb_stats;
+
+int bnb_get_stats(const bnb_handle* h, bnb_stats* out);
+
+/* Message of the last failed call on h (or of the last failed create when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char* bnb_last_error(const bnb_handle* h);
+
+/* Release every device resource of h (NULL is accepted). */
+void bnb_destroy(bnb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BNB_H */

@@ -1,0 +1,119 @@
+// engine.cuh -- device workspace of one solve handle and the stage launchers.
+//
+// One handle = one design matrix X (n x p) shared by every node of the tree
+// (Section 3.2: one copy of X, c = X^T y and the b-update operator for all
+// nodes), K node slots whose ADMM state is held node-major in HBM, a device
+// node pool for the open nodes, and the incumbent.
+//
+// Template parameter R is the arithmetic of the ADMM state and contractions
+// (float for the mixed-precision path, double for the plain FP64 comparator).
+// Certificates (Proposition 1) and upper-bound polishing are FP64 for both.
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+namespace bnb {
+
+constexpr int DMAX = 128;       // deepest node (fixings kept per open node)
+constexpr int SEL_BINS = 2048;  // radix-select histogram width
+
+struct Status {                 // copied to the host after every round
+  double ub, lb;
+  long long pool_count;         // open nodes in the pool
+  int active_slots;
+  int retired;                  // nodes retired this round
+  int pruned;                   // nodes closed this round
+  int polished;
+  int free_top;                 // free pool entries
+  int warm_free;
+  int error;                    // 1: depth limit reached (node kept as lost bound)
+  int max_depth;
+  double lost_lb;
+};
+
+template <class R>
+struct Engine {
+  Prob P{};
+  int n = 0, p = 0, K = 0;
+  int smax = 200, ub_iters = 200;
+  int s1 = 1, s2 = 1;           // split-K depth of the X W^T and G^-1 T products
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+
+  // problem data
+  double *X64 = nullptr, *y64 = nullptr, *c64 = nullptr, *xnorm = nullptr;
+  float* X32 = nullptr;         // FP32 copy (certificate screen)
+  R *XR = nullptr, *yR = nullptr, *cR = nullptr, *Ginv = nullptr;
+  double yy = 0.0;              // y^T y
+
+  // ADMM state, node-major K x p
+  R *beta = nullptr, *V = nullptr;
+  int8_t* fix = nullptr;
+  R *Tpart = nullptr, *T = nullptr, *Upart = nullptr, *U = nullptr;   // n x K (+ splits)
+  R *XBpart = nullptr;          // check product X beta^T partials
+  R* g3part = nullptr;          // [4][nbm3][K] per-block stats of the fused epilogue
+  int nbm3 = 0;
+  R* rstat = nullptr;           // [2][K]  ||y - U||^2, y^T (y - U)
+
+  // slots
+  int *slot_active = nullptr, *slot_iters = nullptr, *slot_depth = nullptr, *slot_nfix = nullptr;
+  int* slot_fixl = nullptr;     // K x DMAX encoded fixings (idx << 1 | dir)
+  double *slot_lbp = nullptr, *slot_gap = nullptr, *slot_dual = nullptr, *slot_primal = nullptr;
+  int* slot_retire = nullptr;
+  int *ret_slot = nullptr, *ret_active = nullptr, *ret_count = nullptr;
+
+  // certificate
+  double *r64 = nullptr, *cert_rr = nullptr, *cert_yr = nullptr, *cert_rn = nullptr;
+  double *cert_lb = nullptr, *node_lb = nullptr;
+  R* rS = nullptr;              // residual in screen precision, K x n
+  float* gscr = nullptr;        // screened X_i^T r, K x p
+  uint8_t* cflag = nullptr;     // K x p: coordinate needs the exact FP64 term
+  int* flist = nullptr;         // K x p flagged index lists
+
+  // branching / upper bound
+  int *br_idx = nullptr, *sup_cnt = nullptr, *sup = nullptr, *nfree = nullptr;
+  R *Qg = nullptr, *qv = nullptr, *ubb = nullptr;   // K x smax^2, K x smax, K x smax
+  double *Q64 = nullptr, *L64 = nullptr, *ubb64 = nullptr, *ub_val = nullptr;
+  int* pol_flag = nullptr;
+  double* inc_beta = nullptr;   // p, FP64 incumbent
+  double* inc_ub = nullptr;     // scalar
+  float* zbuf = nullptr;        // K x p (relax outputs)
+
+  // node pool
+  long long qcap = 0, wcap = 0;
+  double* pool_lb = nullptr;
+  unsigned* pool_key = nullptr;
+  uint8_t* pool_valid = nullptr;
+  int *pool_depth = nullptr, *pool_warm = nullptr, *pool_fix = nullptr;
+  int *free_stack = nullptr, *free_top = nullptr, *pool_hw = nullptr;
+  R *warm_beta = nullptr, *warm_V = nullptr;
+  int *warm_ref = nullptr, *warm_stack = nullptr, *warm_top = nullptr;
+  unsigned* sel = nullptr;      // [3][SEL_BINS] histograms + scalars
+  int* sel_state = nullptr;     // see queue.cu
+  int *popped = nullptr, *free_slots = nullptr;
+  unsigned long long* poolmin = nullptr;
+  Status* status_d = nullptr;
+  Status* status_h = nullptr;   // pinned host mirror
+  double* params_d = nullptr;   // [0] gap target used by pruning
+
+  // counters (host)
+  long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;
+  long long slot_iters_sum = 0;
+  int max_depth = 0;
+};
+
+// ---- stage launchers (all asynchronous on e.st) ----
+template <class R> int setup_data(Engine<R>& e, const double* dX, const double* dy);
+template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol,
+                                  bool use_incumbent);
+template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */);
+template <class R> int branch_support(Engine<R>& e, bool write_z);
+template <class R> int upper_bound(Engine<R>& e, bool force_polish);
+template <class R> int queue_push(Engine<R>& e);
+template <class R> int queue_select_refill(Engine<R>& e);
+template <class R> int queue_init(Engine<R>& e);
+template <class R> int queue_status(Engine<R>& e);
+template <class R> int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K);
+
+}  // namespace bnb

@@ -1,0 +1,228 @@
+// setup.cu -- one-time per-tree setup (not part of the node loop).
+//
+// Forms the data every node shares (Section 3.2, "shared memory reference"):
+//   c = X^T y (FP64), column norms ||X_i|| (FP64, certificate error bound),
+//   X in FP32, and the inverse of G = X X^T + rho I_n used by the b-update
+//   b = D w with D = (1/rho)(I - X^T G^{-1} X)  (Eq. b_update; Woodbury form of
+//   Section 3.1.2 with the 1/rho coefficient that makes D (X^T X + rho I) = I).
+// G is built in FP64 on CUDA cores; G^{-1} by the Newton-Schulz iteration
+// Z <- Z (2I - G Z) (Schulz 1933), started at Z = I / g with g >= lambda_max(G)
+// from Gershgorin's bound, so that ||I - G Z_0|| = 1 - rho/g < 1 and the error
+// squares every step.  The iteration runs in FP32 and, for the FP64 path, two
+// more steps in FP64.
+#include <cmath>
+#include <cstring>
+#include "engine.cuh"
+#include "gemm_simt.cuh"
+
+namespace bnb {
+
+__global__ void k_cast_d2f(const double* __restrict__ a, float* __restrict__ b, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void k_cast_f2d(const float* __restrict__ a, double* __restrict__ b, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void k_copy_d(const double* __restrict__ a, double* __restrict__ b, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// c_j = X_j^T y and ||X_j||_2 in FP64, one warp per column
+__global__ void k_colstats(const double* __restrict__ X, const double* __restrict__ y, int n, int p,
+                           double* __restrict__ c, double* __restrict__ nrm) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= p) return;
+  const double* col = X + (long long)warp * n;
+  double s = 0.0, q = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    double x = col[i];
+    s = fma(x, y[i], s);
+    q = fma(x, x, q);
+  }
+  s = warp_sum(s);
+  q = warp_sum(q);
+  if (lane == 0) {
+    c[warp] = s;
+    nrm[warp] = sqrt(q);
+  }
+}
+
+__global__ void k_dot_self(const double* __restrict__ y, int n, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(y[i], y[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_add_diag(double* G, int n, double v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) G[(long long)i * n + i] += v;
+}
+
+// Gershgorin: max_i sum_j |G_ij| (G symmetric), one warp per row
+__global__ void k_gershgorin(const double* __restrict__ G, int n, unsigned long long* out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += fabs(G[(long long)warp * n + j]);
+  s = warp_sum(s);
+  if (lane == 0) atomicMax(out, dkey(s));
+}
+
+template <class T>
+__global__ void k_scaled_identity(T* Z, int n, double a) {
+  long long m = (long long)n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    Z[i] = (i % (n + 1) == 0) ? (T)a : T(0);
+}
+
+template <class T>
+__global__ void k_symmetrize(const T* __restrict__ Z, T* __restrict__ out, int n) {
+  long long m = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < m;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(idx % n), j = (int)(idx / n);
+    out[idx] = (T)0.5 * (Z[idx] + Z[(long long)i * n + j]);
+  }
+}
+
+// C = 2 Z - acc  (second half of a Newton-Schulz step)
+template <typename T>
+struct EpiSchulz {
+  const T* __restrict__ Z;
+  T* __restrict__ C;
+  int ld;
+  template <int TM, int TN, int TX, int TY>
+  __device__ __forceinline__ void apply(T (&acc)[TM][TN], int m0, int n0, int tm, int tn, int M,
+                                        int N) const {
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int c = n0 + tn + j * TY;
+      if (c >= N) continue;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        int r = m0 + tm + i * TX;
+        if (r < M) {
+          long long o = r + (long long)c * ld;
+          C[o] = T(2) * Z[o] - acc[i][j];
+        }
+      }
+    }
+  }
+};
+
+static inline int grid_for(long long m, int bs = 256) {
+  long long g = (m + bs - 1) / bs;
+  return (int)(g > 148 * 32 ? 148 * 32 : (g < 1 ? 1 : g));
+}
+
+template <class T>
+static int schulz_steps(cudaStream_t st, const T* G, T* Z, T* Y, T* Z2, int n, int steps) {
+  for (int s = 0; s < steps; ++s) {
+    // Y = G Z
+    BNB_CUDA_OK((gemm_simt<T, false, false>(st, G, n, n, n, n, 1, nullptr, BPlainK<T>{Z, n},
+                                            EpiStore<T>{Y, n, 0})));
+    // Z2 = 2 Z - Z Y
+    BNB_CUDA_OK((gemm_simt<T, false, false>(st, Z, n, n, n, n, 1, nullptr, BPlainK<T>{Y, n},
+                                            EpiSchulz<T>{Z, Z2, n})));
+    BNB_CUDA_OK(cudaMemcpyAsync(Z, Z2, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+  }
+  return 0;
+}
+
+template <class R>
+int setup_data(Engine<R>& e, const double* dX, const double* dy) {
+  const int n = e.n, p = e.p;
+  const long long np = (long long)n * p;
+  cudaStream_t st = e.st;
+  BNB_CUDA_OK(cudaMemcpyAsync(e.X64, dX, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+  BNB_CUDA_OK(cudaMemcpyAsync(e.y64, dy, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  k_cast_d2f<<<grid_for(np), 256, 0, st>>>(e.X64, e.X32, np);
+  k_colstats<<<(p * 32 + 255) / 256, 256, 0, st>>>(e.X64, e.y64, n, p, e.c64, e.xnorm);
+  double* yy_d = e.Q64;  // scratch scalar
+  k_dot_self<<<1, 256, 0, st>>>(e.y64, n, yy_d);
+  BNB_CUDA_OK(cudaGetLastError());
+  BNB_CUDA_OK(cudaMemcpyAsync(&e.yy, yy_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if constexpr (sizeof(R) == 4) {
+    k_cast_d2f<<<grid_for(n), 256, 0, st>>>(e.y64, (float*)e.yR, n);
+    k_cast_d2f<<<grid_for(p), 256, 0, st>>>(e.c64, (float*)e.cR, p);
+  } else {
+    k_copy_d<<<grid_for(n), 256, 0, st>>>(e.y64, (double*)e.yR, n);
+    k_copy_d<<<grid_for(p), 256, 0, st>>>(e.c64, (double*)e.cR, p);
+  }
+  BNB_CUDA_OK(cudaGetLastError());
+
+  // G = X X^T + rho I in FP64
+  const long long nn = (long long)n * n;
+  double *G = nullptr, *Z64 = nullptr, *Y64 = nullptr, *W64 = nullptr;
+  float *G32 = nullptr, *Z32 = nullptr, *Y32 = nullptr, *W32 = nullptr;
+  unsigned long long* gk = nullptr;
+  BNB_CUDA_OK(cudaMallocAsync(&G, sizeof(double) * nn, st));
+  BNB_CUDA_OK(cudaMallocAsync(&gk, sizeof(unsigned long long), st));
+  BNB_CUDA_OK((gemm_simt<double, false, true>(st, e.X64, n, n, n, p, 1, nullptr,
+                                              BPlainN<double>{e.X64, n},
+                                              EpiStore<double>{G, n, 0})));
+  k_add_diag<<<(n + 255) / 256, 256, 0, st>>>(G, n, e.P.rho);
+  BNB_CUDA_OK(cudaMemsetAsync(gk, 0, sizeof(unsigned long long), st));
+  k_gershgorin<<<(n * 32 + 255) / 256, 256, 0, st>>>(G, n, gk);
+  BNB_CUDA_OK(cudaGetLastError());
+  unsigned long long gkey = 0;
+  BNB_CUDA_OK(cudaMemcpyAsync(&gkey, gk, sizeof(gkey), cudaMemcpyDeviceToHost, st));
+  BNB_CUDA_OK(cudaStreamSynchronize(st));
+  // decode the order-preserving key on the host
+  unsigned long long u = (gkey & 0x8000000000000000ull) ? (gkey & 0x7fffffffffffffffull) : ~gkey;
+  double gmax;
+  memcpy(&gmax, &u, sizeof(double));
+  const double e0 = 1.0 - e.P.rho / gmax;  // ||I - G/g|| bound
+  int steps = 1;
+  if (e0 > 0.0) steps = (int)std::ceil(std::log2(std::log(1e-9) / std::log(e0))) + 3;
+  if (steps < 3) steps = 3;
+  if (steps > 80) steps = 80;
+
+  BNB_CUDA_OK(cudaMallocAsync(&G32, sizeof(float) * nn, st));
+  BNB_CUDA_OK(cudaMallocAsync(&Z32, sizeof(float) * nn, st));
+  BNB_CUDA_OK(cudaMallocAsync(&Y32, sizeof(float) * nn, st));
+  BNB_CUDA_OK(cudaMallocAsync(&W32, sizeof(float) * nn, st));
+  k_cast_d2f<<<grid_for(nn), 256, 0, st>>>(G, G32, nn);
+  k_scaled_identity<float><<<grid_for(nn), 256, 0, st>>>(Z32, n, 1.0 / gmax);
+  BNB_CUDA_OK(cudaGetLastError());
+  if (int rc = schulz_steps<float>(st, G32, Z32, Y32, W32, n, steps)) return rc;
+  if constexpr (sizeof(R) == 4) {
+    k_symmetrize<float><<<grid_for(nn), 256, 0, st>>>(Z32, (float*)e.Ginv, n);
+  } else {
+    BNB_CUDA_OK(cudaMallocAsync(&Z64, sizeof(double) * nn, st));
+    BNB_CUDA_OK(cudaMallocAsync(&Y64, sizeof(double) * nn, st));
+    BNB_CUDA_OK(cudaMallocAsync(&W64, sizeof(double) * nn, st));
+    k_cast_f2d<<<grid_for(nn), 256, 0, st>>>(Z32, Z64, nn);
+    BNB_CUDA_OK(cudaGetLastError());
+    if (int rc = schulz_steps<double>(st, G, Z64, Y64, W64, n, 3)) return rc;
+    k_symmetrize<double><<<grid_for(nn), 256, 0, st>>>(Z64, (double*)e.Ginv, n);
+  }
+  BNB_CUDA_OK(cudaGetLastError());
+  BNB_CUDA_OK(cudaFreeAsync(G, st));
+  BNB_CUDA_OK(cudaFreeAsync(gk, st));
+  BNB_CUDA_OK(cudaFreeAsync(G32, st));
+  BNB_CUDA_OK(cudaFreeAsync(Z32, st));
+  BNB_CUDA_OK(cudaFreeAsync(Y32, st));
+  BNB_CUDA_OK(cudaFreeAsync(W32, st));
+  if (Z64) {
+    BNB_CUDA_OK(cudaFreeAsync(Z64, st));
+    BNB_CUDA_OK(cudaFreeAsync(Y64, st));
+    BNB_CUDA_OK(cudaFreeAsync(W64, st));
+  }
+  BNB_CUDA_OK(cudaStreamSynchronize(st));
+  return 0;
+}
+
+template int setup_data<float>(Engine<float>&, const double*, const double*);
+template int setup_data<double>(Engine<double>&, const double*, const double*);
+
+}  // namespace bnb
