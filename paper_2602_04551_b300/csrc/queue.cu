@@ -1,0 +1,460 @@
+// queue.cu -- device-resident open-node pool with best-first selection.
+//
+// Section 2.2.1 / Algorithm 1: nodes are (F0, F1, LB of the parent); the batch
+// is the min(K_free, |N|) open nodes of smallest LB; a node whose LB reaches
+// UB (1 - gap) is pruned; a branched node adds (F0 + {j}, F1) and (F0, F1 + {j}),
+// both carrying the parent's LB.  Warm start (Section 3.1.3): both children
+// take the parent's final (beta, v); the F0 child sets beta_j = 0.
+//
+// Layout: struct-of-arrays records in a pool of fixed capacity; free entries
+// on a stack (allocation only in k_push, release only in the selection
+// kernels, so no kernel both pops and pushes).  Each record stores its fixings
+// as a list of (index << 1 | value) of length depth.  Parent (beta, v) rows go
+// to a reference-counted warm store; when it is full the children start cold
+// (beta = v = 0), which changes iteration counts but never a bound.
+//
+// Selection keys are the node LB rounded down to FP32 and made order-preserving
+// as unsigned integers; an exact 3-pass radix select (11 + 11 + 10 bits) finds
+// the threshold key, ties at the threshold are taken in arbitrary order.
+#include <cfloat>
+#include "engine.cuh"
+
+namespace bnb {
+
+// sel_state slots
+enum {
+  SS_TAKE_ALL = 0, SS_F = 1, SS_PREFIX = 2, SS_NEED = 3, SS_LESS = 4, SS_TAU = 5, SS_EQ = 6,
+  SS_OUT = 7, SS_POLISHED = 8, SS_PRUNED = 9, SS_COUNT = 10, SS_ERROR = 11, SS_MAXDEPTH = 12,
+  SS_WORDS = 16
+};
+
+__device__ __forceinline__ void warm_release(int w, int* warm_ref, int* warm_stack, int* warm_top) {
+  if (w >= 0 && atomicSub(&warm_ref[w], 1) == 1) warm_stack[atomicAdd(warm_top, 1)] = w;
+}
+
+__global__ void k_queue_init(long long qcap, long long wcap, int* free_stack, int* free_top,
+                             int* pool_hw, int* warm_stack, int* warm_top, uint8_t* pool_valid,
+                             double* pool_lb, unsigned* pool_key, int* pool_depth, int* pool_warm,
+                             double* inc_ub, double ub0) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < qcap;
+       t += (long long)gridDim.x * blockDim.x) {
+    free_stack[t] = (int)(qcap - 1 - t);
+    pool_valid[t] = 0;
+  }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < wcap;
+       t += (long long)gridDim.x * blockDim.x)
+    warm_stack[t] = (int)(wcap - 1 - t);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *free_top = (int)qcap - 1;  // entry 0 goes to the root
+    *warm_top = (int)wcap;
+    *pool_hw = 1;
+    pool_valid[0] = 1;
+    pool_lb[0] = -INFINITY;
+    pool_key[0] = fkey(-INFINITY);
+    pool_depth[0] = 0;
+    pool_warm[0] = -1;
+    inc_ub[0] = ub0;
+  }
+}
+
+// Prune or branch each retired node (one block per retired node).
+template <class R>
+__global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+                       const double* __restrict__ node_lb, const int* __restrict__ br_idx,
+                       const double* __restrict__ inc_ub, const double* __restrict__ params,
+                       const int* __restrict__ slot_depth, const int* __restrict__ slot_fixl,
+                       const R* __restrict__ beta, const R* __restrict__ V, int* free_stack,
+                       int* free_top, int* pool_hw, uint8_t* pool_valid, double* pool_lb,
+                       unsigned* pool_key, int* pool_depth, int* pool_warm, int* pool_fix,
+                       R* warm_beta, R* warm_V, int* warm_ref, int* warm_stack, int* warm_top,
+                       int* sel_state, unsigned long long* poolmin, unsigned long long* lost_key) {
+  __shared__ int c0, c1, wslot, decision;
+  const int q = blockIdx.x;
+  if (q >= *ret_count) return;
+  const int slot = ret_slot[q];
+  const int d = slot_depth[slot];
+  const double lbu = node_lb[q];
+  const int j = br_idx[q];
+  if (threadIdx.x == 0) {
+    const double thr = inc_ub[0] * (1.0 - params[0]);
+    decision = 0;
+    if (lbu >= thr || j < 0) {
+      atomicAdd(&sel_state[SS_PRUNED], 1);
+    } else if (d + 1 > DMAX) {
+      atomicOr(&sel_state[SS_ERROR], 1);
+      atomicMin(lost_key, dkey(lbu));
+    } else {
+      decision = 1;
+      const int t = atomicSub(free_top, 2);
+      c0 = free_stack[t - 1];
+      c1 = free_stack[t - 2];
+      atomicMax(pool_hw, (c0 > c1 ? c0 : c1) + 1);
+      const int wt = atomicSub(warm_top, 1);
+      if (wt > 0) {
+        wslot = warm_stack[wt - 1];
+        warm_ref[wslot] = 2;
+      } else {
+        atomicAdd(warm_top, 1);
+        wslot = -1;
+      }
+      const unsigned key = fkey(__double2float_rd(lbu));
+      pool_lb[c0] = lbu;
+      pool_lb[c1] = lbu;
+      pool_key[c0] = key;
+      pool_key[c1] = key;
+      pool_depth[c0] = d + 1;
+      pool_depth[c1] = d + 1;
+      pool_warm[c0] = wslot;
+      pool_warm[c1] = wslot;
+      atomicMax(&sel_state[SS_MAXDEPTH], d + 1);
+      // the children are open nodes for this round's global lower bound
+      atomicMin(poolmin, dkey(lbu));
+      atomicAdd(&sel_state[SS_COUNT], 2);
+    }
+  }
+  __syncthreads();
+  if (!decision) return;
+  for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    const int e = slot_fixl[(long long)slot * DMAX + t];
+    pool_fix[(long long)c0 * DMAX + t] = e;
+    pool_fix[(long long)c1 * DMAX + t] = e;
+  }
+  if (threadIdx.x == 0) {
+    pool_fix[(long long)c0 * DMAX + d] = (j << 1) | 0;
+    pool_fix[(long long)c1 * DMAX + d] = (j << 1) | 1;
+  }
+  if (wslot >= 0) {
+    const long long so = (long long)slot * p, wo = (long long)wslot * p;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      warm_beta[wo + i] = beta[so + i];
+      warm_V[wo + i] = V[so + i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pool_valid[c0] = 1;
+    pool_valid[c1] = 1;
+  }
+}
+
+__global__ void k_sel_reset(unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+  for (int t = threadIdx.x; t < 3 * SEL_BINS; t += blockDim.x) hist[t] = 0;
+  if (threadIdx.x == 0) {
+    sel_state[SS_TAKE_ALL] = 0;
+    sel_state[SS_PREFIX] = 0;
+    sel_state[SS_NEED] = 0;
+    sel_state[SS_LESS] = 0;
+    sel_state[SS_TAU] = 0;
+    sel_state[SS_EQ] = 0;
+    sel_state[SS_OUT] = 0;
+    sel_state[SS_COUNT] = 0;
+    *poolmin = ~0ull;
+  }
+}
+
+// pass 1: drop prunable entries, count, min LB, histogram of the top 11 key bits
+__global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid,
+                            const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
+                            const int* __restrict__ pool_warm, int* free_stack, int* free_top,
+                            int* warm_ref, int* warm_stack, int* warm_top,
+                            const double* __restrict__ inc_ub, const double* __restrict__ params,
+                            unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+  __shared__ unsigned sh[SEL_BINS];
+  for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
+  __syncthreads();
+  const int hw = *pool_hw;
+  const double thr = inc_ub[0] * (1.0 - params[0]);
+  int cnt = 0;
+  unsigned long long mn = ~0ull;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+    if (!pool_valid[i]) continue;
+    const double lb = pool_lb[i];
+    if (lb >= thr) {
+      pool_valid[i] = 0;
+      free_stack[atomicAdd(free_top, 1)] = i;
+      warm_release(pool_warm[i], warm_ref, warm_stack, warm_top);
+      atomicAdd(&sel_state[SS_PRUNED], 1);
+      continue;
+    }
+    ++cnt;
+    const unsigned long long k = dkey(lb);
+    mn = k < mn ? k : mn;
+    atomicAdd(&sh[pool_key[i] >> 21], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x)
+    if (sh[t]) atomicAdd(&hist[t], sh[t]);
+  if (cnt) atomicAdd(&sel_state[SS_COUNT], cnt);
+  if (mn != ~0ull) atomicMin(poolmin, mn);
+}
+
+// level-L scan (single block).  Level 1 also lists the free slots in order.
+__global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* sel_state, int K,
+                           const int* __restrict__ slot_active, int* free_slots) {
+  __shared__ int wcnt[32];
+  __shared__ int base;
+  if (level == 1) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int s0 = 0; s0 < K; s0 += blockDim.x) {
+      const int s = s0 + threadIdx.x;
+      const int f = (s < K) ? !slot_active[s] : 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) wcnt[w] = __popc(bal);
+      __syncthreads();
+      int off = base;
+      for (int t = 0; t < w; ++t) off += wcnt[t];
+      if (f) free_slots[off + __popc(bal & ((1u << lane) - 1u))] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int t = 0; t < nw; ++t) tot += wcnt[t];
+        base += tot;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x != 0) return;
+  if (level == 1) {
+    const int F = base;
+    sel_state[SS_F] = F;
+    const int count = sel_state[SS_COUNT];
+    if (count <= F) {
+      sel_state[SS_TAKE_ALL] = 1;
+      return;
+    }
+    sel_state[SS_NEED] = F;
+    sel_state[SS_LESS] = 0;
+  } else if (sel_state[SS_TAKE_ALL]) {
+    return;
+  }
+  const int nbins = level == 3 ? 1024 : SEL_BINS;
+  const unsigned* h = hist + (level - 1) * SEL_BINS;
+  const int need = sel_state[SS_NEED];
+  int cum = 0, b = 0;
+  for (b = 0; b < nbins; ++b) {
+    if (cum + (int)h[b] >= need) break;
+    cum += (int)h[b];
+  }
+  if (b >= nbins) b = nbins - 1;  // cannot happen when the counts are consistent
+  sel_state[SS_NEED] = need - cum;
+  sel_state[SS_LESS] += cum;
+  if (level == 1) sel_state[SS_PREFIX] = b;
+  else if (level == 2) sel_state[SS_PREFIX] = (sel_state[SS_PREFIX] << 11) | b;
+  else sel_state[SS_TAU] = (int)(((unsigned)sel_state[SS_PREFIX] << 10) | (unsigned)b);
+}
+
+// levels 2 and 3: histogram of the next key bits among entries matching the prefix
+__global__ void k_sel_pass(int level, const int* __restrict__ pool_hw,
+                           const uint8_t* __restrict__ pool_valid,
+                           const unsigned* __restrict__ pool_key, unsigned* hist,
+                           const int* __restrict__ sel_state) {
+  if (sel_state[SS_TAKE_ALL]) return;
+  __shared__ unsigned sh[SEL_BINS];
+  for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
+  __syncthreads();
+  const int hw = *pool_hw;
+  const unsigned pre = (unsigned)sel_state[SS_PREFIX];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+    if (!pool_valid[i]) continue;
+    const unsigned k = pool_key[i];
+    if (level == 2) {
+      if ((k >> 21) == pre) atomicAdd(&sh[(k >> 10) & 2047u], 1u);
+    } else {
+      if ((k >> 10) == pre) atomicAdd(&sh[k & 1023u], 1u);
+    }
+  }
+  __syncthreads();
+  unsigned* h = hist + (level - 1) * SEL_BINS;
+  for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x)
+    if (sh[t]) atomicAdd(&h[t], sh[t]);
+}
+
+__global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_valid,
+                              const unsigned* __restrict__ pool_key, int* free_stack, int* free_top,
+                              int* sel_state, int* popped) {
+  const int hw = *pool_hw;
+  const int all = sel_state[SS_TAKE_ALL];
+  const unsigned tau = (unsigned)sel_state[SS_TAU];
+  const int need_eq = sel_state[SS_NEED];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+    if (!pool_valid[i]) continue;
+    const unsigned k = pool_key[i];
+    bool take = all || k < tau;
+    if (!take && k == tau) take = atomicAdd(&sel_state[SS_EQ], 1) < need_eq;
+    if (!take) continue;
+    popped[atomicAdd(&sel_state[SS_OUT], 1)] = i;
+    pool_valid[i] = 0;
+    free_stack[atomicAdd(free_top, 1)] = i;
+  }
+}
+
+// load popped nodes into free slots (one block per popped node)
+template <class R>
+__global__ void k_refill(int p, const int* __restrict__ sel_state, const int* __restrict__ popped,
+                         const int* __restrict__ free_slots, const double* __restrict__ pool_lb,
+                         const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
+                         const int* __restrict__ pool_fix, const R* __restrict__ warm_beta,
+                         const R* __restrict__ warm_V, int* warm_ref, int* warm_stack,
+                         int* warm_top, int8_t* fix, R* beta, R* V, int* slot_active,
+                         int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
+                         int* slot_fixl) {
+  const int t = blockIdx.x;
+  if (t >= sel_state[SS_OUT]) return;
+  const int slot = free_slots[t];
+  const int idx = popped[t];
+  const int d = pool_depth[idx];
+  const int w = pool_warm[idx];
+  const long long so = (long long)slot * p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    fix[so + i] = -1;
+    beta[so + i] = w >= 0 ? warm_beta[(long long)w * p + i] : R(0);
+    V[so + i] = w >= 0 ? warm_V[(long long)w * p + i] : R(0);
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < d; u += blockDim.x) {
+    const int e = pool_fix[(long long)idx * DMAX + u];
+    slot_fixl[(long long)slot * DMAX + u] = e;
+    fix[so + (e >> 1)] = (int8_t)(e & 1);
+    if ((e & 1) == 0) beta[so + (e >> 1)] = R(0);  // the new F0 coordinate starts at zero
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    slot_active[slot] = 1;
+    slot_iters[slot] = 0;
+    slot_lbp[slot] = pool_lb[idx];
+    slot_depth[slot] = d;
+    slot_nfix[slot] = d;
+    warm_release(w, warm_ref, warm_stack, warm_top);
+  }
+}
+
+__global__ void k_status(int K, const int* __restrict__ slot_active,
+                         const double* __restrict__ slot_lbp, const int* __restrict__ sel_state,
+                         const unsigned long long* __restrict__ poolmin,
+                         const unsigned long long* __restrict__ lost_key,
+                         const double* __restrict__ inc_ub, const int* __restrict__ free_top,
+                         const int* __restrict__ warm_top, const int* __restrict__ ret_count,
+                         Status* st) {
+  __shared__ int act_s[32];
+  __shared__ unsigned long long mn_s[32];
+  int act = 0;
+  unsigned long long mn = ~0ull;
+  for (int s = threadIdx.x; s < K; s += blockDim.x)
+    if (slot_active[s]) {
+      ++act;
+      const unsigned long long k = dkey(slot_lbp[s]);
+      mn = k < mn ? k : mn;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    act += __shfl_xor_sync(0xffffffffu, act, o);
+    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mn, o);
+    mn = m2 < mn ? m2 : mn;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    act_s[w] = act;
+    mn_s[w] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  act = 0;
+  mn = ~0ull;
+  for (int t = 0; t < nw; ++t) {
+    act += act_s[t];
+    mn = mn_s[t] < mn ? mn_s[t] : mn;
+  }
+  const long long pool_after = (long long)sel_state[SS_COUNT] - sel_state[SS_OUT];
+  if (pool_after > 0 && *poolmin < mn) mn = *poolmin;
+  if (*lost_key < mn) mn = *lost_key;
+  const double ub = inc_ub[0];
+  st->ub = ub;
+  st->lb = (mn == ~0ull) ? ub : dkey_inv(mn);
+  if (st->lb > ub) st->lb = ub;
+  st->pool_count = pool_after;
+  st->active_slots = act;
+  st->retired = *ret_count;
+  st->pruned = sel_state[SS_PRUNED];
+  st->polished = sel_state[SS_POLISHED];
+  st->free_top = *free_top;
+  st->warm_free = *warm_top;
+  st->error = sel_state[SS_ERROR];
+  st->max_depth = sel_state[SS_MAXDEPTH];
+  st->lost_lb = (*lost_key == ~0ull) ? INFINITY : dkey_inv(*lost_key);
+}
+
+static inline int pool_grid(long long qcap) {
+  long long g = (qcap + 255) / 256;
+  return (int)(g > 148 * 8 ? 148 * 8 : (g < 1 ? 1 : g));
+}
+
+template <class R>
+int queue_init(Engine<R>& e) {
+  BNB_CUDA_OK(cudaMemsetAsync(e.sel_state, 0, sizeof(int) * SS_WORDS, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.poolmin + 1, 0xff, sizeof(unsigned long long), e.st));  // lost key
+  k_queue_init<<<pool_grid(e.qcap), 256, 0, e.st>>>(e.qcap, e.wcap, e.free_stack, e.free_top,
+                                                    e.pool_hw, e.warm_stack, e.warm_top,
+                                                    e.pool_valid, e.pool_lb, e.pool_key,
+                                                    e.pool_depth, e.pool_warm, e.inc_ub, INFINITY);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template <class R>
+int queue_push(Engine<R>& e) {
+  k_push<R><<<e.K, 256, 0, e.st>>>(e.p, e.ret_slot, e.ret_count, e.node_lb, e.br_idx, e.inc_ub,
+                                   e.params_d, e.slot_depth, e.slot_fixl, e.beta, e.V,
+                                   e.free_stack, e.free_top, e.pool_hw, e.pool_valid, e.pool_lb,
+                                   e.pool_key, e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
+                                   e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.sel_state,
+                                   e.poolmin, e.poolmin + 1);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template <class R>
+int queue_select_refill(Engine<R>& e) {
+  cudaStream_t st = e.st;
+  const int g = pool_grid(e.qcap);
+  k_sel_reset<<<1, 256, 0, st>>>(e.sel, e.sel_state, e.poolmin);
+  k_sel_pass1<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_lb, e.pool_key, e.pool_warm,
+                                 e.free_stack, e.free_top, e.warm_ref, e.warm_stack, e.warm_top,
+                                 e.inc_ub, e.params_d, e.sel, e.sel_state, e.poolmin);
+  k_sel_scan<<<1, 1024, 0, st>>>(1, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_pass<<<g, 256, 0, st>>>(2, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
+  k_sel_scan<<<1, 32, 0, st>>>(2, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_pass<<<g, 256, 0, st>>>(3, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
+  k_sel_scan<<<1, 32, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_collect<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_key, e.free_stack, e.free_top,
+                                   e.sel_state, e.popped);
+  k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.sel_state, e.popped, e.free_slots, e.pool_lb,
+                                   e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta, e.warm_V,
+                                   e.warm_ref, e.warm_stack, e.warm_top, e.fix, e.beta, e.V,
+                                   e.slot_active, e.slot_iters, e.slot_lbp, e.slot_depth,
+                                   e.slot_nfix, e.slot_fixl);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template <class R>
+int queue_status(Engine<R>& e) {
+  k_status<<<1, 256, 0, e.st>>>(e.K, e.slot_active, e.slot_lbp, e.sel_state, e.poolmin,
+                                e.poolmin + 1, e.inc_ub, e.free_top, e.warm_top, e.ret_count,
+                                e.status_d);
+  BNB_CUDA_OK(cudaGetLastError());
+  BNB_CUDA_OK(cudaMemcpyAsync(e.status_h, e.status_d, sizeof(Status), cudaMemcpyDeviceToHost, e.st));
+  return 0;
+}
+
+#define INST(R)                                      \
+  template int queue_init<R>(Engine<R>&);            \
+  template int queue_push<R>(Engine<R>&);            \
+  template int queue_select_refill<R>(Engine<R>&);   \
+  template int queue_status<R>(Engine<R>&);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace bnb
