@@ -1,0 +1,231 @@
+"""Python binding of libbnb.so, the B300 (sm_103a) l0-l2 branch-and-bound library.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI declared in include/bnb.h.  The function names are
+those of the C ABI.  Host arrays are numpy; the *_device entry points accept
+torch CUDA tensors (their data pointers are passed through).
+
+The library must have been built (``python -m paper_2602_04551_b300.build`` or
+``__graft_entry__.build()``); importing the binding without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbnb.so")
+
+BNB_OK = 0
+BNB_EINVAL, BNB_ENOMEM, BNB_ECUDA, BNB_ETIMEOUT, BNB_EQUEUE, BNB_ENODEV = -1, -2, -3, -4, -5, -6
+BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit"}
+
+# exported symbols (kept in step with include/bnb.h)
+SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
+           "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
+           "bnb_get_stats", "bnb_last_error", "bnb_destroy")
+
+
+class bnb_options(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_double), ("rho", ctypes.c_double), ("node_tol", ctypes.c_double),
+                ("max_admm_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("batch_K", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("time_limit_s", ctypes.c_double),
+                ("max_nodes", ctypes.c_longlong), ("queue_capacity", ctypes.c_longlong),
+                ("warm_capacity", ctypes.c_longlong), ("support_max", ctypes.c_int),
+                ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class bnb_stats(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+                ("admm_iters", ctypes.c_longlong), ("slot_iters", ctypes.c_longlong),
+                ("pruned", ctypes.c_longlong), ("ub_polished", ctypes.c_longlong),
+                ("pool_peak", ctypes.c_longlong), ("max_depth", ctypes.c_int),
+                ("solve_seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double),
+                ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double)]
+
+
+class BnbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bnb error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libbnb.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run python -m paper_2602_04551_b300.build")
+    lib = ctypes.CDLL(path)
+    P, D, I, LL = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "bnb_options_default": ([P], I),
+        "bnb_create": ([P, P, I, I, D, D, P, P], I),
+        "bnb_create_device": ([P, P, I, I, D, D, P, P], I),
+        "bnb_relax_batch": ([P, I, P, P, P, I, P, P, P, P, P, P, P], I),
+        "bnb_relax_batch_device": ([P, I, P, P, P, I, P, P, P, P, P, P, P], I),
+        "bnb_dual_bound": ([P, I, P, P, P], I),
+        "bnb_upper_batch": ([P, I, P, P, P], I),
+        "bnb_solve": ([P, D, P, P, P, P, P], I),
+        "bnb_get_stats": ([P, P], I),
+        "bnb_last_error": ([P], ctypes.c_char_p),
+        "bnb_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, h=None):
+    if rc != BNB_OK:
+        msg = load_library().bnb_last_error(h)
+        raise BnbError(rc, msg.decode() if msg else "")
+
+
+def bnb_options_default(**overrides) -> bnb_options:
+    lib = load_library()
+    o = bnb_options()
+    _check(lib.bnb_options_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns a bnb_handle*; destroyed with bnb_destroy."""
+
+    def __init__(self, ptr, n, p, options):
+        self.ptr = ptr
+        self.n, self.p = n, p
+        self.options = options
+
+    def close(self):
+        if self.ptr:
+            load_library().bnb_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def bnb_create(X, y, lambda0: float, lambda2: float, options: bnb_options) -> Handle:
+    lib = load_library()
+    X = np.asfortranarray(X, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    n, p = X.shape
+    h = ctypes.c_void_p()
+    _check(lib.bnb_create(_ptr(X), _ptr(y), n, p, float(lambda0), float(lambda2),
+                          ctypes.byref(options), ctypes.byref(h)))
+    return Handle(h, n, p, options)
+
+
+def bnb_create_device(dX, dy, n: int, p: int, lambda0: float, lambda2: float,
+                      options: bnb_options) -> Handle:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.bnb_create_device(_ptr(dX), _ptr(dy), n, p, float(lambda0), float(lambda2),
+                                 ctypes.byref(options), ctypes.byref(h)))
+    return Handle(h, n, p, options)
+
+
+def bnb_relax_batch(h: Handle, fix, warm_beta=None, warm_v=None, max_iter: int = 0,
+                    want_beta=True, want_v=False, want_z=True):
+    lib = load_library()
+    fix = np.ascontiguousarray(fix, dtype=np.int8)
+    K, p = fix.shape
+    wb = None if warm_beta is None else np.ascontiguousarray(warm_beta, dtype=np.float32)
+    wv = None if warm_v is None else np.ascontiguousarray(warm_v, dtype=np.float32)
+    lb = np.empty(K, np.float64)
+    beta = np.empty((K, p), np.float32) if want_beta else None
+    v = np.empty((K, p), np.float32) if want_v else None
+    z = np.empty((K, p), np.float32) if want_z else None
+    br = np.empty(K, np.int32)
+    gap = np.empty(K, np.float64)
+    iters = np.empty(K, np.int32)
+    _check(lib.bnb_relax_batch(h.ptr, K, _ptr(fix), _ptr(wb), _ptr(wv), int(max_iter), _ptr(lb),
+                               _ptr(beta), _ptr(v), _ptr(z), _ptr(br), _ptr(gap), _ptr(iters)), h.ptr)
+    return dict(lb=lb, beta=beta, v=v, z=z, branch=br, gap=gap, iters=iters)
+
+
+def bnb_relax_batch_device(h: Handle, K: int, dfix, dwarm_beta, dwarm_v, max_iter, dlb,
+                           dbeta=None, dv=None, dz=None, dbr=None, dgap=None, diters=None):
+    lib = load_library()
+    _check(lib.bnb_relax_batch_device(h.ptr, K, _ptr(dfix), _ptr(dwarm_beta), _ptr(dwarm_v),
+                                      int(max_iter), _ptr(dlb), _ptr(dbeta), _ptr(dv), _ptr(dz),
+                                      _ptr(dbr), _ptr(dgap), _ptr(diters)), h.ptr)
+
+
+def bnb_dual_bound(h: Handle, fix, r):
+    lib = load_library()
+    fix = np.ascontiguousarray(fix, dtype=np.int8)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    K = fix.shape[0]
+    lb = np.empty(K, np.float64)
+    _check(lib.bnb_dual_bound(h.ptr, K, _ptr(fix), _ptr(r), _ptr(lb)), h.ptr)
+    return lb
+
+
+def bnb_upper_batch(h: Handle, support):
+    lib = load_library()
+    support = np.ascontiguousarray(support, dtype=np.uint8)
+    K, p = support.shape
+    ub = np.empty(K, np.float64)
+    beta = np.empty((K, p), np.float64)
+    _check(lib.bnb_upper_batch(h.ptr, K, _ptr(support), _ptr(ub), _ptr(beta)), h.ptr)
+    return ub, beta
+
+
+def bnb_solve(h: Handle, rel_gap: float):
+    lib = load_library()
+    beta = np.empty(h.p, np.float64)
+    ub, lb = ctypes.c_double(), ctypes.c_double()
+    nodes, status = ctypes.c_longlong(), ctypes.c_int()
+    _check(lib.bnb_solve(h.ptr, float(rel_gap), _ptr(beta), ctypes.byref(ub), ctypes.byref(lb),
+                         ctypes.byref(nodes), ctypes.byref(status)), h.ptr)
+    return dict(beta=beta, ub=ub.value, lb=lb.value, nodes=nodes.value,
+                status=STATUS_NAMES.get(status.value, status.value))
+
+
+def bnb_get_stats(h: Handle) -> dict:
+    lib = load_library()
+    s = bnb_stats()
+    _check(lib.bnb_get_stats(h.ptr, ctypes.byref(s)), h.ptr)
+    return {k: getattr(s, k) for k, _ in bnb_stats._fields_}
+
+
+def bnb_last_error(h: Handle | None = None) -> str:
+    m = load_library().bnb_last_error(h.ptr if h else None)
+    return m.decode() if m else ""
+
+
+def bnb_destroy(h: Handle):
+    h.close()

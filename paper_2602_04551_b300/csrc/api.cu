@@ -1,0 +1,719 @@
+// api.cu -- the C ABI declared in include/bnb.h.
+//
+// A handle owns one Engine<float> (mixed-precision path: FP32 ADMM state and
+// contractions, FP64 certificates and polish) or one Engine<double> (plain
+// FP64 path).  bnb_solve runs Algorithm 1 as device "rounds":
+//   refill free slots from the pool (best-first) -> check_every ADMM iterations
+//   -> stop test -> FP64 certificates of retired nodes -> branch pick + rounded
+//   support -> batched upper bound (+ FP64 polish) -> prune / push children
+//   -> status word to the host.
+// With use_graphs a round is captured once into a CUDA graph and replayed; the
+// host only reads the status word between rounds.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+
+#include "bnb.h"
+#include "engine.cuh"
+#include "gemm_simt.cuh"
+
+namespace bnb {
+
+static thread_local std::string g_err;
+
+void set_cuda_error(const char* what, cudaError_t e, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_err = buf;
+}
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+template <class R>
+static int dalloc(Engine<R>& e, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t rc = cudaMalloc(ptr, bytes);
+  if (rc != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BNB_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(rc));
+  }
+  e.allocs.push_back(*ptr);
+  return 0;
+}
+#define ALLOC(ptr, count)                                                                 \
+  do {                                                                                    \
+    if (int _rc = dalloc(e, (void**)&(ptr), sizeof(*(ptr)) * (size_t)(count))) return _rc; \
+  } while (0)
+
+template <class R>
+static void free_all(Engine<R>& e) {
+  for (void* p : e.allocs) cudaFree(p);
+  e.allocs.clear();
+  if (e.status_h) cudaFreeHost(e.status_h);
+  e.status_h = nullptr;
+  if (e.own_stream && e.st) cudaStreamDestroy(e.st);
+  e.st = nullptr;
+}
+
+static int pick_splits(int m, int nn, int kred, int bm, int bn, int bk) {
+  const int tiles = ((m + bm - 1) / bm) * ((nn + bn - 1) / bn);
+  int s = (2 * 148 + tiles - 1) / tiles;
+  const int smax = kred / (8 * bk);
+  if (s > smax) s = smax;
+  return s < 1 ? 1 : s;
+}
+
+template <class R>
+static int allocate(Engine<R>& e) {
+  using C = TileCfg<R>;
+  const long long n = e.n, p = e.p, K = e.K, sm = e.smax;
+  e.s1 = gemm_simt_splits<R>(e.p, pick_splits(e.n, e.K, e.p, C::BM, C::BN, C::BK));
+  e.s2 = gemm_simt_splits<R>(e.n, pick_splits(e.n, e.K, e.n, C::BM, C::BN, C::BK));
+  e.nbm3 = (e.p + C::BM - 1) / C::BM;
+  ALLOC(e.X64, n * p);
+  ALLOC(e.X32, n * p);
+  if constexpr (sizeof(R) == 4) e.XR = (R*)e.X32; else e.XR = (R*)e.X64;
+  ALLOC(e.y64, n);
+  ALLOC(e.c64, p);
+  ALLOC(e.xnorm, p);
+  ALLOC(e.yR, n);
+  ALLOC(e.cR, p);
+  ALLOC(e.Ginv, n * n);
+  ALLOC(e.beta, K * p);
+  ALLOC(e.V, K * p);
+  ALLOC(e.fix, K * p);
+  ALLOC(e.Tpart, (long long)e.s1 * n * K);
+  ALLOC(e.T, n * K);
+  ALLOC(e.Upart, (long long)e.s2 * n * K);
+  ALLOC(e.U, n * K);
+  ALLOC(e.XBpart, (long long)e.s1 * n * K);
+  ALLOC(e.g3part, 4LL * e.nbm3 * K);
+  ALLOC(e.rstat, 2 * K);
+  ALLOC(e.slot_active, K);
+  ALLOC(e.slot_iters, K);
+  ALLOC(e.slot_depth, K);
+  ALLOC(e.slot_nfix, K);
+  ALLOC(e.slot_fixl, K * DMAX);
+  ALLOC(e.slot_lbp, K);
+  ALLOC(e.slot_gap, K);
+  ALLOC(e.slot_dual, K);
+  ALLOC(e.slot_primal, K);
+  ALLOC(e.slot_retire, K);
+  ALLOC(e.ret_slot, K);
+  ALLOC(e.ret_active, K);
+  ALLOC(e.ret_count, 1);
+  ALLOC(e.r64, K * n);
+  ALLOC(e.rS, K * n);
+  ALLOC(e.gscr, K * p);
+  ALLOC(e.cflag, K * p);
+  ALLOC(e.cert_rr, K);
+  ALLOC(e.cert_yr, K);
+  ALLOC(e.cert_rn, K);
+  ALLOC(e.cert_lb, K);
+  ALLOC(e.node_lb, K);
+  ALLOC(e.br_idx, K);
+  ALLOC(e.sup_cnt, K);
+  ALLOC(e.nfree, K);
+  ALLOC(e.sup, K * sm);
+  ALLOC(e.Qg, K * sm * sm);
+  ALLOC(e.qv, K * sm);
+  ALLOC(e.ubb, K * sm);
+  ALLOC(e.Q64, K * sm * sm);
+  ALLOC(e.L64, K * sm * sm);
+  ALLOC(e.ubb64, K * 2 * sm);
+  ALLOC(e.ub_val, K);
+  ALLOC(e.pol_flag, K);
+  ALLOC(e.inc_beta, p);
+  ALLOC(e.inc_ub, 1);
+  ALLOC(e.zbuf, K * p);
+  ALLOC(e.pool_lb, e.qcap);
+  ALLOC(e.pool_key, e.qcap);
+  ALLOC(e.pool_valid, e.qcap);
+  ALLOC(e.pool_depth, e.qcap);
+  ALLOC(e.pool_warm, e.qcap);
+  ALLOC(e.pool_fix, e.qcap * DMAX);
+  ALLOC(e.free_stack, e.qcap);
+  ALLOC(e.free_top, 1);
+  ALLOC(e.pool_hw, 1);
+  ALLOC(e.warm_beta, e.wcap * p);
+  ALLOC(e.warm_V, e.wcap * p);
+  ALLOC(e.warm_ref, e.wcap);
+  ALLOC(e.warm_stack, e.wcap);
+  ALLOC(e.warm_top, 1);
+  ALLOC(e.sel, 3 * SEL_BINS);
+  ALLOC(e.sel_state, 16);
+  ALLOC(e.popped, K);
+  ALLOC(e.free_slots, K);
+  ALLOC(e.poolmin, 2);
+  ALLOC(e.status_d, 1);
+  ALLOC(e.params_d, 4);
+  if (cudaMallocHost((void**)&e.status_h, sizeof(Status)) != cudaSuccess)
+    return fail(BNB_ENOMEM, "pinned status allocation failed");
+  BNB_CUDA_OK(cudaMemsetAsync(e.beta, 0, sizeof(R) * K * p, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.V, 0, sizeof(R) * K * p, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.fix, 0xff, K * p, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * K, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.sel_state, 0, sizeof(int) * 16, e.st));
+  return 0;
+}
+
+// ----------------------------------------------------------------- small kernels
+
+template <class R>
+__global__ void k_load_nodes(int K, int p, const int8_t* __restrict__ fix_in,
+                             const float* __restrict__ wb, const float* __restrict__ wv,
+                             int8_t* __restrict__ fix, R* __restrict__ beta, R* __restrict__ V) {
+  const long long m = (long long)K * p;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = fix_in[i];
+    fix[i] = (int8_t)f;
+    R b = wb ? (R)wb[i] : R(0);
+    if (f == 0) b = R(0);
+    beta[i] = b;
+    V[i] = wv ? (R)wv[i] : R(0);
+  }
+}
+
+__global__ void k_init_slots(int K, int Kact, int* slot_active, int* slot_iters, double* slot_lbp,
+                             int* slot_depth, int* ret_slot, int* ret_active, int* ret_count,
+                             int set_ret) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < K; s += gridDim.x * blockDim.x) {
+    slot_active[s] = (s < Kact && !set_ret) ? 1 : 0;
+    slot_iters[s] = 0;
+    slot_lbp[s] = -INFINITY;
+    slot_depth[s] = 0;
+    if (set_ret) {
+      ret_slot[s] = s;
+      ret_active[s] = s < Kact ? 1 : 0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && set_ret) *ret_count = Kact;
+}
+
+// per-slot results of the nodes retired this round (relax_batch)
+__global__ void k_scatter_relax(const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+                                const double* __restrict__ cert_lb, const int* __restrict__ br_idx,
+                                double* out_lb, int* out_br) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *ret_count) return;
+  const int s = ret_slot[q];
+  out_lb[s] = cert_lb[q];
+  out_br[s] = br_idx[q];
+}
+
+__global__ void k_count_active(int K, const int* __restrict__ a, int* out) {
+  __shared__ int sh[32];
+  int c = 0;
+  for (int s = threadIdx.x; s < K; s += blockDim.x) c += a[s];
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+template <class R>
+__global__ void k_to_float(const R* __restrict__ a, float* __restrict__ b, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_scatter_ub(int K, int p, int smax, const int* __restrict__ sup,
+                             const int* __restrict__ sup_cnt, const double* __restrict__ ubb64,
+                             double* __restrict__ out) {
+  const int q = blockIdx.x;
+  if (q >= K) return;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) out[(long long)q * p + i] = 0.0;
+  __syncthreads();
+  const int s = sup_cnt[q];
+  for (int a = threadIdx.x; a < s; a += blockDim.x)
+    out[(long long)q * p + sup[(long long)q * smax + a]] = ubb64[(long long)q * 2 * smax + a];
+}
+
+static inline int g1d(long long m) {
+  long long g = (m + 255) / 256;
+  return (int)(g > 148 * 16 ? 148 * 16 : (g < 1 ? 1 : g));
+}
+
+}  // namespace bnb
+
+using namespace bnb;
+
+struct bnb_handle {
+  bnb_options opt{};
+  int n = 0, p = 0;
+  double lam0 = 0, lam2 = 0;
+  Engine<float>* ef = nullptr;
+  Engine<double>* ed = nullptr;
+  std::string err;
+  bnb_stats stats{};
+  // per-call staging (device)
+  double *d_lb = nullptr, *d_rgiven = nullptr, *d_gap = nullptr;
+  int *d_br = nullptr, *d_cnt = nullptr, *h_cnt = nullptr;
+  float* d_stage = nullptr;
+  double* d_ubbeta = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+static int set_err(bnb_handle* h, int rc) {
+  if (h) h->err = g_err;
+  return rc;
+}
+
+extern "C" int bnb_options_default(bnb_options* o) {
+  if (!o) return BNB_EINVAL;
+  memset(o, 0, sizeof(*o));
+  o->M = 0.0;
+  o->rho = 1.0;
+  o->node_tol = 1e-4;
+  o->max_admm_iter = 400;
+  o->check_every = 10;
+  o->batch_K = 512;
+  o->precision = BNB_PREC_FP32;
+  o->use_graphs = 1;
+  o->time_limit_s = 3600.0;
+  o->max_nodes = 1000000000LL;
+  o->queue_capacity = 1LL << 20;
+  o->warm_capacity = 0;
+  o->support_max = 200;
+  o->ub_max_iter = 200;
+  o->device = 0;
+  o->stream = nullptr;
+  return BNB_OK;
+}
+
+template <class R>
+static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const double* dy) {
+  e = new Engine<R>();
+  const bnb_options& o = h->opt;
+  e->n = h->n;
+  e->p = h->p;
+  e->K = o.batch_K;
+  e->smax = o.support_max;
+  e->ub_iters = o.ub_max_iter;
+  e->qcap = o.queue_capacity;
+  long long wdef = (4LL << 30) / (2LL * h->p * (long long)sizeof(R));
+  if (wdef > e->qcap / 2) wdef = e->qcap / 2;
+  if (wdef < 64) wdef = 64;
+  e->wcap = o.warm_capacity > 0 ? o.warm_capacity : wdef;
+  Prob& P = e->P;
+  P.n = h->n;
+  P.p = h->p;
+  P.lam0 = h->lam0;
+  P.lam2 = h->lam2;
+  P.M = o.M;
+  P.rho = o.rho;
+  P.s0 = std::sqrt(h->lam0 / h->lam2);
+  P.linear = P.s0 > o.M ? 1 : 0;
+  P.ridge_scale = o.rho / (o.rho + 2.0 * h->lam2);
+  P.thr_soft = 2.0 * std::sqrt(h->lam0 * h->lam2) / o.rho;
+  P.tau = P.thr_soft + P.s0;
+  P.c_lin = h->lam0 / o.M + h->lam2 * o.M;
+  P.thr_lin = P.c_lin / o.rho;
+  P.c_soft = 2.0 * std::sqrt(h->lam0 * h->lam2);
+  P.x0 = P.linear ? P.c_lin : P.c_soft;
+  P.sqrt_l2_l0 = h->lam0 > 0 ? std::sqrt(h->lam2 / h->lam0) : INFINITY;
+  if (o.stream) {
+    e->st = (cudaStream_t)o.stream;
+  } else {
+    BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
+    e->own_stream = true;
+  }
+  if (int rc = allocate(*e)) return rc;
+  if (int rc = setup_data(*e, dX, dy)) return rc;
+  return 0;
+}
+
+static int check_device(int dev) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
+    cudaGetLastError();
+    return fail(BNB_ENODEV, "no CUDA device available");
+  }
+  if (dev < 0 || dev >= count) return fail(BNB_EINVAL, "device %d out of range", dev);
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return fail(BNB_ECUDA, "device query failed");
+  if (pr.major != 10) return fail(BNB_ENODEV, "device %d is sm_%d%d, this library is built for sm_103a", dev, pr.major, pr.minor);
+  if (cudaSetDevice(dev) != cudaSuccess) return fail(BNB_ECUDA, "cudaSetDevice failed");
+  return 0;
+}
+
+static int create_common(const double* dX, const double* dy, int n, int p, double lam0,
+                         double lam2, const bnb_options* opt, bnb_handle** out) {
+  if (!out) return fail(BNB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || p <= 0) return fail(BNB_EINVAL, "n and p must be positive");
+  if (!(lam0 >= 0.0) || !(lam2 > 0.0)) return fail(BNB_EINVAL, "need lambda0 >= 0 and lambda2 > 0");
+  bnb_options o;
+  if (opt) o = *opt; else bnb_options_default(&o);
+  if (!(o.M > 0.0)) return fail(BNB_EINVAL, "options.M must be > 0");
+  if (!(o.rho > 0.0)) return fail(BNB_EINVAL, "options.rho must be > 0");
+  if (o.batch_K < 1 || o.batch_K > 65536) return fail(BNB_EINVAL, "batch_K out of range");
+  if (o.support_max < 1 || o.support_max > 256) return fail(BNB_EINVAL, "support_max must be in [1, 256]");
+  if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
+  if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
+    return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
+  if (o.precision != BNB_PREC_FP64 && o.precision != BNB_PREC_FP32)
+    return fail(BNB_EINVAL, "precision %d not available in this build", o.precision);
+  if (int rc = check_device(o.device)) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  bnb_handle* h = new bnb_handle();
+  h->opt = o;
+  h->n = n;
+  h->p = p;
+  h->lam0 = lam0;
+  h->lam2 = lam2;
+  int rc = (o.precision == BNB_PREC_FP64) ? engine_create<double>(h, h->ed, dX, dy)
+                                          : engine_create<float>(h, h->ef, dX, dy);
+  if (rc) {
+    std::string msg = g_err;
+    bnb_destroy(h);
+    g_err = msg;
+    return rc;
+  }
+  const int K = o.batch_K;
+  cudaError_t ce = cudaSuccess;
+  ce = ce ? ce : cudaMalloc(&h->d_lb, sizeof(double) * K);
+  ce = ce ? ce : cudaMalloc(&h->d_gap, sizeof(double) * K);
+  ce = ce ? ce : cudaMalloc(&h->d_br, sizeof(int) * K);
+  ce = ce ? ce : cudaMalloc(&h->d_cnt, sizeof(int));
+  ce = ce ? ce : cudaMallocHost(&h->h_cnt, sizeof(int));
+  ce = ce ? ce : cudaMalloc(&h->d_rgiven, sizeof(double) * (size_t)K * n);
+  ce = ce ? ce : cudaMalloc(&h->d_stage, sizeof(float) * (size_t)K * p);
+  ce = ce ? ce : cudaMalloc(&h->d_ubbeta, sizeof(double) * (size_t)K * p);
+  if (ce != cudaSuccess) {
+    bnb_destroy(h);
+    return fail(BNB_ENOMEM, "staging allocation failed: %s", cudaGetErrorString(ce));
+  }
+  h->stats.setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = h;
+  return BNB_OK;
+}
+
+extern "C" int bnb_create(const double* X, const double* y, int n, int p, double lambda0,
+                          double lambda2, const bnb_options* opt, bnb_handle** out) {
+  if (!X || !y) return fail(BNB_EINVAL, "X or y is NULL");
+  if (n <= 0 || p <= 0) return fail(BNB_EINVAL, "n and p must be positive");
+  int dev = opt ? opt->device : 0;
+  if (int rc = check_device(dev)) return rc;
+  double *dX = nullptr, *dy = nullptr;
+  if (cudaMalloc(&dX, sizeof(double) * (size_t)n * p) != cudaSuccess ||
+      cudaMalloc(&dy, sizeof(double) * n) != cudaSuccess) {
+    cudaFree(dX);
+    return fail(BNB_ENOMEM, "input staging allocation failed");
+  }
+  int rc = BNB_OK;
+  if (cudaMemcpy(dX, X, sizeof(double) * (size_t)n * p, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dy, y, sizeof(double) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = fail(BNB_ECUDA, "input upload failed");
+  if (!rc) rc = create_common(dX, dy, n, p, lambda0, lambda2, opt, out);
+  cudaFree(dX);
+  cudaFree(dy);
+  return rc;
+}
+
+extern "C" int bnb_create_device(const double* dX, const double* dy, int n, int p,
+                                 double lambda0, double lambda2, const bnb_options* opt,
+                                 bnb_handle** out) {
+  if (!dX || !dy) return fail(BNB_EINVAL, "X or y is NULL");
+  return create_common(dX, dy, n, p, lambda0, lambda2, opt, out);
+}
+
+extern "C" void bnb_destroy(bnb_handle* h) {
+  if (!h) return;
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->ef) { free_all(*h->ef); delete h->ef; }
+  if (h->ed) { free_all(*h->ed); delete h->ed; }
+  cudaFree(h->d_lb);
+  cudaFree(h->d_gap);
+  cudaFree(h->d_br);
+  cudaFree(h->d_cnt);
+  cudaFreeHost(h->h_cnt);
+  cudaFree(h->d_rgiven);
+  cudaFree(h->d_stage);
+  cudaFree(h->d_ubbeta);
+  delete h;
+}
+
+extern "C" const char* bnb_last_error(const bnb_handle* h) {
+  if (h && !h->err.empty()) return h->err.c_str();
+  return g_err.c_str();
+}
+
+// ------------------------------------------------------------------- relax batch
+
+template <class R>
+static int relax_impl(bnb_handle* h, Engine<R>& e, int K, const int8_t* dfix, const float* dwb,
+                      const float* dwv, int max_iter, double* lb, float* beta_out, float* v_out,
+                      float* z_out, int* br, double* gap, int* iters) {
+  cudaStream_t st = e.st;
+  const bnb_options& o = h->opt;
+  if (max_iter <= 0) max_iter = o.max_admm_iter;
+  const long long Kp = (long long)K * e.p;
+  k_load_nodes<R><<<g1d(Kp), 256, 0, st>>>(K, e.p, dfix, dwb, dwv, e.fix, e.beta, e.V);
+  k_init_slots<<<g1d(e.K), 256, 0, st>>>(e.K, K, e.slot_active, e.slot_iters, e.slot_lbp,
+                                         e.slot_depth, e.ret_slot, e.ret_active, e.ret_count, 0);
+  BNB_CUDA_OK(cudaGetLastError());
+  double inf = INFINITY;
+  BNB_CUDA_OK(cudaMemcpyAsync(e.inc_ub, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
+  int rounds = 0;
+  const int max_rounds = (max_iter + o.check_every - 1) / o.check_every + 1;
+  while (true) {
+    if (int rc = admm_round(e, o.check_every, max_iter, o.node_tol, false)) return rc;
+    if (int rc = certify(e, nullptr)) return rc;
+    if (int rc = branch_support(e, true)) return rc;
+    k_scatter_relax<<<(e.K + 255) / 256, 256, 0, st>>>(e.ret_slot, e.ret_count, e.cert_lb,
+                                                       e.br_idx, h->d_lb, h->d_br);
+    k_count_active<<<1, 1024, 0, st>>>(e.K, e.slot_active, h->d_cnt);
+    BNB_CUDA_OK(cudaGetLastError());
+    BNB_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BNB_CUDA_OK(cudaStreamSynchronize(st));
+    ++rounds;
+    if (*h->h_cnt == 0) break;
+    if (rounds > max_rounds + 2) return fail(BNB_ETIMEOUT, "relax_batch did not retire all nodes");
+  }
+  // outputs
+  BNB_CUDA_OK(cudaMemcpyAsync(lb, h->d_lb, sizeof(double) * K, cudaMemcpyDefault, st));
+  if (br) BNB_CUDA_OK(cudaMemcpyAsync(br, h->d_br, sizeof(int) * K, cudaMemcpyDefault, st));
+  if (gap) BNB_CUDA_OK(cudaMemcpyAsync(gap, e.slot_gap, sizeof(double) * K, cudaMemcpyDefault, st));
+  if (iters) BNB_CUDA_OK(cudaMemcpyAsync(iters, e.slot_iters, sizeof(int) * K, cudaMemcpyDefault, st));
+  if (beta_out) {
+    k_to_float<R><<<g1d(Kp), 256, 0, st>>>(e.beta, h->d_stage, Kp);
+    BNB_CUDA_OK(cudaMemcpyAsync(beta_out, h->d_stage, sizeof(float) * Kp, cudaMemcpyDefault, st));
+  }
+  if (v_out) {
+    BNB_CUDA_OK(cudaStreamSynchronize(st));
+    k_to_float<R><<<g1d(Kp), 256, 0, st>>>(e.V, h->d_stage, Kp);
+    BNB_CUDA_OK(cudaMemcpyAsync(v_out, h->d_stage, sizeof(float) * Kp, cudaMemcpyDefault, st));
+  }
+  if (z_out) BNB_CUDA_OK(cudaMemcpyAsync(z_out, e.zbuf, sizeof(float) * Kp, cudaMemcpyDefault, st));
+  BNB_CUDA_OK(cudaStreamSynchronize(st));
+  e.rounds += rounds;
+  return 0;
+}
+
+template <class F>
+static int dispatch(bnb_handle* h, F&& f) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  cudaSetDevice(h->opt.device);
+  int rc = h->ef ? f(*h->ef) : f(*h->ed);
+  if (rc) set_err(h, rc);
+  return rc;
+}
+
+static int relax_common(bnb_handle* h, int K, const int8_t* fix, const float* wb, const float* wv,
+                        int max_iter, double* lb, float* beta_out, float* v_out, float* z_out,
+                        int* br, double* gap, int* iters, bool host) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (K < 1 || K > h->opt.batch_K) return set_err(h, fail(BNB_EINVAL, "K=%d outside [1, %d]", K, h->opt.batch_K));
+  if (!fix || !lb) return set_err(h, fail(BNB_EINVAL, "fix and lb are required"));
+  const size_t Kp = (size_t)K * h->p;
+  return dispatch(h, [&](auto& e) -> int {
+    const int8_t* dfix = fix;
+    const float *dwb = wb, *dwv = wv;
+    int8_t* tfix = nullptr;
+    float *twb = nullptr, *twv = nullptr;
+    if (host) {
+      BNB_CUDA_OK(cudaMallocAsync(&tfix, Kp, e.st));
+      BNB_CUDA_OK(cudaMemcpyAsync(tfix, fix, Kp, cudaMemcpyHostToDevice, e.st));
+      dfix = tfix;
+      if (wb) {
+        BNB_CUDA_OK(cudaMallocAsync(&twb, Kp * 4, e.st));
+        BNB_CUDA_OK(cudaMemcpyAsync(twb, wb, Kp * 4, cudaMemcpyHostToDevice, e.st));
+        dwb = twb;
+      }
+      if (wv) {
+        BNB_CUDA_OK(cudaMallocAsync(&twv, Kp * 4, e.st));
+        BNB_CUDA_OK(cudaMemcpyAsync(twv, wv, Kp * 4, cudaMemcpyHostToDevice, e.st));
+        dwv = twv;
+      }
+    }
+    int rc = relax_impl(h, e, K, dfix, dwb, dwv, max_iter, lb, beta_out, v_out, z_out, br, gap, iters);
+    if (tfix) cudaFreeAsync(tfix, e.st);
+    if (twb) cudaFreeAsync(twb, e.st);
+    if (twv) cudaFreeAsync(twv, e.st);
+    cudaStreamSynchronize(e.st);
+    return rc;
+  });
+}
+
+extern "C" int bnb_relax_batch(bnb_handle* h, int K, const int8_t* fix, const float* wb,
+                               const float* wv, int max_iter, double* lb, float* beta_out,
+                               float* v_out, float* z_out, int* br, double* gap, int* iters) {
+  return relax_common(h, K, fix, wb, wv, max_iter, lb, beta_out, v_out, z_out, br, gap, iters, true);
+}
+
+extern "C" int bnb_relax_batch_device(bnb_handle* h, int K, const int8_t* fix, const float* wb,
+                                      const float* wv, int max_iter, double* lb, float* beta_out,
+                                      float* v_out, float* z_out, int* br, double* gap, int* iters) {
+  return relax_common(h, K, fix, wb, wv, max_iter, lb, beta_out, v_out, z_out, br, gap, iters, false);
+}
+
+// -------------------------------------------------------------------- dual bound
+
+extern "C" int bnb_dual_bound(bnb_handle* h, int K, const int8_t* fix, const double* r, double* lb) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (K < 1 || K > h->opt.batch_K) return set_err(h, fail(BNB_EINVAL, "K out of range"));
+  if (!fix || !r || !lb) return set_err(h, fail(BNB_EINVAL, "NULL argument"));
+  return dispatch(h, [&](auto& e) -> int {
+    const size_t Kp = (size_t)K * e.p;
+    BNB_CUDA_OK(cudaMemcpyAsync(e.fix, fix, Kp, cudaMemcpyHostToDevice, e.st));
+    BNB_CUDA_OK(cudaMemcpyAsync(h->d_rgiven, r, sizeof(double) * (size_t)K * e.n,
+                                cudaMemcpyHostToDevice, e.st));
+    k_init_slots<<<g1d(e.K), 256, 0, e.st>>>(e.K, K, e.slot_active, e.slot_iters, e.slot_lbp,
+                                             e.slot_depth, e.ret_slot, e.ret_active, e.ret_count, 1);
+    BNB_CUDA_OK(cudaGetLastError());
+    if (int rc = certify(e, h->d_rgiven)) return rc;
+    BNB_CUDA_OK(cudaMemcpyAsync(lb, e.cert_lb, sizeof(double) * K, cudaMemcpyDeviceToHost, e.st));
+    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+    return 0;
+  });
+}
+
+// ------------------------------------------------------------------- upper bound
+
+extern "C" int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, double* ub,
+                               double* beta_out) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (K < 1 || K > h->opt.batch_K) return set_err(h, fail(BNB_EINVAL, "K out of range"));
+  if (!support || !ub) return set_err(h, fail(BNB_EINVAL, "NULL argument"));
+  return dispatch(h, [&](auto& e) -> int {
+    const size_t Kp = (size_t)K * e.p;
+    BNB_CUDA_OK(cudaMemcpyAsync(e.cflag, support, Kp, cudaMemcpyHostToDevice, e.st));
+    k_init_slots<<<g1d(e.K), 256, 0, e.st>>>(e.K, K, e.slot_active, e.slot_iters, e.slot_lbp,
+                                             e.slot_depth, e.ret_slot, e.ret_active, e.ret_count, 1);
+    BNB_CUDA_OK(cudaGetLastError());
+    if (int rc = ub_from_masks(e, e.cflag, K)) return rc;
+    double inf = INFINITY;
+    BNB_CUDA_OK(cudaMemcpyAsync(e.inc_ub, &inf, sizeof(double), cudaMemcpyHostToDevice, e.st));
+    if (int rc = upper_bound(e, true)) return rc;
+    BNB_CUDA_OK(cudaMemcpyAsync(ub, e.ub_val, sizeof(double) * K, cudaMemcpyDeviceToHost, e.st));
+    if (beta_out) {
+      k_scatter_ub<<<K, 256, 0, e.st>>>(K, e.p, e.smax, e.sup, e.sup_cnt, e.ubb64, h->d_ubbeta);
+      BNB_CUDA_OK(cudaGetLastError());
+      BNB_CUDA_OK(cudaMemcpyAsync(beta_out, h->d_ubbeta, sizeof(double) * Kp,
+                                  cudaMemcpyDeviceToHost, e.st));
+    }
+    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+    return 0;
+  });
+}
+
+// ------------------------------------------------------------------------- solve
+
+template <class R>
+static int round_body(bnb_handle* h, Engine<R>& e) {
+  const bnb_options& o = h->opt;
+  if (int rc = queue_select_refill(e)) return rc;
+  if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
+  if (int rc = certify(e, nullptr)) return rc;
+  if (int rc = branch_support(e, false)) return rc;
+  if (int rc = upper_bound(e, false)) return rc;
+  if (int rc = queue_push(e)) return rc;
+  if (int rc = queue_status(e)) return rc;
+  return 0;
+}
+
+template <class R>
+static int solve_impl(bnb_handle* h, Engine<R>& e, double gap, double* beta_out, double* ub,
+                      double* lb, long long* nodes, int* status) {
+  const bnb_options& o = h->opt;
+  auto t0 = std::chrono::steady_clock::now();
+  double params[4] = {gap, 0, 0, 0};
+  BNB_CUDA_OK(cudaMemcpyAsync(e.params_d, params, sizeof(params), cudaMemcpyHostToDevice, e.st));
+  if (int rc = queue_init(e)) return rc;
+  BNB_CUDA_OK(cudaMemsetAsync(e.inc_beta, 0, sizeof(double) * e.p, e.st));
+  BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  e.nodes = e.rounds = e.admm_iters = e.pruned = e.polished = e.pool_peak = 0;
+  e.max_depth = 0;
+  cudaGraphExec_t exec = nullptr;
+  if (o.use_graphs) {
+    cudaGraph_t g;
+    BNB_CUDA_OK(cudaStreamBeginCapture(e.st, cudaStreamCaptureModeThreadLocal));
+    int rc = round_body(h, e);
+    cudaError_t ce = cudaStreamEndCapture(e.st, &g);
+    if (rc) return rc;
+    if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+  }
+  int st_code = BNB_STATUS_OPTIMAL;
+  Status s{};
+  while (true) {
+    if (exec) {
+      BNB_CUDA_OK(cudaGraphLaunch(exec, e.st));
+    } else if (int rc = round_body(h, e)) {
+      return rc;
+    }
+    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+    s = *e.status_h;
+    e.rounds++;
+    e.admm_iters += 0;
+    e.nodes += s.retired;
+    if (s.pool_count > e.pool_peak) e.pool_peak = s.pool_count;
+    e.max_depth = s.max_depth;
+    if (s.active_slots == 0 && s.pool_count == 0) {
+      st_code = (s.error ? BNB_STATUS_GAP : BNB_STATUS_OPTIMAL);
+      break;
+    }
+    if (std::isfinite(s.ub) && (s.ub - s.lb) <= gap * std::fabs(s.ub)) { st_code = BNB_STATUS_GAP; break; }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > o.time_limit_s) { st_code = BNB_STATUS_TIME_LIMIT; break; }
+    if (e.nodes >= o.max_nodes) { st_code = BNB_STATUS_NODE_LIMIT; break; }
+    if (s.free_top < 2 * e.K + 2) { st_code = BNB_STATUS_QUEUE_FULL; break; }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  e.admm_iters = e.rounds * o.check_every;
+  if (beta_out)
+    BNB_CUDA_OK(cudaMemcpy(beta_out, e.inc_beta, sizeof(double) * e.p, cudaMemcpyDeviceToHost));
+  double lbv = s.lb;
+  if (s.active_slots == 0 && s.pool_count == 0 && !s.error) lbv = s.ub;
+  if (ub) *ub = s.ub;
+  if (lb) *lb = lbv;
+  if (nodes) *nodes = e.nodes;
+  if (status) *status = st_code;
+  bnb_stats& S = h->stats;
+  S.nodes = e.nodes;
+  S.rounds = e.rounds;
+  S.admm_iters = e.admm_iters;
+  S.pruned = s.pruned;
+  S.ub_polished = s.polished;
+  S.pool_peak = e.pool_peak;
+  S.max_depth = e.max_depth;
+  S.final_ub = s.ub;
+  S.final_lb = lbv;
+  S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return 0;
+}
+
+extern "C" int bnb_solve(bnb_handle* h, double rel_gap, double* beta_out, double* ub, double* lb,
+                         long long* nodes, int* status) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (!(rel_gap >= 0.0) || rel_gap >= 1.0) return set_err(h, fail(BNB_EINVAL, "rel_gap must be in [0, 1)"));
+  return dispatch(h, [&](auto& e) -> int {
+    return solve_impl(h, e, rel_gap, beta_out, ub, lb, nodes, status);
+  });
+}
+
+extern "C" int bnb_get_stats(const bnb_handle* h, bnb_stats* out) {
+  if (!h || !out) return fail(BNB_EINVAL, "NULL argument");
+  *out = h->stats;
+  return BNB_OK;
+}

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "bnb.h"
+
 namespace bnb {
 
 // Per-tree scalar parameters, computed once on the host in FP64.
