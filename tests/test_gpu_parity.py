@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (stated per precision):
+  * certificates (Proposition 1 bound for a given r): FP64 on both sides, only the
+    summation order differs -> |LB_gpu - LB_oracle| <= 1e-10 max(1, |LB|);
+  * one ADMM iteration: FP64 path 1e-8; FP32 path (FP32 Woodbury b-update with a
+    Newton-Schulz G^-1) 2e-4 * max(1, |ref|);
+  * converged node bound: valid (<= the relaxation optimum of the independent
+    second solver) and within the node tolerance of it;
+  * upper bound on a support: FP64 polish -> 1e-10 relative objective, 1e-7 in beta;
+  * full solve: identical optimal support, objective within 1e-8 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+from oracle import relax, admm, pgd, ub as oub, bnb as obnb, brute
+
+pytestmark = pytest.mark.gpu
+
+bnb = pytest.importorskip("paper_2602_04551_b300")
+PRECS = [pytest.param(1, id="fp32"), pytest.param(0, id="fp64")]
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "c1_optimum.json")
+
+
+def _inst(name, inst_id=0, frac=0.05, mfac=1.5):
+    c = datagen.CONFIGS[name]
+    inst = datagen.config_instance(name, inst_id)
+    lam2 = c["lam2"]
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2, mfac)
+    lam0 = frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    return inst, lam0, lam2, M
+
+
+def _handle(inst, lam0, lam2, M, prec, K=64, **kw):
+    kw.setdefault("time_limit_s", 60.0)
+    o = bnb.bnb_options_default(M=M, precision=prec, batch_K=K, queue_capacity=1 << 16, **kw)
+    return bnb.bnb_create(inst.X, inst.y, lam0, lam2, o)
+
+
+# ------------------------------------------------------------------ certificate
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mfac", [1.5, 0.3])
+def test_dual_bound_matches_oracle(prec, mfac):
+    inst, lam0, lam2, M = _inst("c2_small", 0, mfac=mfac)
+    rng = np.random.default_rng(11)
+    K = 37  # ragged against every tile width
+    fix = datagen.random_fixings(inst.p, K, rng, 12)
+    fix[0] = -1
+    fix[1] = 0          # every coordinate in F0
+    fix[2] = 1          # every coordinate in F1 (a leaf)
+    r = inst.y[None, :] * rng.uniform(0.2, 1.2, (K, 1)) + rng.normal(0, 0.3, (K, inst.n))
+    with _handle(inst, lam0, lam2, M, prec, K=48) as h:
+        lb = bnb.bnb_dual_bound(h, fix, r)
+    for k in range(K):
+        ref = relax.dual_value(inst.X, inst.y, r[k], fix[k], lam0, lam2, M)
+        assert abs(lb[k] - ref) <= 1e-10 * max(1.0, abs(ref)), (k, lb[k], ref)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dual_bound_full_size_sampled(prec):
+    """C2 shape (n=1000, p=5000) in the bench launch width K=512; eight nodes checked."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    rng = np.random.default_rng(12)
+    K = 8
+    fix = datagen.random_fixings(inst.p, K, rng, 30)
+    r = inst.y[None, :] * rng.uniform(0.5, 1.0, (K, 1)) + rng.normal(0, 0.05, (K, inst.n))
+    with _handle(inst, lam0, lam2, M, prec, K=512) as h:
+        lb = bnb.bnb_dual_bound(h, fix, r)
+    for k in range(K):
+        ref = relax.dual_value(inst.X, inst.y, r[k], fix[k], lam0, lam2, M)
+        assert abs(lb[k] - ref) <= 1e-10 * max(1.0, abs(ref))
+
+
+# ------------------------------------------------------------------ ADMM iteration
+
+
+def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed):
+    rng = np.random.default_rng(seed)
+    fix = datagen.random_fixings(inst.p, K, rng, 20)
+    wb = (rng.uniform(-M, M, (K, inst.p)) * (rng.random((K, inst.p)) < 0.05)).astype(np.float32)
+    wb[fix == 0] = 0.0
+    wv = rng.normal(0, 0.05, (K, inst.p)).astype(np.float32)
+    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1) as h:
+        out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
+    assert np.all(out["iters"] == 1)
+    data = admm.AdmmData(inst.X, inst.y, 1.0)
+    tol = 1e-8 if prec == 0 else 2e-4
+    for k in rows:
+        b, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
+                                         fix[k], lam0, lam2, M)
+        sb = max(1.0, np.max(np.abs(beta)))
+        sv = max(1.0, np.max(np.abs(v)))
+        np.testing.assert_allclose(out["beta"][k], beta, atol=tol * sb)
+        np.testing.assert_allclose(out["v"][k], v, atol=tol * sv)
+        assert np.all(out["beta"][k][fix[k] == 0] == 0.0)
+        assert np.all(np.abs(out["beta"][k]) <= M * (1 + 1e-7))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_one_admm_iteration_matches_oracle(prec):
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=64, rows=range(45), seed=3)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_one_admm_iteration_full_size_sampled(prec):
+    """C2 shape at the bench width K=512; four sampled nodes against the oracle."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=512, Kopt=512, rows=[0, 131, 300, 511], seed=4)
+
+
+# ------------------------------------------------------------------ converged node
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_relaxation_bound_valid_and_tight(prec):
+    inst, lam0, lam2, M = _inst("c1", 0, frac=0.05)
+    rng = np.random.default_rng(5)
+    K = 10
+    fix = datagen.random_fixings(inst.p, K, rng, 6)
+    tol = 1e-7 if prec == 0 else 1e-5
+    with _handle(inst, lam0, lam2, M, prec, K=16, node_tol=tol, max_admm_iter=20000) as h:
+        out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+    for k in range(K):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))          # valid (Prop. 1.1)
+        assert out["lb"][k] >= opt - 20 * tol * max(1.0, abs(opt))      # tight at convergence
+        z = out["z"][k]
+        zref = relax.z_of_beta(out["beta"][k].astype(np.float64), fix[k], lam0, lam2, M)
+        np.testing.assert_allclose(z, zref, atol=1e-6)
+        free = np.nonzero(fix[k] == -1)[0]
+        frac = np.minimum(z[free], 1 - z[free])
+        if frac.max() > 0:
+            assert out["branch"][k] == free[int(np.argmax(frac))]
+
+
+# ------------------------------------------------------------------ upper bound
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("mfac", [1.5, 0.25])   # box loose / binding
+def test_upper_batch_matches_oracle(prec, mfac):
+    inst, lam0, lam2, M = _inst("c2_small", 2, mfac=mfac)
+    rng = np.random.default_rng(6)
+    K = 21
+    sup = np.zeros((K, inst.p), np.uint8)
+    for k in range(1, K):
+        sup[k, rng.choice(inst.p, size=int(rng.integers(1, 15)), replace=False)] = 1
+    sup[K - 1, inst.support_true] = 1
+    with _handle(inst, lam0, lam2, M, prec, K=32) as h:
+        ubv, beta = bnb.bnb_upper_batch(h, sup)
+    for k in range(K):
+        S = np.nonzero(sup[k])[0]
+        obj, bref = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
+        assert ubv[k] == pytest.approx(obj, rel=1e-10), k
+        np.testing.assert_allclose(beta[k], bref, atol=1e-7)
+
+
+# ------------------------------------------------------------------ full solve
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_solve_c1_golden(prec):
+    cases = json.load(open(GOLD))["cases"]
+    for case in cases:
+        inst = datagen.config_instance("c1", case["instance"])
+        o = bnb.bnb_options_default(M=case["M"], precision=prec, batch_K=64, node_tol=1e-7,
+                                    max_admm_iter=5000, queue_capacity=1 << 16,
+                                    time_limit_s=60.0)
+        with bnb.bnb_create(inst.X, inst.y, case["lambda0"], case["lambda2"], o) as h:
+            res = bnb.bnb_solve(h, case["gap"])
+        assert [int(i) for i in np.nonzero(res["beta"])[0]] == case["support"]
+        assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
+        assert res["lb"] <= res["ub"] * (1 + 1e-12)
+        assert (res["ub"] - res["lb"]) <= case["gap"] * res["ub"] * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("frac", [0.2, 0.02])
+def test_solve_matches_brute_force_p16(prec, frac):
+    inst, lam0, lam2, M = _inst("c1_p16", 0, frac=frac)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, prec, K=8, node_tol=1e-7, max_admm_iter=5000) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+
+
+@pytest.mark.parametrize("K", [1, 3, 128])
+def test_solve_batch_width_does_not_change_the_answer(K):
+    inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, 1, K=K, node_tol=1e-7, max_admm_iter=5000) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
