@@ -76,7 +76,7 @@ typedef struct {
 int bnb_options_default(bnb_options* opt);
 
 /*
- * Create a solve handle (setup, §8 row R0): copies X (n x p, column-major,
+ * Create a solve handle (per-tree setup): copies X (n x p, column-major,
  * FP64 host array) and y (n) to the device, keeps X in FP64 (certificates,
  * polish) and in the ADMM precision, forms c = X^T y and the inverse of
  * G = X X^T + rho I (b-update of Eq. b_update via the Woodbury identity,
@@ -151,6 +151,39 @@ int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, double* ub, do
  */
 int bnb_solve(bnb_handle* h, double rel_gap, double* beta_out, double* ub, double* lb,
               long long* nodes, int* status);
+
+/*
+ * Stepping form of bnb_solve, for callers that interleave several solves on
+ * one GPU (each handle runs on its own stream):
+ *   bnb_solve_start   initialise the node pool with the root and capture one
+ *                     round (refill, ADMM iterations, certificates, upper
+ *                     bounds, prune/branch) as a CUDA graph;
+ *   bnb_solve_launch  enqueue `rounds` rounds on the handle's stream and return
+ *                     at once (rounds after the tree is closed do no work);
+ *   bnb_solve_poll    wait for the enqueued rounds and report progress; sets
+ *                     done/status when the gap, the time or node limit, or the
+ *                     pool capacity ends the solve;
+ *   bnb_solve_finish  copy the incumbent and the final bounds out.
+ * bnb_solve is start + (launch 1, poll) until done + finish.
+ */
+typedef struct {
+  double ub, lb;            /* global bounds after the last completed round */
+  long long nodes;          /* nodes certified so far */
+  long long open_nodes;     /* nodes in the pool plus nodes in slots */
+  long long rounds;         /* rounds completed */
+  double seconds;           /* wall time since bnb_solve_start */
+  int done;                 /* 1 once the solve has stopped */
+  int status;               /* BNB_STATUS_* once done */
+} bnb_progress;
+
+int bnb_solve_start(bnb_handle* h, double rel_gap);
+int bnb_solve_launch(bnb_handle* h, int rounds);
+int bnb_solve_poll(bnb_handle* h, bnb_progress* out);
+int bnb_solve_finish(bnb_handle* h, double* beta_out, double* ub, double* lb, long long* nodes,
+                     int* status);
+
+/* The CUDA stream the handle runs on (cudaStream_t as void*). */
+void* bnb_stream(const bnb_handle* h);
 
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */

@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 # exported symbols (kept in step with include/bnb.h)
 SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
-           "bnb_get_stats", "bnb_last_error", "bnb_destroy")
+           "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
+           "bnb_stream", "bnb_get_stats", "bnb_last_error", "bnb_destroy")
 
 
 class bnb_options(ctypes.Structure):
@@ -47,6 +48,12 @@ class bnb_stats(ctypes.Structure):
                 ("pool_peak", ctypes.c_longlong), ("max_depth", ctypes.c_int),
                 ("solve_seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double)]
+
+
+class bnb_progress(ctypes.Structure):
+    _fields_ = [("ub", ctypes.c_double), ("lb", ctypes.c_double), ("nodes", ctypes.c_longlong),
+                ("open_nodes", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+                ("seconds", ctypes.c_double), ("done", ctypes.c_int), ("status", ctypes.c_int)]
 
 
 class BnbError(RuntimeError):
@@ -76,6 +83,11 @@ def load_library(path: str = LIB_PATH):
         "bnb_dual_bound": ([P, I, P, P, P], I),
         "bnb_upper_batch": ([P, I, P, P, P], I),
         "bnb_solve": ([P, D, P, P, P, P, P], I),
+        "bnb_solve_start": ([P, D], I),
+        "bnb_solve_launch": ([P, I], I),
+        "bnb_solve_poll": ([P, P], I),
+        "bnb_solve_finish": ([P, P, P, P, P, P], I),
+        "bnb_stream": ([P], P),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
         "bnb_destroy": ([P], None),
@@ -213,6 +225,38 @@ def bnb_solve(h: Handle, rel_gap: float):
                          ctypes.byref(nodes), ctypes.byref(status)), h.ptr)
     return dict(beta=beta, ub=ub.value, lb=lb.value, nodes=nodes.value,
                 status=STATUS_NAMES.get(status.value, status.value))
+
+
+def bnb_solve_start(h: Handle, rel_gap: float):
+    _check(load_library().bnb_solve_start(h.ptr, float(rel_gap)), h.ptr)
+
+
+def bnb_solve_launch(h: Handle, rounds: int = 1):
+    _check(load_library().bnb_solve_launch(h.ptr, int(rounds)), h.ptr)
+
+
+def bnb_solve_poll(h: Handle) -> dict:
+    pr = bnb_progress()
+    _check(load_library().bnb_solve_poll(h.ptr, ctypes.byref(pr)), h.ptr)
+    d = {k: getattr(pr, k) for k, _ in bnb_progress._fields_}
+    d["done"] = bool(d["done"])
+    d["status"] = STATUS_NAMES.get(d["status"], d["status"])
+    return d
+
+
+def bnb_solve_finish(h: Handle):
+    lib = load_library()
+    beta = np.empty(h.p, np.float64)
+    ub, lb = ctypes.c_double(), ctypes.c_double()
+    nodes, status = ctypes.c_longlong(), ctypes.c_int()
+    _check(lib.bnb_solve_finish(h.ptr, _ptr(beta), ctypes.byref(ub), ctypes.byref(lb),
+                                ctypes.byref(nodes), ctypes.byref(status)), h.ptr)
+    return dict(beta=beta, ub=ub.value, lb=lb.value, nodes=nodes.value,
+                status=STATUS_NAMES.get(status.value, status.value))
+
+
+def bnb_stream(h: Handle) -> int:
+    return load_library().bnb_stream(h.ptr) or 0
 
 
 def bnb_get_stats(h: Handle) -> dict:

@@ -254,6 +254,8 @@ static inline int g1d(long long m) {
 
 using namespace bnb;
 
+struct SolveState;
+
 struct bnb_handle {
   bnb_options opt{};
   int n = 0, p = 0;
@@ -268,6 +270,7 @@ struct bnb_handle {
   float* d_stage = nullptr;
   double* d_ubbeta = nullptr;
   cudaGraphExec_t graph = nullptr;
+  SolveState* solve = nullptr;
 };
 
 static int set_err(bnb_handle* h, int rc) {
@@ -438,6 +441,10 @@ extern "C" int bnb_create_device(const double* dX, const double* dy, int n, int 
 extern "C" void bnb_destroy(bnb_handle* h) {
   if (!h) return;
   if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->solve) {
+    if (h->solve->exec) cudaGraphExecDestroy(h->solve->exec);
+    delete h->solve;
+  }
   if (h->ef) { free_all(*h->ef); delete h->ef; }
   if (h->ed) { free_all(*h->ed); delete h->ed; }
   cudaFree(h->d_lb);
@@ -630,11 +637,25 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   return 0;
 }
 
+struct SolveState {
+  bool started = false, done = false;
+  int status = BNB_STATUS_OPTIMAL;
+  double gap = 0.0;
+  std::chrono::steady_clock::time_point t0;
+  cudaGraphExec_t exec = nullptr;
+  Status last{};
+};
+
 template <class R>
-static int solve_impl(bnb_handle* h, Engine<R>& e, double gap, double* beta_out, double* ub,
-                      double* lb, long long* nodes, int* status) {
+static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
   const bnb_options& o = h->opt;
-  auto t0 = std::chrono::steady_clock::now();
+  if (S.exec) {
+    cudaGraphExecDestroy(S.exec);
+    S.exec = nullptr;
+  }
+  S = SolveState{};
+  S.gap = gap;
+  S.t0 = std::chrono::steady_clock::now();
   double params[4] = {gap, 0, 0, 0};
   BNB_CUDA_OK(cudaMemcpyAsync(e.params_d, params, sizeof(params), cudaMemcpyHostToDevice, e.st));
   if (int rc = queue_init(e)) return rc;
@@ -642,7 +663,6 @@ static int solve_impl(bnb_handle* h, Engine<R>& e, double gap, double* beta_out,
   BNB_CUDA_OK(cudaStreamSynchronize(e.st));
   e.nodes = e.rounds = e.admm_iters = e.pruned = e.polished = e.pool_peak = 0;
   e.max_depth = 0;
-  cudaGraphExec_t exec = nullptr;
   if (o.use_graphs) {
     cudaGraph_t g;
     BNB_CUDA_OK(cudaStreamBeginCapture(e.st, cudaStreamCaptureModeThreadLocal));
@@ -650,66 +670,151 @@ static int solve_impl(bnb_handle* h, Engine<R>& e, double gap, double* beta_out,
     cudaError_t ce = cudaStreamEndCapture(e.st, &g);
     if (rc) return rc;
     if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&exec, g, 0);
+    ce = cudaGraphInstantiate(&S.exec, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
   }
-  int st_code = BNB_STATUS_OPTIMAL;
-  Status s{};
-  while (true) {
-    if (exec) {
-      BNB_CUDA_OK(cudaGraphLaunch(exec, e.st));
+  S.started = true;
+  return 0;
+}
+
+template <class R>
+static int solve_launch(bnb_handle* h, Engine<R>& e, SolveState& S, int rounds) {
+  if (!S.started) return fail(BNB_EINVAL, "bnb_solve_start was not called");
+  for (int r = 0; r < rounds; ++r) {
+    if (S.exec) {
+      BNB_CUDA_OK(cudaGraphLaunch(S.exec, e.st));
     } else if (int rc = round_body(h, e)) {
       return rc;
     }
-    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
-    s = *e.status_h;
-    e.rounds++;
-    e.admm_iters += 0;
-    e.nodes += s.retired;
-    if (s.pool_count > e.pool_peak) e.pool_peak = s.pool_count;
-    e.max_depth = s.max_depth;
-    if (s.active_slots == 0 && s.pool_count == 0) {
-      st_code = (s.error ? BNB_STATUS_GAP : BNB_STATUS_OPTIMAL);
-      break;
-    }
-    if (std::isfinite(s.ub) && (s.ub - s.lb) <= gap * std::fabs(s.ub)) { st_code = BNB_STATUS_GAP; break; }
-    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (el > o.time_limit_s) { st_code = BNB_STATUS_TIME_LIMIT; break; }
-    if (e.nodes >= o.max_nodes) { st_code = BNB_STATUS_NODE_LIMIT; break; }
-    if (s.free_top < 2 * e.K + 2) { st_code = BNB_STATUS_QUEUE_FULL; break; }
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  e.admm_iters = e.rounds * o.check_every;
+  return 0;
+}
+
+template <class R>
+static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* out) {
+  const bnb_options& o = h->opt;
+  if (!S.started) return fail(BNB_EINVAL, "bnb_solve_start was not called");
+  BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  const Status s = *e.status_h;
+  S.last = s;
+  e.rounds = s.rounds_total;
+  e.nodes = s.nodes_total;
+  if (s.pool_count > e.pool_peak) e.pool_peak = s.pool_count;
+  e.max_depth = s.max_depth;
+  const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+  if (!S.done) {
+    if (s.active_slots == 0 && s.pool_count == 0) {
+      S.done = true;
+      S.status = s.error ? BNB_STATUS_QUEUE_FULL : BNB_STATUS_OPTIMAL;
+      if (s.error && std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub))
+        S.status = BNB_STATUS_GAP;
+    } else if (std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub)) {
+      S.done = true;
+      S.status = BNB_STATUS_GAP;
+    } else if (s.error & 2) {
+      S.done = true;
+      S.status = BNB_STATUS_QUEUE_FULL;
+    } else if (el > o.time_limit_s) {
+      S.done = true;
+      S.status = BNB_STATUS_TIME_LIMIT;
+    } else if (e.nodes >= o.max_nodes) {
+      S.done = true;
+      S.status = BNB_STATUS_NODE_LIMIT;
+    } else if (s.free_top < 2 * e.K + 2) {
+      S.done = true;
+      S.status = BNB_STATUS_QUEUE_FULL;
+    }
+  }
+  if (out) {
+    out->ub = s.ub;
+    out->lb = (s.active_slots == 0 && s.pool_count == 0 && !s.error) ? s.ub : s.lb;
+    out->nodes = s.nodes_total;
+    out->open_nodes = s.pool_count + s.active_slots;
+    out->rounds = s.rounds_total;
+    out->seconds = el;
+    out->done = S.done ? 1 : 0;
+    out->status = S.status;
+  }
+  return 0;
+}
+
+template <class R>
+static int solve_finish(bnb_handle* h, Engine<R>& e, SolveState& S, double* beta_out, double* ub,
+                        double* lb, long long* nodes, int* status) {
+  if (!S.started) return fail(BNB_EINVAL, "bnb_solve_start was not called");
+  bnb_progress pr{};
+  if (int rc = solve_poll(h, e, S, &pr)) return rc;
   if (beta_out)
     BNB_CUDA_OK(cudaMemcpy(beta_out, e.inc_beta, sizeof(double) * e.p, cudaMemcpyDeviceToHost));
-  double lbv = s.lb;
-  if (s.active_slots == 0 && s.pool_count == 0 && !s.error) lbv = s.ub;
-  if (ub) *ub = s.ub;
-  if (lb) *lb = lbv;
-  if (nodes) *nodes = e.nodes;
-  if (status) *status = st_code;
-  bnb_stats& S = h->stats;
-  S.nodes = e.nodes;
-  S.rounds = e.rounds;
-  S.admm_iters = e.admm_iters;
-  S.pruned = s.pruned;
-  S.ub_polished = s.polished;
-  S.pool_peak = e.pool_peak;
-  S.max_depth = e.max_depth;
-  S.final_ub = s.ub;
-  S.final_lb = lbv;
-  S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (ub) *ub = pr.ub;
+  if (lb) *lb = pr.lb;
+  if (nodes) *nodes = pr.nodes;
+  if (status) *status = S.done ? S.status : BNB_STATUS_TIME_LIMIT;
+  bnb_stats& st = h->stats;
+  st.nodes = pr.nodes;
+  st.rounds = pr.rounds;
+  st.admm_iters = pr.rounds * h->opt.check_every;
+  st.pruned = S.last.pruned;
+  st.ub_polished = S.last.polished;
+  st.pool_peak = e.pool_peak;
+  st.max_depth = e.max_depth;
+  st.final_ub = pr.ub;
+  st.final_lb = pr.lb;
+  st.solve_seconds = pr.seconds;
+  if (S.exec) {
+    cudaGraphExecDestroy(S.exec);
+    S.exec = nullptr;
+  }
+  S.started = false;
   return 0;
+}
+
+static SolveState& state_of(bnb_handle* h) {
+  if (!h->solve) h->solve = new SolveState();
+  return *h->solve;
+}
+
+extern "C" int bnb_solve_start(bnb_handle* h, double rel_gap) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (!(rel_gap >= 0.0) || rel_gap >= 1.0) return set_err(h, fail(BNB_EINVAL, "rel_gap must be in [0, 1)"));
+  return dispatch(h, [&](auto& e) -> int { return solve_start(h, e, state_of(h), rel_gap); });
+}
+
+extern "C" int bnb_solve_launch(bnb_handle* h, int rounds) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  if (rounds < 0) return set_err(h, fail(BNB_EINVAL, "rounds must be >= 0"));
+  return dispatch(h, [&](auto& e) -> int { return solve_launch(h, e, state_of(h), rounds); });
+}
+
+extern "C" int bnb_solve_poll(bnb_handle* h, bnb_progress* out) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  return dispatch(h, [&](auto& e) -> int { return solve_poll(h, e, state_of(h), out); });
+}
+
+extern "C" int bnb_solve_finish(bnb_handle* h, double* beta_out, double* ub, double* lb,
+                                long long* nodes, int* status) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  return dispatch(h, [&](auto& e) -> int {
+    return solve_finish(h, e, state_of(h), beta_out, ub, lb, nodes, status);
+  });
 }
 
 extern "C" int bnb_solve(bnb_handle* h, double rel_gap, double* beta_out, double* ub, double* lb,
                          long long* nodes, int* status) {
-  if (!h) return fail(BNB_EINVAL, "handle is NULL");
-  if (!(rel_gap >= 0.0) || rel_gap >= 1.0) return set_err(h, fail(BNB_EINVAL, "rel_gap must be in [0, 1)"));
-  return dispatch(h, [&](auto& e) -> int {
-    return solve_impl(h, e, rel_gap, beta_out, ub, lb, nodes, status);
-  });
+  if (int rc = bnb_solve_start(h, rel_gap)) return rc;
+  bnb_progress pr{};
+  while (true) {
+    if (int rc = bnb_solve_launch(h, 1)) return rc;
+    if (int rc = bnb_solve_poll(h, &pr)) return rc;
+    if (pr.done) break;
+  }
+  return bnb_solve_finish(h, beta_out, ub, lb, nodes, status);
+}
+
+extern "C" void* bnb_stream(const bnb_handle* h) {
+  if (!h) return nullptr;
+  return h->ef ? (void*)h->ef->st : (h->ed ? (void*)h->ed->st : nullptr);
 }
 
 extern "C" int bnb_get_stats(const bnb_handle* h, bnb_stats* out) {

@@ -29,6 +29,8 @@ struct Status {                 // copied to the host after every round
   int error;                    // 1: depth limit reached (node kept as lost bound)
   int max_depth;
   double lost_lb;
+  long long nodes_total;        // nodes certified since the solve started
+  long long rounds_total;
 };
 
 template <class R>

@@ -84,8 +84,14 @@ __global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __res
       atomicOr(&sel_state[SS_ERROR], 1);
       atomicMin(lost_key, dkey(lbu));
     } else {
-      decision = 1;
       const int t = atomicSub(free_top, 2);
+      if (t < 2) {  // pool full: keep the node's bound as a lost bound, stop the solve
+        atomicAdd(free_top, 2);
+        atomicOr(&sel_state[SS_ERROR], 2);
+        atomicMin(lost_key, dkey(lbu));
+        goto decided;
+      }
+      decision = 1;
       c0 = free_stack[t - 1];
       c1 = free_stack[t - 2];
       atomicMax(pool_hw, (c0 > c1 ? c0 : c1) + 1);
@@ -111,6 +117,7 @@ __global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __res
       atomicMin(poolmin, dkey(lbu));
       atomicAdd(&sel_state[SS_COUNT], 2);
     }
+  decided:;
   }
   __syncthreads();
   if (!decision) return;
@@ -382,6 +389,8 @@ __global__ void k_status(int K, const int* __restrict__ slot_active,
   st->error = sel_state[SS_ERROR];
   st->max_depth = sel_state[SS_MAXDEPTH];
   st->lost_lb = (*lost_key == ~0ull) ? INFINITY : dkey_inv(*lost_key);
+  st->nodes_total += *ret_count;
+  st->rounds_total += 1;
 }
 
 static inline int pool_grid(long long qcap) {
@@ -394,6 +403,7 @@ int queue_init(Engine<R>& e) {
   BNB_CUDA_OK(cudaMemsetAsync(e.sel_state, 0, sizeof(int) * SS_WORDS, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.poolmin + 1, 0xff, sizeof(unsigned long long), e.st));  // lost key
+  BNB_CUDA_OK(cudaMemsetAsync(e.status_d, 0, sizeof(Status), e.st));
   k_queue_init<<<pool_grid(e.qcap), 256, 0, e.st>>>(e.qcap, e.wcap, e.free_stack, e.free_top,
                                                     e.pool_hw, e.warm_stack, e.warm_top,
                                                     e.pool_valid, e.pool_lb, e.pool_key,
