@@ -254,7 +254,13 @@ static inline int g1d(long long m) {
 
 using namespace bnb;
 
-struct SolveState;
+struct SolveState {
+  bool started = false, done = false;
+  int status = BNB_STATUS_OPTIMAL;
+  double gap = 0.0;
+  std::chrono::steady_clock::time_point t0;
+  cudaGraphExec_t exec = nullptr;
+  Status last{};
 
 struct bnb_handle {
   bnb_options opt{};
@@ -637,13 +643,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   return 0;
 }
 
-struct SolveState {
-  bool started = false, done = false;
-  int status = BNB_STATUS_OPTIMAL;
-  double gap = 0.0;
-  std::chrono::steady_clock::time_point t0;
-  cudaGraphExec_t exec = nullptr;
-  Status last{};
+
 };
 
 template <class R>
