@@ -261,6 +261,7 @@ struct SolveState {
   std::chrono::steady_clock::time_point t0;
   cudaGraphExec_t exec = nullptr;
   Status last{};
+};
 
 struct bnb_handle {
   bnb_options opt{};
@@ -644,7 +645,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
 }
 
 
-};
+
 
 template <class R>
 static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
