@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: certified branch-and-bound nodes per second on one B300.
+
+Workload (default "c2"): n=1000, p=5000, Toeplitz rho=0.3, k=10 true ones,
+SNR=5, lambda2=1e-3, M = 1.5 ||ridge on the true support||_inf, lambda0 from a
+sweep relative to max_j (X_j^T y)^2 / (2(||X_j||^2 + 2 lambda2)), node-batch
+width K=512, target gap 1e-4, FP32 ADMM with FP64 certificates.
+
+A "step" is one device round of the solve: refill free slots best-first,
+check_every ADMM iterations over all K slots, FP64 certificates of the nodes
+that stopped, branch pick + batched upper bound, prune/branch into the pool.
+  value     nodes certified per second over the timed steps (device time, CUDA
+            events on the solve's stream; L2 flushed with a 256 MiB write
+            before every step, outside the timed interval)
+  e2e       nodes certified per second through bnb_relax_batch with host
+            buffers: each step uploads K nodes (fixings + warm starts) from
+            pinned memory and reads back bounds, beta, z
+  fp64_path the same rounds on the plain FP64 GPU path (the comparator)
+  roofline  the dominant kernel of a profiled round (CUDA events per launch)
+  cpu_baseline the FP64 oracle's node solves on the host cores, bounded sample
+
+`--impl reference` times the FP64 oracle itself (the reference arm for this
+build): node solves of the same workload on the host cores.
+Multi-GPU (torchrun): every rank solves its own instance (independent trees,
+no collective on the data path); value = all ranks' nodes / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT, FP32_LANES = 148, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--lam0-frac", type=float, default=0.02)
+    ap.add_argument("--K", type=int, default=512)
+    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, inst_id, lam0_frac):
+    c = datagen.CONFIGS[name]
+    inst = datagen.config_instance(name, inst_id)
+    lam2 = c["lam2"]
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = lam0_frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    cfg = {"workload": name, "n": c["n"], "p": c["p"], "toeplitz_rho": c["rho"], "k_true": c["k"],
+           "snr": c["snr"], "lambda2": lam2, "lambda0": lam0, "lambda0_frac": lam0_frac, "M": M,
+           "seed": inst.seed}
+    return inst, lam0, lam2, M, cfg
+
+
+def node_sample(inst, K, seed, depth=8):
+    """K child-like nodes: random fixings of depth <= `depth` (datagen recipe)."""
+    rng = np.random.default_rng(seed)
+    return datagen.random_fixings(inst.p, K, rng, depth)
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------- mine
+
+
+def run_mine(args, rank, world):
+    import torch
+    import paper_2602_04551_b300 as bnb
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    inst, lam0, lam2, M, cfg = workload(args.workload, rank, args.lam0_frac)
+    s = torch.cuda.Stream()
+    opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+                                  precision=bnb.BNB_PREC_FP32, device=dev, stream=s.cuda_stream,
+                                  queue_capacity=1 << 21, time_limit_s=1e9)
+    h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    gap = 1e-4
+    bnb.bnb_solve_start(h, gap)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            bnb.bnb_solve_launch(h, 1)
+    before = bnb.bnb_solve_poll(h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(dev)
+    with torch.cuda.stream(s):
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(s)
+            bnb.bnb_solve_launch(h, 1)
+            ev[i][1].record(s)
+    s.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    after = bnb.bnb_solve_poll(h)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    nodes = after["nodes"] - before["nodes"]
+    stats = bnb.bnb_get_stats(h)
+    prof = bnb.bnb_profile_round(h)   # one extra round with per-stage CUDA events
+    prog = bnb.bnb_solve_poll(h)
+    kernels_per_round = stats.get("round_kernels", 0)
+    res = bnb.bnb_solve_finish(h)
+    h.close()
+    out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg,
+               kernels=kernels_per_round * args.steps, after=after, res=res)
+    if rank == 0:
+        out["e2e"] = run_e2e(args, inst, lam0, lam2, M, dev)
+        out["fp64"] = run_fp64(args, inst, lam0, lam2, M, dev)
+    return out
+
+
+def run_e2e(args, inst, lam0, lam2, M, dev):
+    """bnb_relax_batch with pinned host buffers: K child nodes per step."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+
+    K = args.K
+    opt = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every, device=dev,
+                                  precision=bnb.BNB_PREC_FP32)
+    h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
+    p = inst.p
+    root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    fix = pin((K, p), torch.int8)
+    wb = pin((K, p), torch.float32)
+    wv = pin((K, p), torch.float32)
+    fix[:] = node_sample(inst, K, 7)
+    wb[:] = root["beta"][0][None, :]
+    wb[fix == 0] = 0.0
+    wv[:] = root["v"][0][None, :]
+    h2d = fix.nbytes + wb.nbytes + wv.nbytes
+    d2h = K * 8 + 2 * K * p * 4 + K * 4 + K * 8 + K * 4
+    bnb.bnb_relax_batch(h, fix, wb, wv)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        bnb.bnb_relax_batch(h, fix, wb, wv)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h.close()
+    return {"value": K * args.e2e_steps / dt, "unit": "nodes/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "call": "bnb_relax_batch (host buffers)",
+            "nodes_per_step": K}
+
+
+def run_fp64(args, inst, lam0, lam2, M, dev):
+    """The same solve rounds on the plain FP64 GPU path."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+
+    s = torch.cuda.Stream()
+    opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every, device=dev,
+                                  precision=bnb.BNB_PREC_FP64, stream=s.cuda_stream,
+                                  queue_capacity=1 << 21, time_limit_s=1e9)
+    h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
+    bnb.bnb_solve_start(h, 1e-4)
+    bnb.bnb_solve_launch(h, max(1, args.warmup // 2))
+    before = bnb.bnb_solve_poll(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    bnb.bnb_solve_launch(h, args.fp64_steps)
+    e1.record(s)
+    s.synchronize()
+    after = bnb.bnb_solve_poll(h)
+    ms = e0.elapsed_time(e1)
+    bnb.bnb_solve_finish(h)
+    h.close()
+    return {"value": (after["nodes"] - before["nodes"]) / (ms / 1e3), "unit": "nodes/s",
+            "steps": args.fp64_steps, "ms_per_step": ms / args.fp64_steps}
+
+
+# ---------------------------------------------------------------------- oracle
+
+
+def run_oracle(args, seconds, inst=None, lam0=None, lam2=None, M=None, cfg=None):
+    """FP64 oracle node solves (as the oracle stands) on a bounded sample."""
+    from oracle import admm
+    if inst is None:
+        inst, lam0, lam2, M, cfg = workload(args.workload, 0, args.lam0_frac)
+    data = admm.AdmmData(inst.X, inst.y, 1.0)   # setup (inverse of X^T X + rho I): not timed
+    p = inst.p
+    root = admm.solve_node(data, np.full(p, -1, np.int8), lam0, lam2, M, tol=1e-4, max_iter=400)
+    fix = node_sample(inst, 64, 7)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(fix.shape[0]):
+        wb = root.beta.copy()
+        wb[fix[k] == 0] = 0.0
+        admm.solve_node(data, fix[k], lam0, lam2, M, beta0=wb, v0=root.v, tol=1e-4, max_iter=400)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "nodes/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} child nodes of the {cfg['workload']} workload (warm start from the "
+                      f"root, node tol 1e-4, <=400 ADMM iterations), FP64 numpy, {dt:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    inst, lam0, lam2, M, cfg = workload(args.workload, 0, args.lam0_frac)
+    budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        run_oracle(args, budget * 0.2, inst, lam0, lam2, M, cfg)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(run_oracle(args, budget, inst, lam0, lam2, M, cfg))
+    wall = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": "certified BnB nodes/s", "value": v, "unit": "nodes/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "nodes/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ main
+
+
+def roofline(out, args, pk):
+    """Dominant kernel of the profiled round, against the FP32 CUDA-core peak."""
+    prof = out["prof"]
+    cfg = out["cfg"]
+    n, p = cfg["n"], cfg["p"]
+    active = max(1, int(out["prog"]["active_slots"]))
+    total = {k: v[0] * v[1] for k, v in prof.items()}
+    top = max(total, key=total.get)
+    flops = {"gemm_xw": 2.0 * n * p * active, "gemm_xtu_prox": 2.0 * n * p * active,
+             "check_xbeta": 2.0 * n * p * active, "gemm_ginv_t": 2.0 * n * n * active}
+    name = top if top in flops else "gemm_xtu_prox"
+    ms = prof[name][0]
+    mhz = 2032.0
+    peak = SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    ach = flops[name] / (ms * 1e-3) / 1e12
+    share = total[name] / max(1e-12, sum(total.values()))
+    return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "share_of_round": share,
+            "peak_note": "FP32 FMA peak 148 SM x 128 lanes x 2 x 2032 MHz (derived)",
+            "flops_per_launch": flops[name], "ms_per_launch": ms, "active_slots": active}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out = run_mine(args, rank, world)
+    ms, nodes = out["ms"], out["nodes"]
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, float(nodes)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms, nodes = float(mx[0]), float(t[1])
+    if rank == 0:
+        pk = peaks()
+        cpu = None if args.no_cpu else run_oracle(args, args.cpu_seconds)
+        value = nodes / (ms / 1e3)
+        line = {
+            "metric": "certified BnB nodes/s (FP32 ADMM, FP64 certificates)",
+            "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(out["cfg"], K=args.K, check_every=args.check_every, gap=1e-4,
+                           l2="flushed (256 MiB write) before every step", parallelism="replicas"),
+            "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
+            "roofline": roofline(out, args, pk),
+            "fp64_path": dict(out["fp64"], ratio=value / max(1e-12, out["fp64"]["value"])),
+            "cpu_baseline": cpu,
+            "solve_progress": {"nodes": out["after"]["nodes"], "ub": out["after"]["ub"],
+                               "lb": out["after"]["lb"], "open_nodes": out["after"]["open_nodes"],
+                               "done": out["after"]["done"]},
+            "stages_ms": {k: v[0] for k, v in out["prof"].items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -170,6 +170,7 @@ typedef struct {
   double ub, lb;            /* global bounds after the last completed round */
   long long nodes;          /* nodes certified so far */
   long long open_nodes;     /* nodes in the pool plus nodes in slots */
+  long long active_slots;   /* nodes in slots */
   long long rounds;         /* rounds completed */
   double seconds;           /* wall time since bnb_solve_start */
   int done;                 /* 1 once the solve has stopped */
@@ -185,6 +186,16 @@ int bnb_solve_finish(bnb_handle* h, double* beta_out, double* ub, double* lb, lo
 /* The CUDA stream the handle runs on (cudaStream_t as void*). */
 void* bnb_stream(const bnb_handle* h);
 
+/*
+ * Diagnostics: run one round of the started solve outside the CUDA graph with
+ * CUDA events around each stage on the handle's stream.  stage_ms[k] receives
+ * the mean duration of stage k in milliseconds and stage_launches[k] how many
+ * times it ran; stages in order: select/refill, X W^T, split-K reduce,
+ * G^-1 T, U finalise, X^T U + fused prox/v, check X beta^T, stop test,
+ * certificate, branch pick, upper bound, push, status (13 stages).
+ */
+int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int nstages);
+
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */
   long long rounds;         /* device rounds run */
@@ -197,6 +208,7 @@ typedef struct {
   double solve_seconds;     /* wall time of the last bnb_solve */
   double setup_seconds;     /* wall time of bnb_create */
   double final_ub, final_lb;
+  int round_kernels;        /* kernels in one captured round (CUDA graph) */
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_get_stats", "bnb_last_error", "bnb_destroy")
+           "bnb_stream", "bnb_profile_round", "bnb_get_stats", "bnb_last_error", "bnb_destroy")
+STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
+          "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status")
 
 
 class bnb_options(ctypes.Structure):
@@ -47,12 +49,14 @@ class bnb_stats(ctypes.Structure):
                 ("pruned", ctypes.c_longlong), ("ub_polished", ctypes.c_longlong),
                 ("pool_peak", ctypes.c_longlong), ("max_depth", ctypes.c_int),
                 ("solve_seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double),
-                ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double)]
+                ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double),
+                ("round_kernels", ctypes.c_int)]
 
 
 class bnb_progress(ctypes.Structure):
     _fields_ = [("ub", ctypes.c_double), ("lb", ctypes.c_double), ("nodes", ctypes.c_longlong),
-                ("open_nodes", ctypes.c_longlong), ("rounds", ctypes.c_longlong),
+                ("open_nodes", ctypes.c_longlong), ("active_slots", ctypes.c_longlong),
+                ("rounds", ctypes.c_longlong),
                 ("seconds", ctypes.c_double), ("done", ctypes.c_int), ("status", ctypes.c_int)]
 
 
@@ -88,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_solve_poll": ([P, P], I),
         "bnb_solve_finish": ([P, P, P, P, P, P], I),
         "bnb_stream": ([P], P),
+        "bnb_profile_round": ([P, P, P, I], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
         "bnb_destroy": ([P], None),
@@ -253,6 +258,13 @@ def bnb_solve_finish(h: Handle):
                                 ctypes.byref(nodes), ctypes.byref(status)), h.ptr)
     return dict(beta=beta, ub=ub.value, lb=lb.value, nodes=nodes.value,
                 status=STATUS_NAMES.get(status.value, status.value))
+
+
+def bnb_profile_round(h: Handle) -> dict:
+    ms = np.zeros(len(STAGES), np.float64)
+    cnt = np.zeros(len(STAGES), np.int32)
+    _check(load_library().bnb_profile_round(h.ptr, _ptr(ms), _ptr(cnt), len(STAGES)), h.ptr)
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
 
 
 def bnb_stream(h: Handle) -> int:

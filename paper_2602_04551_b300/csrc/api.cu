@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "bnb.h"
 #include "engine.cuh"
@@ -634,13 +635,56 @@ extern "C" int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, dou
 template <class R>
 static int round_body(bnb_handle* h, Engine<R>& e) {
   const bnb_options& o = h->opt;
+  Profiler* pf = e.prof;
+  prof_begin(pf, e.st);
   if (int rc = queue_select_refill(e)) return rc;
+  prof_end(pf, e.st, PK_SELECT);
   if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
+  prof_begin(pf, e.st);
   if (int rc = certify(e, nullptr)) return rc;
+  prof_end(pf, e.st, PK_CERT);
+  prof_begin(pf, e.st);
   if (int rc = branch_support(e, false)) return rc;
+  prof_end(pf, e.st, PK_BRANCH);
+  prof_begin(pf, e.st);
   if (int rc = upper_bound(e, false)) return rc;
+  prof_end(pf, e.st, PK_UB);
+  prof_begin(pf, e.st);
   if (int rc = queue_push(e)) return rc;
+  prof_end(pf, e.st, PK_PUSH);
+  prof_begin(pf, e.st);
   if (int rc = queue_status(e)) return rc;
+  prof_end(pf, e.st, PK_STATUS);
+  return 0;
+}
+
+// One round of the current solve outside the graph, with CUDA events around
+// every stage on the handle's stream; returns per-stage mean milliseconds and
+// launch counts.
+template <class R>
+static int profile_round(bnb_handle* h, Engine<R>& e, double* ms, int* counts, int nk) {
+  Profiler pf;
+  e.prof = &pf;
+  int rc = round_body(h, e);
+  e.prof = nullptr;
+  if (rc) return rc;
+  BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  for (int k = 0; k < nk; ++k) {
+    ms[k] = 0.0;
+    counts[k] = 0;
+  }
+  for (size_t i = 0; i < pf.kind.size(); ++i) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, pf.ev[2 * i], pf.ev[2 * i + 1]);
+    const int k = pf.kind[i];
+    if (k < nk) {
+      ms[k] += t;
+      counts[k] += 1;
+    }
+  }
+  for (cudaEvent_t ev : pf.ev) cudaEventDestroy(ev);
+  for (int k = 0; k < nk; ++k)
+    if (counts[k]) ms[k] /= counts[k];
   return 0;
 }
 
@@ -671,6 +715,17 @@ static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
     cudaError_t ce = cudaStreamEndCapture(e.st, &g);
     if (rc) return rc;
     if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kern = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      cudaGraphNodeGetType(nd, &t);
+      kern += (t == cudaGraphNodeTypeKernel) ? 1 : 0;
+    }
+    h->stats.round_kernels = kern;
     ce = cudaGraphInstantiate(&S.exec, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return fail(BNB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
@@ -732,6 +787,7 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
     out->lb = (s.active_slots == 0 && s.pool_count == 0 && !s.error) ? s.ub : s.lb;
     out->nodes = s.nodes_total;
     out->open_nodes = s.pool_count + s.active_slots;
+    out->active_slots = s.active_slots;
     out->rounds = s.rounds_total;
     out->seconds = el;
     out->done = S.done ? 1 : 0;
@@ -811,6 +867,14 @@ extern "C" int bnb_solve(bnb_handle* h, double rel_gap, double* beta_out, double
     if (pr.done) break;
   }
   return bnb_solve_finish(h, beta_out, ub, lb, nodes, status);
+}
+
+extern "C" int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int nstages) {
+  if (!h || !stage_ms || !stage_launches) return fail(BNB_EINVAL, "NULL argument");
+  return dispatch(h, [&](auto& e) -> int {
+    if (!state_of(h).started) return fail(BNB_EINVAL, "bnb_solve_start was not called");
+    return profile_round(h, e, stage_ms, stage_launches, nstages);
+  });
 }
 
 extern "C" void* bnb_stream(const bnb_handle* h) {

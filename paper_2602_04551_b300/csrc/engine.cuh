@@ -33,6 +33,32 @@ struct Status {                 // copied to the host after every round
   long long rounds_total;
 };
 
+// Optional per-stage CUDA-event timing of a round (bnb_profile_round).
+enum ProfKind {
+  PK_SELECT = 0, PK_GEMM_XW, PK_REDUCE_T, PK_GEMM_GT, PK_FINAL_U, PK_GEMM_XTU, PK_CHECK, PK_STOP,
+  PK_CERT, PK_BRANCH, PK_UB, PK_PUSH, PK_STATUS, PK_COUNT
+};
+struct Profiler {
+  std::vector<int> kind;
+  std::vector<cudaEvent_t> ev;  // two per mark
+  cudaEvent_t open = nullptr;
+};
+inline void prof_begin(Profiler* pf, cudaStream_t st) {
+  if (!pf) return;
+  cudaEventCreate(&pf->open);
+  cudaEventRecord(pf->open, st);
+}
+inline void prof_end(Profiler* pf, cudaStream_t st, int kind) {
+  if (!pf) return;
+  cudaEvent_t e1;
+  cudaEventCreate(&e1);
+  cudaEventRecord(e1, st);
+  pf->kind.push_back(kind);
+  pf->ev.push_back(pf->open);
+  pf->ev.push_back(e1);
+  pf->open = nullptr;
+}
+
 template <class R>
 struct Engine {
   Prob P{};
@@ -98,6 +124,8 @@ struct Engine {
   Status* status_d = nullptr;
   Status* status_h = nullptr;   // pinned host mirror
   double* params_d = nullptr;   // [0] gap target used by pruning
+
+  Profiler* prof = nullptr;     // non-null only inside bnb_profile_round
 
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;
