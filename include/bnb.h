@@ -196,6 +196,17 @@ void* bnb_stream(const bnb_handle* h);
  */
 int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int nstages);
 
+/*
+ * Diagnostics: the tcgen05 tensor-core contraction on its own.  C = A B^T with
+ * A (M x Kd) and B (N x Kd) given K-major in FP64 device memory (element (m, k)
+ * at A[k + m*Kd]), split into BF16 operands (nsplit 1: hi; 3: hi/lo pairs,
+ * three products), tile width bn (128 or 256), `splits` split-K chunks summed
+ * in order; C is M x N column-major FP32 (device).  *err_out (host) receives the
+ * kernel's pipeline error word (0 when every bounded wait completed).
+ */
+int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd, int nsplit, int bn,
+                      int splits, float* dC, int* err_out);
+
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */
   long long rounds;         /* device rounds run */

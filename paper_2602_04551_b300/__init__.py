@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_profile_round", "bnb_get_stats", "bnb_last_error", "bnb_destroy")
+           "bnb_stream", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_get_stats",
+           "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status")
 
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_solve_finish": ([P, P, P, P, P, P], I),
         "bnb_stream": ([P], P),
         "bnb_profile_round": ([P, P, P, I], I),
+        "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
         "bnb_destroy": ([P], None),
@@ -265,6 +267,14 @@ def bnb_profile_round(h: Handle) -> dict:
     cnt = np.zeros(len(STAGES), np.int32)
     _check(load_library().bnb_profile_round(h.ptr, _ptr(ms), _ptr(cnt), len(STAGES)), h.ptr)
     return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(STAGES)}
+
+
+def bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit=1, bn=128, splits=1, dC=None):
+    """Tensor-core contraction C = A B^T on torch CUDA tensors (FP64 in, FP32 out)."""
+    err = ctypes.c_int(0)
+    _check(load_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
+                                            _ptr(dC), ctypes.byref(err)))
+    return err.value
 
 
 def bnb_stream(h: Handle) -> int:

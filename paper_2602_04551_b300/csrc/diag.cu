@@ -1,0 +1,84 @@
+// diag.cu -- diagnostics entry point: the tcgen05 contraction on its own.
+//
+// bnb_tc_gemm_check runs C = A B^T for FP64 inputs split into BF16 operands
+// (1 term: hi only; 3 terms: hi/lo pairs), K-major A (M x Kred) and B (N x Kred),
+// with split-K over `splits` chunks summed in order, and writes C (M x N,
+// column-major FP32).  Used by the tests to check the tensor-core kernel against
+// a plain product before it is used inside the ADMM iteration.
+#include <cuda_bf16.h>
+#include "bnb.h"
+#include "tc_host.cuh"
+
+namespace bnb {
+
+__global__ void k_sum_splits_f32(const float* __restrict__ part, int S, long long m,
+                                 float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    float a = part[i];
+    for (int z = 1; z < S; ++z) a += part[z * m + i];
+    out[i] = a;
+  }
+}
+
+template <int BN, int NS>
+static int run_check(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kd,
+                     int splits, float* part, int* err, int* ns_out) {
+  int ns = 1;
+  tc_chunk(Kd, splits, &ns);
+  *ns_out = ns;
+  return tc_gemm<BN, NS>(st, A, B, M, N, Kd, splits, nullptr, err,
+                         TcEpiStore{part, (long long)M, (long long)M * N});
+}
+
+}  // namespace bnb
+
+extern "C" int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd,
+                                 int nsplit, int bn, int splits, float* dC, int* dev_err) {
+  using namespace bnb;
+  if (M <= 0 || N <= 0 || Kd <= 0 || (nsplit != 1 && nsplit != 3) || (bn != 128 && bn != 256))
+    return BNB_EINVAL;
+  cudaStream_t st = 0;
+  const long long ld = ((long long)Kd + 7) / 8 * 8;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  float* part = nullptr;
+  int* err = nullptr;
+  const long long sp = splits < 1 ? 1 : splits;
+  cudaError_t ce = cudaSuccess;
+  ce = ce ? ce : cudaMalloc(&ah, sizeof(__nv_bfloat16) * ld * M);
+  ce = ce ? ce : cudaMalloc(&al, sizeof(__nv_bfloat16) * ld * M);
+  ce = ce ? ce : cudaMalloc(&bh, sizeof(__nv_bfloat16) * ld * N);
+  ce = ce ? ce : cudaMalloc(&bl, sizeof(__nv_bfloat16) * ld * N);
+  ce = ce ? ce : cudaMalloc(&part, sizeof(float) * (size_t)M * N * (sp + 1));
+  ce = ce ? ce : cudaMalloc(&err, sizeof(int));
+  int rc = ce == cudaSuccess ? 0 : BNB_ENOMEM;
+  if (!rc) rc = cudaMemset(err, 0, sizeof(int)) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(ah, 0, sizeof(__nv_bfloat16) * ld * M) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(al, 0, sizeof(__nv_bfloat16) * ld * M) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(bh, 0, sizeof(__nv_bfloat16) * ld * N) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(bl, 0, sizeof(__nv_bfloat16) * ld * N) == cudaSuccess ? 0 : BNB_ECUDA;
+  // A, B are K-major: element (k, row) of a column-major Kd x rows array
+  if (!rc) rc = split_bf16(st, dA, Kd, M, Kd, ld, false, ah, al);
+  if (!rc) rc = split_bf16(st, dB, Kd, N, Kd, ld, false, bh, bl);
+  TcOperand A{ah, al, M, Kd, ld}, B{bh, bl, N, Kd, ld};
+  int ns = 1;
+  if (!rc) {
+    if (bn == 128 && nsplit == 1) rc = run_check<128, 1>(st, A, B, M, N, Kd, splits, part, err, &ns);
+    if (bn == 128 && nsplit == 3) rc = run_check<128, 3>(st, A, B, M, N, Kd, splits, part, err, &ns);
+    if (bn == 256 && nsplit == 1) rc = run_check<256, 1>(st, A, B, M, N, Kd, splits, part, err, &ns);
+    if (bn == 256 && nsplit == 3) rc = run_check<256, 3>(st, A, B, M, N, Kd, splits, part, err, &ns);
+  }
+  if (!rc) {
+    k_sum_splits_f32<<<256, 256, 0, st>>>(part, ns, (long long)M * N, dC);
+    rc = cudaGetLastError() == cudaSuccess ? 0 : BNB_ECUDA;
+  }
+  if (!rc) rc = cudaMemcpy(dev_err, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : BNB_ECUDA;
+  cudaFree(ah);
+  cudaFree(al);
+  cudaFree(bh);
+  cudaFree(bl);
+  cudaFree(part);
+  cudaFree(err);
+  return rc;
+}

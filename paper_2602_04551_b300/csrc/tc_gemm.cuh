@@ -1,0 +1,262 @@
+// tc_gemm.cuh -- Blackwell (sm_103a) tensor-core contraction for the ADMM products.
+//
+//   C[m, n] = sum_{k in chunk z} A[m, k] B[n, k]        (both operands K-major, BF16)
+//
+// Tiles of 128 x BN outputs, 64-wide K steps.  One CTA = 6 warps:
+//   warp 0  (one thread)  TMA producer: cp.async.bulk.tensor 2D loads of the A and B
+//                         tiles (128-byte swizzle) into an S-stage shared-memory ring,
+//                         completion counted on the stage's "full" mbarrier;
+//   warp 1  (one thread)  MMA issuer: tcgen05.mma kind::f16 (BF16 x BF16 -> FP32) into a
+//                         128 x BN accumulator in tensor memory; tcgen05.commit frees a
+//                         stage ("empty" mbarrier) and finally signals "done";
+//                         the whole warp allocates / frees the TMEM columns;
+//   warps 2-5             epilogue: tcgen05.ld of the accumulator rows (each warp reads
+//                         its 32-lane quarter of TMEM), handed to the epilogue functor.
+// NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
+// accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
+// FP32-class arithmetic of the ADMM path.  NSPLIT = 1 is the plain BF16 product.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records an error code in
+// *err and leaves its loops, so a fault in the pipeline never hangs the GPU.
+#pragma once
+#include <cuda.h>
+#include "common.cuh"
+
+namespace bnb {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;             // 64 BF16 = 128 bytes: one swizzle row
+constexpr long long WAIT_LIMIT = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait on the phase with parity `ph` (at most WAIT_LIMIT polls and 2 s);
+// false (and *err set) on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph, int* err, int code) {
+  const uint32_t a = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(ph)
+        : "memory");
+    if (ok) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+  }
+  atomicOr(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;            // start address
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)2 << 61;                  // layout: 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: dense, D = F32, A = B = BF16, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+      " [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int BN, int NSPLIT>
+struct Geo {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (NSPLIT == 3 ? 2 : 1);
+  static constexpr int STAGES = (NSPLIT == 3) ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+struct Maps {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+};
+
+// Epilogue interface: epi(row m, first column n, 16 accumulator values, M, N)
+template <int BN, int NSPLIT, class Epi>
+__global__ void __launch_bounds__(192, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant__ CUtensorMap ma_lo,
+               const __grid_constant__ CUtensorMap mb_hi, const __grid_constant__ CUtensorMap mb_lo,
+               int M, int N, int Kred, int kchunk, const int* __restrict__ active, int* err, Epi epi) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (active != nullptr) {
+    int any = 0;
+    for (int j = threadIdx.x; j < BN; j += blockDim.x)
+      if (n0 + j < N && active[n0 + j]) any = 1;
+    if (!__syncthreads_or(any)) return;
+  }
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(Kred, kbeg + kchunk);
+  const int nk = (kend - kbeg + BK - 1) / BK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  auto sA = [&](int s, int part) { return base + s * G::STAGE_BYTES + part * (G::A_BYTES + G::B_BYTES); };
+  auto sB = [&](int s, int part) { return sA(s, part) + G::A_BYTES; };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % S;
+      if (kb >= S && !mbar_wait(&empty_bar[s], ((kb / S) & 1) ^ 1, err, 1)) break;
+      mbar_expect_tx(&full_bar[s], G::STAGE_BYTES);
+      const int k = kbeg + kb * BK;
+      tma_load_2d(sA(s, 0), &ma_hi, &full_bar[s], k, m0);
+      tma_load_2d(sB(s, 0), &mb_hi, &full_bar[s], k, n0);
+      if (NSPLIT == 3) {
+        tma_load_2d(sA(s, 1), &ma_lo, &full_bar[s], k, m0);
+        tma_load_2d(sB(s, 1), &mb_lo, &full_bar[s], k, n0);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % S;
+      ok = mbar_wait(&full_bar[s], (kb / S) & 1, err, 2);
+      if (!ok) break;
+      fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t ah = smem_desc_sw128(sA(s, 0) + kk * 32);
+        const uint64_t bh = smem_desc_sw128(sB(s, 0) + kk * 32);
+        mma_bf16(tmem, ah, bh, idesc, acc);
+        if (NSPLIT == 3) {
+          const uint64_t al = smem_desc_sw128(sA(s, 1) + kk * 32);
+          const uint64_t bl = smem_desc_sw128(sB(s, 1) + kk * 32);
+          mma_bf16(tmem, ah, bl, idesc, 1u);
+          mma_bf16(tmem, al, bh, idesc, 1u);
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&done_bar);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: each warp owns TMEM lanes [32 q, 32 q + 32)
+    const int q = warp & 3;
+    const bool ok = mbar_wait(&done_bar, 0, err, 4);
+    fence_after();
+    const int row = m0 + 32 * q + lane;
+    if (ok) {
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+        epi(row, n0 + c, v, M, N);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace tc
+}  // namespace bnb

@@ -1,0 +1,84 @@
+// tc_host.cuh -- launch helpers for the tcgen05 contraction (host side).
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace bnb {
+
+int make_map_bf16(CUtensorMap* map, const void* ptr, long long inner, long long rows, long long ld,
+                  int box_rows);
+int split_bf16(cudaStream_t st, const double* x, long long rows, long long cols, long long ld_in,
+               long long ld_out, bool transpose, __nv_bfloat16* hi, __nv_bfloat16* lo);
+
+// Operand pair: hi (and lo for the 3-term product) BF16, K-major, rows x K.
+struct TcOperand {
+  const __nv_bfloat16* hi = nullptr;
+  const __nv_bfloat16* lo = nullptr;
+  long long rows = 0, kdim = 0, ld = 0;
+};
+
+inline int tc_splits_for(int M, int N, int BN, int Kred, int want_blocks = 2 * 148) {
+  const int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN);
+  int s = (want_blocks + tiles - 1) / tiles;
+  const int maxs = (Kred + tc::BK - 1) / tc::BK;
+  if (s > maxs) s = maxs;
+  return s < 1 ? 1 : s;
+}
+
+// number of split-K chunks actually launched for a requested count (each >= 1 K step)
+inline int tc_chunk(int Kred, int splits, int* nsplit) {
+  int steps = (Kred + tc::BK - 1) / tc::BK;
+  if (splits > steps) splits = steps;
+  if (splits < 1) splits = 1;
+  const int per = (steps + splits - 1) / splits;
+  *nsplit = (steps + per - 1) / per;
+  return per * tc::BK;
+}
+
+template <int BN, int NSPLIT, class Epi>
+int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
+            int splits, const int* active, int* err, Epi epi) {
+  using G = tc::Geo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
+  if (NSPLIT == 3) {
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
+  } else {
+    al = ah;
+    bl = bh;
+  }
+  int ns = 1;
+  const int kchunk = tc_chunk(Kred, splits, &ns);
+  auto kern = tc::tc_gemm_kernel<BN, NSPLIT, Epi>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    attr_set = true;
+  }
+  dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, ns);
+  kern<<<grid, 192, G::SMEM, st>>>(ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// Split-K partial store: C + z * zstride [m + n * ldc] = acc
+struct TcEpiStore {
+  float* __restrict__ C;
+  long long ldc, zstride;
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N) const {
+    if (m >= M) return;
+    float* Cz = C + (long long)blockIdx.z * zstride;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = n0 + j;
+      if (n < N) Cz[m + (long long)n * ldc] = v[j];
+    }
+  }
+};
+
+}  // namespace bnb

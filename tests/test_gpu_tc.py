@@ -1,0 +1,48 @@
+"""The tcgen05 tensor-core contraction on its own (through the C ABI diagnostics
+entry), against plain products of the same operands.
+
+Tolerances: one BF16 term is compared with the FP64 product of the BF16-rounded
+operands (only the FP32 accumulation differs: <= 1e-5 of sum |a||b|); three
+terms (hi/lo splits) with the FP64 product of the unrounded operands
+(<= 4e-5 of sum |a||b|: each operand keeps ~16 significant bits).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+bnb = pytest.importorskip("paper_2602_04551_b300")
+
+CASES = [
+    # M, N, Kd, nsplit, bn, splits
+    (128, 128, 64, 1, 128, 1),
+    (256, 128, 512, 1, 128, 1),
+    (200, 100, 1000, 1, 128, 1),      # ragged M, N and K tails
+    (200, 300, 1000, 1, 256, 3),      # split-K, two N tiles
+    (256, 256, 640, 3, 128, 1),
+    (333, 77, 1111, 3, 128, 4),
+    (128, 512, 4096, 3, 256, 2),
+]
+
+
+@pytest.mark.parametrize("M,N,Kd,nsplit,bn,splits", CASES)
+def test_tc_gemm_matches_plain_product(M, N, Kd, nsplit, bn, splits):
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 13 + Kd)
+    A = torch.randn(M, Kd, generator=g, dtype=torch.float64)
+    B = torch.randn(N, Kd, generator=g, dtype=torch.float64)
+    dA, dB = A.cuda(), B.cuda()
+    dC = torch.empty(N, M, dtype=torch.float32, device="cuda")   # M x N column-major
+    err = bnb.bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit, bn, splits, dC)
+    assert err == 0
+    C = dC.cpu().double().T.numpy()
+    if nsplit == 1:
+        Ar = A.to(torch.bfloat16).double()
+        Br = B.to(torch.bfloat16).double()
+        ref = (Ar @ Br.T).numpy()
+        scale = (Ar.abs() @ Br.abs().T).numpy()
+        tol = 1e-5
+    else:
+        ref = (A @ B.T).numpy()
+        scale = (A.abs() @ B.abs().T).numpy()
+        tol = 4e-5
+    assert np.all(np.abs(C - ref) <= tol * scale + 1e-6), np.max(np.abs(C - ref) / (scale + 1e-30))
