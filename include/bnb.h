@@ -129,6 +129,31 @@ int bnb_relax_batch_device(bnb_handle* h, int K, const int8_t* fix, const float*
 int bnb_dual_bound(bnb_handle* h, int K, const int8_t* fix, const double* r, double* lb);
 
 /*
+ * Allocation-free dual bound.  The paper has no counterpart: this is a service
+ * entry point for callers that must not allocate device memory (for example code
+ * that runs under another framework which already owns the GPU's memory budget
+ * through its own allocator, or latency-critical loops that cannot afford
+ * cudaMalloc's implicit synchronisation or an allocation failure mid-run).
+ * Computes the same bound as bnb_dual_bound, without a handle:
+ *   lb[k] = -1/2 ||r_k||^2 + y^T r_k - sum_i nu_i(|X_i^T r_k|),   k < K,
+ * all in FP64.  Every pointer is device memory on the current device:
+ *   dX  n x p FP64 column-major;  dy  n;  dfix  K x p int8 (-1 free, 0 F0, 1 F1);
+ *   dr  K x n FP64 residuals (node-major);  dlb  K outputs.
+ * Runs asynchronously on `stream` (cudaStream_t, NULL = default stream).
+ * Scratch: a fixed 8 MiB device array inside the library (every GPU that loads the
+ * library keeps it until the process exits); a call needs K * (ceil(p/256) + 2)
+ * doubles of it and returns BNB_EINVAL beyond 2^20 doubles (or K > 65535).
+ * The first call on a device looks up the array's device address once (with that
+ * device current); make that first call before any stream capture.  All calls on
+ * a device share the array: calls whose kernels overlap on the GPU race on it, so
+ * order them (one stream, or events).  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ */
+int bnb_dual_bound_static(const double* dX, const double* dy, int n, int p, double lambda0,
+                          double lambda2, double M, int K, const int8_t* dfix, const double* dr,
+                          double* dlb, void* stream);
+
+/*
  * Batched upper bound (Sections 3.3-3.4, Eq. upperboundbeta): for each of K
  * supports (K x p uint8 mask, host), projected gradient with t/(t+3)
  * extrapolation and Armijo backtracking in the ADMM precision, then an FP64

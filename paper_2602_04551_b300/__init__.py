@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_get_stats",
+           "bnb_stream", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_dual_bound_static",
+           "bnb_get_stats",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status")
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_stream": ([P], P),
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
+        "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
         "bnb_destroy": ([P], None),
@@ -211,6 +213,14 @@ def bnb_dual_bound(h: Handle, fix, r):
     lb = np.empty(K, np.float64)
     _check(lib.bnb_dual_bound(h.ptr, K, _ptr(fix), _ptr(r), _ptr(lb)), h.ptr)
     return lb
+
+
+def bnb_dual_bound_static(dX, dy, n, p, lambda0, lambda2, M, dfix, dr, dlb, stream=0):
+    """Allocation-free dual bound on device tensors (see include/bnb.h)."""
+    K = int(dfix.shape[0])
+    _check(load_library().bnb_dual_bound_static(_ptr(dX), _ptr(dy), int(n), int(p), float(lambda0),
+                                                float(lambda2), float(M), K, _ptr(dfix), _ptr(dr),
+                                                _ptr(dlb), ctypes.c_void_p(stream or 0)))
 
 
 def bnb_upper_batch(h: Handle, support):
