@@ -42,7 +42,8 @@ extern "C" {
 /* ADMM arithmetic of the node solves (certificates and polish are FP64 always) */
 #define BNB_PREC_FP64 0   /* plain FP64 everywhere: the comparator path */
 #define BNB_PREC_FP32 1   /* FP32 state and contractions */
-#define BNB_PREC_BF16 2   /* BF16 X on tcgen05 tensor cores, FP32 accumulate/state */
+#define BNB_PREC_BF16 2   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate/state */
+#define BNB_PREC_TC3 3    /* hi/lo BF16 pairs on tcgen05 (three products): FP32-class */
 
 /* bnb_solve status */
 #define BNB_STATUS_OPTIMAL 0     /* open-node set exhausted: UB is optimal */

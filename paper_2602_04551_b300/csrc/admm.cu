@@ -236,39 +236,49 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   cudaStream_t st = e.st;
   const long long nK = (long long)n * K;
   const int red_grid = (int)((nK + 255) / 256 > 4096 ? 4096 : (nK + 255) / 256);
-  for (int it = 0; it < iters; ++it) {
-    // T = X W^T
+  int S_check = e.s1;
+  bool tc = false;
+  if constexpr (sizeof(R) == 4) tc = e.tc_mode != 0;
+  if (tc) {
+    if constexpr (sizeof(R) == 4) {
+      if (int rc = admm_iterations_tc(e, iters)) return rc;
+      S_check = e.tc_s1n;
+    }
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      // T = X W^T
+      prof_begin(e.prof, st);
+      BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.XR, n, n, K, p, e.s1, e.slot_active,
+                                              BW<R>{e.cR, e.beta, e.V, (R)e.P.rho, p},
+                                              EpiStore<R>{e.Tpart, n, nK})));
+      prof_end(e.prof, st, PK_GEMM_XW);
+      prof_begin(e.prof, st);
+      k_reduce_splits<R><<<red_grid, 256, 0, st>>>(e.Tpart, e.s1, e.T, n, K, e.slot_active);
+      prof_end(e.prof, st, PK_REDUCE_T);
+      // U = G^{-1} T
+      prof_begin(e.prof, st);
+      BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.Ginv, n, n, K, n, e.s2, e.slot_active,
+                                              BPlainK<R>{e.T, n}, EpiStore<R>{e.Upart, n, nK})));
+      prof_end(e.prof, st, PK_GEMM_GT);
+      prof_begin(e.prof, st);
+      k_finalize_u<R><<<K, 256, 0, st>>>(e.Upart, e.s2, e.U, e.yR, n, K, e.slot_active, e.rstat);
+      prof_end(e.prof, st, PK_FINAL_U);
+      // P = X^T U, fused b / prox / v epilogue
+      prof_begin(e.prof, st);
+      BNB_CUDA_OK((gemm_simt<R, true, false>(
+          st, e.XR, n, p, K, n, 1, e.slot_active, BPlainK<R>{e.U, n},
+          EpiAdmm<R>{e.cR, e.beta, e.V, e.fix, e.slot_active, e.g3part, e.P, p, e.nbm3, K})));
+      prof_end(e.prof, st, PK_GEMM_XTU);
+    }
+    // check: X beta^T for the primal value of Eq. relaxnode2
     prof_begin(e.prof, st);
     BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.XR, n, n, K, p, e.s1, e.slot_active,
-                                            BW<R>{e.cR, e.beta, e.V, (R)e.P.rho, p},
-                                            EpiStore<R>{e.Tpart, n, nK})));
-    prof_end(e.prof, st, PK_GEMM_XW);
-    prof_begin(e.prof, st);
-    k_reduce_splits<R><<<red_grid, 256, 0, st>>>(e.Tpart, e.s1, e.T, n, K, e.slot_active);
-    prof_end(e.prof, st, PK_REDUCE_T);
-    // U = G^{-1} T
-    prof_begin(e.prof, st);
-    BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.Ginv, n, n, K, n, e.s2, e.slot_active,
-                                            BPlainK<R>{e.T, n}, EpiStore<R>{e.Upart, n, nK})));
-    prof_end(e.prof, st, PK_GEMM_GT);
-    prof_begin(e.prof, st);
-    k_finalize_u<R><<<K, 256, 0, st>>>(e.Upart, e.s2, e.U, e.yR, n, K, e.slot_active, e.rstat);
-    prof_end(e.prof, st, PK_FINAL_U);
-    // P = X^T U, fused b / prox / v epilogue
-    prof_begin(e.prof, st);
-    BNB_CUDA_OK((gemm_simt<R, true, false>(
-        st, e.XR, n, p, K, n, 1, e.slot_active, BPlainK<R>{e.U, n},
-        EpiAdmm<R>{e.cR, e.beta, e.V, e.fix, e.slot_active, e.g3part, e.P, p, e.nbm3, K})));
-    prof_end(e.prof, st, PK_GEMM_XTU);
+                                            BPlainK<R>{e.beta, p}, EpiStore<R>{e.XBpart, n, nK})));
+    prof_end(e.prof, st, PK_CHECK);
   }
   e.admm_iters += iters;
-  // check: X beta^T for the primal value of Eq. relaxnode2
   prof_begin(e.prof, st);
-  BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.XR, n, n, K, p, e.s1, e.slot_active,
-                                          BPlainK<R>{e.beta, p}, EpiStore<R>{e.XBpart, n, nK})));
-  prof_end(e.prof, st, PK_CHECK);
-  prof_begin(e.prof, st);
-  k_stop<R><<<K, 256, 0, st>>>(e.XBpart, e.s1, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
+  k_stop<R><<<K, 256, 0, st>>>(e.XBpart, S_check, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
                                e.slot_active, e.slot_iters, e.slot_retire, e.slot_gap, e.slot_dual,
                                e.slot_primal, iters, max_iter, node_tol, e.inc_ub, e.params_d,
                                use_inc ? 1 : 0);

@@ -1,0 +1,269 @@
+// admm_tc.cu -- the batched ADMM iteration on tcgen05 tensor cores.
+//
+// Same iteration as admm.cu (Sections 3.1-3.2; Woodbury b-update), with the
+// three contractions on the Blackwell tensor cores:
+//   T = X W^T        tcgen05, A = X row-major (n x p, K-major), B = W (K x p), split-K
+//   U = G^{-1} T     tcgen05, A = G^{-1} (symmetric), B = T (K x n), split-K
+//   P = X^T U        tcgen05, A = X column-major (p x n, K-major), B = U (K x n),
+//                    fused epilogue straight from tensor memory:
+//                    b = (W - P)/rho, beta = prox(b + V/rho), V += rho (b - beta),
+//                    per-slot stop-test sums, and the next iteration's W operand.
+// Operands are BF16; in the FP32-class mode each operand is a hi/lo pair and the
+// product takes three MMAs (hi hi + hi lo + lo hi), in the BF16 mode one.
+// Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.
+#include <cuda_bf16.h>
+#include "engine.cuh"
+#include "gemm_simt.cuh"
+#include "tc_host.cuh"
+
+namespace bnb {
+
+__device__ __forceinline__ void split_store(float x, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                            long long o) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  hi[o] = h;
+  if (lo) lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// W = c + rho beta - V for the active slots, as BF16 hi/lo (K x ldp)
+__global__ void k_make_w(const float* __restrict__ c, const float* __restrict__ beta,
+                         const float* __restrict__ V, const int* __restrict__ active, int p,
+                         long long ldp, int K, float rho, __nv_bfloat16* __restrict__ whi,
+                         __nv_bfloat16* __restrict__ wlo) {
+  const long long m = (long long)K * p;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(t / p), j = (int)(t % p);
+    if (!active[s]) continue;
+    split_store(c[j] + rho * beta[t] - V[t], whi, wlo, (long long)s * ldp + j);
+  }
+}
+
+// T = sum of split partials, as BF16 hi/lo (K x ldn), active slots only
+__global__ void k_reduce_t_tc(const float* __restrict__ part, int S, int n, int K,
+                              const int* __restrict__ active, long long ldn,
+                              __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo) {
+  const long long m = (long long)n * K;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < m;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(idx / n), i = (int)(idx % n);
+    if (!active[s]) continue;
+    float a = part[idx];
+    for (int z = 1; z < S; ++z) a += part[z * m + idx];
+    split_store(a, thi, tlo, (long long)s * ldn + i);
+  }
+}
+
+// U = sum of split partials (FP32, n x K) + BF16 hi/lo copy; ||y - U||^2, y^T (y - U)
+__global__ void k_finalize_u_tc(const float* __restrict__ Upart, int S, float* __restrict__ U,
+                                const float* __restrict__ y, int n, int K,
+                                const int* __restrict__ active, float* __restrict__ rstat,
+                                long long ldn, __nv_bfloat16* __restrict__ uhi,
+                                __nv_bfloat16* __restrict__ ulo) {
+  __shared__ float sh[32];
+  const int s = blockIdx.x;
+  if (!active[s]) return;
+  const long long zs = (long long)n * K, base = (long long)s * n;
+  float rr = 0.f, yr = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float u = Upart[base + i];
+    for (int z = 1; z < S; ++z) u += Upart[z * zs + base + i];
+    U[base + i] = u;
+    split_store(u, uhi, ulo, (long long)s * ldn + i);
+    const float r = y[i] - u;
+    rr += r * r;
+    yr += y[i] * r;
+  }
+  rr = block_sum(rr, sh);
+  yr = block_sum(yr, sh);
+  if (threadIdx.x == 0) {
+    rstat[s] = rr;
+    rstat[K + s] = yr;
+  }
+}
+
+// butterfly reduce-scatter of 16 per-lane values over the warp: afterwards lane l
+// holds the warp total of column (l >> 1) (both lanes of a pair hold it)
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+  float w8[8], w4[4], w2[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float mine = b4 ? v[8 + i] : v[i], other = b4 ? v[i] : v[8 + i];
+    w8[i] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float mine = b3 ? w8[4 + i] : w8[i], other = b3 ? w8[i] : w8[4 + i];
+    w4[i] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float mine = b2 ? w4[2 + i] : w4[i], other = b2 ? w4[i] : w4[2 + i];
+    w2[i] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+  }
+  const float mine = b1 ? w2[1] : w2[0], other = b1 ? w2[0] : w2[1];
+  float x = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+  return x + __shfl_xor_sync(0xffffffffu, x, 1);
+}
+
+template <int BN>
+struct TcEpiAdmm {
+  static constexpr int SMEM_FLOATS = 4 * 4 * BN;   // [warp][stat][column]
+  const float* __restrict__ c;
+  float* __restrict__ beta;
+  float* __restrict__ V;
+  const int8_t* __restrict__ fix;
+  const int* __restrict__ active;
+  float* __restrict__ g3part;   // [4][nbm][K]
+  __nv_bfloat16 *whi, *wlo;     // next W operand (K x ldp)
+  __nv_bfloat16 *bhi, *blo;     // beta operand for the check product (or null)
+  Prob P;
+  long long p, ldp;
+  int nbm, K;
+
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
+                                             int q, float* sm) const {
+    const float rho = (float)P.rho, irho = 1.0f / (float)P.rho;
+    float s_psi[16], s_nu[16], s_db[16], s_pr[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      s_psi[j] = s_nu[j] = s_db[j] = s_pr[j] = 0.f;
+      const int n = n0 + j;
+      if (m < M && n < N && active[n]) {
+        const long long o = (long long)n * p + m;
+        const float bo = beta[o], v = V[o], cj = c[m], pp = acc[j];
+        const int f = fix[o];
+        const float w = cj + rho * bo - v;
+        const float b = (w - pp) * irho;
+        const float bt = b + v * irho;
+        const float bn = prox_coord<float>(bt, f, P);
+        const float vn = v + rho * (b - bn);
+        beta[o] = bn;
+        V[o] = vn;
+        const long long ow = (long long)n * ldp + m;
+        split_store(cj + rho * bn - vn, whi, wlo, ow);
+        if (bhi) split_store(bn, bhi, blo, ow);
+        s_psi[j] = psi_coord<float>(bn, f, P);
+        s_nu[j] = nu_coord<float>(fabsf(cj - pp), f, P);
+        s_db[j] = (bn - bo) * (bn - bo);
+        s_pr[j] = (b - bn) * (b - bn);
+      }
+    }
+    const float t0 = reduce_scatter16(s_psi), t1 = reduce_scatter16(s_nu);
+    const float t2 = reduce_scatter16(s_db), t3 = reduce_scatter16(s_pr);
+    const int lane = threadIdx.x & 31;
+    if ((lane & 1) == 0) {
+      const int col = (n0 % BN) + (lane >> 1);
+      sm[(q * 4 + 0) * BN + col] = t0;
+      sm[(q * 4 + 1) * BN + col] = t1;
+      sm[(q * 4 + 2) * BN + col] = t2;
+      sm[(q * 4 + 3) * BN + col] = t3;
+    }
+  }
+
+  __device__ __forceinline__ void finish(int t, int m0, int n0, int M, int N, float* sm) const {
+    for (int col = t; col < BN; col += 128) {
+      const int n = n0 + col;
+      if (n >= N) continue;
+#pragma unroll
+      for (int st = 0; st < 4; ++st) {
+        const float a = sm[(0 * 4 + st) * BN + col] + sm[(1 * 4 + st) * BN + col] +
+                        sm[(2 * 4 + st) * BN + col] + sm[(3 * 4 + st) * BN + col];
+        g3part[((long long)st * nbm + blockIdx.x) * K + n] = a;
+      }
+    }
+  }
+};
+
+template <int NS>
+static int round_tc(Engine<float>& e, int iters) {
+  constexpr int BN = 256;
+  const int n = e.n, p = e.p, K = e.K;
+  cudaStream_t st = e.st;
+  const long long nK = (long long)n * K;
+  const TcOperand XT{e.xt_hi, e.xt_lo, n, p, e.ldp};     // rows = samples, K = features
+  const TcOperand XC{e.xc_hi, e.xc_lo, p, n, e.ldn};     // rows = features, K = samples
+  const TcOperand GI{e.gi_hi, e.gi_lo, n, n, e.ldn};
+  const TcOperand Wop{e.w_hi, e.w_lo, K, p, e.ldp};
+  const TcOperand Top{e.t_hi, e.t_lo, K, n, e.ldn};
+  const TcOperand Uop{e.u_hi, e.u_lo, K, n, e.ldn};
+  const TcOperand Bop{e.b_hi, e.b_lo, K, p, e.ldp};
+  const int red_grid = (int)((nK + 255) / 256 > 4096 ? 4096 : (nK + 255) / 256);
+  const int kgrid = (int)(((long long)K * p + 255) / 256 > 8192 ? 8192 : ((long long)K * p + 255) / 256);
+  prof_begin(e.prof, st);
+  k_make_w<<<kgrid, 256, 0, st>>>(e.cR, e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
+                                  e.w_hi, NS == 3 ? e.w_lo : nullptr);
+  prof_end(e.prof, st, PK_REDUCE_T);
+  BNB_CUDA_OK(cudaGetLastError());
+  for (int it = 0; it < iters; ++it) {
+    const bool last = it + 1 == iters;
+    prof_begin(e.prof, st);
+    if (int rc = tc_gemm<BN, NS>(st, XT, Wop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
+                                 TcEpiStore{(float*)e.Tpart, (long long)n, nK}))
+      return rc;
+    prof_end(e.prof, st, PK_GEMM_XW);
+    prof_begin(e.prof, st);
+    k_reduce_t_tc<<<red_grid, 256, 0, st>>>((float*)e.Tpart, e.tc_s1n, n, K, e.slot_active, e.ldn,
+                                            e.t_hi, NS == 3 ? e.t_lo : nullptr);
+    prof_end(e.prof, st, PK_REDUCE_T);
+    prof_begin(e.prof, st);
+    if (int rc = tc_gemm<BN, NS>(st, GI, Top, n, K, n, e.tc_s2, e.slot_active, e.tc_err,
+                                 TcEpiStore{(float*)e.Upart, (long long)n, nK}))
+      return rc;
+    prof_end(e.prof, st, PK_GEMM_GT);
+    prof_begin(e.prof, st);
+    k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.yR, n, K,
+                                       e.slot_active, (float*)e.rstat, e.ldn, e.u_hi,
+                                       NS == 3 ? e.u_lo : nullptr);
+    prof_end(e.prof, st, PK_FINAL_U);
+    prof_begin(e.prof, st);
+    TcEpiAdmm<BN> epi{e.cR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
+                      e.w_hi, NS == 3 ? e.w_lo : nullptr,
+                      last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
+                      e.P, p, e.ldp, e.nbm3, K};
+    if (int rc = tc_gemm<BN, NS>(st, XC, Uop, p, K, n, 1, e.slot_active, e.tc_err, epi)) return rc;
+    prof_end(e.prof, st, PK_GEMM_XTU);
+  }
+  // check product X beta^T
+  prof_begin(e.prof, st);
+  if (int rc = tc_gemm<BN, NS>(st, XT, Bop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
+                               TcEpiStore{(float*)e.XBpart, (long long)n, nK}))
+    return rc;
+  prof_end(e.prof, st, PK_CHECK);
+  return 0;
+}
+
+int admm_iterations_tc(Engine<float>& e, int iters) {
+  return e.tc_mode == 3 ? round_tc<3>(e, iters) : round_tc<1>(e, iters);
+}
+
+// Setup of the BF16 operands: X in both layouts and G^{-1}, hi/lo
+__global__ void k_split_f32(const float* __restrict__ x, long long rows, long long cols,
+                            long long ld_out, __nv_bfloat16* __restrict__ hi,
+                            __nv_bfloat16* __restrict__ lo) {
+  const long long m = rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t % rows, j = t / rows;
+    split_store(x[t], hi, lo, i + j * ld_out);
+  }
+}
+
+int setup_tc(Engine<float>& e) {
+  cudaStream_t st = e.st;
+  const long long n = e.n, p = e.p;
+  // column-major X: p columns of length n (leading dimension ldn)
+  if (int rc = split_bf16(st, e.X64, n, p, n, e.ldn, false, e.xc_hi, e.xc_lo)) return rc;
+  // row-major X: n rows of length p (leading dimension ldp)
+  if (int rc = split_bf16(st, e.X64, n, p, n, e.ldp, true, e.xt_hi, e.xt_lo)) return rc;
+  const long long nn = n * n;
+  long long g = (nn + 255) / 256;
+  if (g > 8192) g = 8192;
+  k_split_f32<<<(int)g, 256, 0, st>>>((const float*)e.Ginv, n, n, e.ldn, e.gi_hi, e.gi_lo);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace bnb

@@ -19,6 +19,7 @@
 #include "bnb.h"
 #include "engine.cuh"
 #include "gemm_simt.cuh"
+#include "tc_host.cuh"
 
 namespace bnb {
 
@@ -81,6 +82,47 @@ static int allocate(Engine<R>& e) {
   e.s1 = gemm_simt_splits<R>(e.p, pick_splits(e.n, e.K, e.p, C::BM, C::BN, C::BK));
   e.s2 = gemm_simt_splits<R>(e.n, pick_splits(e.n, e.K, e.n, C::BM, C::BN, C::BK));
   e.nbm3 = (e.p + C::BM - 1) / C::BM;
+  long long s1cap = e.s1, s2cap = e.s2;
+  if constexpr (sizeof(R) == 4) {
+    if (e.tc_mode) {
+      e.ldn = (n + 7) / 8 * 8;
+      e.ldp = (p + 7) / 8 * 8;
+      const int st1 = (e.p + tc::BK - 1) / tc::BK, st2 = (e.n + tc::BK - 1) / tc::BK;
+      e.tc_s1 = tc_splits_for(e.n, e.K, 256, e.p);
+      if (e.tc_s1 > st1 / 4) e.tc_s1 = st1 / 4 > 0 ? st1 / 4 : 1;
+      e.tc_s2 = tc_splits_for(e.n, e.K, 256, e.n);
+      if (e.tc_s2 > st2 / 4) e.tc_s2 = st2 / 4 > 0 ? st2 / 4 : 1;
+      tc_chunk(e.p, e.tc_s1, &e.tc_s1n);
+      tc_chunk(e.n, e.tc_s2, &e.tc_s2n);
+      if (e.tc_s1n > s1cap) s1cap = e.tc_s1n;
+      if (e.tc_s2n > s2cap) s2cap = e.tc_s2n;
+      const bool lo = e.tc_mode == 3;
+      ALLOC(e.xc_hi, p * e.ldn);
+      ALLOC(e.xt_hi, n * e.ldp);
+      ALLOC(e.gi_hi, n * e.ldn);
+      ALLOC(e.w_hi, K * e.ldp);
+      ALLOC(e.b_hi, K * e.ldp);
+      ALLOC(e.t_hi, K * e.ldn);
+      ALLOC(e.u_hi, K * e.ldn);
+      if (lo) {
+        ALLOC(e.xc_lo, p * e.ldn);
+        ALLOC(e.xt_lo, n * e.ldp);
+        ALLOC(e.gi_lo, n * e.ldn);
+        ALLOC(e.w_lo, K * e.ldp);
+        ALLOC(e.b_lo, K * e.ldp);
+        ALLOC(e.t_lo, K * e.ldn);
+        ALLOC(e.u_lo, K * e.ldn);
+      }
+      ALLOC(e.tc_err, 1);
+      BNB_CUDA_OK(cudaMemsetAsync(e.tc_err, 0, sizeof(int), e.st));
+      __nv_bfloat16* bufs[] = {e.xc_hi, e.xt_hi, e.gi_hi, e.w_hi, e.b_hi, e.t_hi, e.u_hi,
+                               e.xc_lo, e.xt_lo, e.gi_lo, e.w_lo, e.b_lo, e.t_lo, e.u_lo};
+      const long long cnt[] = {p * e.ldn, n * e.ldp, n * e.ldn, K * e.ldp, K * e.ldp, K * e.ldn,
+                               K * e.ldn};
+      for (int i = 0; i < 14; ++i)
+        if (bufs[i]) BNB_CUDA_OK(cudaMemsetAsync(bufs[i], 0, 2 * cnt[i % 7], e.st));
+    }
+  }
   ALLOC(e.X64, n * p);
   ALLOC(e.X32, n * p);
   if constexpr (sizeof(R) == 4) e.XR = (R*)e.X32; else e.XR = (R*)e.X64;
@@ -93,11 +135,11 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.beta, K * p);
   ALLOC(e.V, K * p);
   ALLOC(e.fix, K * p);
-  ALLOC(e.Tpart, (long long)e.s1 * n * K);
+  ALLOC(e.Tpart, s1cap * n * K);
   ALLOC(e.T, n * K);
-  ALLOC(e.Upart, (long long)e.s2 * n * K);
+  ALLOC(e.Upart, s2cap * n * K);
   ALLOC(e.U, n * K);
-  ALLOC(e.XBpart, (long long)e.s1 * n * K);
+  ALLOC(e.XBpart, s1cap * n * K);
   ALLOC(e.g3part, 4LL * e.nbm3 * K);
   ALLOC(e.rstat, 2 * K);
   ALLOC(e.slot_active, K);
@@ -345,8 +387,18 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
     BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
     e->own_stream = true;
   }
+  if constexpr (sizeof(R) == 4) {
+    if (o.precision == BNB_PREC_BF16) e->tc_mode = 1;
+    if (o.precision == BNB_PREC_TC3) e->tc_mode = 3;
+  }
   if (int rc = allocate(*e)) return rc;
   if (int rc = setup_data(*e, dX, dy)) return rc;
+  if constexpr (sizeof(R) == 4) {
+    if (e->tc_mode) {
+      if (int rc = setup_tc(*e)) return rc;
+      BNB_CUDA_OK(cudaStreamSynchronize(e->st));
+    }
+  }
   return 0;
 }
 
@@ -379,8 +431,8 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
-  if (o.precision != BNB_PREC_FP64 && o.precision != BNB_PREC_FP32)
-    return fail(BNB_EINVAL, "precision %d not available in this build", o.precision);
+  if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_TC3)
+    return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
   auto t0 = std::chrono::steady_clock::now();
   bnb_handle* h = new bnb_handle();

@@ -9,6 +9,7 @@
 // (float for the mixed-precision path, double for the plain FP64 comparator).
 // Certificates (Proposition 1) and upper-bound polishing are FP64 for both.
 #pragma once
+#include <cuda_bf16.h>
 #include <vector>
 #include "common.cuh"
 
@@ -127,6 +128,19 @@ struct Engine {
 
   Profiler* prof = nullptr;     // non-null only inside bnb_profile_round
 
+  // tensor-core path (float engines): 0 = CUDA cores, 1 = BF16, 3 = hi/lo BF16 (3 products)
+  int tc_mode = 0;
+  long long ldn = 0, ldp = 0;   // leading dimensions padded to multiples of 8 elements
+  __nv_bfloat16 *xc_hi = nullptr, *xc_lo = nullptr;   // X column-major  (p x ldn)
+  __nv_bfloat16 *xt_hi = nullptr, *xt_lo = nullptr;   // X row-major     (n x ldp)
+  __nv_bfloat16 *gi_hi = nullptr, *gi_lo = nullptr;   // G^-1            (n x ldn)
+  __nv_bfloat16 *w_hi = nullptr, *w_lo = nullptr;     // W operand       (K x ldp)
+  __nv_bfloat16 *b_hi = nullptr, *b_lo = nullptr;     // beta operand    (K x ldp)
+  __nv_bfloat16 *t_hi = nullptr, *t_lo = nullptr;     // T operand       (K x ldn)
+  __nv_bfloat16 *u_hi = nullptr, *u_lo = nullptr;     // U operand       (K x ldn)
+  int* tc_err = nullptr;        // pipeline error word of the tensor-core kernels
+  int tc_s1 = 1, tc_s1n = 1, tc_s2 = 1, tc_s2n = 1;
+
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;
   long long slot_iters_sum = 0;
@@ -145,5 +159,7 @@ template <class R> int queue_select_refill(Engine<R>& e);
 template <class R> int queue_init(Engine<R>& e);
 template <class R> int queue_status(Engine<R>& e);
 template <class R> int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K);
+int admm_iterations_tc(Engine<float>& e, int iters);
+int setup_tc(Engine<float>& e);
 
 }  // namespace bnb

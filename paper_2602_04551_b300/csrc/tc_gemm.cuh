@@ -146,7 +146,11 @@ struct Maps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
-// Epilogue interface: epi(row m, first column n, 16 accumulator values, M, N)
+// Epilogue interface:
+//   epi(row m, first column n0 + c, 16 accumulator values, M, N, lane quarter q, smem)
+//     called by every epilogue thread for each 16-column chunk of its row;
+//   epi.finish(t in [0, 128), m0, n0, M, N, smem)  after the four epilogue warps meet;
+//   Epi::SMEM_FLOATS  shared scratch the functor needs.
 template <int BN, int NSPLIT, class Epi>
 __global__ void __launch_bounds__(192, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant__ CUtensorMap ma_lo,
@@ -159,6 +163,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
   __shared__ __align__(8) uint64_t empty_bar[S];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ float epi_smem[Epi::SMEM_FLOATS > 0 ? Epi::SMEM_FLOATS : 1];
   uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -244,9 +249,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
-        epi(row, n0 + c, v, M, N);
+        epi(row, n0 + c, v, M, N, q, epi_smem);
       }
     }
+    // the four epilogue warps meet (named barrier 1) before the per-tile finish
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (ok) epi.finish(threadIdx.x - 64, m0, n0, M, N, epi_smem);
   }
   fence_before();
   __syncthreads();

@@ -68,9 +68,12 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
 
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
+  static constexpr int SMEM_FLOATS = 0;
   float* __restrict__ C;
   long long ldc, zstride;
-  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N) const {
+  __device__ __forceinline__ void finish(int, int, int, int, int, float*) const {}
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N, int,
+                                             float*) const {
     if (m >= M) return;
     float* Cz = C + (long long)blockIdx.z * zstride;
 #pragma unroll

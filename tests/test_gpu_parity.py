@@ -22,7 +22,12 @@ from oracle import relax, admm, pgd, ub as oub, bnb as obnb, brute
 pytestmark = pytest.mark.gpu
 
 bnb = pytest.importorskip("paper_2602_04551_b300")
-PRECS = [pytest.param(1, id="fp32"), pytest.param(0, id="fp64")]
+PRECS = [pytest.param(1, id="fp32"), pytest.param(0, id="fp64"), pytest.param(3, id="tc3"),
+         pytest.param(2, id="bf16")]
+# one-iteration tolerance per precision (relative to max(1, |ref|))
+ITER_TOL = {0: 1e-8, 1: 2e-4, 3: 3e-4, 2: 3e-2}
+# node tolerance used for converged-bound checks per precision
+NODE_TOL = {0: 1e-7, 1: 1e-5, 3: 1e-5, 2: 1e-3}
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "c1_optimum.json")
 
 
@@ -90,7 +95,7 @@ def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed):
         out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
     assert np.all(out["iters"] == 1)
     data = admm.AdmmData(inst.X, inst.y, 1.0)
-    tol = 1e-8 if prec == 0 else 2e-4
+    tol = ITER_TOL[prec]
     for k in rows:
         b, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
                                          fix[k], lam0, lam2, M)
@@ -124,13 +129,15 @@ def test_relaxation_bound_valid_and_tight(prec):
     rng = np.random.default_rng(5)
     K = 10
     fix = datagen.random_fixings(inst.p, K, rng, 6)
-    tol = 1e-7 if prec == 0 else 1e-5
+    tol = NODE_TOL[prec]
     with _handle(inst, lam0, lam2, M, prec, K=16, node_tol=tol, max_admm_iter=20000) as h:
         out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
     for k in range(K):
         _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
         assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))          # valid (Prop. 1.1)
         assert out["lb"][k] >= opt - 20 * tol * max(1.0, abs(opt))      # tight at convergence
+        if prec == 2:
+            continue  # BF16 iterates: z/branch checked on the FP32-class paths
         z = out["z"][k]
         zref = relax.z_of_beta(out["beta"][k].astype(np.float64), fix[k], lam0, lam2, M)
         np.testing.assert_allclose(z, zref, atol=1e-6)
@@ -143,7 +150,7 @@ def test_relaxation_bound_valid_and_tight(prec):
 # ------------------------------------------------------------------ upper bound
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", PRECS[:2])
 @pytest.mark.parametrize("mfac", [1.5, 0.25])   # box loose / binding
 def test_upper_batch_matches_oracle(prec, mfac):
     inst, lam0, lam2, M = _inst("c2_small", 2, mfac=mfac)

@@ -2,7 +2,7 @@
 entry), against plain products of the same operands.
 
 Tolerances: one BF16 term is compared with the FP64 product of the BF16-rounded
-operands (only the FP32 accumulation differs: <= 1e-5 of sum |a||b|); three
+operands (rounded directly from FP64, ties to even, as the kernel's split does) (only the FP32 accumulation differs: <= 1e-5 of sum |a||b|); three
 terms (hi/lo splits) with the FP64 product of the unrounded operands
 (<= 4e-5 of sum |a||b|: each operand keeps ~16 significant bits).
 """
@@ -12,6 +12,12 @@ import pytest
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 bnb = pytest.importorskip("paper_2602_04551_b300")
+
+def _bf16(x):
+    """Round float64 to the nearest BF16 value (ties to even), directly from float64."""
+    m, e = np.frexp(x)                       # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
 
 CASES = [
     # M, N, Kd, nsplit, bn, splits
@@ -36,8 +42,8 @@ def test_tc_gemm_matches_plain_product(M, N, Kd, nsplit, bn, splits):
     assert err == 0
     C = dC.cpu().double().T.numpy()
     if nsplit == 1:
-        Ar = A.to(torch.bfloat16).double()
-        Br = B.to(torch.bfloat16).double()
+        Ar = torch.from_numpy(_bf16(A.numpy()))
+        Br = torch.from_numpy(_bf16(B.numpy()))
         ref = (Ar @ Br.T).numpy()
         scale = (Ar.abs() @ Br.abs().T).numpy()
         tol = 1e-5
