@@ -43,6 +43,8 @@ sys.path.insert(0, ROOT)
 import datagen  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PREC = {"fp32": 1, "bf16": 2, "tc3": 3, "fp64": 0}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "tc3": "bf16x3", "fp64": "f64"}
 SM_COUNT, FP32_LANES = 148, 128
 
 
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--prime-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc3", "bf16"])
+    ap.add_argument("--rho", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -145,8 +149,8 @@ def run_mine(args, rank, world):
     inst, lam0, lam2, M, cfg = workload(args.workload, rank, args.lam0_frac)
     s = torch.cuda.Stream()
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
-                                  precision=bnb.BNB_PREC_FP32, device=dev, stream=s.cuda_stream,
-                                  queue_capacity=1 << 21, time_limit_s=1e9)
+                                  precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
+                                  queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
@@ -206,7 +210,7 @@ def run_e2e(args, inst, lam0, lam2, M, dev):
 
     K = args.K
     opt = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every, device=dev,
-                                  precision=bnb.BNB_PREC_FP32)
+                                  precision=PREC[args.precision], rho=args.rho)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     p = inst.p
     root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
@@ -242,10 +246,10 @@ def run_fp64(args, inst, lam0, lam2, M, dev):
     K, p = args.K, inst.p
     fix = node_sample(inst, K, 7)
     res = {}
-    for name, prec in (("fp32", bnb.BNB_PREC_FP32), ("fp64", bnb.BNB_PREC_FP64)):
+    for name, prec in (("mixed", PREC[args.precision]), ("fp64", bnb.BNB_PREC_FP64)):
         s = torch.cuda.Stream()
         opt = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every, device=dev,
-                                      precision=prec, stream=s.cuda_stream)
+                                      precision=prec, stream=s.cuda_stream, rho=args.rho)
         h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
         root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
         wb = np.repeat(root["beta"], K, 0)
@@ -270,7 +274,7 @@ def run_fp64(args, inst, lam0, lam2, M, dev):
                      "mean_iters": float(dit.float().mean()), "lb_mean": float(dlb.mean())}
         h.close()
     return {"value": res["fp64"]["nodes_per_s"], "unit": "nodes/s",
-            "fp32_same_batch": res["fp32"], "fp64": res["fp64"],
+            "mixed_same_batch": res["mixed"], "fp64": res["fp64"],
             "how": "K child nodes of the workload, warm start from the root, node tol 1e-4; "
                    "bnb_relax_batch_device, CUDA events"}
 
@@ -378,15 +382,16 @@ def main():
         cpu = None if args.no_cpu else run_oracle(args, args.cpu_seconds)
         value = nodes / (ms / 1e3)
         line = {
-            "metric": "certified BnB nodes/s (FP32 ADMM, FP64 certificates)",
+            "metric": "certified BnB nodes/s (mixed-precision ADMM, FP64 certificates)",
             "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": dict(out["cfg"], K=args.K, check_every=args.check_every, gap=1e-4,
+                           precision=args.precision, rho=args.rho,
                            l2="flushed (256 MiB write) before every step", parallelism="replicas"),
             "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
             "roofline": roofline(out, args, pk),
-            "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["fp32_same_batch"]["nodes_per_s"]
+            "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]
                               / max(1e-12, out["fp64"]["value"])),
             "prime": out["prime"],
             "cpu_baseline": cpu,
