@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--prime-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc3", "bf16"])
-    ap.add_argument("--rho", type=float, default=1.0)
+    ap.add_argument("--precision", default="tc3", choices=["fp32", "tc3", "bf16"])
+    ap.add_argument("--rho", type=float, default=0.0, help="0: chosen by the autotuner")
     return ap.parse_args()
 
 
@@ -147,6 +147,16 @@ def run_mine(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     inst, lam0, lam2, M, cfg = workload(args.workload, rank, args.lam0_frac)
+    tune = None
+    if args.rho <= 0:
+        from paper_2602_04551_b300 import autotune
+        best, entry = autotune.autotune(inst.X, inst.y, lam0, lam2, M, device=dev, use_cache=False,
+                                        grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
+                                              "check_every": [args.check_every]})
+        args.rho = float(best["rho"])
+        tune = {"chosen": best, "seconds": entry["seconds"],
+                "trials": [{k: t[k] for k in ("rho", "nodes_per_s", "mean_iters", "lb_mean")}
+                           for t in entry["trials"]]}
     s = torch.cuda.Stream()
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
@@ -193,7 +203,7 @@ def run_mine(args, rank, world):
     kernels_per_round = stats.get("round_kernels", 0)
     res = bnb.bnb_solve_finish(h)
     h.close()
-    out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg,
+    out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                kernels=kernels_per_round * args.steps, after=after, res=res,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
                       "active_slots": before["active_slots"], "open_nodes": before["open_nodes"]})
@@ -409,6 +419,7 @@ def main():
             "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]
                               / max(1e-12, out["fp64"]["value"])),
             "prime": out["prime"],
+            "autotune": out["tune"],
             "cpu_baseline": cpu,
             "solve_progress": {"nodes": out["after"]["nodes"], "ub": out["after"]["ub"],
                                "lb": out["after"]["lb"], "open_nodes": out["after"]["open_nodes"],

@@ -61,7 +61,7 @@ typedef struct {
   int max_admm_iter;     /* ADMM iteration cap per node visit, default 400 */
   int check_every;       /* ADMM iterations between stop tests (one "round"), default 10 */
   int batch_K;           /* node slots solved together, default 512 */
-  int precision;         /* BNB_PREC_*, default BNB_PREC_FP32 */
+  int precision;         /* BNB_PREC_*, default BNB_PREC_TC3 */
   int use_graphs;        /* capture each round in a CUDA graph, default 1 */
   double time_limit_s;   /* bnb_solve wall-clock limit, default 3600 */
   long long max_nodes;   /* bnb_solve node limit, default 1e9 */
@@ -87,6 +87,11 @@ int bnb_options_default(bnb_options* opt);
 int bnb_create(const double* X_colmajor, const double* y, int n, int p,
                double lambda0, double lambda2, const bnb_options* opt,
                bnb_handle** out);
+
+/* Device memory (bytes) that bnb_create would hold for an n x p problem with
+ * these options (its allocations, staging and setup temporaries); used to admit
+ * solves under an HBM budget.  Allocates nothing. */
+int bnb_footprint(int n, int p, const bnb_options* opt, size_t* bytes);
 
 /* Same as bnb_create with X and y already on the device (FP64, column-major).
  * The data are copied; the caller's buffers may be freed after the call. */

@@ -24,7 +24,7 @@ BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16, BNB_PREC_TC3 = 0, 1, 2, 3
 STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit"}
 
 # exported symbols (kept in step with include/bnb.h)
-SYMBOLS = ("bnb_options_default", "bnb_create", "bnb_create_device", "bnb_relax_batch",
+SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
            "bnb_stream", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_dual_bound_static",
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     sig = {
         "bnb_options_default": ([P], I),
         "bnb_create": ([P, P, I, I, D, D, P, P], I),
+        "bnb_footprint": ([I, I, P, P], I),
         "bnb_create_device": ([P, P, I, I, D, D, P, P], I),
         "bnb_relax_batch": ([P, I, P, P, P, I, P, P, P, P, P, P, P], I),
         "bnb_relax_batch_device": ([P, I, P, P, P, I, P, P, P, P, P, P, P], I),
@@ -156,6 +157,12 @@ class Handle:
 
     def __exit__(self, *a):
         self.close()
+
+
+def bnb_footprint(n: int, p: int, options: bnb_options) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load_library().bnb_footprint(int(n), int(p), ctypes.byref(options), ctypes.byref(b)))
+    return int(b.value)
 
 
 def bnb_create(X, y, lambda0: float, lambda2: float, options: bnb_options) -> Handle:

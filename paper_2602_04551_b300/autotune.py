@@ -1,0 +1,107 @@
+"""Autotuner for the node-batch solve: ADMM penalty rho, batch width K, stop-test
+interval (check_every) and arithmetic mode, chosen per problem by measurement.
+
+Each trial creates a handle with the candidate options, solves the root once and
+then a batch of K child nodes warm-started from it (random fixings of small
+depth, the shape of the nodes the tree produces) through bnb_relax_batch_device,
+timed with CUDA events on the handle's stream.  The score is certified nodes per
+second; the mean FP64 bound of the batch is recorded so that a mode whose bounds
+are markedly weaker (e.g. plain BF16) is not chosen for speed alone.
+Results are cached in a JSON file keyed by (n, p) bucket.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import time
+
+import numpy as np
+
+DEFAULT_GRID = {
+    "rho": [0.1, 0.2, 0.3, 0.5, 1.0],
+    "batch_K": [256, 512, 1024],
+    "check_every": [10],
+    "precision": [3],
+}
+
+
+def _cache_path():
+    return os.environ.get("BNB_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "bnb_autotune.json"))
+
+
+def _key(n, p, grid):
+    b = lambda v: round(2.0 * float(np.log2(max(v, 1)))) / 2.0      # half-octave buckets
+    g = ",".join(f"{k}={grid[k]}" for k in sorted(grid))
+    return f"{b(n)}x{b(p)}|{g}"
+
+
+def _children(p, K, seed, depth=8):
+    rng = np.random.default_rng(seed)
+    fix = np.full((K, p), -1, np.int8)
+    for k in range(K):
+        d = int(rng.integers(1, depth + 1))
+        idx = rng.choice(p, size=min(d, p), replace=False)
+        fix[k, idx] = (rng.random(len(idx)) < 0.3).astype(np.int8)
+    return fix
+
+
+def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0):
+    import torch
+    import paper_2602_04551_b300 as bnb
+    K = int(opts["batch_K"])
+    p = X.shape[1]
+    s = torch.cuda.Stream(device=device)
+    o = bnb.bnb_options_default(M=M, device=device, stream=s.cuda_stream, **opts)
+    with bnb.bnb_create(X, y, lam0, lam2, o) as h:
+        root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
+        fix = _children(p, K, seed)
+        wb = np.repeat(root["beta"], K, 0)
+        wb[fix == 0] = 0.0
+        dfix = torch.tensor(fix, device=f"cuda:{device}")
+        dwb = torch.tensor(wb, device=f"cuda:{device}")
+        dwv = torch.tensor(np.repeat(root["v"], K, 0), device=f"cuda:{device}")
+        dlb = torch.empty(K, dtype=torch.float64, device=f"cuda:{device}")
+        dit = torch.empty(K, dtype=torch.int32, device=f"cuda:{device}")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.synchronize()
+        e0.record(s)
+        bnb.bnb_relax_batch_device(h, K, dfix, dwb, dwv, 0, dlb, diters=dit)
+        e1.record(s)
+        s.synchronize()
+        ms = e0.elapsed_time(e1)
+        return {"nodes_per_s": K / (ms / 1e3), "ms": ms, "mean_iters": float(dit.float().mean()),
+                "lb_mean": float(dlb.mean())}
+
+
+def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol=1e-3):
+    grid = dict(DEFAULT_GRID, **(grid or {}))
+    n, p = X.shape
+    key = _key(n, p, grid)
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except Exception:
+            cache = {}
+        if key in cache:
+            return cache[key]["best"], cache[key]
+    names = list(grid)
+    results = []
+    t0 = time.time()
+    for combo in itertools.product(*[grid[k] for k in names]):
+        opts = dict(zip(names, combo))
+        r = trial(X, y, lam0, lam2, M, opts, device=device)
+        results.append((opts, r))
+    best_lb = max(r["lb_mean"] for _, r in results)
+    ok = [(o, r) for o, r in results if r["lb_mean"] >= best_lb - bound_tol * max(1.0, abs(best_lb))]
+    best, br = max(ok, key=lambda t: t[1]["nodes_per_s"])
+    entry = {"best": best, "score": br, "trials": [dict(o, **r) for o, r in results],
+             "seconds": time.time() - t0}
+    if use_cache:
+        cache[key] = entry
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        json.dump(cache, open(path, "w"), indent=1)
+    return best, entry

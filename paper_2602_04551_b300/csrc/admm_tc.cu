@@ -126,28 +126,40 @@ struct TcEpiAdmm {
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
     const float rho = (float)P.rho, irho = 1.0f / (float)P.rho;
+    // all loads of the chunk first (independent), then the arithmetic and the stores
+    bool ok[16];
+    float bo[16], vv[16];
+    int ff[16];
+    const float cj = m < M ? c[m] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = n0 + j;
+      ok[j] = (m < M) && (n < N) && active[n];
+      const long long o = (long long)n * p + m;
+      bo[j] = ok[j] ? beta[o] : 0.f;
+      vv[j] = ok[j] ? V[o] : 0.f;
+      ff[j] = ok[j] ? (int)fix[o] : 0;
+    }
     float s_psi[16], s_nu[16], s_db[16], s_pr[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       s_psi[j] = s_nu[j] = s_db[j] = s_pr[j] = 0.f;
-      const int n = n0 + j;
-      if (m < M && n < N && active[n]) {
+      if (ok[j]) {
+        const int n = n0 + j;
         const long long o = (long long)n * p + m;
-        const float bo = beta[o], v = V[o], cj = c[m], pp = acc[j];
-        const int f = fix[o];
-        const float w = cj + rho * bo - v;
-        const float b = (w - pp) * irho;
-        const float bt = b + v * irho;
-        const float bn = prox_coord<float>(bt, f, P);
-        const float vn = v + rho * (b - bn);
+        const float w = cj + rho * bo[j] - vv[j];
+        const float b = (w - acc[j]) * irho;
+        const float bt = b + vv[j] * irho;
+        const float bn = prox_coord<float>(bt, ff[j], P);
+        const float vn = vv[j] + rho * (b - bn);
         beta[o] = bn;
         V[o] = vn;
         const long long ow = (long long)n * ldp + m;
         split_store(cj + rho * bn - vn, whi, wlo, ow);
         if (bhi) split_store(bn, bhi, blo, ow);
-        s_psi[j] = psi_coord<float>(bn, f, P);
-        s_nu[j] = nu_coord<float>(fabsf(cj - pp), f, P);
-        s_db[j] = (bn - bo) * (bn - bo);
+        s_psi[j] = psi_coord<float>(bn, ff[j], P);
+        s_nu[j] = nu_coord<float>(fabsf(cj - acc[j]), ff[j], P);
+        s_db[j] = (bn - bo[j]) * (bn - bo[j]);
         s_pr[j] = (b - bn) * (b - bn);
       }
     }
@@ -164,7 +176,7 @@ struct TcEpiAdmm {
   }
 
   __device__ __forceinline__ void finish(int t, int m0, int n0, int M, int N, float* sm) const {
-    for (int col = t; col < BN; col += 128) {
+    for (int col = t; col < BN; col += 32 * tc::EPI_WARPS) {
       const int n = n0 + col;
       if (n >= N) continue;
 #pragma unroll

@@ -41,9 +41,17 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// When non-null, allocations are only counted (footprint query), not made.
+static thread_local size_t* g_count_only = nullptr;
+
 template <class R>
 static int dalloc(Engine<R>& e, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (g_count_only) {
+    *g_count_only += (bytes + 511) / 512 * 512;
+    *ptr = nullptr;
+    return 0;
+  }
   cudaError_t rc = cudaMalloc(ptr, bytes);
   if (rc != cudaSuccess) {
     cudaGetLastError();
@@ -114,13 +122,13 @@ static int allocate(Engine<R>& e) {
         ALLOC(e.u_lo, K * e.ldn);
       }
       ALLOC(e.tc_err, 1);
-      BNB_CUDA_OK(cudaMemsetAsync(e.tc_err, 0, sizeof(int), e.st));
+      if (!g_count_only) BNB_CUDA_OK(cudaMemsetAsync(e.tc_err, 0, sizeof(int), e.st));
       __nv_bfloat16* bufs[] = {e.xc_hi, e.xt_hi, e.gi_hi, e.w_hi, e.b_hi, e.t_hi, e.u_hi,
                                e.xc_lo, e.xt_lo, e.gi_lo, e.w_lo, e.b_lo, e.t_lo, e.u_lo};
       const long long cnt[] = {p * e.ldn, n * e.ldp, n * e.ldn, K * e.ldp, K * e.ldp, K * e.ldn,
                                K * e.ldn};
       for (int i = 0; i < 14; ++i)
-        if (bufs[i]) BNB_CUDA_OK(cudaMemsetAsync(bufs[i], 0, 2 * cnt[i % 7], e.st));
+        if (bufs[i] && !g_count_only) BNB_CUDA_OK(cudaMemsetAsync(bufs[i], 0, 2 * cnt[i % 7], e.st));
     }
   }
   ALLOC(e.X64, n * p);
@@ -200,6 +208,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.poolmin, 2);
   ALLOC(e.status_d, 1);
   ALLOC(e.params_d, 4);
+  if (g_count_only) return 0;
   if (cudaMallocHost((void**)&e.status_h, sizeof(Status)) != cudaSuccess)
     return fail(BNB_ENOMEM, "pinned status allocation failed");
   BNB_CUDA_OK(cudaMemsetAsync(e.beta, 0, sizeof(R) * K * p, e.st));
@@ -337,7 +346,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->max_admm_iter = 400;
   o->check_every = 10;
   o->batch_K = 512;
-  o->precision = BNB_PREC_FP32;
+  o->precision = BNB_PREC_TC3;
   o->use_graphs = 1;
   o->time_limit_s = 3600.0;
   o->max_nodes = 1000000000LL;
@@ -466,6 +475,42 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   h->stats.setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h;
+  return BNB_OK;
+}
+
+template <class R>
+static size_t footprint_of(int n, int p, const bnb_options& o) {
+  Engine<R> e;
+  e.n = n;
+  e.p = p;
+  e.K = o.batch_K;
+  e.smax = o.support_max;
+  e.qcap = o.queue_capacity;
+  long long wdef = (4LL << 30) / (2LL * p * (long long)sizeof(R));
+  if (wdef > e.qcap / 2) wdef = e.qcap / 2;
+  if (wdef < 64) wdef = 64;
+  e.wcap = o.warm_capacity > 0 ? o.warm_capacity : wdef;
+  if constexpr (sizeof(R) == 4) {
+    if (o.precision == BNB_PREC_BF16) e.tc_mode = 1;
+    if (o.precision == BNB_PREC_TC3) e.tc_mode = 3;
+  }
+  size_t bytes = 0;
+  g_count_only = &bytes;
+  allocate(e);
+  g_count_only = nullptr;
+  // per-handle staging, setup temporaries (G, Newton-Schulz iterates) and input copies
+  const size_t Kz = (size_t)o.batch_K;
+  bytes += Kz * (8 + 8 + 4) + Kz * n * 8 + Kz * p * (4 + 8);
+  bytes += (size_t)n * n * (8 + 3 * 4) + (sizeof(R) == 8 ? (size_t)n * n * 24 : 0);
+  bytes += (size_t)n * p * 8 + (size_t)n * 8;
+  return bytes;
+}
+
+extern "C" int bnb_footprint(int n, int p, const bnb_options* opt, size_t* bytes) {
+  if (!bytes || n <= 0 || p <= 0) return fail(BNB_EINVAL, "bad arguments");
+  bnb_options o;
+  if (opt) o = *opt; else bnb_options_default(&o);
+  *bytes = (o.precision == BNB_PREC_FP64) ? footprint_of<double>(n, p, o) : footprint_of<float>(n, p, o);
   return BNB_OK;
 }
 

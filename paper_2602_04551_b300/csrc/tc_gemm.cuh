@@ -10,8 +10,9 @@
 //                         128 x BN accumulator in tensor memory; tcgen05.commit frees a
 //                         stage ("empty" mbarrier) and finally signals "done";
 //                         the whole warp allocates / frees the TMEM columns;
-//   warps 2-5             epilogue: tcgen05.ld of the accumulator rows (each warp reads
-//                         its 32-lane quarter of TMEM), handed to the epilogue functor.
+//   warps 2-9             epilogue: tcgen05.ld of the accumulator rows (a warp reads its
+//                         32-lane quarter of TMEM, the two warps of a quarter take
+//                         alternate 16-column chunks), handed to the epilogue functor.
 // NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
 // accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
 // FP32-class arithmetic of the ADMM path.  NSPLIT = 1 is the plain BF16 product.
@@ -27,6 +28,8 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;             // 64 BF16 = 128 bytes: one swizzle row
+constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -152,7 +155,7 @@ struct Maps {
 //   epi.finish(t in [0, 128), m0, n0, M, N, smem)  after the four epilogue warps meet;
 //   Epi::SMEM_FLOATS  shared scratch the functor needs.
 template <int BN, int NSPLIT, class Epi>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant__ CUtensorMap ma_lo,
                const __grid_constant__ CUtensorMap mb_hi, const __grid_constant__ CUtensorMap mb_lo,
                int M, int N, int Kred, int kchunk, const int* __restrict__ active, int* err, Epi epi) {
@@ -239,21 +242,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
     }
     mma_commit(&done_bar);
   } else if (warp >= 2) {
-    // ---------------- epilogue: each warp owns TMEM lanes [32 q, 32 q + 32)
+    // ---------------- epilogue: warp w owns TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
     const int q = warp & 3;
+    const int g = (warp - 2) >> 2;      // which of the quarter's two warps
     const bool ok = mbar_wait(&done_bar, 0, err, 4);
     fence_after();
     const int row = m0 + 32 * q + lane;
     if (ok) {
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
+      for (int c = 16 * g; c < BN; c += 32) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
         epi(row, n0 + c, v, M, N, q, epi_smem);
       }
     }
-    // the four epilogue warps meet (named barrier 1) before the per-tile finish
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    // the epilogue warps meet (named barrier 1) before the per-tile finish
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
     if (ok) epi.finish(threadIdx.x - 64, m0, n0, M, N, epi_smem);
   }
   fence_before();

@@ -61,7 +61,7 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
     attr_set = true;
   }
   dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, ns);
-  kern<<<grid, 192, G::SMEM, st>>>(ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi);
+  kern<<<grid, tc::THREADS, G::SMEM, st>>>(ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }
