@@ -185,6 +185,7 @@ def run_mine(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(dev)
+    torch.cuda.nvtx.range_push("bench_timed")
     with torch.cuda.stream(s):
         for i in range(args.steps):
             flush.fill_(i & 0xff)
@@ -192,6 +193,7 @@ def run_mine(args, rank, world):
             bnb.bnb_solve_launch(h, 1)
             ev[i][1].record(s)
     s.synchronize()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = clk.stop()
     after = bnb.bnb_solve_poll(h)

@@ -1,0 +1,56 @@
+"""Profiling driver: a solve primed to steady state, then a few rounds, for ncu.
+
+    python -m paper_2602_04551_b300.profile_case --workload c4 --rounds 3
+
+Used for the ncu captures of the top kernels (small enough that the capture ends in
+a minute or two; the c4 shape keeps X and the node state larger than the L2 cache).
+"""
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+    import datagen
+    import paper_2602_04551_b300 as bnb
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--lam0-frac", type=float, default=0.02)
+    ap.add_argument("--K", type=int, default=512)
+    ap.add_argument("--rho", type=float, default=0.3)
+    ap.add_argument("--precision", type=int, default=3)
+    ap.add_argument("--rounds", type=int, default=3)
+    ap.add_argument("--prime-seconds", type=float, default=30.0)
+    a = ap.parse_args()
+    c = datagen.CONFIGS[a.workload]
+    inst = datagen.config_instance(a.workload, 0)
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, c["lam2"])
+    lam0 = a.lam0_frac * datagen.lambda0_scale(inst.X, inst.y, c["lam2"])
+    o = bnb.bnb_options_default(M=M, batch_K=a.K, rho=a.rho, precision=a.precision,
+                                queue_capacity=1 << 20, time_limit_s=1e9)
+    with bnb.bnb_create(inst.X, inst.y, lam0, c["lam2"], o) as h:
+        bnb.bnb_solve_start(h, 1e-4)
+        t0 = time.time()
+        while True:
+            bnb.bnb_solve_launch(h, 10)
+            pr = bnb.bnb_solve_poll(h)
+            if pr["done"] or pr["active_slots"] >= 0.9 * a.K or time.time() - t0 > a.prime_seconds:
+                break
+        torch.cuda.nvtx.range_push("profiled_rounds")
+        bnb.bnb_solve_launch(h, a.rounds)
+        pr = bnb.bnb_solve_poll(h)
+        torch.cuda.nvtx.range_pop()
+        print({k: pr[k] for k in ("nodes", "active_slots", "open_nodes", "ub", "lb")})
+        bnb.bnb_solve_finish(h)
+
+
+if __name__ == "__main__":
+    main()
