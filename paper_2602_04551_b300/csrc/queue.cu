@@ -222,34 +222,68 @@ __global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* se
       __syncthreads();
     }
   }
-  if (threadIdx.x != 0) return;
-  if (level == 1) {
-    const int F = base;
-    sel_state[SS_F] = F;
-    const int count = sel_state[SS_COUNT];
-    if (count <= F) {
-      sel_state[SS_TAKE_ALL] = 1;
-      return;
+  // level decisions (all threads take part in the bin scan below)
+  __shared__ int need_s, done_s;
+  if (threadIdx.x == 0) {
+    done_s = 0;
+    if (level == 1) {
+      const int F = base;
+      sel_state[SS_F] = F;
+      const int count = sel_state[SS_COUNT];
+      if (count <= F) {
+        sel_state[SS_TAKE_ALL] = 1;
+        done_s = 1;
+      } else {
+        sel_state[SS_NEED] = F;
+        sel_state[SS_LESS] = 0;
+      }
+    } else if (sel_state[SS_TAKE_ALL]) {
+      done_s = 1;
     }
-    sel_state[SS_NEED] = F;
-    sel_state[SS_LESS] = 0;
-  } else if (sel_state[SS_TAKE_ALL]) {
-    return;
+    need_s = sel_state[SS_NEED];
   }
+  __syncthreads();
+  if (done_s) return;
+  // block-wide inclusive scan of the histogram (bins split evenly over the threads),
+  // then the first bin whose cumulative count reaches `need`
   const int nbins = level == 3 ? 1024 : SEL_BINS;
   const unsigned* h = hist + (level - 1) * SEL_BINS;
-  const int need = sel_state[SS_NEED];
-  int cum = 0, b = 0;
-  for (b = 0; b < nbins; ++b) {
-    if (cum + (int)h[b] >= need) break;
-    cum += (int)h[b];
+  const int per = (nbins + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  int local = 0;
+  for (int b = b0; b < b0 + per && b < nbins; ++b) local += (int)h[b];
+  // exclusive prefix of `local` over the block
+  int x = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) >= o) x += y;
   }
-  if (b >= nbins) b = nbins - 1;  // cannot happen when the counts are consistent
-  sel_state[SS_NEED] = need - cum;
-  sel_state[SS_LESS] += cum;
-  if (level == 1) sel_state[SS_PREFIX] = b;
-  else if (level == 2) sel_state[SS_PREFIX] = (sel_state[SS_PREFIX] << 11) | b;
-  else sel_state[SS_TAU] = (int)(((unsigned)sel_state[SS_PREFIX] << 10) | (unsigned)b);
+  if ((threadIdx.x & 31) == 31) wcnt[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    int v = threadIdx.x < nw ? wcnt[threadIdx.x] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (threadIdx.x >= o) v += y;
+    }
+    if (threadIdx.x < nw) wcnt[threadIdx.x] = v;   // inclusive warp totals
+  }
+  __syncthreads();
+  const int excl = x - local + ((threadIdx.x >> 5) > 0 ? wcnt[(threadIdx.x >> 5) - 1] : 0);
+  const int need = need_s;
+  if (excl < need && excl + local >= need) {
+    int cum = excl, b = b0;
+    for (; b < b0 + per && b < nbins; ++b) {
+      if (cum + (int)h[b] >= need) break;
+      cum += (int)h[b];
+    }
+    sel_state[SS_NEED] = need - cum;
+    sel_state[SS_LESS] += cum;
+    if (level == 1) sel_state[SS_PREFIX] = b;
+    else if (level == 2) sel_state[SS_PREFIX] = (sel_state[SS_PREFIX] << 11) | b;
+    else sel_state[SS_TAU] = (int)(((unsigned)sel_state[SS_PREFIX] << 10) | (unsigned)b);
+  }
 }
 
 // levels 2 and 3: histogram of the next key bits among entries matching the prefix
@@ -434,9 +468,9 @@ int queue_select_refill(Engine<R>& e) {
                                  e.inc_ub, e.params_d, e.sel, e.sel_state, e.poolmin);
   k_sel_scan<<<1, 1024, 0, st>>>(1, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
   k_sel_pass<<<g, 256, 0, st>>>(2, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
-  k_sel_scan<<<1, 32, 0, st>>>(2, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_scan<<<1, 1024, 0, st>>>(2, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
   k_sel_pass<<<g, 256, 0, st>>>(3, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
-  k_sel_scan<<<1, 32, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_scan<<<1, 1024, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
   k_sel_collect<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_key, e.free_stack, e.free_top,
                                    e.sel_state, e.popped);
   k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.sel_state, e.popped, e.free_slots, e.pool_lb,
