@@ -71,6 +71,9 @@ typedef struct {
   int ub_max_iter;       /* projected-gradient iterations per candidate, default 200 */
   int device;            /* CUDA device ordinal, default 0 */
   void* stream;          /* cudaStream_t to run on; NULL = a stream owned by the handle */
+  double relax_alpha;    /* ADMM over-relaxation in [1, 1.9]; 1 = the plain update order of
+                            Eq. admm-update (default); alpha > 1 uses alpha b + (1 - alpha)
+                            beta in the beta- and v-updates.  Bounds are valid for any alpha. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */

@@ -42,7 +42,7 @@ class bnb_options(ctypes.Structure):
                 ("max_nodes", ctypes.c_longlong), ("queue_capacity", ctypes.c_longlong),
                 ("warm_capacity", ctypes.c_longlong), ("support_max", ctypes.c_int),
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double)]
 
 
 class bnb_stats(ctypes.Structure):

@@ -20,6 +20,7 @@ import numpy as np
 
 DEFAULT_GRID = {
     "rho": [0.1, 0.2, 0.3, 0.5, 1.0],
+    "relax_alpha": [1.0, 1.6],
     "batch_K": [256, 512, 1024],
     "check_every": [10],
     "precision": [3],

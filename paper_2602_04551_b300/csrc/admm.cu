@@ -64,10 +64,11 @@ struct EpiAdmm {
             const int f = fix[o];
             const R w = cj + rho * bo - v;
             const R b = (w - pp) * irho;
-            const R bt = b + v * irho;
+            const R bh = (R)P.alpha * b + (R(1) - (R)P.alpha) * bo;   // over-relaxed b
+            const R bt = bh + v * irho;
             const R bn = prox_coord<R>(bt, f, P);
             beta[o] = bn;
-            V[o] = v + rho * (b - bn);
+            V[o] = v + rho * (bh - bn);
             s_psi += psi_coord<R>(bn, f, P);
             s_nu += nu_coord<R>(fabs(cj - pp), f, P);
             s_db += (bn - bo) * (bn - bo);

@@ -149,9 +149,10 @@ struct TcEpiAdmm {
         const long long o = (long long)n * p + m;
         const float w = cj + rho * bo[j] - vv[j];
         const float b = (w - acc[j]) * irho;
-        const float bt = b + vv[j] * irho;
+        const float bh = (float)P.alpha * b + (1.0f - (float)P.alpha) * bo[j];   // over-relaxed
+        const float bt = bh + vv[j] * irho;
         const float bn = prox_coord<float>(bt, ff[j], P);
-        const float vn = vv[j] + rho * (b - bn);
+        const float vn = vv[j] + rho * (bh - bn);
         beta[o] = bn;
         V[o] = vn;
         const long long ow = (long long)n * ldp + m;

@@ -356,6 +356,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->ub_max_iter = 200;
   o->device = 0;
   o->stream = nullptr;
+  o->relax_alpha = 1.0;
   return BNB_OK;
 }
 
@@ -390,6 +391,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   P.c_soft = 2.0 * std::sqrt(h->lam0 * h->lam2);
   P.x0 = P.linear ? P.c_lin : P.c_soft;
   P.sqrt_l2_l0 = h->lam0 > 0 ? std::sqrt(h->lam2 / h->lam0) : INFINITY;
+  P.alpha = o.relax_alpha;
   if (o.stream) {
     e->st = (cudaStream_t)o.stream;
   } else {
@@ -438,6 +440,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.batch_K < 1 || o.batch_K > 65536) return fail(BNB_EINVAL, "batch_K out of range");
   if (o.support_max < 1 || o.support_max > 256) return fail(BNB_EINVAL, "support_max must be in [1, 256]");
   if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
+  if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_TC3)

@@ -32,6 +32,7 @@ struct Prob {
   double c_soft;     // 2 sqrt(l0 l2)                 (slope of psi near 0)
   double x0;         // nu_i(x) = 0 for free i iff x <= x0
   double sqrt_l2_l0; // sqrt(l2/l0) (z recovery), +inf when l0 = 0
+  double alpha;      // ADMM over-relaxation (1 = plain)
 };
 
 template <class T>

@@ -207,3 +207,26 @@ def test_solve_batch_width_does_not_change_the_answer(K):
         res = bnb.bnb_solve(h, 1e-9)
     assert tuple(np.nonzero(res["beta"])[0]) == br.support
     assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_over_relaxed_admm_keeps_bounds_valid_and_answers_exact(prec):
+    """relax_alpha > 1 changes the iterates, not the certificate: bounds stay below
+    the relaxation optimum and the solve returns the brute-force optimum."""
+    inst, lam0, lam2, M = _inst("c1", 0, frac=0.05)
+    rng = np.random.default_rng(9)
+    fix = datagen.random_fixings(inst.p, 8, rng, 6)
+    with _handle(inst, lam0, lam2, M, prec, K=16, node_tol=1e-5, max_admm_iter=20000,
+                 relax_alpha=1.6) as h:
+        out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+    for k in range(8):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+        assert out["lb"][k] >= opt - 2e-4 * max(1.0, abs(opt))
+    inst, lam0, lam2, M = _inst("c1_p16", 0, frac=0.02)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, prec, K=8, node_tol=1e-7, max_admm_iter=5000,
+                 relax_alpha=1.6) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
