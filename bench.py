@@ -51,7 +51,7 @@ SM_COUNT, FP32_LANES = 148, 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="c2")
@@ -96,7 +96,7 @@ class Clocks:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -175,6 +175,8 @@ def run_mine(args, rank, world):
         pr = bnb.bnb_solve_poll(h)
         if pr["done"] or pr["active_slots"] >= 0.9 * args.K or time.time() - t0 > args.prime_seconds:
             break
+    clk = Clocks(dev)            # sampling spans the warm-up and the timed steps
+    time.sleep(0.3)
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
             bnb.bnb_solve_launch(h, 1)
@@ -184,7 +186,6 @@ def run_mine(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = Clocks(dev)
     torch.cuda.nvtx.range_push("bench_timed")
     with torch.cuda.stream(s):
         for i in range(args.steps):

@@ -2,16 +2,17 @@
 //
 // Per iteration, for all K slots at once (Eqs. batched_b_update,
 // batched_beta_update, beta_update_vector, batched_v_update):
-//   W  = c 1^T + rho beta - V                  (formed while loading, never stored)
-//   T  = X W^T                  n x K           contraction over p
-//   U  = G^{-1} T               n x K           (U = X b exactly: X (X^T X + rho I)^{-1}
+//   W' = rho beta - V                          (formed while loading, never stored)
+//   T  = X W'^T                 n x K           contraction over p
+//   U' = G^{-1} T               n x K           U = u_c + U' = X b exactly (X (X^T X + rho I)^{-1}
 //                                                = (X X^T + rho I)^{-1} X)
-//   P  = X^T U                  p x K           contraction over n, fused epilogue:
-//        b    = (W - P) / rho                  (b = D W, Woodbury with 1/rho)
+//   P  = X^T U'                 p x K           contraction over n, fused epilogue:
+//        b    = b_c + (W' - P) / rho           (b = D (c + W'), Woodbury with 1/rho;
+//                                               b_c = D c formed once in FP64)
 //        bt   = b + V / rho
 //        beta = prox(bt)                       (Eq. minbetalower, masks of the fixings)
 //        V    = V + rho (b - beta)             (Eq. v_i-update)
-//        and per slot: sum psi(beta), sum nu(|c - P|) (= nu(|X^T r|), r = y - U),
+//        and per slot: sum psi(beta), sum nu(|rho b_c - P|) (= nu(|X^T r|), r = y - U),
 //        ||beta_new - beta_old||^2, ||b - beta_new||^2.
 // Every check_every iterations a check product X beta^T gives the primal
 // value of Eq. relaxnode2, and the node stop rule (relative primal-dual gap,
@@ -23,21 +24,21 @@
 namespace bnb {
 
 template <class R>
-struct BW {  // B(k = feature j, n = slot) = c_j + rho beta_sj - V_sj
-  const R* __restrict__ c;
+struct BW {  // B(k = feature j, n = slot) = W'_sj = rho beta_sj - V_sj
   const R* __restrict__ beta;
   const R* __restrict__ V;
   R rho;
   long long p;
   __device__ __forceinline__ R operator()(int k, int n) const {
     long long o = (long long)n * p + k;
-    return c[k] + rho * beta[o] - V[o];
+    return rho * beta[o] - V[o];
   }
 };
 
 template <class R>
 struct EpiAdmm {
-  const R* __restrict__ c;
+  const R* __restrict__ bc;     // b_c = D c
+  const R* __restrict__ rbc;    // rho b_c = c - X^T u_c
   R* __restrict__ beta;
   R* __restrict__ V;
   const int8_t* __restrict__ fix;
@@ -60,17 +61,17 @@ struct EpiAdmm {
           const int m = m0 + tm + i * TX;
           if (m < M) {
             const long long o = (long long)n * p + m;
-            const R bo = beta[o], v = V[o], cj = c[m], pp = acc[i][j];
+            const R bo = beta[o], v = V[o], pp = acc[i][j];
             const int f = fix[o];
-            const R w = cj + rho * bo - v;
-            const R b = (w - pp) * irho;
+            const R w = rho * bo - v;                      // W'
+            const R b = bc[m] + (w - pp) * irho;           // b = b_c + D W'
             const R bh = (R)P.alpha * b + (R(1) - (R)P.alpha) * bo;   // over-relaxed b
             const R bt = bh + v * irho;
             const R bn = prox_coord<R>(bt, f, P);
             beta[o] = bn;
             V[o] = v + rho * (bh - bn);
             s_psi += psi_coord<R>(bn, f, P);
-            s_nu += nu_coord<R>(fabs(cj - pp), f, P);
+            s_nu += nu_coord<R>(fabs(rbc[m] - pp), f, P);   // X^T r = rho b_c - P'
             s_db += (bn - bo) * (bn - bo);
             s_pr += (b - bn) * (b - bn);
           }
@@ -109,9 +110,10 @@ __global__ void k_reduce_splits(const R* __restrict__ part, int S, R* __restrict
   }
 }
 
-// U = sum of split partials; per slot ||y - U||^2 and y^T (y - U)
+// U' = sum of split partials, U = u_c + U'; per slot ||y - U||^2 and y^T (y - U)
 template <class R>
 __global__ void k_finalize_u(const R* __restrict__ Upart, int S, R* __restrict__ U,
+                             R* __restrict__ Up, const R* __restrict__ uc,
                              const R* __restrict__ y, int n, int K, const int* __restrict__ active,
                              R* __restrict__ rstat) {
   __shared__ R sh[32];
@@ -120,8 +122,10 @@ __global__ void k_finalize_u(const R* __restrict__ Upart, int S, R* __restrict__
   const long long zs = (long long)n * K, base = (long long)s * n;
   R rr = 0, yr = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    R u = Upart[base + i];
-    for (int z = 1; z < S; ++z) u += Upart[z * zs + base + i];
+    R up = Upart[base + i];
+    for (int z = 1; z < S; ++z) up += Upart[z * zs + base + i];
+    Up[base + i] = up;
+    const R u = uc[i] + up;
     U[base + i] = u;
     R r = y[i] - u;
     rr += r * r;
@@ -250,7 +254,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
       // T = X W^T
       prof_begin(e.prof, st);
       BNB_CUDA_OK((gemm_simt<R, false, false>(st, e.XR, n, n, K, p, e.s1, e.slot_active,
-                                              BW<R>{e.cR, e.beta, e.V, (R)e.P.rho, p},
+                                              BW<R>{e.beta, e.V, (R)e.P.rho, p},
                                               EpiStore<R>{e.Tpart, n, nK})));
       prof_end(e.prof, st, PK_GEMM_XW);
       prof_begin(e.prof, st);
@@ -262,13 +266,15 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
                                               BPlainK<R>{e.T, n}, EpiStore<R>{e.Upart, n, nK})));
       prof_end(e.prof, st, PK_GEMM_GT);
       prof_begin(e.prof, st);
-      k_finalize_u<R><<<K, 256, 0, st>>>(e.Upart, e.s2, e.U, e.yR, n, K, e.slot_active, e.rstat);
+      k_finalize_u<R><<<K, 256, 0, st>>>(e.Upart, e.s2, e.U, e.Up, e.ucR, e.yR, n, K,
+                                         e.slot_active, e.rstat);
       prof_end(e.prof, st, PK_FINAL_U);
       // P = X^T U, fused b / prox / v epilogue
       prof_begin(e.prof, st);
       BNB_CUDA_OK((gemm_simt<R, true, false>(
-          st, e.XR, n, p, K, n, 1, e.slot_active, BPlainK<R>{e.U, n},
-          EpiAdmm<R>{e.cR, e.beta, e.V, e.fix, e.slot_active, e.g3part, e.P, p, e.nbm3, K})));
+          st, e.XR, n, p, K, n, 1, e.slot_active, BPlainK<R>{e.Up, n},
+          EpiAdmm<R>{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, e.g3part, e.P, p, e.nbm3,
+                     K})));
       prof_end(e.prof, st, PK_GEMM_XTU);
     }
     // check: X beta^T for the primal value of Eq. relaxnode2

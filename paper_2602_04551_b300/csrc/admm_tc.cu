@@ -1,13 +1,13 @@
 // admm_tc.cu -- the batched ADMM iteration on tcgen05 tensor cores.
 //
-// Same iteration as admm.cu (Sections 3.1-3.2; Woodbury b-update), with the
-// three contractions on the Blackwell tensor cores:
-//   T = X W^T        tcgen05, A = X row-major (n x p, K-major), B = W (K x p), split-K
-//   U = G^{-1} T     tcgen05, A = G^{-1} (symmetric), B = T (K x n), split-K
-//   P = X^T U        tcgen05, A = X column-major (p x n, K-major), B = U (K x n),
+// Same iteration as admm.cu (Sections 3.1-3.2; Woodbury b-update on the shifted
+// operand W' = rho beta - V), with the three contractions on the tensor cores:
+//   T  = X W'^T      tcgen05, A = X row-major (n x p, K-major), B = W' (K x p), split-K
+//   U' = G^{-1} T    tcgen05, A = G^{-1} (symmetric), B = T (K x n), split-K
+//   P  = X^T U'      tcgen05, A = X column-major (p x n, K-major), B = U' (K x n),
 //                    fused epilogue straight from tensor memory:
-//                    b = (W - P)/rho, beta = prox(b + V/rho), V += rho (b - beta),
-//                    per-slot stop-test sums, and the next iteration's W operand.
+//                    b = b_c + (W' - P)/rho, beta = prox(b + V/rho), V += rho (b - beta),
+//                    per-slot stop-test sums, and the next iteration's W' operand.
 // Operands are BF16; in the FP32-class mode each operand is a hi/lo pair and the
 // product takes three MMAs (hi hi + hi lo + lo hi), in the BF16 mode one.
 // Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.
@@ -25,8 +25,8 @@ __device__ __forceinline__ void split_store(float x, __nv_bfloat16* hi, __nv_bfl
   if (lo) lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// W = c + rho beta - V for the active slots, as BF16 hi/lo (K x ldp)
-__global__ void k_make_w(const float* __restrict__ c, const float* __restrict__ beta,
+// W' = rho beta - V for the active slots, as BF16 hi/lo (K x ldp)
+__global__ void k_make_w(const float* __restrict__ beta,
                          const float* __restrict__ V, const int* __restrict__ active, int p,
                          long long ldp, int K, float rho, __nv_bfloat16* __restrict__ whi,
                          __nv_bfloat16* __restrict__ wlo) {
@@ -35,7 +35,7 @@ __global__ void k_make_w(const float* __restrict__ c, const float* __restrict__ 
        t += (long long)gridDim.x * blockDim.x) {
     const int s = (int)(t / p), j = (int)(t % p);
     if (!active[s]) continue;
-    split_store(c[j] + rho * beta[t] - V[t], whi, wlo, (long long)s * ldp + j);
+    split_store(rho * beta[t] - V[t], whi, wlo, (long long)s * ldp + j);
   }
 }
 
@@ -54,9 +54,11 @@ __global__ void k_reduce_t_tc(const float* __restrict__ part, int S, int n, int 
   }
 }
 
-// U = sum of split partials (FP32, n x K) + BF16 hi/lo copy; ||y - U||^2, y^T (y - U)
+// U' = sum of split partials, U = u_c + U' (FP32, n x K), BF16 hi/lo copy of U' (the
+// X^T U' operand); ||y - U||^2, y^T (y - U)
 __global__ void k_finalize_u_tc(const float* __restrict__ Upart, int S, float* __restrict__ U,
-                                const float* __restrict__ y, int n, int K,
+                                const float* __restrict__ uc, const float* __restrict__ y, int n,
+                                int K,
                                 const int* __restrict__ active, float* __restrict__ rstat,
                                 long long ldn, __nv_bfloat16* __restrict__ uhi,
                                 __nv_bfloat16* __restrict__ ulo) {
@@ -66,10 +68,11 @@ __global__ void k_finalize_u_tc(const float* __restrict__ Upart, int S, float* _
   const long long zs = (long long)n * K, base = (long long)s * n;
   float rr = 0.f, yr = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float u = Upart[base + i];
-    for (int z = 1; z < S; ++z) u += Upart[z * zs + base + i];
+    float up = Upart[base + i];
+    for (int z = 1; z < S; ++z) up += Upart[z * zs + base + i];
+    const float u = uc[i] + up;
     U[base + i] = u;
-    split_store(u, uhi, ulo, (long long)s * ldn + i);
+    split_store(up, uhi, ulo, (long long)s * ldn + i);
     const float r = y[i] - u;
     rr += r * r;
     yr += y[i] * r;
@@ -111,7 +114,8 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16]) {
 template <int BN>
 struct TcEpiAdmm {
   static constexpr int SMEM_FLOATS = 4 * 4 * BN;   // [warp][stat][column]
-  const float* __restrict__ c;
+  const float* __restrict__ bc;     // b_c = D c
+  const float* __restrict__ rbc;    // rho b_c
   float* __restrict__ beta;
   float* __restrict__ V;
   const int8_t* __restrict__ fix;
@@ -130,7 +134,7 @@ struct TcEpiAdmm {
     bool ok[16];
     float bo[16], vv[16];
     int ff[16];
-    const float cj = m < M ? c[m] : 0.f;
+    const float bcm = m < M ? bc[m] : 0.f, rbcm = m < M ? rbc[m] : 0.f;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int n = n0 + j;
@@ -147,8 +151,8 @@ struct TcEpiAdmm {
       if (ok[j]) {
         const int n = n0 + j;
         const long long o = (long long)n * p + m;
-        const float w = cj + rho * bo[j] - vv[j];
-        const float b = (w - acc[j]) * irho;
+        const float w = rho * bo[j] - vv[j];               // W'
+        const float b = bcm + (w - acc[j]) * irho;         // b = b_c + D W'
         const float bh = (float)P.alpha * b + (1.0f - (float)P.alpha) * bo[j];   // over-relaxed
         const float bt = bh + vv[j] * irho;
         const float bn = prox_coord<float>(bt, ff[j], P);
@@ -156,10 +160,10 @@ struct TcEpiAdmm {
         beta[o] = bn;
         V[o] = vn;
         const long long ow = (long long)n * ldp + m;
-        split_store(cj + rho * bn - vn, whi, wlo, ow);
+        split_store(rho * bn - vn, whi, wlo, ow);          // next W'
         if (bhi) split_store(bn, bhi, blo, ow);
         s_psi[j] = psi_coord<float>(bn, ff[j], P);
-        s_nu[j] = nu_coord<float>(fabsf(cj - acc[j]), ff[j], P);
+        s_nu[j] = nu_coord<float>(fabsf(rbcm - acc[j]), ff[j], P);   // X^T r = rho b_c - P'
         s_db[j] = (bn - bo[j]) * (bn - bo[j]);
         s_pr[j] = (b - bn) * (b - bn);
       }
@@ -206,7 +210,7 @@ static int round_tc(Engine<float>& e, int iters) {
   const int red_grid = (int)((nK + 255) / 256 > 4096 ? 4096 : (nK + 255) / 256);
   const int kgrid = (int)(((long long)K * p + 255) / 256 > 8192 ? 8192 : ((long long)K * p + 255) / 256);
   prof_begin(e.prof, st);
-  k_make_w<<<kgrid, 256, 0, st>>>(e.cR, e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
+  k_make_w<<<kgrid, 256, 0, st>>>(e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
                                   e.w_hi, NS == 3 ? e.w_lo : nullptr);
   prof_end(e.prof, st, PK_REDUCE_T);
   BNB_CUDA_OK(cudaGetLastError());
@@ -227,12 +231,13 @@ static int round_tc(Engine<float>& e, int iters) {
       return rc;
     prof_end(e.prof, st, PK_GEMM_GT);
     prof_begin(e.prof, st);
-    k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.yR, n, K,
+    k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.ucR,
+                                       (float*)e.yR, n, K,
                                        e.slot_active, (float*)e.rstat, e.ldn, e.u_hi,
                                        NS == 3 ? e.u_lo : nullptr);
     prof_end(e.prof, st, PK_FINAL_U);
     prof_begin(e.prof, st);
-    TcEpiAdmm<BN> epi{e.cR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
+    TcEpiAdmm<BN> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                       e.w_hi, NS == 3 ? e.w_lo : nullptr,
                       last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
                       e.P, p, e.ldp, e.nbm3, K};

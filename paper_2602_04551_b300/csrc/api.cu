@@ -139,6 +139,10 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.xnorm, p);
   ALLOC(e.yR, n);
   ALLOC(e.cR, p);
+  ALLOC(e.bcR, p);
+  ALLOC(e.rbcR, p);
+  ALLOC(e.ucR, n);
+  ALLOC(e.Up, n * K);
   ALLOC(e.Ginv, n * n);
   ALLOC(e.beta, K * p);
   ALLOC(e.V, K * p);

@@ -74,6 +74,10 @@ struct Engine {
   double *X64 = nullptr, *y64 = nullptr, *c64 = nullptr, *xnorm = nullptr;
   float* X32 = nullptr;         // FP32 copy (certificate screen)
   R *XR = nullptr, *yR = nullptr, *cR = nullptr, *Ginv = nullptr;
+  // shift of the b-update (formed once in FP64): b_c = D c, u_c = G^-1 X c = X b_c.
+  // The iteration runs on W' = rho beta - V, so b = b_c + D W' and U = u_c + G^-1 X W'.
+  R *bcR = nullptr, *rbcR = nullptr, *ucR = nullptr;   // b_c, rho b_c (p), u_c (n)
+  R* Up = nullptr;              // U' = G^-1 X W'^T (n x K), the X^T U' operand
   double yy = 0.0;              // y^T y
 
   // ADMM state, node-major K x p

@@ -5,6 +5,10 @@
 //   X in FP32, and the inverse of G = X X^T + rho I_n used by the b-update
 //   b = D w with D = (1/rho)(I - X^T G^{-1} X)  (Eq. b_update; Woodbury form of
 //   Section 3.1.2 with the 1/rho coefficient that makes D (X^T X + rho I) = I).
+// The b-update is shifted by its constant part: b_c = D c and u_c = G^{-1} X c
+// (= X b_c) are formed once in FP64, so the iteration works on W' = rho beta - V,
+// whose entries are far smaller than those of c, and low-precision products lose
+// correspondingly less (b = b_c + D W', U = u_c + G^{-1} X W').
 // G is built in FP64 on CUDA cores; G^{-1} by the Newton-Schulz iteration
 // Z <- Z (2I - G Z) (Schulz 1933), started at Z = I / g with g >= lambda_max(G)
 // from Gershgorin's bound, so that ||I - G Z_0|| = 1 - rho/g < 1 and the error
@@ -119,6 +123,62 @@ struct EpiSchulz {
   }
 };
 
+// t_i = sum_j X_ij v_j  (thread per row; FP64)
+__global__ void k_x_times(const double* __restrict__ X, const double* __restrict__ v, int n, int p,
+                          double* __restrict__ t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int j = 0; j < p; ++j) a = fma(X[(long long)j * n + i], v[j], a);
+  t[i] = a;
+}
+
+// g_j = X_j^T u  (warp per column; FP64); optional out2_j = (c_j - g_j) / rho
+__global__ void k_xt_times(const double* __restrict__ X, const double* __restrict__ u, int n, int p,
+                           double* __restrict__ g, const double* __restrict__ c, double rho,
+                           double* __restrict__ out2) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= p) return;
+  const double* col = X + (long long)warp * n;
+  double a = 0.0;
+  for (int i = lane; i < n; i += 32) a = fma(col[i], u[i], a);
+  a = warp_sum(a);
+  if (lane == 0) {
+    g[warp] = a;
+    if (out2) out2[warp] = (c[warp] - a) / rho;
+  }
+}
+
+// u += Z r  (Z symmetric n x n in precision R; FP64 accumulation); thread per row
+template <class R>
+__global__ void k_ginv_apply(const R* __restrict__ Z, const double* __restrict__ r, int n,
+                             double* __restrict__ u, int accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int j = 0; j < n; ++j) a = fma((double)Z[(long long)j * n + i], r[j], a);
+  u[i] = accumulate ? u[i] + a : a;
+}
+
+// res = t - (h + rho u)
+__global__ void k_residual(const double* __restrict__ t, const double* __restrict__ h,
+                           const double* __restrict__ u, double rho, int n, double* __restrict__ res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) res[i] = t[i] - (h[i] + rho * u[i]);
+}
+
+template <class R>
+__global__ void k_store_shift(const double* __restrict__ bc, const double* __restrict__ uc, int n,
+                              int p, double rho, R* __restrict__ bcR, R* __restrict__ rbcR,
+                              R* __restrict__ ucR) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < p) {
+    bcR[t] = (R)bc[t];
+    rbcR[t] = (R)(rho * bc[t]);
+  }
+  if (t < n) ucR[t] = (R)uc[t];
+}
+
 static inline int grid_for(long long m, int bs = 256) {
   long long g = (m + bs - 1) / bs;
   return (int)(g > 148 * 32 ? 148 * 32 : (g < 1 ? 1 : g));
@@ -207,6 +267,37 @@ int setup_data(Engine<R>& e, const double* dX, const double* dy) {
     k_symmetrize<double><<<grid_for(nn), 256, 0, st>>>(Z64, (double*)e.Ginv, n);
   }
   BNB_CUDA_OK(cudaGetLastError());
+  // shift of the b-update in FP64: u_c = G^-1 (X c) by the stored inverse plus three
+  // steps of iterative refinement against G applied exactly (X (X^T u) + rho u),
+  // then b_c = (c - X^T u_c) / rho  (= D c)
+  {
+    double *t = nullptr, *u = nullptr, *g = nullptr, *hh = nullptr, *res = nullptr, *bc = nullptr;
+    BNB_CUDA_OK(cudaMallocAsync(&t, sizeof(double) * n, st));
+    BNB_CUDA_OK(cudaMallocAsync(&u, sizeof(double) * n, st));
+    BNB_CUDA_OK(cudaMallocAsync(&hh, sizeof(double) * n, st));
+    BNB_CUDA_OK(cudaMallocAsync(&res, sizeof(double) * n, st));
+    BNB_CUDA_OK(cudaMallocAsync(&g, sizeof(double) * p, st));
+    BNB_CUDA_OK(cudaMallocAsync(&bc, sizeof(double) * p, st));
+    const int gn = (n + 255) / 256, gp = (p * 32 + 255) / 256;
+    k_x_times<<<gn, 256, 0, st>>>(e.X64, e.c64, n, p, t);
+    k_ginv_apply<R><<<gn, 256, 0, st>>>(e.Ginv, t, n, u, 0);
+    for (int it = 0; it < 3; ++it) {
+      k_xt_times<<<gp, 256, 0, st>>>(e.X64, u, n, p, g, nullptr, 1.0, nullptr);
+      k_x_times<<<gn, 256, 0, st>>>(e.X64, g, n, p, hh);
+      k_residual<<<gn, 256, 0, st>>>(t, hh, u, e.P.rho, n, res);
+      k_ginv_apply<R><<<gn, 256, 0, st>>>(e.Ginv, res, n, u, 1);
+    }
+    k_xt_times<<<gp, 256, 0, st>>>(e.X64, u, n, p, g, e.c64, e.P.rho, bc);
+    const int gm = ((n > p ? n : p) + 255) / 256;
+    k_store_shift<R><<<gm, 256, 0, st>>>(bc, u, n, p, e.P.rho, e.bcR, e.rbcR, e.ucR);
+    BNB_CUDA_OK(cudaGetLastError());
+    BNB_CUDA_OK(cudaFreeAsync(t, st));
+    BNB_CUDA_OK(cudaFreeAsync(u, st));
+    BNB_CUDA_OK(cudaFreeAsync(hh, st));
+    BNB_CUDA_OK(cudaFreeAsync(res, st));
+    BNB_CUDA_OK(cudaFreeAsync(g, st));
+    BNB_CUDA_OK(cudaFreeAsync(bc, st));
+  }
   BNB_CUDA_OK(cudaFreeAsync(G, st));
   BNB_CUDA_OK(cudaFreeAsync(gk, st));
   BNB_CUDA_OK(cudaFreeAsync(G32, st));
