@@ -23,10 +23,11 @@ numpy, in the order the paper states them, with no blocking or fusion:
   brute   enumeration of every support (p <= 16): the definition of the
           optimum of Eq. perspective.
   bnb     best-first branch-and-bound (Section 2.2.1, Algorithm 1).
+  mp      the matching-pursuit root heuristic (Appendix A.2).
 
 Pins (tests marked "not gpu"): brute force, closed forms against 1-D numeric
 optimisation, weak and strong duality, agreement of two independent
 relaxation solvers, the orthonormal-design special case, library
 box-constrained least squares.
 """
-from . import relax, admm, pgd, ub, brute, bnb  # noqa: F401
+from . import relax, admm, pgd, ub, brute, bnb, mp  # noqa: F401

@@ -180,8 +180,9 @@ struct TcEpiAdmm {
     }
   }
 
-  __device__ __forceinline__ void finish(int t, int m0, int n0, int M, int N, float* sm) const {
-    for (int col = t; col < BN; col += 32 * tc::EPI_WARPS) {
+  __device__ __forceinline__ void finish(int t, int nthr, int m0, int n0, int M, int N,
+                                         float* sm) const {
+    for (int col = t; col < BN; col += nthr) {
       const int n = n0 + col;
       if (n >= N) continue;
 #pragma unroll
@@ -196,7 +197,9 @@ struct TcEpiAdmm {
 
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
-  constexpr int BN = 256;
+  constexpr int BN = 256;   // X W'^T, G^-1 T and X beta^T: wide tiles, split-K
+  constexpr int BN3 = 64;   // X^T U' + fused update: narrow tiles, two CTAs per SM so that
+                            // one CTA's epilogue overlaps the other's tensor-core work
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   const long long nK = (long long)n * K;
@@ -237,11 +240,13 @@ static int round_tc(Engine<float>& e, int iters) {
                                        NS == 3 ? e.u_lo : nullptr);
     prof_end(e.prof, st, PK_FINAL_U);
     prof_begin(e.prof, st);
-    TcEpiAdmm<BN> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
+    TcEpiAdmm<BN3> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                       e.w_hi, NS == 3 ? e.w_lo : nullptr,
                       last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
                       e.P, p, e.ldp, e.nbm3, K};
-    if (int rc = tc_gemm<BN, NS>(st, XC, Uop, p, K, n, 1, e.slot_active, e.tc_err, epi)) return rc;
+    if (int rc = tc_gemm<BN3, NS, TcEpiAdmm<BN3>, 4>(st, XC, Uop, p, K, n, 1, e.slot_active,
+                                                     e.tc_err, epi))
+      return rc;
     prof_end(e.prof, st, PK_GEMM_XTU);
   }
   // check product X beta^T

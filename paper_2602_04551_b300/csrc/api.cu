@@ -171,6 +171,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.rS, K * n);
   ALLOC(e.gscr, K * p);
   ALLOC(e.cflag, K * p);
+  ALLOC(e.cpart, 2 * ((p + 63) / 64) * K);
   ALLOC(e.cert_rr, K);
   ALLOC(e.cert_yr, K);
   ALLOC(e.cert_rn, K);
@@ -595,7 +596,7 @@ static int relax_impl(bnb_handle* h, Engine<R>& e, int K, const int8_t* dfix, co
   const int max_rounds = (max_iter + o.check_every - 1) / o.check_every + 1;
   while (true) {
     if (int rc = admm_round(e, o.check_every, max_iter, o.node_tol, false)) return rc;
-    if (int rc = certify(e, nullptr)) return rc;
+    if (int rc = certify(e, nullptr, false)) return rc;
     if (int rc = branch_support(e, true)) return rc;
     k_scatter_relax<<<(e.K + 255) / 256, 256, 0, st>>>(e.ret_slot, e.ret_count, e.cert_lb,
                                                        e.br_idx, h->d_lb, h->d_br);
@@ -698,7 +699,7 @@ extern "C" int bnb_dual_bound(bnb_handle* h, int K, const int8_t* fix, const dou
     k_init_slots<<<g1d(e.K), 256, 0, e.st>>>(e.K, K, e.slot_active, e.slot_iters, e.slot_lbp,
                                              e.slot_depth, e.ret_slot, e.ret_active, e.ret_count, 1);
     BNB_CUDA_OK(cudaGetLastError());
-    if (int rc = certify(e, h->d_rgiven)) return rc;
+    if (int rc = certify(e, h->d_rgiven, false)) return rc;
     BNB_CUDA_OK(cudaMemcpyAsync(lb, e.cert_lb, sizeof(double) * K, cudaMemcpyDeviceToHost, e.st));
     BNB_CUDA_OK(cudaStreamSynchronize(e.st));
     return 0;
@@ -745,7 +746,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   prof_end(pf, e.st, PK_SELECT);
   if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
   prof_begin(pf, e.st);
-  if (int rc = certify(e, nullptr)) return rc;
+  if (int rc = certify(e, nullptr, true)) return rc;
   prof_end(pf, e.st, PK_CERT);
   prof_begin(pf, e.st);
   if (int rc = branch_support(e, false)) return rc;

@@ -14,9 +14,14 @@
 // Numerical Algorithms", Sec. 3.1, plus the rounding of X and r to FP32, and
 // Cauchy-Schwarz).  For a free coordinate nu_i(x) = 0 exactly when x <= x0
 // (x0 = 2 sqrt(l0 l2), or l0/M + l2 M in the linear regime), so |a_i| + e_i <= x0
-// proves the term is zero.  Every other coordinate (all of F1, and the free
-// coordinates the screen cannot settle) gets its X_i^T r in FP64.  F0 terms are
-// zero.  The FP64 path (R = double) screens in FP64 with u = 2^-53.
+// proves the term is zero.  F1 coordinates always get their X_i^T r in FP64.
+// A free coordinate the screen cannot settle lies in |X_i^T r| in [|a_i| - e_i,
+// |a_i| + e_i]; nu_i is nondecreasing, so nu_i(|a_i| + e_i) bounds its term from
+// above and nu_i(|a_i| - e_i) from below.  During a solve the bound with the upper
+// values is kept whenever the exact FP64 terms could not change the prune decision
+// (see k_cert_exact); otherwise, and always for bnb_relax_batch and bnb_dual_bound,
+// those coordinates get their X_i^T r in FP64 too.  F0 terms are zero.  The FP64
+// path (R = double) screens in FP64 with u = 2^-53.
 #include <cfloat>
 #include "engine.cuh"
 #include "gemm_simt.cuh"
@@ -60,54 +65,67 @@ struct EpiScreen {
   const double* __restrict__ cert_rn;
   float* __restrict__ gscr;
   uint8_t* __restrict__ cflag;
+  double* __restrict__ cpart;   // [2][nbm][K]: sum nu(|a|+e), sum nu(|a|+e) - nu(|a|-e)
+  Prob P;
   double errc, x0;
   long long p;
+  int nbm, K;
   template <int TM, int TN, int TX, int TY>
   __device__ __forceinline__ void apply(R (&acc)[TM][TN], int m0, int n0, int tm, int tn, int M,
                                         int N) const {
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int q = n0 + tn + j * TY;
-      if (q >= N || !ret_active[q]) continue;
-      const long long slot = ret_slot[q];
-      const double rn = cert_rn[q];
+      const bool col = q < N && ret_active[q];
+      double su = 0.0, ss = 0.0;
+      if (col) {
+        const long long slot = ret_slot[q];
+        const double rn = cert_rn[q];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) {
-        const int m = m0 + tm + i * TX;
-        if (m >= M) continue;
-        const int f = fix[slot * p + m];
-        const double a = (double)acc[i][j];
-        uint8_t need;
-        if (f == 0) need = 0;
-        else if (f == 1) need = 1;
-        else need = (fabs(a) + errc * xnorm[m] * rn + 1e-30 > x0) ? 1 : 0;
-        gscr[(long long)q * p + m] = (float)a;
-        cflag[(long long)q * p + m] = need;
+        for (int i = 0; i < TM; ++i) {
+          const int m = m0 + tm + i * TX;
+          if (m >= M) continue;
+          const int f = fix[slot * p + m];
+          const double a = (double)acc[i][j];
+          const double e = errc * xnorm[m] * rn + 1e-30;
+          uint8_t need = 0;
+          if (f == 1) {
+            need = 1;                                   // F1: always the exact FP64 term
+          } else if (f == -1 && fabs(a) + e > x0) {
+            need = 2;                                   // free, not settled by the screen
+            const double up = nu_coord<double>(fabs(a) + e, -1, P);
+            const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), -1, P);
+            su += up;
+            ss += up - lo;
+          }
+          gscr[(long long)q * p + m] = (float)a;
+          cflag[(long long)q * p + m] = need;
+        }
+      }
+#pragma unroll
+      for (int o = TX / 2; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      }
+      if (tm == 0 && col) {
+        cpart[(long long)blockIdx.x * K + q] = su;
+        cpart[((long long)nbm + blockIdx.x) * K + q] = ss;
       }
     }
   }
 };
 
-// Exact FP64 terms for the flagged coordinates, then the bound (one block per node).
-__global__ void k_cert_exact(const double* __restrict__ X64, const double* __restrict__ r64,
-                             const int8_t* __restrict__ fix, const uint8_t* __restrict__ cflag,
-                             int n, int p, Prob P, const int* __restrict__ ret_slot,
-                             const int* __restrict__ ret_count, const double* __restrict__ cert_rr,
-                             const double* __restrict__ cert_yr, const double* __restrict__ slot_lbp,
-                             double* __restrict__ cert_lb, double* __restrict__ node_lb) {
-  __shared__ int list[256];
-  __shared__ int wcnt[8];
-  __shared__ int cnt;
-  __shared__ double wacc[8];
-  const int q = blockIdx.x;
-  if (q >= *ret_count) return;
-  const int slot = ret_slot[q];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;  // 8 warps
-  const double* r = r64 + (long long)q * n;
-  double nu_w = 0.0;  // this warp's running sum, taken in a fixed order
+// sum over the flagged coordinates with cflag == code of nu_i(|X_i^T r|), exact FP64,
+// in a fixed order (per warp: increasing index; warps combined in order)
+__device__ double exact_terms(const double* __restrict__ X64, const double* __restrict__ r,
+                              const int8_t* __restrict__ fixrow, const uint8_t* __restrict__ flags,
+                              int n, int p, const Prob& P, int code, int* list, int* wcnt, int* cnt,
+                              double* wacc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double nu_w = 0.0;
   for (int i0 = 0; i0 < p; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
-    const int f = (i < p) ? cflag[(long long)q * p + i] : 0;
+    const int f = (i < p) ? (flags[i] == code) : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcnt[w] = __popc(bal);
     __syncthreads();
@@ -117,25 +135,70 @@ __global__ void k_cert_exact(const double* __restrict__ X64, const double* __res
     if (threadIdx.x == 0) {
       int tot = 0;
       for (int t = 0; t < nw; ++t) tot += wcnt[t];
-      cnt = tot;
+      *cnt = tot;
     }
     __syncthreads();
-    for (int t = w; t < cnt; t += nw) {
-      const int col = list[t];
-      const double* x = X64 + (long long)col * n;
+    for (int t = w; t < *cnt; t += nw) {
+      const int c = list[t];
+      const double* x = X64 + (long long)c * n;
       double d = 0.0;
       for (int k = lane; k < n; k += 32) d = fma(x[k], r[k], d);
       d = warp_sum(d);
-      nu_w += nu_coord<double>(fabs(d), fix[(long long)slot * p + col], P);
+      nu_w += nu_coord<double>(fabs(d), fixrow[c], P);
     }
     __syncthreads();
   }
   if (lane == 0) wacc[w] = nu_w;
   __syncthreads();
+  double s = 0.0;
+  for (int t = 0; t < nw; ++t) s += wacc[t];
+  __syncthreads();
+  return s;
+}
+
+// The bound for each retired node (one block of 256 threads per node).
+// F1 terms are exact FP64.  Free coordinates the screen could not settle enter
+// through rigorous upper values nu(|a| + e) (LB_cheap); when a prune threshold is
+// given and LB_cheap already reaches it, or even LB_cheap plus the total interval
+// width cannot reach it, the exact FP64 terms cannot change the decision and
+// LB_cheap (a valid bound) is kept; otherwise they are computed exactly.
+__global__ void k_cert_exact(const double* __restrict__ X64, const double* __restrict__ r64,
+                             const int8_t* __restrict__ fix, const uint8_t* __restrict__ cflag,
+                             const double* __restrict__ cpart, int nbm, int K, int n, int p,
+                             Prob P, const int* __restrict__ ret_slot,
+                             const int* __restrict__ ret_count, const double* __restrict__ cert_rr,
+                             const double* __restrict__ cert_yr, const double* __restrict__ slot_lbp,
+                             const double* __restrict__ inc_ub, const double* __restrict__ params,
+                             int use_threshold, double* __restrict__ cert_lb,
+                             double* __restrict__ node_lb) {
+  __shared__ int list[256];
+  __shared__ int wcnt[8];
+  __shared__ int cnt;
+  __shared__ double wacc[8];
+  __shared__ double shd[32];
+  const int q = blockIdx.x;
+  if (q >= *ret_count) return;
+  const int slot = ret_slot[q];
+  const double* r = r64 + (long long)q * n;
+  const int8_t* fixrow = fix + (long long)slot * p;
+  const uint8_t* flags = cflag + (long long)q * p;
+  double su = 0.0, ss = 0.0;
+  for (int b = threadIdx.x; b < nbm; b += blockDim.x) {
+    su += cpart[(long long)b * K + q];
+    ss += cpart[((long long)nbm + b) * K + q];
+  }
+  su = block_sum(su, shd);
+  ss = block_sum(ss, shd);
+  const double s1 = exact_terms(X64, r, fixrow, flags, n, p, P, 1, list, wcnt, &cnt, wacc);
+  const double base = -0.5 * cert_rr[q] + cert_yr[q] - s1;
+  double lb = base - su;
+  bool exact = true;
+  if (use_threshold) {
+    const double thr = inc_ub[0] * (1.0 - params[0]);
+    if (lb >= thr || lb + ss < thr) exact = false;
+  }
+  if (exact) lb = base - exact_terms(X64, r, fixrow, flags, n, p, P, 2, list, wcnt, &cnt, wacc);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int t = 0; t < nw; ++t) s += wacc[t];
-    const double lb = -0.5 * cert_rr[q] + cert_yr[q] - s;
     cert_lb[q] = lb;
     const double lp = slot_lbp[slot];
     node_lb[q] = lb > lp ? lb : lp;
@@ -143,7 +206,8 @@ __global__ void k_cert_exact(const double* __restrict__ X64, const double* __res
 }
 
 template <class R>
-int certify(Engine<R>& e, const double* r_given) {
+int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
+  using C = TileCfg<R>;
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   k_cert_prep<R><<<K, 256, 0, st>>>(e.y64, e.U, r_given, n, e.ret_slot, e.ret_count, e.r64, e.rS,
@@ -155,18 +219,21 @@ int certify(Engine<R>& e, const double* r_given) {
   const double errc = (sizeof(R) == 4 ? (gam * (1 + u) * (1 + u) + 2 * u * (1 + u))
                                       : (gam * (1 + u) * (1 + u) + 2 * u)) * (1.0 + 1e-3);
   const double x0 = e.P.x0;
+  const int nbm = (p + C::BM - 1) / C::BM;
   const R* Xs;
   if constexpr (sizeof(R) == 4) Xs = (const R*)e.X32; else Xs = (const R*)e.X64;
   BNB_CUDA_OK((gemm_simt<R, true, false>(
       st, Xs, n, p, K, n, 1, e.ret_active, BPlainK<R>{e.rS, n},
-      EpiScreen<R>{e.fix, e.ret_slot, e.ret_active, e.xnorm, e.cert_rn, e.gscr, e.cflag, errc, x0, p})));
-  k_cert_exact<<<K, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot, e.ret_count,
-                                  e.cert_rr, e.cert_yr, e.slot_lbp, e.cert_lb, e.node_lb);
+      EpiScreen<R>{e.fix, e.ret_slot, e.ret_active, e.xnorm, e.cert_rn, e.gscr, e.cflag, e.cpart,
+                   e.P, errc, x0, p, nbm, K})));
+  k_cert_exact<<<K, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,
+                                  e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr, e.slot_lbp,
+                                  e.inc_ub, e.params_d, use_threshold ? 1 : 0, e.cert_lb, e.node_lb);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }
 
-template int certify<float>(Engine<float>&, const double*);
-template int certify<double>(Engine<double>&, const double*);
+template int certify<float>(Engine<float>&, const double*, bool);
+template int certify<double>(Engine<double>&, const double*, bool);
 
 }  // namespace bnb

@@ -101,7 +101,8 @@ struct Engine {
   double *cert_lb = nullptr, *node_lb = nullptr;
   R* rS = nullptr;              // residual in screen precision, K x n
   float* gscr = nullptr;        // screened X_i^T r, K x p
-  uint8_t* cflag = nullptr;     // K x p: coordinate needs the exact FP64 term
+  uint8_t* cflag = nullptr;     // K x p: 1 = exact FP64 term (F1), 2 = free, unsettled by the screen
+  double* cpart = nullptr;      // [2][ceil(p/64)][K] screen partial sums
   int* flist = nullptr;         // K x p flagged index lists
 
   // branching / upper bound
@@ -155,7 +156,8 @@ struct Engine {
 template <class R> int setup_data(Engine<R>& e, const double* dX, const double* dy);
 template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol,
                                   bool use_incumbent);
-template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */);
+template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */,
+                               bool use_threshold);
 template <class R> int branch_support(Engine<R>& e, bool write_z);
 template <class R> int upper_bound(Engine<R>& e, bool force_polish);
 template <class R> int queue_push(Engine<R>& e);

@@ -28,7 +28,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;             // 64 BF16 = 128 bytes: one swizzle row
-constexpr int EPI_WARPS = 8;       // two warps per TMEM lane quarter
+constexpr int EPI_WARPS = 8;       // default: two warps per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
@@ -140,7 +140,8 @@ struct Geo {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (NSPLIT == 3 ? 2 : 1);
-  static constexpr int STAGES = (NSPLIT == 3) ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
+  static constexpr int STAGES = (BN <= 64) ? (NSPLIT == 3 ? 2 : 4)          // ~100 KB: 2 CTAs per SM
+                                            : (NSPLIT == 3) ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
   static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
@@ -152,10 +153,10 @@ struct Maps {
 // Epilogue interface:
 //   epi(row m, first column n0 + c, 16 accumulator values, M, N, lane quarter q, smem)
 //     called by every epilogue thread for each 16-column chunk of its row;
-//   epi.finish(t in [0, 128), m0, n0, M, N, smem)  after the four epilogue warps meet;
+//   epi.finish(t, nthreads, m0, n0, M, N, smem)  after the epilogue warps meet;
 //   Epi::SMEM_FLOATS  shared scratch the functor needs.
-template <int BN, int NSPLIT, class Epi>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int BN, int NSPLIT, class Epi, int EPIW>
+__global__ void __launch_bounds__(64 + 32 * EPIW, EPIW == 4 ? 2 : 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant__ CUtensorMap ma_lo,
                const __grid_constant__ CUtensorMap mb_hi, const __grid_constant__ CUtensorMap mb_lo,
                int M, int N, int Kred, int kchunk, const int* __restrict__ active, int* err, Epi epi) {
@@ -244,21 +245,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
   } else if (warp >= 2) {
     // ---------------- epilogue: warp w owns TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
     const int q = warp & 3;
-    const int g = (warp - 2) >> 2;      // which of the quarter's two warps
+    const int g = (warp - 2) >> 2;      // which of the quarter's EPIW/4 warps
     const bool ok = mbar_wait(&done_bar, 0, err, 4);
     fence_after();
     const int row = m0 + 32 * q + lane;
     if (ok) {
 #pragma unroll 1
-      for (int c = 16 * g; c < BN; c += 32) {
+      for (int c = 16 * g; c < BN; c += 16 * (EPIW / 4)) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
         epi(row, n0 + c, v, M, N, q, epi_smem);
       }
     }
     // the epilogue warps meet (named barrier 1) before the per-tile finish
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
-    if (ok) epi.finish(threadIdx.x - 64, m0, n0, M, N, epi_smem);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * EPIW) : "memory");
+    if (ok) epi.finish(threadIdx.x - 64, 32 * EPIW, m0, n0, M, N, epi_smem);
   }
   fence_before();
   __syncthreads();

@@ -37,7 +37,7 @@ inline int tc_chunk(int Kred, int splits, int* nsplit) {
   return per * tc::BK;
 }
 
-template <int BN, int NSPLIT, class Epi>
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
 int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
             int splits, const int* active, int* err, Epi epi) {
   using G = tc::Geo<BN, NSPLIT>;
@@ -54,14 +54,14 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
   }
   int ns = 1;
   const int kchunk = tc_chunk(Kred, splits, &ns);
-  auto kern = tc::tc_gemm_kernel<BN, NSPLIT, Epi>;
+  auto kern = tc::tc_gemm_kernel<BN, NSPLIT, Epi, EPIW>;
   static bool attr_set = false;
   if (!attr_set) {
     BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
     attr_set = true;
   }
   dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, ns);
-  kern<<<grid, tc::THREADS, G::SMEM, st>>>(ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi);
+  kern<<<grid, 64 + 32 * EPIW, G::SMEM, st>>>(ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }
@@ -71,7 +71,7 @@ struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;
   float* __restrict__ C;
   long long ldc, zstride;
-  __device__ __forceinline__ void finish(int, int, int, int, int, float*) const {}
+  __device__ __forceinline__ void finish(int, int, int, int, int, int, float*) const {}
   __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N, int,
                                              float*) const {
     if (m >= M) return;
