@@ -74,6 +74,8 @@ typedef struct {
   double relax_alpha;    /* ADMM over-relaxation in [1, 1.9]; 1 = the plain update order of
                             Eq. admm-update (default); alpha > 1 uses alpha b + (1 - alpha)
                             beta in the beta- and v-updates.  Bounds are valid for any alpha. */
+  int root_heuristic;    /* 1 (default): seed the incumbent with the matching-pursuit
+                            heuristic (Appendix A.2) polished exactly in FP64 */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */
@@ -216,6 +218,15 @@ int bnb_solve_launch(bnb_handle* h, int rounds);
 int bnb_solve_poll(bnb_handle* h, bnb_progress* out);
 int bnb_solve_finish(bnb_handle* h, double* beta_out, double* ub, double* lb, long long* nodes,
                      int* status);
+
+/*
+ * Matching-pursuit root heuristic (Section 3.5, Appendix A.2): greedy forward /
+ * backward single-coordinate moves from beta = 0 (scores in the ADMM precision),
+ * then the exact FP64 box ridge on the support it ends on.  Writes that solution
+ * (p FP64, host) and its objective of Eq. original.  Overwrites the handle's
+ * incumbent (bnb_solve re-initialises it).
+ */
+int bnb_root_heuristic(bnb_handle* h, double* beta_out, double* ub_out);
 
 /* The CUDA stream the handle runs on (cudaStream_t as void*). */
 void* bnb_stream(const bnb_handle* h);

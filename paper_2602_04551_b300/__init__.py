@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_dual_bound_static",
+           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_dual_bound_static",
            "bnb_get_stats",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
@@ -42,7 +42,8 @@ class bnb_options(ctypes.Structure):
                 ("max_nodes", ctypes.c_longlong), ("queue_capacity", ctypes.c_longlong),
                 ("warm_capacity", ctypes.c_longlong), ("support_max", ctypes.c_int),
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
+                ("root_heuristic", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_solve_poll": ([P, P], I),
         "bnb_solve_finish": ([P, P, P, P, P, P], I),
         "bnb_stream": ([P], P),
+        "bnb_root_heuristic": ([P, P, P], I),
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
@@ -292,6 +294,13 @@ def bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit=1, bn=128, splits=1, dC=None):
     _check(load_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
                                             _ptr(dC), ctypes.byref(err)))
     return err.value
+
+
+def bnb_root_heuristic(h: Handle):
+    beta = np.empty(h.p, np.float64)
+    ub = ctypes.c_double()
+    _check(load_library().bnb_root_heuristic(h.ptr, _ptr(beta), ctypes.byref(ub)), h.ptr)
+    return beta, ub.value
 
 
 def bnb_stream(h: Handle) -> int:

@@ -311,6 +311,12 @@ static inline int g1d(long long m) {
 
 using namespace bnb;
 
+template <class R>
+static int mp_moves(const Engine<R>& e) {
+  const int m = 2 * e.smax + 16;
+  return m < 4 * e.p ? m : 4 * e.p;
+}
+
 struct SolveState {
   bool started = false, done = false;
   int status = BNB_STATUS_OPTIMAL;
@@ -362,6 +368,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->device = 0;
   o->stream = nullptr;
   o->relax_alpha = 1.0;
+  o->root_heuristic = 1;
   return BNB_OK;
 }
 
@@ -810,6 +817,9 @@ static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
   BNB_CUDA_OK(cudaMemcpyAsync(e.params_d, params, sizeof(params), cudaMemcpyHostToDevice, e.st));
   if (int rc = queue_init(e)) return rc;
   BNB_CUDA_OK(cudaMemsetAsync(e.inc_beta, 0, sizeof(double) * e.p, e.st));
+  if (o.root_heuristic) {
+    if (int rc = root_heuristic(e, mp_moves(e))) return rc;
+  }
   BNB_CUDA_OK(cudaStreamSynchronize(e.st));
   e.nodes = e.rounds = e.admm_iters = e.pruned = e.polished = e.pool_peak = 0;
   e.max_depth = 0;
@@ -979,6 +989,21 @@ extern "C" int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_lau
   return dispatch(h, [&](auto& e) -> int {
     if (!state_of(h).started) return fail(BNB_EINVAL, "bnb_solve_start was not called");
     return profile_round(h, e, stage_ms, stage_launches, nstages);
+  });
+}
+
+extern "C" int bnb_root_heuristic(bnb_handle* h, double* beta_out, double* ub_out) {
+  if (!h) return fail(BNB_EINVAL, "handle is NULL");
+  return dispatch(h, [&](auto& e) -> int {
+    double inf = INFINITY;
+    BNB_CUDA_OK(cudaMemcpyAsync(e.inc_ub, &inf, sizeof(double), cudaMemcpyHostToDevice, e.st));
+    BNB_CUDA_OK(cudaMemsetAsync(e.inc_beta, 0, sizeof(double) * e.p, e.st));
+    if (int rc = root_heuristic(e, mp_moves(e))) return rc;
+    if (beta_out)
+      BNB_CUDA_OK(cudaMemcpyAsync(beta_out, e.inc_beta, sizeof(double) * e.p, cudaMemcpyDeviceToHost, e.st));
+    if (ub_out) BNB_CUDA_OK(cudaMemcpyAsync(ub_out, e.inc_ub, sizeof(double), cudaMemcpyDeviceToHost, e.st));
+    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+    return 0;
   });
 }
 

@@ -166,6 +166,7 @@ template <class R> int queue_init(Engine<R>& e);
 template <class R> int queue_status(Engine<R>& e);
 template <class R> int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K);
 int admm_iterations_tc(Engine<float>& e, int iters);
+template <class R> int root_heuristic(Engine<R>& e, int max_moves);
 int setup_tc(Engine<float>& e);
 
 }  // namespace bnb

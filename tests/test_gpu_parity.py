@@ -230,3 +230,23 @@ def test_over_relaxed_admm_keeps_bounds_valid_and_answers_exact(prec):
         res = bnb.bnb_solve(h, 1e-9)
     assert tuple(np.nonzero(res["beta"])[0]) == br.support
     assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_root_heuristic_matches_oracle(prec):
+    """Matching pursuit + exact polish: in FP64 the same greedy decisions as the
+    oracle (same support, objective within 1e-10); in the mixed path a feasible
+    point whose reported objective is its exact FP64 value."""
+    from oracle import mp as omp
+    for name, frac in (("c1", 0.05), ("c2_small", 0.05), ("c1_p16", 0.02)):
+        inst, lam0, lam2, M = _inst(name, 0, frac=frac)
+        with _handle(inst, lam0, lam2, M, prec, K=16) as h:
+            beta, ubv = bnb.bnb_root_heuristic(h)
+        assert np.all(np.abs(beta) <= M * (1 + 1e-12))
+        assert ubv == pytest.approx(relax.mip_objective(inst.X, inst.y, beta, lam0, lam2), rel=1e-12)
+        (obj, bref), S = omp.root_incumbent(inst.X, inst.y, lam0, lam2, M)
+        if prec == 0:
+            assert tuple(np.nonzero(beta)[0]) == tuple(np.nonzero(bref)[0])
+            assert ubv == pytest.approx(obj, rel=1e-10)
+        else:
+            assert ubv <= relax.mip_objective(inst.X, inst.y, np.zeros(inst.p), lam0, lam2)
