@@ -60,11 +60,14 @@ def parse():
     ap.add_argument("--check-every", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--fp64-K", type=int, default=512,
+                    help="nodes in the FP64-vs-mixed comparison batch (bounded for large shapes)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--prime-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="tc3", choices=["fp32", "tc3", "bf16"])
     ap.add_argument("--rho", type=float, default=0.0, help="0: chosen by the autotuner")
+    ap.add_argument("--alpha", type=float, default=1.0, help="ADMM over-relaxation (autotuned with rho)")
     return ap.parse_args()
 
 
@@ -154,13 +157,15 @@ def run_mine(args, rank, world):
                                         grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
                                               "check_every": [args.check_every]})
         args.rho = float(best["rho"])
+        args.alpha = float(best.get("relax_alpha", 1.0))
         tune = {"chosen": best, "seconds": entry["seconds"],
                 "trials": [{k: t[k] for k in ("rho", "nodes_per_s", "mean_iters", "lb_mean")}
                            for t in entry["trials"]]}
     s = torch.cuda.Stream()
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
-                                  queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho)
+                                  queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
+                                  relax_alpha=args.alpha)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
@@ -223,7 +228,8 @@ def run_e2e(args, inst, lam0, lam2, M, dev):
 
     K = args.K
     opt = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every, device=dev,
-                                  precision=PREC[args.precision], rho=args.rho)
+                                  precision=PREC[args.precision], rho=args.rho,
+                                  relax_alpha=args.alpha)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     p = inst.p
     root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
@@ -256,13 +262,14 @@ def run_fp64(args, inst, lam0, lam2, M, dev):
     import torch
     import paper_2602_04551_b300 as bnb
 
-    K, p = args.K, inst.p
+    K, p = min(args.K, args.fp64_K), inst.p
     fix = node_sample(inst, K, 7)
     res = {}
     for name, prec in (("mixed", PREC[args.precision]), ("fp64", bnb.BNB_PREC_FP64)):
         s = torch.cuda.Stream()
         opt = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every, device=dev,
-                                      precision=prec, stream=s.cuda_stream, rho=args.rho)
+                                      precision=prec, stream=s.cuda_stream, rho=args.rho,
+                                      relax_alpha=args.alpha)
         h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
         root = bnb.bnb_relax_batch(h, np.full((1, p), -1, np.int8), want_v=True)
         wb = np.repeat(root["beta"], K, 0)
@@ -430,7 +437,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": dict(out["cfg"], K=args.K, check_every=args.check_every, gap=1e-4,
-                           precision=args.precision, rho=args.rho,
+                           precision=args.precision, rho=args.rho, relax_alpha=args.alpha,
                            l2="flushed (256 MiB write) before every step", parallelism="replicas"),
             "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
             "roofline": roofline(out, args, pk),
