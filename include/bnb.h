@@ -237,7 +237,8 @@ void* bnb_stream(const bnb_handle* h);
  * the mean duration of stage k in milliseconds and stage_launches[k] how many
  * times it ran; stages in order: select/refill, X W^T, split-K reduce,
  * G^-1 T, U finalise, X^T U + fused prox/v, check X beta^T, stop test,
- * certificate, branch pick, upper bound, push, status (13 stages).
+ * certificate, branch pick, upper bound, push, status, and inside the certificate
+ * its FP32 screen and its exact FP64 part (15 stages).
  */
 int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int nstages);
 

@@ -31,7 +31,8 @@ SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_dev
            "bnb_get_stats",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
-          "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status")
+          "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status",
+          "cert_screen", "cert_exact")
 
 
 class bnb_options(ctypes.Structure):

@@ -47,6 +47,7 @@ struct EpiAdmm {
   Prob P;
   long long p;
   int nbm, K;
+  int stats;   // 1 on the round's last iteration: per-slot stop-test sums
   template <int TM, int TN, int TX, int TY>
   __device__ __forceinline__ void apply(R (&acc)[TM][TN], int m0, int n0, int tm, int tn, int M,
                                         int N) const {
@@ -70,13 +71,16 @@ struct EpiAdmm {
             const R bn = prox_coord<R>(bt, f, P);
             beta[o] = bn;
             V[o] = v + rho * (bh - bn);
-            s_psi += psi_coord<R>(bn, f, P);
-            s_nu += nu_coord<R>(fabs(rbc[m] - pp), f, P);   // X^T r = rho b_c - P'
-            s_db += (bn - bo) * (bn - bo);
-            s_pr += (b - bn) * (b - bn);
+            if (stats) {
+              s_psi += psi_coord<R>(bn, f, P);
+              s_nu += nu_coord<R>(fabs(rbc[m] - pp), f, P);   // X^T r = rho b_c - P'
+              s_db += (bn - bo) * (bn - bo);
+              s_pr += (b - bn) * (b - bn);
+            }
           }
         }
       }
+      if (!stats) continue;
       // the TX (=16) threads sharing tn are 16 consecutive lanes
 #pragma unroll
       for (int o = TX / 2; o > 0; o >>= 1) {
@@ -274,7 +278,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
       BNB_CUDA_OK((gemm_simt<R, true, false>(
           st, e.XR, n, p, K, n, 1, e.slot_active, BPlainK<R>{e.Up, n},
           EpiAdmm<R>{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, e.g3part, e.P, p, e.nbm3,
-                     K})));
+                     K, it + 1 == iters ? 1 : 0})));
       prof_end(e.prof, st, PK_GEMM_XTU);
     }
     // check: X beta^T for the primal value of Eq. relaxnode2

@@ -126,6 +126,7 @@ struct TcEpiAdmm {
   Prob P;
   long long p, ldp;
   int nbm, K;
+  int stats;                    // 1 on the round's last iteration: per-slot stop-test sums
 
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
@@ -143,6 +144,24 @@ struct TcEpiAdmm {
       bo[j] = ok[j] ? beta[o] : 0.f;
       vv[j] = ok[j] ? V[o] : 0.f;
       ff[j] = ok[j] ? (int)fix[o] : 0;
+    }
+    if (!stats) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (ok[j]) {
+          const int n = n0 + j;
+          const long long o = (long long)n * p + m;
+          const float w = rho * bo[j] - vv[j];
+          const float b = bcm + (w - acc[j]) * irho;
+          const float bh = (float)P.alpha * b + (1.0f - (float)P.alpha) * bo[j];
+          const float bn = prox_coord<float>(bh + vv[j] * irho, ff[j], P);
+          const float vn = vv[j] + rho * (bh - bn);
+          beta[o] = bn;
+          V[o] = vn;
+          split_store(rho * bn - vn, whi, wlo, (long long)n * ldp + m);
+        }
+      }
+      return;
     }
     float s_psi[16], s_nu[16], s_db[16], s_pr[16];
 #pragma unroll
@@ -182,6 +201,7 @@ struct TcEpiAdmm {
 
   __device__ __forceinline__ void finish(int t, int nthr, int m0, int n0, int M, int N,
                                          float* sm) const {
+    if (!stats) return;
     for (int col = t; col < BN; col += nthr) {
       const int n = n0 + col;
       if (n >= N) continue;
@@ -243,7 +263,7 @@ static int round_tc(Engine<float>& e, int iters) {
     TcEpiAdmm<BN3> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                       e.w_hi, NS == 3 ? e.w_lo : nullptr,
                       last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
-                      e.P, p, e.ldp, e.nbm3, K};
+                      e.P, p, e.ldp, e.nbm3, K, last ? 1 : 0};
     if (int rc = tc_gemm<BN3, NS, TcEpiAdmm<BN3>, 4>(st, XC, Uop, p, K, n, 1, e.slot_active,
                                                      e.tc_err, epi))
       return rc;

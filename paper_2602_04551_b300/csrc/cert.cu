@@ -222,13 +222,17 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
   const int nbm = (p + C::BM - 1) / C::BM;
   const R* Xs;
   if constexpr (sizeof(R) == 4) Xs = (const R*)e.X32; else Xs = (const R*)e.X64;
+  prof_begin(e.prof, st);
   BNB_CUDA_OK((gemm_simt<R, true, false>(
       st, Xs, n, p, K, n, 1, e.ret_active, BPlainK<R>{e.rS, n},
       EpiScreen<R>{e.fix, e.ret_slot, e.ret_active, e.xnorm, e.cert_rn, e.gscr, e.cflag, e.cpart,
                    e.P, errc, x0, p, nbm, K})));
+  prof_end(e.prof, st, PK_CERT_SCREEN);
+  prof_begin(e.prof, st);
   k_cert_exact<<<K, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,
                                   e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr, e.slot_lbp,
                                   e.inc_ub, e.params_d, use_threshold ? 1 : 0, e.cert_lb, e.node_lb);
+  prof_end(e.prof, st, PK_CERT_EXACT);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }

@@ -37,7 +37,7 @@ struct Status {                 // copied to the host after every round
 // Optional per-stage CUDA-event timing of a round (bnb_profile_round).
 enum ProfKind {
   PK_SELECT = 0, PK_GEMM_XW, PK_REDUCE_T, PK_GEMM_GT, PK_FINAL_U, PK_GEMM_XTU, PK_CHECK, PK_STOP,
-  PK_CERT, PK_BRANCH, PK_UB, PK_PUSH, PK_STATUS, PK_COUNT
+  PK_CERT, PK_BRANCH, PK_UB, PK_PUSH, PK_STATUS, PK_CERT_SCREEN, PK_CERT_EXACT, PK_COUNT
 };
 struct Profiler {
   std::vector<int> kind;
