@@ -54,6 +54,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--mode", default="rounds", choices=["rounds", "solves", "serve"],
+                    help="rounds: steady-state nodes/s (default); solves: full solves over a "
+                         "lambda0 sweep; serve: Poisson request stream through the serving loop")
+    ap.add_argument("--lam0-fracs", default="0.3,0.15,0.08,0.05,0.03")
+    ap.add_argument("--solve-time-limit", type=float, default=120.0)
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--arrival-rate", type=float, default=20.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--lam0-frac", type=float, default=0.02)
     ap.add_argument("--K", type=int, default=512)
@@ -413,10 +421,112 @@ def combine_ranks(ms, nodes, world):
     return float(mx[0]), float(t[1])
 
 
+def run_solves(args):
+    """Full solves to gap 1e-4 of the workload over a lambda0 sweep (certified solves/s)."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+    from paper_2602_04551_b300 import autotune
+    out = []
+    t_all = time.perf_counter()
+    for frac in [float(f) for f in args.lam0_fracs.split(",")]:
+        inst, lam0, lam2, M, cfg = workload(args.workload, 0, frac)
+        best, _ = autotune.autotune(inst.X, inst.y, lam0, lam2, M, use_cache=False,
+                                    grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
+                                          "check_every": [args.check_every]})
+        o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+                                    precision=PREC[args.precision], rho=best["rho"],
+                                    relax_alpha=best["relax_alpha"], queue_capacity=1 << 22,
+                                    time_limit_s=args.solve_time_limit)
+        with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = bnb.bnb_solve(h, 1e-4)
+            dt = time.perf_counter() - t0
+            st = bnb.bnb_get_stats(h)
+        out.append({"lambda0_frac": frac, "lambda0": lam0, "seconds": dt, "status": res["status"],
+                    "nodes": res["nodes"], "nnz": int(np.count_nonzero(res["beta"])),
+                    "ub": res["ub"], "lb": res["lb"], "gap": (res["ub"] - res["lb"]) / res["ub"],
+                    "nodes_per_s": res["nodes"] / dt, "rho": best["rho"],
+                    "relax_alpha": best["relax_alpha"], "max_depth": st["max_depth"]})
+        print(json.dumps({"solve": out[-1]}), file=sys.stderr, flush=True)
+    done = [r for r in out if r["status"] in ("optimal", "gap")]
+    total = time.perf_counter() - t_all
+    lat = np.array([r["seconds"] for r in done]) if done else np.array([np.nan])
+    line = {"metric": "certified solves/s (gap 1e-4)", "mode": "solves",
+            "value": len(done) / sum(r["seconds"] for r in out), "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE[args.precision],
+            "data": "synthetic", "config": {"workload": args.workload, "K": args.K,
+                                            "lambda0_fracs": args.lam0_fracs,
+                                            "time_limit_s": args.solve_time_limit},
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "wall_s": total, "solves": out}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """The serving workload: independent solves of random shapes arriving as a
+    Poisson stream, admitted under an HBM budget and interleaved on the GPU."""
+    import paper_2602_04551_b300 as bnb
+    from paper_2602_04551_b300.serve import Request, Server, poisson_arrivals, latency_summary
+    rng = np.random.Generator(np.random.PCG64(5000))
+    times = poisson_arrivals(args.requests, args.arrival_rate, 5000)
+    reqs = []
+    for i in range(args.requests):
+        n = int(rng.integers(500, 5001))
+        p = int(rng.integers(1000, 20001))
+        rho = float(rng.choice([0.1, 0.3, 0.5, 0.7]))
+        k = int(rng.integers(5, 26))
+        snr = float(rng.uniform(2, 10))
+        inst = datagen.make_instance(n, p, rho, k, snr, 5000 + i)
+        lam2 = 0.01
+        M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+        lam0 = 0.1 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+        reqs.append(Request(rid=i, X=inst.X, y=inst.y, lambda0=lam0, lambda2=lam2, M=M, gap=1e-4,
+                            arrival=float(times[i]),
+                            options=dict(batch_K=256, rho=0.3, relax_alpha=1.6,
+                                         precision=PREC[args.precision],
+                                         time_limit_s=args.solve_time_limit)))
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), rounds_per_step=4)
+    res = srv.run(reqs)
+    summ = latency_summary(res)
+    status = {}
+    for r in res:
+        status[r.status] = status.get(r.status, 0) + 1
+    # a sample of requests re-solved alone: same support and objective
+    check = []
+    for r in res[: min(4, len(res))]:
+        q = reqs[r.rid]
+        o = bnb.bnb_options_default(M=q.M, batch_K=256, rho=0.3, relax_alpha=1.6,
+                                    precision=PREC[args.precision],
+                                    time_limit_s=args.solve_time_limit, queue_capacity=1 << 18)
+        with bnb.bnb_create(q.X, q.y, q.lambda0, q.lambda2, o) as h:
+            a = bnb.bnb_solve(h, q.gap)
+        check.append({"rid": r.rid, "same_support": bool(np.array_equal(np.nonzero(a["beta"])[0],
+                                                                          np.nonzero(r.beta)[0])),
+                      "ub_rel_diff": abs(a["ub"] - r.ub) / abs(a["ub"])})
+    line = {"metric": "serving: p50/p99 time to certified gap 1e-4", "mode": "serve",
+            "value": summ["solves_per_s"], "unit": "solves/s", "p50_s": summ["p50_s"],
+            "p99_s": summ["p99_s"], "mean_s": summ["mean_s"], "makespan_s": summ["makespan_s"],
+            "solves": summ["solves"], "status": status, "nodes": summ["nodes"],
+            "peak_admitted": srv.peak_active, "peak_bytes": srv.peak_used, "n_gpus": 1,
+            "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": "serve", "requests": args.requests,
+                       "arrival_rate_per_s": args.arrival_rate, "budget_gb": args.budget_gb,
+                       "time_limit_s": args.solve_time_limit},
+            "alone_vs_mix": check}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.mode == "solves":
+        run_solves(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
