@@ -471,18 +471,25 @@ def run_serve(args):
     rng = np.random.Generator(np.random.PCG64(5000))
     times = poisson_arrivals(args.requests, args.arrival_rate, 5000)
     reqs = []
+    lam2 = 0.01
+
+    def loader(n, p, rho, k, snr, seed):
+        def make():
+            inst = datagen.make_instance(n, p, rho, k, snr, seed)
+            M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+            lam0 = 0.1 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+            return inst.X, inst.y, lam0, M
+        return make
+
     for i in range(args.requests):
         n = int(rng.integers(500, 5001))
         p = int(rng.integers(1000, 20001))
         rho = float(rng.choice([0.1, 0.3, 0.5, 0.7]))
         k = int(rng.integers(5, 26))
         snr = float(rng.uniform(2, 10))
-        inst = datagen.make_instance(n, p, rho, k, snr, 5000 + i)
-        lam2 = 0.01
-        M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
-        lam0 = 0.1 * datagen.lambda0_scale(inst.X, inst.y, lam2)
-        reqs.append(Request(rid=i, X=inst.X, y=inst.y, lambda0=lam0, lambda2=lam2, M=M, gap=1e-4,
-                            arrival=float(times[i]),
+        reqs.append(Request(rid=i, X=None, y=None, lambda0=0.0, lambda2=lam2, M=1.0, gap=1e-4,
+                            arrival=float(times[i]), shape=(n, p),
+                            loader=loader(n, p, rho, k, snr, 5000 + i),
                             options=dict(batch_K=256, rho=0.3, relax_alpha=1.6,
                                          precision=PREC[args.precision],
                                          time_limit_s=args.solve_time_limit)))
@@ -496,10 +503,12 @@ def run_serve(args):
     check = []
     for r in res[: min(4, len(res))]:
         q = reqs[r.rid]
-        o = bnb.bnb_options_default(M=q.M, batch_K=256, rho=0.3, relax_alpha=1.6,
+        X, y, lam0, M = q.loader()
+        o = bnb.bnb_options_default(M=M, batch_K=256, rho=0.3, relax_alpha=1.6,
                                     precision=PREC[args.precision],
-                                    time_limit_s=args.solve_time_limit, queue_capacity=1 << 18)
-        with bnb.bnb_create(q.X, q.y, q.lambda0, q.lambda2, o) as h:
+                                    time_limit_s=args.solve_time_limit, queue_capacity=1 << 18,
+                                    warm_capacity=1 << 14)
+        with bnb.bnb_create(X, y, lam0, q.lambda2, o) as h:
             a = bnb.bnb_solve(h, q.gap)
         check.append({"rid": r.rid, "same_support": bool(np.array_equal(np.nonzero(a["beta"])[0],
                                                                           np.nonzero(r.beta)[0])),

@@ -24,14 +24,25 @@ import numpy as np
 @dataclasses.dataclass
 class Request:
     rid: int
-    X: np.ndarray
-    y: np.ndarray
+    X: Any                          # (n, p) design, or None with `loader`
+    y: Any
     lambda0: float
     lambda2: float
     M: float
     gap: float = 1e-4
     arrival: float = 0.0            # seconds after the start of the run
     options: dict = dataclasses.field(default_factory=dict)
+    shape: tuple = None             # (n, p); taken from X when not given
+    loader: Callable = None         # () -> (X, y, lambda0, M), called at admission
+
+    def dims(self):
+        return self.shape if self.shape is not None else self.X.shape
+
+    def data(self):
+        """(X, y, lambda0, M), generating them on first use when a loader is set."""
+        if self.X is None:
+            self.X, self.y, self.lambda0, self.M = self.loader()
+        return self.X, self.y, self.lambda0, self.M
 
 
 @dataclasses.dataclass
@@ -59,18 +70,21 @@ class LibraryBackend:
         self.bnb = bnb
         self.device = device
 
-    def _options(self, req: Request):
+    def _options(self, req: Request, M=1.0):
         kw = dict(batch_K=256, queue_capacity=1 << 18, warm_capacity=1 << 14, device=self.device)
         kw.update(req.options)
-        return self.bnb.bnb_options_default(M=req.M, **kw)
+        return self.bnb.bnb_options_default(M=M, **kw)
 
     def footprint(self, req: Request) -> int:
-        n, p = req.X.shape
+        n, p = req.dims()
         return self.bnb.bnb_footprint(n, p, self._options(req))
 
     def start(self, req: Request) -> Any:
-        h = self.bnb.bnb_create(req.X, req.y, req.lambda0, req.lambda2, self._options(req))
+        X, y, lam0, M = req.data()
+        h = self.bnb.bnb_create(X, y, lam0, req.lambda2, self._options(req, M))
         self.bnb.bnb_solve_start(h, req.gap)
+        if req.loader is not None:      # the handle holds its own copy on the device
+            req.X = req.y = None
         return h
 
     def launch(self, h, rounds: int):

@@ -27,7 +27,8 @@ class FakeBackend:
         self.started = []
 
     def footprint(self, r):
-        return r.X.shape[0] * r.X.shape[1]
+        n, p = r.dims()
+        return n * p
 
     def start(self, r):
         self.started.append(r.rid)
