@@ -426,6 +426,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
 }
 
 static int check_device(int dev) {
+  cudaGetLastError();  // a failure left by unrelated earlier work must not be reported here
   int count = 0;
   if (cudaGetDeviceCount(&count) != cudaSuccess || count <= 0) {
     cudaGetLastError();

@@ -41,23 +41,25 @@ enum ProfKind {
 };
 struct Profiler {
   std::vector<int> kind;
-  std::vector<cudaEvent_t> ev;  // two per mark
-  cudaEvent_t open = nullptr;
+  std::vector<cudaEvent_t> ev;    // two per mark
+  std::vector<cudaEvent_t> open;  // begin events of the intervals still open (nesting)
 };
 inline void prof_begin(Profiler* pf, cudaStream_t st) {
   if (!pf) return;
-  cudaEventCreate(&pf->open);
-  cudaEventRecord(pf->open, st);
+  cudaEvent_t e0;
+  cudaEventCreate(&e0);
+  cudaEventRecord(e0, st);
+  pf->open.push_back(e0);
 }
 inline void prof_end(Profiler* pf, cudaStream_t st, int kind) {
-  if (!pf) return;
+  if (!pf || pf->open.empty()) return;
   cudaEvent_t e1;
   cudaEventCreate(&e1);
   cudaEventRecord(e1, st);
   pf->kind.push_back(kind);
-  pf->ev.push_back(pf->open);
+  pf->ev.push_back(pf->open.back());
   pf->ev.push_back(e1);
-  pf->open = nullptr;
+  pf->open.pop_back();
 }
 
 template <class R>
