@@ -253,6 +253,16 @@ int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int 
 int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd, int nsplit, int bn,
                       int splits, float* dC, int* err_out);
 
+/* Diagnostics: the same product through the cluster-reduced tcgen05 kernel that the
+ * ADMM iteration uses for X W'^T and G^-1 T (128 x 256 tiles; the K range split over
+ * `cluster` CTAs of one thread-block cluster, 1 <= cluster <= 8, whose partial tiles
+ * are summed in rank order through distributed shared memory).  Arguments as for
+ * bnb_tc_gemm_check; C (device, M x N column-major FP32) is written directly.
+ * Returns BNB_EINVAL for bad sizes or a cluster size the device cannot co-schedule.
+ * The paper has no counterpart: this checks a B300-specific kernel in isolation. */
+int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
+                              int nsplit, int cluster, float* dC, int* err_out);
+
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */
   long long rounds;         /* device rounds run */

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_dual_bound_static",
+           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_dual_bound_static",
            "bnb_get_stats",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_root_heuristic": ([P, P, P], I),
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
+        "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
@@ -294,6 +295,14 @@ def bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit=1, bn=128, splits=1, dC=None):
     err = ctypes.c_int(0)
     _check(load_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
                                             _ptr(dC), ctypes.byref(err)))
+    return err.value
+
+
+def bnb_tc_gemm_check_cluster(dA, dB, M, N, Kd, nsplit=3, cluster=8, dC=None):
+    """C = A B^T through the cluster-reduced tensor-core kernel (FP64 in, FP32 out)."""
+    err = ctypes.c_int(0)
+    _check(load_library().bnb_tc_gemm_check_cluster(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, cluster,
+                                                    _ptr(dC), ctypes.byref(err)))
     return err.value
 
 

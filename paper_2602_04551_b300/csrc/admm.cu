@@ -151,22 +151,37 @@ __global__ void k_stop(const R* __restrict__ XBpart, int S, const R* __restrict_
                        int* __restrict__ slot_retire, double* __restrict__ slot_gap,
                        double* __restrict__ slot_dual, double* __restrict__ slot_primal, int iters,
                        int max_iter, double node_tol, const double* __restrict__ inc_ub,
-                       const double* __restrict__ params, int use_inc) {
+                       const double* __restrict__ params, int use_inc,
+                       const float* __restrict__ tstat, int nbt) {
   __shared__ R sh[32];
   const int s = blockIdx.x;
   if (!slot_active[s]) {
     if (threadIdx.x == 0) slot_retire[s] = 0;
     return;
   }
-  const long long zs = (long long)n * K, base = (long long)s * n;
   R xr = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    R xb = XBpart[base + i];
-    for (int z = 1; z < S; ++z) xb += XBpart[z * zs + base + i];
-    R r = y[i] - xb;
-    xr += r * r;
+  R rs[2] = {0, 0};
+  if (tstat) {
+    // per-tile column sums of the cluster-reduced products, added in tile order
+    R a[3] = {0, 0, 0};
+    for (int b = threadIdx.x; b < nbt; b += blockDim.x)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) a[t] += (R)tstat[((long long)t * nbt + b) * K + s];
+    rs[0] = block_sum(a[0], sh);
+    rs[1] = block_sum(a[1], sh);
+    xr = block_sum(a[2], sh);
+  } else {
+    const long long zs = (long long)n * K, base = (long long)s * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      R xb = XBpart[base + i];
+      for (int z = 1; z < S; ++z) xb += XBpart[z * zs + base + i];
+      R r = y[i] - xb;
+      xr += r * r;
+    }
+    xr = block_sum(xr, sh);
+    rs[0] = rstat[s];
+    rs[1] = rstat[K + s];
   }
-  xr = block_sum(xr, sh);
   R q[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
@@ -176,7 +191,7 @@ __global__ void k_stop(const R* __restrict__ XBpart, int S, const R* __restrict_
   }
   if (threadIdx.x == 0) {
     const double primal = 0.5 * (double)xr + (double)q[0];
-    const double dual = -0.5 * (double)rstat[s] + (double)rstat[K + s] - (double)q[1];
+    const double dual = -0.5 * (double)rs[0] + (double)rs[1] - (double)q[1];
     const double gap = (primal - dual) / fmax(1.0, fabs(primal));
     const int it = slot_iters[s] + iters;
     slot_iters[s] = it;
@@ -292,7 +307,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   k_stop<R><<<K, 256, 0, st>>>(e.XBpart, S_check, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
                                e.slot_active, e.slot_iters, e.slot_retire, e.slot_gap, e.slot_dual,
                                e.slot_primal, iters, max_iter, node_tol, e.inc_ub, e.params_d,
-                               use_inc ? 1 : 0);
+                               use_inc ? 1 : 0, e.tc_c1 > 0 ? e.tc_stat : nullptr, e.nbt);
   k_retired_list<<<1, 1024, 0, st>>>(K, e.slot_retire, e.slot_active, e.ret_slot, e.ret_active,
                                      e.ret_count);
   prof_end(e.prof, st, PK_STOP);

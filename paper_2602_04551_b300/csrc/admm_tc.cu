@@ -85,6 +85,97 @@ __global__ void k_finalize_u_tc(const float* __restrict__ Upart, int S, float* _
   }
 }
 
+// ---- epilogues of the cluster-reduced products (4 consecutive rows m.. of column n)
+
+__device__ __forceinline__ void split_store4(const float (&v)[4], __nv_bfloat16* hi,
+                                             __nv_bfloat16* lo, long long o, int cnt) {
+  __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = __float2bfloat16_rn(v[j]);
+    l[j] = __float2bfloat16_rn(v[j] - __bfloat162float(h[j]));
+  }
+  if (cnt == 4) {                 // o is a multiple of 4 elements: 8-byte stores
+    *reinterpret_cast<uint2*>(hi + o) = *reinterpret_cast<const uint2*>(h);
+    if (lo) *reinterpret_cast<uint2*>(lo + o) = *reinterpret_cast<const uint2*>(l);
+  } else {
+    for (int j = 0; j < cnt; ++j) {
+      hi[o + j] = h[j];
+      if (lo) lo[o + j] = l[j];
+    }
+  }
+}
+
+// T = X W'^T: the BF16 (hi/lo) operand of the next product, K x ld
+struct TcEpiT {
+  static constexpr int NSTAT = 0;
+  __nv_bfloat16 *hi, *lo;
+  long long ld;
+  const int* __restrict__ active;
+  int stats;
+  __device__ __forceinline__ void put4(int m, int n, float4 a, int M, int, float*) const {
+    if (m >= M || !active[n]) return;
+    const float v[4] = {a.x, a.y, a.z, a.w};
+    split_store4(v, hi, lo, (long long)n * ld + m, min(4, M - m));
+  }
+  __device__ __forceinline__ void col(int, int, const float*) const {}
+};
+
+// U' = G^-1 T: the BF16 operand of X^T U'; with `stats` (the round's last iteration)
+// also U = u_c + U' in FP32 and the per-tile sums ||y - U||^2, y^T (y - U)
+struct TcEpiU {
+  static constexpr int NSTAT = 2;
+  __nv_bfloat16 *hi, *lo;
+  long long ld;
+  const int* __restrict__ active;
+  float* __restrict__ U;
+  const float* __restrict__ uc;
+  const float* __restrict__ y;
+  float* __restrict__ stat;     // [3][nbt][K]
+  int nbt, K;
+  int stats;
+  __device__ __forceinline__ void put4(int m, int n, float4 a, int M, int, float* st) const {
+    if (m >= M || !active[n]) return;
+    const float v[4] = {a.x, a.y, a.z, a.w};
+    const int cnt = min(4, M - m);
+    split_store4(v, hi, lo, (long long)n * ld + m, cnt);
+    if (!stats) return;
+    for (int j = 0; j < cnt; ++j) {
+      const float u = uc[m + j] + v[j];
+      U[(long long)n * M + m + j] = u;
+      const float r = y[m + j] - u;
+      st[0] += r * r;
+      st[1] += y[m + j] * r;
+    }
+  }
+  __device__ __forceinline__ void col(int mt, int n, const float* st) const {
+    stat[(0LL * nbt + mt) * K + n] = st[0];
+    stat[(1LL * nbt + mt) * K + n] = st[1];
+  }
+};
+
+// check product X beta^T: per-tile sums of (y - X beta)^2 (nothing else is stored)
+struct TcEpiResid {
+  static constexpr int NSTAT = 1;
+  const int* __restrict__ active;
+  const float* __restrict__ y;
+  float* __restrict__ stat;
+  int nbt, K;
+  int stats;
+  __device__ __forceinline__ void put4(int m, int n, float4 a, int M, int, float* st) const {
+    if (m >= M || !active[n]) return;
+    const float v[4] = {a.x, a.y, a.z, a.w};
+    const int cnt = min(4, M - m);
+    for (int j = 0; j < cnt; ++j) {
+      const float r = y[m + j] - v[j];
+      st[0] += r * r;
+    }
+  }
+  __device__ __forceinline__ void col(int mt, int n, const float* st) const {
+    stat[(2LL * nbt + mt) * K + n] = st[0];
+  }
+};
+
 // butterfly reduce-scatter of 16 per-lane values over the warp: afterwards lane l
 // holds the warp total of column (l >> 1) (both lanes of a pair hold it)
 __device__ __forceinline__ float reduce_scatter16(float (&v)[16]) {
@@ -239,26 +330,42 @@ static int round_tc(Engine<float>& e, int iters) {
   BNB_CUDA_OK(cudaGetLastError());
   for (int it = 0; it < iters; ++it) {
     const bool last = it + 1 == iters;
-    prof_begin(e.prof, st);
-    if (int rc = tc_gemm<BN, NS>(st, XT, Wop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
-                                 TcEpiStore{(float*)e.Tpart, (long long)n, nK}))
-      return rc;
-    prof_end(e.prof, st, PK_GEMM_XW);
-    prof_begin(e.prof, st);
-    k_reduce_t_tc<<<red_grid, 256, 0, st>>>((float*)e.Tpart, e.tc_s1n, n, K, e.slot_active, e.ldn,
-                                            e.t_hi, NS == 3 ? e.t_lo : nullptr);
-    prof_end(e.prof, st, PK_REDUCE_T);
-    prof_begin(e.prof, st);
-    if (int rc = tc_gemm<BN, NS>(st, GI, Top, n, K, n, e.tc_s2, e.slot_active, e.tc_err,
-                                 TcEpiStore{(float*)e.Upart, (long long)n, nK}))
-      return rc;
-    prof_end(e.prof, st, PK_GEMM_GT);
-    prof_begin(e.prof, st);
-    k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.ucR,
-                                       (float*)e.yR, n, K,
-                                       e.slot_active, (float*)e.rstat, e.ldn, e.u_hi,
-                                       NS == 3 ? e.u_lo : nullptr);
-    prof_end(e.prof, st, PK_FINAL_U);
+    if (e.tc_c1 > 0) {
+      // split-K reduced inside clusters, epilogues write the next operands directly
+      prof_begin(e.prof, st);
+      if (int rc = tc_gemm_cred<BN, NS>(st, XT, Wop, n, K, p, e.tc_c1, e.slot_active, e.tc_err,
+                                        TcEpiT{e.t_hi, NS == 3 ? e.t_lo : nullptr, e.ldn,
+                                               e.slot_active, 0}))
+        return rc;
+      prof_end(e.prof, st, PK_GEMM_XW);
+      prof_begin(e.prof, st);
+      if (int rc = tc_gemm_cred<BN, NS>(
+              st, GI, Top, n, K, n, e.tc_c2, e.slot_active, e.tc_err,
+              TcEpiU{e.u_hi, NS == 3 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
+                     (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
+        return rc;
+      prof_end(e.prof, st, PK_GEMM_GT);
+    } else {
+      prof_begin(e.prof, st);
+      if (int rc = tc_gemm<BN, NS>(st, XT, Wop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
+                                   TcEpiStore{(float*)e.Tpart, (long long)n, nK}))
+        return rc;
+      prof_end(e.prof, st, PK_GEMM_XW);
+      prof_begin(e.prof, st);
+      k_reduce_t_tc<<<red_grid, 256, 0, st>>>((float*)e.Tpart, e.tc_s1n, n, K, e.slot_active,
+                                              e.ldn, e.t_hi, NS == 3 ? e.t_lo : nullptr);
+      prof_end(e.prof, st, PK_REDUCE_T);
+      prof_begin(e.prof, st);
+      if (int rc = tc_gemm<BN, NS>(st, GI, Top, n, K, n, e.tc_s2, e.slot_active, e.tc_err,
+                                   TcEpiStore{(float*)e.Upart, (long long)n, nK}))
+        return rc;
+      prof_end(e.prof, st, PK_GEMM_GT);
+      prof_begin(e.prof, st);
+      k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.ucR,
+                                         (float*)e.yR, n, K, e.slot_active, (float*)e.rstat,
+                                         e.ldn, e.u_hi, NS == 3 ? e.u_lo : nullptr);
+      prof_end(e.prof, st, PK_FINAL_U);
+    }
     prof_begin(e.prof, st);
     TcEpiAdmm<BN3> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                       e.w_hi, NS == 3 ? e.w_lo : nullptr,
@@ -271,9 +378,16 @@ static int round_tc(Engine<float>& e, int iters) {
   }
   // check product X beta^T
   prof_begin(e.prof, st);
-  if (int rc = tc_gemm<BN, NS>(st, XT, Bop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
-                               TcEpiStore{(float*)e.XBpart, (long long)n, nK}))
-    return rc;
+  if (e.tc_c1 > 0) {
+    if (int rc = tc_gemm_cred<BN, NS>(st, XT, Bop, n, K, p, e.tc_c1, e.slot_active, e.tc_err,
+                                      TcEpiResid{e.slot_active, (const float*)e.yR, e.tc_stat,
+                                                 e.nbt, K, 1}))
+      return rc;
+  } else {
+    if (int rc = tc_gemm<BN, NS>(st, XT, Bop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
+                                 TcEpiStore{(float*)e.XBpart, (long long)n, nK}))
+      return rc;
+  }
   prof_end(e.prof, st, PK_CHECK);
   return 0;
 }
@@ -294,8 +408,22 @@ __global__ void k_split_f32(const float* __restrict__ x, long long rows, long lo
   }
 }
 
+template <int NS>
+static int cred_max_cluster(int want) {
+  int c = tc_cred_max_cluster<256, NS, TcEpiT>(want);
+  c = tc_cred_max_cluster<256, NS, TcEpiU>(c);
+  return tc_cred_max_cluster<256, NS, TcEpiResid>(c);
+}
+
 int setup_tc(Engine<float>& e) {
   cudaStream_t st = e.st;
+  if (e.tc_c1 > 0) {
+    const int c1 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c1) : cred_max_cluster<1>(e.tc_c1);
+    const int c2 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c2) : cred_max_cluster<1>(e.tc_c2);
+    if (c1 < 1 || c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
+    e.tc_c1 = c1;
+    e.tc_c2 = c2;
+  }
   const long long n = e.n, p = e.p;
   // column-major X: p columns of length n (leading dimension ldn)
   if (int rc = split_bf16(st, e.X64, n, p, n, e.ldn, false, e.xc_hi, e.xc_lo)) return rc;

@@ -102,8 +102,21 @@ static int allocate(Engine<R>& e) {
       if (e.tc_s2 > st2 / 4) e.tc_s2 = st2 / 4 > 0 ? st2 / 4 : 1;
       tc_chunk(e.p, e.tc_s1, &e.tc_s1n);
       tc_chunk(e.n, e.tc_s2, &e.tc_s2n);
-      if (e.tc_s1n > s1cap) s1cap = e.tc_s1n;
-      if (e.tc_s2n > s2cap) s2cap = e.tc_s2n;
+      // cluster-reduced split-K for the n x K products: enough clusters of <= 8 CTAs to
+      // cover the SMs, each CTA with >= 2 K steps (setup_tc clamps to what the device
+      // can co-schedule); no split-K partial buffers are needed then
+      e.nbt = (int)((n + tc::BM - 1) / tc::BM);
+      const int tiles = e.nbt * (int)((K + 255) / 256);
+      auto cl = [&](int steps) {
+        int c = 148 / tiles;
+        if (c > 8) c = 8;
+        if (c > steps / 2) c = steps / 2;
+        return c < 1 ? 1 : c;
+      };
+      e.tc_c1 = cl(st1);
+      e.tc_c2 = cl(st2);
+      ALLOC(e.tc_stat, 3LL * e.nbt * K);
+      s1cap = s2cap = 0;
       const bool lo = e.tc_mode == 3;
       ALLOC(e.xc_hi, p * e.ldn);
       ALLOC(e.xt_hi, n * e.ldp);
@@ -171,7 +184,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.rS, K * n);
   ALLOC(e.gscr, K * p);
   ALLOC(e.cflag, K * p);
-  ALLOC(e.cpart, 2 * ((p + 63) / 64) * K);
+  ALLOC(e.cpart, 2 * ((p + 31) / 32) * K);   // screen tiles of 32 (FP32) or 64 (FP64) rows
   ALLOC(e.cert_rr, K);
   ALLOC(e.cert_yr, K);
   ALLOC(e.cert_rn, K);

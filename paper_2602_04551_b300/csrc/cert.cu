@@ -115,6 +115,122 @@ struct EpiScreen {
   }
 };
 
+// Screening product of the FP32 engine, a[q][m] = fl32(X32_m^T r32_q) for the retired
+// columns q < R, followed by the EpiScreen bookkeeping.  The shape is tall and skinny
+// (p features x a few dozen retired nodes, contraction n), so the tiles are 32 x 32
+// (about two tiles per SM at R <= 64) and the contraction is split over the four
+// 64-thread groups of a CTA (4 x 4 outputs per thread, register-prefetched 32-wide k
+// steps); the four partial sums are added in a fixed order, so the result does not
+// depend on scheduling.  The rounding bound holds for any summation order; the host
+// adds the SC_G - 1 extra additions to n in gamma.
+constexpr int SC_BM = 32, SC_BN = 32, SC_BK = 32, SC_G = 4, SC_LD = SC_BK + 4;
+
+__global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X32, int n, int p,
+                                                     const float* __restrict__ rS,
+                                                     const int* __restrict__ ret_count,
+                                                     EpiScreen<float> epi) {
+  // operand tiles; after the k loop the same bytes hold the four partial tiles
+  __shared__ __align__(16) float sm[2 * SC_G * SC_BM * SC_LD];
+  static_assert(SC_G * SC_BM * (SC_BN + 1) <= 2 * SC_G * SC_BM * SC_LD, "partial tiles fit");
+  auto As = reinterpret_cast<float(*)[SC_BM][SC_LD]>(sm);
+  auto Bs = reinterpret_cast<float(*)[SC_BN][SC_LD]>(sm + SC_G * SC_BM * SC_LD);
+  auto red = reinterpret_cast<float(*)[SC_BM][SC_BN + 1]>(sm);
+  const int R = *ret_count;
+  const int q0 = blockIdx.y * SC_BN, m0 = blockIdx.x * SC_BM;
+  if (q0 >= R) return;
+  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int tx = t & 7, ty = t >> 3;            // rows tx + 8i, columns ty + 8j
+  const int nk = (n + SC_BK - 1) / SC_BK;
+  const int per = (nk + SC_G - 1) / SC_G;
+  const int kb0 = g * per;
+  float ra[16], rb[16];
+  auto load = [&](int kb) {
+    const int k0 = kb * SC_BK;
+    const bool live = kb < nk;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = t + 64 * i, kk = e & 31, rr = e >> 5;
+      const int k = k0 + kk, m = m0 + rr, q = q0 + rr;
+      ra[i] = (live && k < n && m < p) ? X32[(long long)m * n + k] : 0.f;
+      rb[i] = (live && k < n && q < R) ? rS[(long long)q * n + k] : 0.f;
+    }
+  };
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  load(kb0);
+  for (int it = 0; it < per; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = t + 64 * i, kk = e & 31, rr = e >> 5;
+      As[g][rr][kk] = ra[i];
+      Bs[g][rr][kk] = rb[i];
+    }
+    __syncthreads();
+    if (it + 1 < per) load(kb0 + it + 1);
+#pragma unroll
+    for (int k4 = 0; k4 < SC_BK; k4 += 4) {
+      float4 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = *(const float4*)&As[g][tx + 8 * i][k4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = *(const float4*)&Bs[g][ty + 8 * j][k4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j] = fmaf(a[i].x, b[j].x, acc[i][j]);
+          acc[i][j] = fmaf(a[i].y, b[j].y, acc[i][j]);
+          acc[i][j] = fmaf(a[i].z, b[j].z, acc[i][j]);
+          acc[i][j] = fmaf(a[i].w, b[j].w, acc[i][j]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[g][tx + 8 * i][ty + 8 * j] = acc[i][j];
+  __syncthreads();
+  // epilogue: warp w takes columns w, w + 8, w + 16, w + 24; lane = row
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = m0 + lane;
+  const double xn = m < p ? epi.xnorm[m] : 0.0;
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    const int qq = w + 8 * j, q = q0 + qq;
+    if (q >= R) break;
+    const float a32 = ((red[0][lane][qq] + red[1][lane][qq]) + red[2][lane][qq]) + red[3][lane][qq];
+    double su = 0.0, ss = 0.0;
+    if (m < p) {
+      const long long slot = epi.ret_slot[q];
+      const int f = epi.fix[slot * epi.p + m];
+      const double a = (double)a32;
+      const double e = epi.errc * xn * epi.cert_rn[q] + 1e-30;
+      uint8_t need = 0;
+      if (f == 1) {
+        need = 1;
+      } else if (f == -1 && fabs(a) + e > epi.x0) {
+        need = 2;
+        const double up = nu_coord<double>(fabs(a) + e, -1, epi.P);
+        const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), -1, epi.P);
+        su = up;
+        ss = up - lo;
+      }
+      epi.gscr[(long long)q * epi.p + m] = a32;
+      epi.cflag[(long long)q * epi.p + m] = need;
+    }
+    su = warp_sum(su);
+    ss = warp_sum(ss);
+    if (lane == 0) {
+      epi.cpart[(long long)blockIdx.x * epi.K + q] = su;
+      epi.cpart[((long long)epi.nbm + blockIdx.x) * epi.K + q] = ss;
+    }
+  }
+}
+
 // sum over the flagged coordinates with cflag == code of nu_i(|X_i^T r|), exact FP64,
 // in a fixed order (per warp: increasing index; warps combined in order)
 __device__ double exact_terms(const double* __restrict__ X64, const double* __restrict__ r,
@@ -214,19 +330,23 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
                                     e.cert_rr, e.cert_yr, e.cert_rn);
   BNB_CUDA_OK(cudaGetLastError());
   const double u = (sizeof(R) == 4) ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
-  const double nu_ = (double)(n + 2) * u;
+  const double nu_ = (double)(n + 2 + (sizeof(R) == 4 ? SC_G : 0)) * u;
   const double gam = nu_ / (1.0 - nu_);
   const double errc = (sizeof(R) == 4 ? (gam * (1 + u) * (1 + u) + 2 * u * (1 + u))
                                       : (gam * (1 + u) * (1 + u) + 2 * u)) * (1.0 + 1e-3);
   const double x0 = e.P.x0;
-  const int nbm = (p + C::BM - 1) / C::BM;
-  const R* Xs;
-  if constexpr (sizeof(R) == 4) Xs = (const R*)e.X32; else Xs = (const R*)e.X64;
+  const int nbm = (p + (sizeof(R) == 4 ? SC_BM : C::BM) - 1) / (sizeof(R) == 4 ? SC_BM : C::BM);
+  const EpiScreen<R> epi{e.fix, e.ret_slot, e.ret_active, e.xnorm, e.cert_rn, e.gscr, e.cflag,
+                         e.cpart, e.P, errc, x0, p, nbm, K};
   prof_begin(e.prof, st);
-  BNB_CUDA_OK((gemm_simt<R, true, false>(
-      st, Xs, n, p, K, n, 1, e.ret_active, BPlainK<R>{e.rS, n},
-      EpiScreen<R>{e.fix, e.ret_slot, e.ret_active, e.xnorm, e.cert_rn, e.gscr, e.cflag, e.cpart,
-                   e.P, errc, x0, p, nbm, K})));
+  if constexpr (sizeof(R) == 4) {
+    k_screen32<<<dim3(nbm, (K + SC_BN - 1) / SC_BN), 256, 0, st>>>((const float*)e.X32, n, p,
+                                                                 (const float*)e.rS, e.ret_count, epi);
+    BNB_CUDA_OK(cudaGetLastError());
+  } else {
+    BNB_CUDA_OK((gemm_simt<R, true, false>(st, (const R*)e.X64, n, p, K, n, 1, e.ret_active,
+                                           BPlainK<R>{e.rS, n}, epi)));
+  }
   prof_end(e.prof, st, PK_CERT_SCREEN);
   prof_begin(e.prof, st);
   k_cert_exact<<<K, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,

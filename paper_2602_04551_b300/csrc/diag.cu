@@ -31,7 +31,72 @@ static int run_check(cudaStream_t st, const TcOperand& A, const TcOperand& B, in
                          TcEpiStore{part, (long long)M, (long long)M * N});
 }
 
+// plain FP32 store of the cluster-reduced product, C[m + n M]
+struct TcEpiPlain4 {
+  static constexpr int NSTAT = 0;
+  float* __restrict__ C;
+  int stats;
+  __device__ __forceinline__ void put4(int m, int n, float4 a, int M, int, float*) const {
+    const float v[4] = {a.x, a.y, a.z, a.w};
+    for (int j = 0; j < 4 && m + j < M; ++j) C[(long long)n * M + m + j] = v[j];
+  }
+  __device__ __forceinline__ void col(int, int, const float*) const {}
+};
+
+template <int NS>
+static int run_check_cluster(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N,
+                             int Kd, int cluster, float* C, int* err) {
+  const int c = tc_cred_max_cluster<256, NS, TcEpiPlain4>(cluster);
+  if (c < cluster) return BNB_EINVAL;
+  return tc_gemm_cred<256, NS>(st, A, B, M, N, Kd, cluster, nullptr, err, TcEpiPlain4{C, 0});
+}
+
+// FP64 inputs -> BF16 (hi, and lo for 3 terms) K-major operands with leading dimension ld
+static int make_operands(cudaStream_t st, const double* dA, const double* dB, int M, int N, int Kd,
+                         long long ld, __nv_bfloat16** ah, __nv_bfloat16** al, __nv_bfloat16** bh,
+                         __nv_bfloat16** bl) {
+  cudaError_t ce = cudaSuccess;
+  ce = ce ? ce : cudaMalloc(ah, sizeof(__nv_bfloat16) * ld * M);
+  ce = ce ? ce : cudaMalloc(al, sizeof(__nv_bfloat16) * ld * M);
+  ce = ce ? ce : cudaMalloc(bh, sizeof(__nv_bfloat16) * ld * N);
+  ce = ce ? ce : cudaMalloc(bl, sizeof(__nv_bfloat16) * ld * N);
+  if (ce != cudaSuccess) return BNB_ENOMEM;
+  int rc = 0;
+  if (!rc) rc = cudaMemset(*ah, 0, sizeof(__nv_bfloat16) * ld * M) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(*al, 0, sizeof(__nv_bfloat16) * ld * M) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(*bh, 0, sizeof(__nv_bfloat16) * ld * N) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaMemset(*bl, 0, sizeof(__nv_bfloat16) * ld * N) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = split_bf16(st, dA, Kd, M, Kd, ld, false, *ah, *al);
+  if (!rc) rc = split_bf16(st, dB, Kd, N, Kd, ld, false, *bh, *bl);
+  return rc;
+}
+
 }  // namespace bnb
+
+extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
+                                         int nsplit, int cluster, float* dC, int* err_out) {
+  using namespace bnb;
+  if (M <= 0 || N <= 0 || Kd <= 0 || (nsplit != 1 && nsplit != 3) || cluster < 1 || cluster > 8)
+    return BNB_EINVAL;
+  cudaStream_t st = 0;
+  const long long ld = ((long long)Kd + 7) / 8 * 8;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* err = nullptr;
+  int rc = make_operands(st, dA, dB, M, N, Kd, ld, &ah, &al, &bh, &bl);
+  if (!rc) rc = cudaMalloc(&err, sizeof(int)) == cudaSuccess ? 0 : BNB_ENOMEM;
+  if (!rc) rc = cudaMemset(err, 0, sizeof(int)) == cudaSuccess ? 0 : BNB_ECUDA;
+  TcOperand A{ah, al, M, Kd, ld}, B{bh, bl, N, Kd, ld};
+  if (!rc) rc = nsplit == 3 ? run_check_cluster<3>(st, A, B, M, N, Kd, cluster, dC, err)
+                            : run_check_cluster<1>(st, A, B, M, N, Kd, cluster, dC, err);
+  if (!rc) rc = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : BNB_ECUDA;
+  cudaFree(ah);
+  cudaFree(al);
+  cudaFree(bh);
+  cudaFree(bl);
+  cudaFree(err);
+  return rc;
+}
 
 extern "C" int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd,
                                  int nsplit, int bn, int splits, float* dC, int* dev_err) {

@@ -104,7 +104,7 @@ struct Engine {
   R* rS = nullptr;              // residual in screen precision, K x n
   float* gscr = nullptr;        // screened X_i^T r, K x p
   uint8_t* cflag = nullptr;     // K x p: 1 = exact FP64 term (F1), 2 = free, unsettled by the screen
-  double* cpart = nullptr;      // [2][ceil(p/64)][K] screen partial sums
+  double* cpart = nullptr;      // [2][row tiles of the screen][K] screen partial sums
   int* flist = nullptr;         // K x p flagged index lists
 
   // branching / upper bound
@@ -147,6 +147,9 @@ struct Engine {
   __nv_bfloat16 *u_hi = nullptr, *u_lo = nullptr;     // U operand       (K x ldn)
   int* tc_err = nullptr;        // pipeline error word of the tensor-core kernels
   int tc_s1 = 1, tc_s1n = 1, tc_s2 = 1, tc_s2n = 1;
+  int tc_c1 = 0, tc_c2 = 0;     // cluster sizes of the cluster-reduced X W'^T / G^-1 T (0: split-K buffers)
+  float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2
+  int nbt = 0;                  // row tiles of the n x K products
 
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;

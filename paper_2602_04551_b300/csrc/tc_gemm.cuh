@@ -135,6 +135,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+
+// ---- thread-block clusters (split-K reduction through distributed shared memory)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster arrives (release) and waits (acquire)
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// 16 bytes at the same shared-memory offset in the CTA of rank `rank`
+__device__ __forceinline__ float4 ld_dsmem_f4(uint32_t local_addr, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local_addr), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(ra)
+               : "memory");
+  return v;
+}
+
 template <int BN, int NSPLIT>
 struct Geo {
   static constexpr int A_BYTES = BM * BK * 2;
@@ -149,6 +177,71 @@ struct Geo {
 struct Maps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
+
+// Operand ring of one CTA: stage s holds [A hi | B hi | A lo | B lo] (lo parts only for
+// the 3-term product).
+template <int BN, int NSPLIT>
+__device__ __forceinline__ uint8_t* ring_a(uint8_t* base, int s, int part) {
+  using G = Geo<BN, NSPLIT>;
+  return base + s * G::STAGE_BYTES + part * (G::A_BYTES + G::B_BYTES);
+}
+
+// TMA producer (one thread): nk K steps from kbeg, A rows m0.., B rows n0..
+template <int BN, int NSPLIT>
+__device__ __forceinline__ void tma_producer(const CUtensorMap* ma_hi, const CUtensorMap* ma_lo,
+                                             const CUtensorMap* mb_hi, const CUtensorMap* mb_lo,
+                                             uint8_t* base, uint64_t* full_bar, uint64_t* empty_bar,
+                                             int nk, int kbeg, int m0, int n0, int* err) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  for (int kb = 0; kb < nk; ++kb) {
+    const int s = kb % S;
+    if (kb >= S && !mbar_wait(&empty_bar[s], ((kb / S) & 1) ^ 1, err, 1)) break;
+    mbar_expect_tx(&full_bar[s], G::STAGE_BYTES);
+    const int k = kbeg + kb * BK;
+    uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+    tma_load_2d(a0, ma_hi, &full_bar[s], k, m0);
+    tma_load_2d(a0 + G::A_BYTES, mb_hi, &full_bar[s], k, n0);
+    if (NSPLIT == 3) {
+      uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+      tma_load_2d(a1, ma_lo, &full_bar[s], k, m0);
+      tma_load_2d(a1 + G::A_BYTES, mb_lo, &full_bar[s], k, n0);
+    }
+  }
+}
+
+// MMA issuer (one thread): accumulates the nk K steps into the 128 x BN tensor-memory
+// tile at `tmem`, frees each stage with a commit, and finally commits `done_bar`.
+template <int BN, int NSPLIT>
+__device__ __forceinline__ void mma_issuer(uint32_t tmem, uint8_t* base, uint64_t* full_bar,
+                                           uint64_t* empty_bar, uint64_t* done_bar, int nk,
+                                           int* err) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  constexpr uint32_t idesc = idesc_bf16(BN);
+  for (int kb = 0; kb < nk; ++kb) {
+    const int s = kb % S;
+    if (!mbar_wait(&full_bar[s], (kb / S) & 1, err, 2)) break;
+    fence_after();
+    uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+    uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+      const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+      const uint64_t ah = smem_desc_sw128(a0 + kk * 32);
+      const uint64_t bh = smem_desc_sw128(a0 + G::A_BYTES + kk * 32);
+      mma_bf16(tmem, ah, bh, idesc, acc);
+      if (NSPLIT == 3) {
+        const uint64_t al = smem_desc_sw128(a1 + kk * 32);
+        const uint64_t bl = smem_desc_sw128(a1 + G::A_BYTES + kk * 32);
+        mma_bf16(tmem, ah, bl, idesc, 1u);
+        mma_bf16(tmem, al, bh, idesc, 1u);
+      }
+    }
+    mma_commit(&empty_bar[s]);
+  }
+  mma_commit(done_bar);
+}
 
 // Epilogue interface:
 //   epi(row m, first column n0 + c, 16 accumulator values, M, N, lane quarter q, smem)
@@ -200,48 +293,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  auto sA = [&](int s, int part) { return base + s * G::STAGE_BYTES + part * (G::A_BYTES + G::B_BYTES); };
-  auto sB = [&](int s, int part) { return sA(s, part) + G::A_BYTES; };
-
   if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % S;
-      if (kb >= S && !mbar_wait(&empty_bar[s], ((kb / S) & 1) ^ 1, err, 1)) break;
-      mbar_expect_tx(&full_bar[s], G::STAGE_BYTES);
-      const int k = kbeg + kb * BK;
-      tma_load_2d(sA(s, 0), &ma_hi, &full_bar[s], k, m0);
-      tma_load_2d(sB(s, 0), &mb_hi, &full_bar[s], k, n0);
-      if (NSPLIT == 3) {
-        tma_load_2d(sA(s, 1), &ma_lo, &full_bar[s], k, m0);
-        tma_load_2d(sB(s, 1), &mb_lo, &full_bar[s], k, n0);
-      }
-    }
+    tma_producer<BN, NSPLIT>(&ma_hi, &ma_lo, &mb_hi, &mb_lo, base, full_bar, empty_bar, nk, kbeg,
+                             m0, n0, err);
   } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BN);
-    bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % S;
-      ok = mbar_wait(&full_bar[s], (kb / S) & 1, err, 2);
-      if (!ok) break;
-      fence_after();
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t ah = smem_desc_sw128(sA(s, 0) + kk * 32);
-        const uint64_t bh = smem_desc_sw128(sB(s, 0) + kk * 32);
-        mma_bf16(tmem, ah, bh, idesc, acc);
-        if (NSPLIT == 3) {
-          const uint64_t al = smem_desc_sw128(sA(s, 1) + kk * 32);
-          const uint64_t bl = smem_desc_sw128(sB(s, 1) + kk * 32);
-          mma_bf16(tmem, ah, bl, idesc, 1u);
-          mma_bf16(tmem, al, bh, idesc, 1u);
-        }
-      }
-      mma_commit(&empty_bar[s]);
-    }
-    mma_commit(&done_bar);
+    mma_issuer<BN, NSPLIT>(tmem, base, full_bar, empty_bar, &done_bar, nk, err);
   } else if (warp >= 2) {
     // ---------------- epilogue: warp w owns TMEM lanes [32 (w % 4), 32 (w % 4) + 32)
     const int q = warp & 3;
@@ -261,6 +317,134 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap ma_hi, const __grid_constant_
     asm volatile("bar.sync 1, %0;" ::"n"(32 * EPIW) : "memory");
     if (ok) epi.finish(threadIdx.x - 64, 32 * EPIW, m0, n0, M, N, epi_smem);
   }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+
+// Split-K with the reduction inside a thread-block cluster.  The CTAs of a cluster
+// (cluster dimension = gridDim.z) take consecutive K chunks of the same 128 x BN output
+// tile.  Each copies its tensor-memory accumulator into its own (now idle) operand ring
+// as a column-major 128 x BN FP32 tile; after a cluster barrier, CTA rank r sums the
+// column slice [r BN / S, (r + 1) BN / S) over the S partial tiles, read through
+// distributed shared memory in rank order (a fixed order: the result does not depend
+// on scheduling), and hands each 4-row group to the epilogue:
+//   epi.put4(m, n, {C[m..m+3][n]}, M, N, st)   accumulates Epi::NSTAT per-column sums
+//   epi.col(tile_m, n, st)                     the warp totals (when epi.stats), lane 0.
+// Every CTA of a cluster takes the same path (the early exit depends only on the tile),
+// and every thread reaches both cluster barriers, so the barriers always complete.
+template <int BN, int NSPLIT, class Epi>
+__global__ void __launch_bounds__(64 + 32 * 8, 1)
+tc_gemm_cred_kernel(const __grid_constant__ CUtensorMap ma_hi,
+                    const __grid_constant__ CUtensorMap ma_lo,
+                    const __grid_constant__ CUtensorMap mb_hi,
+                    const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred, int kchunk,
+                    const int* __restrict__ active, int* err, Epi epi) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  static_assert(S * G::STAGE_BYTES >= BN * BM * 4, "the partial tile reuses the operand ring");
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  if (active != nullptr) {
+    int any = 0;
+    for (int j = threadIdx.x; j < BN; j += blockDim.x)
+      if (n0 + j < N && active[n0 + j]) any = 1;
+    if (!__syncthreads_or(any)) return;     // the whole cluster shares this tile
+  }
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(Kred, kbeg + kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+  float* part = reinterpret_cast<float*>(base);   // [BN][BM] after the main loop
+
+  if (warp == 0 && lane == 0) {
+    tma_producer<BN, NSPLIT>(&ma_hi, &ma_lo, &mb_hi, &mb_lo, base, full_bar, empty_bar, nk, kbeg,
+                             m0, n0, err);
+  } else if (warp == 1 && lane == 0) {
+    mma_issuer<BN, NSPLIT>(tmem, base, full_bar, empty_bar, &done_bar, nk, err);
+  } else if (warp >= 2) {
+    // accumulator -> own partial tile (warp w: TMEM lanes 32 (w % 4) .., alternate chunks)
+    const int q = warp & 3, g = (warp - 2) >> 2;
+    const bool ok = mbar_wait(&done_bar, 0, err, 4);
+    fence_after();
+    const int row = 32 * q + lane;
+#pragma unroll 1
+    for (int c = 16 * g; c < BN; c += 32) {
+      float v[16];
+      if (ok && nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[(c + j) * BM + row] = v[j];
+    }
+  }
+  cluster_sync_all();
+  if (warp >= 2) {
+    const uint32_t rank = cluster_rank(), cs = cluster_size();
+    const int w = warp - 2;
+    const int per = (BN + (int)cs - 1) / (int)cs;
+    const int c0 = (int)rank * per, c1 = min(BN, c0 + per);
+    const uint32_t lbase = smem_u32(part);
+#pragma unroll 1
+    for (int c = c0 + w; c < c1; c += 8) {
+      const int n = n0 + c;
+      if (n >= N) break;                         // warp-uniform; later columns are out too
+      const uint32_t off = lbase + (uint32_t)(c * BM + 4 * lane) * 4u;
+      float4 a = ld_dsmem_f4(off, 0);
+      for (uint32_t r = 1; r < cs; ++r) {
+        const float4 b = ld_dsmem_f4(off, r);
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+      }
+      float st[Epi::NSTAT > 0 ? Epi::NSTAT : 1];
+#pragma unroll
+      for (int k = 0; k < (Epi::NSTAT > 0 ? Epi::NSTAT : 1); ++k) st[k] = 0.f;
+      epi.put4(m0 + 4 * lane, n, a, M, N, st);
+      if constexpr (Epi::NSTAT > 0) {
+        if (epi.stats) {
+#pragma unroll
+          for (int k = 0; k < Epi::NSTAT; ++k) st[k] = warp_sum(st[k]);
+          if (lane == 0) epi.col(blockIdx.x, n, st);
+        }
+      }
+    }
+  }
+  cluster_sync_all();                            // no CTA leaves while its tile is read
   fence_before();
   __syncthreads();
   if (warp == 1) {

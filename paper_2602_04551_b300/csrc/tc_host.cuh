@@ -66,6 +66,85 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
   return 0;
 }
 
+// Largest cluster size (<= want, a power of two) for which at least one cluster of the
+// cluster-reduce kernel fits on the device.
+template <int BN, int NSPLIT, class Epi>
+int tc_cred_max_cluster(int want) {
+  using G = tc::Geo<BN, NSPLIT>;
+  static int cached = -1;
+  if (cached < 0) {
+    auto kern = tc::tc_gemm_cred_kernel<BN, NSPLIT, Epi>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cached = 0;
+    for (int cs = 8; cs >= 1; cs >>= 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(1, 1, cs);
+      cfg.blockDim = dim3(64 + 32 * 8);
+      cfg.dynamicSmemBytes = G::SMEM;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = cs;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc > 0) {
+        cached = cs;
+        break;
+      }
+      cudaGetLastError();
+    }
+  }
+  return cached < want ? cached : want;
+}
+
+// C = A B^T over K split into `cluster` chunks reduced inside a cluster (see
+// tc_gemm_cred_kernel); `cluster` must not exceed tc_cred_max_cluster.
+template <int BN, int NSPLIT, class Epi>
+int tc_gemm_cred(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
+                 int cluster, const int* active, int* err, Epi epi) {
+  using G = tc::Geo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  if (cluster < 1 || cluster > 8) return BNB_EINVAL;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
+  if (NSPLIT == 3) {
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
+  } else {
+    al = ah;
+    bl = bh;
+  }
+  int ns = 1;
+  const int kchunk = tc_chunk(Kred, cluster, &ns);
+  auto kern = tc::tc_gemm_cred_kernel<BN, NSPLIT, Epi>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, ns);
+  cfg.blockDim = dim3(64 + 32 * 8);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = ns;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi));
+  return 0;
+}
+
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;

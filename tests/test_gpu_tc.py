@@ -40,7 +40,44 @@ def test_tc_gemm_matches_plain_product(M, N, Kd, nsplit, bn, splits):
     dC = torch.empty(N, M, dtype=torch.float32, device="cuda")   # M x N column-major
     err = bnb.bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit, bn, splits, dC)
     assert err == 0
-    C = dC.cpu().double().T.numpy()
+    _compare(A, B, dC.cpu().double().T.numpy(), nsplit)
+
+
+CLUSTER_CASES = [
+    # M, N, Kd, nsplit, cluster
+    (128, 256, 64, 1, 1),             # one CTA, one K step
+    (1000, 512, 5000, 3, 8),          # the X W'^T shape of a n=1000, p=5000, K=512 batch
+    (1000, 512, 1000, 3, 8),          # the G^-1 T shape (two K steps per CTA)
+    (300, 100, 1111, 3, 3),           # ragged M, N, K; cluster size not a power of two
+    (129, 300, 200, 1, 8),            # more CTAs asked for than K steps: 4 chunks
+    (257, 513, 777, 3, 2),
+]
+
+
+@pytest.mark.parametrize("M,N,Kd,nsplit,cluster", CLUSTER_CASES)
+def test_tc_gemm_cluster_matches_plain_product(M, N, Kd, nsplit, cluster):
+    g = torch.Generator(device="cpu").manual_seed(M * 5 + N * 11 + Kd + cluster)
+    A = torch.randn(M, Kd, generator=g, dtype=torch.float64)
+    B = torch.randn(N, Kd, generator=g, dtype=torch.float64)
+    dC = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
+    err = bnb.bnb_tc_gemm_check_cluster(A.cuda(), B.cuda(), M, N, Kd, nsplit, cluster, dC)
+    assert err == 0
+    _compare(A, B, dC.cpu().double().T.numpy(), nsplit)
+
+
+def test_tc_gemm_cluster_is_deterministic():
+    g = torch.Generator(device="cpu").manual_seed(3)
+    A = torch.randn(1000, 3000, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(512, 3000, generator=g, dtype=torch.float64).cuda()
+    outs = []
+    for _ in range(3):
+        dC = torch.empty(512, 1000, dtype=torch.float32, device="cuda")
+        assert bnb.bnb_tc_gemm_check_cluster(A, B, 1000, 512, 3000, 3, 8, dC) == 0
+        outs.append(dC.cpu())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def _compare(A, B, C, nsplit):
     if nsplit == 1:
         Ar = torch.from_numpy(_bf16(A.numpy()))
         Br = torch.from_numpy(_bf16(B.numpy()))
