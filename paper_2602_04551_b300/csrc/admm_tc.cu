@@ -300,7 +300,7 @@ struct TcEpiAdmm {
       for (int st = 0; st < 4; ++st) {
         const float a = sm[(0 * 4 + st) * BN + col] + sm[(1 * 4 + st) * BN + col] +
                         sm[(2 * 4 + st) * BN + col] + sm[(3 * 4 + st) * BN + col];
-        g3part[((long long)st * nbm + blockIdx.x) * K + n] = a;
+        g3part[((long long)st * nbm + m0 / tc::BM) * K + n] = a;
       }
     }
   }
@@ -309,8 +309,8 @@ struct TcEpiAdmm {
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
   constexpr int BN = 256;   // X W'^T, G^-1 T and X beta^T: wide tiles, split-K
-  constexpr int BN3 = 64;   // X^T U' + fused update: narrow tiles, two CTAs per SM so that
-                            // one CTA's epilogue overlaps the other's tensor-core work
+  constexpr int BN3 = 64;   // X^T U' + fused update: 128 x 64 tiles, persistent CTAs with a
+                            // double-buffered accumulator (epilogue overlaps the next tile)
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   const long long nK = (long long)n * K;
@@ -371,8 +371,8 @@ static int round_tc(Engine<float>& e, int iters) {
                       e.w_hi, NS == 3 ? e.w_lo : nullptr,
                       last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
                       e.P, p, e.ldp, e.nbm3, K, last ? 1 : 0};
-    if (int rc = tc_gemm<BN3, NS, TcEpiAdmm<BN3>, 4>(st, XC, Uop, p, K, n, 1, e.slot_active,
-                                                     e.tc_err, epi))
+    if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3>, 8>(st, XC, Uop, p, K, n, e.sms,
+                                                             e.slot_active, e.tc_err, epi))
       return rc;
     prof_end(e.prof, st, PK_GEMM_XTU);
   }
@@ -417,6 +417,12 @@ static int cred_max_cluster(int want) {
 
 int setup_tc(Engine<float>& e) {
   cudaStream_t st = e.st;
+  {
+    int dev = 0, sm = 0;
+    BNB_CUDA_OK(cudaGetDevice(&dev));
+    BNB_CUDA_OK(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+    e.sms = sm > 0 ? sm : 148;
+  }
   if (e.tc_c1 > 0) {
     const int c1 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c1) : cred_max_cluster<1>(e.tc_c1);
     const int c2 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c2) : cred_max_cluster<1>(e.tc_c2);

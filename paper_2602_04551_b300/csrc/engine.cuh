@@ -150,6 +150,7 @@ struct Engine {
   int tc_c1 = 0, tc_c2 = 0;     // cluster sizes of the cluster-reduced X W'^T / G^-1 T (0: split-K buffers)
   float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2
   int nbt = 0;                  // row tiles of the n x K products
+  int sms = 148;                // multiprocessors of the device (persistent grids)
 
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;

@@ -171,6 +171,9 @@ struct Geo {
   static constexpr int STAGES = (BN <= 64) ? (NSPLIT == 3 ? 2 : 4)          // ~100 KB: 2 CTAs per SM
                                             : (NSPLIT == 3) ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
+  // persistent variant (one CTA per SM): as many stages as fit in ~200 KB
+  static constexpr int PSTAGES = (200 * 1024) / STAGE_BYTES < 2 ? 2 : (200 * 1024) / STAGE_BYTES;
+  static constexpr int PSMEM = PSTAGES * STAGE_BYTES + 1024;
   static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
@@ -451,6 +454,190 @@ tc_gemm_cred_kernel(const __grid_constant__ CUtensorMap ma_hi,
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+
+// Persistent variant for the product whose epilogue is heavy (X^T U' with the fused
+// ADMM update): one CTA per SM walks the 128 x BN output tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (column-tile-major, so that CTAs working at the same
+// time share the B slice in L2).  The accumulator is double-buffered in tensor memory
+// (2 x BN columns): while the epilogue warps drain tile i from buffer i & 1, the MMA
+// issuer already accumulates tile i + 1 into the other buffer, and the TMA ring runs
+// continuously across tiles.  Hand-offs:
+//   tmem_full[b]   MMA -> epilogue  (tcgen05.commit after the tile's last K step)
+//   tmem_empty[b]  epilogue -> MMA  (one arrive per epilogue warp once it has read b)
+// Tiles whose columns are all inactive are skipped by every role alike.  The epilogue
+// interface is the one of tc_gemm_kernel (per 16-column chunk, then finish per tile).
+template <int BN, int NSPLIT, class Epi, int EPIW>
+__global__ void __maxnreg__(200)
+tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
+                       const __grid_constant__ CUtensorMap ma_lo,
+                       const __grid_constant__ CUtensorMap mb_hi,
+                       const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred,
+                       const int* __restrict__ active, int* err, Epi epi) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::PSTAGES;
+  constexpr int MAXNT = 64;                      // column tiles (N <= 64 BN)
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int tile_on[MAXNT];
+  __shared__ float epi_smem[Epi::SMEM_FLOATS > 0 ? Epi::SMEM_FLOATS : 1];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mtiles = (M + BM - 1) / BM, ntiles = (N + BN - 1) / BN;
+  const int ntot = mtiles * ntiles;
+  const int nk = (Kred + BK - 1) / BK;
+  for (int j = threadIdx.x; j < MAXNT; j += blockDim.x) {
+    int on = 0;
+    if (j < ntiles) {
+      for (int c = 0; c < BN && j * BN + c < N; ++c)
+        if (active == nullptr || active[j * BN + c]) {
+          on = 1;
+          break;
+        }
+    }
+    tile_on[j] = on;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], EPIW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(2 * G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: one continuous ring over all tiles of this CTA
+    long long g = 0;                             // K steps issued so far
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntot && ok; t += gridDim.x) {
+      const int mt = t % mtiles, nt = t / mtiles;
+      if (!tile_on[nt]) continue;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)(((g / S) & 1) ^ 1), err, 1)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], G::STAGE_BYTES);
+        const int k = kb * BK;
+        uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+        tma_load_2d(a0, &ma_hi, &full_bar[s], k, mt * BM);
+        tma_load_2d(a0 + G::A_BYTES, &mb_hi, &full_bar[s], k, nt * BN);
+        if (NSPLIT == 3) {
+          uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+          tma_load_2d(a1, &ma_lo, &full_bar[s], k, mt * BM);
+          tma_load_2d(a1 + G::A_BYTES, &mb_lo, &full_bar[s], k, nt * BN);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    long long g = 0;
+    int i = 0;                                   // tiles of this CTA so far
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntot && ok; t += gridDim.x) {
+      const int nt = t / mtiles;
+      if (!tile_on[nt]) continue;
+      const int b = i & 1;
+      if (i >= 2 && !mbar_wait(&tempty_bar[b], (uint32_t)(((i >> 1) & 1) ^ 1), err, 8)) break;
+      fence_after();
+      const uint32_t acc_addr = tmem + (uint32_t)(b * G::TMEM_COLS);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (!mbar_wait(&full_bar[s], (uint32_t)((g / S) & 1), err, 2)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+        uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ah = smem_desc_sw128(a0 + kk * 32);
+          const uint64_t bh = smem_desc_sw128(a0 + G::A_BYTES + kk * 32);
+          mma_bf16(acc_addr, ah, bh, idesc, acc);
+          if (NSPLIT == 3) {
+            const uint64_t al = smem_desc_sw128(a1 + kk * 32);
+            const uint64_t bl = smem_desc_sw128(a1 + G::A_BYTES + kk * 32);
+            mma_bf16(acc_addr, ah, bl, idesc, 1u);
+            mma_bf16(acc_addr, al, bh, idesc, 1u);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+      }
+      mma_commit(&tfull_bar[b]);
+      ++i;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps: warp w reads TMEM lanes 32 (w % 4) ..
+    const int q = warp & 3;
+    const int gq = (warp - 2) >> 2;             // which of the quarter's EPIW/4 warps
+    int i = 0;
+    for (int t = blockIdx.x; t < ntot; t += gridDim.x) {
+      const int mt = t % mtiles, nt = t / mtiles;
+      if (!tile_on[nt]) continue;
+      const int b = i & 1;
+      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4);
+      fence_after();
+      const int m0 = mt * BM, n0 = nt * BN;
+      const int row = m0 + 32 * q + lane;
+      if (ok) {
+#pragma unroll 1
+        for (int c = 16 * gq; c < BN; c += 16 * (EPIW / 4)) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::TMEM_COLS + c), v);
+          epi(row, n0 + c, v, M, N, q, epi_smem);
+        }
+      }
+      fence_before();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b]))
+                     : "memory");
+      // the epilogue warps meet (and agree whether every wait completed) before the
+      // per-tile finish, and again before the next tile reuses the shared scratch
+      uint32_t all_ok;
+      asm volatile(
+          "{\n .reg .pred p, r;\n setp.ne.u32 p, %1, 0;\n"
+          " bar.red.and.pred r, 1, %2, p;\n selp.u32 %0, 1, 0, r;\n}\n"
+          : "=r"(all_ok)
+          : "r"((uint32_t)ok), "n"(32 * EPIW)
+          : "memory");
+      if (all_ok) epi.finish(threadIdx.x - 64, 32 * EPIW, m0, n0, M, N, epi_smem);
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPIW) : "memory");
+      ++i;
+      if (!all_ok) break;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * G::TMEM_COLS)
                  : "memory");
   }
 }

@@ -145,6 +145,37 @@ int tc_gemm_cred(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M,
   return 0;
 }
 
+// Persistent launch of the heavy-epilogue product (see tc_gemm_persist_kernel): one CTA
+// per SM (at most one per tile).  N must not exceed 64 BN.
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
+int tc_gemm_persist(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N,
+                    int Kred, int sms, const int* active, int* err, Epi epi) {
+  using G = tc::Geo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  if (N > 64 * BN) return BNB_EINVAL;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
+  if (NSPLIT == 3) {
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
+  } else {
+    al = ah;
+    bl = bh;
+  }
+  auto kern = tc::tc_gemm_persist_kernel<BN, NSPLIT, Epi, EPIW>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::PSMEM));
+    attr_set = true;
+  }
+  const long long tiles = (long long)((M + tc::BM - 1) / tc::BM) * ((N + BN - 1) / BN);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  kern<<<grid, 64 + 32 * EPIW, G::PSMEM, st>>>(ah, al, bh, bl, M, N, Kred, active, err, epi);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;
