@@ -202,7 +202,7 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16]) {
   return x + __shfl_xor_sync(0xffffffffu, x, 1);
 }
 
-template <int BN>
+template <int BN, bool STATS>
 struct TcEpiAdmm {
   static constexpr int SMEM_FLOATS = 4 * 4 * BN;   // [warp][stat][column]
   const float* __restrict__ bc;     // b_c = D c
@@ -217,7 +217,8 @@ struct TcEpiAdmm {
   Prob P;
   long long p, ldp;
   int nbm, K;
-  int stats;                    // 1 on the round's last iteration: per-slot stop-test sums
+  // STATS (the round's last iteration): per-slot stop-test sums and the beta operand of
+  // the check product; a separate instantiation so the other iterations stay lean
 
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
@@ -236,7 +237,7 @@ struct TcEpiAdmm {
       vv[j] = ok[j] ? V[o] : 0.f;
       ff[j] = ok[j] ? (int)fix[o] : 0;
     }
-    if (!stats) {
+    if constexpr (!STATS) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         if (ok[j]) {
@@ -253,7 +254,7 @@ struct TcEpiAdmm {
         }
       }
       return;
-    }
+    } else {
     float s_psi[16], s_nu[16], s_db[16], s_pr[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -288,11 +289,12 @@ struct TcEpiAdmm {
       sm[(q * 4 + 2) * BN + col] = t2;
       sm[(q * 4 + 3) * BN + col] = t3;
     }
+    }
   }
 
   __device__ __forceinline__ void finish(int t, int nthr, int m0, int n0, int M, int N,
                                          float* sm) const {
-    if (!stats) return;
+    if constexpr (!STATS) return;
     for (int col = t; col < BN; col += nthr) {
       const int n = n0 + col;
       if (n >= N) continue;
@@ -367,13 +369,21 @@ static int round_tc(Engine<float>& e, int iters) {
       prof_end(e.prof, st, PK_FINAL_U);
     }
     prof_begin(e.prof, st);
-    TcEpiAdmm<BN3> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
-                      e.w_hi, NS == 3 ? e.w_lo : nullptr,
-                      last ? e.b_hi : nullptr, (last && NS == 3) ? e.b_lo : nullptr,
-                      e.P, p, e.ldp, e.nbm3, K, last ? 1 : 0};
-    if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3>, 8>(st, XC, Uop, p, K, n, e.sms,
-                                                             e.slot_active, e.tc_err, epi))
-      return rc;
+    if (last) {
+      TcEpiAdmm<BN3, true> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active,
+                               (float*)e.g3part, e.w_hi, NS == 3 ? e.w_lo : nullptr, e.b_hi,
+                               NS == 3 ? e.b_lo : nullptr, e.P, p, e.ldp, e.nbm3, K};
+      if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, true>, 8>(
+              st, XC, Uop, p, K, n, e.sms, e.slot_active, e.tc_err, epi))
+        return rc;
+    } else {
+      TcEpiAdmm<BN3, false> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active,
+                                (float*)e.g3part, e.w_hi, NS == 3 ? e.w_lo : nullptr, nullptr,
+                                nullptr, e.P, p, e.ldp, e.nbm3, K};
+      if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, false>, 8>(
+              st, XC, Uop, p, K, n, e.sms, e.slot_active, e.tc_err, epi))
+        return rc;
+    }
     prof_end(e.prof, st, PK_GEMM_XTU);
   }
   // check product X beta^T

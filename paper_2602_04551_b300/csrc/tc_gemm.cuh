@@ -471,7 +471,7 @@ tc_gemm_cred_kernel(const __grid_constant__ CUtensorMap ma_hi,
 // Tiles whose columns are all inactive are skipped by every role alike.  The epilogue
 // interface is the one of tc_gemm_kernel (per 16-column chunk, then finish per tile).
 template <int BN, int NSPLIT, class Epi, int EPIW>
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(64 + 32 * EPIW, 1)
 tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
                        const __grid_constant__ CUtensorMap ma_lo,
                        const __grid_constant__ CUtensorMap mb_hi,
