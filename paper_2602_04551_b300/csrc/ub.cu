@@ -52,7 +52,7 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
                                  int* __restrict__ sup_cnt, int* __restrict__ nfree,
                                  float* __restrict__ zbuf) {
   __shared__ unsigned long long shk[32];
-  __shared__ int wcnt[8];
+  __shared__ int wcnt[32];
   __shared__ int base;
   __shared__ double shd[32];
   const int q = blockIdx.x;
@@ -130,7 +130,9 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
   const int* S = sup + (long long)q * smax;
   R* Q = Qg + (long long)q * smax * smax;
   const int npair = s * (s + 1) / 2;
-  for (int t = threadIdx.x; t < npair + s; t += blockDim.x) {
+  // one warp per entry: lanes stride over the n samples, fixed-order butterfly sum
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = w; t < npair + s; t += nw) {
     if (t < npair) {
       // unrank t -> (a, b), a >= b
       int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -140,16 +142,20 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
       const R* xa = XR + (long long)S[a] * n;
       const R* xb = XR + (long long)S[b] * n;
       R d = 0;
-      for (int k = 0; k < n; ++k) d = fma(xa[k], xb[k], d);
-      if (a == b) d += (R)(2.0 * lam2);
-      Q[a * s + b] = d;
-      Q[b * s + a] = d;
+      for (int k = lane; k < n; k += 32) d = fma(xa[k], xb[k], d);
+      d = warp_sum(d);
+      if (lane == 0) {
+        if (a == b) d += (R)(2.0 * lam2);
+        Q[a * s + b] = d;
+        Q[b * s + a] = d;
+      }
     } else {
       const int a = t - npair;
       const R* xa = XR + (long long)S[a] * n;
       R d = 0;
-      for (int k = 0; k < n; ++k) d = fma(xa[k], yR[k], d);
-      qv[(long long)q * smax + a] = d;
+      for (int k = lane; k < n; k += 32) d = fma(xa[k], yR[k], d);
+      d = warp_sum(d);
+      if (lane == 0) qv[(long long)q * smax + a] = d;
     }
   }
 }
@@ -528,7 +534,7 @@ __global__ void k_sup_from_mask(const uint8_t* __restrict__ mask, int p, int sma
 
 template <class R>
 int branch_support(Engine<R>& e, bool write_z) {
-  k_branch_support<R><<<e.K, 256, 0, e.st>>>(e.beta, e.fix, e.gscr, e.p, e.P, e.ret_slot,
+  k_branch_support<R><<<e.K, 1024, 0, e.st>>>(e.beta, e.fix, e.gscr, e.p, e.P, e.ret_slot,
                                              e.ret_count, e.smax, e.br_idx, e.sup, e.sup_cnt,
                                              e.nfree, write_z ? e.zbuf : nullptr);
   BNB_CUDA_OK(cudaGetLastError());
