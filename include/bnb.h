@@ -51,6 +51,8 @@ extern "C" {
 #define BNB_STATUS_TIME_LIMIT 2
 #define BNB_STATUS_QUEUE_FULL 3
 #define BNB_STATUS_NODE_LIMIT 4
+#define BNB_STATUS_DEPTH_LIMIT 5  /* a node deeper than options.max_depth was needed; its
+                                     bound stays in LB, so LB remains valid */
 
 typedef struct bnb_handle bnb_handle;
 
@@ -76,6 +78,8 @@ typedef struct {
                             beta in the beta- and v-updates.  Bounds are valid for any alpha. */
   int root_heuristic;    /* 1 (default): seed the incumbent with the matching-pursuit
                             heuristic (Appendix A.2) polished exactly in FP64 */
+  int max_depth;         /* deepest node kept (fixings stored per open node), default 256,
+                            in [8, 4096]; the pool takes queue_capacity x max_depth x 4 bytes */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libbnb.so")
 BNB_OK = 0
 BNB_EINVAL, BNB_ENOMEM, BNB_ECUDA, BNB_ETIMEOUT, BNB_EQUEUE, BNB_ENODEV = -1, -2, -3, -4, -5, -6
 BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16, BNB_PREC_TC3 = 0, 1, 2, 3
-STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit"}
+STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit",
+                5: "depth_limit"}
 
 # exported symbols (kept in step with include/bnb.h)
 SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
@@ -44,7 +45,7 @@ class bnb_options(ctypes.Structure):
                 ("warm_capacity", ctypes.c_longlong), ("support_max", ctypes.c_int),
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
-                ("root_heuristic", ctypes.c_int)]
+                ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):

@@ -171,7 +171,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.slot_iters, K);
   ALLOC(e.slot_depth, K);
   ALLOC(e.slot_nfix, K);
-  ALLOC(e.slot_fixl, K * DMAX);
+  ALLOC(e.slot_fixl, K * e.dmax);
   ALLOC(e.slot_lbp, K);
   ALLOC(e.slot_gap, K);
   ALLOC(e.slot_dual, K);
@@ -210,7 +210,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.pool_valid, e.qcap);
   ALLOC(e.pool_depth, e.qcap);
   ALLOC(e.pool_warm, e.qcap);
-  ALLOC(e.pool_fix, e.qcap * DMAX);
+  ALLOC(e.pool_fix, e.qcap * e.dmax);
   ALLOC(e.free_stack, e.qcap);
   ALLOC(e.free_top, 1);
   ALLOC(e.pool_hw, 1);
@@ -382,6 +382,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->stream = nullptr;
   o->relax_alpha = 1.0;
   o->root_heuristic = 1;
+  o->max_depth = 256;
   return BNB_OK;
 }
 
@@ -392,6 +393,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->n = h->n;
   e->p = h->p;
   e->K = o.batch_K;
+  e->dmax = o.max_depth;
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
   e->qcap = o.queue_capacity;
@@ -466,6 +468,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.batch_K < 1 || o.batch_K > 65536) return fail(BNB_EINVAL, "batch_K out of range");
   if (o.support_max < 1 || o.support_max > 256) return fail(BNB_EINVAL, "support_max must be in [1, 256]");
   if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
+  if (o.max_depth < 8 || o.max_depth > 4096) return fail(BNB_EINVAL, "max_depth must be in [8, 4096]");
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
@@ -514,6 +517,7 @@ static size_t footprint_of(int n, int p, const bnb_options& o) {
   e.p = p;
   e.K = o.batch_K;
   e.smax = o.support_max;
+  e.dmax = o.max_depth;
   e.qcap = o.queue_capacity;
   long long wdef = (4LL << 30) / (2LL * p * (long long)sizeof(R));
   if (wdef > e.qcap / 2) wdef = e.qcap / 2;
@@ -891,7 +895,8 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
   if (!S.done) {
     if (s.active_slots == 0 && s.pool_count == 0) {
       S.done = true;
-      S.status = s.error ? BNB_STATUS_QUEUE_FULL : BNB_STATUS_OPTIMAL;
+      S.status = (s.error & 2) ? BNB_STATUS_QUEUE_FULL
+                 : (s.error & 1) ? BNB_STATUS_DEPTH_LIMIT : BNB_STATUS_OPTIMAL;
       if (s.error && std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub))
         S.status = BNB_STATUS_GAP;
     } else if (std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub)) {

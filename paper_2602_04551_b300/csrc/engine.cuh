@@ -15,7 +15,6 @@
 
 namespace bnb {
 
-constexpr int DMAX = 128;       // deepest node (fixings kept per open node)
 constexpr int SEL_BINS = 2048;  // radix-select histogram width
 
 struct Status {                 // copied to the host after every round
@@ -93,7 +92,8 @@ struct Engine {
 
   // slots
   int *slot_active = nullptr, *slot_iters = nullptr, *slot_depth = nullptr, *slot_nfix = nullptr;
-  int* slot_fixl = nullptr;     // K x DMAX encoded fixings (idx << 1 | dir)
+  int dmax = 256;               // deepest node (fixings kept per open node)
+  int* slot_fixl = nullptr;     // K x dmax encoded fixings (idx << 1 | dir)
   double *slot_lbp = nullptr, *slot_gap = nullptr, *slot_dual = nullptr, *slot_primal = nullptr;
   int* slot_retire = nullptr;
   int *ret_slot = nullptr, *ret_active = nullptr, *ret_count = nullptr;

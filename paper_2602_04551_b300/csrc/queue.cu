@@ -59,7 +59,7 @@ __global__ void k_queue_init(long long qcap, long long wcap, int* free_stack, in
 
 // Prune or branch each retired node (one block per retired node).
 template <class R>
-__global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+__global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
                        const double* __restrict__ node_lb, const int* __restrict__ br_idx,
                        const double* __restrict__ inc_ub, const double* __restrict__ params,
                        const int* __restrict__ slot_depth, const int* __restrict__ slot_fixl,
@@ -80,7 +80,7 @@ __global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __res
     decision = 0;
     if (lbu >= thr || j < 0) {
       atomicAdd(&sel_state[SS_PRUNED], 1);
-    } else if (d + 1 > DMAX) {
+    } else if (d + 1 > dmax) {
       atomicOr(&sel_state[SS_ERROR], 1);
       atomicMin(lost_key, dkey(lbu));
     } else {
@@ -122,13 +122,13 @@ __global__ void k_push(int p, const int* __restrict__ ret_slot, const int* __res
   __syncthreads();
   if (!decision) return;
   for (int t = threadIdx.x; t < d; t += blockDim.x) {
-    const int e = slot_fixl[(long long)slot * DMAX + t];
-    pool_fix[(long long)c0 * DMAX + t] = e;
-    pool_fix[(long long)c1 * DMAX + t] = e;
+    const int e = slot_fixl[(long long)slot * dmax + t];
+    pool_fix[(long long)c0 * dmax + t] = e;
+    pool_fix[(long long)c1 * dmax + t] = e;
   }
   if (threadIdx.x == 0) {
-    pool_fix[(long long)c0 * DMAX + d] = (j << 1) | 0;
-    pool_fix[(long long)c1 * DMAX + d] = (j << 1) | 1;
+    pool_fix[(long long)c0 * dmax + d] = (j << 1) | 0;
+    pool_fix[(long long)c1 * dmax + d] = (j << 1) | 1;
   }
   if (wslot >= 0) {
     const long long so = (long long)slot * p, wo = (long long)wslot * p;
@@ -333,7 +333,7 @@ __global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_val
 
 // load popped nodes into free slots (one block per popped node)
 template <class R>
-__global__ void k_refill(int p, const int* __restrict__ sel_state, const int* __restrict__ popped,
+__global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, const int* __restrict__ popped,
                          const int* __restrict__ free_slots, const double* __restrict__ pool_lb,
                          const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
                          const int* __restrict__ pool_fix, const R* __restrict__ warm_beta,
@@ -355,8 +355,8 @@ __global__ void k_refill(int p, const int* __restrict__ sel_state, const int* __
   }
   __syncthreads();
   for (int u = threadIdx.x; u < d; u += blockDim.x) {
-    const int e = pool_fix[(long long)idx * DMAX + u];
-    slot_fixl[(long long)slot * DMAX + u] = e;
+    const int e = pool_fix[(long long)idx * dmax + u];
+    slot_fixl[(long long)slot * dmax + u] = e;
     fix[so + (e >> 1)] = (int8_t)(e & 1);
     if ((e & 1) == 0) beta[so + (e >> 1)] = R(0);  // the new F0 coordinate starts at zero
   }
@@ -448,7 +448,7 @@ int queue_init(Engine<R>& e) {
 
 template <class R>
 int queue_push(Engine<R>& e) {
-  k_push<R><<<e.K, 256, 0, e.st>>>(e.p, e.ret_slot, e.ret_count, e.node_lb, e.br_idx, e.inc_ub,
+  k_push<R><<<e.K, 256, 0, e.st>>>(e.p, e.dmax, e.ret_slot, e.ret_count, e.node_lb, e.br_idx, e.inc_ub,
                                    e.params_d, e.slot_depth, e.slot_fixl, e.beta, e.V,
                                    e.free_stack, e.free_top, e.pool_hw, e.pool_valid, e.pool_lb,
                                    e.pool_key, e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
@@ -473,7 +473,7 @@ int queue_select_refill(Engine<R>& e) {
   k_sel_scan<<<1, 1024, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
   k_sel_collect<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_key, e.free_stack, e.free_top,
                                    e.sel_state, e.popped);
-  k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.sel_state, e.popped, e.free_slots, e.pool_lb,
+  k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb,
                                    e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta, e.warm_V,
                                    e.warm_ref, e.warm_stack, e.warm_top, e.fix, e.beta, e.V,
                                    e.slot_active, e.slot_iters, e.slot_lbp, e.slot_depth,
