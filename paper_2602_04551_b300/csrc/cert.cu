@@ -232,7 +232,10 @@ __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X
 }
 
 // sum over the flagged coordinates with cflag == code of nu_i(|X_i^T r|), exact FP64,
-// in a fixed order (per warp: increasing index; warps combined in order)
+// in a fixed order: p is taken in chunks of blockDim coordinates; each chunk's flagged
+// coordinates are listed in increasing index (ballot compaction), warp w takes list
+// entries w, w + nw, ... (one FP64 dot product per warp, lanes over the n samples);
+// per-warp sums are combined in warp order at the end.
 __device__ double exact_terms(const double* __restrict__ X64, const double* __restrict__ r,
                               const int8_t* __restrict__ fixrow, const uint8_t* __restrict__ flags,
                               int n, int p, const Prob& P, int code, int* list, int* wcnt, int* cnt,
@@ -254,12 +257,18 @@ __device__ double exact_terms(const double* __restrict__ X64, const double* __re
       *cnt = tot;
     }
     __syncthreads();
-    for (int t = w; t < *cnt; t += nw) {
+    const int c_n = *cnt;
+    for (int t = w; t < c_n; t += nw) {
       const int c = list[t];
       const double* x = X64 + (long long)c * n;
-      double d = 0.0;
-      for (int k = lane; k < n; k += 32) d = fma(x[k], r[k], d);
-      d = warp_sum(d);
+      double d0 = 0.0, d1 = 0.0;            // two chains: more loads in flight
+      int k = lane;
+      for (; k + 32 < n; k += 64) {
+        d0 = fma(x[k], r[k], d0);
+        d1 = fma(x[k + 32], r[k + 32], d1);
+      }
+      if (k < n) d0 = fma(x[k], r[k], d0);
+      const double d = warp_sum(d0 + d1);
       nu_w += nu_coord<double>(fabs(d), fixrow[c], P);
     }
     __syncthreads();
@@ -278,7 +287,8 @@ __device__ double exact_terms(const double* __restrict__ X64, const double* __re
 // given and LB_cheap already reaches it, or even LB_cheap plus the total interval
 // width cannot reach it, the exact FP64 terms cannot change the decision and
 // LB_cheap (a valid bound) is kept; otherwise they are computed exactly.
-__global__ void k_cert_exact(const double* __restrict__ X64, const double* __restrict__ r64,
+__global__ void __launch_bounds__(1024) k_cert_exact(const double* __restrict__ X64,
+                                                    const double* __restrict__ r64,
                              const int8_t* __restrict__ fix, const uint8_t* __restrict__ cflag,
                              const double* __restrict__ cpart, int nbm, int K, int n, int p,
                              Prob P, const int* __restrict__ ret_slot,
@@ -287,10 +297,10 @@ __global__ void k_cert_exact(const double* __restrict__ X64, const double* __res
                              const double* __restrict__ inc_ub, const double* __restrict__ params,
                              int use_threshold, double* __restrict__ cert_lb,
                              double* __restrict__ node_lb) {
-  __shared__ int list[256];
-  __shared__ int wcnt[8];
+  __shared__ int list[1024];
+  __shared__ int wcnt[32];
   __shared__ int cnt;
-  __shared__ double wacc[8];
+  __shared__ double wacc[32];
   __shared__ double shd[32];
   const int q = blockIdx.x;
   if (q >= *ret_count) return;
@@ -349,7 +359,7 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
   }
   prof_end(e.prof, st, PK_CERT_SCREEN);
   prof_begin(e.prof, st);
-  k_cert_exact<<<K, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,
+  k_cert_exact<<<K, 1024, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,
                                   e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr, e.slot_lbp,
                                   e.inc_ub, e.params_d, use_threshold ? 1 : 0, e.cert_lb, e.node_lb);
   prof_end(e.prof, st, PK_CERT_EXACT);

@@ -156,10 +156,11 @@ __device__ __forceinline__ float4 ld_dsmem_f4(uint32_t local_addr, uint32_t rank
   uint32_t ra;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local_addr), "r"(rank));
   float4 v;
+  // volatile keeps the loads after the cluster barrier; no memory clobber, so that
+  // consecutive loads are not serialised by the compiler
   asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(ra)
-               : "memory");
+               : "r"(ra));
   return v;
 }
 
@@ -426,14 +427,21 @@ tc_gemm_cred_kernel(const __grid_constant__ CUtensorMap ma_hi,
       const int n = n0 + c;
       if (n >= N) break;                         // warp-uniform; later columns are out too
       const uint32_t off = lbase + (uint32_t)(c * BM + 4 * lane) * 4u;
-      float4 a = ld_dsmem_f4(off, 0);
-      for (uint32_t r = 1; r < cs; ++r) {
-        const float4 b = ld_dsmem_f4(off, r);
-        a.x += b.x;
-        a.y += b.y;
-        a.z += b.z;
-        a.w += b.w;
-      }
+      // issue every rank's load before the first add (independent remote loads in
+      // flight together), then add in rank order
+      float4 pr[8];
+#pragma unroll
+      for (uint32_t r = 0; r < 8; ++r)
+        if (r < cs) pr[r] = ld_dsmem_f4(off, r);
+      float4 a = pr[0];
+#pragma unroll
+      for (uint32_t r = 1; r < 8; ++r)
+        if (r < cs) {
+          a.x += pr[r].x;
+          a.y += pr[r].y;
+          a.z += pr[r].z;
+          a.w += pr[r].w;
+        }
       float st[Epi::NSTAT > 0 ? Epi::NSTAT : 1];
 #pragma unroll
       for (int k = 0; k < (Epi::NSTAT > 0 ? Epi::NSTAT : 1); ++k) st[k] = 0.f;
