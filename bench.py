@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--arrival-rate", type=float, default=20.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--fp64-compare", action="store_true",
+                    help="solves mode: also solve each instance with the plain FP64 path")
+    ap.add_argument("--fp64-time-limit", type=float, default=60.0)
+    ap.add_argument("--seeds", type=int, default=1, help="solves mode: instances per lambda0")
+    ap.add_argument("--max-depth", type=int, default=1024)
     ap.add_argument("--lam0-frac", type=float, default=0.02)
     ap.add_argument("--K", type=int, default=512)
     ap.add_argument("--check-every", type=int, default=10)
@@ -428,38 +433,65 @@ def run_solves(args):
     from paper_2602_04551_b300 import autotune
     out = []
     t_all = time.perf_counter()
-    for frac in [float(f) for f in args.lam0_fracs.split(",")]:
-        inst, lam0, lam2, M, cfg = workload(args.workload, 0, frac)
+    jobs = [(float(f), sd) for f in args.lam0_fracs.split(",") for sd in range(args.seeds)]
+    for frac, seed in jobs:
+        inst, lam0, lam2, M, cfg = workload(args.workload, seed, frac)
         best, _ = autotune.autotune(inst.X, inst.y, lam0, lam2, M, use_cache=False,
                                     grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
                                           "check_every": [args.check_every]})
         o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                     precision=PREC[args.precision], rho=best["rho"],
-                                    relax_alpha=best["relax_alpha"], queue_capacity=1 << 22,
-                                    time_limit_s=args.solve_time_limit)
+                                    relax_alpha=best["relax_alpha"], queue_capacity=1 << 21,
+                                    max_depth=args.max_depth, time_limit_s=args.solve_time_limit)
         with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             res = bnb.bnb_solve(h, 1e-4)
             dt = time.perf_counter() - t0
             st = bnb.bnb_get_stats(h)
-        out.append({"lambda0_frac": frac, "lambda0": lam0, "seconds": dt, "status": res["status"],
-                    "nodes": res["nodes"], "nnz": int(np.count_nonzero(res["beta"])),
-                    "ub": res["ub"], "lb": res["lb"], "gap": (res["ub"] - res["lb"]) / res["ub"],
-                    "nodes_per_s": res["nodes"] / dt, "rho": best["rho"],
-                    "relax_alpha": best["relax_alpha"], "max_depth": st["max_depth"]})
+            dh, sh = bnb.bnb_get_histograms(h, args.max_depth + 1, 202)
+        rec = {"lambda0_frac": frac, "seed": seed, "lambda0": lam0, "seconds": dt,
+               "status": res["status"], "nodes": res["nodes"],
+               "nnz": int(np.count_nonzero(res["beta"])), "ub": res["ub"], "lb": res["lb"],
+               "gap": (res["ub"] - res["lb"]) / res["ub"], "nodes_per_s": res["nodes"] / dt,
+               "rho": best["rho"], "relax_alpha": best["relax_alpha"], "max_depth": st["max_depth"],
+               # solved nodes by depth 0..40 (+ deeper) and by rounded-support size 0..200 (+ larger)
+               "depth_hist": [int(x) for x in dh[:41]] + [int(dh[41:].sum())],
+               "support_hist": [int(x) for x in sh[:201]] + [int(sh[201:].sum())]}
+        if args.fp64_compare:
+            o64 = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+                                          precision=0, rho=best["rho"],
+                                          relax_alpha=best["relax_alpha"], queue_capacity=1 << 21,
+                                          max_depth=args.max_depth,
+                                          time_limit_s=args.fp64_time_limit)
+            with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o64) as h:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r64 = bnb.bnb_solve(h, 1e-4)
+                d64 = time.perf_counter() - t0
+            rec["fp64"] = {"seconds": d64, "status": r64["status"], "nodes": r64["nodes"],
+                           "ub": r64["ub"], "lb": r64["lb"], "nodes_per_s": r64["nodes"] / d64,
+                           "same_support": bool(np.array_equal(np.nonzero(r64["beta"])[0],
+                                                               np.nonzero(res["beta"])[0]))}
+        out.append(rec)
         print(json.dumps({"solve": out[-1]}), file=sys.stderr, flush=True)
     done = [r for r in out if r["status"] in ("optimal", "gap")]
     total = time.perf_counter() - t_all
+    fp64 = None
+    if args.fp64_compare:
+        d64 = [r for r in out if r["fp64"]["status"] in ("optimal", "gap")]
+        fp64 = {"solves_per_s": len(d64) / sum(r["fp64"]["seconds"] for r in out),
+                "time_limit_s": args.fp64_time_limit,
+                "note": "same instances, autotuned rho and K, precision FP64 everywhere"}
     lat = np.array([r["seconds"] for r in done]) if done else np.array([np.nan])
     line = {"metric": "certified solves/s (gap 1e-4)", "mode": "solves",
             "value": len(done) / sum(r["seconds"] for r in out), "unit": "solves/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE[args.precision],
             "data": "synthetic", "config": {"workload": args.workload, "K": args.K,
-                                            "lambda0_fracs": args.lam0_fracs,
+                                            "lambda0_fracs": args.lam0_fracs, "seeds": args.seeds,
                                             "time_limit_s": args.solve_time_limit},
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "wall_s": total, "solves": out}
+            "wall_s": total, "fp64_path": fp64, "solves": out}
     print(json.dumps(line), flush=True)
 
 

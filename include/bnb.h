@@ -284,6 +284,16 @@ typedef struct {
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);
 
+/* Histograms of the nodes solved since the last bnb_solve / bnb_solve_start (host
+ * arrays, caller-owned): depth_hist[d] = nodes solved at depth d (the bin at index
+ * max_depth also counts anything deeper), support_hist[s] = nodes whose rounded support
+ * S = F1 + {free i : z_i >= 1/2} (the upper-bound candidate, Section 3.3) has s
+ * elements (the bin at support_max + 1 counts larger supports).  Bins beyond those are
+ * written as 0.  Synchronises the handle's stream.  Measurement aid for the tree-shape
+ * reports; the paper has no counterpart call. */
+int bnb_get_histograms(bnb_handle* h, long long* depth_hist, int ndepth, long long* support_hist,
+                       int nsupport);
+
 /* Message of the last failed call on h (or of the last failed create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char* bnb_last_error(const bnb_handle* h);

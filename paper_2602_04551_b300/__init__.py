@@ -29,7 +29,7 @@ SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_dev
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
            "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_dual_bound_static",
-           "bnb_get_stats",
+           "bnb_get_stats", "bnb_get_histograms",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status",
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
         "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
+        "bnb_get_histograms": ([P, P, I, P, I], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
@@ -297,6 +298,14 @@ def bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit=1, bn=128, splits=1, dC=None):
     _check(load_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
                                             _ptr(dC), ctypes.byref(err)))
     return err.value
+
+
+def bnb_get_histograms(h: Handle, ndepth: int = 257, nsupport: int = 258):
+    """Solved-node histograms: (depth counts, rounded-support-size counts)."""
+    d = np.zeros(ndepth, np.int64)
+    s = np.zeros(nsupport, np.int64)
+    _check(load_library().bnb_get_histograms(h.ptr, _ptr(d), ndepth, _ptr(s), nsupport), h.ptr)
+    return d, s
 
 
 def bnb_tc_gemm_check_cluster(dA, dB, M, N, Kd, nsplit=3, cluster=8, dC=None):

@@ -211,6 +211,8 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.pool_depth, e.qcap);
   ALLOC(e.pool_warm, e.qcap);
   ALLOC(e.pool_fix, e.qcap * e.dmax);
+  ALLOC(e.hist_depth, e.dmax + 1);
+  ALLOC(e.hist_sup, e.smax + 2);
   ALLOC(e.free_stack, e.qcap);
   ALLOC(e.free_top, 1);
   ALLOC(e.pool_hw, 1);
@@ -1029,6 +1031,30 @@ extern "C" int bnb_root_heuristic(bnb_handle* h, double* beta_out, double* ub_ou
 extern "C" void* bnb_stream(const bnb_handle* h) {
   if (!h) return nullptr;
   return h->ef ? (void*)h->ef->st : (h->ed ? (void*)h->ed->st : nullptr);
+}
+
+template <class R>
+static int read_histograms(Engine<R>& e, long long* depth_hist, int ndepth,
+                           long long* support_hist, int nsupport) {
+  std::vector<int> d(e.dmax + 1), s(e.smax + 2);
+  BNB_CUDA_OK(cudaMemcpyAsync(d.data(), e.hist_depth, sizeof(int) * d.size(),
+                              cudaMemcpyDeviceToHost, e.st));
+  BNB_CUDA_OK(cudaMemcpyAsync(s.data(), e.hist_sup, sizeof(int) * s.size(),
+                              cudaMemcpyDeviceToHost, e.st));
+  BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  for (int i = 0; i < ndepth; ++i) depth_hist[i] = i < (int)d.size() ? d[i] : 0;
+  for (int i = 0; i < nsupport; ++i) support_hist[i] = i < (int)s.size() ? s[i] : 0;
+  return BNB_OK;
+}
+
+extern "C" int bnb_get_histograms(bnb_handle* h, long long* depth_hist, int ndepth,
+                                  long long* support_hist, int nsupport) {
+  if (!h || (!depth_hist && ndepth > 0) || (!support_hist && nsupport > 0) || ndepth < 0 ||
+      nsupport < 0)
+    return fail(BNB_EINVAL, "bad histogram arguments");
+  int rc = h->ef ? read_histograms(*h->ef, depth_hist, ndepth, support_hist, nsupport)
+                 : read_histograms(*h->ed, depth_hist, ndepth, support_hist, nsupport);
+  return set_err(h, rc);
 }
 
 extern "C" int bnb_get_stats(const bnb_handle* h, bnb_stats* out) {

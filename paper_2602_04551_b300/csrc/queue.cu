@@ -67,7 +67,9 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
                        int* free_top, int* pool_hw, uint8_t* pool_valid, double* pool_lb,
                        unsigned* pool_key, int* pool_depth, int* pool_warm, int* pool_fix,
                        R* warm_beta, R* warm_V, int* warm_ref, int* warm_stack, int* warm_top,
-                       int* sel_state, unsigned long long* poolmin, unsigned long long* lost_key) {
+                       int* sel_state, unsigned long long* poolmin, unsigned long long* lost_key,
+                       const int* __restrict__ sup_cnt, int smax, int* hist_depth,
+                       int* hist_sup) {
   __shared__ int c0, c1, wslot, decision;
   const int q = blockIdx.x;
   if (q >= *ret_count) return;
@@ -76,6 +78,10 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
   const double lbu = node_lb[q];
   const int j = br_idx[q];
   if (threadIdx.x == 0) {
+    // solved-node histograms: depth, and size of the rounded support (smax + 1: larger)
+    atomicAdd(&hist_depth[d < dmax ? d : dmax], 1);
+    const int sc = sup_cnt[q];
+    atomicAdd(&hist_sup[(sc < 0 || sc > smax) ? smax + 1 : sc], 1);
     const double thr = inc_ub[0] * (1.0 - params[0]);
     decision = 0;
     if (lbu >= thr || j < 0) {
@@ -438,6 +444,8 @@ int queue_init(Engine<R>& e) {
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.poolmin + 1, 0xff, sizeof(unsigned long long), e.st));  // lost key
   BNB_CUDA_OK(cudaMemsetAsync(e.status_d, 0, sizeof(Status), e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.hist_depth, 0, sizeof(int) * (e.dmax + 1), e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.hist_sup, 0, sizeof(int) * (e.smax + 2), e.st));
   k_queue_init<<<pool_grid(e.qcap), 256, 0, e.st>>>(e.qcap, e.wcap, e.free_stack, e.free_top,
                                                     e.pool_hw, e.warm_stack, e.warm_top,
                                                     e.pool_valid, e.pool_lb, e.pool_key,
@@ -453,7 +461,8 @@ int queue_push(Engine<R>& e) {
                                    e.free_stack, e.free_top, e.pool_hw, e.pool_valid, e.pool_lb,
                                    e.pool_key, e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
                                    e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.sel_state,
-                                   e.poolmin, e.poolmin + 1);
+                                   e.poolmin, e.poolmin + 1, e.sup_cnt, e.smax, e.hist_depth,
+                                   e.hist_sup);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }

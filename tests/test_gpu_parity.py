@@ -199,6 +199,28 @@ def test_solve_matches_brute_force_p16(prec, frac):
     assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
 
 
+def test_histograms_count_every_solved_node_and_depth_limit_is_reported():
+    inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, 3, K=8, node_tol=1e-7, max_admm_iter=5000) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+        dh, sh = bnb.bnb_get_histograms(h, 300, 300)
+        st = bnb.bnb_get_stats(h)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert dh.sum() == res["nodes"] == sh.sum()
+    assert dh[0] == 1                                  # the root, once
+    assert np.nonzero(dh)[0].max() <= st["max_depth"]
+    assert sh[17:].sum() == 0                          # p = 16: no support is larger
+    # a depth limit below the tree's depth ends the solve with its own status and a
+    # lower bound that is still valid
+    with _handle(inst, lam0, lam2, M, 3, K=8, node_tol=1e-7, max_admm_iter=5000, max_depth=8) as h:
+        r8 = bnb.bnb_solve(h, 1e-9)
+    if r8["status"] == "depth_limit":
+        assert r8["lb"] <= br.objective * (1 + 1e-9)
+    else:
+        assert tuple(np.nonzero(r8["beta"])[0]) == br.support
+
+
 @pytest.mark.parametrize("K", [1, 3, 128])
 def test_solve_batch_width_does_not_change_the_answer(K):
     inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
