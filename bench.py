@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--arrival-rate", type=float, default=20.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-lam0-frac", type=float, default=0.3,
+                    help="serve mode: lambda0 = frac x max_j (X_j^T y)^2 / (2 (||X_j||^2 + 2 lambda2))")
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="solves mode: also solve each instance with the plain FP64 path")
@@ -509,7 +511,7 @@ def run_serve(args):
         def make():
             inst = datagen.make_instance(n, p, rho, k, snr, seed)
             M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
-            lam0 = 0.1 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+            lam0 = args.serve_lam0_frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
             return inst.X, inst.y, lam0, M
         return make
 
@@ -553,7 +555,8 @@ def run_serve(args):
             "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": {"workload": "serve", "requests": args.requests,
                        "arrival_rate_per_s": args.arrival_rate, "budget_gb": args.budget_gb,
-                       "time_limit_s": args.solve_time_limit},
+                       "time_limit_s": args.solve_time_limit,
+                       "lambda0_frac": args.serve_lam0_frac},
             "alone_vs_mix": check}
     print(json.dumps(line), flush=True)
 
