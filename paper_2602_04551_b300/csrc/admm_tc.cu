@@ -419,10 +419,14 @@ __global__ void k_split_f32(const float* __restrict__ x, long long rows, long lo
 }
 
 template <int NS>
-static int cred_max_cluster(int want) {
-  int c = tc_cred_max_cluster<256, NS, TcEpiT>(want);
-  c = tc_cred_max_cluster<256, NS, TcEpiU>(c);
-  return tc_cred_max_cluster<256, NS, TcEpiResid>(c);
+static int cred_cluster(int tiles, int steps) {
+  // the three epilogues share one resource footprint; take the most constrained
+  int c = tc_cred_pick_cluster<256, NS, TcEpiT>(tiles, steps);
+  const int cu = tc_cred_pick_cluster<256, NS, TcEpiU>(tiles, steps);
+  const int cr = tc_cred_pick_cluster<256, NS, TcEpiResid>(tiles, steps);
+  if (cu < c) c = cu;
+  if (cr < c) c = cr;
+  return c;
 }
 
 int setup_tc(Engine<float>& e) {
@@ -434,8 +438,10 @@ int setup_tc(Engine<float>& e) {
     e.sms = sm > 0 ? sm : 148;
   }
   if (e.tc_c1 > 0) {
-    const int c1 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c1) : cred_max_cluster<1>(e.tc_c1);
-    const int c2 = e.tc_mode == 3 ? cred_max_cluster<3>(e.tc_c2) : cred_max_cluster<1>(e.tc_c2);
+    const int tiles = e.nbt * ((e.K + 255) / 256);
+    const int st1 = (e.p + tc::BK - 1) / tc::BK, st2 = (e.n + tc::BK - 1) / tc::BK;
+    const int c1 = e.tc_mode == 3 ? cred_cluster<3>(tiles, st1) : cred_cluster<1>(tiles, st1);
+    const int c2 = e.tc_mode == 3 ? cred_cluster<3>(tiles, st2) : cred_cluster<1>(tiles, st2);
     if (c1 < 1 || c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
     e.tc_c1 = c1;
     e.tc_c2 = c2;

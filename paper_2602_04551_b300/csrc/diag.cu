@@ -46,8 +46,7 @@ struct TcEpiPlain4 {
 template <int NS>
 static int run_check_cluster(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N,
                              int Kd, int cluster, float* C, int* err) {
-  const int c = tc_cred_max_cluster<256, NS, TcEpiPlain4>(cluster);
-  if (c < cluster) return BNB_EINVAL;
+  if (tc_cred_active_clusters<256, NS, TcEpiPlain4>(cluster) < 1) return BNB_EINVAL;
   return tc_gemm_cred<256, NS>(st, A, B, M, N, Kd, cluster, nullptr, err, TcEpiPlain4{C, 0});
 }
 

@@ -66,45 +66,64 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
   return 0;
 }
 
-// Largest cluster size (<= want, a power of two) for which at least one cluster of the
-// cluster-reduce kernel fits on the device.
+// Co-resident clusters of size cs (1, 2, 4 or 8) of the cluster-reduce kernel on the
+// current device (0 when none fits); cached per instantiation.
 template <int BN, int NSPLIT, class Epi>
-int tc_cred_max_cluster(int want) {
+int tc_cred_active_clusters(int cs) {
   using G = tc::Geo<BN, NSPLIT>;
-  static int cached = -1;
-  if (cached < 0) {
+  static int cached[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+  if (cs < 1 || cs > 8) return 0;
+  if (cached[cs] < 0) {
     auto kern = tc::tc_gemm_cred_kernel<BN, NSPLIT, Epi>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
         cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
-    cached = 0;
-    for (int cs = 8; cs >= 1; cs >>= 1) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(1, 1, cs);
-      cfg.blockDim = dim3(64 + 32 * 8);
-      cfg.dynamicSmemBytes = G::SMEM;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 1;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = cs;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int nc = 0;
-      if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc > 0) {
-        cached = cs;
-        break;
-      }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1, 1, cs);
+    cfg.blockDim = dim3(64 + 32 * 8);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = cs;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
       cudaGetLastError();
+      nc = 0;
+    }
+    cached[cs] = nc;
+  }
+  return cached[cs];
+}
+
+// Cluster size for `tiles` output tiles over `steps` K steps: the size (1, 2, 4, 8, at
+// most steps / 2) with the least estimated time, waves x (K steps per CTA + 2), where a
+// wave is as many clusters as the device co-schedules.  0 when nothing fits.
+template <int BN, int NSPLIT, class Epi>
+int tc_cred_pick_cluster(int tiles, int steps) {
+  int best = 0;
+  long long best_t = 0;
+  for (int cs = 1; cs <= 8; cs <<= 1) {
+    if (cs > 1 && cs > steps / 2) break;
+    const int act = tc_cred_active_clusters<BN, NSPLIT, Epi>(cs);
+    if (act < 1) continue;
+    const long long waves = (tiles + act - 1) / act;
+    const long long t = waves * ((steps + cs - 1) / cs + 2);
+    if (best == 0 || t < best_t) {
+      best = cs;
+      best_t = t;
     }
   }
-  return cached < want ? cached : want;
+  return best;
 }
 
 // C = A B^T over K split into `cluster` chunks reduced inside a cluster (see
-// tc_gemm_cred_kernel); `cluster` must not exceed tc_cred_max_cluster.
+// tc_gemm_cred_kernel); `cluster` must be a size tc_cred_active_clusters accepts.
 template <int BN, int NSPLIT, class Epi>
 int tc_gemm_cred(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
                  int cluster, const int* active, int* err, Epi epi) {
