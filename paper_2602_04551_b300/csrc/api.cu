@@ -185,6 +185,9 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.gscr, K * p);
   ALLOC(e.cflag, K * p);
   ALLOC(e.cpart, 2 * ((p + 31) / 32) * K);   // screen tiles of 32 (FP32) or 64 (FP64) rows
+  ALLOC(e.cx_part, 2LL * K * 8);
+  ALLOC(e.cx_base, K);
+  ALLOC(e.cx_need, K);
   ALLOC(e.cert_rr, K);
   ALLOC(e.cert_yr, K);
   ALLOC(e.cert_rn, K);

@@ -238,13 +238,13 @@ __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X
 // per-warp sums are combined in warp order at the end.
 __device__ double exact_terms(const double* __restrict__ X64, const double* __restrict__ r,
                               const int8_t* __restrict__ fixrow, const uint8_t* __restrict__ flags,
-                              int n, int p, const Prob& P, int code, int* list, int* wcnt, int* cnt,
-                              double* wacc) {
+                              int n, int i_beg, int i_end, const Prob& P, int code, int* list,
+                              int* wcnt, int* cnt, double* wacc) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double nu_w = 0.0;
-  for (int i0 = 0; i0 < p; i0 += blockDim.x) {
+  for (int i0 = i_beg; i0 < i_end; i0 += blockDim.x) {
     const int i = i0 + threadIdx.x;
-    const int f = (i < p) ? (flags[i] == code) : 0;
+    const int f = (i < i_end) ? (flags[i] == code) : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, f);
     if (lane == 0) wcnt[w] = __popc(bal);
     __syncthreads();
@@ -281,54 +281,91 @@ __device__ double exact_terms(const double* __restrict__ X64, const double* __re
   return s;
 }
 
-// The bound for each retired node (one block of 256 threads per node).
-// F1 terms are exact FP64.  Free coordinates the screen could not settle enter
-// through rigorous upper values nu(|a| + e) (LB_cheap); when a prune threshold is
-// given and LB_cheap already reaches it, or even LB_cheap plus the total interval
-// width cannot reach it, the exact FP64 terms cannot change the decision and
-// LB_cheap (a valid bound) is kept; otherwise they are computed exactly.
-__global__ void __launch_bounds__(1024) k_cert_exact(const double* __restrict__ X64,
+// The bound of each retired node, in three steps so that a node with many exact terms
+// is spread over CX_G blocks (one per slice of p) instead of one:
+//   k_cert_terms (code 1)  exact FP64 terms of the F1 coordinates, per slice;
+//   k_cert_decide          LB_cheap = base - sum nu(|a| + e) over the unsettled free
+//                          coordinates (rigorous upper values from the screen); when a
+//                          prune threshold is given and LB_cheap already reaches it, or
+//                          even LB_cheap plus the total interval width cannot reach it, the
+//                          exact terms cannot change the decision and LB_cheap (a valid
+//                          bound) is final; otherwise the node is marked;
+//   k_cert_terms (code 2)  exact FP64 terms of the unsettled coordinates of marked nodes;
+//   k_cert_final           LB = base - their sum for the marked nodes.
+// Every sum is taken in a fixed order (slices in order, warps in order inside a slice).
+constexpr int CX_G = 8;
+
+__global__ void __launch_bounds__(256) k_cert_terms(const double* __restrict__ X64,
                                                     const double* __restrict__ r64,
-                             const int8_t* __restrict__ fix, const uint8_t* __restrict__ cflag,
-                             const double* __restrict__ cpart, int nbm, int K, int n, int p,
-                             Prob P, const int* __restrict__ ret_slot,
-                             const int* __restrict__ ret_count, const double* __restrict__ cert_rr,
-                             const double* __restrict__ cert_yr, const double* __restrict__ slot_lbp,
-                             const double* __restrict__ inc_ub, const double* __restrict__ params,
-                             int use_threshold, double* __restrict__ cert_lb,
-                             double* __restrict__ node_lb) {
-  __shared__ int list[1024];
-  __shared__ int wcnt[32];
+                                                    const int8_t* __restrict__ fix,
+                                                    const uint8_t* __restrict__ cflag, int n, int p,
+                                                    Prob P, const int* __restrict__ ret_slot,
+                                                    const int* __restrict__ ret_count, int code,
+                                                    const uint8_t* __restrict__ need,
+                                                    double* __restrict__ part) {
+  __shared__ int list[256];
+  __shared__ int wcnt[8];
   __shared__ int cnt;
-  __shared__ double wacc[32];
-  __shared__ double shd[32];
-  const int q = blockIdx.x;
+  __shared__ double wacc[8];
+  const int q = blockIdx.x, g = blockIdx.y;
   if (q >= *ret_count) return;
+  if (need != nullptr && !need[q]) return;
   const int slot = ret_slot[q];
-  const double* r = r64 + (long long)q * n;
-  const int8_t* fixrow = fix + (long long)slot * p;
-  const uint8_t* flags = cflag + (long long)q * p;
+  const int per = (p + CX_G - 1) / CX_G;
+  const int i_beg = g * per, i_end = min(p, i_beg + per);
+  const double s = exact_terms(X64, r64 + (long long)q * n, fix + (long long)slot * p,
+                               cflag + (long long)q * p, n, i_beg, i_end, P, code, list, wcnt,
+                               &cnt, wacc);
+  if (threadIdx.x == 0) part[(long long)q * CX_G + g] = s;
+}
+
+// one warp per retired node
+__global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
+                              const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+                              const double* __restrict__ cert_rr, const double* __restrict__ cert_yr,
+                              const double* __restrict__ slot_lbp, const double* __restrict__ inc_ub,
+                              const double* __restrict__ params, int use_threshold,
+                              const double* __restrict__ part1, double* __restrict__ base_out,
+                              uint8_t* __restrict__ need, double* __restrict__ cert_lb,
+                              double* __restrict__ node_lb) {
+  const int q = blockIdx.x, lane = threadIdx.x;
+  if (q >= *ret_count) return;
   double su = 0.0, ss = 0.0;
-  for (int b = threadIdx.x; b < nbm; b += blockDim.x) {
+  for (int b = lane; b < nbm; b += 32) {
     su += cpart[(long long)b * K + q];
     ss += cpart[((long long)nbm + b) * K + q];
   }
-  su = block_sum(su, shd);
-  ss = block_sum(ss, shd);
-  const double s1 = exact_terms(X64, r, fixrow, flags, n, p, P, 1, list, wcnt, &cnt, wacc);
+  su = warp_sum(su);
+  ss = warp_sum(ss);
+  if (lane != 0) return;
+  double s1 = 0.0;
+  for (int g = 0; g < CX_G; ++g) s1 += part1[(long long)q * CX_G + g];
   const double base = -0.5 * cert_rr[q] + cert_yr[q] - s1;
-  double lb = base - su;
+  const double lb = base - su;
   bool exact = true;
   if (use_threshold) {
     const double thr = inc_ub[0] * (1.0 - params[0]);
     if (lb >= thr || lb + ss < thr) exact = false;
   }
-  if (exact) lb = base - exact_terms(X64, r, fixrow, flags, n, p, P, 2, list, wcnt, &cnt, wacc);
-  if (threadIdx.x == 0) {
-    cert_lb[q] = lb;
-    const double lp = slot_lbp[slot];
-    node_lb[q] = lb > lp ? lb : lp;
-  }
+  base_out[q] = base;
+  need[q] = exact ? 1 : 0;
+  cert_lb[q] = lb;                    // final unless the exact terms follow
+  const double lp = slot_lbp[ret_slot[q]];
+  node_lb[q] = lb > lp ? lb : lp;
+}
+
+__global__ void k_cert_final(const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+                             const double* __restrict__ slot_lbp, const double* __restrict__ base,
+                             const uint8_t* __restrict__ need, const double* __restrict__ part2,
+                             double* __restrict__ cert_lb, double* __restrict__ node_lb, int K) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= K || q >= *ret_count || !need[q]) return;
+  double s2 = 0.0;
+  for (int g = 0; g < CX_G; ++g) s2 += part2[(long long)q * CX_G + g];
+  const double lb = base[q] - s2;
+  cert_lb[q] = lb;
+  const double lp = slot_lbp[ret_slot[q]];
+  node_lb[q] = lb > lp ? lb : lp;
 }
 
 template <class R>
@@ -359,9 +396,17 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
   }
   prof_end(e.prof, st, PK_CERT_SCREEN);
   prof_begin(e.prof, st);
-  k_cert_exact<<<K, 1024, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, e.cpart, nbm, K, n, p, e.P,
-                                  e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr, e.slot_lbp,
-                                  e.inc_ub, e.params_d, use_threshold ? 1 : 0, e.cert_lb, e.node_lb);
+  const dim3 gx(K, CX_G);
+  k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
+                                   e.ret_count, 1, nullptr, e.cx_part);
+  k_cert_decide<<<K, 32, 0, st>>>(e.cpart, nbm, K, e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr,
+                                  e.slot_lbp, e.inc_ub, e.params_d, use_threshold ? 1 : 0,
+                                  e.cx_part, e.cx_base, e.cx_need, e.cert_lb, e.node_lb);
+  k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
+                                   e.ret_count, 2, e.cx_need, e.cx_part + (long long)K * CX_G);
+  k_cert_final<<<(K + 127) / 128, 128, 0, st>>>(e.ret_slot, e.ret_count, e.slot_lbp, e.cx_base,
+                                                e.cx_need, e.cx_part + (long long)K * CX_G,
+                                                e.cert_lb, e.node_lb, K);
   prof_end(e.prof, st, PK_CERT_EXACT);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;

@@ -106,6 +106,9 @@ struct Engine {
   R* rS = nullptr;              // residual in screen precision, K x n
   float* gscr = nullptr;        // screened X_i^T r, K x p
   uint8_t* cflag = nullptr;     // K x p: 1 = exact FP64 term (F1), 2 = free, unsettled by the screen
+  double* cx_part = nullptr;    // [2][K][8] exact certificate terms per p slice (F1, unsettled)
+  double* cx_base = nullptr;    // [K] -1/2 ||r||^2 + y^T r - F1 terms
+  uint8_t* cx_need = nullptr;   // [K] unsettled terms needed exactly
   double* cpart = nullptr;      // [2][row tiles of the screen][K] screen partial sums
   int* flist = nullptr;         // K x p flagged index lists
 

@@ -131,8 +131,9 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
   R* Q = Qg + (long long)q * smax * smax;
   const int npair = s * (s + 1) / 2;
   // one warp per entry: lanes stride over the n samples, fixed-order butterfly sum
+  // the node's entries are spread over the gridDim.y blocks of its row of the grid
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = w; t < npair + s; t += nw) {
+  for (int t = blockIdx.y * nw + w; t < npair + s; t += nw * gridDim.y) {
     if (t < npair) {
       // unrank t -> (a, b), a >= b
       int a = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
@@ -545,7 +546,7 @@ template <class R>
 int upper_bound(Engine<R>& e, bool force_polish) {
   cudaStream_t st = e.st;
   const int K = e.K;
-  k_ub_gram<R><<<K, 256, 0, st>>>(e.XR, e.yR, e.n, e.smax, e.P.lam2, e.sup, e.sup_cnt,
+  k_ub_gram<R><<<dim3(K, 16), 256, 0, st>>>(e.XR, e.yR, e.n, e.smax, e.P.lam2, e.sup, e.sup_cnt,
                                   e.ret_count, e.Qg, e.qv);
   const size_t sm = sizeof(R) * 4 * e.smax;
   k_ub_fista<R><<<K, 256, sm, st>>>(e.Qg, e.qv, e.smax, e.P.M, e.sup_cnt, e.ret_count,
