@@ -375,6 +375,27 @@ def reference_arm(args):
 # ------------------------------------------------------------------------ main
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel per
+# launch, from one ncu capture summarised under profiles/; it is reported only while the
+# kernel's sources are the ones captured (hash of the files below), else null.
+KERNEL_SOURCES = ("tc_gemm.cuh", "admm_tc.cu", "common.cuh", "engine.cuh", "tc_host.cuh")
+TRAFFIC = {
+    ("gemm_xtu_prox", "c2", 512, "tc3"): {
+        "sources": "bee8cdfd0441d312", "bytes": 45.079808e6 + 0.696832e6,
+        "note": "ncu capture of tc_gemm_persist_kernel<TcEpiAdmm> on the c2 workload "
+                "(~500 active slots), profiles/admm_tc_kernels_c2_K512_tc3.md"},
+}
+
+
+def sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2602_04551_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def roofline(out, args, pk):
     """Dominant contraction of the profiled round against its peak.
 
@@ -399,6 +420,10 @@ def roofline(out, args, pk):
     r = {"kernel": name, "achieved": ach, "unit": "TFLOP/s", "traffic": None,
          "share_of_round": share, "flops_per_launch": flops[name], "ms_per_launch": ms,
          "active_slots": active}
+    tr = TRAFFIC.get((name, args.workload, args.K, args.precision))
+    if tr is not None and tr["sources"] == sources_hash():
+        r["traffic"] = tr["bytes"]
+        r["traffic_note"] = tr["note"]
     if args.precision == "fp32":
         peak = SM_COUNT * FP32_LANES * 2 * 2032.0 * 1e6 / 1e12
         r.update(bound="alu", peak=peak, frac=ach / peak,
