@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--mode", default="rounds", choices=["rounds", "solves", "serve"],
+    ap.add_argument("--mode", default="rounds", choices=["rounds", "solves", "serve", "kcurve"],
                     help="rounds: steady-state nodes/s (default); solves: full solves over a "
                          "lambda0 sweep; serve: Poisson request stream through the serving loop")
     ap.add_argument("--lam0-fracs", default="0.3,0.15,0.08,0.05,0.03")
@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--fp64-time-limit", type=float, default=60.0)
     ap.add_argument("--seeds", type=int, default=1, help="solves mode: instances per lambda0")
     ap.add_argument("--max-depth", type=int, default=1024)
+    ap.add_argument("--k-list", default="1,4,16,64,256,512",
+                    help="kcurve mode: batch widths; each solve runs --solve-time-limit seconds")
     ap.add_argument("--lam0-frac", type=float, default=0.02)
     ap.add_argument("--K", type=int, default=512)
     ap.add_argument("--check-every", type=int, default=10)
@@ -522,6 +524,43 @@ def run_solves(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kcurve(args):
+    """Node throughput against the batch width K, for continuous slot refill and for the
+    lockstep batches of Algorithm 1, on one workload instance (time-limited solves)."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+    inst, lam0, lam2, M, cfg = workload(args.workload, 0, args.lam0_frac)
+    rho = args.rho if args.rho > 0 else 0.3
+    rows = []
+    for K in [int(k) for k in args.k_list.split(",")]:
+        for lock in (0, 1):
+            o = bnb.bnb_options_default(M=M, batch_K=K, check_every=args.check_every,
+                                        precision=PREC[args.precision], rho=rho,
+                                        relax_alpha=args.alpha, queue_capacity=1 << 21,
+                                        max_depth=args.max_depth, lockstep=lock,
+                                        time_limit_s=args.solve_time_limit)
+            with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = bnb.bnb_solve(h, 1e-4)
+                dt = time.perf_counter() - t0
+            rows.append({"K": K, "lockstep": lock, "nodes": res["nodes"], "seconds": dt,
+                         "nodes_per_s": res["nodes"] / dt, "status": res["status"],
+                         "ub": res["ub"], "lb": res["lb"]})
+            print(json.dumps({"kcurve": rows[-1]}), file=sys.stderr, flush=True)
+    base = {r["lockstep"]: r["nodes_per_s"] for r in rows if r["K"] == rows[0]["K"]}
+    for r in rows:
+        r["speedup_vs_first_K"] = r["nodes_per_s"] / base[r["lockstep"]]
+    line = {"metric": "BnB nodes/s vs batch width K", "mode": "kcurve", "unit": "nodes/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE[args.precision],
+            "data": "synthetic", "config": {"workload": args.workload,
+                                            "lambda0_frac": args.lam0_frac, "rho": rho,
+                                            "relax_alpha": args.alpha,
+                                            "time_limit_s": args.solve_time_limit},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args):
     """The serving workload: independent solves of random shapes arriving as a
     Poisson stream, admitted under an HBM budget and interleaved on the GPU."""
@@ -596,6 +635,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "kcurve":
+        run_kcurve(args)
         return
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))

@@ -80,6 +80,9 @@ typedef struct {
                             heuristic (Appendix A.2) polished exactly in FP64 */
   int max_depth;         /* deepest node kept (fixings stored per open node), default 256,
                             in [8, 4096]; the pool takes queue_capacity x max_depth x 4 bytes */
+  int lockstep;          /* 0 (default): a freed slot is refilled with the best open node at
+                            the next round; 1: the batches of Algorithm 1 -- select up to K
+                            nodes, solve them all, then branch/prune and select again */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */

@@ -45,7 +45,8 @@ class bnb_options(ctypes.Structure):
                 ("warm_capacity", ctypes.c_longlong), ("support_max", ctypes.c_int),
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
-                ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int)]
+                ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("lockstep", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):

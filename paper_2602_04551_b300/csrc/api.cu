@@ -388,6 +388,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->relax_alpha = 1.0;
   o->root_heuristic = 1;
   o->max_depth = 256;
+  o->lockstep = 0;
   return BNB_OK;
 }
 
@@ -399,6 +400,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->p = h->p;
   e->K = o.batch_K;
   e->dmax = o.max_depth;
+  e->lockstep = o.lockstep ? 1 : 0;
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
   e->qcap = o.queue_capacity;

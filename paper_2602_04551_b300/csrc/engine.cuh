@@ -93,6 +93,7 @@ struct Engine {
   // slots
   int *slot_active = nullptr, *slot_iters = nullptr, *slot_depth = nullptr, *slot_nfix = nullptr;
   int dmax = 256;               // deepest node (fixings kept per open node)
+  int lockstep = 0;             // 1: refill only when every slot is free (Algorithm 1 batches)
   int* hist_depth = nullptr;    // [dmax + 1] solved nodes by depth (last bin: deeper)
   int* hist_sup = nullptr;      // [smax + 2] solved nodes by rounded-support size
   int* slot_fixl = nullptr;     // K x dmax encoded fixings (idx << 1 | dir)

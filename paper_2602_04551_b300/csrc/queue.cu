@@ -202,8 +202,10 @@ __global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid
 }
 
 // level-L scan (single block).  Level 1 also lists the free slots in order.
+// With `lockstep` (Algorithm 1's batches) nothing is selected until every slot is free;
+// SS_TAKE_ALL = 2 then means "take none" for the later levels and the collection.
 __global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* sel_state, int K,
-                           const int* __restrict__ slot_active, int* free_slots) {
+                           const int* __restrict__ slot_active, int* free_slots, int lockstep) {
   __shared__ int wcnt[32];
   __shared__ int base;
   if (level == 1) {
@@ -236,7 +238,11 @@ __global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* se
       const int F = base;
       sel_state[SS_F] = F;
       const int count = sel_state[SS_COUNT];
-      if (count <= F) {
+      if (lockstep && F < K) {
+        sel_state[SS_TAKE_ALL] = 2;
+        sel_state[SS_F] = 0;
+        done_s = 1;
+      } else if (count <= F) {
         sel_state[SS_TAKE_ALL] = 1;
         done_s = 1;
       } else {
@@ -323,12 +329,13 @@ __global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_val
                               int* sel_state, int* popped) {
   const int hw = *pool_hw;
   const int all = sel_state[SS_TAKE_ALL];
+  if (all == 2) return;                     // lockstep: slots still busy
   const unsigned tau = (unsigned)sel_state[SS_TAU];
   const int need_eq = sel_state[SS_NEED];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
     if (!pool_valid[i]) continue;
     const unsigned k = pool_key[i];
-    bool take = all || k < tau;
+    bool take = all == 1 || k < tau;
     if (!take && k == tau) take = atomicAdd(&sel_state[SS_EQ], 1) < need_eq;
     if (!take) continue;
     popped[atomicAdd(&sel_state[SS_OUT], 1)] = i;
@@ -475,11 +482,14 @@ int queue_select_refill(Engine<R>& e) {
   k_sel_pass1<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_lb, e.pool_key, e.pool_warm,
                                  e.free_stack, e.free_top, e.warm_ref, e.warm_stack, e.warm_top,
                                  e.inc_ub, e.params_d, e.sel, e.sel_state, e.poolmin);
-  k_sel_scan<<<1, 1024, 0, st>>>(1, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_scan<<<1, 1024, 0, st>>>(1, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots,
+                                 e.lockstep);
   k_sel_pass<<<g, 256, 0, st>>>(2, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
-  k_sel_scan<<<1, 1024, 0, st>>>(2, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_scan<<<1, 1024, 0, st>>>(2, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots,
+                                 e.lockstep);
   k_sel_pass<<<g, 256, 0, st>>>(3, e.pool_hw, e.pool_valid, e.pool_key, e.sel, e.sel_state);
-  k_sel_scan<<<1, 1024, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots);
+  k_sel_scan<<<1, 1024, 0, st>>>(3, e.sel, e.sel_state, e.K, e.slot_active, e.free_slots,
+                                 e.lockstep);
   k_sel_collect<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_key, e.free_stack, e.free_top,
                                    e.sel_state, e.popped);
   k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb,

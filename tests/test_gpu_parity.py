@@ -221,6 +221,18 @@ def test_histograms_count_every_solved_node_and_depth_limit_is_reported():
         assert tuple(np.nonzero(r8["beta"])[0]) == br.support
 
 
+@pytest.mark.parametrize("K", [1, 8])
+def test_lockstep_batches_reach_the_same_optimum(K):
+    """Algorithm 1's select-solve-branch batches (lockstep) against brute force."""
+    inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, 3, K=K, node_tol=1e-7, max_admm_iter=5000, lockstep=1) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+    assert res["lb"] <= br.objective * (1 + 1e-9)
+
+
 @pytest.mark.parametrize("K", [1, 3, 128])
 def test_solve_batch_width_does_not_change_the_answer(K):
     inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
