@@ -308,6 +308,15 @@ struct TcEpiAdmm {
   }
 };
 
+// cluster-reduced product with the tile width chosen at setup (128 or 256 columns)
+template <int NS, class Epi>
+static int cred(Engine<float>& e, int bn, const TcOperand& A, const TcOperand& B, int M, int N,
+                int Kred, int cluster, Epi epi) {
+  if (bn == 128)
+    return tc_gemm_cred<128, NS>(e.st, A, B, M, N, Kred, cluster, e.slot_active, e.tc_err, epi);
+  return tc_gemm_cred<256, NS>(e.st, A, B, M, N, Kred, cluster, e.slot_active, e.tc_err, epi);
+}
+
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
   constexpr int BN = 256;   // X W'^T, G^-1 T and X beta^T: wide tiles, split-K
@@ -335,14 +344,13 @@ static int round_tc(Engine<float>& e, int iters) {
     if (e.tc_c1 > 0) {
       // split-K reduced inside clusters, epilogues write the next operands directly
       prof_begin(e.prof, st);
-      if (int rc = tc_gemm_cred<BN, NS>(st, XT, Wop, n, K, p, e.tc_c1, e.slot_active, e.tc_err,
-                                        TcEpiT{e.t_hi, NS == 3 ? e.t_lo : nullptr, e.ldn,
-                                               e.slot_active, 0}))
+      if (int rc = cred<NS>(e, e.tc_bn1, XT, Wop, n, K, p, e.tc_c1,
+                            TcEpiT{e.t_hi, NS == 3 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
         return rc;
       prof_end(e.prof, st, PK_GEMM_XW);
       prof_begin(e.prof, st);
-      if (int rc = tc_gemm_cred<BN, NS>(
-              st, GI, Top, n, K, n, e.tc_c2, e.slot_active, e.tc_err,
+      if (int rc = cred<NS>(
+              e, e.tc_bn2, GI, Top, n, K, n, e.tc_c2,
               TcEpiU{e.u_hi, NS == 3 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
                      (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
         return rc;
@@ -389,9 +397,8 @@ static int round_tc(Engine<float>& e, int iters) {
   // check product X beta^T
   prof_begin(e.prof, st);
   if (e.tc_c1 > 0) {
-    if (int rc = tc_gemm_cred<BN, NS>(st, XT, Bop, n, K, p, e.tc_c1, e.slot_active, e.tc_err,
-                                      TcEpiResid{e.slot_active, (const float*)e.yR, e.tc_stat,
-                                                 e.nbt, K, 1}))
+    if (int rc = cred<NS>(e, e.tc_bn1, XT, Bop, n, K, p, e.tc_c1,
+                          TcEpiResid{e.slot_active, (const float*)e.yR, e.tc_stat, e.nbt, K, 1}))
       return rc;
   } else {
     if (int rc = tc_gemm<BN, NS>(st, XT, Bop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
@@ -418,15 +425,29 @@ __global__ void k_split_f32(const float* __restrict__ x, long long rows, long lo
   }
 }
 
+// Tile width and cluster size of a cluster-reduced n x K product: the pair with the least
+// estimated time, waves x (K steps per CTA + 2) x relative cost of a K step (a 128-wide
+// step moves 64 KB of operands against 96 KB for 256 in TC3: 0.65).
 template <int NS>
-static int cred_cluster(int tiles, int steps) {
-  // the three epilogues share one resource footprint; take the most constrained
-  int c = tc_cred_pick_cluster<256, NS, TcEpiT>(tiles, steps);
-  const int cu = tc_cred_pick_cluster<256, NS, TcEpiU>(tiles, steps);
-  const int cr = tc_cred_pick_cluster<256, NS, TcEpiResid>(tiles, steps);
-  if (cu < c) c = cu;
-  if (cr < c) c = cr;
-  return c;
+static void cred_shape(int nbt, int K, int steps, int* bn, int* cs) {
+  *bn = 0;
+  *cs = 0;
+  double best = 0.0;
+  for (int w : {256, 128}) {
+    const int tiles = nbt * ((K + w - 1) / w);
+    int c = w == 256 ? tc_cred_pick_cluster<256, NS, TcEpiT>(tiles, steps)
+                     : tc_cred_pick_cluster<128, NS, TcEpiT>(tiles, steps);
+    if (c < 1) continue;
+    const int act = w == 256 ? tc_cred_active_clusters<256, NS, TcEpiT>(c)
+                             : tc_cred_active_clusters<128, NS, TcEpiT>(c);
+    const double waves = (double)((tiles + act - 1) / act);
+    const double t = waves * ((steps + c - 1) / c + 2) * (w == 256 ? 1.0 : 0.65);
+    if (*bn == 0 || t < best) {
+      best = t;
+      *bn = w;
+      *cs = c;
+    }
+  }
 }
 
 int setup_tc(Engine<float>& e) {
@@ -438,13 +459,15 @@ int setup_tc(Engine<float>& e) {
     e.sms = sm > 0 ? sm : 148;
   }
   if (e.tc_c1 > 0) {
-    const int tiles = e.nbt * ((e.K + 255) / 256);
     const int st1 = (e.p + tc::BK - 1) / tc::BK, st2 = (e.n + tc::BK - 1) / tc::BK;
-    const int c1 = e.tc_mode == 3 ? cred_cluster<3>(tiles, st1) : cred_cluster<1>(tiles, st1);
-    const int c2 = e.tc_mode == 3 ? cred_cluster<3>(tiles, st2) : cred_cluster<1>(tiles, st2);
-    if (c1 < 1 || c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
-    e.tc_c1 = c1;
-    e.tc_c2 = c2;
+    if (e.tc_mode == 3) {
+      cred_shape<3>(e.nbt, e.K, st1, &e.tc_bn1, &e.tc_c1);
+      cred_shape<3>(e.nbt, e.K, st2, &e.tc_bn2, &e.tc_c2);
+    } else {
+      cred_shape<1>(e.nbt, e.K, st1, &e.tc_bn1, &e.tc_c1);
+      cred_shape<1>(e.nbt, e.K, st2, &e.tc_bn2, &e.tc_c2);
+    }
+    if (e.tc_c1 < 1 || e.tc_c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
   }
   const long long n = e.n, p = e.p;
   // column-major X: p columns of length n (leading dimension ldn)
