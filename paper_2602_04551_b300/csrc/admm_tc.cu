@@ -317,11 +317,34 @@ static int cred(Engine<float>& e, int bn, const TcOperand& A, const TcOperand& B
   return tc_gemm_cred<256, NS>(e.st, A, B, M, N, Kred, cluster, e.slot_active, e.tc_err, epi);
 }
 
+// X^T U' with the fused ADMM epilogue, persistent, tile width chosen at setup
+template <int NS, int BN3, bool STATS>
+static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
+  TcEpiAdmm<BN3, STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
+                            e.w_hi, NS == 3 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
+                            (STATS && NS == 3) ? e.b_lo : nullptr, e.P, e.p, e.ldp, e.nbm3, e.K};
+  return tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, STATS>, 8>(e.st, XC, Uop, e.p, e.K, e.n, e.sms,
+                                                           e.slot_active, e.tc_err, epi);
+}
+
+template <int NS>
+static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop, bool last) {
+  switch (e.tc_bn3) {
+    case 80:
+      return last ? fused_xtu_bn<NS, 80, true>(e, XC, Uop) : fused_xtu_bn<NS, 80, false>(e, XC, Uop);
+    case 96:
+      return last ? fused_xtu_bn<NS, 96, true>(e, XC, Uop) : fused_xtu_bn<NS, 96, false>(e, XC, Uop);
+    case 128:
+      return last ? fused_xtu_bn<NS, 128, true>(e, XC, Uop)
+                  : fused_xtu_bn<NS, 128, false>(e, XC, Uop);
+    default:
+      return last ? fused_xtu_bn<NS, 64, true>(e, XC, Uop) : fused_xtu_bn<NS, 64, false>(e, XC, Uop);
+  }
+}
+
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
   constexpr int BN = 256;   // X W'^T, G^-1 T and X beta^T: wide tiles, split-K
-  constexpr int BN3 = 64;   // X^T U' + fused update: 128 x 64 tiles, persistent CTAs with a
-                            // double-buffered accumulator (epilogue overlaps the next tile)
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   const long long nK = (long long)n * K;
@@ -377,21 +400,8 @@ static int round_tc(Engine<float>& e, int iters) {
       prof_end(e.prof, st, PK_FINAL_U);
     }
     prof_begin(e.prof, st);
-    if (last) {
-      TcEpiAdmm<BN3, true> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active,
-                               (float*)e.g3part, e.w_hi, NS == 3 ? e.w_lo : nullptr, e.b_hi,
-                               NS == 3 ? e.b_lo : nullptr, e.P, p, e.ldp, e.nbm3, K};
-      if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, true>, 8>(
-              st, XC, Uop, p, K, n, e.sms, e.slot_active, e.tc_err, epi))
-        return rc;
-    } else {
-      TcEpiAdmm<BN3, false> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active,
-                                (float*)e.g3part, e.w_hi, NS == 3 ? e.w_lo : nullptr, nullptr,
-                                nullptr, e.P, p, e.ldp, e.nbm3, K};
-      if (int rc = tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, false>, 8>(
-              st, XC, Uop, p, K, n, e.sms, e.slot_active, e.tc_err, epi))
-        return rc;
-    }
+    if (int rc = fused_xtu<NS>(e, XC, Uop, last))
+      return rc;
     prof_end(e.prof, st, PK_GEMM_XTU);
   }
   // check product X beta^T
@@ -468,6 +478,22 @@ int setup_tc(Engine<float>& e) {
       cred_shape<1>(e.nbt, e.K, st2, &e.tc_bn2, &e.tc_c2);
     }
     if (e.tc_c1 < 1 || e.tc_c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
+  }
+  // fused X^T U' tiles: the width with the least operand bytes on the busiest CTA,
+  // ceil(tiles / SMs) x (128 + width) rows of length n (K > 64 x width is not supported)
+  {
+    const int mt = (e.p + tc::BM - 1) / tc::BM;
+    long long best = -1;
+    for (int w : {64, 80, 96, 128}) {
+      if (e.K > 64 * w) continue;
+      const long long tiles = (long long)mt * ((e.K + w - 1) / w);
+      const long long t = (tiles + e.sms - 1) / e.sms * (128 + w);
+      if (best < 0 || t < best) {
+        best = t;
+        e.tc_bn3 = w;
+      }
+    }
+    if (best < 0) return BNB_EINVAL;
   }
   const long long n = e.n, p = e.p;
   // column-major X: p columns of length n (leading dimension ldn)

@@ -176,6 +176,8 @@ struct Geo {
   static constexpr int PSTAGES = (200 * 1024) / STAGE_BYTES < 2 ? 2 : (200 * 1024) / STAGE_BYTES;
   static constexpr int PSMEM = PSTAGES * STAGE_BYTES + 1024;
   static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  // persistent kernel: each of its two accumulators starts at a power-of-two column
+  static constexpr int PBUF = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 };
 
 struct Maps {
@@ -488,6 +490,7 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
   using G = Geo<BN, NSPLIT>;
   constexpr int S = G::PSTAGES;
   constexpr int MAXNT = 64;                      // column tiles (N <= 64 BN)
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N: a multiple of 16 up to 256");
   extern __shared__ uint8_t dsm_raw[];
   __shared__ __align__(8) uint64_t full_bar[S];
   __shared__ __align__(8) uint64_t empty_bar[S];
@@ -526,7 +529,7 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
-                 "r"(2 * G::TMEM_COLS)
+                 "r"(2 * G::PBUF)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -572,7 +575,7 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
       const int b = i & 1;
       if (i >= 2 && !mbar_wait(&tempty_bar[b], (uint32_t)(((i >> 1) & 1) ^ 1), err, 8)) break;
       fence_after();
-      const uint32_t acc_addr = tmem + (uint32_t)(b * G::TMEM_COLS);
+      const uint32_t acc_addr = tmem + (uint32_t)(b * G::PBUF);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % S);
         if (!mbar_wait(&full_bar[s], (uint32_t)((g / S) & 1), err, 2)) {
@@ -617,7 +620,7 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
 #pragma unroll 1
         for (int c = 16 * gq; c < BN; c += 16 * (EPIW / 4)) {
           float v[16];
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::TMEM_COLS + c), v);
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::PBUF + c), v);
           epi(row, n0 + c, v, M, N, q, epi_smem);
         }
       }
@@ -645,7 +648,7 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * G::TMEM_COLS)
+                 "r"(2 * G::PBUF)
                  : "memory");
   }
 }

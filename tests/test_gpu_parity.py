@@ -120,6 +120,14 @@ def test_one_admm_iteration_full_size_sampled(prec):
     _one_iteration_check(inst, lam0, lam2, M, prec, K=512, Kopt=512, rows=[0, 131, 300, 511], seed=4)
 
 
+@pytest.mark.parametrize("prec", [3, 2])
+def test_one_admm_iteration_full_size_wide_batch(prec):
+    """C2 shape at K=1024 (other tile widths of the fused and cluster-reduced products);
+    the last slot of the last column tile and a ragged middle one are sampled."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=1000, Kopt=1024, rows=[0, 517, 999], seed=5)
+
+
 # ------------------------------------------------------------------ converged node
 
 
