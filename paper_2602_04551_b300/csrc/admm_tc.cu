@@ -215,6 +215,7 @@ struct TcEpiAdmm {
   __nv_bfloat16 *whi, *wlo;     // next W operand (K x ldp)
   __nv_bfloat16 *bhi, *blo;     // beta operand for the check product (or null)
   Prob P;
+  ProbF PF;
   long long p, ldp;
   int nbm, K;
   // STATS (the round's last iteration): per-slot stop-test sums and the beta operand of
@@ -222,7 +223,7 @@ struct TcEpiAdmm {
 
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
-    const float rho = (float)P.rho, irho = 1.0f / (float)P.rho;
+    const float rho = PF.rho, irho = PF.irho;
     // all loads of the chunk first (independent), then the arithmetic and the stores
     bool ok[16];
     float bo[16], vv[16];
@@ -245,8 +246,8 @@ struct TcEpiAdmm {
           const long long o = (long long)n * p + m;
           const float w = rho * bo[j] - vv[j];
           const float b = bcm + (w - acc[j]) * irho;
-          const float bh = (float)P.alpha * b + (1.0f - (float)P.alpha) * bo[j];
-          const float bn = prox_coord<float>(bh + vv[j] * irho, ff[j], P);
+          const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];
+          const float bn = prox_coord_f(bh + vv[j] * irho, ff[j], PF);
           const float vn = vv[j] + rho * (bh - bn);
           beta[o] = bn;
           V[o] = vn;
@@ -264,9 +265,9 @@ struct TcEpiAdmm {
         const long long o = (long long)n * p + m;
         const float w = rho * bo[j] - vv[j];               // W'
         const float b = bcm + (w - acc[j]) * irho;         // b = b_c + D W'
-        const float bh = (float)P.alpha * b + (1.0f - (float)P.alpha) * bo[j];   // over-relaxed
+        const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];   // over-relaxed
         const float bt = bh + vv[j] * irho;
-        const float bn = prox_coord<float>(bt, ff[j], P);
+        const float bn = prox_coord_f(bt, ff[j], PF);
         const float vn = vv[j] + rho * (bh - bn);
         beta[o] = bn;
         V[o] = vn;
@@ -322,7 +323,8 @@ template <int NS, int BN3, bool STATS>
 static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
   TcEpiAdmm<BN3, STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                             e.w_hi, NS == 3 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
-                            (STATS && NS == 3) ? e.b_lo : nullptr, e.P, e.p, e.ldp, e.nbm3, e.K};
+                            (STATS && NS == 3) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
+                            e.nbm3, e.K};
   return tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, STATS>, 8>(e.st, XC, Uop, e.p, e.K, e.n, e.sms,
                                                            e.slot_active, e.tc_err, epi);
 }

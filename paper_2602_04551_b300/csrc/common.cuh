@@ -56,6 +56,39 @@ __device__ __forceinline__ T prox_coord(T bt, int f, const Prob& P) {
   return box_soft<T>(bt, (T)P.thr_soft, M);
 }
 
+// FP32 copies of the constants the FP32 prox needs, rounded once on the host exactly as
+// the (float) conversions inside prox_coord<float> round them, so the two agree bit for
+// bit; the hot epilogue then converts nothing.
+struct ProbF {
+  float rho, irho, alpha, one_minus_alpha, M, ridge_scale, thr_lin, tau, thr_soft;
+  int linear;
+};
+
+inline ProbF prob_f32(const Prob& P) {
+  ProbF f;
+  f.rho = (float)P.rho;
+  f.irho = 1.0f / f.rho;
+  f.alpha = (float)P.alpha;
+  f.one_minus_alpha = 1.0f - f.alpha;
+  f.M = (float)P.M;
+  f.ridge_scale = (float)P.ridge_scale;
+  f.thr_lin = (float)P.thr_lin;
+  f.tau = (float)P.tau;
+  f.thr_soft = (float)P.thr_soft;
+  f.linear = P.linear;
+  return f;
+}
+
+__device__ __forceinline__ float prox_coord_f(float bt, int f, const ProbF& P) {
+  if (f == 0) return 0.0f;
+  float ridge = bt * P.ridge_scale;
+  ridge = ridge > P.M ? P.M : (ridge < -P.M ? -P.M : ridge);
+  if (f == 1) return ridge;
+  if (P.linear) return box_soft<float>(bt, P.thr_lin, P.M);
+  if (fabsf(bt) >= P.tau) return ridge;
+  return box_soft<float>(bt, P.thr_soft, P.M);
+}
+
 template <class T>
 __device__ __forceinline__ T psi_coord(T b, int f, const Prob& P) {
   if (f == 0) return T(0);
