@@ -224,11 +224,47 @@ struct TcEpiAdmm {
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
     const float rho = PF.rho, irho = PF.irho;
+    const float bcm = m < M ? bc[m] : 0.f;
+    if constexpr (!STATS) {
+      // two halves of 8 columns: loads of a half first (independent), then its arithmetic
+      // and stores (keeps the register footprint under the 10-warp limit)
+#pragma unroll
+      for (int h = 0; h < 16; h += 8) {
+        bool ok[8];
+        float bo[8], vv[8];
+        int ff[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + h + j;
+          ok[j] = (m < M) && (n < N) && active[n];
+          const long long o = (long long)n * p + m;
+          bo[j] = ok[j] ? beta[o] : 0.f;
+          vv[j] = ok[j] ? V[o] : 0.f;
+          ff[j] = ok[j] ? (int)fix[o] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (ok[j]) {
+            const int n = n0 + h + j;
+            const long long o = (long long)n * p + m;
+            const float w = rho * bo[j] - vv[j];
+            const float b = bcm + (w - acc[h + j]) * irho;
+            const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];
+            const float bn = prox_coord_f(bh + vv[j] * irho, ff[j], PF);
+            const float vn = vv[j] + rho * (bh - bn);
+            beta[o] = bn;
+            V[o] = vn;
+            split_store(rho * bn - vn, whi, wlo, (long long)n * ldp + m);
+          }
+        }
+      }
+      return;
+    } else {
     // all loads of the chunk first (independent), then the arithmetic and the stores
     bool ok[16];
     float bo[16], vv[16];
     int ff[16];
-    const float bcm = m < M ? bc[m] : 0.f, rbcm = m < M ? rbc[m] : 0.f;
+    const float rbcm = m < M ? rbc[m] : 0.f;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int n = n0 + j;
@@ -238,24 +274,6 @@ struct TcEpiAdmm {
       vv[j] = ok[j] ? V[o] : 0.f;
       ff[j] = ok[j] ? (int)fix[o] : 0;
     }
-    if constexpr (!STATS) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        if (ok[j]) {
-          const int n = n0 + j;
-          const long long o = (long long)n * p + m;
-          const float w = rho * bo[j] - vv[j];
-          const float b = bcm + (w - acc[j]) * irho;
-          const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];
-          const float bn = prox_coord_f(bh + vv[j] * irho, ff[j], PF);
-          const float vn = vv[j] + rho * (bh - bn);
-          beta[o] = bn;
-          V[o] = vn;
-          split_store(rho * bn - vn, whi, wlo, (long long)n * ldp + m);
-        }
-      }
-      return;
-    } else {
     float s_psi[16], s_nu[16], s_db[16], s_pr[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
