@@ -83,6 +83,10 @@ typedef struct {
   int lockstep;          /* 0 (default): a freed slot is refilled with the best open node at
                             the next round; 1: the batches of Algorithm 1 -- select up to K
                             nodes, solve them all, then branch/prune and select again */
+  int mv_crossover;      /* tensor-core precisions: a round whose active slots are at most this
+                            many runs the ADMM products as coalesced matrix-vector kernels on
+                            CUDA cores (FP32) instead of tensor-core tiles; -1 (default) = 16,
+                            0 = never, at most 32.  Chosen per round on the device. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */

@@ -46,7 +46,7 @@ class bnb_options(ctypes.Structure):
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
                 ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
-                ("lockstep", ctypes.c_int)]
+                ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):

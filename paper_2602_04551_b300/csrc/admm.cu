@@ -265,7 +265,26 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   if constexpr (sizeof(R) == 4) tc = e.tc_mode != 0;
   if (tc) {
     if constexpr (sizeof(R) == 4) {
-      if (int rc = admm_iterations_tc(e, iters)) return rc;
+      if (e.mv_cross > 0) {
+        // narrow or wide form, chosen from the active-slot count: on the device inside a
+        // captured round (conditional node), else on the host
+        if (int rc = act_list(e)) return rc;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        BNB_CUDA_OK(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) {
+          if (int rc = capture_mv_or_tc(e, iters)) return rc;
+        } else {
+          int a = e.mv_hint;
+          if (a < 0) {
+            BNB_CUDA_OK(cudaMemcpyAsync(&a, e.act_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+            BNB_CUDA_OK(cudaStreamSynchronize(st));
+          }
+          if (int rc = a <= e.mv_cross ? admm_iterations_mv(e, iters) : admm_iterations_tc(e, iters))
+            return rc;
+        }
+      } else {
+        if (int rc = admm_iterations_tc(e, iters)) return rc;
+      }
       S_check = e.tc_s1n;
     }
   } else {

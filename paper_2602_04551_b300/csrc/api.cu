@@ -71,6 +71,8 @@ static void free_all(Engine<R>& e) {
   e.allocs.clear();
   if (e.status_h) cudaFreeHost(e.status_h);
   e.status_h = nullptr;
+  if (e.st_side) cudaStreamDestroy(e.st_side);
+  e.st_side = nullptr;
   if (e.own_stream && e.st) cudaStreamDestroy(e.st);
   e.st = nullptr;
 }
@@ -117,6 +119,9 @@ static int allocate(Engine<R>& e) {
       e.tc_c2 = cl(st2);
       ALLOC(e.tc_stat, 3LL * e.nbt * K);
       s1cap = s2cap = 0;
+      ALLOC(e.act_list, K);
+      ALLOC(e.act_count, 1);
+      ALLOC(e.mv_part, (long long)MV_ZMAX * MV_MAX * n);
       const bool lo = e.tc_mode == 3;
       ALLOC(e.xc_hi, p * e.ldn);
       ALLOC(e.xt_hi, n * e.ldp);
@@ -389,6 +394,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->root_heuristic = 1;
   o->max_depth = 256;
   o->lockstep = 0;
+  o->mv_crossover = -1;
   return BNB_OK;
 }
 
@@ -441,6 +447,9 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   if constexpr (sizeof(R) == 4) {
     if (e->tc_mode) {
       if (int rc = setup_tc(*e)) return rc;
+      e->mv_cross = o.mv_crossover < 0 ? 16 : (o.mv_crossover > MV_MAX ? MV_MAX : o.mv_crossover);
+      if (int rc = mv_setup(*e)) return rc;
+      BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st_side, cudaStreamNonBlocking));
       BNB_CUDA_OK(cudaStreamSynchronize(e->st));
     }
   }
@@ -476,6 +485,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.support_max < 1 || o.support_max > 256) return fail(BNB_EINVAL, "support_max must be in [1, 256]");
   if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
   if (o.max_depth < 8 || o.max_depth > 4096) return fail(BNB_EINVAL, "max_depth must be in [8, 4096]");
+  if (o.mv_crossover < -1 || o.mv_crossover > 32) return fail(BNB_EINVAL, "mv_crossover must be in [-1, 32]");
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
@@ -626,6 +636,7 @@ static int relax_impl(bnb_handle* h, Engine<R>& e, int K, const int8_t* dfix, co
   BNB_CUDA_OK(cudaMemcpyAsync(e.inc_ub, &inf, sizeof(double), cudaMemcpyHostToDevice, st));
   int rounds = 0;
   const int max_rounds = (max_iter + o.check_every - 1) / o.check_every + 1;
+  e.mv_hint = K;                      // active slots, known exactly on the host here
   while (true) {
     if (int rc = admm_round(e, o.check_every, max_iter, o.node_tol, false)) return rc;
     if (int rc = certify(e, nullptr, false)) return rc;
@@ -637,9 +648,11 @@ static int relax_impl(bnb_handle* h, Engine<R>& e, int K, const int8_t* dfix, co
     BNB_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
     BNB_CUDA_OK(cudaStreamSynchronize(st));
     ++rounds;
+    e.mv_hint = *h->h_cnt;
     if (*h->h_cnt == 0) break;
     if (rounds > max_rounds + 2) return fail(BNB_ETIMEOUT, "relax_batch did not retire all nodes");
   }
+  e.mv_hint = -1;
   // outputs
   BNB_CUDA_OK(cudaMemcpyAsync(lb, h->d_lb, sizeof(double) * K, cudaMemcpyDefault, st));
   if (br) BNB_CUDA_OK(cudaMemcpyAsync(br, h->d_br, sizeof(int) * K, cudaMemcpyDefault, st));
@@ -865,6 +878,9 @@ static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
       cudaGraphNodeGetType(nd, &t);
       kern += (t == cudaGraphNodeTypeKernel) ? 1 : 0;
     }
+    // a round with both ADMM forms runs one body of its conditional node: count the
+    // tensor-core body (the form of wide batches)
+    if constexpr (sizeof(R) == 4) kern += e.tc_body_kernels;
     h->stats.round_kernels = kern;
     ce = cudaGraphInstantiate(&S.exec, g, 0);
     cudaGraphDestroy(g);

@@ -15,6 +15,8 @@
 
 namespace bnb {
 
+constexpr int MV_MAX = 32;      // most active slots the matrix-vector round form handles
+constexpr int MV_ZMAX = 48;     // most contraction chunks of its partial products
 constexpr int SEL_BINS = 2048;  // radix-select histogram width
 
 struct Status {                 // copied to the host after every round
@@ -159,6 +161,14 @@ struct Engine {
   float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2
   int nbt = 0;                  // row tiles of the n x K products
   int sms = 148;                // multiprocessors of the device (persistent grids)
+  // narrow batches: matrix-vector round form (admm_mv.cu)
+  int mv_cross = 0;             // use it while the active slots are <= mv_cross (0: never)
+  int mv_hint = -1;             // active slots known on the host (-1: read from the device)
+  int* act_list = nullptr;      // [K] active slots in order
+  int* act_count = nullptr;
+  float* mv_part = nullptr;     // [MV_ZMAX][MV_MAX][n] partial products
+  cudaStream_t st_side = nullptr;  // capture of the conditional bodies
+  int mv_body_kernels = 0, tc_body_kernels = 0;
 
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;
@@ -180,6 +190,10 @@ template <class R> int queue_init(Engine<R>& e);
 template <class R> int queue_status(Engine<R>& e);
 template <class R> int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K);
 int admm_iterations_tc(Engine<float>& e, int iters);
+int admm_iterations_mv(Engine<float>& e, int iters);
+int mv_setup(Engine<float>& e);
+int act_list(Engine<float>& e);
+int capture_mv_or_tc(Engine<float>& e, int iters);
 template <class R> int root_heuristic(Engine<R>& e, int max_moves);
 int setup_tc(Engine<float>& e);
 

@@ -85,17 +85,17 @@ def test_dual_bound_full_size_sampled(prec):
 # ------------------------------------------------------------------ ADMM iteration
 
 
-def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed):
+def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed, tol=None, **kw):
     rng = np.random.default_rng(seed)
     fix = datagen.random_fixings(inst.p, K, rng, 20)
     wb = (rng.uniform(-M, M, (K, inst.p)) * (rng.random((K, inst.p)) < 0.05)).astype(np.float32)
     wb[fix == 0] = 0.0
     wv = rng.normal(0, 0.05, (K, inst.p)).astype(np.float32)
-    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1) as h:
+    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1, **kw) as h:
         out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
     assert np.all(out["iters"] == 1)
     data = admm.AdmmData(inst.X, inst.y, 1.0)
-    tol = ITER_TOL[prec]
+    tol = ITER_TOL[prec] if tol is None else tol
     for k in rows:
         b, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
                                          fix[k], lam0, lam2, M)
@@ -118,6 +118,55 @@ def test_one_admm_iteration_full_size_sampled(prec):
     """C2 shape at the bench width K=512; four sampled nodes against the oracle."""
     inst, lam0, lam2, M = _inst("c2", 0)
     _one_iteration_check(inst, lam0, lam2, M, prec, K=512, Kopt=512, rows=[0, 131, 300, 511], seed=4)
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_one_admm_iteration_narrow_batch_matches_oracle(prec):
+    """12 active nodes in a tensor-core handle: the matrix-vector round form (FP32 on the
+    FP32 data, so the FP32 tolerance applies in both precisions)."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=12, Kopt=64, rows=range(12), seed=8,
+                         tol=ITER_TOL[1])
+
+
+def test_one_admm_iteration_narrow_batch_full_size():
+    """c2 shape, 9 active nodes (partial slot group) through the matrix-vector form."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=9, Kopt=512, rows=[0, 4, 8], seed=9,
+                         tol=ITER_TOL[1], mv_crossover=32)
+
+
+def test_narrow_and_wide_forms_agree_on_converged_bounds():
+    """The same 20 nodes relaxed with the matrix-vector form (crossover 32) and with the
+    tensor-core form (crossover 0): both bounds valid, equal within the node tolerance."""
+    inst, lam0, lam2, M = _inst("c2_small", 2)
+    rng = np.random.default_rng(21)
+    fix = datagen.random_fixings(inst.p, 20, rng, 10)
+    outs = []
+    for cross in (32, 0):
+        with _handle(inst, lam0, lam2, M, 3, K=32, node_tol=1e-5, max_admm_iter=20000,
+                     mv_crossover=cross) as h:
+            outs.append(bnb.bnb_relax_batch(h, fix, max_iter=20000))
+    for k in range(20):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        for out in outs:
+            assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+            assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
+
+
+@pytest.mark.parametrize("cross", [0, 8, 32])
+def test_solve_same_answer_with_any_crossover(cross):
+    """Solves whose rounds switch between the narrow and wide forms on the device (CUDA-
+    graph conditional) return the stored optimum."""
+    case = json.load(open(GOLD))["cases"][0]
+    inst = datagen.config_instance("c1", case["instance"])
+    o = bnb.bnb_options_default(M=case["M"], precision=3, batch_K=32, node_tol=1e-7,
+                                max_admm_iter=5000, queue_capacity=1 << 16, time_limit_s=60.0,
+                                mv_crossover=cross)
+    with bnb.bnb_create(inst.X, inst.y, case["lambda0"], case["lambda2"], o) as h:
+        res = bnb.bnb_solve(h, case["gap"])
+    assert [int(i) for i in np.nonzero(res["beta"])[0]] == case["support"]
+    assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
 
 
 @pytest.mark.parametrize("prec", [3, 2])
