@@ -43,8 +43,8 @@ sys.path.insert(0, ROOT)
 import datagen  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-PREC = {"fp32": 1, "bf16": 2, "tc3": 3, "fp64": 0}
-DTYPE = {"fp32": "f32", "bf16": "bf16", "tc3": "bf16x3", "fp64": "f64"}
+PREC = {"fp32": 1, "bf16": 2, "tc3": 3, "fp64": 0, "bf16x2": 4}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "tc3": "bf16x3", "fp64": "f64", "bf16x2": "bf16x2"}
 SM_COUNT, FP32_LANES = 148, 128
 
 
@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--prime-seconds", type=float, default=90.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="tc3", choices=["fp32", "tc3", "bf16"])
+    ap.add_argument("--precision", default="tc3", choices=["fp32", "tc3", "bf16", "bf16x2"])
     ap.add_argument("--rho", type=float, default=0.0, help="0: chosen by the autotuner")
     ap.add_argument("--alpha", type=float, default=1.0, help="ADMM over-relaxation (autotuned with rho)")
     return ap.parse_args()
@@ -432,7 +432,7 @@ def roofline(out, args, pk):
                  peak_note="FP32 FMA peak 148 SM x 128 lanes x 2 x 2032 MHz (derived)")
     else:
         peak = float(pk.get("bf16_tflops_sustained", 1341.1))
-        mult = 3.0 if args.precision == "tc3" else 1.0
+        mult = {"tc3": 3.0, "bf16x2": 2.0}.get(args.precision, 1.0)
         r.update(bound="tensor", peak=peak, frac=ach / peak, achieved_hw=ach * mult,
                  frac_hw=ach * mult / peak,
                  peak_note="measured sustained dense BF16 (MEASURED_PEAKS.json)")

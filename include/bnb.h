@@ -44,6 +44,9 @@ extern "C" {
 #define BNB_PREC_FP32 1   /* FP32 state and contractions */
 #define BNB_PREC_BF16 2   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate/state */
 #define BNB_PREC_TC3 3    /* hi/lo BF16 pairs on tcgen05 (three products): FP32-class */
+#define BNB_PREC_BF16X2 4 /* X stored as one BF16 term, the ADMM iterates as hi/lo pairs
+                             (two products; G^-1 T with three): BF16 data, FP32-class
+                             iterates; certificates and polish use the FP64 data */
 
 /* bnb_solve status */
 #define BNB_STATUS_OPTIMAL 0     /* open-node set exhausted: UB is optimal */
@@ -256,8 +259,9 @@ int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int 
 /*
  * Diagnostics: the tcgen05 tensor-core contraction on its own.  C = A B^T with
  * A (M x Kd) and B (N x Kd) given K-major in FP64 device memory (element (m, k)
- * at A[k + m*Kd]), split into BF16 operands (nsplit 1: hi; 3: hi/lo pairs,
- * three products), tile width bn (128 or 256), `splits` split-K chunks summed
+ * at A[k + m*Kd]), split into BF16 operands (nsplit 1: hi; 2: A hi, B a hi/lo pair,
+ * two products; 3: hi/lo pairs, three products), tile width bn (128 or 256), `splits`
+ * split-K chunks summed
  * in order; C is M x N column-major FP32 (device).  *err_out (host) receives the
  * kernel's pipeline error word (0 when every bounded wait completed).
  */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libbnb.so")
 
 BNB_OK = 0
 BNB_EINVAL, BNB_ENOMEM, BNB_ECUDA, BNB_ETIMEOUT, BNB_EQUEUE, BNB_ENODEV = -1, -2, -3, -4, -5, -6
-BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16, BNB_PREC_TC3 = 0, 1, 2, 3
+BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16, BNB_PREC_TC3, BNB_PREC_BF16X2 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit",
                 5: "depth_limit"}
 

@@ -340,8 +340,8 @@ static int cred(Engine<float>& e, int bn, const TcOperand& A, const TcOperand& B
 template <int NS, int BN3, bool STATS>
 static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
   TcEpiAdmm<BN3, STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
-                            e.w_hi, NS == 3 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
-                            (STATS && NS == 3) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
+                            e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
+                            (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
                             e.nbm3, e.K};
   return tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, STATS>, 8>(e.st, XC, Uop, e.p, e.K, e.n, e.sms,
                                                            e.slot_active, e.tc_err, epi);
@@ -379,7 +379,7 @@ static int round_tc(Engine<float>& e, int iters) {
   const int kgrid = (int)(((long long)K * p + 255) / 256 > 8192 ? 8192 : ((long long)K * p + 255) / 256);
   prof_begin(e.prof, st);
   k_make_w<<<kgrid, 256, 0, st>>>(e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
-                                  e.w_hi, NS == 3 ? e.w_lo : nullptr);
+                                  e.w_hi, NS >= 2 ? e.w_lo : nullptr);
   prof_end(e.prof, st, PK_REDUCE_T);
   BNB_CUDA_OK(cudaGetLastError());
   for (int it = 0; it < iters; ++it) {
@@ -388,13 +388,14 @@ static int round_tc(Engine<float>& e, int iters) {
       // split-K reduced inside clusters, epilogues write the next operands directly
       prof_begin(e.prof, st);
       if (int rc = cred<NS>(e, e.tc_bn1, XT, Wop, n, K, p, e.tc_c1,
-                            TcEpiT{e.t_hi, NS == 3 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
+                            TcEpiT{e.t_hi, NS >= 2 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
         return rc;
       prof_end(e.prof, st, PK_GEMM_XW);
       prof_begin(e.prof, st);
-      if (int rc = cred<NS>(
+      // G^-1 T: both operands are pairs from the 2-term mode up (G^-1 is small)
+      if (int rc = cred<NS == 1 ? 1 : 3>(
               e, e.tc_bn2, GI, Top, n, K, n, e.tc_c2,
-              TcEpiU{e.u_hi, NS == 3 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
+              TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
                      (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
         return rc;
       prof_end(e.prof, st, PK_GEMM_GT);
@@ -406,7 +407,7 @@ static int round_tc(Engine<float>& e, int iters) {
       prof_end(e.prof, st, PK_GEMM_XW);
       prof_begin(e.prof, st);
       k_reduce_t_tc<<<red_grid, 256, 0, st>>>((float*)e.Tpart, e.tc_s1n, n, K, e.slot_active,
-                                              e.ldn, e.t_hi, NS == 3 ? e.t_lo : nullptr);
+                                              e.ldn, e.t_hi, NS >= 2 ? e.t_lo : nullptr);
       prof_end(e.prof, st, PK_REDUCE_T);
       prof_begin(e.prof, st);
       if (int rc = tc_gemm<BN, NS>(st, GI, Top, n, K, n, e.tc_s2, e.slot_active, e.tc_err,
@@ -416,7 +417,7 @@ static int round_tc(Engine<float>& e, int iters) {
       prof_begin(e.prof, st);
       k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.ucR,
                                          (float*)e.yR, n, K, e.slot_active, (float*)e.rstat,
-                                         e.ldn, e.u_hi, NS == 3 ? e.u_lo : nullptr);
+                                         e.ldn, e.u_hi, NS >= 2 ? e.u_lo : nullptr);
       prof_end(e.prof, st, PK_FINAL_U);
     }
     prof_begin(e.prof, st);
@@ -440,7 +441,8 @@ static int round_tc(Engine<float>& e, int iters) {
 }
 
 int admm_iterations_tc(Engine<float>& e, int iters) {
-  return e.tc_mode == 3 ? round_tc<3>(e, iters) : round_tc<1>(e, iters);
+  return e.tc_mode == 3 ? round_tc<3>(e, iters)
+                        : e.tc_mode == 2 ? round_tc<2>(e, iters) : round_tc<1>(e, iters);
 }
 
 // Setup of the BF16 operands: X in both layouts and G^{-1}, hi/lo
@@ -492,6 +494,9 @@ int setup_tc(Engine<float>& e) {
     const int st1 = (e.p + tc::BK - 1) / tc::BK, st2 = (e.n + tc::BK - 1) / tc::BK;
     if (e.tc_mode == 3) {
       cred_shape<3>(e.nbt, e.K, st1, &e.tc_bn1, &e.tc_c1);
+      cred_shape<3>(e.nbt, e.K, st2, &e.tc_bn2, &e.tc_c2);
+    } else if (e.tc_mode == 2) {
+      cred_shape<2>(e.nbt, e.K, st1, &e.tc_bn1, &e.tc_c1);
       cred_shape<3>(e.nbt, e.K, st2, &e.tc_bn2, &e.tc_c2);
     } else {
       cred_shape<1>(e.nbt, e.K, st1, &e.tc_bn1, &e.tc_c1);

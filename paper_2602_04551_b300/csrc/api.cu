@@ -122,7 +122,8 @@ static int allocate(Engine<R>& e) {
       ALLOC(e.act_list, K);
       ALLOC(e.act_count, 1);
       ALLOC(e.mv_part, (long long)MV_ZMAX * MV_MAX * n);
-      const bool lo = e.tc_mode == 3;
+      const bool xlo = e.tc_mode == 3;   // X as a hi/lo pair (3 terms)
+      const bool lo = e.tc_mode >= 2;    // iterates and G^-1 as pairs (2 and 3 terms)
       ALLOC(e.xc_hi, p * e.ldn);
       ALLOC(e.xt_hi, n * e.ldp);
       ALLOC(e.gi_hi, n * e.ldn);
@@ -130,9 +131,11 @@ static int allocate(Engine<R>& e) {
       ALLOC(e.b_hi, K * e.ldp);
       ALLOC(e.t_hi, K * e.ldn);
       ALLOC(e.u_hi, K * e.ldn);
-      if (lo) {
+      if (xlo) {
         ALLOC(e.xc_lo, p * e.ldn);
         ALLOC(e.xt_lo, n * e.ldp);
+      }
+      if (lo) {
         ALLOC(e.gi_lo, n * e.ldn);
         ALLOC(e.w_lo, K * e.ldp);
         ALLOC(e.b_lo, K * e.ldp);
@@ -440,6 +443,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   }
   if constexpr (sizeof(R) == 4) {
     if (o.precision == BNB_PREC_BF16) e->tc_mode = 1;
+    if (o.precision == BNB_PREC_BF16X2) e->tc_mode = 2;
     if (o.precision == BNB_PREC_TC3) e->tc_mode = 3;
   }
   if (int rc = allocate(*e)) return rc;
@@ -489,7 +493,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
-  if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_TC3)
+  if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
   auto t0 = std::chrono::steady_clock::now();
@@ -542,6 +546,7 @@ static size_t footprint_of(int n, int p, const bnb_options& o) {
   e.wcap = o.warm_capacity > 0 ? o.warm_capacity : wdef;
   if constexpr (sizeof(R) == 4) {
     if (o.precision == BNB_PREC_BF16) e.tc_mode = 1;
+    if (o.precision == BNB_PREC_BF16X2) e.tc_mode = 2;
     if (o.precision == BNB_PREC_TC3) e.tc_mode = 3;
   }
   size_t bytes = 0;

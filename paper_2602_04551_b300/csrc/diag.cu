@@ -75,7 +75,7 @@ static int make_operands(cudaStream_t st, const double* dA, const double* dB, in
 extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
                                          int nsplit, int cluster, float* dC, int* err_out) {
   using namespace bnb;
-  if (M <= 0 || N <= 0 || Kd <= 0 || (nsplit != 1 && nsplit != 3) || cluster < 1 || cluster > 8)
+  if (M <= 0 || N <= 0 || Kd <= 0 || nsplit < 1 || nsplit > 3 || cluster < 1 || cluster > 8)
     return BNB_EINVAL;
   cudaStream_t st = 0;
   const long long ld = ((long long)Kd + 7) / 8 * 8;
@@ -85,8 +85,9 @@ extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int
   if (!rc) rc = cudaMalloc(&err, sizeof(int)) == cudaSuccess ? 0 : BNB_ENOMEM;
   if (!rc) rc = cudaMemset(err, 0, sizeof(int)) == cudaSuccess ? 0 : BNB_ECUDA;
   TcOperand A{ah, al, M, Kd, ld}, B{bh, bl, N, Kd, ld};
-  if (!rc) rc = nsplit == 3 ? run_check_cluster<3>(st, A, B, M, N, Kd, cluster, dC, err)
-                            : run_check_cluster<1>(st, A, B, M, N, Kd, cluster, dC, err);
+  if (!rc) rc = nsplit == 3   ? run_check_cluster<3>(st, A, B, M, N, Kd, cluster, dC, err)
+                : nsplit == 2 ? run_check_cluster<2>(st, A, B, M, N, Kd, cluster, dC, err)
+                              : run_check_cluster<1>(st, A, B, M, N, Kd, cluster, dC, err);
   if (!rc) rc = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : BNB_ECUDA;
   if (!rc) rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : BNB_ECUDA;
   cudaFree(ah);
@@ -100,7 +101,7 @@ extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int
 extern "C" int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd,
                                  int nsplit, int bn, int splits, float* dC, int* dev_err) {
   using namespace bnb;
-  if (M <= 0 || N <= 0 || Kd <= 0 || (nsplit != 1 && nsplit != 3) || (bn != 128 && bn != 256))
+  if (M <= 0 || N <= 0 || Kd <= 0 || nsplit < 1 || nsplit > 3 || (bn != 128 && bn != 256))
     return BNB_EINVAL;
   cudaStream_t st = 0;
   const long long ld = ((long long)Kd + 7) / 8 * 8;
@@ -131,6 +132,8 @@ extern "C" int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int 
     if (bn == 128 && nsplit == 3) rc = run_check<128, 3>(st, A, B, M, N, Kd, splits, part, err, &ns);
     if (bn == 256 && nsplit == 1) rc = run_check<256, 1>(st, A, B, M, N, Kd, splits, part, err, &ns);
     if (bn == 256 && nsplit == 3) rc = run_check<256, 3>(st, A, B, M, N, Kd, splits, part, err, &ns);
+    if (bn == 128 && nsplit == 2) rc = run_check<128, 2>(st, A, B, M, N, Kd, splits, part, err, &ns);
+    if (bn == 256 && nsplit == 2) rc = run_check<256, 2>(st, A, B, M, N, Kd, splits, part, err, &ns);
   }
   if (!rc) {
     k_sum_splits_f32<<<256, 256, 0, st>>>(part, ns, (long long)M * N, dC);

@@ -15,7 +15,9 @@
 //                         alternate 16-column chunks), handed to the epilogue functor.
 // NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
 // accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
-// FP32-class arithmetic of the ADMM path.  NSPLIT = 1 is the plain BF16 product.
+// FP32-class arithmetic of the ADMM path.  NSPLIT = 2 keeps A as one BF16 term and B as
+// a pair (Ah Bh + Ah Bl: the data matrix stored in BF16, the iterates FP32-class).
+// NSPLIT = 1 is the plain BF16 product.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records an error code in
 // *err and leaves its loops, so a fault in the pipeline never hangs the GPU.
@@ -168,9 +170,12 @@ template <int BN, int NSPLIT>
 struct Geo {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (NSPLIT == 3 ? 2 : 1);
-  static constexpr int STAGES = (BN <= 64) ? (NSPLIT == 3 ? 2 : 4)          // ~100 KB: 2 CTAs per SM
-                                            : (NSPLIT == 3) ? (BN >= 256 ? 2 : 3) : (BN >= 256 ? 4 : 6);
+  // a stage holds [A hi | B hi], then [A lo | B lo] (3 terms) or [B lo] (2 terms)
+  static constexpr int STAGE_BYTES =
+      A_BYTES * (NSPLIT == 3 ? 2 : 1) + B_BYTES * (NSPLIT >= 2 ? 2 : 1);
+  static constexpr int SBUDGET = BN <= 64 ? 100 * 1024 : 196 * 1024;  // <= 64: 2 CTAs per SM
+  static constexpr int STAGES =
+      SBUDGET / STAGE_BYTES < 2 ? 2 : (SBUDGET / STAGE_BYTES > 6 ? 6 : SBUDGET / STAGE_BYTES);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;  // + alignment slack
   // persistent variant (one CTA per SM): as many stages as fit in ~200 KB
   static constexpr int PSTAGES = (200 * 1024) / STAGE_BYTES < 2 ? 2 : (200 * 1024) / STAGE_BYTES;
@@ -184,12 +189,19 @@ struct Maps {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;
 };
 
-// Operand ring of one CTA: stage s holds [A hi | B hi | A lo | B lo] (lo parts only for
-// the 3-term product).
+// Operand ring of one CTA: stage s holds [A hi | B hi | A lo | B lo] for the 3-term
+// product, [A hi | B hi | B lo] for the 2-term one (A single, B a hi/lo pair), and
+// [A hi | B hi] for the 1-term one.
 template <int BN, int NSPLIT>
 __device__ __forceinline__ uint8_t* ring_a(uint8_t* base, int s, int part) {
   using G = Geo<BN, NSPLIT>;
   return base + s * G::STAGE_BYTES + part * (G::A_BYTES + G::B_BYTES);
+}
+template <int BN, int NSPLIT>
+__device__ __forceinline__ uint8_t* ring_blo(uint8_t* base, int s) {
+  using G = Geo<BN, NSPLIT>;
+  return NSPLIT == 3 ? ring_a<BN, NSPLIT>(base, s, 1) + G::A_BYTES
+                     : base + s * G::STAGE_BYTES + G::A_BYTES + G::B_BYTES;
 }
 
 // TMA producer (one thread): nk K steps from kbeg, A rows m0.., B rows n0..
@@ -208,11 +220,8 @@ __device__ __forceinline__ void tma_producer(const CUtensorMap* ma_hi, const CUt
     uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
     tma_load_2d(a0, ma_hi, &full_bar[s], k, m0);
     tma_load_2d(a0 + G::A_BYTES, mb_hi, &full_bar[s], k, n0);
-    if (NSPLIT == 3) {
-      uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
-      tma_load_2d(a1, ma_lo, &full_bar[s], k, m0);
-      tma_load_2d(a1 + G::A_BYTES, mb_lo, &full_bar[s], k, n0);
-    }
+    if (NSPLIT >= 2) tma_load_2d(ring_blo<BN, NSPLIT>(base, s), mb_lo, &full_bar[s], k, n0);
+    if (NSPLIT == 3) tma_load_2d(ring_a<BN, NSPLIT>(base, s, 1), ma_lo, &full_bar[s], k, m0);
   }
 }
 
@@ -231,18 +240,15 @@ __device__ __forceinline__ void mma_issuer(uint32_t tmem, uint8_t* base, uint64_
     fence_after();
     uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
     uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+    uint8_t* b1 = ring_blo<BN, NSPLIT>(base, s);
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
       const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
       const uint64_t ah = smem_desc_sw128(a0 + kk * 32);
       const uint64_t bh = smem_desc_sw128(a0 + G::A_BYTES + kk * 32);
       mma_bf16(tmem, ah, bh, idesc, acc);
-      if (NSPLIT == 3) {
-        const uint64_t al = smem_desc_sw128(a1 + kk * 32);
-        const uint64_t bl = smem_desc_sw128(a1 + G::A_BYTES + kk * 32);
-        mma_bf16(tmem, ah, bl, idesc, 1u);
-        mma_bf16(tmem, al, bh, idesc, 1u);
-      }
+      if (NSPLIT >= 2) mma_bf16(tmem, ah, smem_desc_sw128(b1 + kk * 32), idesc, 1u);
+      if (NSPLIT == 3) mma_bf16(tmem, smem_desc_sw128(a1 + kk * 32), bh, idesc, 1u);
     }
     mma_commit(&empty_bar[s]);
   }
@@ -556,11 +562,10 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
         uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
         tma_load_2d(a0, &ma_hi, &full_bar[s], k, mt * BM);
         tma_load_2d(a0 + G::A_BYTES, &mb_hi, &full_bar[s], k, nt * BN);
-        if (NSPLIT == 3) {
-          uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
-          tma_load_2d(a1, &ma_lo, &full_bar[s], k, mt * BM);
-          tma_load_2d(a1 + G::A_BYTES, &mb_lo, &full_bar[s], k, nt * BN);
-        }
+        if (NSPLIT >= 2)
+          tma_load_2d(ring_blo<BN, NSPLIT>(base, s), &mb_lo, &full_bar[s], k, nt * BN);
+        if (NSPLIT == 3)
+          tma_load_2d(ring_a<BN, NSPLIT>(base, s, 1), &ma_lo, &full_bar[s], k, mt * BM);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -585,18 +590,15 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
         fence_after();
         uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
         uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+        uint8_t* b1 = ring_blo<BN, NSPLIT>(base, s);
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk) {
           const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
           const uint64_t ah = smem_desc_sw128(a0 + kk * 32);
           const uint64_t bh = smem_desc_sw128(a0 + G::A_BYTES + kk * 32);
           mma_bf16(acc_addr, ah, bh, idesc, acc);
-          if (NSPLIT == 3) {
-            const uint64_t al = smem_desc_sw128(a1 + kk * 32);
-            const uint64_t bl = smem_desc_sw128(a1 + G::A_BYTES + kk * 32);
-            mma_bf16(acc_addr, ah, bl, idesc, 1u);
-            mma_bf16(acc_addr, al, bh, idesc, 1u);
-          }
+          if (NSPLIT >= 2) mma_bf16(acc_addr, ah, smem_desc_sw128(b1 + kk * 32), idesc, 1u);
+          if (NSPLIT == 3) mma_bf16(acc_addr, smem_desc_sw128(a1 + kk * 32), bh, idesc, 1u);
         }
         mma_commit(&empty_bar[s]);
       }

@@ -45,13 +45,12 @@ int tc_gemm(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int 
   CUtensorMap ah, al, bh, bl;
   if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
   if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
-  if (NSPLIT == 3) {
+  al = ah;
+  bl = bh;
+  if (NSPLIT == 3)
     if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (NSPLIT >= 2)
     if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
-  } else {
-    al = ah;
-    bl = bh;
-  }
   int ns = 1;
   const int kchunk = tc_chunk(Kred, splits, &ns);
   auto kern = tc::tc_gemm_kernel<BN, NSPLIT, Epi, EPIW>;
@@ -133,13 +132,12 @@ int tc_gemm_cred(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M,
   CUtensorMap ah, al, bh, bl;
   if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
   if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
-  if (NSPLIT == 3) {
+  al = ah;
+  bl = bh;
+  if (NSPLIT == 3)
     if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (NSPLIT >= 2)
     if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
-  } else {
-    al = ah;
-    bl = bh;
-  }
   int ns = 1;
   const int kchunk = tc_chunk(Kred, cluster, &ns);
   auto kern = tc::tc_gemm_cred_kernel<BN, NSPLIT, Epi>;
@@ -175,13 +173,12 @@ int tc_gemm_persist(cudaStream_t st, const TcOperand& A, const TcOperand& B, int
   CUtensorMap ah, al, bh, bl;
   if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
   if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
-  if (NSPLIT == 3) {
+  al = ah;
+  bl = bh;
+  if (NSPLIT == 3)
     if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (NSPLIT >= 2)
     if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
-  } else {
-    al = ah;
-    bl = bh;
-  }
   auto kern = tc::tc_gemm_persist_kernel<BN, NSPLIT, Epi, EPIW>;
   static bool attr_set = false;
   if (!attr_set) {

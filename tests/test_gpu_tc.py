@@ -28,6 +28,8 @@ CASES = [
     (256, 256, 640, 3, 128, 1),
     (333, 77, 1111, 3, 128, 4),
     (128, 512, 4096, 3, 256, 2),
+    (200, 300, 1000, 2, 256, 3),      # 2 terms: A one BF16 term, B a pair
+    (333, 77, 1111, 2, 128, 1),
 ]
 
 
@@ -51,6 +53,8 @@ CLUSTER_CASES = [
     (300, 100, 1111, 3, 3),           # ragged M, N, K; cluster size not a power of two
     (129, 300, 200, 1, 8),            # more CTAs asked for than K steps: 4 chunks
     (257, 513, 777, 3, 2),
+    (1000, 512, 5000, 2, 4),          # 2 terms, the X W'^T shape
+    (300, 100, 1111, 2, 3),
 ]
 
 
@@ -78,6 +82,13 @@ def test_tc_gemm_cluster_is_deterministic():
 
 
 def _compare(A, B, C, nsplit):
+    if nsplit == 2:
+        # A rounded to one BF16 term (ties to even), B kept to ~16 bits by its pair
+        Ar = torch.from_numpy(_bf16(A.numpy()))
+        ref = (Ar @ B.T).numpy()
+        scale = (Ar.abs() @ B.abs().T).numpy()
+        assert np.all(np.abs(C - ref) <= 4e-5 * scale + 1e-6), np.max(np.abs(C - ref) / (scale + 1e-30))
+        return
     if nsplit == 1:
         Ar = torch.from_numpy(_bf16(A.numpy()))
         Br = torch.from_numpy(_bf16(B.numpy()))
