@@ -31,7 +31,7 @@ SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_dev
            "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_dual_bound_static",
            "bnb_get_stats", "bnb_get_histograms",
            "bnb_last_error", "bnb_destroy")
-STAGES = ("select_refill", "gemm_xw", "reduce_t", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
+STAGES = ("select_refill", "gemm_xw", "reduce_t_or_make_w", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status",
           "cert_screen", "cert_exact")
 

@@ -39,52 +39,6 @@ __global__ void k_make_w(const float* __restrict__ beta,
   }
 }
 
-// T = sum of split partials, as BF16 hi/lo (K x ldn), active slots only
-__global__ void k_reduce_t_tc(const float* __restrict__ part, int S, int n, int K,
-                              const int* __restrict__ active, long long ldn,
-                              __nv_bfloat16* __restrict__ thi, __nv_bfloat16* __restrict__ tlo) {
-  const long long m = (long long)n * K;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < m;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(idx / n), i = (int)(idx % n);
-    if (!active[s]) continue;
-    float a = part[idx];
-    for (int z = 1; z < S; ++z) a += part[z * m + idx];
-    split_store(a, thi, tlo, (long long)s * ldn + i);
-  }
-}
-
-// U' = sum of split partials, U = u_c + U' (FP32, n x K), BF16 hi/lo copy of U' (the
-// X^T U' operand); ||y - U||^2, y^T (y - U)
-__global__ void k_finalize_u_tc(const float* __restrict__ Upart, int S, float* __restrict__ U,
-                                const float* __restrict__ uc, const float* __restrict__ y, int n,
-                                int K,
-                                const int* __restrict__ active, float* __restrict__ rstat,
-                                long long ldn, __nv_bfloat16* __restrict__ uhi,
-                                __nv_bfloat16* __restrict__ ulo) {
-  __shared__ float sh[32];
-  const int s = blockIdx.x;
-  if (!active[s]) return;
-  const long long zs = (long long)n * K, base = (long long)s * n;
-  float rr = 0.f, yr = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float up = Upart[base + i];
-    for (int z = 1; z < S; ++z) up += Upart[z * zs + base + i];
-    const float u = uc[i] + up;
-    U[base + i] = u;
-    split_store(up, uhi, ulo, (long long)s * ldn + i);
-    const float r = y[i] - u;
-    rr += r * r;
-    yr += y[i] * r;
-  }
-  rr = block_sum(rr, sh);
-  yr = block_sum(yr, sh);
-  if (threadIdx.x == 0) {
-    rstat[s] = rr;
-    rstat[K + s] = yr;
-  }
-}
-
 // ---- epilogues of the cluster-reduced products (4 consecutive rows m.. of column n)
 
 __device__ __forceinline__ void split_store4(const float (&v)[4], __nv_bfloat16* hi,
@@ -364,10 +318,8 @@ static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop
 
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
-  constexpr int BN = 256;   // X W'^T, G^-1 T and X beta^T: wide tiles, split-K
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
-  const long long nK = (long long)n * K;
   const TcOperand XT{e.xt_hi, e.xt_lo, n, p, e.ldp};     // rows = samples, K = features
   const TcOperand XC{e.xc_hi, e.xc_lo, p, n, e.ldn};     // rows = features, K = samples
   const TcOperand GI{e.gi_hi, e.gi_lo, n, n, e.ldn};
@@ -375,51 +327,28 @@ static int round_tc(Engine<float>& e, int iters) {
   const TcOperand Top{e.t_hi, e.t_lo, K, n, e.ldn};
   const TcOperand Uop{e.u_hi, e.u_lo, K, n, e.ldn};
   const TcOperand Bop{e.b_hi, e.b_lo, K, p, e.ldp};
-  const int red_grid = (int)((nK + 255) / 256 > 4096 ? 4096 : (nK + 255) / 256);
   const int kgrid = (int)(((long long)K * p + 255) / 256 > 8192 ? 8192 : ((long long)K * p + 255) / 256);
   prof_begin(e.prof, st);
   k_make_w<<<kgrid, 256, 0, st>>>(e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
                                   e.w_hi, NS >= 2 ? e.w_lo : nullptr);
-  prof_end(e.prof, st, PK_REDUCE_T);
+  prof_end(e.prof, st, PK_REDUCE_T);   // (the operand formation takes the reduce_t stage)
   BNB_CUDA_OK(cudaGetLastError());
   for (int it = 0; it < iters; ++it) {
     const bool last = it + 1 == iters;
-    if (e.tc_c1 > 0) {
-      // split-K reduced inside clusters, epilogues write the next operands directly
-      prof_begin(e.prof, st);
-      if (int rc = cred<NS>(e, e.tc_bn1, XT, Wop, n, K, p, e.tc_c1,
-                            TcEpiT{e.t_hi, NS >= 2 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
-        return rc;
-      prof_end(e.prof, st, PK_GEMM_XW);
-      prof_begin(e.prof, st);
-      // G^-1 T: both operands are pairs from the 2-term mode up (G^-1 is small)
-      if (int rc = cred<NS == 1 ? 1 : 3>(
-              e, e.tc_bn2, GI, Top, n, K, n, e.tc_c2,
-              TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
-                     (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
-        return rc;
-      prof_end(e.prof, st, PK_GEMM_GT);
-    } else {
-      prof_begin(e.prof, st);
-      if (int rc = tc_gemm<BN, NS>(st, XT, Wop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
-                                   TcEpiStore{(float*)e.Tpart, (long long)n, nK}))
-        return rc;
-      prof_end(e.prof, st, PK_GEMM_XW);
-      prof_begin(e.prof, st);
-      k_reduce_t_tc<<<red_grid, 256, 0, st>>>((float*)e.Tpart, e.tc_s1n, n, K, e.slot_active,
-                                              e.ldn, e.t_hi, NS >= 2 ? e.t_lo : nullptr);
-      prof_end(e.prof, st, PK_REDUCE_T);
-      prof_begin(e.prof, st);
-      if (int rc = tc_gemm<BN, NS>(st, GI, Top, n, K, n, e.tc_s2, e.slot_active, e.tc_err,
-                                   TcEpiStore{(float*)e.Upart, (long long)n, nK}))
-        return rc;
-      prof_end(e.prof, st, PK_GEMM_GT);
-      prof_begin(e.prof, st);
-      k_finalize_u_tc<<<K, 256, 0, st>>>((float*)e.Upart, e.tc_s2n, (float*)e.U, (float*)e.ucR,
-                                         (float*)e.yR, n, K, e.slot_active, (float*)e.rstat,
-                                         e.ldn, e.u_hi, NS >= 2 ? e.u_lo : nullptr);
-      prof_end(e.prof, st, PK_FINAL_U);
-    }
+    // split-K reduced inside clusters, epilogues write the next operands directly
+    prof_begin(e.prof, st);
+    if (int rc = cred<NS>(e, e.tc_bn1, XT, Wop, n, K, p, e.tc_c1,
+                          TcEpiT{e.t_hi, NS >= 2 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
+      return rc;
+    prof_end(e.prof, st, PK_GEMM_XW);
+    prof_begin(e.prof, st);
+    // G^-1 T: both operands are pairs from the 2-term mode up (G^-1 is small)
+    if (int rc = cred<NS == 1 ? 1 : 3>(
+            e, e.tc_bn2, GI, Top, n, K, n, e.tc_c2,
+            TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
+                   (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
+      return rc;
+    prof_end(e.prof, st, PK_GEMM_GT);
     prof_begin(e.prof, st);
     if (int rc = fused_xtu<NS>(e, XC, Uop, last))
       return rc;
@@ -427,15 +356,9 @@ static int round_tc(Engine<float>& e, int iters) {
   }
   // check product X beta^T
   prof_begin(e.prof, st);
-  if (e.tc_c1 > 0) {
-    if (int rc = cred<NS>(e, e.tc_bn1, XT, Bop, n, K, p, e.tc_c1,
-                          TcEpiResid{e.slot_active, (const float*)e.yR, e.tc_stat, e.nbt, K, 1}))
-      return rc;
-  } else {
-    if (int rc = tc_gemm<BN, NS>(st, XT, Bop, n, K, p, e.tc_s1, e.slot_active, e.tc_err,
-                                 TcEpiStore{(float*)e.XBpart, (long long)n, nK}))
-      return rc;
-  }
+  if (int rc = cred<NS>(e, e.tc_bn1, XT, Bop, n, K, p, e.tc_c1,
+                        TcEpiResid{e.slot_active, (const float*)e.yR, e.tc_stat, e.nbt, K, 1}))
+    return rc;
   prof_end(e.prof, st, PK_CHECK);
   return 0;
 }
