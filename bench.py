@@ -170,9 +170,11 @@ def run_mine(args, rank, world):
     tune = None
     if args.rho <= 0:
         from paper_2602_04551_b300 import autotune
+        # (the timed rounds are wide batches: the narrow-form crossover does not enter)
         best, entry = autotune.autotune(inst.X, inst.y, lam0, lam2, M, device=dev, use_cache=False,
                                         grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
-                                              "check_every": [args.check_every]})
+                                              "check_every": [args.check_every]},
+                                        tune_crossover=False)
         args.rho = float(best["rho"])
         args.alpha = float(best.get("relax_alpha", 1.0))
         tune = {"chosen": best, "seconds": entry["seconds"],
@@ -471,6 +473,7 @@ def run_solves(args):
         o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                     precision=PREC[args.precision], rho=best["rho"],
                                     relax_alpha=best["relax_alpha"], queue_capacity=1 << 21,
+                                    mv_crossover=int(best.get("mv_crossover", -1)),
                                     max_depth=args.max_depth, time_limit_s=args.solve_time_limit)
         with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
             torch.cuda.synchronize()
@@ -483,7 +486,8 @@ def run_solves(args):
                "status": res["status"], "nodes": res["nodes"],
                "nnz": int(np.count_nonzero(res["beta"])), "ub": res["ub"], "lb": res["lb"],
                "gap": (res["ub"] - res["lb"]) / res["ub"], "nodes_per_s": res["nodes"] / dt,
-               "rho": best["rho"], "relax_alpha": best["relax_alpha"], "max_depth": st["max_depth"],
+               "rho": best["rho"], "relax_alpha": best["relax_alpha"],
+               "mv_crossover": best.get("mv_crossover"), "max_depth": st["max_depth"],
                # solved nodes by depth 0..40 (+ deeper) and by rounded-support size 0..200 (+ larger)
                "depth_hist": [int(x) for x in dh[:41]] + [int(dh[41:].sum())],
                "support_hist": [int(x) for x in sh[:201]] + [int(sh[201:].sum())]}

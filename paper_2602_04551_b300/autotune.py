@@ -7,6 +7,10 @@ depth, the shape of the nodes the tree produces) through bnb_relax_batch_device,
 timed with CUDA events on the handle's stream.  The score is certified nodes per
 second; the mean FP64 bound of the batch is recorded so that a mode whose bounds
 are markedly weaker (e.g. plain BF16) is not chosen for speed alone.
+A second, short measurement picks the crossover below which a round runs the
+narrow matrix-vector form instead of tensor-core tiles (mv_crossover): batches of 4 to
+32 children are timed with the narrow form forced on and off, and the crossover is the
+largest width at which it is faster.
 Results are cached in a JSON file keyed by (n, p) bucket.
 """
 from __future__ import annotations
@@ -48,10 +52,11 @@ def _children(p, K, seed, depth=8):
     return fix
 
 
-def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0):
+def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0, nodes=None):
+    """Time the root plus a batch of `nodes` (default batch_K) warm-started children."""
     import torch
     import paper_2602_04551_b300 as bnb
-    K = int(opts["batch_K"])
+    K = int(opts["batch_K"]) if nodes is None else int(nodes)
     p = X.shape[1]
     s = torch.cuda.Stream(device=device)
     o = bnb.bnb_options_default(M=M, device=device, stream=s.cuda_stream, **opts)
@@ -76,7 +81,22 @@ def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0):
                 "lb_mean": float(dlb.mean())}
 
 
-def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol=1e-3):
+def crossover(X, y, lam0, lam2, M, opts: dict, device=0, widths=(4, 8, 16, 32)):
+    """Largest batch width (<= 32) at which the narrow matrix-vector form beats the
+    tensor-core form on `widths`-node batches; 0 when it never does."""
+    best = 0
+    rows = []
+    for w in widths:
+        narrow = trial(X, y, lam0, lam2, M, dict(opts, mv_crossover=32), device=device, nodes=w)
+        wide = trial(X, y, lam0, lam2, M, dict(opts, mv_crossover=0), device=device, nodes=w)
+        rows.append({"width": w, "narrow_ms": narrow["ms"], "wide_ms": wide["ms"]})
+        if narrow["ms"] < wide["ms"]:
+            best = w
+    return best, rows
+
+
+def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol=1e-3,
+             tune_crossover=True):
     grid = dict(DEFAULT_GRID, **(grid or {}))
     n, p = X.shape
     key = _key(n, p, grid)
@@ -99,8 +119,12 @@ def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol
     best_lb = max(r["lb_mean"] for _, r in results)
     ok = [(o, r) for o, r in results if r["lb_mean"] >= best_lb - bound_tol * max(1.0, abs(best_lb))]
     best, br = max(ok, key=lambda t: t[1]["nodes_per_s"])
+    best = dict(best)
+    cross_rows = []
+    if tune_crossover and best.get("precision", 3) in (2, 3, 4):
+        best["mv_crossover"], cross_rows = crossover(X, y, lam0, lam2, M, best, device=device)
     entry = {"best": best, "score": br, "trials": [dict(o, **r) for o, r in results],
-             "seconds": time.time() - t0}
+             "crossover": cross_rows, "seconds": time.time() - t0}
     if use_cache:
         cache[key] = entry
         os.makedirs(os.path.dirname(path), exist_ok=True)
