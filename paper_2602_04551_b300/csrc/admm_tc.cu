@@ -2,15 +2,18 @@
 //
 // Same iteration as admm.cu (Sections 3.1-3.2; Woodbury b-update on the shifted
 // operand W' = rho beta - V), with the three contractions on the tensor cores:
-//   T  = X W'^T      tcgen05, A = X row-major (n x p, K-major), B = W' (K x p), split-K
-//   U' = G^{-1} T    tcgen05, A = G^{-1} (symmetric), B = T (K x n), split-K
-//   P  = X^T U'      tcgen05, A = X column-major (p x n, K-major), B = U' (K x n),
+//   T  = X W'^T      A = X row-major (n x p, K-major), B = W' (K x p); K split over a
+//                    cluster and reduced through DSMEM; epilogue: T as the BF16 operand
+//   U' = G^{-1} T    A = G^{-1} (symmetric), B = T (K x n), same scheme; epilogue: U', and
+//                    on the round's last iteration U = u_c + U' and ||y - U||^2, y^T(y - U)
+//   P  = X^T U'      A = X column-major (p x n, K-major), B = U' (K x n), persistent,
 //                    fused epilogue straight from tensor memory:
 //                    b = b_c + (W' - P)/rho, beta = prox(b + V/rho), V += rho (b - beta),
 //                    per-slot stop-test sums, and the next iteration's W' operand.
-// Operands are BF16; in the FP32-class mode each operand is a hi/lo pair and the
-// product takes three MMAs (hi hi + hi lo + lo hi), in the BF16 mode one.
-// Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.
+// Operands are BF16: TC3 stores each as a hi/lo pair (three MMAs: hi hi + hi lo + lo hi),
+// BF16X2 keeps X as one term and the iterates as pairs (two), BF16 uses one term.
+// Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.  Tile
+// widths and cluster sizes are chosen at setup (setup_tc).
 #include <cuda_bf16.h>
 #include "engine.cuh"
 #include "gemm_simt.cuh"

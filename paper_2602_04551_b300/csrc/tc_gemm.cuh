@@ -2,7 +2,7 @@
 //
 //   C[m, n] = sum_{k in chunk z} A[m, k] B[n, k]        (both operands K-major, BF16)
 //
-// Tiles of 128 x BN outputs, 64-wide K steps.  One CTA = 6 warps:
+// Tiles of 128 x BN outputs, 64-wide K steps.  One CTA = 2 + EPIW warps:
 //   warp 0  (one thread)  TMA producer: cp.async.bulk.tensor 2D loads of the A and B
 //                         tiles (128-byte swizzle) into an S-stage shared-memory ring,
 //                         completion counted on the stage's "full" mbarrier;
@@ -10,9 +10,17 @@
 //                         128 x BN accumulator in tensor memory; tcgen05.commit frees a
 //                         stage ("empty" mbarrier) and finally signals "done";
 //                         the whole warp allocates / frees the TMEM columns;
-//   warps 2-9             epilogue: tcgen05.ld of the accumulator rows (a warp reads its
-//                         32-lane quarter of TMEM, the two warps of a quarter take
+//   warps 2..             epilogue: tcgen05.ld of the accumulator rows (a warp reads its
+//                         32-lane quarter of TMEM, the warps of a quarter take
 //                         alternate 16-column chunks), handed to the epilogue functor.
+// Three kernel shapes share the producer and MMA code:
+//   tc_gemm_kernel          one tile per CTA, split-K partials stored (diagnostics);
+//   tc_gemm_cred_kernel     K split over the CTAs of a thread-block cluster, partial tiles
+//                           summed through distributed shared memory in rank order, fused
+//                           epilogue on the sum (X W'^T, G^-1 T, the check product);
+//   tc_gemm_persist_kernel  one CTA per SM over the tiles, double-buffered accumulator so
+//                           the epilogue of a tile overlaps the next tile (X^T U' with the
+//                           fused ADMM update).
 // NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
 // accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
 // FP32-class arithmetic of the ADMM path.  NSPLIT = 2 keeps A as one BF16 term and B as
