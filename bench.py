@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--fp64-time-limit", type=float, default=60.0)
     ap.add_argument("--seeds", type=int, default=1, help="solves mode: instances per lambda0")
     ap.add_argument("--max-depth", type=int, default=1024)
+    ap.add_argument("--mv-crossover", type=int, default=-1,
+                    help="narrow-form crossover (-1 default; 0 = tensor-core form only: graphs "
+                         "without conditional nodes, which ncu can profile kernel by kernel)")
     ap.add_argument("--k-list", default="1,4,16,64,256,512",
                     help="kcurve mode: batch widths; each solve runs --solve-time-limit seconds")
     ap.add_argument("--lam0-frac", type=float, default=0.02)
@@ -184,7 +187,7 @@ def run_mine(args, rank, world):
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
                                   queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
-                                  relax_alpha=args.alpha)
+                                  relax_alpha=args.alpha, mv_crossover=args.mv_crossover)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4

@@ -4,6 +4,9 @@
 
 Used for the ncu captures of the top kernels (small enough that the capture ends in
 a minute or two; the c4 shape keeps X and the node state larger than the L2 cache).
+ncu does not profile the kernels of a CUDA graph that contains conditional nodes, so
+captures run with --mv-crossover 0 (wide rounds: the tensor-core form, no conditional
+node) or --no-graphs (the narrow matrix-vector form launched directly).
 """
 import argparse
 import os
@@ -29,13 +32,16 @@ def main():
     ap.add_argument("--precision", type=int, default=3)
     ap.add_argument("--rounds", type=int, default=3)
     ap.add_argument("--prime-seconds", type=float, default=30.0)
+    ap.add_argument("--mv-crossover", type=int, default=-1)
+    ap.add_argument("--no-graphs", action="store_true")
     a = ap.parse_args()
     c = datagen.CONFIGS[a.workload]
     inst = datagen.config_instance(a.workload, 0)
     M = datagen.big_m(inst.X, inst.y, inst.support_true, c["lam2"])
     lam0 = a.lam0_frac * datagen.lambda0_scale(inst.X, inst.y, c["lam2"])
     o = bnb.bnb_options_default(M=M, batch_K=a.K, rho=a.rho, precision=a.precision,
-                                queue_capacity=1 << 20, time_limit_s=1e9)
+                                queue_capacity=1 << 20, time_limit_s=1e9,
+                                mv_crossover=a.mv_crossover, use_graphs=0 if a.no_graphs else 1)
     with bnb.bnb_create(inst.X, inst.y, lam0, c["lam2"], o) as h:
         bnb.bnb_solve_start(h, 1e-4)
         t0 = time.time()
