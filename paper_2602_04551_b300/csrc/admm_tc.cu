@@ -300,8 +300,28 @@ static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& 
                             e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
                             (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
                             e.nbm3, e.K};
+  if (e.tc_mc3 > 0)   // clusters of two CTAs sharing the X tile
+    return tc_gemm_persist_mc<BN3, NS, TcEpiAdmm<BN3, STATS>, 8>(
+        e.st, XC, Uop, e.p, e.K, e.n, e.tc_mc3, e.slot_active, e.tc_err, epi);
   return tc_gemm_persist<BN3, NS, TcEpiAdmm<BN3, STATS>, 8>(e.st, XC, Uop, e.p, e.K, e.n, e.sms,
                                                            e.slot_active, e.tc_err, epi);
+}
+
+template <int NS, int BN3>
+static int mc_clusters_bn() {
+  const int a = tc_persist_mc_clusters<BN3, NS, TcEpiAdmm<BN3, false>, 8>();
+  const int b = tc_persist_mc_clusters<BN3, NS, TcEpiAdmm<BN3, true>, 8>();
+  return a < b ? a : b;
+}
+
+template <int NS>
+static int mc_clusters(int bn) {
+  switch (bn) {
+    case 80: return mc_clusters_bn<NS, 80>();
+    case 96: return mc_clusters_bn<NS, 96>();
+    case 128: return mc_clusters_bn<NS, 128>();
+    default: return mc_clusters_bn<NS, 64>();
+  }
 }
 
 template <int NS>
@@ -445,6 +465,14 @@ int setup_tc(Engine<float>& e) {
       }
     }
     if (best < 0) return BNB_EINVAL;
+    // pairs of column tiles share the X tile through cluster multicast when the device
+    // co-schedules clusters of two and there are two column tiles to pair
+    e.tc_mc3 = 0;
+    if ((e.K + e.tc_bn3 - 1) / e.tc_bn3 >= 2) {
+      const int c = e.tc_mode == 3 ? mc_clusters<3>(e.tc_bn3)
+                  : e.tc_mode == 2 ? mc_clusters<2>(e.tc_bn3) : mc_clusters<1>(e.tc_bn3);
+      e.tc_mc3 = c > e.sms / 2 ? e.sms / 2 : c;
+    }
   }
   const long long n = e.n, p = e.p;
   // column-major X: p columns of length n (leading dimension ldn)

@@ -124,6 +124,24 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+// multicast variants (thread-block cluster): the TMA box lands at the same shared-memory
+// offset in every CTA of `mask`, each CTA's mbarrier at that offset counting the bytes;
+// the commit arrives on the mbarrier at the same offset in every CTA of `mask`
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                               int c0, int c1, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -655,6 +673,199 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
   }
   fence_before();
   __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(2 * G::PBUF)
+                 : "memory");
+  }
+}
+
+
+// Persistent kernel in clusters of two CTAs that share the A tile: the cluster walks
+// units (row tile mt, column-tile pair ntp); CTA rank r computes the tile (mt, 2 ntp + r),
+// loads rows [64 r, 64 r + 64) of the A tile and multicasts them to both CTAs, and loads
+// its own B tile.  Each A tile therefore crosses L2 once per pair of column tiles
+// instead of once per column tile.  A stage is refilled only after both CTAs' MMAs
+// released it (its "empty" barrier counts the two commits, which are multicast).
+// Barriers are initialised on both CTAs before any remote signal (cluster barrier) and
+// neither CTA leaves while the other may still signal it (cluster barrier at the end);
+// every thread reaches both cluster barriers.  The A tensor maps have 64-row boxes.
+template <int BN, int NSPLIT, class Epi, int EPIW>
+__global__ void __launch_bounds__(64 + 32 * EPIW, 1)
+tc_gemm_persist_mc_kernel(const __grid_constant__ CUtensorMap ma_hi,
+                          const __grid_constant__ CUtensorMap ma_lo,
+                          const __grid_constant__ CUtensorMap mb_hi,
+                          const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred,
+                          const int* __restrict__ active, int* err, Epi epi) {
+  using G = Geo<BN, NSPLIT>;
+  constexpr int S = G::PSTAGES;
+  constexpr int MAXNT = 64;
+  constexpr int AH = G::A_BYTES / 2;             // 64 rows x 128 bytes
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N: a multiple of 16 up to 256");
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int tile_on[MAXNT];
+  __shared__ float epi_smem[Epi::SMEM_FLOATS > 0 ? Epi::SMEM_FLOATS : 1];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = (int)cluster_rank();
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int mtiles = (M + BM - 1) / BM, ntiles = (N + BN - 1) / BN;
+  const int npairs = (ntiles + 1) / 2;
+  const int nunits = mtiles * npairs;
+  const int nk = (Kred + BK - 1) / BK;
+  for (int j = threadIdx.x; j < MAXNT; j += blockDim.x) {
+    int on = 0;
+    if (j < ntiles) {
+      for (int c = 0; c < BN && j * BN + c < N; ++c)
+        if (active == nullptr || active[j * BN + c]) {
+          on = 1;
+          break;
+        }
+    }
+    tile_on[j] = on;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 2);             // both CTAs' MMA commits
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], EPIW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(2 * G::PBUF)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  cluster_sync_all();                            // both CTAs' barriers exist
+  const uint32_t tmem = tmem_slot;
+  auto unit_on = [&](int ntp) {
+    return tile_on[2 * ntp] || (2 * ntp + 1 < ntiles && tile_on[2 * ntp + 1]);
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    long long g = 0;
+    bool ok = true;
+    for (int u = cid; u < nunits && ok; u += ncl) {
+      const int mt = u % mtiles, ntp = u / mtiles;
+      if (!unit_on(ntp)) continue;
+      const int nt = 2 * ntp + rank;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)(((g / S) & 1) ^ 1), err, 1)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], G::STAGE_BYTES);
+        const int k = kb * BK;
+        uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+        tma_load_2d_mc(a0 + rank * AH, &ma_hi, &full_bar[s], k, mt * BM + 64 * rank, 3);
+        tma_load_2d(a0 + G::A_BYTES, &mb_hi, &full_bar[s], k, nt * BN);
+        if (NSPLIT >= 2)
+          tma_load_2d(ring_blo<BN, NSPLIT>(base, s), &mb_lo, &full_bar[s], k, nt * BN);
+        if (NSPLIT == 3)
+          tma_load_2d_mc(ring_a<BN, NSPLIT>(base, s, 1) + rank * AH, &ma_lo, &full_bar[s], k,
+                         mt * BM + 64 * rank, 3);
+      }
+    }
+    // every copy this CTA issued has landed before the cluster may be left (after an
+    // error the MMA may not have consumed them); bounded like every wait
+    for (long long j = g - S < 0 ? 0 : g - S; j < g; ++j)
+      mbar_wait(&full_bar[(int)(j % S)], (uint32_t)((j / S) & 1), err, 16);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BN);
+    long long g = 0;
+    int i = 0;
+    bool ok = true;
+    for (int u = cid; u < nunits && ok; u += ncl) {
+      const int ntp = u / mtiles;
+      if (!unit_on(ntp)) continue;
+      const int b = i & 1;
+      if (i >= 2 && !mbar_wait(&tempty_bar[b], (uint32_t)(((i >> 1) & 1) ^ 1), err, 8)) break;
+      fence_after();
+      const uint32_t acc_addr = tmem + (uint32_t)(b * G::PBUF);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (!mbar_wait(&full_bar[s], (uint32_t)((g / S) & 1), err, 2)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        uint8_t* a0 = ring_a<BN, NSPLIT>(base, s, 0);
+        uint8_t* a1 = ring_a<BN, NSPLIT>(base, s, 1);
+        uint8_t* b1 = ring_blo<BN, NSPLIT>(base, s);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ah = smem_desc_sw128(a0 + kk * 32);
+          const uint64_t bh = smem_desc_sw128(a0 + G::A_BYTES + kk * 32);
+          mma_bf16(acc_addr, ah, bh, idesc, acc);
+          if (NSPLIT >= 2) mma_bf16(acc_addr, ah, smem_desc_sw128(b1 + kk * 32), idesc, 1u);
+          if (NSPLIT == 3) mma_bf16(acc_addr, smem_desc_sw128(a1 + kk * 32), bh, idesc, 1u);
+        }
+        mma_commit_mc(&empty_bar[s], 3);         // frees stage s in both CTAs
+      }
+      mma_commit(&tfull_bar[b]);
+      ++i;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue warps (own tile of each unit)
+    const int q = warp & 3;
+    const int gq = (warp - 2) >> 2;
+    int i = 0;
+    for (int u = cid; u < nunits; u += ncl) {
+      const int mt = u % mtiles, ntp = u / mtiles;
+      if (!unit_on(ntp)) continue;
+      const int nt = 2 * ntp + rank;
+      const int b = i & 1;
+      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4);
+      fence_after();
+      const int m0 = mt * BM, n0 = nt * BN;
+      const int row = m0 + 32 * q + lane;
+      if (ok && n0 < N) {
+#pragma unroll 1
+        for (int c = 16 * gq; c < BN; c += 16 * (EPIW / 4)) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::PBUF + c), v);
+          epi(row, n0 + c, v, M, N, q, epi_smem);
+        }
+      }
+      fence_before();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty_bar[b]))
+                     : "memory");
+      uint32_t all_ok;
+      asm volatile(
+          "{\n .reg .pred p, r;\n setp.ne.u32 p, %1, 0;\n"
+          " bar.red.and.pred r, 1, %2, p;\n selp.u32 %0, 1, 0, r;\n}\n"
+          : "=r"(all_ok)
+          : "r"((uint32_t)ok), "n"(32 * EPIW)
+          : "memory");
+      if (all_ok && n0 < N) epi.finish(threadIdx.x - 64, 32 * EPIW, m0, n0, M, N, epi_smem);
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPIW) : "memory");
+      ++i;
+      if (!all_ok) break;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();                            // no remote signal can still arrive
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

@@ -192,6 +192,81 @@ int tc_gemm_persist(cudaStream_t st, const TcOperand& A, const TcOperand& B, int
   return 0;
 }
 
+// Co-resident clusters of two of the multicast persistent kernel (0: none).
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
+int tc_persist_mc_clusters() {
+  using G = tc::Geo<BN, NSPLIT>;
+  static int cached = -1;
+  if (cached < 0) {
+    auto kern = tc::tc_gemm_persist_mc_kernel<BN, NSPLIT, Epi, EPIW>;
+    cached = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::PSMEM) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(64 + 32 * EPIW);
+    cfg.dynamicSmemBytes = G::PSMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      nc = 0;
+    }
+    cached = nc;
+  }
+  return cached;
+}
+
+// Persistent product in clusters of two sharing the A tile (tc_gemm_persist_mc_kernel):
+// `clusters` co-resident clusters at most.
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
+int tc_gemm_persist_mc(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N,
+                       int Kred, int clusters, const int* active, int* err, Epi epi) {
+  using G = tc::Geo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  if (N > 64 * BN || clusters < 1) return BNB_EINVAL;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM / 2)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN)) return rc;
+  al = ah;
+  bl = bh;
+  if (NSPLIT == 3)
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM / 2)) return rc;
+  if (NSPLIT >= 2)
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN)) return rc;
+  auto kern = tc::tc_gemm_persist_mc_kernel<BN, NSPLIT, Epi, EPIW>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::PSMEM));
+    attr_set = true;
+  }
+  const long long units = (long long)((M + tc::BM - 1) / tc::BM) * (((N + BN - 1) / BN + 1) / 2);
+  const int ncl = (int)(units < clusters ? units : clusters);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * ncl);
+  cfg.blockDim = dim3(64 + 32 * EPIW);
+  cfg.dynamicSmemBytes = G::PSMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, active, err, epi));
+  return 0;
+}
+
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;
