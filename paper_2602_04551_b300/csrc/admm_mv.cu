@@ -103,7 +103,17 @@ __global__ void __launch_bounds__(256) k_mv_part(const float* __restrict__ A, lo
     if (i < M) {
       const int jn = min(MV_TJ, j1 - jb);
       const float* ap = A + (long long)jb * lda + i;
-      for (int jj = 0; jj < jn; ++jj) {
+      int jj = 0;
+      for (; jj + 4 <= jn; jj += 4) {          // four independent column loads in flight
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = ap[(long long)(jj + u) * lda];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < MV_G; ++c) acc[c] = fmaf(x[u], vs[c][jj + u], acc[c]);
+      }
+      for (; jj < jn; ++jj) {
         const float x = ap[(long long)jj * lda];
 #pragma unroll
         for (int c = 0; c < MV_G; ++c) acc[c] = fmaf(x, vs[c][jj], acc[c]);
