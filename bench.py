@@ -233,8 +233,10 @@ def run_mine(args, rank, world):
     kernels_per_round = stats.get("round_kernels", 0)
     res = bnb.bnb_solve_finish(h)
     h.close()
+    shapes = {k: stats.get(k) for k in ("xw_tile_width", "xw_cluster", "fused_tile_width",
+                                          "fused_clusters")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
-               kernels=kernels_per_round * args.steps, after=after, res=res,
+               kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
                       "active_slots": before["active_slots"], "open_nodes": before["open_nodes"]})
     if rank == 0:
@@ -678,6 +680,7 @@ def main():
                                "lb": out["after"]["lb"], "open_nodes": out["after"]["open_nodes"],
                                "done": out["after"]["done"]},
             "stages_ms": {k: v[0] for k, v in out["prof"].items()},
+            "kernel_shapes": out["shapes"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -291,6 +291,10 @@ typedef struct {
   double setup_seconds;     /* wall time of bnb_create */
   double final_ub, final_lb;
   int round_kernels;        /* kernels in one captured round (CUDA graph) */
+  /* tensor-core shapes chosen at creation (0 for the CUDA-core precisions): output tile
+     width and cluster size of X W'^T, tile width of the fused X^T U' product and the
+     number of two-CTA clusters it runs in (0: one CTA per tile) */
+  int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters;
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

@@ -56,7 +56,9 @@ class bnb_stats(ctypes.Structure):
                 ("pool_peak", ctypes.c_longlong), ("max_depth", ctypes.c_int),
                 ("solve_seconds", ctypes.c_double), ("setup_seconds", ctypes.c_double),
                 ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double),
-                ("round_kernels", ctypes.c_int)]
+                ("round_kernels", ctypes.c_int), ("xw_tile_width", ctypes.c_int),
+                ("xw_cluster", ctypes.c_int), ("fused_tile_width", ctypes.c_int),
+                ("fused_clusters", ctypes.c_int)]
 
 
 class bnb_progress(ctypes.Structure):

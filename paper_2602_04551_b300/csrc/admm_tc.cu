@@ -14,6 +14,9 @@
 // BF16X2 keeps X as one term and the iterates as pairs (two), BF16 uses one term.
 // Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.  Tile
 // widths and cluster sizes are chosen at setup (setup_tc).
+#include <algorithm>
+#include <utility>
+#include <vector>
 #include <cuda_bf16.h>
 #include "engine.cuh"
 #include "gemm_simt.cuh"
@@ -428,6 +431,70 @@ static void cred_shape(int nbt, int K, int steps, int* bn, int* cs) {
   }
 }
 
+// Tile width and form of the fused X^T U' product (one CTA per tile, or clusters of two
+// sharing the X tile), measured: the kernel streams operand tiles and node state through
+// L2 and overlaps its epilogue with the next tile, so no simple count of bytes ranks the
+// candidates reliably.  Each candidate runs on the handle's stream with every slot
+// marked active (the work does not depend on the values), timed with CUDA events; the
+// state the runs wrote is cleared afterwards.
+template <int NS>
+static int pick_fused_shape(Engine<float>& e) {
+  cudaStream_t st = e.st;
+  const TcOperand XC{e.xc_hi, e.xc_lo, e.p, e.n, e.ldn};
+  const TcOperand Uop{e.u_hi, e.u_lo, e.K, e.n, e.ldn};
+  std::vector<std::pair<int, int>> cands;
+  for (int w : {64, 80, 96, 128}) {
+    if (e.K > 64 * w) continue;
+    cands.push_back({w, 0});
+    if ((e.K + w - 1) / w >= 2) {
+      int cl = mc_clusters<NS>(w);
+      if (cl > e.sms / 2) cl = e.sms / 2;
+      if (cl >= 1) cands.push_back({w, cl});
+    }
+  }
+  if (cands.empty()) return BNB_EINVAL;
+  e.tc_bn3 = cands[0].first;
+  e.tc_mc3 = cands[0].second;
+  if (cands.size() == 1) return 0;
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0xff, sizeof(int) * e.K, st));   // nonzero: active
+  cudaEvent_t ev[2];
+  BNB_CUDA_OK(cudaEventCreate(&ev[0]));
+  BNB_CUDA_OK(cudaEventCreate(&ev[1]));
+  float best = -1.f;
+  std::pair<int, int> pick = cands[0];
+  int rc = 0;
+  for (const auto& c : cands) {
+    e.tc_bn3 = c.first;
+    e.tc_mc3 = c.second;
+    if ((rc = fused_xtu<NS>(e, XC, Uop, false))) break;          // warm-up
+    cudaEventRecord(ev[0], st);
+    for (int r = 0; r < 3 && !rc; ++r) rc = fused_xtu<NS>(e, XC, Uop, false);
+    cudaEventRecord(ev[1], st);
+    if (rc || cudaEventSynchronize(ev[1]) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (best < 0 || ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  e.tc_bn3 = pick.first;
+  e.tc_mc3 = pick.second;
+  const long long Kp = (long long)e.K * e.p;
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.beta, 0, sizeof(float) * Kp, st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.V, 0, sizeof(float) * Kp, st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.w_hi, 0, 2 * (size_t)e.K * e.ldp, st));
+  if (e.w_lo) BNB_CUDA_OK(cudaMemsetAsync(e.w_lo, 0, 2 * (size_t)e.K * e.ldp, st));
+  int err = 0;
+  BNB_CUDA_OK(cudaMemcpyAsync(&err, e.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BNB_CUDA_OK(cudaStreamSynchronize(st));
+  return err ? BNB_ECUDA : 0;
+}
+
 int setup_tc(Engine<float>& e) {
   cudaStream_t st = e.st;
   {
@@ -450,30 +517,6 @@ int setup_tc(Engine<float>& e) {
     }
     if (e.tc_c1 < 1 || e.tc_c2 < 1) return BNB_ECUDA;   // the kernel does not fit on this device
   }
-  // fused X^T U' tiles: the width with the least operand bytes on the busiest CTA,
-  // ceil(tiles / SMs) x (128 + width) rows of length n (K > 64 x width is not supported)
-  {
-    const int mt = (e.p + tc::BM - 1) / tc::BM;
-    long long best = -1;
-    for (int w : {64, 80, 96, 128}) {
-      if (e.K > 64 * w) continue;
-      const long long tiles = (long long)mt * ((e.K + w - 1) / w);
-      const long long t = (tiles + e.sms - 1) / e.sms * (128 + w);
-      if (best < 0 || t < best) {
-        best = t;
-        e.tc_bn3 = w;
-      }
-    }
-    if (best < 0) return BNB_EINVAL;
-    // pairs of column tiles share the X tile through cluster multicast when the device
-    // co-schedules clusters of two and there are two column tiles to pair
-    e.tc_mc3 = 0;
-    if ((e.K + e.tc_bn3 - 1) / e.tc_bn3 >= 2) {
-      const int c = e.tc_mode == 3 ? mc_clusters<3>(e.tc_bn3)
-                  : e.tc_mode == 2 ? mc_clusters<2>(e.tc_bn3) : mc_clusters<1>(e.tc_bn3);
-      e.tc_mc3 = c > e.sms / 2 ? e.sms / 2 : c;
-    }
-  }
   const long long n = e.n, p = e.p;
   // column-major X: p columns of length n (leading dimension ldn)
   if (int rc = split_bf16(st, e.X64, n, p, n, e.ldn, false, e.xc_hi, e.xc_lo)) return rc;
@@ -484,7 +527,8 @@ int setup_tc(Engine<float>& e) {
   if (g > 8192) g = 8192;
   k_split_f32<<<(int)g, 256, 0, st>>>((const float*)e.Ginv, n, n, e.ldn, e.gi_hi, e.gi_lo);
   BNB_CUDA_OK(cudaGetLastError());
-  return 0;
+  return e.tc_mode == 3 ? pick_fused_shape<3>(e) : e.tc_mode == 2 ? pick_fused_shape<2>(e)
+                                                                  : pick_fused_shape<1>(e);
 }
 
 }  // namespace bnb

@@ -527,6 +527,12 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   }
   h->stats.setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (h->ef && h->ef->tc_mode) {
+    h->stats.xw_tile_width = h->ef->tc_bn1;
+    h->stats.xw_cluster = h->ef->tc_c1;
+    h->stats.fused_tile_width = h->ef->tc_bn3;
+    h->stats.fused_clusters = h->ef->tc_mc3;
+  }
   *out = h;
   return BNB_OK;
 }
