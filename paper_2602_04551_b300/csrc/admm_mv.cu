@@ -2,12 +2,13 @@
 // matrix-vector products on CUDA cores instead of tensor-core tiles.
 //
 // Same iteration and the same state as admm_tc.cu (Sections 3.1-3.2, the shifted
-// Woodbury b-update: W' = rho beta - V, T = X W', U' = G^{-1} T, b = b_c + (W' - X^T U')/rho,
+// Woodbury b-update: W' = rho beta - V, U' = G^{-1} X W' = H W', b = b_c + (W' - X^T U')/rho,
 // prox, v-update), in FP32 on FP32 data, for the active slots listed by k_act_list
 // (at most MV_MAX of them).  With a few active nodes a 128-wide tensor-core tile is
 // almost all padding, while these kernels read X once per product and do only the
 // useful work:
 //   k_mv_part     Y_c = A v_c over a chunk of the contraction (one thread per output row,
+//                 A = H = G^-1 X for U' = H W', A = X for the check product X beta;
 //                 coalesced column reads of the column-major A, the vectors of 8 slots
 //                 staged in shared memory); partial sums per chunk
 //   k_mv_reduce   sum of the chunks in order, plus the product's epilogue (T; U', U and
@@ -282,27 +283,21 @@ int admm_iterations_mv(Engine<float>& e, int iters) {
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   const int G = (MV_MAX + MV_G - 1) / MV_G;
-  int zc1 = 0, zc2 = 0;
-  const int Z1 = mv_chunks(n, p, &zc1);          // X W'  and  X beta: contraction over p
-  const int Z2 = mv_chunks(n, n, &zc2);          // G^{-1} T: contraction over n
-  const dim3 g1((n + 255) / 256, Z1, G), g2((n + 255) / 256, Z2, G);
+  int zc1 = 0;
+  const int Z1 = mv_chunks(n, p, &zc1);          // H W' and X beta: contraction over p
+  const dim3 g1((n + 255) / 256, Z1, G);
   const dim3 gr((n + 127) / 128, MV_MAX);
   const ProbF PF = prob_f32(e.P);
   const size_t ush = sizeof(float) * MV_G * (size_t)n;
   for (int it = 0; it < iters; ++it) {
     const int last = it + 1 == iters;
+    // U' = H W' with H = G^-1 X (one product), then U and the stop-test sums
     prof_begin(e.prof, st);
-    k_mv_part<0><<<g1, 256, 0, st>>>((const float*)e.X32, n, n, p, zc1, e.act_list, e.act_count,
-                                     e.beta, e.V, PF.rho, nullptr, p, e.mv_part);
-    k_mv_reduce<0><<<gr, 128, 0, st>>>(e.mv_part, Z1, n, e.act_list, e.act_count, e.T, nullptr,
-                                       nullptr, nullptr, 0, nullptr, e.nbt, K);
-    prof_end(e.prof, st, PK_GEMM_XW);
-    prof_begin(e.prof, st);
-    k_mv_part<2><<<g2, 256, 0, st>>>(e.Ginv, n, n, n, zc2, e.act_list, e.act_count, nullptr,
-                                     nullptr, 0.f, e.T, n, e.mv_part);
-    k_mv_reduce<1><<<gr, 128, 0, st>>>(e.mv_part, Z2, n, e.act_list, e.act_count, e.Up, e.U,
+    k_mv_part<0><<<g1, 256, 0, st>>>(e.H32, n, n, p, zc1, e.act_list, e.act_count, e.beta, e.V,
+                                     PF.rho, nullptr, p, e.mv_part);
+    k_mv_reduce<1><<<gr, 128, 0, st>>>(e.mv_part, Z1, n, e.act_list, e.act_count, e.Up, e.U,
                                        e.ucR, e.yR, last, e.tc_stat, e.nbt, K);
-    prof_end(e.prof, st, PK_GEMM_GT);
+    prof_end(e.prof, st, PK_GEMM_XW);
     prof_begin(e.prof, st);
     k_mv_prox<<<dim3((p + 127) / 128, G), 256, ush, st>>>(
         (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,

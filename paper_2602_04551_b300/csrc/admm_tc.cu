@@ -347,6 +347,7 @@ static int round_tc(Engine<float>& e, int iters) {
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
   const TcOperand XT{e.xt_hi, e.xt_lo, n, p, e.ldp};     // rows = samples, K = features
+  const TcOperand HT{e.ht_hi, e.ht_lo, n, p, e.ldp};     // H = G^-1 X, same layout
   const TcOperand XC{e.xc_hi, e.xc_lo, p, n, e.ldn};     // rows = features, K = samples
   const TcOperand GI{e.gi_hi, e.gi_lo, n, n, e.ldn};
   const TcOperand Wop{e.w_hi, e.w_lo, K, p, e.ldp};
@@ -361,20 +362,16 @@ static int round_tc(Engine<float>& e, int iters) {
   BNB_CUDA_OK(cudaGetLastError());
   for (int it = 0; it < iters; ++it) {
     const bool last = it + 1 == iters;
-    // split-K reduced inside clusters, epilogues write the next operands directly
+    // U' = H W'^T (H = G^-1 X): split-K reduced inside clusters; the epilogue writes the
+    // BF16 operand of X^T U' and, on the round's last iteration, U = u_c + U' and the
+    // stop-test sums of r = y - U
     prof_begin(e.prof, st);
-    if (int rc = cred<NS>(e, e.tc_bn1, XT, Wop, n, K, p, e.tc_c1,
-                          TcEpiT{e.t_hi, NS >= 2 ? e.t_lo : nullptr, e.ldn, e.slot_active, 0}))
-      return rc;
-    prof_end(e.prof, st, PK_GEMM_XW);
-    prof_begin(e.prof, st);
-    // G^-1 T: both operands are pairs from the 2-term mode up (G^-1 is small)
-    if (int rc = cred<NS == 1 ? 1 : 3>(
-            e, e.tc_bn2, GI, Top, n, K, n, e.tc_c2,
+    if (int rc = cred<NS>(
+            e, e.tc_bn1, HT, Wop, n, K, p, e.tc_c1,
             TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
                    (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
       return rc;
-    prof_end(e.prof, st, PK_GEMM_GT);
+    prof_end(e.prof, st, PK_GEMM_XW);
     prof_begin(e.prof, st);
     if (int rc = fused_xtu<NS>(e, XC, Uop, last))
       return rc;
@@ -403,6 +400,18 @@ __global__ void k_split_f32(const float* __restrict__ x, long long rows, long lo
        t += (long long)gridDim.x * blockDim.x) {
     const long long i = t % rows, j = t / rows;
     split_store(x[t], hi, lo, i + j * ld_out);
+  }
+}
+
+// FP32 column-major rows x cols -> BF16 hi/lo row-major (element (i, j) at i ld_out + j)
+__global__ void k_split_f32_t(const float* __restrict__ x, long long rows, long long cols,
+                              long long ld_out, __nv_bfloat16* __restrict__ hi,
+                              __nv_bfloat16* __restrict__ lo) {
+  const long long m = rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t % rows, j = t / rows;
+    split_store(x[t], hi, lo, i * ld_out + j);
   }
 }
 
@@ -526,6 +535,15 @@ int setup_tc(Engine<float>& e) {
   long long g = (nn + 255) / 256;
   if (g > 8192) g = 8192;
   k_split_f32<<<(int)g, 256, 0, st>>>((const float*)e.Ginv, n, n, e.ldn, e.gi_hi, e.gi_lo);
+  BNB_CUDA_OK(cudaGetLastError());
+  // H = G^-1 X (FP32, CUDA cores), then its row-major BF16 operand: the iteration forms
+  // U' = G^-1 X W' = H W' in one product (the Woodbury identity, associated once per tree)
+  BNB_CUDA_OK((gemm_simt<float, false, false>(st, (const float*)e.Ginv, n, (int)n, (int)p, (int)n,
+                                              1, nullptr, BPlainK<float>{(const float*)e.X32, n},
+                                              EpiStore<float>{e.H32, n, 0})));
+  long long gh = (n * p + 255) / 256;
+  if (gh > 8192) gh = 8192;
+  k_split_f32_t<<<(int)gh, 256, 0, st>>>(e.H32, n, p, e.ldp, e.ht_hi, e.ht_lo);
   BNB_CUDA_OK(cudaGetLastError());
   return e.tc_mode == 3 ? pick_fused_shape<3>(e) : e.tc_mode == 2 ? pick_fused_shape<2>(e)
                                                                   : pick_fused_shape<1>(e);

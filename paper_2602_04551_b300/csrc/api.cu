@@ -131,9 +131,12 @@ static int allocate(Engine<R>& e) {
       ALLOC(e.b_hi, K * e.ldp);
       ALLOC(e.t_hi, K * e.ldn);
       ALLOC(e.u_hi, K * e.ldn);
+      ALLOC(e.H32, n * p);
+      ALLOC(e.ht_hi, n * e.ldp);
       if (xlo) {
         ALLOC(e.xc_lo, p * e.ldn);
         ALLOC(e.xt_lo, n * e.ldp);
+        ALLOC(e.ht_lo, n * e.ldp);
       }
       if (lo) {
         ALLOC(e.gi_lo, n * e.ldn);

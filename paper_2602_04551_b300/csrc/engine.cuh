@@ -143,8 +143,11 @@ struct Engine {
 
   Profiler* prof = nullptr;     // non-null only inside bnb_profile_round
 
-  // tensor-core path (float engines): 0 = CUDA cores, 1 = BF16, 3 = hi/lo BF16 (3 products)
+  // tensor-core path (float engines): 0 = CUDA cores, 1 = BF16, 2 = BF16 data with hi/lo
+  // iterates (2 products), 3 = hi/lo BF16 (3 products)
   int tc_mode = 0;
+  float* H32 = nullptr;         // H = G^-1 X, n x p column-major (U' = H W' in one product)
+  __nv_bfloat16 *ht_hi = nullptr, *ht_lo = nullptr;   // H row-major     (n x ldp)
   long long ldn = 0, ldp = 0;   // leading dimensions padded to multiples of 8 elements
   __nv_bfloat16 *xc_hi = nullptr, *xc_lo = nullptr;   // X column-major  (p x ldn)
   __nv_bfloat16 *xt_hi = nullptr, *xt_lo = nullptr;   // X row-major     (n x ldp)
