@@ -390,7 +390,7 @@ def reference_arm(args):
 KERNEL_SOURCES = ("tc_gemm.cuh", "admm_tc.cu", "common.cuh", "engine.cuh", "tc_host.cuh")
 TRAFFIC = {
     ("gemm_xtu_prox", "c2", 512, "tc3"): {
-        "sources": "1df7b96cd6224a56", "bytes": 45.092096e6 + 0.578560e6,
+        "sources": "bad468b09d46926f", "bytes": 45.092096e6 + 0.578560e6,
         "note": "ncu capture of tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8> on the c2 "
                 "workload (~500 active slots), profiles/admm_tc_kernels_c2_K512_tc3.md"},
 }
