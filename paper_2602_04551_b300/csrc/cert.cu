@@ -14,14 +14,14 @@
 // Numerical Algorithms", Sec. 3.1, plus the rounding of X and r to FP32, and
 // Cauchy-Schwarz).  For a free coordinate nu_i(x) = 0 exactly when x <= x0
 // (x0 = 2 sqrt(l0 l2), or l0/M + l2 M in the linear regime), so |a_i| + e_i <= x0
-// proves the term is zero.  F1 coordinates always get their X_i^T r in FP64.
-// A free coordinate the screen cannot settle lies in |X_i^T r| in [|a_i| - e_i,
-// |a_i| + e_i]; nu_i is nondecreasing, so nu_i(|a_i| + e_i) bounds its term from
-// above and nu_i(|a_i| - e_i) from below.  During a solve the bound with the upper
-// values is kept whenever the exact FP64 terms could not change the prune decision
-// (see k_cert_exact); otherwise, and always for bnb_relax_batch and bnb_dual_bound,
-// those coordinates get their X_i^T r in FP64 too.  F0 terms are zero.  The FP64
-// path (R = double) screens in FP64 with u = 2^-53.
+// proves the term is zero.  An F1 coordinate (nu_i = h) and a free coordinate the
+// screen cannot settle have |X_i^T r| in [|a_i| - e_i, |a_i| + e_i]; both nu_i are
+// nondecreasing in |x|, so nu_i(|a_i| + e_i) bounds the term from above and
+// nu_i(|a_i| - e_i) from below.  During a solve the bound with the upper values is kept
+// whenever the exact FP64 terms could not change the prune decision (k_cert_decide);
+// otherwise, and always for bnb_relax_batch and bnb_dual_bound, those coordinates get
+// their X_i^T r in FP64.  F0 terms are zero.  The FP64 path (R = double) screens in
+// FP64 with u = 2^-53.
 #include <cfloat>
 #include "engine.cuh"
 #include "gemm_simt.cuh"
@@ -89,12 +89,12 @@ struct EpiScreen {
           const double a = (double)acc[i][j];
           const double e = errc * xnorm[m] * rn + 1e-30;
           uint8_t need = 0;
-          if (f == 1) {
-            need = 1;                                   // F1: always the exact FP64 term
-          } else if (f == -1 && fabs(a) + e > x0) {
-            need = 2;                                   // free, not settled by the screen
-            const double up = nu_coord<double>(fabs(a) + e, -1, P);
-            const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), -1, P);
+          if (f == 1 || (f == -1 && fabs(a) + e > x0)) {
+            // F1 (nu = h) or a free coordinate the screen cannot settle: both terms are
+            // nondecreasing in |X_i^T r|, so they enter through their rigorous interval
+            need = f == 1 ? 1 : 2;
+            const double up = nu_coord<double>(fabs(a) + e, f, P);
+            const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), f, P);
             su += up;
             ss += up - lo;
           }
@@ -210,12 +210,10 @@ __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X
       const double a = (double)a32;
       const double e = epi.errc * xn * epi.cert_rn[q] + 1e-30;
       uint8_t need = 0;
-      if (f == 1) {
-        need = 1;
-      } else if (f == -1 && fabs(a) + e > epi.x0) {
-        need = 2;
-        const double up = nu_coord<double>(fabs(a) + e, -1, epi.P);
-        const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), -1, epi.P);
+      if (f == 1 || (f == -1 && fabs(a) + e > epi.x0)) {
+        need = f == 1 ? 1 : 2;                    // F1, or free and not settled
+        const double up = nu_coord<double>(fabs(a) + e, f, epi.P);
+        const double lo = nu_coord<double>(fmax(0.0, fabs(a) - e), f, epi.P);
         su = up;
         ss = up - lo;
       }
@@ -281,17 +279,17 @@ __device__ double exact_terms(const double* __restrict__ X64, const double* __re
   return s;
 }
 
-// The bound of each retired node, in three steps so that a node with many exact terms
-// is spread over CX_G blocks (one per slice of p) instead of one:
-//   k_cert_terms (code 1)  exact FP64 terms of the F1 coordinates, per slice;
-//   k_cert_decide          LB_cheap = base - sum nu(|a| + e) over the unsettled free
+// The bound of each retired node, base = -1/2 ||r||^2 + y^T r minus the nu terms:
+//   k_cert_decide          LB_cheap = base - sum nu(|a| + e) over the F1 and unsettled free
 //                          coordinates (rigorous upper values from the screen); when a
 //                          prune threshold is given and LB_cheap already reaches it, or
 //                          even LB_cheap plus the total interval width cannot reach it, the
 //                          exact terms cannot change the decision and LB_cheap (a valid
 //                          bound) is final; otherwise the node is marked;
-//   k_cert_terms (code 2)  exact FP64 terms of the unsettled coordinates of marked nodes;
-//   k_cert_final           LB = base - their sum for the marked nodes.
+//   k_cert_terms (code 1)  exact FP64 terms of the F1 coordinates of marked nodes, and
+//   k_cert_terms (code 2)  of their unsettled free coordinates, each node spread over
+//                          CX_G blocks (one per slice of p);
+//   k_cert_final           LB = (base - F1 terms) - free terms for the marked nodes.
 // Every sum is taken in a fixed order (slices in order, warps in order inside a slice).
 constexpr int CX_G = 8;
 
@@ -325,9 +323,8 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
                               const double* __restrict__ cert_rr, const double* __restrict__ cert_yr,
                               const double* __restrict__ slot_lbp, const double* __restrict__ inc_ub,
                               const double* __restrict__ params, int use_threshold,
-                              const double* __restrict__ part1, double* __restrict__ base_out,
-                              uint8_t* __restrict__ need, double* __restrict__ cert_lb,
-                              double* __restrict__ node_lb) {
+                              double* __restrict__ base_out, uint8_t* __restrict__ need,
+                              double* __restrict__ cert_lb, double* __restrict__ node_lb) {
   const int q = blockIdx.x, lane = threadIdx.x;
   if (q >= *ret_count) return;
   double su = 0.0, ss = 0.0;
@@ -338,9 +335,7 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
   su = warp_sum(su);
   ss = warp_sum(ss);
   if (lane != 0) return;
-  double s1 = 0.0;
-  for (int g = 0; g < CX_G; ++g) s1 += part1[(long long)q * CX_G + g];
-  const double base = -0.5 * cert_rr[q] + cert_yr[q] - s1;
+  const double base = -0.5 * cert_rr[q] + cert_yr[q];
   const double lb = base - su;
   bool exact = true;
   if (use_threshold) {
@@ -356,13 +351,15 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
 
 __global__ void k_cert_final(const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
                              const double* __restrict__ slot_lbp, const double* __restrict__ base,
-                             const uint8_t* __restrict__ need, const double* __restrict__ part2,
-                             double* __restrict__ cert_lb, double* __restrict__ node_lb, int K) {
+                             const uint8_t* __restrict__ need, const double* __restrict__ part1,
+                             const double* __restrict__ part2, double* __restrict__ cert_lb,
+                             double* __restrict__ node_lb, int K) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= K || q >= *ret_count || !need[q]) return;
-  double s2 = 0.0;
+  double s1 = 0.0, s2 = 0.0;
+  for (int g = 0; g < CX_G; ++g) s1 += part1[(long long)q * CX_G + g];
   for (int g = 0; g < CX_G; ++g) s2 += part2[(long long)q * CX_G + g];
-  const double lb = base[q] - s2;
+  const double lb = (base[q] - s1) - s2;
   cert_lb[q] = lb;
   const double lp = slot_lbp[ret_slot[q]];
   node_lb[q] = lb > lp ? lb : lp;
@@ -397,16 +394,17 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
   prof_end(e.prof, st, PK_CERT_SCREEN);
   prof_begin(e.prof, st);
   const dim3 gx(K, CX_G);
-  k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
-                                   e.ret_count, 1, nullptr, e.cx_part);
   k_cert_decide<<<K, 32, 0, st>>>(e.cpart, nbm, K, e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr,
                                   e.slot_lbp, e.inc_ub, e.params_d, use_threshold ? 1 : 0,
-                                  e.cx_part, e.cx_base, e.cx_need, e.cert_lb, e.node_lb);
+                                  e.cx_base, e.cx_need, e.cert_lb, e.node_lb);
+  k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
+                                   e.ret_count, 1, e.cx_need, e.cx_part);
   k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
                                    e.ret_count, 2, e.cx_need, e.cx_part + (long long)K * CX_G);
   k_cert_final<<<(K + 127) / 128, 128, 0, st>>>(e.ret_slot, e.ret_count, e.slot_lbp, e.cx_base,
-                                                e.cx_need, e.cx_part + (long long)K * CX_G,
-                                                e.cert_lb, e.node_lb, K);
+                                                e.cx_need, e.cx_part,
+                                                e.cx_part + (long long)K * CX_G, e.cert_lb,
+                                                e.node_lb, K);
   prof_end(e.prof, st, PK_CERT_EXACT);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
