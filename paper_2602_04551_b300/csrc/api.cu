@@ -225,6 +225,8 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.pool_depth, e.qcap);
   ALLOC(e.pool_warm, e.qcap);
   ALLOC(e.pool_fix, e.qcap * e.dmax);
+  ALLOC(e.ub_seen, UB_SEEN);
+  ALLOC(e.sup_size, K);
   ALLOC(e.hist_depth, e.dmax + 1);
   ALLOC(e.hist_sup, e.smax + 2);
   ALLOC(e.free_stack, e.qcap);
@@ -808,7 +810,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   if (int rc = certify(e, nullptr, true)) return rc;
   prof_end(pf, e.st, PK_CERT);
   prof_begin(pf, e.st);
-  if (int rc = branch_support(e, false)) return rc;
+  if (int rc = branch_support(e, false, true)) return rc;
   prof_end(pf, e.st, PK_BRANCH);
   prof_begin(pf, e.st);
   if (int rc = upper_bound(e, false)) return rc;

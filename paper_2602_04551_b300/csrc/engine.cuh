@@ -15,6 +15,7 @@
 
 namespace bnb {
 
+constexpr int UB_SEEN = 1 << 16;  // supports remembered per solve (upper bound already taken)
 constexpr int MV_MAX = 32;      // most active slots the matrix-vector round form handles
 constexpr int MV_ZMAX = 48;     // most contraction chunks of its partial products
 constexpr int SEL_BINS = 2048;  // radix-select histogram width
@@ -96,6 +97,8 @@ struct Engine {
   int *slot_active = nullptr, *slot_iters = nullptr, *slot_depth = nullptr, *slot_nfix = nullptr;
   int dmax = 256;               // deepest node (fixings kept per open node)
   int lockstep = 0;             // 1: refill only when every slot is free (Algorithm 1 batches)
+  unsigned long long* ub_seen = nullptr;  // [UB_SEEN] keys of evaluated supports (0: empty)
+  int* sup_size = nullptr;      // [K] rounded-support size of each retired node (-1: > smax)
   int* hist_depth = nullptr;    // [dmax + 1] solved nodes by depth (last bin: deeper)
   int* hist_sup = nullptr;      // [smax + 2] solved nodes by rounded-support size
   int* slot_fixl = nullptr;     // K x dmax encoded fixings (idx << 1 | dir)
@@ -186,7 +189,7 @@ template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double 
                                   bool use_incumbent);
 template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */,
                                bool use_threshold);
-template <class R> int branch_support(Engine<R>& e, bool write_z);
+template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false);
 template <class R> int upper_bound(Engine<R>& e, bool force_polish);
 template <class R> int queue_push(Engine<R>& e);
 template <class R> int queue_select_refill(Engine<R>& e);

@@ -452,6 +452,7 @@ int queue_init(Engine<R>& e) {
   BNB_CUDA_OK(cudaMemsetAsync(e.poolmin + 1, 0xff, sizeof(unsigned long long), e.st));  // lost key
   BNB_CUDA_OK(cudaMemsetAsync(e.status_d, 0, sizeof(Status), e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.hist_depth, 0, sizeof(int) * (e.dmax + 1), e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.ub_seen, 0, sizeof(unsigned long long) * UB_SEEN, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.hist_sup, 0, sizeof(int) * (e.smax + 2), e.st));
   k_queue_init<<<pool_grid(e.qcap), 256, 0, e.st>>>(e.qcap, e.wcap, e.free_stack, e.free_top,
                                                     e.pool_hw, e.warm_stack, e.warm_top,
@@ -468,7 +469,7 @@ int queue_push(Engine<R>& e) {
                                    e.free_stack, e.free_top, e.pool_hw, e.pool_valid, e.pool_lb,
                                    e.pool_key, e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
                                    e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.sel_state,
-                                   e.poolmin, e.poolmin + 1, e.sup_cnt, e.smax, e.hist_depth,
+                                   e.poolmin, e.poolmin + 1, e.sup_size, e.smax, e.hist_depth,
                                    e.hist_sup);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;

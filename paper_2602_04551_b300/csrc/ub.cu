@@ -43,6 +43,46 @@ __device__ unsigned long long block_max_u64(unsigned long long v, unsigned long 
   return r;
 }
 
+// Order-independent 64-bit key of a support set: the sum (mod 2^64) of a splitmix64-style
+// mix of each index (a published integer hash finalizer, Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long support_mix(int i) {
+  unsigned long long z = (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int t = 0; t < nw; ++t) s += sh[t];
+    sh[0] = s;
+  }
+  __syncthreads();
+  const unsigned long long r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Open-addressed set of support keys (0 = empty slot; key 0 is mapped to 1): true when the
+// key was present, else inserted (or the probe sequence is full: treated as new).
+__device__ bool support_seen(unsigned long long* table, int mask, unsigned long long key) {
+  if (key == 0) key = 1;
+  unsigned idx = (unsigned)(key ^ (key >> 32)) & (unsigned)mask;
+  for (int probe = 0; probe < 16; ++probe) {
+    const unsigned long long cur = atomicCAS(&table[idx], 0ull, key);
+    if (cur == 0ull) return false;      // inserted here
+    if (cur == key) return true;        // already evaluated
+    idx = (idx + 1) & (unsigned)mask;
+  }
+  return false;
+}
+
 // one block (256 threads) per retired node
 template <class R>
 __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __restrict__ fix,
@@ -50,7 +90,8 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
                                  const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
                                  int smax, int* __restrict__ br_idx, int* __restrict__ sup,
                                  int* __restrict__ sup_cnt, int* __restrict__ nfree,
-                                 float* __restrict__ zbuf) {
+                                 float* __restrict__ zbuf, unsigned long long* __restrict__ seen,
+                                 int seen_mask, int* __restrict__ sup_size) {
   __shared__ unsigned long long shk[32];
   __shared__ int wcnt[32];
   __shared__ int base;
@@ -59,7 +100,7 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
   if (q >= *ret_count) return;
   const long long slot = ret_slot[q];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned long long kf = 0, kg = 0;
+  unsigned long long kf = 0, kg = 0, hsum = 0;
   int nf = 0;
   if (threadIdx.x == 0) base = 0;
   __syncthreads();
@@ -86,6 +127,7 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
         insup = (f == 1);
       }
     }
+    if (insup) hsum += support_mix(i);
     const unsigned bal = __ballot_sync(0xffffffffu, insup);
     if (lane == 0) wcnt[w] = __popc(bal);
     __syncthreads();
@@ -103,6 +145,7 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
   }
   kf = block_max_u64(kf, shk);
   kg = block_max_u64(kg, shk);
+  const unsigned long long hs = block_sum_u64(hsum, shk);
   const double nft = block_sum<double>((double)nf, shd);
   if (threadIdx.x == 0) {
     const int nfi = (int)nft;
@@ -114,7 +157,12 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
       j = 0x7fffffff - (int)(unsigned)(k & 0xffffffffu);
     }
     br_idx[q] = j;
-    sup_cnt[q] = base <= smax ? base : -1;
+    int sc = base <= smax ? base : -1;
+    if (sup_size) sup_size[q] = sc;
+    // a support whose upper bound was already taken in this solve cannot improve the
+    // incumbent: -2 makes the upper-bound kernels skip it (like an oversized one)
+    if (seen != nullptr && sc > 0 && support_seen(seen, seen_mask, hs)) sc = -2;
+    sup_cnt[q] = sc;
   }
 }
 
@@ -489,7 +537,8 @@ __global__ void k_ub_update(int p, int smax, const int* __restrict__ sup,
     best_v = inc_ub[0];
     const int R = *ret_count;
     for (int q = 0; q < R; ++q)
-      if (sup_cnt[q] >= 0 && ub_val[q] < best_v) { best_v = ub_val[q]; best_q = q; }
+      // only supports evaluated in this call (empty or skipped ones left ub_val untouched)
+      if (sup_cnt[q] > 0 && ub_val[q] < best_v) { best_v = ub_val[q]; best_q = q; }
   }
   __syncthreads();
   const int q = best_q;
@@ -534,10 +583,11 @@ __global__ void k_sup_from_mask(const uint8_t* __restrict__ mask, int p, int sma
 }
 
 template <class R>
-int branch_support(Engine<R>& e, bool write_z) {
+int branch_support(Engine<R>& e, bool write_z, bool memo) {
   k_branch_support<R><<<e.K, 1024, 0, e.st>>>(e.beta, e.fix, e.gscr, e.p, e.P, e.ret_slot,
                                              e.ret_count, e.smax, e.br_idx, e.sup, e.sup_cnt,
-                                             e.nfree, write_z ? e.zbuf : nullptr);
+                                             e.nfree, write_z ? e.zbuf : nullptr,
+                                             memo ? e.ub_seen : nullptr, UB_SEEN - 1, e.sup_size);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }
@@ -570,8 +620,8 @@ int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K) {
   return 0;
 }
 
-template int branch_support<float>(Engine<float>&, bool);
-template int branch_support<double>(Engine<double>&, bool);
+template int branch_support<float>(Engine<float>&, bool, bool);
+template int branch_support<double>(Engine<double>&, bool, bool);
 template int upper_bound<float>(Engine<float>&, bool);
 template int upper_bound<double>(Engine<double>&, bool);
 template int ub_from_masks<float>(Engine<float>&, const uint8_t*, int);
