@@ -226,6 +226,25 @@ def test_upper_batch_matches_oracle(prec, mfac):
         np.testing.assert_allclose(beta[k], bref, atol=1e-7)
 
 
+def test_solve_after_upper_batch_reports_its_own_incumbent():
+    """Upper bounds left on the handle by an earlier bnb_upper_batch call never become the
+    solve's incumbent: the returned beta's objective is the returned UB, and both are
+    the brute-force optimum."""
+    inst, lam0, lam2, M = _inst("c1_p16", 0, frac=0.05)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    sup = np.zeros((8, inst.p), np.uint8)
+    sup[0, list(br.support)] = 1
+    sup[1, :3] = 1
+    with _handle(inst, lam0, lam2, M, 3, K=8, node_tol=1e-7, max_admm_iter=5000) as h:
+        bnb.bnb_upper_batch(h, sup)
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    obj = 0.5 * np.sum((inst.y - inst.X @ res["beta"]) ** 2) + lam0 * np.count_nonzero(res["beta"]) \
+        + lam2 * np.sum(res["beta"] ** 2)
+    assert obj == pytest.approx(res["ub"], rel=1e-10)
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+
+
 # ------------------------------------------------------------------ full solve
 
 
