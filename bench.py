@@ -386,21 +386,33 @@ def reference_arm(args):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel per
 # launch, from one ncu capture summarised under profiles/; it is reported only while the
-# kernel's sources are the ones captured (hash of the files below), else null.
-KERNEL_SOURCES = ("tc_gemm.cuh", "admm_tc.cu", "common.cuh", "engine.cuh", "tc_host.cuh")
+# source that defines the captured kernel is unchanged (hash of the kernel template, its
+# epilogue, the shared device helpers and the tile geometry), else null.
+KERNEL_SOURCE_BLOCKS = (
+    ("tc_gemm.cuh", "tc_gemm_persist_kernel(", "\n}\n"),
+    ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct Geo {", "\n};\n"),
+    ("admm_tc.cu", "struct TcEpiAdmm {", "\n};\n"),
+    ("common.cuh", "", None),
+)
 TRAFFIC = {
-    ("gemm_xtu_prox", "c2", 512, "tc3"): {
-        "sources": "bad468b09d46926f", "bytes": 45.092096e6 + 0.578560e6,
+    # (stage, workload, K, precision, fused tile width, fused clusters of two used)
+    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False): {
+        "sources": "e5c2f3d8dfce1d9e", "bytes": 45.092096e6 + 0.578560e6,
         "note": "ncu capture of tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8> on the c2 "
-                "workload (~500 active slots), profiles/admm_tc_kernels_c2_K512_tc3.md"},
+                "workload (~500 active slots)"},
 }
+
 
 def sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2602_04551_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f, start, end in KERNEL_SOURCE_BLOCKS:
+        with open(os.path.join(ROOT, "paper_2602_04551_b300", "csrc", f)) as fh:
+            text = fh.read()
+        if start:
+            i = text.index(start)
+            text = text[i:text.index(end, i) + len(end)]
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 
@@ -428,7 +440,9 @@ def roofline(out, args, pk):
     r = {"kernel": name, "achieved": ach, "unit": "TFLOP/s", "traffic": None,
          "share_of_round": share, "flops_per_launch": flops[name], "ms_per_launch": ms,
          "active_slots": active}
-    tr = TRAFFIC.get((name, args.workload, args.K, args.precision))
+    sh = out.get("shapes") or {}
+    tr = TRAFFIC.get((name, args.workload, args.K, args.precision, sh.get("fused_tile_width"),
+                      bool(sh.get("fused_clusters"))))
     if tr is not None and tr["sources"] == sources_hash():
         r["traffic"] = tr["bytes"]
         r["traffic_note"] = tr["note"]
