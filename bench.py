@@ -388,25 +388,33 @@ def reference_arm(args):
 # launch, from one ncu capture summarised under profiles/; it is reported only while the
 # source that defines the captured kernel is unchanged (hash of the kernel template, its
 # epilogue, the shared device helpers and the tile geometry), else null.
-KERNEL_SOURCE_BLOCKS = (
-    ("tc_gemm.cuh", "tc_gemm_persist_kernel(", "\n}\n"),
+SHARED_SOURCE_BLOCKS = (
     ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct Geo {", "\n};\n"),
     ("admm_tc.cu", "struct TcEpiAdmm {", "\n};\n"),
     ("common.cuh", "", None),
 )
+_FUSED_NOTE = ("ncu capture of {k} on the c2 workload (~500 active slots), "
+               "profiles/fused_xtu_prox_shapes_c2_K512_tc3.md")
 TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, fused clusters of two used)
     ("gemm_xtu_prox", "c2", 512, "tc3", 80, False): {
-        "sources": "e5c2f3d8dfce1d9e", "bytes": 45.092096e6 + 0.578560e6,
-        "note": "ncu capture of tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8> on the c2 "
-                "workload (~500 active slots)"},
+        "kernel": "tc_gemm_persist_kernel(", "sources": "e5c2f3d8dfce1d9e", "bytes": 45.092096e6 + 0.578560e6,
+        "note": _FUSED_NOTE.format(k="tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
+    ("gemm_xtu_prox", "c2", 512, "tc3", 80, True): {
+        "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.101312e6 + 0.423424e6,
+        "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
+    ("gemm_xtu_prox", "c2", 512, "tc3", 128, True): {
+        "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.173504e6 + 0.635392e6,
+        "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<128, 3, TcEpiAdmm<128, 0>, 8>")},
 }
 
 
-def sources_hash():
+def sources_hash(kernel):
+    """Hash of the source that defines one captured kernel: its template, the tile
+    geometry, the fused epilogue and the shared device helpers."""
     import hashlib
     h = hashlib.sha256()
-    for f, start, end in KERNEL_SOURCE_BLOCKS:
+    for f, start, end in (("tc_gemm.cuh", kernel, "\n}\n"),) + SHARED_SOURCE_BLOCKS:
         with open(os.path.join(ROOT, "paper_2602_04551_b300", "csrc", f)) as fh:
             text = fh.read()
         if start:
@@ -443,7 +451,7 @@ def roofline(out, args, pk):
     sh = out.get("shapes") or {}
     tr = TRAFFIC.get((name, args.workload, args.K, args.precision, sh.get("fused_tile_width"),
                       bool(sh.get("fused_clusters"))))
-    if tr is not None and tr["sources"] == sources_hash():
+    if tr is not None and tr["sources"] == sources_hash(tr["kernel"]):
         r["traffic"] = tr["bytes"]
         r["traffic_note"] = tr["note"]
     if args.precision == "fp32":
