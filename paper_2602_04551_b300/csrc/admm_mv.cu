@@ -7,15 +7,19 @@
 // (at most MV_MAX of them).  With a few active nodes a 128-wide tensor-core tile is
 // almost all padding, while these kernels read X once per product and do only the
 // useful work:
-//   k_mv_part     Y_c = A v_c over a chunk of the contraction (one thread per output row,
-//                 A = H = G^-1 X for U' = H W', A = X for the check product X beta;
-//                 coalesced column reads of the column-major A, the vectors of 8 slots
-//                 staged in shared memory); partial sums per chunk
+//   k_mv_part     Y_c = A v_c over a chunk of the contraction (a thread per 4 output
+//                 rows, float4 loads of the column-major A, eight columns in flight,
+//                 the vectors of 16 slots staged in shared memory); A = H = G^-1 X for
+//                 U' = H W', A = X for the check product X beta; partial sums per chunk
 //   k_mv_reduce   sum of the chunks in order, plus the product's epilogue (T; U', U and
 //                 the stop-test sums of r = y - U; the check ||y - X beta||^2)
-//   k_mv_prox     X^T U' by warp-reduction dot products (one warp per feature column,
-//                 lanes over the samples, U' of 8 slots in shared memory) fused with the
-//                 coordinate update of Eq. minbetalower and the v-update
+//   k_mv_prox     X^T U' for 32 feature columns per block: a warp takes four columns at
+//                 a time, lanes over the samples (float4), U' of 16 slots in shared
+//                 memory; the 64 dot products of a warp are reduce-scattered so that
+//                 each lane ends with two (column, slot) totals and applies the
+//                 coordinate update of Eq. minbetalower and the v-update to them
+//   k_mv_fold     the per-32-column stop-test sums folded into the per-128-column
+//                 layout the stop test reads (last iteration only)
 // They write exactly what the tensor-core round writes (beta, V, U, the per-tile sums
 // read by the stop test), so the stop test, the certificate and the node pool do not
 // depend on which form ran.  The choice is made per round on the device (a CUDA-graph
@@ -25,8 +29,9 @@
 
 namespace bnb {
 
-constexpr int MV_G = 8;      // slots per block group
-constexpr int MV_TJ = 64;    // contraction step staged in shared memory
+constexpr int MV_G = 16;     // slots per group
+constexpr int MV_TJ = 32;    // contraction step staged in shared memory
+constexpr int MV_PC = 32;    // feature columns per block of k_mv_prox
 
 // ordered list of the active slots (single block)
 __global__ void k_act_list(int K, const int* __restrict__ slot_active, int* __restrict__ act_list,
@@ -74,9 +79,10 @@ __device__ __forceinline__ float mv_vec(int s, long long j, const float* beta, c
 }
 
 // part[z][c][i] = sum_{j in chunk z} A[i + j lda] v_c[j],  c = compact slot index.
-// grid (ceil(M / 256), Z, ceil(MV_MAX / MV_G)); block 256.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_mv_part(const float* __restrict__ A, long long lda, int M,
+// R rows per thread (4: float4 loads, needs lda and M multiples of 4).
+// grid (ceil(M / (128 R)), Z, MV_MAX / MV_G); block 128.
+template <int MODE, int R>
+__global__ void __launch_bounds__(128) k_mv_part(const float* __restrict__ A, long long lda, int M,
                                                  int L, int zchunk,
                                                  const int* __restrict__ act_list,
                                                  const int* __restrict__ act_count,
@@ -89,41 +95,77 @@ __global__ void __launch_bounds__(256) k_mv_part(const float* __restrict__ A, lo
   const int c0 = blockIdx.z * MV_G;
   if (c0 >= a) return;
   const int nc = min(MV_G, a - c0);
-  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int i0 = (blockIdx.x * 128 + threadIdx.x) * R;
   const int j0 = blockIdx.y * zchunk, j1 = min(L, j0 + zchunk);
-  float acc[MV_G];
+  float acc[R][MV_G];
 #pragma unroll
-  for (int c = 0; c < MV_G; ++c) acc[c] = 0.f;
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < MV_G; ++c) acc[r][c] = 0.f;
   for (int jb = j0; jb < j1; jb += MV_TJ) {
-    for (int e = threadIdx.x; e < MV_G * MV_TJ; e += 256) {
+    for (int e = threadIdx.x; e < MV_G * MV_TJ; e += 128) {
       const int c = e / MV_TJ, jj = e % MV_TJ, j = jb + jj;
       vs[c][jj] = (c < nc && j < j1) ? mv_vec<MODE>(act_list[c0 + c], j, beta, V, rho, src, ldv)
                                      : 0.f;
     }
     __syncthreads();
-    if (i < M) {
+    if (i0 < M) {
       const int jn = min(MV_TJ, j1 - jb);
-      const float* ap = A + (long long)jb * lda + i;
+      const float* ap = A + (long long)jb * lda + i0;
       int jj = 0;
-      for (; jj + 4 <= jn; jj += 4) {          // four independent column loads in flight
-        float x[4];
+      for (; jj + 8 <= jn; jj += 8) {          // eight independent column loads in flight
+        float x[8][R];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = ap[(long long)(jj + u) * lda];
+        for (int u = 0; u < 8; ++u) {
+          if constexpr (R == 4) {
+            const float4 t = *reinterpret_cast<const float4*>(ap + (long long)(jj + u) * lda);
+            x[u][0] = t.x;
+            x[u][1] = t.y;
+            x[u][2] = t.z;
+            x[u][3] = t.w;
+          } else {
+            x[u][0] = ap[(long long)(jj + u) * lda];
+          }
+        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-          for (int c = 0; c < MV_G; ++c) acc[c] = fmaf(x[u], vs[c][jj + u], acc[c]);
+          for (int c = 0; c < MV_G; ++c) {
+            const float w = vs[c][jj + u];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[u][r], w, acc[r][c]);
+          }
       }
       for (; jj < jn; ++jj) {
-        const float x = ap[(long long)jj * lda];
+        float x[R];
+        if constexpr (R == 4) {
+          const float4 t = *reinterpret_cast<const float4*>(ap + (long long)jj * lda);
+          x[0] = t.x;
+          x[1] = t.y;
+          x[2] = t.z;
+          x[3] = t.w;
+        } else {
+          x[0] = ap[(long long)jj * lda];
+        }
 #pragma unroll
-        for (int c = 0; c < MV_G; ++c) acc[c] = fmaf(x, vs[c][jj], acc[c]);
+        for (int c = 0; c < MV_G; ++c)
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[r], vs[c][jj], acc[r][c]);
       }
     }
     __syncthreads();
   }
-  if (i < M)
-    for (int c = 0; c < nc; ++c) part[((long long)blockIdx.y * MV_MAX + c0 + c) * M + i] = acc[c];
+  if (i0 < M)
+#pragma unroll
+    for (int c = 0; c < MV_G; ++c) {
+      if (c >= nc) break;
+      float* out = part + ((long long)blockIdx.y * MV_MAX + c0 + c) * M + i0;
+      if constexpr (R == 4) {
+        *reinterpret_cast<float4*>(out) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+      } else {
+        out[0] = acc[0][c];
+      }
+    }
 }
 
 // Sum of the Z chunks in order, per (128-row block, compact slot); block 128.
@@ -178,13 +220,38 @@ __global__ void __launch_bounds__(128) k_mv_reduce(const float* __restrict__ par
   }
 }
 
-// X^T U' by warp-reduction dot products, fused with the coordinate update.
-// grid (ceil(p / 128), ceil(MV_MAX / MV_G)); block 256 (8 warps x 16 columns);
-// dynamic shared memory MV_G x n floats (U' of the group's slots).
-// With stats (the round's last iteration) the per-slot sums of psi(beta), nu(|X^T r|),
-// ||beta - beta_prev||^2, ||b - beta||^2 over the block's 128 columns go to
-// g3part[stat][block][slot] (the layout the tensor-core epilogue writes).
-__global__ void __launch_bounds__(256) k_mv_prox(const float* __restrict__ X, int n, int p,
+// One reduce-scatter step over 2H values: the lanes with bit H set keep the upper half,
+// the others the lower half, each adding the partner lane's copy of the half it keeps.
+template <int H>
+__device__ __forceinline__ void rs_step(float* v, int lane) {
+  const bool up = (lane & H) != 0;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float send = up ? v[k] : v[k + H];
+    const float keep = up ? v[k + H] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+  }
+}
+// 32 per-lane values -> lane l holds the warp total of value l (31 shuffles)
+__device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
+  rs_step<16>(v, lane);
+  rs_step<8>(v, lane);
+  rs_step<4>(v, lane);
+  rs_step<2>(v, lane);
+  rs_step<1>(v, lane);
+  return v[0];
+}
+
+// X^T U' for MV_PC feature columns per block, fused with the coordinate update.
+// grid (ceil(p / MV_PC), MV_MAX / MV_G); block 128 (4 warps x 8 columns, four at a time);
+// dynamic shared memory MV_G x nu floats (U' of the group's slots, nu = n rounded up to
+// 4, zero padded).  W = 4: float4 loads along the samples (n a multiple of 4), else 1.
+// Lane l owns the totals (column l / 16, slot l % 16) and (column 2 + l / 16, slot
+// l % 16) of each four-column pass.  With stats (the round's last iteration) the
+// per-slot sums of psi(beta), nu(|X^T r|), ||beta - beta_prev||^2, ||b - beta||^2 over
+// the block's columns go to g3mv[stat][block][compact slot index].
+template <int W>
+__global__ void __launch_bounds__(128) k_mv_prox(const float* __restrict__ X, int n, int p,
                                                  const float* __restrict__ Up,
                                                  const int* __restrict__ act_list,
                                                  const int* __restrict__ act_count,
@@ -192,60 +259,99 @@ __global__ void __launch_bounds__(256) k_mv_prox(const float* __restrict__ X, in
                                                  const float* __restrict__ rbc,
                                                  float* __restrict__ beta, float* __restrict__ V,
                                                  const int8_t* __restrict__ fix, Prob P, ProbF PF,
-                                                 int stats, float* __restrict__ g3part, int nbm,
-                                                 int K) {
-  extern __shared__ float us[];            // [MV_G][n]
-  __shared__ float wst[8][4][MV_G];        // per-warp stop-test sums
+                                                 int stats, float* __restrict__ g3mv, int nb32) {
+  extern __shared__ float us[];            // [MV_G][nu]
+  __shared__ float wst[4][4][MV_G];        // per-warp stop-test sums
   const int a = min(*act_count, MV_MAX);
   const int c0 = blockIdx.y * MV_G;
   if (c0 >= a) return;
   const int nc = min(MV_G, a - c0);
-  for (int e = threadIdx.x; e < MV_G * n; e += blockDim.x) {
-    const int c = e / n, i = e % n;
-    us[e] = c < nc ? Up[(long long)act_list[c0 + c] * n + i] : 0.f;
+  const int nu = (n + 3) & ~3;
+  for (int e = threadIdx.x; e < MV_G * nu; e += blockDim.x) {
+    const int c = e / nu, i = e % nu;
+    us[e] = (c < nc && i < n) ? Up[(long long)act_list[c0 + c] * n + i] : 0.f;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s_l = lane < nc ? act_list[c0 + lane] : 0;   // lane c < nc updates slot c
+  const int cs = lane & 15;                               // the lane's slot in the group
+  const int s_l = cs < nc ? act_list[c0 + cs] : 0;
   float st0 = 0.f, st1 = 0.f, st2 = 0.f, st3 = 0.f;
-  for (int jj = 0; jj < 16; ++jj) {
-    const int j = blockIdx.x * 128 + w * 16 + jj;
-    if (j >= p) break;                                     // warp-uniform
-    const float* xj = X + (long long)j * n;
-    float acc[MV_G];
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int jb = blockIdx.x * MV_PC + w * 8 + pass * 4;   // columns jb .. jb + 3
+    if (jb >= p) break;                                      // warp-uniform
+    const float* xc[4];
 #pragma unroll
-    for (int c = 0; c < MV_G; ++c) acc[c] = 0.f;
-    for (int i = lane; i < n; i += 32) {
-      const float x = xj[i];
+    for (int t = 0; t < 4; ++t) xc[t] = X + (long long)min(jb + t, p - 1) * n;
+    float acc[4 * MV_G];
 #pragma unroll
-      for (int c = 0; c < MV_G; ++c) acc[c] = fmaf(x, us[c * n + i], acc[c]);
+    for (int k = 0; k < 4 * MV_G; ++k) acc[k] = 0.f;
+#pragma unroll 2
+    for (int i = W * lane; i < n; i += 32 * W) {
+      float x[4][W];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if constexpr (W == 4) {
+          const float4 v4 = *reinterpret_cast<const float4*>(xc[t] + i);
+          x[t][0] = v4.x;
+          x[t][1] = v4.y;
+          x[t][2] = v4.z;
+          x[t][3] = v4.w;
+        } else {
+          x[t][0] = xc[t][i];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < MV_G; ++c) {
+        float u[W];
+        if constexpr (W == 4) {
+          const float4 u4 = *reinterpret_cast<const float4*>(us + c * nu + i);
+          u[0] = u4.x;
+          u[1] = u4.y;
+          u[2] = u4.z;
+          u[3] = u4.w;
+        } else {
+          u[0] = us[c * nu + i];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int r = 0; r < W; ++r) acc[t * MV_G + c] = fmaf(x[t][r], u[r], acc[t * MV_G + c]);
+      }
     }
-    float mine = 0.f;
+    float tot[2];
+    tot[0] = reduce_scatter32(acc, lane);                 // (column lane / 16, slot cs)
+    tot[1] = reduce_scatter32(acc + 32, lane);            // (column 2 + lane / 16, slot cs)
 #pragma unroll
-    for (int c = 0; c < MV_G; ++c) {
-      const float t = warp_sum(acc[c]);
-      if (lane == c) mine = t;
-    }
-    if (lane < nc) {
-      const long long o = (long long)s_l * p + j;
-      const float bo = beta[o], vv = V[o];
-      const int ff = fix[o];
-      const float wv = PF.rho * bo - vv;
-      const float b = bc[j] + (wv - mine) * PF.irho;
-      const float bh = PF.alpha * b + PF.one_minus_alpha * bo;
-      const float bn = prox_coord_f(bh + vv * PF.irho, ff, PF);
-      const float vn = vv + PF.rho * (bh - bn);
-      beta[o] = bn;
-      V[o] = vn;
-      if (stats) {
-        st0 += psi_coord<float>(bn, ff, P);
-        st1 += nu_coord<float>(fabsf(rbc[j] - mine), ff, P);
-        st2 += (bn - bo) * (bn - bo);
-        st3 += (b - bn) * (b - bn);
+    for (int h = 0; h < 2; ++h) {
+      const int j = jb + 2 * h + (lane >> 4);
+      if (cs < nc && j < p) {
+        const float mine = tot[h];
+        const long long o = (long long)s_l * p + j;
+        const float bo = beta[o], vv = V[o];
+        const int ff = fix[o];
+        const float wv = PF.rho * bo - vv;
+        const float b = bc[j] + (wv - mine) * PF.irho;
+        const float bh = PF.alpha * b + PF.one_minus_alpha * bo;
+        const float bn = prox_coord_f(bh + vv * PF.irho, ff, PF);
+        const float vn = vv + PF.rho * (bh - bn);
+        beta[o] = bn;
+        V[o] = vn;
+        if (stats) {
+          st0 += psi_coord<float>(bn, ff, P);
+          st1 += nu_coord<float>(fabsf(rbc[j] - mine), ff, P);
+          st2 += (bn - bo) * (bn - bo);
+          st3 += (b - bn) * (b - bn);
+        }
       }
     }
   }
   if (!stats) return;
+  // lanes l and l + 16 hold the same slot
+  st0 += __shfl_xor_sync(0xffffffffu, st0, 16);
+  st1 += __shfl_xor_sync(0xffffffffu, st1, 16);
+  st2 += __shfl_xor_sync(0xffffffffu, st2, 16);
+  st3 += __shfl_xor_sync(0xffffffffu, st3, 16);
   if (lane < MV_G) {
     wst[w][0][lane] = st0;
     wst[w][1][lane] = st1;
@@ -256,19 +362,34 @@ __global__ void __launch_bounds__(256) k_mv_prox(const float* __restrict__ X, in
   if (threadIdx.x < 4 * MV_G) {
     const int t = threadIdx.x / MV_G, c = threadIdx.x % MV_G;
     if (c < nc) {
-      float sum = 0.f;
-      for (int ww = 0; ww < 8; ++ww) sum += wst[ww][t][c];
-      g3part[((long long)t * nbm + blockIdx.x) * K + act_list[c0 + c]] = sum;
+      const float sum = wst[0][t][c] + wst[1][t][c] + wst[2][t][c] + wst[3][t][c];
+      g3mv[((long long)t * nb32 + blockIdx.x) * MV_MAX + c0 + c] = sum;
     }
   }
 }
 
+// g3part[stat][b][slot] = sum over the (up to) four 32-column blocks of the 128-column
+// block b, in order.  grid (ceil(nbm / 32), MV_MAX); block 128 = 32 blocks b x 4 stats.
+__global__ void k_mv_fold(const float* __restrict__ g3mv, int nb32, const int* __restrict__ act_list,
+                          const int* __restrict__ act_count, float* __restrict__ g3part, int nbm,
+                          int K) {
+  const int c = blockIdx.y;
+  const int b = blockIdx.x * 32 + (threadIdx.x >> 2), t = threadIdx.x & 3;
+  if (c >= min(*act_count, MV_MAX) || b >= nbm) return;
+  float sum = 0.f;
+  for (int q = 0; q < 4; ++q) {
+    const int b32 = 4 * b + q;
+    if (b32 < nb32) sum += g3mv[((long long)t * nb32 + b32) * MV_MAX + c];
+  }
+  g3part[((long long)t * nbm + b) * K + act_list[c]] = sum;
+}
+
 // ----------------------------------------------------------------------------- host
 
-// chunks of the contraction for k_mv_part: enough blocks to cover the SMs
-static int mv_chunks(int M, int L, int* zchunk) {
-  const int rows = (M + 255) / 256;
-  int Z = (2 * 148 + rows - 1) / rows;
+// chunks of the contraction for k_mv_part: about two blocks per SM
+static int mv_chunks(int M, int L, int R, int sms, int* zchunk) {
+  const int rows = (M + 128 * R - 1) / (128 * R);
+  int Z = (2 * sms + rows - 1) / rows;
   const int zmax = (L + MV_TJ - 1) / MV_TJ;
   if (Z > zmax) Z = zmax;
   if (Z > MV_ZMAX) Z = MV_ZMAX;
@@ -279,36 +400,55 @@ static int mv_chunks(int M, int L, int* zchunk) {
   return (L + zc - 1) / zc;
 }
 
+template <int MODE>
+static void mv_part(Engine<float>& e, const float* A, int Z, int zc, int R, const float* beta,
+                    const float* V, float rho) {
+  const int n = e.n, p = e.p, G = MV_MAX / MV_G;
+  if (R == 4)
+    k_mv_part<MODE, 4><<<dim3((n + 511) / 512, Z, G), 128, 0, e.st>>>(
+        A, n, n, p, zc, e.act_list, e.act_count, beta, V, rho, nullptr, p, e.mv_part);
+  else
+    k_mv_part<MODE, 1><<<dim3((n + 127) / 128, Z, G), 128, 0, e.st>>>(
+        A, n, n, p, zc, e.act_list, e.act_count, beta, V, rho, nullptr, p, e.mv_part);
+}
+
 int admm_iterations_mv(Engine<float>& e, int iters) {
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
-  const int G = (MV_MAX + MV_G - 1) / MV_G;
+  const int G = MV_MAX / MV_G;
+  const int R = (n % 4 == 0) ? 4 : 1;             // float4 rows (H, X columns 16-byte aligned)
   int zc1 = 0;
-  const int Z1 = mv_chunks(n, p, &zc1);          // H W' and X beta: contraction over p
-  const dim3 g1((n + 255) / 256, Z1, G);
+  const int Z1 = mv_chunks(n, p, R, e.sms > 0 ? e.sms : 148, &zc1);   // contraction over p
   const dim3 gr((n + 127) / 128, MV_MAX);
   const ProbF PF = prob_f32(e.P);
-  const size_t ush = sizeof(float) * MV_G * (size_t)n;
+  const size_t ush = sizeof(float) * MV_G * (size_t)((n + 3) & ~3);
+  const int nb32 = (p + MV_PC - 1) / MV_PC;
   for (int it = 0; it < iters; ++it) {
     const int last = it + 1 == iters;
     // U' = H W' with H = G^-1 X (one product), then U and the stop-test sums
     prof_begin(e.prof, st);
-    k_mv_part<0><<<g1, 256, 0, st>>>(e.H32, n, n, p, zc1, e.act_list, e.act_count, e.beta, e.V,
-                                     PF.rho, nullptr, p, e.mv_part);
+    mv_part<0>(e, e.H32, Z1, zc1, R, e.beta, e.V, PF.rho);
     k_mv_reduce<1><<<gr, 128, 0, st>>>(e.mv_part, Z1, n, e.act_list, e.act_count, e.Up, e.U,
                                        e.ucR, e.yR, last, e.tc_stat, e.nbt, K);
     prof_end(e.prof, st, PK_GEMM_XW);
     prof_begin(e.prof, st);
-    k_mv_prox<<<dim3((p + 127) / 128, G), 256, ush, st>>>(
-        (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,
-        e.fix, e.P, PF, last, e.g3part, e.nbm3, K);
+    if (R == 4)
+      k_mv_prox<4><<<dim3(nb32, G), 128, ush, st>>>(
+          (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,
+          e.fix, e.P, PF, last, e.g3mv, nb32);
+    else
+      k_mv_prox<1><<<dim3(nb32, G), 128, ush, st>>>(
+          (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,
+          e.fix, e.P, PF, last, e.g3mv, nb32);
+    if (last)
+      k_mv_fold<<<dim3((e.nbm3 + 31) / 32, MV_MAX), 128, 0, st>>>(
+          e.g3mv, nb32, e.act_list, e.act_count, e.g3part, e.nbm3, K);
     prof_end(e.prof, st, PK_GEMM_XTU);
     BNB_CUDA_OK(cudaGetLastError());
   }
   // check product X beta
   prof_begin(e.prof, st);
-  k_mv_part<1><<<g1, 256, 0, st>>>((const float*)e.X32, n, n, p, zc1, e.act_list, e.act_count,
-                                   e.beta, nullptr, 0.f, nullptr, p, e.mv_part);
+  mv_part<1>(e, (const float*)e.X32, Z1, zc1, R, e.beta, nullptr, 0.f);
   k_mv_reduce<2><<<gr, 128, 0, st>>>(e.mv_part, Z1, n, e.act_list, e.act_count, nullptr, nullptr,
                                      nullptr, e.yR, 1, e.tc_stat, e.nbt, K);
   prof_end(e.prof, st, PK_CHECK);
@@ -317,12 +457,14 @@ int admm_iterations_mv(Engine<float>& e, int iters) {
 }
 
 int mv_setup(Engine<float>& e) {
-  const size_t ush = sizeof(float) * MV_G * (size_t)e.n;
+  const size_t ush = sizeof(float) * MV_G * (size_t)((e.n + 3) & ~3);
   if (ush > 200 * 1024) {
     e.mv_cross = 0;                               // U' of a group does not fit: no matvec form
     return 0;
   }
-  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_prox, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_prox<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)ush));
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_prox<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)ush));
   return 0;
 }

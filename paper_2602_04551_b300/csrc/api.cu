@@ -122,6 +122,7 @@ static int allocate(Engine<R>& e) {
       ALLOC(e.act_list, K);
       ALLOC(e.act_count, 1);
       ALLOC(e.mv_part, (long long)MV_ZMAX * MV_MAX * n);
+      ALLOC(e.g3mv, 4LL * MV_MAX * ((p + 31) / 32));
       const bool xlo = e.tc_mode == 3;   // X as a hi/lo pair (3 terms)
       const bool lo = e.tc_mode >= 2;    // iterates and G^-1 as pairs (2 and 3 terms)
       ALLOC(e.xc_hi, p * e.ldn);

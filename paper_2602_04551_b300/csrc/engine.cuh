@@ -17,7 +17,7 @@ namespace bnb {
 
 constexpr int UB_SEEN = 1 << 16;  // supports remembered per solve (upper bound already taken)
 constexpr int MV_MAX = 32;      // most active slots the matrix-vector round form handles
-constexpr int MV_ZMAX = 48;     // most contraction chunks of its partial products
+constexpr int MV_ZMAX = 96;     // most contraction chunks of its partial products
 constexpr int SEL_BINS = 2048;  // radix-select histogram width
 
 struct Status {                 // copied to the host after every round
@@ -174,6 +174,7 @@ struct Engine {
   int* act_list = nullptr;      // [K] active slots in order
   int* act_count = nullptr;
   float* mv_part = nullptr;     // [MV_ZMAX][MV_MAX][n] partial products
+  float* g3mv = nullptr;        // [4][ceil(p / 32)][MV_MAX] per-32-column stop-test sums
   cudaStream_t st_side = nullptr;  // capture of the conditional bodies
   int mv_body_kernels = 0, tc_body_kernels = 0;
 
