@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--fp64-time-limit", type=float, default=60.0)
     ap.add_argument("--seeds", type=int, default=1, help="solves mode: instances per lambda0")
     ap.add_argument("--max-depth", type=int, default=1024)
+    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="fused X^T U' shape: 0 measured at setup, 1 one CTA per tile, "
+                         "2 clusters of two sharing X, 3 transposed on CTA pairs")
     ap.add_argument("--mv-crossover", type=int, default=-1,
                     help="narrow-form crossover (-1 default; 0 = tensor-core form only: graphs "
                          "without conditional nodes, which ncu can profile kernel by kernel)")
@@ -187,7 +190,8 @@ def run_mine(args, rank, world):
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
                                   queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
-                                  relax_alpha=args.alpha, mv_crossover=args.mv_crossover)
+                                  relax_alpha=args.alpha, mv_crossover=args.mv_crossover,
+                                  fused_shape=args.fused_shape)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
@@ -234,7 +238,7 @@ def run_mine(args, rank, world):
     res = bnb.bnb_solve_finish(h)
     h.close()
     shapes = {k: stats.get(k) for k in ("xw_tile_width", "xw_cluster", "fused_tile_width",
-                                          "fused_clusters")}
+                                          "fused_clusters", "fused_pairs")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
@@ -396,14 +400,14 @@ SHARED_SOURCE_BLOCKS = (
 _FUSED_NOTE = ("ncu capture of {k} on the c2 workload (~500 active slots), "
                "profiles/fused_xtu_prox_shapes_c2_K512_tc3.md")
 TRAFFIC = {
-    # (stage, workload, K, precision, fused tile width, fused clusters of two used)
-    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False): {
+    # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs)
+    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False, False): {
         "kernel": "tc_gemm_persist_kernel(", "sources": "e5c2f3d8dfce1d9e", "bytes": 45.092096e6 + 0.578560e6,
         "note": _FUSED_NOTE.format(k="tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 80, True): {
+    ("gemm_xtu_prox", "c2", 512, "tc3", 80, True, False): {
         "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.101312e6 + 0.423424e6,
         "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 128, True): {
+    ("gemm_xtu_prox", "c2", 512, "tc3", 128, True, False): {
         "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.173504e6 + 0.635392e6,
         "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<128, 3, TcEpiAdmm<128, 0>, 8>")},
 }
@@ -450,7 +454,7 @@ def roofline(out, args, pk):
          "active_slots": active}
     sh = out.get("shapes") or {}
     tr = TRAFFIC.get((name, args.workload, args.K, args.precision, sh.get("fused_tile_width"),
-                      bool(sh.get("fused_clusters"))))
+                      bool(sh.get("fused_clusters")), bool(sh.get("fused_pairs"))))
     if tr is not None and tr["sources"] == sources_hash(tr["kernel"]):
         r["traffic"] = tr["bytes"]
         r["traffic_note"] = tr["note"]

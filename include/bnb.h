@@ -90,6 +90,12 @@ typedef struct {
                             many runs the ADMM products as coalesced matrix-vector kernels on
                             CUDA cores (FP32) instead of tensor-core tiles; -1 (default) = 16,
                             0 = never, at most 32.  Chosen per round on the device. */
+  int fused_shape;       /* tensor-core precisions, the fused X^T U' product: 0 (default) =
+                            the fastest shape measured at creation; 1 = one CTA per output
+                            tile; 2 = clusters of two CTAs sharing the X tile; 3 = the
+                            transposed product on CTA pairs (tcgen05 cta_group::2).  A shape
+                            the device or the problem cannot run fails bnb_create with
+                            BNB_EINVAL. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */
@@ -278,6 +284,19 @@ int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd, 
 int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
                               int nsplit, int cluster, float* dC, int* err_out);
 
+/* Diagnostics: the same product through the CTA-pair tcgen05 kernel (cta_group::2) that
+ * the ADMM iteration can use for X^T U' with the roles exchanged: 256 x bn tiles
+ * (bn = 128, 144 or 256), each computed by two CTAs on two SMs, the first holding rows
+ * [0, 128) of the tile and B rows [0, bn/2), the second the rest.  nsplit: 1 (BF16),
+ * 2 (A as a hi/lo pair, B one BF16 term: the iterate is A in that use) or 3 (both
+ * pairs).  Arguments otherwise as for bnb_tc_gemm_check; C (device, M x N column-major
+ * FP32) is written directly; M <= 16384.  Returns BNB_EINVAL for bad sizes or when the
+ * device cannot co-schedule a pair; err_out receives the kernel's error word (0 when
+ * every bounded wait completed and both CTAs of each pair held the same tensor-memory
+ * columns).  The paper has no counterpart: this checks a B300-specific kernel alone. */
+int bnb_tc_gemm_check_pair(const double* dA, const double* dB, int M, int N, int Kd, int nsplit,
+                           int bn, float* dC, int* err_out);
+
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */
   long long rounds;         /* device rounds run */
@@ -292,9 +311,11 @@ typedef struct {
   double final_ub, final_lb;
   int round_kernels;        /* kernels in one captured round (CUDA graph) */
   /* tensor-core shapes chosen at creation (0 for the CUDA-core precisions): output tile
-     width and cluster size of X W'^T, tile width of the fused X^T U' product and the
-     number of two-CTA clusters it runs in (0: one CTA per tile) */
-  int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters;
+     width and cluster size of the product H W'^T, tile width of the fused X^T U' product,
+     the number of two-CTA clusters sharing the X tile it runs in (0: one CTA per tile),
+     and the number of CTA pairs it runs on when computed transposed (0: not transposed;
+     the width then counts features) */
+  int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters, fused_pairs;
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

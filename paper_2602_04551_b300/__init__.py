@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "no
 SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_dual_bound_static",
+           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_tc_gemm_check_pair", "bnb_dual_bound_static",
            "bnb_get_stats", "bnb_get_histograms",
            "bnb_last_error", "bnb_destroy")
 STAGES = ("select_refill", "gemm_xw", "reduce_t_or_make_w", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
@@ -46,7 +46,8 @@ class bnb_options(ctypes.Structure):
                 ("ub_max_iter", ctypes.c_int), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
                 ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
-                ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int)]
+                ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int),
+                ("fused_shape", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):
@@ -58,7 +59,7 @@ class bnb_stats(ctypes.Structure):
                 ("final_ub", ctypes.c_double), ("final_lb", ctypes.c_double),
                 ("round_kernels", ctypes.c_int), ("xw_tile_width", ctypes.c_int),
                 ("xw_cluster", ctypes.c_int), ("fused_tile_width", ctypes.c_int),
-                ("fused_clusters", ctypes.c_int)]
+                ("fused_clusters", ctypes.c_int), ("fused_pairs", ctypes.c_int)]
 
 
 class bnb_progress(ctypes.Structure):
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
         "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
+        "bnb_tc_gemm_check_pair": ([P, P, I, I, I, I, I, P, P], I),
         "bnb_get_histograms": ([P, P, I, P, I], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
@@ -309,6 +311,14 @@ def bnb_get_histograms(h: Handle, ndepth: int = 257, nsupport: int = 258):
     s = np.zeros(nsupport, np.int64)
     _check(load_library().bnb_get_histograms(h.ptr, _ptr(d), ndepth, _ptr(s), nsupport), h.ptr)
     return d, s
+
+
+def bnb_tc_gemm_check_pair(dA, dB, M, N, Kd, nsplit=3, bn=144, dC=None):
+    """C = A B^T through the CTA-pair tensor-core kernel (FP64 in, FP32 out)."""
+    err = ctypes.c_int(0)
+    _check(load_library().bnb_tc_gemm_check_pair(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn,
+                                                 _ptr(dC), ctypes.byref(err)))
+    return err.value
 
 
 def bnb_tc_gemm_check_cluster(dA, dB, M, N, Kd, nsplit=3, cluster=8, dC=None):

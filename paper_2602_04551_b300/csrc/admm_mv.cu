@@ -13,9 +13,9 @@
 //                 U' = H W', A = X for the check product X beta; partial sums per chunk
 //   k_mv_reduce   sum of the chunks in order, plus the product's epilogue (T; U', U and
 //                 the stop-test sums of r = y - U; the check ||y - X beta||^2)
-//   k_mv_prox     X^T U' for 32 feature columns per block: a warp takes four columns at
-//                 a time, lanes over the samples (float4), U' of 16 slots in shared
-//                 memory; the 64 dot products of a warp are reduce-scattered so that
+//   k_mv_prox     X^T U' for 32 feature columns per block: a warp takes four columns,
+//                 lanes over the samples (float4), U' of 16 slots in shared memory
+//                 (asynchronous copies); the 64 dot products of a warp are reduce-scattered so that
 //                 each lane ends with two (column, slot) totals and applies the
 //                 coordinate update of Eq. minbetalower and the v-update to them
 //   k_mv_fold     the per-32-column stop-test sums folded into the per-128-column
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(128) k_mv_reduce(const float* __restrict__ par
   const int i = blockIdx.x * 128 + threadIdx.x;
   float v = 0.f;
   if (i < M)
+#pragma unroll 8
     for (int z = 0; z < Z; ++z) v += part[((long long)z * MV_MAX + c) * M + i];
   float r0 = 0.f, r1 = 0.f;
   if (i < M) {
@@ -243,15 +244,16 @@ __device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
 }
 
 // X^T U' for MV_PC feature columns per block, fused with the coordinate update.
-// grid (ceil(p / MV_PC), MV_MAX / MV_G); block 128 (4 warps x 8 columns, four at a time);
-// dynamic shared memory MV_G x nu floats (U' of the group's slots, nu = n rounded up to
-// 4, zero padded).  W = 4: float4 loads along the samples (n a multiple of 4), else 1.
-// Lane l owns the totals (column l / 16, slot l % 16) and (column 2 + l / 16, slot
-// l % 16) of each four-column pass.  With stats (the round's last iteration) the
-// per-slot sums of psi(beta), nu(|X^T r|), ||beta - beta_prev||^2, ||b - beta||^2 over
-// the block's columns go to g3mv[stat][block][compact slot index].
+// grid (ceil(p / MV_PC), MV_MAX / MV_G); block 256 (8 warps x 4 columns); dynamic shared
+// memory MV_G x nu floats (U' of the group's slots, nu = n rounded up to 4, zero
+// padded), staged with asynchronous 16-byte copies when n is a multiple of 4.
+// W = 4: float4 loads along the samples (n a multiple of 4), else 1.  Lane l owns the
+// totals (column l / 16, slot l % 16) and (column 2 + l / 16, slot l % 16) of its
+// warp's four columns.  With stats (the round's last iteration) the per-slot sums of
+// psi(beta), nu(|X^T r|), ||beta - beta_prev||^2, ||b - beta||^2 over the block's
+// columns go to g3mv[stat][block][compact slot index].
 template <int W>
-__global__ void __launch_bounds__(128) k_mv_prox(const float* __restrict__ X, int n, int p,
+__global__ void __launch_bounds__(256) k_mv_prox(const float* __restrict__ X, int n, int p,
                                                  const float* __restrict__ Up,
                                                  const int* __restrict__ act_list,
                                                  const int* __restrict__ act_count,
@@ -261,32 +263,49 @@ __global__ void __launch_bounds__(128) k_mv_prox(const float* __restrict__ X, in
                                                  const int8_t* __restrict__ fix, Prob P, ProbF PF,
                                                  int stats, float* __restrict__ g3mv, int nb32) {
   extern __shared__ float us[];            // [MV_G][nu]
-  __shared__ float wst[4][4][MV_G];        // per-warp stop-test sums
+  __shared__ float wst[8][4][MV_G];        // per-warp stop-test sums
   const int a = min(*act_count, MV_MAX);
   const int c0 = blockIdx.y * MV_G;
   if (c0 >= a) return;
   const int nc = min(MV_G, a - c0);
   const int nu = (n + 3) & ~3;
-  for (int e = threadIdx.x; e < MV_G * nu; e += blockDim.x) {
-    const int c = e / nu, i = e % nu;
-    us[e] = (c < nc && i < n) ? Up[(long long)act_list[c0 + c] * n + i] : 0.f;
+  if constexpr (W == 4) {
+    // nu == n: every 16-byte chunk of a slot's row is copied without waiting in between
+    const int q4 = n / 4;
+    for (int e = threadIdx.x; e < MV_G * q4; e += blockDim.x) {
+      const int c = e / q4, i4 = e % q4;
+      float* dst = us + c * nu + 4 * i4;
+      if (c < nc) {
+        const float* src = Up + (long long)act_list[c0 + c] * n + 4 * i4;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(dst)),
+                     "l"(src)
+                     : "memory");
+      } else {
+        *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  } else {
+    for (int e = threadIdx.x; e < MV_G * nu; e += blockDim.x) {
+      const int c = e / nu, i = e % nu;
+      us[e] = (c < nc && i < n) ? Up[(long long)act_list[c0 + c] * n + i] : 0.f;
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int cs = lane & 15;                               // the lane's slot in the group
   const int s_l = cs < nc ? act_list[c0 + cs] : 0;
   float st0 = 0.f, st1 = 0.f, st2 = 0.f, st3 = 0.f;
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const int jb = blockIdx.x * MV_PC + w * 8 + pass * 4;   // columns jb .. jb + 3
-    if (jb >= p) break;                                      // warp-uniform
+  const int jb = blockIdx.x * MV_PC + w * 4;              // this warp's columns jb .. jb + 3
+  if (jb < p) {                                           // warp-uniform
     const float* xc[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) xc[t] = X + (long long)min(jb + t, p - 1) * n;
     float acc[4 * MV_G];
 #pragma unroll
     for (int k = 0; k < 4 * MV_G; ++k) acc[k] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
     for (int i = W * lane; i < n; i += 32 * W) {
       float x[4][W];
 #pragma unroll
@@ -362,7 +381,9 @@ __global__ void __launch_bounds__(128) k_mv_prox(const float* __restrict__ X, in
   if (threadIdx.x < 4 * MV_G) {
     const int t = threadIdx.x / MV_G, c = threadIdx.x % MV_G;
     if (c < nc) {
-      const float sum = wst[0][t][c] + wst[1][t][c] + wst[2][t][c] + wst[3][t][c];
+      float sum = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) sum += wst[ww][t][c];
       g3mv[((long long)t * nb32 + blockIdx.x) * MV_MAX + c0 + c] = sum;
     }
   }
@@ -433,11 +454,11 @@ int admm_iterations_mv(Engine<float>& e, int iters) {
     prof_end(e.prof, st, PK_GEMM_XW);
     prof_begin(e.prof, st);
     if (R == 4)
-      k_mv_prox<4><<<dim3(nb32, G), 128, ush, st>>>(
+      k_mv_prox<4><<<dim3(nb32, G), 256, ush, st>>>(
           (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,
           e.fix, e.P, PF, last, e.g3mv, nb32);
     else
-      k_mv_prox<1><<<dim3(nb32, G), 128, ush, st>>>(
+      k_mv_prox<1><<<dim3(nb32, G), 256, ush, st>>>(
           (const float*)e.X32, n, p, e.Up, e.act_list, e.act_count, e.bcR, e.rbcR, e.beta, e.V,
           e.fix, e.P, PF, last, e.g3mv, nb32);
     if (last)

@@ -9,7 +9,10 @@
 //   P  = X^T U'      A = X column-major (p x n, K-major), B = U' (K x n), persistent,
 //                    fused epilogue straight from tensor memory:
 //                    b = b_c + (W' - P)/rho, beta = prox(b + V/rho), V += rho (b - beta),
-//                    per-slot stop-test sums, and the next iteration's W' operand.
+//                    per-slot stop-test sums, and the next iteration's W' operand;
+//                    or, measured faster at setup, its transpose P^T = U'^T X on CTA
+//                    pairs (tc_gemm_pair_kernel: rows = node slots, 256 per pair tile,
+//                    columns = features) with the same update per element.
 // Operands are BF16: TC3 stores each as a hi/lo pair (three MMAs: hi hi + hi lo + lo hi),
 // BF16X2 keeps X as one term and the iterates as pairs (two), BF16 uses one term.
 // Accumulation is FP32 in TMEM.  The ADMM state (beta, V) stays FP32 in HBM.  Tile
@@ -29,6 +32,19 @@ __device__ __forceinline__ void split_store(float x, __nv_bfloat16* hi, __nv_bfl
   const __nv_bfloat16 h = __float2bfloat16_rn(x);
   hi[o] = h;
   if (lo) lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// eight consecutive values as BF16 hi (and lo) at a 16-byte aligned offset o
+__device__ __forceinline__ void store8_split(const float (&x)[8], __nv_bfloat16* hi,
+                                             __nv_bfloat16* lo, long long o) {
+  __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    h[j] = __float2bfloat16_rn(x[j]);
+    l[j] = __float2bfloat16_rn(x[j] - __bfloat162float(h[j]));
+  }
+  *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(h);
+  if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
 }
 
 // W' = rho beta - V for the active slots, as BF16 hi/lo (K x ldp)
@@ -287,6 +303,143 @@ struct TcEpiAdmm {
   }
 };
 
+// The fused update for the CTA-pair product P^T = U'^T X: row m = node slot, columns
+// f0 .. f0 + 15 = features of that slot.  Per element the arithmetic of TcEpiAdmm; a
+// thread's loads and stores run along its slot's contiguous features (16-byte vectors
+// where p allows), and its per-slot stop-test sums accumulate in registers over the
+// tile, then over the epilogue warps of the lane quarter in shared memory.
+template <bool STATS>
+struct TcEpiAdmmT {
+  static constexpr int SMEM_FLOATS = STATS ? 2 * 4 * 128 : 0;   // [warp group][stat][row]
+  struct State {
+    float s[4];
+  };
+  const float* __restrict__ bc;     // b_c = D c (per feature)
+  const float* __restrict__ rbc;    // rho b_c
+  float* __restrict__ beta;
+  float* __restrict__ V;
+  const int8_t* __restrict__ fix;
+  const int* __restrict__ active;
+  float* __restrict__ g3part;       // [4][nbm][K]
+  __nv_bfloat16 *whi, *wlo;         // next W' operand (K x ldp)
+  __nv_bfloat16 *bhi, *blo;         // beta operand of the check product (or null)
+  Prob P;
+  ProbF PF;
+  long long p, ldp;
+  int nbm, ntiles, K;
+  int vec;                          // p % 8 == 0: vector loads of beta, V, fix
+
+  __device__ __forceinline__ void begin(State& st) const {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) st.s[t] = 0.f;
+  }
+
+  __device__ __forceinline__ void operator()(int m, int f0, const float (&acc)[16], int M, int N,
+                                             State& st) const {
+    if (m >= M || !active[m]) return;
+    const float rho = PF.rho, irho = PF.irho;
+    const long long rb = (long long)m * p, rw = (long long)m * ldp;
+#pragma unroll
+    for (int h = 0; h < 16; h += 8) {
+      const int f = f0 + h;
+      if (f >= N) break;
+      const bool full = f + 8 <= N;
+      float bo[8], vv[8], cb[8];
+      int ff[8];
+      if (full && vec) {
+        const float4 b0 = *reinterpret_cast<const float4*>(beta + rb + f);
+        const float4 b1 = *reinterpret_cast<const float4*>(beta + rb + f + 4);
+        const float4 v0 = *reinterpret_cast<const float4*>(V + rb + f);
+        const float4 v1 = *reinterpret_cast<const float4*>(V + rb + f + 4);
+        const uint2 fx = *reinterpret_cast<const uint2*>(fix + rb + f);
+        bo[0] = b0.x; bo[1] = b0.y; bo[2] = b0.z; bo[3] = b0.w;
+        bo[4] = b1.x; bo[5] = b1.y; bo[6] = b1.z; bo[7] = b1.w;
+        vv[0] = v0.x; vv[1] = v0.y; vv[2] = v0.z; vv[3] = v0.w;
+        vv[4] = v1.x; vv[5] = v1.y; vv[6] = v1.z; vv[7] = v1.w;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          ff[j] = (int)(int8_t)(((j < 4 ? fx.x : fx.y) >> (8 * (j & 3))) & 0xffu);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const bool in = f + j < N;
+          bo[j] = in ? beta[rb + f + j] : 0.f;
+          vv[j] = in ? V[rb + f + j] : 0.f;
+          ff[j] = in ? (int)fix[rb + f + j] : 0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) cb[j] = f + j < N ? bc[f + j] : 0.f;
+      float nb[8], nv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float w = rho * bo[j] - vv[j];                       // W'
+        const float b = cb[j] + (w - acc[h + j]) * irho;           // b = b_c + D W'
+        const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];
+        nb[j] = prox_coord_f(bh + vv[j] * irho, ff[j], PF);
+        nv[j] = vv[j] + rho * (bh - nb[j]);
+        if (STATS && f + j < N) {
+          st.s[0] += psi_coord<float>(nb[j], ff[j], P);
+          st.s[1] += nu_coord<float>(fabsf(rbc[f + j] - acc[h + j]), ff[j], P);
+          st.s[2] += (nb[j] - bo[j]) * (nb[j] - bo[j]);
+          st.s[3] += (b - nb[j]) * (b - nb[j]);
+        }
+      }
+      if (full) {
+        if (vec) {
+          *reinterpret_cast<float4*>(beta + rb + f) = make_float4(nb[0], nb[1], nb[2], nb[3]);
+          *reinterpret_cast<float4*>(beta + rb + f + 4) = make_float4(nb[4], nb[5], nb[6], nb[7]);
+          *reinterpret_cast<float4*>(V + rb + f) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+          *reinterpret_cast<float4*>(V + rb + f + 4) = make_float4(nv[4], nv[5], nv[6], nv[7]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            beta[rb + f + j] = nb[j];
+            V[rb + f + j] = nv[j];
+          }
+        }
+        float wv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) wv[j] = rho * nb[j] - nv[j];
+        store8_split(wv, whi, wlo, rw + f);                        // next W'
+        if (STATS && bhi) store8_split(nb, bhi, blo, rw + f);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (f + j < N) {
+            beta[rb + f + j] = nb[j];
+            V[rb + f + j] = nv[j];
+            split_store(rho * nb[j] - nv[j], whi, wlo, rw + f + j);
+            if (STATS && bhi) split_store(nb[j], bhi, blo, rw + f + j);
+          }
+      }
+    }
+  }
+
+  __device__ __forceinline__ void end(int r, int gq, State& st, float* sm) const {
+    if constexpr (STATS) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) sm[(gq * 4 + t) * 128 + r] = st.s[t];
+    }
+  }
+
+  __device__ __forceinline__ void finish(int t, int nthr, int m0, int nt, int M, int,
+                                         float* sm) const {
+    if constexpr (!STATS) return;
+    for (int r = t; r < 128; r += nthr) {
+      const int m = m0 + r;
+      if (m >= M || !active[m]) continue;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        g3part[((long long)k * nbm + nt) * K + m] = sm[(0 * 4 + k) * 128 + r] + sm[(1 * 4 + k) * 128 + r];
+        // the stop test sums nbm blocks; the blocks past this product's last tile are zero
+        if (nt == ntiles - 1)
+          for (int b = ntiles; b < nbm; ++b) g3part[((long long)k * nbm + b) * K + m] = 0.f;
+      }
+    }
+  }
+};
+
 // cluster-reduced product with the tile width chosen at setup (128 or 256 columns)
 template <int NS, class Epi>
 static int cred(Engine<float>& e, int bn, const TcOperand& A, const TcOperand& B, int M, int N,
@@ -327,8 +480,31 @@ static int mc_clusters(int bn) {
   }
 }
 
+// the transposed product P^T = U'^T X on CTA pairs (tile width 128 or 144 features)
+template <int NS, int BN, bool STATS>
+static int fused_pair_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
+  TcEpiAdmmT<STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
+                        e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
+                        (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
+                        e.nbm3, (e.p + BN - 1) / BN, e.K, e.p % 8 == 0 ? 1 : 0};
+  return tc_gemm_pair<BN, NS, TcEpiAdmmT<STATS>, 8>(e.st, Uop, XC, e.K, e.p, e.n, e.tc_pair3,
+                                                    e.slot_active, e.tc_err, epi);
+}
+
+template <int NS, int BN>
+static int pair_clusters_bn() {
+  const int a = tc_pair_clusters<BN, NS, TcEpiAdmmT<false>, 8>();
+  const int b = tc_pair_clusters<BN, NS, TcEpiAdmmT<true>, 8>();
+  return a < b ? a : b;
+}
+
 template <int NS>
 static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop, bool last) {
+  if (e.tc_pair3 > 0) {
+    if (e.tc_bn3 == 144)
+      return last ? fused_pair_bn<NS, 144, true>(e, XC, Uop) : fused_pair_bn<NS, 144, false>(e, XC, Uop);
+    return last ? fused_pair_bn<NS, 128, true>(e, XC, Uop) : fused_pair_bn<NS, 128, false>(e, XC, Uop);
+  }
   switch (e.tc_bn3) {
     case 80:
       return last ? fused_xtu_bn<NS, 80, true>(e, XC, Uop) : fused_xtu_bn<NS, 80, false>(e, XC, Uop);
@@ -451,19 +627,39 @@ static int pick_fused_shape(Engine<float>& e) {
   cudaStream_t st = e.st;
   const TcOperand XC{e.xc_hi, e.xc_lo, e.p, e.n, e.ldn};
   const TcOperand Uop{e.u_hi, e.u_lo, e.K, e.n, e.ldn};
-  std::vector<std::pair<int, int>> cands;
+  struct Shape {
+    int w, mc, pair;
+  };
+  std::vector<Shape> cands;
   for (int w : {64, 80, 96, 128}) {
     if (e.K > 64 * w) continue;
-    cands.push_back({w, 0});
+    cands.push_back({w, 0, 0});
     if ((e.K + w - 1) / w >= 2) {
       int cl = mc_clusters<NS>(w);
       if (cl > e.sms / 2) cl = e.sms / 2;
-      if (cl >= 1) cands.push_back({w, cl});
+      if (cl >= 1) cands.push_back({w, cl, 0});
     }
   }
+  // CTA pairs on the transposed product: 256 slots x 128 or 144 features per pair tile
+  if (e.K <= 64 * 256) {
+    for (int w : {128, 144}) {
+      int cl = w == 144 ? pair_clusters_bn<NS, 144>() : pair_clusters_bn<NS, 128>();
+      if (cl > e.sms / 2) cl = e.sms / 2;
+      if (cl >= 1) cands.push_back({w, 0, cl});
+    }
+  }
+  if (e.fused_kind > 0) {   // a requested kind: only its widths compete
+    std::vector<Shape> keep;
+    for (const Shape& c : cands)
+      if ((e.fused_kind == 1 && !c.mc && !c.pair) || (e.fused_kind == 2 && c.mc) ||
+          (e.fused_kind == 3 && c.pair))
+        keep.push_back(c);
+    cands.swap(keep);
+  }
   if (cands.empty()) return BNB_EINVAL;
-  e.tc_bn3 = cands[0].first;
-  e.tc_mc3 = cands[0].second;
+  e.tc_bn3 = cands[0].w;
+  e.tc_mc3 = cands[0].mc;
+  e.tc_pair3 = cands[0].pair;
   if (cands.size() == 1) return 0;
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0xff, sizeof(int) * e.K, st));   // nonzero: active
   cudaEvent_t ev[2];
@@ -475,8 +671,9 @@ static int pick_fused_shape(Engine<float>& e) {
   int rc = 0;
   for (int sweep = 0; sweep < 2 && !rc; ++sweep) {
     for (size_t ci = 0; ci < cands.size() && !rc; ++ci) {
-      e.tc_bn3 = cands[ci].first;
-      e.tc_mc3 = cands[ci].second;
+      e.tc_bn3 = cands[ci].w;
+      e.tc_mc3 = cands[ci].mc;
+      e.tc_pair3 = cands[ci].pair;
       if ((rc = fused_xtu<NS>(e, XC, Uop, false))) break;        // warm-up
       cudaEventRecord(ev[0], st);
       for (int r = 0; r < 5 && !rc; ++r) rc = fused_xtu<NS>(e, XC, Uop, false);
@@ -487,7 +684,7 @@ static int pick_fused_shape(Engine<float>& e) {
       if (tbest[ci] < 0 || ms < tbest[ci]) tbest[ci] = ms;
     }
   }
-  std::pair<int, int> pick = cands[0];
+  Shape pick = cands[0];
   float best = -1.f;
   for (size_t ci = 0; ci < cands.size(); ++ci)
     if (tbest[ci] >= 0 && (best < 0 || tbest[ci] < best)) {
@@ -497,8 +694,9 @@ static int pick_fused_shape(Engine<float>& e) {
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (rc) return rc;
-  e.tc_bn3 = pick.first;
-  e.tc_mc3 = pick.second;
+  e.tc_bn3 = pick.w;
+  e.tc_mc3 = pick.mc;
+  e.tc_pair3 = pick.pair;
   const long long Kp = (long long)e.K * e.p;
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, st));
   BNB_CUDA_OK(cudaMemsetAsync(e.beta, 0, sizeof(float) * Kp, st));

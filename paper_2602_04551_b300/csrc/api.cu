@@ -404,6 +404,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->max_depth = 256;
   o->lockstep = 0;
   o->mv_crossover = -1;
+  o->fused_shape = 0;
   return BNB_OK;
 }
 
@@ -416,6 +417,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->K = o.batch_K;
   e->dmax = o.max_depth;
   e->lockstep = o.lockstep ? 1 : 0;
+  e->fused_kind = o.fused_shape;
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
   e->qcap = o.queue_capacity;
@@ -456,7 +458,10 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   if (int rc = setup_data(*e, dX, dy)) return rc;
   if constexpr (sizeof(R) == 4) {
     if (e->tc_mode) {
-      if (int rc = setup_tc(*e)) return rc;
+      if (int rc = setup_tc(*e))
+        return rc == BNB_EINVAL ? fail(BNB_EINVAL, "fused_shape %d: no such shape runs here",
+                                       o.fused_shape)
+                                : rc;
       e->mv_cross = o.mv_crossover < 0 ? 16 : (o.mv_crossover > MV_MAX ? MV_MAX : o.mv_crossover);
       if (int rc = mv_setup(*e)) return rc;
       BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st_side, cudaStreamNonBlocking));
@@ -496,6 +501,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.check_every < 1) return fail(BNB_EINVAL, "check_every must be >= 1");
   if (o.max_depth < 8 || o.max_depth > 4096) return fail(BNB_EINVAL, "max_depth must be in [8, 4096]");
   if (o.mv_crossover < -1 || o.mv_crossover > 32) return fail(BNB_EINVAL, "mv_crossover must be in [-1, 32]");
+  if (o.fused_shape < 0 || o.fused_shape > 3) return fail(BNB_EINVAL, "fused_shape must be in [0, 3]");
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
@@ -538,6 +544,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
     h->stats.xw_cluster = h->ef->tc_c1;
     h->stats.fused_tile_width = h->ef->tc_bn3;
     h->stats.fused_clusters = h->ef->tc_mc3;
+    h->stats.fused_pairs = h->ef->tc_pair3;
   }
   *out = h;
   return BNB_OK;

@@ -1,4 +1,4 @@
-// diag.cu -- diagnostics entry point: the tcgen05 contraction on its own.
+// diag.cu -- diagnostics entry points: the tcgen05 contractions on their own.
 //
 // bnb_tc_gemm_check runs C = A B^T for FP64 inputs split into BF16 operands
 // (1 term: hi only; 3 terms: hi/lo pairs), K-major A (M x Kred) and B (N x Kred),
@@ -50,6 +50,31 @@ static int run_check_cluster(cudaStream_t st, const TcOperand& A, const TcOperan
   return tc_gemm_cred<256, NS>(st, A, B, M, N, Kd, cluster, nullptr, err, TcEpiPlain4{C, 0});
 }
 
+// plain FP32 store of the CTA-pair product, C[m + n M] (pair-kernel epilogue interface)
+struct TcEpiPairPlain {
+  static constexpr int SMEM_FLOATS = 0;
+  struct State {};
+  float* __restrict__ C;
+  __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N,
+                                             State&) const {
+    if (m >= M) return;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (n0 + j < N) C[(long long)(n0 + j) * M + m] = v[j];
+  }
+  __device__ __forceinline__ void end(int, int, State&, float*) const {}
+  __device__ __forceinline__ void finish(int, int, int, int, int, int, float*) const {}
+};
+
+template <int BN, int NS>
+static int run_check_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N,
+                          int Kd, float* C, int* err) {
+  const int cl = tc_pair_clusters<BN, NS, TcEpiPairPlain>();
+  if (cl < 1) return BNB_EINVAL;
+  return tc_gemm_pair<BN, NS>(st, A, B, M, N, Kd, cl, nullptr, err, TcEpiPairPlain{C});
+}
+
 // FP64 inputs -> BF16 (hi, and lo for 3 terms) K-major operands with leading dimension ld
 static int make_operands(cudaStream_t st, const double* dA, const double* dB, int M, int N, int Kd,
                          long long ld, __nv_bfloat16** ah, __nv_bfloat16** al, __nv_bfloat16** bh,
@@ -88,6 +113,44 @@ extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int
   if (!rc) rc = nsplit == 3   ? run_check_cluster<3>(st, A, B, M, N, Kd, cluster, dC, err)
                 : nsplit == 2 ? run_check_cluster<2>(st, A, B, M, N, Kd, cluster, dC, err)
                               : run_check_cluster<1>(st, A, B, M, N, Kd, cluster, dC, err);
+  if (!rc) rc = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : BNB_ECUDA;
+  if (!rc) rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : BNB_ECUDA;
+  cudaFree(ah);
+  cudaFree(al);
+  cudaFree(bh);
+  cudaFree(bl);
+  cudaFree(err);
+  return rc;
+}
+
+extern "C" int bnb_tc_gemm_check_pair(const double* dA, const double* dB, int M, int N, int Kd,
+                                      int nsplit, int bn, float* dC, int* err_out) {
+  using namespace bnb;
+  if (M <= 0 || N <= 0 || Kd <= 0 || M > 64 * 256 || nsplit < 1 || nsplit > 3 ||
+      (bn != 128 && bn != 144 && bn != 256))
+    return BNB_EINVAL;
+  cudaStream_t st = 0;
+  const long long ld = ((long long)Kd + 7) / 8 * 8;
+  __nv_bfloat16 *ah = nullptr, *al = nullptr, *bh = nullptr, *bl = nullptr;
+  int* err = nullptr;
+  int rc = make_operands(st, dA, dB, M, N, Kd, ld, &ah, &al, &bh, &bl);
+  if (!rc) rc = cudaMalloc(&err, sizeof(int)) == cudaSuccess ? 0 : BNB_ENOMEM;
+  if (!rc) rc = cudaMemset(err, 0, sizeof(int)) == cudaSuccess ? 0 : BNB_ECUDA;
+  TcOperand A{ah, al, M, Kd, ld}, B{bh, bl, N, Kd, ld};
+  if (!rc) {
+    const int key = bn * 4 + nsplit;
+    switch (key) {
+      case 128 * 4 + 1: rc = run_check_pair<128, 1>(st, A, B, M, N, Kd, dC, err); break;
+      case 128 * 4 + 2: rc = run_check_pair<128, 2>(st, A, B, M, N, Kd, dC, err); break;
+      case 128 * 4 + 3: rc = run_check_pair<128, 3>(st, A, B, M, N, Kd, dC, err); break;
+      case 144 * 4 + 1: rc = run_check_pair<144, 1>(st, A, B, M, N, Kd, dC, err); break;
+      case 144 * 4 + 2: rc = run_check_pair<144, 2>(st, A, B, M, N, Kd, dC, err); break;
+      case 144 * 4 + 3: rc = run_check_pair<144, 3>(st, A, B, M, N, Kd, dC, err); break;
+      case 256 * 4 + 1: rc = run_check_pair<256, 1>(st, A, B, M, N, Kd, dC, err); break;
+      case 256 * 4 + 2: rc = run_check_pair<256, 2>(st, A, B, M, N, Kd, dC, err); break;
+      default: rc = run_check_pair<256, 3>(st, A, B, M, N, Kd, dC, err); break;
+    }
+  }
   if (!rc) rc = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : BNB_ECUDA;
   if (!rc) rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : BNB_ECUDA;
   cudaFree(ah);

@@ -20,7 +20,12 @@
 //                           epilogue on the sum (X W'^T, G^-1 T, the check product);
 //   tc_gemm_persist_kernel  one CTA per SM over the tiles, double-buffered accumulator so
 //                           the epilogue of a tile overlaps the next tile (X^T U' with the
-//                           fused ADMM update).
+//                           fused ADMM update);
+//   tc_gemm_pair_kernel     the same product with the operands' roles exchanged (rows =
+//                           node slots, columns = features) on 256 x BN tiles computed by a
+//                           pair of CTAs on two SMs (tcgen05 cta_group::2): each CTA loads
+//                           128 rows of A and half of the B columns, so the B bytes each
+//                           SM receives per output are halved.
 // NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
 // accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
 // FP32-class arithmetic of the ADMM path.  NSPLIT = 2 keeps A as one BF16 term and B as
@@ -870,6 +875,314 @@ tc_gemm_persist_mc_kernel(const __grid_constant__ CUtensorMap ma_hi,
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(2 * G::PBUF)
+                 : "memory");
+  }
+}
+
+
+// ---- CTA pairs (tcgen05 cta_group::2): one 256 x BN tile on two SMs
+//
+// The two CTAs of a cluster of two form the pair; rank 0 (the leader) issues the MMAs.
+// A tile's rows [256 mt, 256 mt + 256) split as 128 per CTA (A operand and the
+// accumulator: each CTA's tensor memory holds its 128 rows x BN columns); its columns
+// [BN nt, BN nt + BN) split as BN/2 per CTA for the B operand, which the MMA reads from
+// both CTAs' shared memory.  Both CTAs load their halves with TMA into the same ring
+// offsets; the completion of both is counted on the leader's "full" barrier.
+
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+// TMA load into this CTA's shared memory, completion counted on the mbarrier at the
+// shared::cluster address `bar` (the leader's)
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar,
+                                                 int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// instruction descriptor: dense, D = F32, A = B = BF16, both K-major, M = 256 (the pair),
+// N = n
+__host__ __device__ constexpr uint32_t idesc_bf16_pair(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem, uint64_t ad, uint64_t bd,
+                                              uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// arrives on the mbarrier at the same offset in both CTAs once the leader's MMAs so far
+// have completed
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"((uint16_t)3)
+      : "memory");
+}
+
+// arrive (release, cluster scope) on the mbarrier at shared::cluster address `bar`
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// bounded wait with cluster-scope acquire (arrivals from the other CTA of the pair)
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t ph, int* err, int code) {
+  const uint32_t a = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(ph)
+        : "memory");
+    if (ok) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+  }
+  atomicOr(err, code);
+  return false;
+}
+
+template <int BN, int NSPLIT>
+struct PairGeo {
+  static constexpr int A_BYTES = BM * BK * 2;              // this CTA's 128 rows of A
+  static constexpr int B_BYTES = (BN / 2) * BK * 2;        // this CTA's BN/2 rows of B
+  // a stage holds [A hi | B hi], then [A lo] (2 and 3 terms), then [B lo] (3 terms): the
+  // 2-term product keeps B (the data) as one BF16 term and A (the iterate) as a pair
+  static constexpr int STAGE_BYTES =
+      A_BYTES * (NSPLIT >= 2 ? 2 : 1) + B_BYTES * (NSPLIT == 3 ? 2 : 1);
+  static constexpr int STAGES =
+      (200 * 1024) / STAGE_BYTES > 8 ? 8 : (200 * 1024) / STAGE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  // 256 tensor-memory columns per CTA: two accumulators up to 128 columns wide, else one
+  static constexpr int BUF = BN <= 128 ? 128 : 256;
+  static constexpr int NBUF = 256 / BUF;
+  static_assert(STAGES >= 2, "at least two stages");
+};
+
+// Persistent product on CTA pairs: cluster c walks the units u = c, c + clusters, ...
+// (row tile mt = u % mtiles, column tile nt = u / mtiles); units whose 256 rows are all
+// inactive are skipped by every role of both CTAs alike.
+//   full[s]      leader: both CTAs' TMA bytes of stage s (expect_tx by the leader)
+//   empty[s]     each CTA: the leader's MMAs have read stage s (multicast commit)
+//   tfull[b]     each CTA: accumulator b holds the tile (multicast commit)
+//   tempty[b]    leader: all epilogue warps of both CTAs have read accumulator b
+//   fin          each CTA: every MMA of the leader has completed (before teardown)
+// Tensor memory is allocated for the pair (cta_group::2, 256 columns in each CTA); the
+// CTAs check that they hold the same address and otherwise skip all work and report it.
+// Epilogue interface (rows = A rows, e.g. node slots; columns = B rows, e.g. features):
+//   typename Epi::State st; epi.begin(st);
+//   epi(row, first column, 16 accumulator values, M, N, st)   per 16-column chunk
+//   epi.end(r, gq, st, smem)      after the thread's last chunk of the tile (r = row in CTA)
+//   epi.finish(t, nthreads, first row of the CTA, nt, M, N, smem)  after the warps meet
+template <int BN, int NSPLIT, class Epi, int EPIW>
+__global__ void __launch_bounds__(64 + 32 * EPIW, 1)
+tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
+                    const __grid_constant__ CUtensorMap ma_lo,
+                    const __grid_constant__ CUtensorMap mb_hi,
+                    const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred,
+                    const int* __restrict__ active, int* err, Epi epi) {
+  using G = PairGeo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  constexpr int MAXMT = 64;                      // row tiles (M <= 64 x 256)
+  static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "pair MMA N: a multiple of 16 up to 256");
+  static_assert(EPIW % 4 == 0, "epilogue warps cover the four lane quarters");
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t tfull_bar[2];
+  __shared__ __align__(8) uint64_t tempty_bar[2];
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int tile_on[MAXMT];
+  __shared__ float epi_smem[Epi::SMEM_FLOATS > 0 ? Epi::SMEM_FLOATS : 1];
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int mtiles = (M + 255) / 256, ntiles = (N + BN - 1) / BN;
+  const int nunits = mtiles * ntiles;
+  const int nk = (Kred + BK - 1) / BK;
+  for (int j = threadIdx.x; j < MAXMT; j += blockDim.x) {
+    int on = 0;
+    if (j < mtiles) {
+      for (int r = 0; r < 256 && j * 256 + r < M; ++r)
+        if (active == nullptr || active[j * 256 + r]) {
+          on = 1;
+          break;
+        }
+    }
+    tile_on[j] = on;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 2 * EPIW);
+    }
+    mbar_init(&fin_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  cluster_sync_all();                            // both CTAs' barriers and TMEM exist
+  const uint32_t tmem = tmem_slot;
+  uint32_t peer_tmem;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];"
+               : "=r"(peer_tmem)
+               : "r"(mapa_u32(smem_u32(&tmem_slot), rank ^ 1u))
+               : "memory");
+  const bool pair_ok = peer_tmem == tmem;
+  if (!pair_ok && threadIdx.x == 0) atomicOr(err, 32);
+  const uint32_t full_l = mapa_u32(smem_u32(&full_bar[0]), 0);     // the leader's barriers
+  const uint32_t tempty_l = mapa_u32(smem_u32(&tempty_bar[0]), 0);
+
+  if (pair_ok && warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs): this CTA's halves of every stage
+    long long g = 0;
+    bool ok = true;
+    for (int u = cid; u < nunits && ok; u += ncl) {
+      const int mt = u % mtiles, nt = u / mtiles;
+      if (!tile_on[mt]) continue;
+      const int arow = mt * 256 + 128 * (int)rank, brow = nt * BN + (BN / 2) * (int)rank;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)(((g / S) & 1) ^ 1), err, 1)) {
+          ok = false;
+          break;
+        }
+        if (leader) mbar_expect_tx(&full_bar[s], 2 * G::STAGE_BYTES);
+        const int k = kb * BK;
+        const uint32_t fb = full_l + 8u * (uint32_t)s;
+        uint8_t* st0 = base + s * G::STAGE_BYTES;
+        tma_load_2d_pair(st0, &ma_hi, fb, k, arow);
+        tma_load_2d_pair(st0 + G::A_BYTES, &mb_hi, fb, k, brow);
+        if (NSPLIT >= 2) tma_load_2d_pair(st0 + G::A_BYTES + G::B_BYTES, &ma_lo, fb, k, arow);
+        if (NSPLIT == 3)
+          tma_load_2d_pair(st0 + 2 * G::A_BYTES + G::B_BYTES, &mb_lo, fb, k, brow);
+      }
+    }
+    // the leader's last stages count both CTAs' copies: they have all landed before the
+    // pair may be left (bounded like every wait)
+    if (leader)
+      for (long long j = g - S < 0 ? 0 : g - S; j < g; ++j)
+        mbar_wait(&full_bar[(int)(j % S)], (uint32_t)((j / S) & 1), err, 16);
+  } else if (pair_ok && warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader)
+    constexpr uint32_t idesc = idesc_bf16_pair(BN);
+    long long g = 0;
+    int i = 0;
+    bool ok = true;
+    for (int u = cid; u < nunits && ok; u += ncl) {
+      const int mt = u % mtiles;
+      if (!tile_on[mt]) continue;
+      const int b = i % G::NBUF, use = i / G::NBUF;
+      if (use >= 1 && !mbar_wait_cluster(&tempty_bar[b], (uint32_t)((use & 1) ^ 1), err, 8)) break;
+      fence_after();
+      const uint32_t acc_addr = tmem + (uint32_t)(b * G::BUF);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % S);
+        if (!mbar_wait(&full_bar[s], (uint32_t)((g / S) & 1), err, 2)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        uint8_t* st0 = base + s * G::STAGE_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ah = smem_desc_sw128(st0 + kk * 32);
+          const uint64_t bh = smem_desc_sw128(st0 + G::A_BYTES + kk * 32);
+          mma_bf16_pair(acc_addr, ah, bh, idesc, acc);
+          if (NSPLIT >= 2)
+            mma_bf16_pair(acc_addr, smem_desc_sw128(st0 + G::A_BYTES + G::B_BYTES + kk * 32), bh,
+                          idesc, 1u);
+          if (NSPLIT == 3)
+            mma_bf16_pair(acc_addr, ah,
+                          smem_desc_sw128(st0 + 2 * G::A_BYTES + G::B_BYTES + kk * 32), idesc, 1u);
+        }
+        mma_commit_pair(&empty_bar[s]);          // stage s free in both CTAs
+      }
+      if (!ok) break;
+      mma_commit_pair(&tfull_bar[b]);
+      ++i;
+    }
+    mma_commit_pair(&fin_bar);                   // after every MMA issued above
+  } else if (pair_ok && warp >= 2) {
+    // ---------------- epilogue warps (both CTAs): warp w reads TMEM lanes 32 (w % 4) ..
+    const int q = warp & 3;
+    const int gq = (warp - 2) >> 2;
+    int i = 0;
+    for (int u = cid; u < nunits; u += ncl) {
+      const int mt = u % mtiles, nt = u / mtiles;
+      if (!tile_on[mt]) continue;
+      const int b = i % G::NBUF, use = i / G::NBUF;
+      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), err, 4);
+      fence_after();
+      const int m0 = mt * 256 + 128 * (int)rank;
+      const int row = m0 + 32 * q + lane;
+      typename Epi::State es;
+      epi.begin(es);
+      if (ok) {
+#pragma unroll 1
+        for (int c = 16 * gq; c < BN; c += 16 * (EPIW / 4)) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::BUF + c), v);
+          epi(row, nt * BN + c, v, M, N, es);
+        }
+      }
+      fence_before();
+      if (lane == 0) mbar_arrive_cluster(tempty_l + 8u * (uint32_t)b);
+      epi.end(32 * q + lane, gq, es, epi_smem);
+      uint32_t all_ok;
+      asm volatile(
+          "{\n .reg .pred p, r;\n setp.ne.u32 p, %1, 0;\n"
+          " bar.red.and.pred r, 1, %2, p;\n selp.u32 %0, 1, 0, r;\n}\n"
+          : "=r"(all_ok)
+          : "r"((uint32_t)ok), "n"(32 * EPIW)
+          : "memory");
+      if (all_ok) epi.finish(threadIdx.x - 64, 32 * EPIW, m0, nt, M, N, epi_smem);
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * EPIW) : "memory");
+      ++i;
+      if (!all_ok) break;
+    }
+  }
+  // teardown: every MMA of the leader (which writes both CTAs' tensor memory) has
+  // completed, no remote signal can still arrive, then the pair frees its columns
+  if (pair_ok && warp == 1) {
+    if (lane == 0) mbar_wait(&fin_bar, 0u, err, 64);
+    __syncwarp();
+  }
+  fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
                  : "memory");
   }
 }

@@ -267,6 +267,82 @@ int tc_gemm_persist_mc(cudaStream_t st, const TcOperand& A, const TcOperand& B, 
   return 0;
 }
 
+// Co-resident clusters (CTA pairs) of the pair kernel (0: none).
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
+int tc_pair_clusters() {
+  using G = tc::PairGeo<BN, NSPLIT>;
+  static int cached = -1;
+  if (cached < 0) {
+    auto kern = tc::tc_gemm_pair_kernel<BN, NSPLIT, Epi, EPIW>;
+    cached = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(64 + 32 * EPIW);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      nc = 0;
+    }
+    cached = nc;
+  }
+  return cached;
+}
+
+// C = A B^T on CTA pairs (tc_gemm_pair_kernel): 256 x BN tiles, at most `clusters` pairs.
+// A: M rows (boxes of 128 rows, hi and, for 2 and 3 terms, lo); B: N rows (boxes of BN/2
+// rows, hi and, for 3 terms, lo).  M <= 64 x 256.
+template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
+int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
+                 int clusters, const int* active, int* err, Epi epi) {
+  using G = tc::PairGeo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  if (M > 64 * 256 || clusters < 1) return BNB_EINVAL;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN / 2)) return rc;
+  al = ah;
+  bl = bh;
+  if (NSPLIT >= 2)
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (NSPLIT == 3)
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN / 2)) return rc;
+  auto kern = tc::tc_gemm_pair_kernel<BN, NSPLIT, Epi, EPIW>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    attr_set = true;
+  }
+  const long long units = (long long)((M + 255) / 256) * ((N + BN - 1) / BN);
+  const int ncl = (int)(units < clusters ? units : clusters);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * ncl);
+  cfg.blockDim = dim3(64 + 32 * EPIW);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, active, err, epi));
+  return 0;
+}
+
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;

@@ -33,6 +33,7 @@ def main():
     ap.add_argument("--rounds", type=int, default=3)
     ap.add_argument("--prime-seconds", type=float, default=30.0)
     ap.add_argument("--mv-crossover", type=int, default=-1)
+    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--no-graphs", action="store_true")
     a = ap.parse_args()
     c = datagen.CONFIGS[a.workload]
@@ -41,7 +42,8 @@ def main():
     lam0 = a.lam0_frac * datagen.lambda0_scale(inst.X, inst.y, c["lam2"])
     o = bnb.bnb_options_default(M=M, batch_K=a.K, rho=a.rho, precision=a.precision,
                                 queue_capacity=1 << 20, time_limit_s=1e9,
-                                mv_crossover=a.mv_crossover, use_graphs=0 if a.no_graphs else 1)
+                                mv_crossover=a.mv_crossover, use_graphs=0 if a.no_graphs else 1,
+                                fused_shape=a.fused_shape)
     with bnb.bnb_create(inst.X, inst.y, lam0, c["lam2"], o) as h:
         bnb.bnb_solve_start(h, 1e-4)
         t0 = time.time()

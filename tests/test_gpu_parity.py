@@ -177,6 +177,57 @@ def test_one_admm_iteration_full_size_wide_batch(prec):
     _one_iteration_check(inst, lam0, lam2, M, prec, K=1000, Kopt=1024, rows=[0, 517, 999], seed=5)
 
 
+SHAPES = [pytest.param(1, id="single"), pytest.param(2, id="clusters_of_two"),
+          pytest.param(3, id="cta_pairs")]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec", [3, 4, 2])
+def test_one_admm_iteration_every_fused_shape(shape, prec):
+    """Each shape of the fused X^T U' product (one CTA per tile, clusters of two sharing
+    the X tile, the transposed product on CTA pairs) gives the oracle's iteration."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=128, rows=range(45), seed=13,
+                         fused_shape=shape)
+
+
+def test_one_admm_iteration_cta_pairs_full_size():
+    """c2 at K=512 on CTA pairs: slots on both CTAs of both row tiles are sampled (0, 127,
+    128 and 255 of the first tile, 256 and 511 of the second)."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512,
+                         rows=[0, 127, 128, 255, 256, 511], seed=14, fused_shape=3)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_converged_bounds_and_solve_every_fused_shape(shape):
+    """Converged node bounds (the stop-test sums of the fused epilogue decide when a node
+    retires) stay valid and tight, and a solve returns the stored optimum, whatever the
+    shape of the fused product."""
+    inst, lam0, lam2, M = _inst("c2_small", 2)
+    rng = np.random.default_rng(22)
+    fix = datagen.random_fixings(inst.p, 20, rng, 10)
+    with _handle(inst, lam0, lam2, M, 3, K=128, node_tol=1e-5, max_admm_iter=20000,
+                 mv_crossover=0, fused_shape=shape) as h:
+        out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+    for k in range(20):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+        assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
+    case = json.load(open(GOLD))["cases"][0]
+    ci = datagen.config_instance("c1", case["instance"])
+    o = bnb.bnb_options_default(M=case["M"], precision=3, batch_K=128, node_tol=1e-7,
+                                max_admm_iter=5000, queue_capacity=1 << 16, time_limit_s=60.0,
+                                mv_crossover=0, fused_shape=shape)
+    with bnb.bnb_create(ci.X, ci.y, case["lambda0"], case["lambda2"], o) as h:
+        res = bnb.bnb_solve(h, case["gap"])
+        st = bnb.bnb_get_stats(h)
+        assert (st["fused_pairs"] > 0) == (shape == 3)
+        assert (st["fused_clusters"] > 0) == (shape == 2)
+    assert [int(i) for i in np.nonzero(res["beta"])[0]] == case["support"]
+    assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
+
+
 # ------------------------------------------------------------------ converged node
 
 

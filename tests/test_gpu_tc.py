@@ -81,6 +81,45 @@ def test_tc_gemm_cluster_is_deterministic():
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
 
 
+PAIR_CASES = [
+    # M, N, Kd, nsplit, bn
+    (256, 144, 64, 1, 144),           # one pair tile, one K step
+    (512, 5000, 1000, 3, 144),        # (X^T U')^T of a n=1000, p=5000, K=512 batch
+    (300, 333, 777, 3, 128),          # ragged rows (second tile partial), columns and K
+    (200, 100, 1000, 2, 144),         # 2 terms: A the pair, B one BF16 term
+    (1000, 700, 500, 1, 256),         # one accumulator of 256 columns
+    (2048, 5000, 256, 3, 128),        # 320 tiles: several per pair, both accumulators
+    (4096, 2000, 128, 1, 256),        # 128 tiles on single-accumulator pairs
+]
+
+
+@pytest.mark.parametrize("M,N,Kd,nsplit,bn", PAIR_CASES)
+def test_tc_gemm_pair_matches_plain_product(M, N, Kd, nsplit, bn):
+    g = torch.Generator(device="cpu").manual_seed(M * 3 + N * 17 + Kd + bn)
+    A = torch.randn(M, Kd, generator=g, dtype=torch.float64)
+    B = torch.randn(N, Kd, generator=g, dtype=torch.float64)
+    dC = torch.full((N, M), float("nan"), dtype=torch.float32, device="cuda")
+    err = bnb.bnb_tc_gemm_check_pair(A.cuda(), B.cuda(), M, N, Kd, nsplit, bn, dC)
+    assert err == 0
+    C = dC.cpu().double().T.numpy()
+    if nsplit == 2:   # in the pair kernel the first operand is the hi/lo pair
+        _compare(B, A, C.T, nsplit)
+    else:
+        _compare(A, B, C, nsplit)
+
+
+def test_tc_gemm_pair_is_deterministic():
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A = torch.randn(512, 1000, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(5000, 1000, generator=g, dtype=torch.float64).cuda()
+    outs = []
+    for _ in range(3):
+        dC = torch.empty(5000, 512, dtype=torch.float32, device="cuda")
+        assert bnb.bnb_tc_gemm_check_pair(A, B, 512, 5000, 1000, 3, 144, dC) == 0
+        outs.append(dC.cpu())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
 def _compare(A, B, C, nsplit):
     if nsplit == 2:
         # A rounded to one BF16 term (ties to even), B kept to ~16 bits by its pair
