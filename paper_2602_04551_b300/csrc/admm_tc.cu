@@ -310,7 +310,8 @@ struct TcEpiAdmm {
 // tile, then over the epilogue warps of the lane quarter in shared memory.
 template <bool STATS>
 struct TcEpiAdmmT {
-  static constexpr int SMEM_FLOATS = STATS ? 2 * 4 * 128 : 0;   // [warp group][stat][row]
+  static constexpr int MAXG = 4;                                 // warp groups per lane quarter
+  static constexpr int SMEM_FLOATS = STATS ? MAXG * 4 * 128 : 0; // [group][stat][row]
   struct State {
     float s[4];
   };
@@ -328,69 +329,79 @@ struct TcEpiAdmmT {
   long long p, ldp;
   int nbm, ntiles, K;
   int vec;                          // p % 8 == 0: vector loads of beta, V, fix
+  int groups;                       // epilogue warps per lane quarter (<= MAXG)
 
   __device__ __forceinline__ void begin(State& st) const {
 #pragma unroll
     for (int t = 0; t < 4; ++t) st.s[t] = 0.f;
   }
 
+  __device__ __forceinline__ static void ld8(const float* q, float* v) {
+    const float4 a = *reinterpret_cast<const float4*>(q);
+    const float4 b = *reinterpret_cast<const float4*>(q + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  __device__ __forceinline__ static void st8(float* q, const float* v) {
+    *reinterpret_cast<float4*>(q) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(q + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+
+  // the 16 features f0 .. f0 + 15 of slot m: every load of the chunk is issued before
+  // the arithmetic (one round trip per chunk)
   __device__ __forceinline__ void operator()(int m, int f0, const float (&acc)[16], int M, int N,
                                              State& st) const {
     if (m >= M || !active[m]) return;
     const float rho = PF.rho, irho = PF.irho;
     const long long rb = (long long)m * p, rw = (long long)m * ldp;
+    float bo[16], vv[16], cb[16];
+    int ff[16];
+    const bool full = f0 + 16 <= N;
+    if (full && vec) {
+      ld8(beta + rb + f0, bo);
+      ld8(beta + rb + f0 + 8, bo + 8);
+      ld8(V + rb + f0, vv);
+      ld8(V + rb + f0 + 8, vv + 8);
+      const uint2 x0 = *reinterpret_cast<const uint2*>(fix + rb + f0);
+      const uint2 x1 = *reinterpret_cast<const uint2*>(fix + rb + f0 + 8);
+      const uint32_t w[4] = {x0.x, x0.y, x1.x, x1.y};
+#pragma unroll
+      for (int j = 0; j < 16; ++j) ff[j] = (int)(int8_t)((w[j >> 2] >> (8 * (j & 3))) & 0xffu);
+      ld8(bc + f0, cb);
+      ld8(bc + f0 + 8, cb + 8);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const bool in = f0 + j < N;
+        bo[j] = in ? beta[rb + f0 + j] : 0.f;
+        vv[j] = in ? V[rb + f0 + j] : 0.f;
+        ff[j] = in ? (int)fix[rb + f0 + j] : 0;
+        cb[j] = in ? bc[f0 + j] : 0.f;
+      }
+    }
 #pragma unroll
     for (int h = 0; h < 16; h += 8) {
       const int f = f0 + h;
       if (f >= N) break;
-      const bool full = f + 8 <= N;
-      float bo[8], vv[8], cb[8];
-      int ff[8];
-      if (full && vec) {
-        const float4 b0 = *reinterpret_cast<const float4*>(beta + rb + f);
-        const float4 b1 = *reinterpret_cast<const float4*>(beta + rb + f + 4);
-        const float4 v0 = *reinterpret_cast<const float4*>(V + rb + f);
-        const float4 v1 = *reinterpret_cast<const float4*>(V + rb + f + 4);
-        const uint2 fx = *reinterpret_cast<const uint2*>(fix + rb + f);
-        bo[0] = b0.x; bo[1] = b0.y; bo[2] = b0.z; bo[3] = b0.w;
-        bo[4] = b1.x; bo[5] = b1.y; bo[6] = b1.z; bo[7] = b1.w;
-        vv[0] = v0.x; vv[1] = v0.y; vv[2] = v0.z; vv[3] = v0.w;
-        vv[4] = v1.x; vv[5] = v1.y; vv[6] = v1.z; vv[7] = v1.w;
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          ff[j] = (int)(int8_t)(((j < 4 ? fx.x : fx.y) >> (8 * (j & 3))) & 0xffu);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const bool in = f + j < N;
-          bo[j] = in ? beta[rb + f + j] : 0.f;
-          vv[j] = in ? V[rb + f + j] : 0.f;
-          ff[j] = in ? (int)fix[rb + f + j] : 0;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 8; ++j) cb[j] = f + j < N ? bc[f + j] : 0.f;
       float nb[8], nv[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const float w = rho * bo[j] - vv[j];                       // W'
-        const float b = cb[j] + (w - acc[h + j]) * irho;           // b = b_c + D W'
-        const float bh = PF.alpha * b + PF.one_minus_alpha * bo[j];
-        nb[j] = prox_coord_f(bh + vv[j] * irho, ff[j], PF);
-        nv[j] = vv[j] + rho * (bh - nb[j]);
+        const float w = rho * bo[h + j] - vv[h + j];               // W'
+        const float b = cb[h + j] + (w - acc[h + j]) * irho;       // b = b_c + D W'
+        const float bh = PF.alpha * b + PF.one_minus_alpha * bo[h + j];
+        nb[j] = prox_coord_f(bh + vv[h + j] * irho, ff[h + j], PF);
+        nv[j] = vv[h + j] + rho * (bh - nb[j]);
         if (STATS && f + j < N) {
-          st.s[0] += psi_coord<float>(nb[j], ff[j], P);
-          st.s[1] += nu_coord<float>(fabsf(rbc[f + j] - acc[h + j]), ff[j], P);
-          st.s[2] += (nb[j] - bo[j]) * (nb[j] - bo[j]);
+          st.s[0] += psi_coord<float>(nb[j], ff[h + j], P);
+          st.s[1] += nu_coord<float>(fabsf(rbc[f + j] - acc[h + j]), ff[h + j], P);
+          st.s[2] += (nb[j] - bo[h + j]) * (nb[j] - bo[h + j]);
           st.s[3] += (b - nb[j]) * (b - nb[j]);
         }
       }
-      if (full) {
+      if (f + 8 <= N) {
         if (vec) {
-          *reinterpret_cast<float4*>(beta + rb + f) = make_float4(nb[0], nb[1], nb[2], nb[3]);
-          *reinterpret_cast<float4*>(beta + rb + f + 4) = make_float4(nb[4], nb[5], nb[6], nb[7]);
-          *reinterpret_cast<float4*>(V + rb + f) = make_float4(nv[0], nv[1], nv[2], nv[3]);
-          *reinterpret_cast<float4*>(V + rb + f + 4) = make_float4(nv[4], nv[5], nv[6], nv[7]);
+          st8(beta + rb + f, nb);
+          st8(V + rb + f, nv);
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -431,7 +442,9 @@ struct TcEpiAdmmT {
       if (m >= M || !active[m]) continue;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        g3part[((long long)k * nbm + nt) * K + m] = sm[(0 * 4 + k) * 128 + r] + sm[(1 * 4 + k) * 128 + r];
+        float a = 0.f;
+        for (int g = 0; g < groups; ++g) a += sm[(g * 4 + k) * 128 + r];   // in group order
+        g3part[((long long)k * nbm + nt) * K + m] = a;
         // the stop test sums nbm blocks; the blocks past this product's last tile are zero
         if (nt == ntiles - 1)
           for (int b = ntiles; b < nbm; ++b) g3part[((long long)k * nbm + b) * K + m] = 0.f;
@@ -480,21 +493,26 @@ static int mc_clusters(int bn) {
   }
 }
 
-// the transposed product P^T = U'^T X on CTA pairs (tile width 128 or 144 features)
+// the transposed product P^T = U'^T X on CTA pairs (tile width 128 or 144 features);
+// its epilogue is exposed (one tile per pair at c2 sizes), so it runs 12 warps (three per
+// TMEM lane quarter) for more loads in flight
+constexpr int PAIR_EPIW = 12;
 template <int NS, int BN, bool STATS>
 static int fused_pair_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
   TcEpiAdmmT<STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                         e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
                         (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
-                        e.nbm3, (e.p + BN - 1) / BN, e.K, e.p % 8 == 0 ? 1 : 0};
-  return tc_gemm_pair<BN, NS, TcEpiAdmmT<STATS>, 8>(e.st, Uop, XC, e.K, e.p, e.n, e.tc_pair3,
-                                                    e.slot_active, e.tc_err, epi);
+                        e.nbm3, (e.p + BN - 1) / BN, e.K, e.p % 8 == 0 ? 1 : 0,
+                        PAIR_EPIW / 4};
+  return tc_gemm_pair<BN, NS, TcEpiAdmmT<STATS>, PAIR_EPIW>(e.st, Uop, XC, e.K, e.p, e.n,
+                                                            e.tc_pair3, e.slot_active, e.tc_err,
+                                                            epi);
 }
 
 template <int NS, int BN>
 static int pair_clusters_bn() {
-  const int a = tc_pair_clusters<BN, NS, TcEpiAdmmT<false>, 8>();
-  const int b = tc_pair_clusters<BN, NS, TcEpiAdmmT<true>, 8>();
+  const int a = tc_pair_clusters<BN, NS, TcEpiAdmmT<false>, PAIR_EPIW>();
+  const int b = tc_pair_clusters<BN, NS, TcEpiAdmmT<true>, PAIR_EPIW>();
   return a < b ? a : b;
 }
 
