@@ -7,9 +7,10 @@
 // (at most MV_MAX of them).  With a few active nodes a 128-wide tensor-core tile is
 // almost all padding, while these kernels read X once per product and do only the
 // useful work:
-//   k_mv_part     Y_c = A v_c over a chunk of the contraction (a thread per 4 output
-//                 rows, float4 loads of the column-major A, eight columns in flight,
-//                 the vectors of 16 slots staged in shared memory); A = H = G^-1 X for
+//   k_mv_part     Y_c = A v_c over a chunk of the contraction (lanes over 4 output rows
+//                 each with float4 loads of the column-major A, the chunk's columns over
+//                 8 warps with eight in flight each, the vectors of 16 slots staged in
+//                 shared memory, warp partials added in order); A = H = G^-1 X for
 //                 U' = H W', A = X for the check product X beta; partial sums per chunk
 //   k_mv_reduce   sum of the chunks in order, plus the product's epilogue (T; U', U and
 //                 the stop-test sums of r = y - U; the check ||y - X beta||^2)
@@ -79,10 +80,13 @@ __device__ __forceinline__ float mv_vec(int s, long long j, const float* beta, c
 }
 
 // part[z][c][i] = sum_{j in chunk z} A[i + j lda] v_c[j],  c = compact slot index.
-// R rows per thread (4: float4 loads, needs lda and M multiples of 4).
-// grid (ceil(M / (128 R)), Z, MV_MAX / MV_G); block 128.
+// A block takes 32 R rows (lanes over the rows, R per lane: float4 loads for R = 4, which
+// needs lda and M multiples of 4) and the chunk's columns interleaved over its 8 warps
+// (eight columns in flight per warp); the warps' partial sums are added in warp order in
+// shared memory.  grid (ceil(M / (32 R)), Z, MV_MAX / MV_G); block 256; dynamic shared
+// memory (MV_G zchunk + 8 MV_G 32 R) floats: the chunk's vectors, then the partials.
 template <int MODE, int R>
-__global__ void __launch_bounds__(128) k_mv_part(const float* __restrict__ A, long long lda, int M,
+__global__ void __launch_bounds__(256) k_mv_part(const float* __restrict__ A, long long lda, int M,
                                                  int L, int zchunk,
                                                  const int* __restrict__ act_list,
                                                  const int* __restrict__ act_count,
@@ -90,82 +94,90 @@ __global__ void __launch_bounds__(128) k_mv_part(const float* __restrict__ A, lo
                                                  const float* __restrict__ V, float rho,
                                                  const float* __restrict__ src, long long ldv,
                                                  float* __restrict__ part) {
-  __shared__ float vs[MV_G][MV_TJ];
+  extern __shared__ float smv[];
+  constexpr int RB = 32 * R;                              // rows of the block
+  float* vs = smv;                                        // [MV_G][zchunk]
+  float* red = smv + MV_G * zchunk;                       // [8][MV_G][RB]
   const int a = min(*act_count, MV_MAX);
   const int c0 = blockIdx.z * MV_G;
   if (c0 >= a) return;
   const int nc = min(MV_G, a - c0);
-  const int i0 = (blockIdx.x * 128 + threadIdx.x) * R;
-  const int j0 = blockIdx.y * zchunk, j1 = min(L, j0 + zchunk);
+  const int j0 = blockIdx.y * zchunk, jn = min(L, j0 + zchunk) - j0;
+  for (int e = threadIdx.x; e < MV_G * zchunk; e += blockDim.x) {
+    const int c = e / zchunk, jj = e % zchunk;
+    vs[e] = (c < nc && jj < jn) ? mv_vec<MODE>(act_list[c0 + c], j0 + jj, beta, V, rho, src, ldv)
+                                : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * RB + lane * R;
   float acc[R][MV_G];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
     for (int c = 0; c < MV_G; ++c) acc[r][c] = 0.f;
-  for (int jb = j0; jb < j1; jb += MV_TJ) {
-    for (int e = threadIdx.x; e < MV_G * MV_TJ; e += 128) {
-      const int c = e / MV_TJ, jj = e % MV_TJ, j = jb + jj;
-      vs[c][jj] = (c < nc && j < j1) ? mv_vec<MODE>(act_list[c0 + c], j, beta, V, rho, src, ldv)
-                                     : 0.f;
-    }
-    __syncthreads();
-    if (i0 < M) {
-      const int jn = min(MV_TJ, j1 - jb);
-      const float* ap = A + (long long)jb * lda + i0;
-      int jj = 0;
-      for (; jj + 8 <= jn; jj += 8) {          // eight independent column loads in flight
-        float x[8][R];
+  if (i0 < M) {
+    const float* ap = A + (long long)j0 * lda + i0;
+    int jj = w;                                           // this warp: columns w, w + 8, ...
+    for (; jj + 56 < jn; jj += 64) {
+      float x[8][R];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if constexpr (R == 4) {
-            const float4 t = *reinterpret_cast<const float4*>(ap + (long long)(jj + u) * lda);
-            x[u][0] = t.x;
-            x[u][1] = t.y;
-            x[u][2] = t.z;
-            x[u][3] = t.w;
-          } else {
-            x[u][0] = ap[(long long)(jj + u) * lda];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-          for (int c = 0; c < MV_G; ++c) {
-            const float w = vs[c][jj + u];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[u][r], w, acc[r][c]);
-          }
-      }
-      for (; jj < jn; ++jj) {
-        float x[R];
+      for (int u = 0; u < 8; ++u) {
+        const float* q = ap + (long long)(jj + 8 * u) * lda;
         if constexpr (R == 4) {
-          const float4 t = *reinterpret_cast<const float4*>(ap + (long long)jj * lda);
-          x[0] = t.x;
-          x[1] = t.y;
-          x[2] = t.z;
-          x[3] = t.w;
+          const float4 t = *reinterpret_cast<const float4*>(q);
+          x[u][0] = t.x;
+          x[u][1] = t.y;
+          x[u][2] = t.z;
+          x[u][3] = t.w;
         } else {
-          x[0] = ap[(long long)jj * lda];
+          x[u][0] = q[0];
         }
-#pragma unroll
-        for (int c = 0; c < MV_G; ++c)
-#pragma unroll
-          for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[r], vs[c][jj], acc[r][c]);
       }
-    }
-    __syncthreads();
-  }
-  if (i0 < M)
 #pragma unroll
-    for (int c = 0; c < MV_G; ++c) {
-      if (c >= nc) break;
-      float* out = part + ((long long)blockIdx.y * MV_MAX + c0 + c) * M + i0;
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int c = 0; c < MV_G; ++c) {
+          const float wv = vs[c * zchunk + jj + 8 * u];
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[u][r], wv, acc[r][c]);
+        }
+    }
+    for (; jj < jn; jj += 8) {
+      const float* q = ap + (long long)jj * lda;
+      float x[R];
       if constexpr (R == 4) {
-        *reinterpret_cast<float4*>(out) = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+        const float4 t = *reinterpret_cast<const float4*>(q);
+        x[0] = t.x;
+        x[1] = t.y;
+        x[2] = t.z;
+        x[3] = t.w;
       } else {
-        out[0] = acc[0][c];
+        x[0] = q[0];
+      }
+#pragma unroll
+      for (int c = 0; c < MV_G; ++c) {
+        const float wv = vs[c * zchunk + jj];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r][c] = fmaf(x[r], wv, acc[r][c]);
       }
     }
+  }
+#pragma unroll
+  for (int c = 0; c < MV_G; ++c)
+#pragma unroll
+    for (int r = 0; r < R; ++r) red[(w * MV_G + c) * RB + lane * R + r] = acc[r][c];
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * RB; e += blockDim.x) {
+    const int c = e / RB, rr = e % RB;
+    const int i = blockIdx.x * RB + rr;
+    if (i < M) {
+      float sum = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) sum += red[(ww * MV_G + c) * RB + rr];
+      part[((long long)blockIdx.y * MV_MAX + c0 + c) * M + i] = sum;
+    }
+  }
 }
 
 // Sum of the Z chunks in order, per (128-row block, compact slot); block 128.
@@ -407,29 +419,36 @@ __global__ void k_mv_fold(const float* __restrict__ g3mv, int nb32, const int* _
 
 // ----------------------------------------------------------------------------- host
 
-// chunks of the contraction for k_mv_part: about two blocks per SM
+// chunks of the contraction for k_mv_part: about two blocks per SM, chunks of at most
+// MV_ZCOL columns (a multiple of 8: the warps' column interleave)
+constexpr int MV_ZCOL = 1024;
 static int mv_chunks(int M, int L, int R, int sms, int* zchunk) {
-  const int rows = (M + 128 * R - 1) / (128 * R);
+  const int rows = (M + 32 * R - 1) / (32 * R);
   int Z = (2 * sms + rows - 1) / rows;
-  const int zmax = (L + MV_TJ - 1) / MV_TJ;
-  if (Z > zmax) Z = zmax;
+  if (Z < (L + MV_ZCOL - 1) / MV_ZCOL) Z = (L + MV_ZCOL - 1) / MV_ZCOL;
   if (Z > MV_ZMAX) Z = MV_ZMAX;
+  if (Z > (L + 7) / 8) Z = (L + 7) / 8;
   if (Z < 1) Z = 1;
   int zc = (L + Z - 1) / Z;
-  zc = (zc + MV_TJ - 1) / MV_TJ * MV_TJ;
+  zc = (zc + 7) / 8 * 8;
   *zchunk = zc;
   return (L + zc - 1) / zc;
+}
+
+static size_t mv_part_smem(int zc, int R) {
+  return sizeof(float) * ((size_t)MV_G * zc + (size_t)8 * MV_G * 32 * R);
 }
 
 template <int MODE>
 static void mv_part(Engine<float>& e, const float* A, int Z, int zc, int R, const float* beta,
                     const float* V, float rho) {
   const int n = e.n, p = e.p, G = MV_MAX / MV_G;
+  const size_t sh = mv_part_smem(zc, R);
   if (R == 4)
-    k_mv_part<MODE, 4><<<dim3((n + 511) / 512, Z, G), 128, 0, e.st>>>(
+    k_mv_part<MODE, 4><<<dim3((n + 127) / 128, Z, G), 256, sh, e.st>>>(
         A, n, n, p, zc, e.act_list, e.act_count, beta, V, rho, nullptr, p, e.mv_part);
   else
-    k_mv_part<MODE, 1><<<dim3((n + 127) / 128, Z, G), 128, 0, e.st>>>(
+    k_mv_part<MODE, 1><<<dim3((n + 31) / 32, Z, G), 256, sh, e.st>>>(
         A, n, n, p, zc, e.act_list, e.act_count, beta, V, rho, nullptr, p, e.mv_part);
 }
 
@@ -483,6 +502,11 @@ int mv_setup(Engine<float>& e) {
     e.mv_cross = 0;                               // U' of a group does not fit: no matvec form
     return 0;
   }
+  const int psh = (int)mv_part_smem(MV_ZCOL, 4);  // the largest chunk
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_part<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, psh));
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_part<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, psh));
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_part<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, psh));
+  BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_part<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, psh));
   BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_prox<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)ush));
   BNB_CUDA_OK(cudaFuncSetAttribute(k_mv_prox<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -54,10 +54,12 @@ static int run_check_cluster(cudaStream_t st, const TcOperand& A, const TcOperan
 struct TcEpiPairPlain {
   static constexpr int SMEM_FLOATS = 0;
   struct State {};
+  struct Chunk {};
   float* __restrict__ C;
   __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void load(int, int, int, int, Chunk&) const {}
   __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N,
-                                             State&) const {
+                                             State&, const Chunk&) const {
     if (m >= M) return;
 #pragma unroll
     for (int j = 0; j < 16; ++j)

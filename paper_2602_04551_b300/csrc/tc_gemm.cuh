@@ -984,7 +984,9 @@ struct PairGeo {
 // CTAs check that they hold the same address and otherwise skip all work and report it.
 // Epilogue interface (rows = A rows, e.g. node slots; columns = B rows, e.g. features):
 //   typename Epi::State st; epi.begin(st);
-//   epi(row, first column, 16 accumulator values, M, N, st)   per 16-column chunk
+//   typename Epi::Chunk ck; epi.load(row, first column, M, N, ck)   the chunk's other
+//                                 inputs (issued for the first chunk before the wait)
+//   epi(row, first column, 16 accumulator values, M, N, st, ck)   per 16-column chunk
 //   epi.end(r, gq, st, smem)      after the thread's last chunk of the tile (r = row in CTA)
 //   epi.finish(t, nthreads, first row of the CTA, nt, M, N, smem)  after the warps meet
 template <int BN, int NSPLIT, class Epi, int EPIW>
@@ -1141,18 +1143,24 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
       const int mt = u % mtiles, nt = u / mtiles;
       if (!tile_on[mt]) continue;
       const int b = i % G::NBUF, use = i / G::NBUF;
-      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), err, 4);
-      fence_after();
       const int m0 = mt * 256 + 128 * (int)rank;
       const int row = m0 + 32 * q + lane;
+      // the node state of the thread's first chunk is loaded before the accumulator is
+      // ready, so that its latency overlaps the tile's MMAs
+      typename Epi::Chunk ck;
+      const int cf = 16 * gq;
+      if (cf < BN) epi.load(row, nt * BN + cf, M, N, ck);
+      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), err, 4);
+      fence_after();
       typename Epi::State es;
       epi.begin(es);
       if (ok) {
 #pragma unroll 1
-        for (int c = 16 * gq; c < BN; c += 16 * (EPIW / 4)) {
+        for (int c = cf; c < BN; c += 16 * (EPIW / 4)) {
+          if (c != cf) epi.load(row, nt * BN + c, M, N, ck);
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::BUF + c), v);
-          epi(row, nt * BN + c, v, M, N, es);
+          epi(row, nt * BN + c, v, M, N, es, ck);
         }
       }
       fence_before();
