@@ -391,34 +391,36 @@ def reference_arm(args):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel per
 # launch, from one ncu capture summarised under profiles/; it is reported only while the
 # source that defines the captured kernel is unchanged (hash of the kernel template, its
-# epilogue, the shared device helpers and the tile geometry), else null.
-SHARED_SOURCE_BLOCKS = (
-    ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct Geo {", "\n};\n"),
-    ("admm_tc.cu", "struct TcEpiAdmm {", "\n};\n"),
-    ("common.cuh", "", None),
-)
-_FUSED_NOTE = ("ncu capture of {k} on the c2 workload (~500 active slots), "
-               "profiles/fused_xtu_prox_shapes_c2_K512_tc3.md")
+# tile geometry, its epilogue, the epilogue warp count and the shared device helpers),
+# else null.
+_COMMON = (("common.cuh", "", None),)
+_PERSIST = (("tc_gemm.cuh", "tc_gemm_persist_kernel(", "\n}\n"),
+            ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct Geo {", "\n};\n"),
+            ("admm_tc.cu", "struct TcEpiAdmm {", "\n};\n"),
+            ("admm_tc.cu", "constexpr int FUSED_EPIW", "\n")) + _COMMON
+_PAIR = (("tc_gemm.cuh", "tc_gemm_pair_kernel(", "\n}\n"),
+         ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct PairGeo {", "\n};\n"),
+         ("admm_tc.cu", "struct TcEpiAdmmT {", "\n};\n"),
+         ("admm_tc.cu", "constexpr int PAIR_EPIW", "\n")) + _COMMON
+_NOTE = "ncu capture of {k} on the c2 workload (~500 active slots), profiles/{f}"
 TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs)
-    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False, False): {
-        "kernel": "tc_gemm_persist_kernel(", "sources": "e5c2f3d8dfce1d9e", "bytes": 45.092096e6 + 0.578560e6,
-        "note": _FUSED_NOTE.format(k="tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 80, True, False): {
-        "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.101312e6 + 0.423424e6,
-        "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<80, 3, TcEpiAdmm<80, 0>, 8>")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 128, True, False): {
-        "kernel": "tc_gemm_persist_mc_kernel(", "sources": "ff017789b0628965", "bytes": 45.173504e6 + 0.635392e6,
-        "note": _FUSED_NOTE.format(k="tc_gemm_persist_mc_kernel<128, 3, TcEpiAdmm<128, 0>, 8>")},
+    ("gemm_xtu_prox", "c2", 512, "tc3", 144, False, True): {
+        "blocks": _PAIR, "sources": "2868d6d026a99649", "bytes": 45.375488e6 + 0.574720e6,
+        "note": _NOTE.format(k="tc_gemm_pair_kernel<144, 3, TcEpiAdmmT<0>, 12>",
+                             f="admm_tc_kernels_c2_K512_tc3.md")},
+    ("gemm_xtu_prox", "c2", 512, "tc3", 96, False, False): {
+        "blocks": _PERSIST, "sources": "a2fcb4bf20b33bdb", "bytes": 45.169408e6 + 0.503296e6,
+        "note": _NOTE.format(k="tc_gemm_persist_kernel<96, 3, TcEpiAdmm<96, 0>, 12>",
+                             f="fused_xtu_prox_shapes_c2_K512_tc3.md")},
 }
 
 
-def sources_hash(kernel):
-    """Hash of the source that defines one captured kernel: its template, the tile
-    geometry, the fused epilogue and the shared device helpers."""
+def sources_hash(blocks):
+    """Hash of the source text that defines one captured kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f, start, end in (("tc_gemm.cuh", kernel, "\n}\n"),) + SHARED_SOURCE_BLOCKS:
+    for f, start, end in blocks:
         with open(os.path.join(ROOT, "paper_2602_04551_b300", "csrc", f)) as fh:
             text = fh.read()
         if start:
@@ -455,7 +457,7 @@ def roofline(out, args, pk):
     sh = out.get("shapes") or {}
     tr = TRAFFIC.get((name, args.workload, args.K, args.precision, sh.get("fused_tile_width"),
                       bool(sh.get("fused_clusters")), bool(sh.get("fused_pairs"))))
-    if tr is not None and tr["sources"] == sources_hash(tr["kernel"]):
+    if tr is not None and tr["sources"] == sources_hash(tr["blocks"]):
         r["traffic"] = tr["bytes"]
         r["traffic_note"] = tr["note"]
     if args.precision == "fp32":

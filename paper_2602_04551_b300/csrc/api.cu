@@ -73,6 +73,11 @@ static void free_all(Engine<R>& e) {
   e.status_h = nullptr;
   if (e.st_side) cudaStreamDestroy(e.st_side);
   e.st_side = nullptr;
+  if (e.st_aux) cudaStreamDestroy(e.st_aux);
+  e.st_aux = nullptr;
+  if (e.ev_fork) cudaEventDestroy(e.ev_fork);
+  if (e.ev_join) cudaEventDestroy(e.ev_join);
+  e.ev_fork = e.ev_join = nullptr;
   if (e.own_stream && e.st) cudaStreamDestroy(e.st);
   e.st = nullptr;
 }
@@ -219,6 +224,7 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.pol_flag, K);
   ALLOC(e.inc_beta, p);
   ALLOC(e.inc_ub, 1);
+  ALLOC(e.inc_snap, 1);
   ALLOC(e.zbuf, K * p);
   ALLOC(e.pool_lb, e.qcap);
   ALLOC(e.pool_key, e.qcap);
@@ -456,6 +462,9 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   }
   if (int rc = allocate(*e)) return rc;
   if (int rc = setup_data(*e, dX, dy)) return rc;
+  BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st_aux, cudaStreamNonBlocking));
+  BNB_CUDA_OK(cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming));
+  BNB_CUDA_OK(cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming));
   if constexpr (sizeof(R) == 4) {
     if (e->tc_mode) {
       if (int rc = setup_tc(*e))
@@ -806,6 +815,17 @@ extern "C" int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, dou
 
 // ------------------------------------------------------------------------- solve
 
+__global__ void k_copy_scalar(const double* __restrict__ src, double* __restrict__ dst) {
+  if (threadIdx.x == 0) *dst = *src;
+}
+
+// One round: refill, ADMM iterations, certificate, branching and upper bound, push,
+// status.  After the certificate's FP32 screen the round forks: the exact certificate
+// terms run on the handle's stream while branching and the upper bound run on the
+// auxiliary stream (they share no buffer; the certificate decides against the incumbent
+// as it was before this round's upper bound, copied at the fork, as in the sequential
+// order); the push waits for both.  Inside a capture the fork and join become graph
+// edges.  A profiled round (per-stage events on one stream) runs the stages in order.
 template <class R>
 static int round_body(bnb_handle* h, Engine<R>& e) {
   const bnb_options& o = h->opt;
@@ -815,14 +835,32 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   prof_end(pf, e.st, PK_SELECT);
   if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
   prof_begin(pf, e.st);
-  if (int rc = certify(e, nullptr, true)) return rc;
-  prof_end(pf, e.st, PK_CERT);
-  prof_begin(pf, e.st);
-  if (int rc = branch_support(e, false, true)) return rc;
-  prof_end(pf, e.st, PK_BRANCH);
-  prof_begin(pf, e.st);
-  if (int rc = upper_bound(e, false)) return rc;
-  prof_end(pf, e.st, PK_UB);
+  if (int rc = certify_screen(e, nullptr)) return rc;
+  if (pf) {
+    if (int rc = certify_exact(e, true, e.inc_ub)) return rc;
+    prof_end(pf, e.st, PK_CERT);
+    prof_begin(pf, e.st);
+    if (int rc = branch_support(e, false, true)) return rc;
+    prof_end(pf, e.st, PK_BRANCH);
+    prof_begin(pf, e.st);
+    if (int rc = upper_bound(e, false)) return rc;
+    prof_end(pf, e.st, PK_UB);
+  } else {
+    k_copy_scalar<<<1, 32, 0, e.st>>>(e.inc_ub, e.inc_snap);
+    BNB_CUDA_OK(cudaGetLastError());
+    BNB_CUDA_OK(cudaEventRecord(e.ev_fork, e.st));
+    BNB_CUDA_OK(cudaStreamWaitEvent(e.st_aux, e.ev_fork, 0));
+    cudaStream_t main_st = e.st;
+    e.st = e.st_aux;
+    int rc = branch_support(e, false, true);
+    if (!rc) rc = upper_bound(e, false);
+    e.st = main_st;
+    const cudaError_t ce = cudaEventRecord(e.ev_join, e.st_aux);
+    if (rc) return rc;
+    BNB_CUDA_OK(ce);
+    if (int rc2 = certify_exact(e, true, e.inc_snap)) return rc2;
+    BNB_CUDA_OK(cudaStreamWaitEvent(e.st, e.ev_join, 0));
+  }
   prof_begin(pf, e.st);
   if (int rc = queue_push(e)) return rc;
   prof_end(pf, e.st, PK_PUSH);

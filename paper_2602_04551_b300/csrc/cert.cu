@@ -367,6 +367,14 @@ __global__ void k_cert_final(const int* __restrict__ ret_slot, const int* __rest
 
 template <class R>
 int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
+  if (int rc = certify_screen(e, r_given)) return rc;
+  return certify_exact(e, use_threshold, e.inc_ub);
+}
+
+// r = y - U (or the given r) in FP64 and FP32, then the FP32 screen of X^T r with its
+// rigorous error bound
+template <class R>
+int certify_screen(Engine<R>& e, const double* r_given) {
   using C = TileCfg<R>;
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
@@ -392,10 +400,21 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
                                            BPlainK<R>{e.rS, n}, epi)));
   }
   prof_end(e.prof, st, PK_CERT_SCREEN);
+  return 0;
+}
+
+// the decision per node (against the incumbent *inc), the exact FP64 terms it needs and
+// the certified bound
+template <class R>
+int certify_exact(Engine<R>& e, bool use_threshold, const double* inc) {
+  using C = TileCfg<R>;
+  const int n = e.n, p = e.p, K = e.K;
+  cudaStream_t st = e.st;
+  const int nbm = (p + (sizeof(R) == 4 ? SC_BM : C::BM) - 1) / (sizeof(R) == 4 ? SC_BM : C::BM);
   prof_begin(e.prof, st);
   const dim3 gx(K, CX_G);
   k_cert_decide<<<K, 32, 0, st>>>(e.cpart, nbm, K, e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr,
-                                  e.slot_lbp, e.inc_ub, e.params_d, use_threshold ? 1 : 0,
+                                  e.slot_lbp, inc, e.params_d, use_threshold ? 1 : 0,
                                   e.cx_base, e.cx_need, e.cert_lb, e.node_lb);
   k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
                                    e.ret_count, 1, e.cx_need, e.cx_part);
@@ -412,5 +431,9 @@ int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
 
 template int certify<float>(Engine<float>&, const double*, bool);
 template int certify<double>(Engine<double>&, const double*, bool);
+template int certify_screen<float>(Engine<float>&, const double*);
+template int certify_screen<double>(Engine<double>&, const double*);
+template int certify_exact<float>(Engine<float>&, bool, const double*);
+template int certify_exact<double>(Engine<double>&, bool, const double*);
 
 }  // namespace bnb

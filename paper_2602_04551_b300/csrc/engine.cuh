@@ -125,6 +125,7 @@ struct Engine {
   int* pol_flag = nullptr;
   double* inc_beta = nullptr;   // p, FP64 incumbent
   double* inc_ub = nullptr;     // scalar
+  double* inc_snap = nullptr;   // the incumbent when the round's certificate decides (scalar)
   float* zbuf = nullptr;        // K x p (relax outputs)
 
   // node pool
@@ -178,6 +179,8 @@ struct Engine {
   float* mv_part = nullptr;     // [MV_ZMAX][MV_MAX][n] partial products
   float* g3mv = nullptr;        // [4][ceil(p / 32)][MV_MAX] per-32-column stop-test sums
   cudaStream_t st_side = nullptr;  // capture of the conditional bodies
+  cudaStream_t st_aux = nullptr;   // the upper-bound branch of a round, beside the certificate
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int mv_body_kernels = 0, tc_body_kernels = 0;
 
   // counters (host)
@@ -192,6 +195,8 @@ template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double 
                                   bool use_incumbent);
 template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */,
                                bool use_threshold);
+template <class R> int certify_screen(Engine<R>& e, const double* r_given);
+template <class R> int certify_exact(Engine<R>& e, bool use_threshold, const double* inc);
 template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false);
 template <class R> int upper_bound(Engine<R>& e, bool force_polish);
 template <class R> int queue_push(Engine<R>& e);
