@@ -70,9 +70,10 @@ def parse():
     ap.add_argument("--fp64-time-limit", type=float, default=60.0)
     ap.add_argument("--seeds", type=int, default=1, help="solves mode: instances per lambda0")
     ap.add_argument("--max-depth", type=int, default=1024)
-    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="fused X^T U' shape: 0 measured at setup, 1 one CTA per tile, "
-                         "2 clusters of two sharing X, 3 transposed on CTA pairs")
+                         "2 clusters of two sharing X, 3 transposed on CTA pairs, "
+                         "4 untransposed on CTA pairs")
     ap.add_argument("--mv-crossover", type=int, default=-1,
                     help="narrow-form crossover (-1 default; 0 = tensor-core form only: graphs "
                          "without conditional nodes, which ncu can profile kernel by kernel)")
@@ -238,7 +239,7 @@ def run_mine(args, rank, world):
     res = bnb.bnb_solve_finish(h)
     h.close()
     shapes = {k: stats.get(k) for k in ("xw_tile_width", "xw_cluster", "fused_tile_width",
-                                          "fused_clusters", "fused_pairs")}
+                                          "fused_clusters", "fused_pairs", "fused_transposed")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
@@ -404,12 +405,13 @@ _PAIR = (("tc_gemm.cuh", "tc_gemm_pair_kernel(", "\n}\n"),
          ("admm_tc.cu", "constexpr int PAIR_EPIW", "\n")) + _COMMON
 _NOTE = "ncu capture of {k} on the c2 workload (~500 active slots), profiles/{f}"
 TRAFFIC = {
-    # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs)
-    ("gemm_xtu_prox", "c2", 512, "tc3", 144, False, True): {
+    # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
+    #  transposed)
+    ("gemm_xtu_prox", "c2", 512, "tc3", 144, False, True, True): {
         "blocks": _PAIR, "sources": "2868d6d026a99649", "bytes": 45.375488e6 + 0.574720e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<144, 3, TcEpiAdmmT<0>, 12>",
                              f="admm_tc_kernels_c2_K512_tc3.md")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 96, False, False): {
+    ("gemm_xtu_prox", "c2", 512, "tc3", 96, False, False, False): {
         "blocks": _PERSIST, "sources": "a2fcb4bf20b33bdb", "bytes": 45.169408e6 + 0.503296e6,
         "note": _NOTE.format(k="tc_gemm_persist_kernel<96, 3, TcEpiAdmm<96, 0>, 12>",
                              f="fused_xtu_prox_shapes_c2_K512_tc3.md")},
@@ -456,7 +458,8 @@ def roofline(out, args, pk):
          "active_slots": active}
     sh = out.get("shapes") or {}
     tr = TRAFFIC.get((name, args.workload, args.K, args.precision, sh.get("fused_tile_width"),
-                      bool(sh.get("fused_clusters")), bool(sh.get("fused_pairs"))))
+                      bool(sh.get("fused_clusters")), bool(sh.get("fused_pairs")),
+                      bool(sh.get("fused_transposed"))))
     if tr is not None and tr["sources"] == sources_hash(tr["blocks"]):
         r["traffic"] = tr["bytes"]
         r["traffic_note"] = tr["note"]

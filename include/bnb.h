@@ -93,7 +93,9 @@ typedef struct {
   int fused_shape;       /* tensor-core precisions, the fused X^T U' product: 0 (default) =
                             the fastest shape measured at creation; 1 = one CTA per output
                             tile; 2 = clusters of two CTAs sharing the X tile; 3 = the
-                            transposed product on CTA pairs (tcgen05 cta_group::2).  A shape
+                            transposed product on CTA pairs (tcgen05 cta_group::2, 256 node
+                            slots per pair tile); 4 = the product on CTA pairs untransposed
+                            (256 features per pair tile; not for BNB_PREC_BF16X2).  A shape
                             the device or the problem cannot run fails bnb_create with
                             BNB_EINVAL. */
 } bnb_options;
@@ -313,9 +315,10 @@ typedef struct {
   /* tensor-core shapes chosen at creation (0 for the CUDA-core precisions): output tile
      width and cluster size of the product H W'^T, tile width of the fused X^T U' product,
      the number of two-CTA clusters sharing the X tile it runs in (0: one CTA per tile),
-     and the number of CTA pairs it runs on when computed transposed (0: not transposed;
-     the width then counts features) */
-  int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters, fused_pairs;
+     the number of CTA pairs it runs on (0: none), and 1 when the pair product is taken
+     transposed (256 slots x width features per pair tile; else 256 features x width
+     slots) */
+  int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters, fused_pairs, fused_transposed;
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

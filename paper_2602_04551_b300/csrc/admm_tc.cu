@@ -385,7 +385,7 @@ struct TcEpiAdmmT {
 
   // the update of the chunk loaded by load() with the accumulator values of its 16 features
   __device__ __forceinline__ void operator()(int m, int f0, const float (&acc)[16], int M, int N,
-                                             State& st, const Chunk& ck) const {
+                                             State& st, const Chunk& ck, float*) const {
     if (m >= M || !active[m]) return;
     const float rho = PF.rho, irho = PF.irho;
     const long long rb = (long long)m * p, rw = (long long)m * ldp;
@@ -469,6 +469,28 @@ struct TcEpiAdmmT {
   }
 };
 
+// The fused update of TcEpiAdmm (row = feature, columns = node slots: loads and stores
+// coalesced along the features) in the CTA-pair kernel's interface, for the pair product
+// taken untransposed (X^T U' on 256-feature pair tiles)
+template <int BN, bool STATS>
+struct TcEpiAdmmPair {
+  static constexpr int SMEM_FLOATS = TcEpiAdmm<BN, STATS>::SMEM_FLOATS;
+  struct State {};
+  struct Chunk {};
+  TcEpiAdmm<BN, STATS> inner;
+  __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void load(int, int, int, int, Chunk&) const {}
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
+                                             State&, const Chunk&, float* sm) const {
+    inner(m, n0, acc, M, N, (int)(threadIdx.x >> 5) & 3, sm);
+  }
+  __device__ __forceinline__ void end(int, int, State&, float*) const {}
+  __device__ __forceinline__ void finish(int t, int nthr, int m0, int nt, int M, int N,
+                                         float* sm) const {
+    inner.finish(t, nthr, m0, nt * BN, M, N, sm);
+  }
+};
+
 // cluster-reduced product with the tile width chosen at setup (128 or 256 columns)
 template <int NS, class Epi>
 static int cred(Engine<float>& e, int bn, const TcOperand& A, const TcOperand& B, int M, int N,
@@ -530,6 +552,27 @@ static int fused_pair_bn(Engine<float>& e, const TcOperand& XC, const TcOperand&
                                                             epi);
 }
 
+// X^T U' on CTA pairs untransposed: 256 features x BN slots per pair tile, the update of
+// TcEpiAdmm (3 and 1 terms: the pair kernel's 2-term mode pairs the first operand, which
+// here is the data)
+template <int NS, int BN, bool STATS>
+static int fused_pairnt_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop) {
+  TcEpiAdmmPair<BN, STATS> epi{TcEpiAdmm<BN, STATS>{
+      e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part, e.w_hi,
+      NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr, (STATS && NS >= 2) ? e.b_lo : nullptr,
+      e.P, prob_f32(e.P), e.p, e.ldp, e.nbm3, e.K}};
+  return tc_gemm_pair<BN, NS, TcEpiAdmmPair<BN, STATS>, PAIR_EPIW>(e.st, XC, Uop, e.p, e.K, e.n,
+                                                                   e.tc_pair3, nullptr, e.tc_err,
+                                                                   epi);
+}
+
+template <int NS, int BN>
+static int pairnt_clusters_bn() {
+  const int a = tc_pair_clusters<BN, NS, TcEpiAdmmPair<BN, false>, PAIR_EPIW>();
+  const int b = tc_pair_clusters<BN, NS, TcEpiAdmmPair<BN, true>, PAIR_EPIW>();
+  return a < b ? a : b;
+}
+
 template <int NS, int BN>
 static int pair_clusters_bn() {
   const int a = tc_pair_clusters<BN, NS, TcEpiAdmmT<false>, PAIR_EPIW>();
@@ -539,6 +582,12 @@ static int pair_clusters_bn() {
 
 template <int NS>
 static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop, bool last) {
+  if (e.tc_pair3 > 0 && e.tc_pairnt) {
+    if constexpr (NS != 2)
+      return last ? fused_pairnt_bn<NS, 176, true>(e, XC, Uop)
+                  : fused_pairnt_bn<NS, 176, false>(e, XC, Uop);
+    return BNB_EINVAL;
+  }
   if (e.tc_pair3 > 0) {
     if (e.tc_bn3 == 144)
       return last ? fused_pair_bn<NS, 144, true>(e, XC, Uop) : fused_pair_bn<NS, 144, false>(e, XC, Uop);
@@ -667,16 +716,16 @@ static int pick_fused_shape(Engine<float>& e) {
   const TcOperand XC{e.xc_hi, e.xc_lo, e.p, e.n, e.ldn};
   const TcOperand Uop{e.u_hi, e.u_lo, e.K, e.n, e.ldn};
   struct Shape {
-    int w, mc, pair;
+    int w, mc, pair, nt;
   };
   std::vector<Shape> cands;
   for (int w : {64, 80, 96, 128}) {
     if (e.K > 64 * w) continue;
-    cands.push_back({w, 0, 0});
+    cands.push_back({w, 0, 0, 0});
     if ((e.K + w - 1) / w >= 2) {
       int cl = mc_clusters<NS>(w);
       if (cl > e.sms / 2) cl = e.sms / 2;
-      if (cl >= 1) cands.push_back({w, cl, 0});
+      if (cl >= 1) cands.push_back({w, cl, 0, 0});
     }
   }
   // CTA pairs on the transposed product: 256 slots x 128 or 144 features per pair tile
@@ -684,14 +733,20 @@ static int pick_fused_shape(Engine<float>& e) {
     for (int w : {128, 144}) {
       int cl = w == 144 ? pair_clusters_bn<NS, 144>() : pair_clusters_bn<NS, 128>();
       if (cl > e.sms / 2) cl = e.sms / 2;
-      if (cl >= 1) cands.push_back({w, 0, cl});
+      if (cl >= 1) cands.push_back({w, 0, cl, 0});
     }
+  }
+  // CTA pairs untransposed: 256 features x 176 slots per pair tile (3 and 1 terms)
+  if constexpr (NS != 2) {
+    int cl = pairnt_clusters_bn<NS, 176>();
+    if (cl > e.sms / 2) cl = e.sms / 2;
+    if (cl >= 1) cands.push_back({176, 0, cl, 1});
   }
   if (e.fused_kind > 0) {   // a requested kind: only its widths compete
     std::vector<Shape> keep;
     for (const Shape& c : cands)
       if ((e.fused_kind == 1 && !c.mc && !c.pair) || (e.fused_kind == 2 && c.mc) ||
-          (e.fused_kind == 3 && c.pair))
+          (e.fused_kind == 3 && c.pair && !c.nt) || (e.fused_kind == 4 && c.pair && c.nt))
         keep.push_back(c);
     cands.swap(keep);
   }
@@ -699,6 +754,7 @@ static int pick_fused_shape(Engine<float>& e) {
   e.tc_bn3 = cands[0].w;
   e.tc_mc3 = cands[0].mc;
   e.tc_pair3 = cands[0].pair;
+  e.tc_pairnt = cands[0].nt;
   if (cands.size() == 1) return 0;
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0xff, sizeof(int) * e.K, st));   // nonzero: active
   cudaEvent_t ev[2];
@@ -713,6 +769,7 @@ static int pick_fused_shape(Engine<float>& e) {
       e.tc_bn3 = cands[ci].w;
       e.tc_mc3 = cands[ci].mc;
       e.tc_pair3 = cands[ci].pair;
+      e.tc_pairnt = cands[ci].nt;
       if ((rc = fused_xtu<NS>(e, XC, Uop, false))) break;        // warm-up
       cudaEventRecord(ev[0], st);
       for (int r = 0; r < 5 && !rc; ++r) rc = fused_xtu<NS>(e, XC, Uop, false);
@@ -736,6 +793,7 @@ static int pick_fused_shape(Engine<float>& e) {
   e.tc_bn3 = pick.w;
   e.tc_mc3 = pick.mc;
   e.tc_pair3 = pick.pair;
+  e.tc_pairnt = pick.nt;
   const long long Kp = (long long)e.K * e.p;
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, st));
   BNB_CUDA_OK(cudaMemsetAsync(e.beta, 0, sizeof(float) * Kp, st));

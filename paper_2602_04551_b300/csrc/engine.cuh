@@ -166,8 +166,10 @@ struct Engine {
   int tc_bn1 = 256, tc_bn2 = 256; // their output tile widths (128 or 256)
   int tc_bn3 = 64;              // tile width of the fused X^T U' product (64, 80, 96, 128)
   int tc_mc3 = 0;               // > 0: it runs in clusters of two sharing the X tile (this many)
-  int tc_pair3 = 0;             // > 0: it runs transposed on this many CTA pairs (width 128/144)
-  int fused_kind = 0;           // requested shape: 0 measured, 1 single, 2 clusters of two, 3 pairs
+  int tc_pair3 = 0;             // > 0: it runs on this many CTA pairs
+  int tc_pairnt = 0;            // 1: the pair product untransposed (256 features x 176 slots)
+  int fused_kind = 0;           // requested shape: 0 measured, 1 single, 2 clusters of two,
+                                // 3 pairs transposed, 4 pairs untransposed
   float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2
   int nbt = 0;                  // row tiles of the n x K products
   int sms = 148;                // multiprocessors of the device (persistent grids)

@@ -986,7 +986,7 @@ struct PairGeo {
 //   typename Epi::State st; epi.begin(st);
 //   typename Epi::Chunk ck; epi.load(row, first column, M, N, ck)   the chunk's other
 //                                 inputs (issued for the first chunk before the wait)
-//   epi(row, first column, 16 accumulator values, M, N, st, ck)   per 16-column chunk
+//   epi(row, first column, 16 accumulator values, M, N, st, ck, smem)  per 16-column chunk
 //   epi.end(r, gq, st, smem)      after the thread's last chunk of the tile (r = row in CTA)
 //   epi.finish(t, nthreads, first row of the CTA, nt, M, N, smem)  after the warps meet
 template <int BN, int NSPLIT, class Epi, int EPIW>
@@ -998,7 +998,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
                     const int* __restrict__ active, int* err, Epi epi) {
   using G = PairGeo<BN, NSPLIT>;
   constexpr int S = G::STAGES;
-  constexpr int MAXMT = 64;                      // row tiles (M <= 64 x 256)
+  constexpr int MAXMT = 64;                      // row tiles with an activity mask (M <= 64 x 256)
   static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "pair MMA N: a multiple of 16 up to 256");
   static_assert(EPIW % 4 == 0, "epilogue warps cover the four lane quarters");
   extern __shared__ uint8_t dsm_raw[];
@@ -1020,15 +1020,16 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
   const int nk = (Kred + BK - 1) / BK;
   for (int j = threadIdx.x; j < MAXMT; j += blockDim.x) {
     int on = 0;
-    if (j < mtiles) {
+    if (j < mtiles && active != nullptr) {
       for (int r = 0; r < 256 && j * 256 + r < M; ++r)
-        if (active == nullptr || active[j * 256 + r]) {
+        if (active[j * 256 + r]) {
           on = 1;
           break;
         }
     }
     tile_on[j] = on;
   }
+  auto row_tile_on = [&](int mt) { return active == nullptr || tile_on[mt] != 0; };
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -1069,7 +1070,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     bool ok = true;
     for (int u = cid; u < nunits && ok; u += ncl) {
       const int mt = u % mtiles, nt = u / mtiles;
-      if (!tile_on[mt]) continue;
+      if (!row_tile_on(mt)) continue;
       const int arow = mt * 256 + 128 * (int)rank, brow = nt * BN + (BN / 2) * (int)rank;
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % S);
@@ -1101,7 +1102,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     bool ok = true;
     for (int u = cid; u < nunits && ok; u += ncl) {
       const int mt = u % mtiles;
-      if (!tile_on[mt]) continue;
+      if (!row_tile_on(mt)) continue;
       const int b = i % G::NBUF, use = i / G::NBUF;
       if (use >= 1 && !mbar_wait_cluster(&tempty_bar[b], (uint32_t)((use & 1) ^ 1), err, 8)) break;
       fence_after();
@@ -1141,7 +1142,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     int i = 0;
     for (int u = cid; u < nunits; u += ncl) {
       const int mt = u % mtiles, nt = u / mtiles;
-      if (!tile_on[mt]) continue;
+      if (!row_tile_on(mt)) continue;
       const int b = i % G::NBUF, use = i / G::NBUF;
       const int m0 = mt * 256 + 128 * (int)rank;
       const int row = m0 + 32 * q + lane;
@@ -1160,7 +1161,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
           if (c != cf) epi.load(row, nt * BN + c, M, N, ck);
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::BUF + c), v);
-          epi(row, nt * BN + c, v, M, N, es, ck);
+          epi(row, nt * BN + c, v, M, N, es, ck, epi_smem);
         }
       }
       fence_before();

@@ -303,13 +303,14 @@ int tc_pair_clusters() {
 
 // C = A B^T on CTA pairs (tc_gemm_pair_kernel): 256 x BN tiles, at most `clusters` pairs.
 // A: M rows (boxes of 128 rows, hi and, for 2 and 3 terms, lo); B: N rows (boxes of BN/2
-// rows, hi and, for 3 terms, lo).  M <= 64 x 256.
+// rows, hi and, for 3 terms, lo).  With an activity mask over the rows (row tiles with no
+// active row are skipped) M <= 64 x 256.
 template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
 int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
                  int clusters, const int* active, int* err, Epi epi) {
   using G = tc::PairGeo<BN, NSPLIT>;
   if (M <= 0 || N <= 0 || Kred <= 0) return 0;
-  if (M > 64 * 256 || clusters < 1) return BNB_EINVAL;
+  if ((active != nullptr && M > 64 * 256) || clusters < 1) return BNB_EINVAL;
   CUtensorMap ah, al, bh, bl;
   if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
   if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN / 2)) return rc;

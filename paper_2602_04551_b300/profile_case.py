@@ -33,7 +33,7 @@ def main():
     ap.add_argument("--rounds", type=int, default=3)
     ap.add_argument("--prime-seconds", type=float, default=30.0)
     ap.add_argument("--mv-crossover", type=int, default=-1)
-    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3])
+    ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--no-graphs", action="store_true")
     a = ap.parse_args()
     c = datagen.CONFIGS[a.workload]

@@ -178,25 +178,30 @@ def test_one_admm_iteration_full_size_wide_batch(prec):
 
 
 SHAPES = [pytest.param(1, id="single"), pytest.param(2, id="clusters_of_two"),
-          pytest.param(3, id="cta_pairs")]
+          pytest.param(3, id="cta_pairs_transposed"), pytest.param(4, id="cta_pairs")]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("prec", [3, 4, 2])
 def test_one_admm_iteration_every_fused_shape(shape, prec):
     """Each shape of the fused X^T U' product (one CTA per tile, clusters of two sharing
-    the X tile, the transposed product on CTA pairs) gives the oracle's iteration."""
+    the X tile, the product on CTA pairs transposed and not) gives the oracle's iteration."""
+    if shape == 4 and prec == 4:
+        pytest.skip("the untransposed pair product has no two-term (BF16X2) form")
     inst, lam0, lam2, M = _inst("c2_small", 1)
     _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=128, rows=range(45), seed=13,
                          fused_shape=shape)
 
 
-def test_one_admm_iteration_cta_pairs_full_size():
-    """c2 at K=512 on CTA pairs: slots on both CTAs of both row tiles are sampled (0, 127,
-    128 and 255 of the first tile, 256 and 511 of the second)."""
+@pytest.mark.parametrize("shape", [3, 4])
+def test_one_admm_iteration_cta_pairs_full_size(shape):
+    """c2 at K=512 on CTA pairs: transposed, slots on both CTAs of both row tiles are
+    sampled (0, 127, 128 and 255 of the first tile, 256 and 511 of the second);
+    untransposed, the same slots fall in the three 176-wide column tiles, and every
+    feature (both CTAs of all 20 row tiles, the ragged last one included) is compared."""
     inst, lam0, lam2, M = _inst("c2", 0)
     _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512,
-                         rows=[0, 127, 128, 255, 256, 511], seed=14, fused_shape=3)
+                         rows=[0, 127, 128, 255, 256, 511], seed=14, fused_shape=shape)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -222,7 +227,8 @@ def test_converged_bounds_and_solve_every_fused_shape(shape):
     with bnb.bnb_create(ci.X, ci.y, case["lambda0"], case["lambda2"], o) as h:
         res = bnb.bnb_solve(h, case["gap"])
         st = bnb.bnb_get_stats(h)
-        assert (st["fused_pairs"] > 0) == (shape == 3)
+        assert (st["fused_pairs"] > 0) == (shape >= 3)
+        assert st["fused_transposed"] == (1 if shape == 3 else 0)
         assert (st["fused_clusters"] > 0) == (shape == 2)
     assert [int(i) for i in np.nonzero(res["beta"])[0]] == case["support"]
     assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
