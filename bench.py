@@ -403,6 +403,11 @@ _PAIR = (("tc_gemm.cuh", "tc_gemm_pair_kernel(", "\n}\n"),
          ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct PairGeo {", "\n};\n"),
          ("admm_tc.cu", "struct TcEpiAdmmT {", "\n};\n"),
          ("admm_tc.cu", "constexpr int PAIR_EPIW", "\n")) + _COMMON
+_PAIR_NT = (("tc_gemm.cuh", "tc_gemm_pair_kernel(", "\n}\n"),
+            ("tc_gemm.cuh", "template <int BN, int NSPLIT>\nstruct PairGeo {", "\n};\n"),
+            ("admm_tc.cu", "struct TcEpiAdmm {", "\n};\n"),
+            ("admm_tc.cu", "struct TcEpiAdmmPair {", "\n};\n"),
+            ("admm_tc.cu", "constexpr int PAIR_EPIW", "\n")) + _COMMON
 _NOTE = "ncu capture of {k} on the c2 workload (~500 active slots), profiles/{f}"
 TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
@@ -411,6 +416,10 @@ TRAFFIC = {
         "blocks": _PAIR, "sources": "2868d6d026a99649", "bytes": 45.375488e6 + 0.574720e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<144, 3, TcEpiAdmmT<0>, 12>",
                              f="admm_tc_kernels_c2_K512_tc3.md")},
+    ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
+        "blocks": _PAIR_NT, "sources": "37198705fb3b584e", "bytes": 45.174528e6 + 0.457216e6,
+        "note": _NOTE.format(k="tc_gemm_pair_kernel<176, 3, TcEpiAdmmPair<176, 0>, 12>",
+                             f="fused_pair_untransposed_c2_K512_tc3.md")},
     ("gemm_xtu_prox", "c2", 512, "tc3", 96, False, False, False): {
         "blocks": _PERSIST, "sources": "a2fcb4bf20b33bdb", "bytes": 45.169408e6 + 0.503296e6,
         "note": _NOTE.format(k="tc_gemm_persist_kernel<96, 3, TcEpiAdmm<96, 0>, 12>",
