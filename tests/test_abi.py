@@ -42,3 +42,32 @@ def test_options_default_and_errors(lib):
     with pytest.raises(lib.BnbError) as ei:
         lib.bnb_create(np.ones((4, 3)), np.ones(4), 0.1, 0.1, lib.bnb_options_default(M=1.0))
     assert ei.value.code in (lib.BNB_ENODEV, lib.BNB_EINVAL)
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    """The ctypes mirrors of bnb_options, bnb_stats and bnb_progress have the size and
+    the field offsets a C compiler gives the header's structs (a drifted binding would
+    marshal garbage into the library)."""
+    import ctypes
+    structs = {"bnb_options": lib.bnb_options, "bnb_stats": lib.bnb_stats,
+               "bnb_progress": lib.bnb_progress}
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "bnb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        src.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            src.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    src += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = 0
+    for line in out.splitlines():
+        name, field, value = line.split()
+        cls = structs[name]
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
