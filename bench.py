@@ -412,9 +412,9 @@ _NOTE = "ncu capture of {k} on the c2 workload (~500 active slots), profiles/{f}
 TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
     #  transposed)
-    ("gemm_xtu_prox", "c2", 512, "tc3", 144, False, True, True): {
-        "blocks": _PAIR, "sources": "2868d6d026a99649", "bytes": 45.375488e6 + 0.574720e6,
-        "note": _NOTE.format(k="tc_gemm_pair_kernel<144, 3, TcEpiAdmmT<0>, 12>",
+    ("gemm_xtu_prox", "c2", 512, "tc3", 128, False, True, True): {
+        "blocks": _PAIR, "sources": "275860b1ad7bfeba", "bytes": 45.368064e6 + 0.580096e6,
+        "note": _NOTE.format(k="tc_gemm_pair_kernel<128, 3, TcEpiAdmmT<0>, 12>",
                              f="admm_tc_kernels_c2_K512_tc3.md")},
     ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
         "blocks": _PAIR_NT, "sources": "37198705fb3b584e", "bytes": 45.174528e6 + 0.457216e6,
