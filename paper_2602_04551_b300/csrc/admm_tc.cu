@@ -47,6 +47,19 @@ __device__ __forceinline__ void store8_split(const float (&x)[8], __nv_bfloat16*
   if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(l);
 }
 
+// four consecutive values as BF16 hi (and lo) at an 8-byte aligned offset o
+__device__ __forceinline__ void store4_split(const float (&x)[4], __nv_bfloat16* hi,
+                                             __nv_bfloat16* lo, long long o) {
+  __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = __float2bfloat16_rn(x[j]);
+    l[j] = __float2bfloat16_rn(x[j] - __bfloat162float(h[j]));
+  }
+  *reinterpret_cast<uint2*>(hi + o) = *reinterpret_cast<const uint2*>(h);
+  if (lo) *reinterpret_cast<uint2*>(lo + o) = *reinterpret_cast<const uint2*>(l);
+}
+
 // W' = rho beta - V for the active slots, as BF16 hi/lo (K x ldp)
 __global__ void k_make_w(const float* __restrict__ beta,
                          const float* __restrict__ V, const int* __restrict__ active, int p,
@@ -194,11 +207,126 @@ struct TcEpiAdmm {
   ProbF PF;
   long long p, ldp;
   int nbm, K;
+  int vec4;                     // p % 4 == 0: the quad form below (16-byte state accesses)
   // STATS (the round's last iteration): per-slot stop-test sums and the beta operand of
   // the check product; a separate instantiation so the other iterations stay lean
 
+  // Quad form: the four lanes of a quad exchange their accumulator values (two
+  // butterfly steps of 4-value blocks) so that each lane holds 4 consecutive features x
+  // 4 node slots; every node-state access is then a 16-byte vector (4 bytes for the
+  // fixing codes, 8 for a W' term) instead of one 4- or 1-byte access per element.
+  __device__ __forceinline__ void quad(int m, int n0, const float (&acc)[16], int M, int N, int q,
+                                       float* sm) const {
+    const int lane = threadIdx.x & 31, lq = lane & 3;
+    const int fb = m - lq;                                 // the quad's first feature
+    float a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = acc[j];
+    const bool b1 = (lane & 2) != 0, b0 = (lane & 1) != 0;
+    // blocks a[4g .. 4g + 3] = slots n0 + 4g .. of this lane's feature; after the xor-2
+    // step a lane holds its own and its xor-2 partner's feature for two slot groups,
+    // after the xor-1 step all four features for slot group lq
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float send = b1 ? a[4 * k + e] : a[4 * (k + 2) + e];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 2);
+        if (b1) a[4 * k + e] = recv;
+        else a[4 * (k + 2) + e] = recv;
+      }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float send = b0 ? a[4 * (2 * k) + e] : a[4 * (2 * k + 1) + e];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+        if (b0) a[4 * (2 * k) + e] = recv;
+        else a[4 * (2 * k + 1) + e] = recv;
+      }
+    // a[4 r + e] = P'(feature fb + r, slot n0 + 4 lq + e)
+    const float rho = PF.rho, irho = PF.irho;
+    const bool fin = fb < M;                               // M % 4 == 0: all four or none
+    float cb[4] = {0.f, 0.f, 0.f, 0.f}, rb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (fin) {
+      const float4 c4 = *reinterpret_cast<const float4*>(bc + fb);
+      cb[0] = c4.x; cb[1] = c4.y; cb[2] = c4.z; cb[3] = c4.w;
+      if (STATS) {
+        const float4 r4 = *reinterpret_cast<const float4*>(rbc + fb);
+        rb[0] = r4.x; rb[1] = r4.y; rb[2] = r4.z; rb[3] = r4.w;
+      }
+    }
+    bool ok[4];
+    float4 bo4[4], vv4[4];
+    uint32_t fx[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {                          // every load first
+      const int n = n0 + 4 * lq + e;
+      ok[e] = fin && n < N && active[n];
+      const long long o = (long long)n * p + fb;
+      bo4[e] = ok[e] ? *reinterpret_cast<const float4*>(beta + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vv4[e] = ok[e] ? *reinterpret_cast<const float4*>(V + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      fx[e] = ok[e] ? *reinterpret_cast<const uint32_t*>(fix + o) : 0u;
+    }
+    float st[4][4];                                        // [stat][slot]
+#pragma unroll
+    for (int e = 0; e < 4; ++e) st[0][e] = st[1][e] = st[2][e] = st[3][e] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (!ok[e]) continue;
+      const int n = n0 + 4 * lq + e;
+      const long long o = (long long)n * p + fb, ow = (long long)n * ldp + fb;
+      const float bo[4] = {bo4[e].x, bo4[e].y, bo4[e].z, bo4[e].w};
+      const float vv[4] = {vv4[e].x, vv4[e].y, vv4[e].z, vv4[e].w};
+      float nb[4], nv[4], wv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int ff = (int)(int8_t)((fx[e] >> (8 * r)) & 0xffu);
+        const float w = rho * bo[r] - vv[r];               // W'
+        const float b = cb[r] + (w - a[4 * r + e]) * irho; // b = b_c + D W'
+        const float bh = PF.alpha * b + PF.one_minus_alpha * bo[r];
+        nb[r] = prox_coord_f(bh + vv[r] * irho, ff, PF);
+        nv[r] = vv[r] + rho * (bh - nb[r]);
+        wv[r] = rho * nb[r] - nv[r];
+        if (STATS) {
+          st[0][e] += psi_coord<float>(nb[r], ff, P);
+          st[1][e] += nu_coord<float>(fabsf(rb[r] - a[4 * r + e]), ff, P);
+          st[2][e] += (nb[r] - bo[r]) * (nb[r] - bo[r]);
+          st[3][e] += (b - nb[r]) * (b - nb[r]);
+        }
+      }
+      *reinterpret_cast<float4*>(beta + o) = make_float4(nb[0], nb[1], nb[2], nb[3]);
+      *reinterpret_cast<float4*>(V + o) = make_float4(nv[0], nv[1], nv[2], nv[3]);
+      store4_split(wv, whi, wlo, ow);                      // next W'
+      if (STATS && bhi) store4_split(nb, bhi, blo, ow);
+    }
+    if constexpr (STATS) {
+      // per slot: the sum over the warp's 32 features (the 8 quads), in lanes 0..3
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float v = st[t][e];
+          v += __shfl_xor_sync(0xffffffffu, v, 4);
+          v += __shfl_xor_sync(0xffffffffu, v, 8);
+          v += __shfl_xor_sync(0xffffffffu, v, 16);
+          st[t][e] = v;
+        }
+      if (lane < 4) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) sm[(q * 4 + t) * BN + (n0 % BN) + 4 * lane + e] = st[t][e];
+      }
+    }
+  }
+
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
                                              int q, float* sm) const {
+    if (vec4) {
+      quad(m, n0, acc, M, N, q, sm);
+      return;
+    }
     const float rho = PF.rho, irho = PF.irho;
     const float bcm = m < M ? bc[m] : 0.f;
     if constexpr (!STATS) {
@@ -511,7 +639,7 @@ static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& 
   TcEpiAdmm<BN3, STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                             e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
                             (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
-                            e.nbm3, e.K};
+                            e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0};
   if (e.tc_mc3 > 0)   // clusters of two CTAs sharing the X tile
     return tc_gemm_persist_mc<BN3, NS, TcEpiAdmm<BN3, STATS>, FUSED_EPIW>(
         e.st, XC, Uop, e.p, e.K, e.n, e.tc_mc3, e.slot_active, e.tc_err, epi);
@@ -560,7 +688,7 @@ static int fused_pairnt_bn(Engine<float>& e, const TcOperand& XC, const TcOperan
   TcEpiAdmmPair<BN, STATS> epi{TcEpiAdmm<BN, STATS>{
       e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part, e.w_hi,
       NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr, (STATS && NS >= 2) ? e.b_lo : nullptr,
-      e.P, prob_f32(e.P), e.p, e.ldp, e.nbm3, e.K}};
+      e.P, prob_f32(e.P), e.p, e.ldp, e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0}};
   return tc_gemm_pair<BN, NS, TcEpiAdmmPair<BN, STATS>, PAIR_EPIW>(e.st, XC, Uop, e.p, e.K, e.n,
                                                                    e.tc_pair3, nullptr, e.tc_err,
                                                                    epi);

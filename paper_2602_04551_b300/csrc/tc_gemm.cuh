@@ -645,7 +645,8 @@ tc_gemm_persist_kernel(const __grid_constant__ CUtensorMap ma_hi,
       const int mt = t % mtiles, nt = t / mtiles;
       if (!tile_on[nt]) continue;
       const int b = i & 1;
-      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4);
+      // warp-uniform, so that an epilogue using warp shuffles runs in all lanes or none
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4));
       fence_after();
       const int m0 = mt * BM, n0 = nt * BN;
       const int row = m0 + 32 * q + lane;
@@ -839,7 +840,8 @@ tc_gemm_persist_mc_kernel(const __grid_constant__ CUtensorMap ma_hi,
       if (!unit_on(ntp)) continue;
       const int nt = 2 * ntp + rank;
       const int b = i & 1;
-      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4);
+      // warp-uniform, so that an epilogue using warp shuffles runs in all lanes or none
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[b], (uint32_t)((i >> 1) & 1), err, 4));
       fence_after();
       const int m0 = mt * BM, n0 = nt * BN;
       const int row = m0 + 32 * q + lane;
@@ -1151,7 +1153,8 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
       typename Epi::Chunk ck;
       const int cf = 16 * gq;
       if (cf < BN) epi.load(row, nt * BN + cf, M, N, ck);
-      const bool ok = mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), err, 4);
+      // warp-uniform, so that an epilogue using warp shuffles runs in all lanes or none
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull_bar[b], (uint32_t)(use & 1), err, 4));
       fence_after();
       typename Epi::State es;
       epi.begin(es);
