@@ -412,17 +412,13 @@ _NOTE = "ncu capture of {k} on the c2 workload (~500 active slots), profiles/{f}
 TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
     #  transposed)
-    ("gemm_xtu_prox", "c2", 512, "tc3", 128, False, True, True): {
-        "blocks": _PAIR, "sources": "275860b1ad7bfeba", "bytes": 45.368064e6 + 0.580096e6,
-        "note": _NOTE.format(k="tc_gemm_pair_kernel<128, 3, TcEpiAdmmT<0>, 12>",
-                             f="admm_tc_kernels_c2_K512_tc3.md")},
     ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
-        "blocks": _PAIR_NT, "sources": "37198705fb3b584e", "bytes": 45.174528e6 + 0.457216e6,
+        "blocks": _PAIR_NT, "sources": "1955286f4cf01cae", "bytes": 45.181696e6 + 0.556800e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<176, 3, TcEpiAdmmPair<176, 0>, 12>",
                              f="fused_pair_untransposed_c2_K512_tc3.md")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 96, False, False, False): {
-        "blocks": _PERSIST, "sources": "a2fcb4bf20b33bdb", "bytes": 45.169408e6 + 0.503296e6,
-        "note": _NOTE.format(k="tc_gemm_persist_kernel<96, 3, TcEpiAdmm<96, 0>, 12>",
+    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False, False, False): {
+        "blocks": _PERSIST, "sources": "5c2c9a20c3186ba6", "bytes": 45.180416e6 + 0.587776e6,
+        "note": _NOTE.format(k="tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 12>",
                              f="fused_xtu_prox_shapes_c2_K512_tc3.md")},
 }
 
