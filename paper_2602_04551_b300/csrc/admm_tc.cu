@@ -65,12 +65,22 @@ __global__ void k_make_w(const float* __restrict__ beta,
                          const float* __restrict__ V, const int* __restrict__ active, int p,
                          long long ldp, int K, float rho, __nv_bfloat16* __restrict__ whi,
                          __nv_bfloat16* __restrict__ wlo) {
-  const long long m = (long long)K * p;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(t / p), j = (int)(t % p);
-    if (!active[s]) continue;
-    split_store(rho * beta[t] - V[t], whi, wlo, (long long)s * ldp + j);
+  // grid (K, feature blocks): threads over one slot's features, four at a time (16-byte
+  // loads, 8-byte stores) when p is a multiple of 4
+  const int s = blockIdx.x;
+  if (!active[s]) return;
+  const long long rb = (long long)s * p, rw = (long long)s * ldp;
+  const int stride = gridDim.y * blockDim.x;
+  if ((p & 3) == 0) {
+    for (int j = 4 * (blockIdx.y * blockDim.x + threadIdx.x); j < p; j += 4 * stride) {
+      const float4 b = *reinterpret_cast<const float4*>(beta + rb + j);
+      const float4 v = *reinterpret_cast<const float4*>(V + rb + j);
+      const float w[4] = {rho * b.x - v.x, rho * b.y - v.y, rho * b.z - v.z, rho * b.w - v.w};
+      store4_split(w, whi, wlo, rw + j);
+    }
+  } else {
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < p; j += stride)
+      split_store(rho * beta[rb + j] - V[rb + j], whi, wlo, rw + j);
   }
 }
 
@@ -746,7 +756,7 @@ static int round_tc(Engine<float>& e, int iters) {
   const TcOperand Top{e.t_hi, e.t_lo, K, n, e.ldn};
   const TcOperand Uop{e.u_hi, e.u_lo, K, n, e.ldn};
   const TcOperand Bop{e.b_hi, e.b_lo, K, p, e.ldp};
-  const int kgrid = (int)(((long long)K * p + 255) / 256 > 8192 ? 8192 : ((long long)K * p + 255) / 256);
+  const dim3 kgrid(K, (p + 1023) / 1024 > 65535 ? 65535 : (p + 1023) / 1024);
   prof_begin(e.prof, st);
   k_make_w<<<kgrid, 256, 0, st>>>(e.beta, e.V, e.slot_active, p, e.ldp, K, (float)e.P.rho,
                                   e.w_hi, NS >= 2 ? e.w_lo : nullptr);
