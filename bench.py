@@ -197,15 +197,17 @@ def run_mine(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
     bnb.bnb_solve_start(h, gap)
-    # priming (untimed): grow the tree until the slots are busy, so that the timed
-    # rounds measure the steady state of the solve rather than its first nodes
+    # priming (untimed): grow the tree until the slots are busy and a batch's worth of
+    # nodes has been certified, so that the timed rounds measure the steady state of the
+    # solve (slots retiring and refilling) rather than its first nodes
     t0 = time.time()
     prime_rounds = 0
     while True:
         bnb.bnb_solve_launch(h, 20)
         prime_rounds += 20
         pr = bnb.bnb_solve_poll(h)
-        if pr["done"] or pr["active_slots"] >= 0.9 * args.K or time.time() - t0 > args.prime_seconds:
+        busy = pr["active_slots"] >= 0.9 * args.K and pr["nodes"] >= args.K
+        if pr["done"] or busy or time.time() - t0 > args.prime_seconds:
             break
     clk = Clocks(dev)            # sampling spans the warm-up and the timed steps
     time.sleep(0.3)

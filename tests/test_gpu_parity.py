@@ -234,6 +234,45 @@ def test_converged_bounds_and_solve_every_fused_shape(shape):
     assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
 
 
+def _inst_odd():
+    """A c2-recipe instance with n and p that are not multiples of 4 or 8: the scalar
+    forms of the vectorised kernels (matrix-vector products, fused updates, W' formation)
+    and ragged operand boxes."""
+    inst = datagen.make_instance(101, 503, 0.3, 10, 5.0, 2077)
+    lam2 = 1e-3
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2, 1.5)
+    lam0 = 0.05 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    return inst, lam0, lam2, M
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_one_admm_iteration_odd_sizes_every_fused_shape(shape):
+    inst, lam0, lam2, M = _inst_odd()
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=45, Kopt=128, rows=range(45), seed=31,
+                         fused_shape=shape, mv_crossover=0)
+
+
+def test_one_admm_iteration_odd_sizes_narrow_batch():
+    inst, lam0, lam2, M = _inst_odd()
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=11, Kopt=64, rows=range(11), seed=32,
+                         tol=ITER_TOL[1], mv_crossover=32)
+
+
+def test_converged_bounds_odd_sizes():
+    """Converged bounds on the odd instance in both round forms stay valid and tight."""
+    inst, lam0, lam2, M = _inst_odd()
+    rng = np.random.default_rng(33)
+    fix = datagen.random_fixings(inst.p, 12, rng, 10)
+    for cross in (32, 0):
+        with _handle(inst, lam0, lam2, M, 3, K=64, node_tol=1e-5, max_admm_iter=20000,
+                     mv_crossover=cross) as h:
+            out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+        for k in range(12):
+            _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+            assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+            assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
+
+
 # ------------------------------------------------------------------ converged node
 
 
