@@ -821,12 +821,14 @@ __global__ void k_copy_scalar(const double* __restrict__ src, double* __restrict
 }
 
 // One round: refill, ADMM iterations, certificate, branching and upper bound, push,
-// status.  After the certificate's FP32 screen the round forks: the exact certificate
-// terms run on the handle's stream while branching and the upper bound run on the
-// auxiliary stream (they share no buffer; the certificate decides against the incumbent
-// as it was before this round's upper bound, copied at the fork, as in the sequential
-// order); the push waits for both.  Inside a capture the fork and join become graph
-// edges.  A profiled round (per-stage events on one stream) runs the stages in order.
+// status.  After the ADMM iterations the round forks: branching and the upper bound run
+// on the auxiliary stream while the certificate (FP32 screen, exact terms) runs on the
+// handle's stream -- they share no buffer; the certificate decides against the
+// incumbent as it was before this round's upper bound (copied at the fork, as in the
+// sequential order), and the rare branching decisions that need the screened X^T r
+// (every free z integral) are deferred to k_branch_fallback after the join; the push
+// waits for both.  Inside a capture the fork and join become graph edges.  A profiled
+// round (per-stage events on one stream) runs the stages in order.
 template <class R>
 static int round_body(bnb_handle* h, Engine<R>& e) {
   const bnb_options& o = h->opt;
@@ -835,9 +837,9 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   if (int rc = queue_select_refill(e)) return rc;
   prof_end(pf, e.st, PK_SELECT);
   if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
-  prof_begin(pf, e.st);
-  if (int rc = certify_screen(e, nullptr)) return rc;
   if (pf) {
+    prof_begin(pf, e.st);
+    if (int rc = certify_screen(e, nullptr)) return rc;
     if (int rc = certify_exact(e, true, e.inc_ub)) return rc;
     prof_end(pf, e.st, PK_CERT);
     prof_begin(pf, e.st);
@@ -853,14 +855,16 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     BNB_CUDA_OK(cudaStreamWaitEvent(e.st_aux, e.ev_fork, 0));
     cudaStream_t main_st = e.st;
     e.st = e.st_aux;
-    int rc = branch_support(e, false, true);
+    int rc = branch_support(e, false, true, true);
     if (!rc) rc = upper_bound(e, false);
     e.st = main_st;
     const cudaError_t ce = cudaEventRecord(e.ev_join, e.st_aux);
     if (rc) return rc;
     BNB_CUDA_OK(ce);
+    if (int rc2 = certify_screen(e, nullptr)) return rc2;
     if (int rc2 = certify_exact(e, true, e.inc_snap)) return rc2;
     BNB_CUDA_OK(cudaStreamWaitEvent(e.st, e.ev_join, 0));
+    if (int rc2 = branch_fallback(e)) return rc2;
   }
   prof_begin(pf, e.st);
   if (int rc = queue_push(e)) return rc;

@@ -199,7 +199,9 @@ template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or n
                                bool use_threshold);
 template <class R> int certify_screen(Engine<R>& e, const double* r_given);
 template <class R> int certify_exact(Engine<R>& e, bool use_threshold, const double* inc);
-template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false);
+template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false,
+                                      bool defer_fallback = false);
+template <class R> int branch_fallback(Engine<R>& e);
 template <class R> int upper_bound(Engine<R>& e, bool force_polish);
 template <class R> int queue_push(Engine<R>& e);
 template <class R> int queue_select_refill(Engine<R>& e);

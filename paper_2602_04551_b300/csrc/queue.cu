@@ -173,9 +173,10 @@ __global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid
                             const double* __restrict__ inc_ub, const double* __restrict__ params,
                             unsigned* hist, int* sel_state, unsigned long long* poolmin) {
   __shared__ unsigned sh[SEL_BINS];
+  const int hw = *pool_hw;
+  if (blockIdx.x * blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
-  const int hw = *pool_hw;
   const double thr = inc_ub[0] * (1.0 - params[0]);
   int cnt = 0;
   unsigned long long mn = ~0ull;
@@ -305,9 +306,10 @@ __global__ void k_sel_pass(int level, const int* __restrict__ pool_hw,
                            const int* __restrict__ sel_state) {
   if (sel_state[SS_TAKE_ALL]) return;
   __shared__ unsigned sh[SEL_BINS];
+  const int hw = *pool_hw;
+  if (blockIdx.x * blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
-  const int hw = *pool_hw;
   const unsigned pre = (unsigned)sel_state[SS_PREFIX];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
     if (!pool_valid[i]) continue;

@@ -83,7 +83,10 @@ __device__ bool support_seen(unsigned long long* table, int mask, unsigned long 
   return false;
 }
 
-// one block (256 threads) per retired node
+// one block (256 threads) per retired node.  Without gscr (the screened X^T r) a node whose
+// free z are all integral gets br_idx = BR_DEFERRED, decided later by k_branch_fallback.
+constexpr int BR_DEFERRED = -3;
+
 template <class R>
 __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __restrict__ fix,
                                  const float* __restrict__ gscr, int p, Prob P,
@@ -118,10 +121,12 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
         const unsigned long long key =
             ((unsigned long long)__float_as_uint(fr) << 32) | (unsigned)(0x7fffffff - i);
         kf = umax64(kf, key);
-        const float g = fabsf(gscr[(long long)q * p + i]);
-        const unsigned long long kg2 =
-            ((unsigned long long)__float_as_uint(g) << 32) | (unsigned)(0x7fffffff - i);
-        kg = umax64(kg, kg2);
+        if (gscr) {
+          const float g = fabsf(gscr[(long long)q * p + i]);
+          const unsigned long long kg2 =
+              ((unsigned long long)__float_as_uint(g) << 32) | (unsigned)(0x7fffffff - i);
+          kg = umax64(kg, kg2);
+        }
         insup = z >= 0.5f;
       } else {
         insup = (f == 1);
@@ -153,8 +158,12 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
     int j = -1;
     if (nfi > 0) {
       const float fr = __uint_as_float((unsigned)(kf >> 32));
-      const unsigned long long k = fr > 0.0f ? kf : kg;
-      j = 0x7fffffff - (int)(unsigned)(k & 0xffffffffu);
+      if (fr > 0.0f || gscr) {
+        const unsigned long long k = fr > 0.0f ? kf : kg;
+        j = 0x7fffffff - (int)(unsigned)(k & 0xffffffffu);
+      } else {
+        j = BR_DEFERRED;   // every free z integral: k_branch_fallback decides from |X_i^T r|
+      }
     }
     br_idx[q] = j;
     int sc = base <= smax ? base : -1;
@@ -164,6 +173,25 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
     if (seen != nullptr && sc > 0 && support_seen(seen, seen_mask, hs)) sc = -2;
     sup_cnt[q] = sc;
   }
+}
+
+// the deferred branching decisions: the free index with the largest |X_i^T r| (screened,
+// FP32), ties to the lowest index -- the rule k_branch_support applies when it has gscr
+__global__ void k_branch_fallback(const int8_t* __restrict__ fix, const float* __restrict__ gscr,
+                                  int p, const int* __restrict__ ret_slot,
+                                  const int* __restrict__ ret_count, int* __restrict__ br_idx) {
+  __shared__ unsigned long long shk[32];
+  const int q = blockIdx.x;
+  if (q >= *ret_count || br_idx[q] != BR_DEFERRED) return;
+  const long long slot = ret_slot[q];
+  unsigned long long kg = 0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) {
+    if (fix[slot * p + i] != -1) continue;
+    const float g = fabsf(gscr[(long long)q * p + i]);
+    kg = umax64(kg, ((unsigned long long)__float_as_uint(g) << 32) | (unsigned)(0x7fffffff - i));
+  }
+  kg = block_max_u64(kg, shk);
+  if (threadIdx.x == 0) br_idx[q] = 0x7fffffff - (int)(unsigned)(kg & 0xffffffffu);
 }
 
 // Q = X_S^T X_S + 2 lambda2 I, q = X_S^T y in the ADMM precision (one block per node)
@@ -583,8 +611,9 @@ __global__ void k_sup_from_mask(const uint8_t* __restrict__ mask, int p, int sma
 }
 
 template <class R>
-int branch_support(Engine<R>& e, bool write_z, bool memo) {
-  k_branch_support<R><<<e.K, 1024, 0, e.st>>>(e.beta, e.fix, e.gscr, e.p, e.P, e.ret_slot,
+int branch_support(Engine<R>& e, bool write_z, bool memo, bool defer_fallback) {
+  k_branch_support<R><<<e.K, 1024, 0, e.st>>>(e.beta, e.fix, defer_fallback ? nullptr : e.gscr,
+                                             e.p, e.P, e.ret_slot,
                                              e.ret_count, e.smax, e.br_idx, e.sup, e.sup_cnt,
                                              e.nfree, write_z ? e.zbuf : nullptr,
                                              memo ? e.ub_seen : nullptr, UB_SEEN - 1, e.sup_size);
@@ -620,8 +649,17 @@ int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K) {
   return 0;
 }
 
-template int branch_support<float>(Engine<float>&, bool, bool);
-template int branch_support<double>(Engine<double>&, bool, bool);
+template <class R>
+int branch_fallback(Engine<R>& e) {
+  k_branch_fallback<<<e.K, 256, 0, e.st>>>(e.fix, e.gscr, e.p, e.ret_slot, e.ret_count, e.br_idx);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template int branch_support<float>(Engine<float>&, bool, bool, bool);
+template int branch_support<double>(Engine<double>&, bool, bool, bool);
+template int branch_fallback<float>(Engine<float>&);
+template int branch_fallback<double>(Engine<double>&);
 template int upper_bound<float>(Engine<float>&, bool);
 template int upper_bound<double>(Engine<double>&, bool);
 template int ub_from_masks<float>(Engine<float>&, const uint8_t*, int);
