@@ -13,24 +13,26 @@
 //   warps 2..             epilogue: tcgen05.ld of the accumulator rows (a warp reads its
 //                         32-lane quarter of TMEM, the warps of a quarter take
 //                         alternate 16-column chunks), handed to the epilogue functor.
-// Three kernel shapes share the producer and MMA code:
+// The kernel shapes share the device helpers:
 //   tc_gemm_kernel          one tile per CTA, split-K partials stored (diagnostics);
 //   tc_gemm_cred_kernel     K split over the CTAs of a thread-block cluster, partial tiles
 //                           summed through distributed shared memory in rank order, fused
-//                           epilogue on the sum (X W'^T, G^-1 T, the check product);
+//                           epilogue on the sum (H W'^T, the check product X beta^T);
 //   tc_gemm_persist_kernel  one CTA per SM over the tiles, double-buffered accumulator so
 //                           the epilogue of a tile overlaps the next tile (X^T U' with the
-//                           fused ADMM update);
-//   tc_gemm_pair_kernel     the same product with the operands' roles exchanged (rows =
-//                           node slots, columns = features) on 256 x BN tiles computed by a
-//                           pair of CTAs on two SMs (tcgen05 cta_group::2): each CTA loads
-//                           128 rows of A and half of the B columns, so the B bytes each
-//                           SM receives per output are halved.
+//                           fused ADMM update); tc_gemm_persist_mc_kernel the same in
+//                           clusters of two CTAs that share the A tile by TMA multicast;
+//   tc_gemm_pair_kernel     256 x BN tiles computed by a pair of CTAs on two SMs (tcgen05
+//                           cta_group::2): each CTA loads 128 rows of A and half of the B
+//                           columns, so the B bytes each SM receives per output are halved
+//                           (X^T U' with the fused update, as features x slots or, with the
+//                           roles exchanged, slots x features).
 // NSPLIT = 3 uses hi/lo BF16 pairs of both operands (A = Ah + Al, B = Bh + Bl) and
 // accumulates Ah Bh + Ah Bl + Al Bh: about 16 significant bits per operand, the
-// FP32-class arithmetic of the ADMM path.  NSPLIT = 2 keeps A as one BF16 term and B as
-// a pair (Ah Bh + Ah Bl: the data matrix stored in BF16, the iterates FP32-class).
-// NSPLIT = 1 is the plain BF16 product.
+// FP32-class arithmetic of the ADMM path.  NSPLIT = 2 keeps one operand as a single BF16
+// term (the data) and the other as a pair (the iterate): B is the pair in the one-CTA
+// kernels (Ah Bh + Ah Bl), A in the pair kernel (Ah Bh + Al Bh).  NSPLIT = 1 is the plain
+// BF16 product.
 //
 // Every mbarrier wait is bounded; on expiry the kernel records an error code in
 // *err and leaves its loops, so a fault in the pipeline never hangs the GPU.
@@ -43,7 +45,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;             // 64 BF16 = 128 bytes: one swizzle row
-constexpr int EPI_WARPS = 8;       // default: two warps per TMEM lane quarter
+constexpr int EPI_WARPS = 8;       // default epilogue warps: two per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
