@@ -218,6 +218,7 @@ struct TcEpiAdmm {
   long long p, ldp;
   int nbm, K;
   int vec4;                     // p % 4 == 0: the quad form below (16-byte state accesses)
+  int next_cols;                // columns from a thread's chunk to its next one in the tile
   // STATS (the round's last iteration): per-slot stop-test sums and the beta operand of
   // the check product; a separate instantiation so the other iterations stay lean
 
@@ -277,6 +278,20 @@ struct TcEpiAdmm {
       bo4[e] = ok[e] ? *reinterpret_cast<const float4*>(beta + o) : make_float4(0.f, 0.f, 0.f, 0.f);
       vv4[e] = ok[e] ? *reinterpret_cast<const float4*>(V + o) : make_float4(0.f, 0.f, 0.f, 0.f);
       fx[e] = ok[e] ? *reinterpret_cast<const uint32_t*>(fix + o) : 0u;
+    }
+    // the node state of this thread's next chunk of the tile, into L1 while this chunk
+    // computes (prefetches hold no registers; only in-bounds addresses are prefetched)
+    if (fin && (n0 % BN) + next_cols < BN) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int n = n0 + next_cols + 4 * lq + e;
+        if (n < N) {
+          const long long o = (long long)n * p + fb;
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(beta + o));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(V + o));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(fix + o));
+        }
+      }
     }
     float st[4][4];                                        // [stat][slot]
 #pragma unroll
@@ -649,7 +664,7 @@ static int fused_xtu_bn(Engine<float>& e, const TcOperand& XC, const TcOperand& 
   TcEpiAdmm<BN3, STATS> epi{e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part,
                             e.w_hi, NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr,
                             (STATS && NS >= 2) ? e.b_lo : nullptr, e.P, prob_f32(e.P), e.p, e.ldp,
-                            e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0};
+                            e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0, 16 * (FUSED_EPIW / 4)};
   if (e.tc_mc3 > 0)   // clusters of two CTAs sharing the X tile
     return tc_gemm_persist_mc<BN3, NS, TcEpiAdmm<BN3, STATS>, FUSED_EPIW>(
         e.st, XC, Uop, e.p, e.K, e.n, e.tc_mc3, e.slot_active, e.tc_err, epi);
@@ -698,7 +713,7 @@ static int fused_pairnt_bn(Engine<float>& e, const TcOperand& XC, const TcOperan
   TcEpiAdmmPair<BN, STATS> epi{TcEpiAdmm<BN, STATS>{
       e.bcR, e.rbcR, e.beta, e.V, e.fix, e.slot_active, (float*)e.g3part, e.w_hi,
       NS >= 2 ? e.w_lo : nullptr, STATS ? e.b_hi : nullptr, (STATS && NS >= 2) ? e.b_lo : nullptr,
-      e.P, prob_f32(e.P), e.p, e.ldp, e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0}};
+      e.P, prob_f32(e.P), e.p, e.ldp, e.nbm3, e.K, e.p % 4 == 0 ? 1 : 0, 16 * (PAIR_EPIW / 4)}};
   return tc_gemm_pair<BN, NS, TcEpiAdmmPair<BN, STATS>, PAIR_EPIW>(e.st, XC, Uop, e.p, e.K, e.n,
                                                                    e.tc_pair3, nullptr, e.tc_err,
                                                                    epi);
