@@ -443,12 +443,12 @@ TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
     #  transposed)
     ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
-        "blocks": _PAIR_NT, "sources": "1955286f4cf01cae", "bytes": 45.181696e6 + 0.556800e6,
+        "blocks": _PAIR_NT, "sources": "302c84e0a3026e80", "bytes": 45.181440e6 + 0.504320e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<176, 3, TcEpiAdmmPair<176, 0>, 12>",
                              f="fused_pair_untransposed_c2_K512_tc3.md")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 80, False, False, False): {
-        "blocks": _PERSIST, "sources": "5c2c9a20c3186ba6", "bytes": 45.180416e6 + 0.587776e6,
-        "note": _NOTE.format(k="tc_gemm_persist_kernel<80, 3, TcEpiAdmm<80, 0>, 12>",
+    ("gemm_xtu_prox", "c2", 512, "tc3", 64, False, False, False): {
+        "blocks": _PERSIST, "sources": "445fd8171ad98c9b", "bytes": 45.183232e6 + 0.606976e6,
+        "note": _NOTE.format(k="tc_gemm_persist_kernel<64, 3, TcEpiAdmm<64, 0>, 12>",
                              f="fused_xtu_prox_shapes_c2_K512_tc3.md")},
 }
 
