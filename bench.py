@@ -74,6 +74,8 @@ def parse():
                     help="fused X^T U' shape: 0 measured at setup, 1 one CTA per tile, "
                          "2 clusters of two sharing X, 3 transposed on CTA pairs, "
                          "4 untransposed on CTA pairs")
+    ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2],
+                    help="U' = H W'^T: 0 measured at setup, 1 cluster-reduced, 2 CTA pairs split-K")
     ap.add_argument("--mv-crossover", type=int, default=-1,
                     help="narrow-form crossover (-1 default; 0 = tensor-core form only: graphs "
                          "without conditional nodes, which ncu can profile kernel by kernel)")
@@ -192,7 +194,7 @@ def run_mine(args, rank, world):
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
                                   queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
                                   relax_alpha=args.alpha, mv_crossover=args.mv_crossover,
-                                  fused_shape=args.fused_shape)
+                                  fused_shape=args.fused_shape, u_shape=args.u_shape)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
@@ -241,7 +243,8 @@ def run_mine(args, rank, world):
     res = bnb.bnb_solve_finish(h)
     h.close()
     shapes = {k: stats.get(k) for k in ("xw_tile_width", "xw_cluster", "fused_tile_width",
-                                          "fused_clusters", "fused_pairs", "fused_transposed")}
+                                          "fused_clusters", "fused_pairs", "fused_transposed",
+                                          "u_split")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,

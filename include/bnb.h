@@ -98,6 +98,13 @@ typedef struct {
                             (256 features per pair tile; not for BNB_PREC_BF16X2).  A shape
                             the device or the problem cannot run fails bnb_create with
                             BNB_EINVAL. */
+  int u_shape;           /* tensor-core precisions, the product U' = H W'^T: 0 (default) =
+                            the faster of the two forms measured at creation; 1 = K split
+                            over the CTAs of a thread-block cluster, reduced in distributed
+                            shared memory; 2 = 256 x 256 tiles on CTA pairs with K split into
+                            chunks whose partial products a second kernel adds in order
+                            (BNB_PREC_TC3 and BNB_PREC_BF16 only; needs at least two chunks
+                            per tile to fill the GPU).  Otherwise as fused_shape. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */
@@ -319,6 +326,7 @@ typedef struct {
      transposed (256 slots x width features per pair tile; else 256 features x width
      slots) */
   int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters, fused_pairs, fused_transposed;
+  int u_split;              /* K chunks of U' = H W'^T on CTA pairs (0: the cluster-reduced form) */
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

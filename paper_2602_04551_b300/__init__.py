@@ -47,7 +47,7 @@ class bnb_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
                 ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int),
-                ("fused_shape", ctypes.c_int)]
+                ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):
@@ -60,7 +60,7 @@ class bnb_stats(ctypes.Structure):
                 ("round_kernels", ctypes.c_int), ("xw_tile_width", ctypes.c_int),
                 ("xw_cluster", ctypes.c_int), ("fused_tile_width", ctypes.c_int),
                 ("fused_clusters", ctypes.c_int), ("fused_pairs", ctypes.c_int),
-                ("fused_transposed", ctypes.c_int)]
+                ("fused_transposed", ctypes.c_int), ("u_split", ctypes.c_int)]
 
 
 class bnb_progress(ctypes.Structure):

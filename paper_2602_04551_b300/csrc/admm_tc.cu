@@ -538,7 +538,7 @@ struct TcEpiAdmmT {
 
   // the update of the chunk loaded by load() with the accumulator values of its 16 features
   __device__ __forceinline__ void operator()(int m, int f0, const float (&acc)[16], int M, int N,
-                                             State& st, const Chunk& ck, float*) const {
+                                             State& st, const Chunk& ck, float*, int) const {
     if (m >= M || !active[m]) return;
     const float rho = PF.rho, irho = PF.irho;
     const long long rb = (long long)m * p, rw = (long long)m * ldp;
@@ -634,7 +634,7 @@ struct TcEpiAdmmPair {
   __device__ __forceinline__ void begin(State&) const {}
   __device__ __forceinline__ void load(int, int, int, int, Chunk&) const {}
   __device__ __forceinline__ void operator()(int m, int n0, const float (&acc)[16], int M, int N,
-                                             State&, const Chunk&, float* sm) const {
+                                             State&, const Chunk&, float* sm, int) const {
     inner(m, n0, acc, M, N, (int)(threadIdx.x >> 5) & 3, sm);
   }
   __device__ __forceinline__ void end(int, int, State&, float*) const {}
@@ -643,6 +643,66 @@ struct TcEpiAdmmPair {
     inner.finish(t, nthr, m0, nt * BN, M, N, sm);
   }
 };
+
+// U' = H W'^T on CTA pairs with K split into chunks (the alternative to the
+// cluster-reduced form): each pair stores the partial product of its chunk,
+// part[z][slot][sample], and k_u_reduce adds the chunks in order and applies what
+// TcEpiU applies to the cluster sum.
+struct TcEpiPartial {
+  static constexpr int SMEM_FLOATS = 0;
+  struct State {};
+  struct Chunk {};
+  float* __restrict__ part;
+  const int* __restrict__ active;
+  __device__ __forceinline__ void begin(State&) const {}
+  __device__ __forceinline__ void load(int, int, int, int, Chunk&) const {}
+  __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N,
+                                             State&, const Chunk&, float*, int z) const {
+    if (m >= M) return;
+    float* pz = part + (long long)z * N * M;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = n0 + j;
+      if (n < N && active[n]) pz[(long long)n * M + m] = v[j];
+    }
+  }
+  __device__ __forceinline__ void end(int, int, State&, float*) const {}
+  __device__ __forceinline__ void finish(int, int, int, int, int, int, float*) const {}
+};
+
+// grid (ceil(n / 128), K); block 128: sample m of slot s
+__global__ void k_u_reduce(const float* __restrict__ part, int nz, int n, int K,
+                           const int* __restrict__ active, __nv_bfloat16* __restrict__ hi,
+                           __nv_bfloat16* __restrict__ lo, long long ld, float* __restrict__ U,
+                           const float* __restrict__ uc, const float* __restrict__ y,
+                           float* __restrict__ stat, int nbt, int stats) {
+  __shared__ float sh[32];
+  const int s = blockIdx.y;
+  if (!active[s]) return;
+  const int m = blockIdx.x * 128 + threadIdx.x;
+  float v = 0.f;
+  if (m < n)
+    for (int z = 0; z < nz; ++z) v += part[((long long)z * K + s) * n + m];
+  float r0 = 0.f, r1 = 0.f;
+  if (m < n) {
+    split_store(v, hi, lo, (long long)s * ld + m);
+    if (stats) {
+      const float u = uc[m] + v;
+      U[(long long)s * n + m] = u;
+      const float r = y[m] - u;
+      r0 = r * r;
+      r1 = y[m] * r;
+    }
+  }
+  if (stats) {
+    r0 = block_sum(r0, sh);
+    r1 = block_sum(r1, sh);
+    if (threadIdx.x == 0) {
+      stat[(0LL * nbt + blockIdx.x) * K + s] = r0;
+      stat[(1LL * nbt + blockIdx.x) * K + s] = r1;
+    }
+  }
+}
 
 // cluster-reduced product with the tile width chosen at setup (128 or 256 columns)
 template <int NS, class Epi>
@@ -759,6 +819,97 @@ static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop
   }
 }
 
+// the K chunk (a multiple of the K step) of the split pair form of U' = H W'^T
+static int u_chunk(const Engine<float>& e) {
+  const int steps = (e.p + tc::BK - 1) / tc::BK;
+  const int per = (steps + e.tc_usplit - 1) / e.tc_usplit;
+  return per * tc::BK;
+}
+
+// U' = H W'^T with the shape chosen at setup; the epilogue writes the BF16 operand of
+// X^T U' and, on the round's last iteration, U = u_c + U' and the stop-test sums
+template <int NS>
+static int u_product(Engine<float>& e, const TcOperand& HT, const TcOperand& Wop, bool last) {
+  const int n = e.n, p = e.p, K = e.K;
+  if constexpr (NS != 2) {
+    if (e.tc_usplit > 0) {
+      const int kc = u_chunk(e);
+      const int nz = (p + kc - 1) / kc;
+      if (int rc = tc_gemm_pair<256, NS, TcEpiPartial, 8>(e.st, HT, Wop, n, K, p, e.tc_upairs,
+                                                          nullptr, e.tc_err,
+                                                          TcEpiPartial{e.upart, e.slot_active},
+                                                          kc))
+        return rc;
+      k_u_reduce<<<dim3((n + 127) / 128, K), 128, 0, e.st>>>(
+          e.upart, nz, n, K, e.slot_active, e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn,
+          (float*)e.U, (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, last ? 1 : 0);
+      BNB_CUDA_OK(cudaGetLastError());
+      return 0;
+    }
+  }
+  return cred<NS>(e, e.tc_bn1, HT, Wop, n, K, p, e.tc_c1,
+                  TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
+                         (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K,
+                         last ? 1 : 0});
+}
+
+// Times the two forms of U' = H W'^T (cluster-reduced; CTA pairs with the K range split
+// into chunks reduced by k_u_reduce) and keeps the faster, or the one u_product asks for.
+template <int NS>
+static int pick_u_shape(Engine<float>& e) {
+  e.tc_usplit = 0;
+  if constexpr (NS == 2) {
+    return e.u_kind == 2 ? BNB_EINVAL : 0;   // the pair kernel's 2-term form pairs H, not W'
+  } else {
+  const int tiles = ((e.n + 255) / 256) * ((e.K + 255) / 256);
+  int pairs = tc_pair_clusters<256, NS, TcEpiPartial, 8>();
+  if (pairs > e.sms / 2) pairs = e.sms / 2;
+  const int steps = (e.p + tc::BK - 1) / tc::BK;
+  int nz = tiles > 0 ? pairs / tiles : 0;
+  if (nz > e.usplit_max) nz = e.usplit_max;
+  if (nz > steps) nz = steps;
+  if (nz < 2) return e.u_kind == 2 ? BNB_EINVAL : 0;   // the pair form would not fill the GPU
+  if (e.u_kind == 1) return 0;
+  e.tc_upairs = pairs;
+  if (e.u_kind == 2) {
+    e.tc_usplit = nz;
+    return 0;
+  }
+  cudaStream_t st = e.st;
+  const TcOperand HT{e.ht_hi, e.ht_lo, e.n, e.p, e.ldp};
+  const TcOperand Wop{e.w_hi, e.w_lo, e.K, e.p, e.ldp};
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0xff, sizeof(int) * e.K, st));   // nonzero: active
+  cudaEvent_t ev[2];
+  BNB_CUDA_OK(cudaEventCreate(&ev[0]));
+  BNB_CUDA_OK(cudaEventCreate(&ev[1]));
+  float tbest[2] = {-1.f, -1.f};
+  int rc = 0;
+  for (int sweep = 0; sweep < 2 && !rc; ++sweep)
+    for (int c = 0; c < 2 && !rc; ++c) {
+      e.tc_usplit = c ? nz : 0;
+      if ((rc = u_product<NS>(e, HT, Wop, false))) break;                    // warm-up
+      cudaEventRecord(ev[0], st);
+      for (int r = 0; r < 5 && !rc; ++r) rc = u_product<NS>(e, HT, Wop, false);
+      cudaEventRecord(ev[1], st);
+      if (rc || cudaEventSynchronize(ev[1]) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (tbest[c] < 0 || ms < tbest[c]) tbest[c] = ms;
+    }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  e.tc_usplit = (tbest[1] >= 0 && tbest[1] < tbest[0]) ? nz : 0;
+  BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.u_hi, 0, 2 * (size_t)e.K * e.ldn, st));
+  if (e.u_lo) BNB_CUDA_OK(cudaMemsetAsync(e.u_lo, 0, 2 * (size_t)e.K * e.ldn, st));
+  int err = 0;
+  BNB_CUDA_OK(cudaMemcpyAsync(&err, e.tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BNB_CUDA_OK(cudaStreamSynchronize(st));
+  return err ? BNB_ECUDA : 0;
+  }
+}
+
 template <int NS>
 static int round_tc(Engine<float>& e, int iters) {
   const int n = e.n, p = e.p, K = e.K;
@@ -783,11 +934,7 @@ static int round_tc(Engine<float>& e, int iters) {
     // BF16 operand of X^T U' and, on the round's last iteration, U = u_c + U' and the
     // stop-test sums of r = y - U
     prof_begin(e.prof, st);
-    if (int rc = cred<NS>(
-            e, e.tc_bn1, HT, Wop, n, K, p, e.tc_c1,
-            TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
-                   (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0}))
-      return rc;
+    if (int rc = u_product<NS>(e, HT, Wop, last)) return rc;
     prof_end(e.prof, st, PK_GEMM_XW);
     prof_begin(e.prof, st);
     if (int rc = fused_xtu<NS>(e, XC, Uop, last))
@@ -1000,8 +1147,12 @@ int setup_tc(Engine<float>& e) {
   if (gh > 8192) gh = 8192;
   k_split_f32_t<<<(int)gh, 256, 0, st>>>(e.H32, n, p, e.ldp, e.ht_hi, e.ht_lo);
   BNB_CUDA_OK(cudaGetLastError());
-  return e.tc_mode == 3 ? pick_fused_shape<3>(e) : e.tc_mode == 2 ? pick_fused_shape<2>(e)
-                                                                  : pick_fused_shape<1>(e);
+  if (int rc = e.tc_mode == 3   ? pick_fused_shape<3>(e)
+               : e.tc_mode == 2 ? pick_fused_shape<2>(e)
+                                : pick_fused_shape<1>(e))
+    return rc;
+  return e.tc_mode == 3 ? pick_u_shape<3>(e) : e.tc_mode == 2 ? pick_u_shape<2>(e)
+                                                              : pick_u_shape<1>(e);
 }
 
 }  // namespace bnb

@@ -127,6 +127,12 @@ static int allocate(Engine<R>& e) {
       ALLOC(e.act_list, K);
       ALLOC(e.act_count, 1);
       ALLOC(e.mv_part, (long long)MV_ZMAX * MV_MAX * n);
+      {   // K chunks of the split pair form of U' = H W'^T (74 pairs on a B300)
+        const long long tiles = ((n + 255) / 256) * ((K + 255) / 256);
+        e.usplit_max = (int)(tiles > 0 ? (74 / tiles > 16 ? 16 : 74 / tiles) : 0);
+        if (e.usplit_max >= 2) ALLOC(e.upart, (long long)e.usplit_max * K * n);
+        else e.usplit_max = 0;
+      }
       ALLOC(e.g3mv, 4LL * MV_MAX * ((p + 31) / 32));
       const bool xlo = e.tc_mode == 3;   // X as a hi/lo pair (3 terms)
       const bool lo = e.tc_mode >= 2;    // iterates and G^-1 as pairs (2 and 3 terms)
@@ -411,6 +417,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->lockstep = 0;
   o->mv_crossover = -1;
   o->fused_shape = 0;
+  o->u_shape = 0;
   return BNB_OK;
 }
 
@@ -424,6 +431,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->dmax = o.max_depth;
   e->lockstep = o.lockstep ? 1 : 0;
   e->fused_kind = o.fused_shape;
+  e->u_kind = o.u_shape;
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
   e->qcap = o.queue_capacity;
@@ -468,8 +476,8 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   if constexpr (sizeof(R) == 4) {
     if (e->tc_mode) {
       if (int rc = setup_tc(*e))
-        return rc == BNB_EINVAL ? fail(BNB_EINVAL, "fused_shape %d: no such shape runs here",
-                                       o.fused_shape)
+        return rc == BNB_EINVAL ? fail(BNB_EINVAL, "fused_shape %d / u_shape %d: no such shape "
+                                                    "runs here", o.fused_shape, o.u_shape)
                                 : rc;
       e->mv_cross = o.mv_crossover < 0 ? 16 : (o.mv_crossover > MV_MAX ? MV_MAX : o.mv_crossover);
       if (int rc = mv_setup(*e)) return rc;
@@ -511,6 +519,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.max_depth < 8 || o.max_depth > 4096) return fail(BNB_EINVAL, "max_depth must be in [8, 4096]");
   if (o.mv_crossover < -1 || o.mv_crossover > 32) return fail(BNB_EINVAL, "mv_crossover must be in [-1, 32]");
   if (o.fused_shape < 0 || o.fused_shape > 4) return fail(BNB_EINVAL, "fused_shape must be in [0, 4]");
+  if (o.u_shape < 0 || o.u_shape > 2) return fail(BNB_EINVAL, "u_shape must be in [0, 2]");
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
@@ -555,6 +564,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
     h->stats.fused_clusters = h->ef->tc_mc3;
     h->stats.fused_pairs = h->ef->tc_pair3;
     h->stats.fused_transposed = h->ef->tc_pair3 > 0 && !h->ef->tc_pairnt ? 1 : 0;
+    h->stats.u_split = h->ef->tc_usplit;
   }
   *out = h;
   return BNB_OK;

@@ -59,7 +59,7 @@ struct TcEpiPairPlain {
   __device__ __forceinline__ void begin(State&) const {}
   __device__ __forceinline__ void load(int, int, int, int, Chunk&) const {}
   __device__ __forceinline__ void operator()(int m, int n0, const float (&v)[16], int M, int N,
-                                             State&, const Chunk&, float*) const {
+                                             State&, const Chunk&, float*, int) const {
     if (m >= M) return;
 #pragma unroll
     for (int j = 0; j < 16; ++j)

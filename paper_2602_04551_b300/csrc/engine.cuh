@@ -168,6 +168,11 @@ struct Engine {
   int tc_mc3 = 0;               // > 0: it runs in clusters of two sharing the X tile (this many)
   int tc_pair3 = 0;             // > 0: it runs on this many CTA pairs
   int tc_pairnt = 0;            // 1: the pair product untransposed (256 features x 176 slots)
+  int u_kind = 0;               // U' = H W'^T: 0 measured, 1 cluster-reduced, 2 pairs split-K
+  int tc_usplit = 0;            // > 0: U' on CTA pairs in this many K chunks (k_u_reduce)
+  int tc_upairs = 0;            // CTA pairs the split form runs on
+  int usplit_max = 0;           // most K chunks the partial buffer holds
+  float* upart = nullptr;       // [usplit_max][K][n] partial products of U'
   int fused_kind = 0;           // requested shape: 0 measured, 1 single, 2 clusters of two,
                                 // 3 pairs transposed, 4 pairs untransposed
   float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2

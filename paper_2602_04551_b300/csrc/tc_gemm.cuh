@@ -977,8 +977,10 @@ struct PairGeo {
 };
 
 // Persistent product on CTA pairs: cluster c walks the units u = c, c + clusters, ...
-// (row tile mt = u % mtiles, column tile nt = u / mtiles); units whose 256 rows are all
-// inactive are skipped by every role of both CTAs alike.
+// (K chunk z = u / tiles of kchunk elements, row tile mt and column tile nt of u % tiles,
+// rows fastest); units whose 256 rows are all inactive are skipped by every role of both
+// CTAs alike.  With one chunk (kchunk >= Kred) a unit is a whole output tile; with several
+// the epilogue receives the partial product of chunk z.
 //   full[s]      leader: both CTAs' TMA bytes of stage s (expect_tx by the leader)
 //   empty[s]     each CTA: the leader's MMAs have read stage s (multicast commit)
 //   tfull[b]     each CTA: accumulator b holds the tile (multicast commit)
@@ -990,7 +992,8 @@ struct PairGeo {
 //   typename Epi::State st; epi.begin(st);
 //   typename Epi::Chunk ck; epi.load(row, first column, M, N, ck)   the chunk's other
 //                                 inputs (issued for the first chunk before the wait)
-//   epi(row, first column, 16 accumulator values, M, N, st, ck, smem)  per 16-column chunk
+//   epi(row, first column, 16 accumulator values, M, N, st, ck, smem, z)  per 16-column
+//                                 chunk of the partial product of K chunk z
 //   epi.end(r, gq, st, smem)      after the thread's last chunk of the tile (r = row in CTA)
 //   epi.finish(t, nthreads, first row of the CTA, nt, M, N, smem)  after the warps meet
 template <int BN, int NSPLIT, class Epi, int EPIW>
@@ -999,7 +1002,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
                     const __grid_constant__ CUtensorMap ma_lo,
                     const __grid_constant__ CUtensorMap mb_hi,
                     const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred,
-                    const int* __restrict__ active, int* err, Epi epi) {
+                    int kchunk, const int* __restrict__ active, int* err, Epi epi) {
   using G = PairGeo<BN, NSPLIT>;
   constexpr int S = G::STAGES;
   constexpr int MAXMT = 64;                      // row tiles with an activity mask (M <= 64 x 256)
@@ -1020,8 +1023,14 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
   const bool leader = rank == 0;
   const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
   const int mtiles = (M + 255) / 256, ntiles = (N + BN - 1) / BN;
-  const int nunits = mtiles * ntiles;
-  const int nk = (Kred + BK - 1) / BK;
+  const int ntile = mtiles * ntiles;
+  const int nz = (Kred + kchunk - 1) / kchunk;   // K chunks: unit u takes chunk u / ntile
+  const int nunits = ntile * nz;
+  // K steps of a unit's chunk
+  auto unit_nk = [&](int z) {
+    const int kb = z * kchunk, ke = min(Kred, kb + kchunk);
+    return (ke - kb + BK - 1) / BK;
+  };
   for (int j = threadIdx.x; j < MAXMT; j += blockDim.x) {
     int on = 0;
     if (j < mtiles && active != nullptr) {
@@ -1073,9 +1082,10 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     long long g = 0;
     bool ok = true;
     for (int u = cid; u < nunits && ok; u += ncl) {
-      const int mt = u % mtiles, nt = u / mtiles;
+      const int z = u / ntile, mt = (u % ntile) % mtiles, nt = (u % ntile) / mtiles;
       if (!row_tile_on(mt)) continue;
       const int arow = mt * 256 + 128 * (int)rank, brow = nt * BN + (BN / 2) * (int)rank;
+      const int nk = unit_nk(z);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % S);
         if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)(((g / S) & 1) ^ 1), err, 1)) {
@@ -1083,7 +1093,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
           break;
         }
         if (leader) mbar_expect_tx(&full_bar[s], 2 * G::STAGE_BYTES);
-        const int k = kb * BK;
+        const int k = z * kchunk + kb * BK;
         const uint32_t fb = full_l + 8u * (uint32_t)s;
         uint8_t* st0 = base + s * G::STAGE_BYTES;
         tma_load_2d_pair(st0, &ma_hi, fb, k, arow);
@@ -1105,8 +1115,9 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     int i = 0;
     bool ok = true;
     for (int u = cid; u < nunits && ok; u += ncl) {
-      const int mt = u % mtiles;
+      const int z = u / ntile, mt = (u % ntile) % mtiles;
       if (!row_tile_on(mt)) continue;
+      const int nk = unit_nk(z);
       const int b = i % G::NBUF, use = i / G::NBUF;
       if (use >= 1 && !mbar_wait_cluster(&tempty_bar[b], (uint32_t)((use & 1) ^ 1), err, 8)) break;
       fence_after();
@@ -1145,7 +1156,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
     const int gq = (warp - 2) >> 2;
     int i = 0;
     for (int u = cid; u < nunits; u += ncl) {
-      const int mt = u % mtiles, nt = u / mtiles;
+      const int z = u / ntile, mt = (u % ntile) % mtiles, nt = (u % ntile) / mtiles;
       if (!row_tile_on(mt)) continue;
       const int b = i % G::NBUF, use = i / G::NBUF;
       const int m0 = mt * 256 + 128 * (int)rank;
@@ -1166,7 +1177,7 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
           if (c != cf) epi.load(row, nt * BN + c, M, N, ck);
           float v[16];
           tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * G::BUF + c), v);
-          epi(row, nt * BN + c, v, M, N, es, ck, epi_smem);
+          epi(row, nt * BN + c, v, M, N, es, ck, epi_smem, z);
         }
       }
       fence_before();

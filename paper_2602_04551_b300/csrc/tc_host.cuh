@@ -307,7 +307,7 @@ int tc_pair_clusters() {
 // active row are skipped) M <= 64 x 256.
 template <int BN, int NSPLIT, class Epi, int EPIW = tc::EPI_WARPS>
 int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
-                 int clusters, const int* active, int* err, Epi epi) {
+                 int clusters, const int* active, int* err, Epi epi, int kchunk = 0) {
   using G = tc::PairGeo<BN, NSPLIT>;
   if (M <= 0 || N <= 0 || Kred <= 0) return 0;
   if ((active != nullptr && M > 64 * 256) || clusters < 1) return BNB_EINVAL;
@@ -326,7 +326,10 @@ int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M,
     BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
     attr_set = true;
   }
-  const long long units = (long long)((M + 255) / 256) * ((N + BN - 1) / BN);
+  if (kchunk <= 0 || kchunk >= Kred) kchunk = (Kred + tc::BK - 1) / tc::BK * tc::BK;
+  if (kchunk % tc::BK) return BNB_EINVAL;
+  const long long units = (long long)((M + 255) / 256) * ((N + BN - 1) / BN) *
+                          ((Kred + kchunk - 1) / kchunk);
   const int ncl = (int)(units < clusters ? units : clusters);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * ncl);
@@ -340,7 +343,8 @@ int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, active, err, epi));
+  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, kchunk, active, err,
+                                 epi));
   return 0;
 }
 

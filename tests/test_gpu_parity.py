@@ -273,6 +273,44 @@ def test_converged_bounds_odd_sizes():
             assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
 
 
+U_SHAPES = [pytest.param(1, id="cluster_reduced"), pytest.param(2, id="pairs_split_k")]
+
+
+@pytest.mark.parametrize("ushape", U_SHAPES)
+@pytest.mark.parametrize("prec", [3, 2])
+def test_one_admm_iteration_every_u_shape(ushape, prec):
+    """Both forms of U' = H W'^T (K split over a cluster; K chunks on CTA pairs added by
+    a second kernel) give the oracle's iteration."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=128, rows=range(45), seed=41,
+                         u_shape=ushape, mv_crossover=0)
+
+
+def test_one_admm_iteration_pairs_split_k_full_size():
+    """c2 at K = 512 with U' on CTA pairs in 9 K chunks: slots of both slot tiles and both
+    halves of a tile sampled."""
+    inst, lam0, lam2, M = _inst("c2", 0)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512,
+                         rows=[0, 127, 128, 255, 256, 511], seed=42, u_shape=2, mv_crossover=0)
+
+
+@pytest.mark.parametrize("ushape", U_SHAPES)
+def test_converged_bounds_every_u_shape(ushape):
+    """Converged node bounds (the stop-test sums of U come from either form of U') stay
+    valid and tight against the independent second solver."""
+    inst, lam0, lam2, M = _inst("c2_small", 2)
+    rng = np.random.default_rng(43)
+    fix = datagen.random_fixings(inst.p, 20, rng, 10)
+    with _handle(inst, lam0, lam2, M, 3, K=128, node_tol=1e-5, max_admm_iter=20000,
+                 mv_crossover=0, u_shape=ushape) as h:
+        out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+        assert (bnb.bnb_get_stats(h)["u_split"] > 0) == (ushape == 2)
+    for k in range(20):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+        assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
+
+
 # ------------------------------------------------------------------ converged node
 
 
