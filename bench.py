@@ -446,7 +446,7 @@ TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
     #  transposed)
     ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
-        "blocks": _PAIR_NT, "sources": "302c84e0a3026e80", "bytes": 45.181440e6 + 0.504320e6,
+        "blocks": _PAIR_NT, "sources": "cbfa68214a12d6bb", "bytes": 45.185024e6 + 0.526592e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<176, 3, TcEpiAdmmPair<176, 0>, 12>",
                              f="fused_pair_untransposed_c2_K512_tc3.md")},
     ("gemm_xtu_prox", "c2", 512, "tc3", 64, False, False, False): {
