@@ -243,16 +243,6 @@ __global__ void k_retired_list(int K, int* __restrict__ slot_retire, int* __rest
   if (threadIdx.x == 0) *ret_count = base;
 }
 
-static inline int pick_splits(int mblocks, int nblocks, int kred, int bk) {
-  const int want = 2 * 148;
-  int tiles = mblocks * nblocks;
-  int s = (want + tiles - 1) / tiles;
-  int smax = kred / (8 * bk);
-  if (s > smax) s = smax;
-  if (s < 1) s = 1;
-  return s;
-}
-
 template <class R>
 int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_inc) {
   using C = TileCfg<R>;

@@ -31,7 +31,6 @@
 namespace bnb {
 
 constexpr int MV_G = 16;     // slots per group
-constexpr int MV_TJ = 32;    // contraction step staged in shared memory
 constexpr int MV_PC = 32;    // feature columns per block of k_mv_prox
 
 // ordered list of the active slots (single block)

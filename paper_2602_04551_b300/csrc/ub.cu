@@ -409,8 +409,7 @@ __global__ void k_ub_polish(const double* __restrict__ X64, const double* __rest
   __shared__ int Fidx[256];
   __shared__ int W[256];
   __shared__ double bt[256], tgt[256], rhs[256];
-  __shared__ int nf_s, state, block_at;
-  __shared__ double alpha_s;
+  __shared__ int nf_s, state;
   const int q = blockIdx.x;
   if (q >= *ret_count || !pol_flag[q]) return;
   const int s = sup_cnt[q];
