@@ -506,11 +506,15 @@ def roofline(out, args, pk):
         r.update(bound="alu", peak=peak, frac=ach / peak,
                  peak_note="FP32 FMA peak 148 SM x 128 lanes x 2 x 2032 MHz (derived)")
     else:
-        peak = float(pk.get("bf16_tflops_sustained", 1341.1))
+        if "bf16_tflops_sustained" in pk:
+            peak = float(pk["bf16_tflops_sustained"])
+            note = "measured sustained dense BF16 (MEASURED_PEAKS.json)"
+        else:
+            peak = 1400.0
+            note = "fallback: 1.4 PFLOP/s sustained dense BF16 (no measured peaks file)"
         mult = {"tc3": 3.0, "bf16x2": 2.0}.get(args.precision, 1.0)
         r.update(bound="tensor", peak=peak, frac=ach / peak, achieved_hw=ach * mult,
-                 frac_hw=ach * mult / peak,
-                 peak_note="measured sustained dense BF16 (MEASURED_PEAKS.json)")
+                 frac_hw=ach * mult / peak, peak_note=note)
     return r
 
 

@@ -1,0 +1,81 @@
+"""Host logic of bench.py (no GPU): the roofline figures of the dominant kernel and the
+provenance rule of its DRAM traffic (reported only while the captured kernel's source is
+unchanged)."""
+import importlib.util
+import os
+import shutil
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def _out(key, ms_fused=0.036, ms_u=0.028, active=491):
+    _, workload, K, prec, width, mc, pairs, transposed = key
+    return {"prof": {"gemm_xtu_prox": [ms_fused, 10], "gemm_xw": [ms_u, 10], "certificate": [0.08, 1]},
+            "cfg": {"n": 1000, "p": 5000}, "prog": {"active_slots": active},
+            "shapes": {"fused_tile_width": width, "fused_clusters": 74 if mc else 0,
+                       "fused_pairs": 74 if pairs else 0, "fused_transposed": int(transposed)}}
+
+
+def _args(key):
+    _, workload, K, prec, *_ = key
+    return types.SimpleNamespace(workload=workload, K=K, precision=prec)
+
+
+def test_roofline_figures(bench):
+    key = next(iter(bench.TRAFFIC))
+    r = bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1390.1})
+    assert r["kernel"] == "gemm_xtu_prox"
+    flops = 2.0 * 1000 * 5000 * 491
+    assert r["flops_per_launch"] == flops
+    assert r["achieved"] == pytest.approx(flops / 0.036e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1390.1)
+    assert r["achieved_hw"] == pytest.approx(3 * r["achieved"])
+    assert r["bound"] == "tensor" and r["peak"] == 1390.1
+    assert r["share_of_round"] == pytest.approx(0.36 / (0.36 + 0.28 + 0.08))
+    # the committed capture matches the committed kernel source
+    assert r["traffic"] == bench.TRAFFIC[key]["bytes"]
+
+
+def test_fallback_peak_is_labelled(bench):
+    key = next(iter(bench.TRAFFIC))
+    r = bench.roofline(_out(key), _args(key), {})
+    assert r["peak"] == 1400.0 and "fallback" in r["peak_note"]
+
+
+def test_traffic_needs_the_captured_shape(bench):
+    key = next(iter(bench.TRAFFIC))
+    other = key[:4] + (999,) + key[5:]
+    r = bench.roofline(_out(other), _args(other), {"bf16_tflops_sustained": 1390.1})
+    assert r["traffic"] is None
+
+
+def test_traffic_dropped_when_the_kernel_source_changes(bench, tmp_path, monkeypatch):
+    key = next(iter(bench.TRAFFIC))
+    csrc = tmp_path / "paper_2602_04551_b300" / "csrc"
+    shutil.copytree(os.path.join(ROOT, "paper_2602_04551_b300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    r = bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1390.1})
+    assert r["traffic"] is not None                      # an identical copy still matches
+    f, start, _ = bench.TRAFFIC[key]["blocks"][0]
+    text = (csrc / f).read_text()
+    i = text.index(start)
+    (csrc / f).write_text(text[:i] + start + " /* edited */" + text[i + len(start):])
+    r = bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1390.1})
+    assert r["traffic"] is None
