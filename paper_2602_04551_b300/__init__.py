@@ -137,10 +137,16 @@ def _check(rc, h=None):
 
 
 def bnb_options_default(**overrides) -> bnb_options:
+    """bnb_options with the library's defaults, then the given fields (an unknown field
+    name is an error: ctypes would otherwise keep it as a plain Python attribute that the
+    library never sees)."""
     lib = load_library()
     o = bnb_options()
     _check(lib.bnb_options_default(ctypes.byref(o)))
+    fields = {name for name, _ in bnb_options._fields_}
     for k, v in overrides.items():
+        if k not in fields:
+            raise TypeError(f"bnb_options has no field {k!r}")
         setattr(o, k, v)
     return o
 

@@ -71,3 +71,10 @@ def test_struct_layouts_match_header(lib, tmp_path):
         assert got == int(value), (name, field, got, value)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def test_options_reject_unknown_fields(lib):
+    o = lib.bnb_options_default(M=2.0, fused_shape=4, u_shape=1)
+    assert (o.M, o.fused_shape, o.u_shape) == (2.0, 4, 1)
+    with pytest.raises(TypeError):
+        lib.bnb_options_default(M=1.0, fused_shap=3)
