@@ -28,6 +28,8 @@ numpy, in the order the paper states them, with no blocking or fusion:
 Pins (tests marked "not gpu"): brute force, closed forms against 1-D numeric
 optimisation, weak and strong duality, agreement of two independent
 relaxation solvers, the orthonormal-design special case, library
-box-constrained least squares.
+box-constrained least squares, and a branch-and-bound that takes incumbents at
+leaves only.  A mutation test plants one mistake at a time in these functions
+and checks that a pin fails.
 """
 from . import relax, admm, pgd, ub, brute, bnb, mp  # noqa: F401

@@ -7,7 +7,9 @@ Follows Section 2.2.1 and Algorithm 1 (Section 2.4):
     its parent (Section 3.1.3) and bounded by the dual of Proposition 1 at
     r = y - X b;  LB_u = max(LB_parent, D(r)) (both are valid bounds);
   * upper bound (Section 3.3): round z (Appendix A.1 recovery) to the support
-    S = F1 + {free i : z_i >= 1/2}, solve Eq. upperboundbeta exactly;
+    S = F1 + {free i : z_i >= 1/2}, solve Eq. upperboundbeta exactly;  with
+    round_incumbent=False the incumbent comes from leaves only (the textbook
+    rule, Section 2.2.1), so the answer rests on the search alone;
   * prune when LB_u >= UB (1 - gap) (reading of Section 2.2.1 that makes the
     final (UB - LB)/UB <= gap);
   * branch on the free index with the most fractional z_i, ties to the lowest
@@ -15,7 +17,9 @@ Follows Section 2.2.1 and Algorithm 1 (Section 2.4):
     z_i is integral, branch on the free index of largest |X_i^T r|;  a node
     with no free index is a leaf whose value is its support's box ridge plus
     lambda0 |F1|, so it is closed after its upper bound is taken;
-  * global LB = min LB over the open nodes; stop when N is empty or
+  * global LB = min LB over the open nodes, and never above UB (the
+    incumbent is itself a feasible point, so once every open node's bound
+    exceeds it the optimum is the incumbent); stop when N is empty or
     (UB - LB)/UB <= gap.
 """
 from __future__ import annotations
@@ -52,7 +56,8 @@ def branch_index(z, fix, g):
 
 
 def solve(X, y, lam0, lam2, M, gap=1e-6, K=1, rho=1.0, node_tol=1e-10,
-          max_admm_iter=20000, max_nodes=100000, warm_start=True) -> BnbResult:
+          max_admm_iter=20000, max_nodes=100000, warm_start=True,
+          round_incumbent=True) -> BnbResult:
     X = np.asarray(X, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     n, p = X.shape
@@ -86,10 +91,11 @@ def solve(X, y, lam0, lam2, M, gap=1e-6, K=1, rho=1.0, node_tol=1e-10,
             if lb_u >= UB * (1.0 - gap):
                 continue
             z = relax.z_of_beta(res.beta, fix, lam0, lam2, M)
-            S = np.nonzero((fix == relax.F1) | ((fix == relax.FREE) & (z >= 0.5)))[0]
-            obj, beta_s = ub.support_objective(X, y, S, lam0, lam2, M)
-            if obj < UB:
-                UB, best = obj, beta_s
+            if round_incumbent or not np.any(fix == relax.FREE):
+                S = np.nonzero((fix == relax.F1) | ((fix == relax.FREE) & (z >= 0.5)))[0]
+                obj, beta_s = ub.support_objective(X, y, S, lam0, lam2, M)
+                if obj < UB:
+                    UB, best = obj, beta_s
             if lb_u >= UB * (1.0 - gap):
                 continue
             g = X.T @ res.r
@@ -106,7 +112,7 @@ def solve(X, y, lam0, lam2, M, gap=1e-6, K=1, rho=1.0, node_tol=1e-10,
                     if val == relax.F0:
                         wb[j] = 0.0
                 heapq.heappush(heap, (lb_u, next(counter), child, wb, wv, depth + 1))
-        LB = min((e[0] for e in heap), default=UB)
+        LB = min(min((e[0] for e in heap), default=UB), UB)
         history.append((nodes, UB, LB))
     if not heap:
         LB = UB

@@ -32,6 +32,7 @@ def test_forward_delta_is_objective_change(mfac):
     for j in range(inst.p):
         if j in S or b[j] == 0.0:
             continue
+        assert abs(b[j]) <= M          # the single-coordinate step stays in the box
         nb = beta.copy()
         nb[j] = b[j]
         assert d[j] == pytest.approx(relax.mip_objective(X, y, nb, lam0, lam2) - base, abs=1e-10)

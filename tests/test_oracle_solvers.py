@@ -38,16 +38,20 @@ def test_weak_duality_random_r(mfac):
         assert d <= pval + 1e-12
 
 
-@pytest.mark.parametrize("mfac", [1.5, 0.3])
-def test_admm_matches_second_solver_and_strong_duality(mfac):
+# rho != 1 separates v from v / rho; y -> -y flips every coefficient (psi is even), so
+# the negative side of each closed form is exercised too
+@pytest.mark.parametrize("mfac,rho,ysign", [(1.5, 1.0, 1), (0.3, 1.0, 1), (1.5, 0.35, 1),
+                                            (0.3, 0.35, 1), (1.5, 1.0, -1), (0.3, 0.35, -1)])
+def test_admm_matches_second_solver_and_strong_duality(mfac, rho, ysign):
     inst = _small(2)
     lam0, lam2, M = _params(inst, mfac=mfac)
+    y = ysign * inst.y
     rng = np.random.default_rng(4)
-    data = admm.AdmmData(inst.X, inst.y, 1.0)
+    data = admm.AdmmData(inst.X, y, rho)
     for _ in range(4):
         fix = datagen.random_fixings(inst.p, 1, rng, 4)[0]
         a = admm.solve_node(data, fix, lam0, lam2, M, tol=1e-12, max_iter=200000)
-        b, fb = pgd.solve_node(inst.X, inst.y, fix, lam0, lam2, M)
+        b, fb = pgd.solve_node(inst.X, y, fix, lam0, lam2, M)
         # strong duality at the ADMM optimum (Proposition 1.2, 1.3)
         assert a.primal - a.dual <= 1e-9 * max(1.0, abs(a.primal))
         # two independent algorithms reach the same relaxation value
@@ -90,7 +94,8 @@ def test_box_ridge_matches_library(M):
     inst = _small(7, n=80, p=14, k=5)
     X, y, lam2 = inst.X, inst.y, 0.02
     rng = np.random.default_rng(8)
-    for _ in range(10):
+    for t in range(20):
+        y = inst.y if t % 2 == 0 else -inst.y     # upper and lower bounds binding
         S = np.sort(rng.choice(inst.p, size=int(rng.integers(1, 9)), replace=False))
         b = ub.box_ridge(X, y, S, lam2, M)
         A = np.vstack([X[:, S], np.sqrt(2 * lam2) * np.eye(len(S))])
@@ -106,26 +111,35 @@ def test_box_ridge_matches_library(M):
 # ---------------------------------------------------------------- optimum
 
 
-def test_brute_force_two_features_by_hand():
-    """p = 2: enumerate the four supports by explicit formulas."""
+@pytest.mark.parametrize("lam0", [0.05, 3.0, 30.0])   # the best support has 2, 1 and 0 features
+@pytest.mark.parametrize("M", [100.0, 0.5])           # box loose; box binding
+def test_brute_force_two_features_by_hand(lam0, M):
+    """p = 2: enumerate the four supports by explicit formulas (the normal equations,
+    or a library bound-constrained least squares when the box binds); best and
+    second best."""
     rng = np.random.default_rng(9)
     X = rng.normal(size=(10, 2))
-    y = rng.normal(size=10)
-    lam0, lam2, M = 0.3, 0.05, 100.0
+    y = X @ np.array([1.1, -0.6]) + 0.4 * rng.normal(size=10)
+    lam2 = 0.05
 
     def ridge_val(cols):
         if not cols:
             return 0.5 * y @ y
         A = X[:, cols]
         b = np.linalg.solve(A.T @ A + 2 * lam2 * np.eye(len(cols)), A.T @ y)
+        if np.max(np.abs(b)) > M:
+            Aug = np.vstack([A, np.sqrt(2 * lam2) * np.eye(len(cols))])
+            b = lsq_linear(Aug, np.concatenate([y, np.zeros(len(cols))]), bounds=(-M, M),
+                           tol=1e-15, lsmr_tol=1e-15, max_iter=10000).x
         r = y - A @ b
         return 0.5 * r @ r + lam2 * b @ b + lam0 * len(cols)
 
     vals = {(): ridge_val([]), (0,): ridge_val([0]), (1,): ridge_val([1]), (0, 1): ridge_val([0, 1])}
-    best = min(vals, key=vals.get)
+    order = sorted(vals, key=vals.get)
     res = brute.solve(X, y, lam0, lam2, M)
-    assert res.support == best
-    assert res.objective == pytest.approx(vals[best], rel=1e-12)
+    assert res.support == order[0]
+    assert res.objective == pytest.approx(vals[order[0]], rel=1e-11)
+    assert res.second == pytest.approx(vals[order[1]], rel=1e-11)
 
 
 @pytest.mark.parametrize("frac", [0.5, 0.05, 0.005])
@@ -142,6 +156,52 @@ def test_bnb_matches_brute_force_p16(frac):
     for _, U, L in res.history:
         assert L <= br.objective * (1 + 1e-9) + 1e-12
         assert U >= br.objective * (1 - 1e-12)
+
+
+def _check_bound_inheritance(node_log):
+    """Every solved child carries its parent's bound max(LB_parent, D(r)) (Algorithm 1).
+    The parent is the one solved node that equals the child with one index freed."""
+    seen = {fix.tobytes(): (lbp, d) for fix, lbp, d in node_log}
+    assert len(seen) == len(node_log)
+    for fix, lbp, _ in node_log[1:]:
+        parents = []
+        for j in np.nonzero(fix != relax.FREE)[0]:
+            cand = fix.copy()
+            cand[j] = relax.FREE
+            if cand.tobytes() in seen:
+                parents.append(seen[cand.tobytes()])
+        assert len(parents) == 1
+        plbp, pd = parents[0]
+        assert lbp == max(plbp, pd)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("frac", [0.2, 0.02, 0.002])
+def test_bnb_leaf_incumbents_match_brute_force(seed, frac):
+    """Incumbents taken at leaves only: the optimum is then reached by the search
+    itself (both children of every branch, best-first selection, pruning, the
+    global bound), not by a lucky rounding.  Exact node solves and loose batched
+    ones (Prop. 1.1: every r gives a valid bound) must both find it."""
+    inst = datagen.make_instance(50, 10, 0.5, 3, 3.0, 700 + seed)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    assert br.margin > 1e-9 * br.objective
+    for kw in (dict(K=1), dict(K=3, node_tol=1e-2, max_admm_iter=10)):
+        res = bnb.solve(inst.X, inst.y, lam0, lam2, M, gap=1e-9, round_incumbent=False, **kw)
+        assert res.status == "optimal"
+        assert tuple(np.nonzero(res.beta)[0]) == br.support
+        assert res.ub == pytest.approx(br.objective, rel=1e-10)
+        for _, U, L in res.history:
+            assert L <= br.objective * (1 + 1e-12)
+            assert U >= br.objective * (1 - 1e-12)
+        if kw["K"] == 1:
+            # best-first (Section 2.2.1): children inherit at least their parent's bound,
+            # so the bounds of the nodes taken one at a time never decrease
+            keys = np.array([lbp for _, lbp, _ in res.node_log])
+            assert np.all(keys[1:] >= keys[:-1])
+            _check_bound_inheritance(res.node_log)
 
 
 @pytest.mark.parametrize("K", [1, 4])
