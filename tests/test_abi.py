@@ -78,3 +78,27 @@ def test_options_reject_unknown_fields(lib):
     assert (o.M, o.fused_shape, o.u_shape) == (2.0, 4, 1)
     with pytest.raises(TypeError):
         lib.bnb_options_default(M=1.0, fused_shap=3)
+
+
+def test_footprint_host_arithmetic(lib):
+    """bnb_footprint (used to admit solves under an HBM budget) needs no device: it grows
+    with every dimension, covers at least the resident data and node state, rejects bad
+    sizes, and the largest serving request fits the serving loop's 150 GB budget."""
+    def fp(n, p, **kw):
+        return lib.bnb_footprint(n, p, lib.bnb_options_default(M=1.0, **kw))
+
+    base = fp(1000, 5000, batch_K=512)
+    assert fp(2000, 5000, batch_K=512) > base
+    assert fp(1000, 10000, batch_K=512) > base
+    assert fp(1000, 5000, batch_K=1024) > base
+    assert fp(1000, 5000, batch_K=512, queue_capacity=1 << 22) > fp(1000, 5000, batch_K=512,
+                                                                   queue_capacity=1 << 18)
+    for n, p, K in [(200, 50, 64), (1000, 5000, 512), (5000, 50000, 2048)]:
+        # X in FP32 plus beta and V in FP32 for every slot, at the least
+        assert fp(n, p, batch_K=K) >= 4 * n * p + 8 * K * p
+    serve = dict(batch_K=256, queue_capacity=1 << 18, warm_capacity=1 << 14)
+    assert fp(5000, 20000, **serve) < 150 << 30
+    for n, p in [(0, 10), (10, 0), (-1, 5)]:
+        with pytest.raises(lib.BnbError) as ei:
+            fp(n, p)
+        assert ei.value.code == lib.BNB_EINVAL
