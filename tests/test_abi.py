@@ -102,3 +102,62 @@ def test_footprint_host_arithmetic(lib):
         with pytest.raises(lib.BnbError) as ei:
             fp(n, p)
         assert ei.value.code == lib.BNB_EINVAL
+
+
+def _header_arity():
+    """Parameter count of every function the header declares."""
+    txt = open(os.path.join(ROOT, "include", "bnb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(bnb_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header(lib):
+    """Every ctypes prototype has as many arguments as the header's declaration (a
+    missing or extra argument would shift every pointer after it)."""
+    raw = lib.load_library()
+    arity = _header_arity()
+    assert set(arity) == set(lib.SYMBOLS)
+    for name, count in arity.items():
+        assert len(getattr(raw, name).argtypes) == count, name
+
+
+def test_null_handle_and_bad_sizes_rejected_without_a_device(lib):
+    """Argument errors are reported as BNB_EINVAL before any device work, with a message;
+    the calls that take no status (stream, destroy) accept NULL."""
+    raw = lib.load_library()
+    calls = {
+        "bnb_relax_batch": (None, 4) + (None,) * 3 + (10,) + (None,) * 7,
+        "bnb_relax_batch_device": (None, 4) + (None,) * 3 + (10,) + (None,) * 7,
+        "bnb_dual_bound": (None, 4, None, None, None),
+        "bnb_upper_batch": (None, 4, None, None, None),
+        "bnb_solve": (None, 1e-4) + (None,) * 5,
+        "bnb_solve_start": (None, 1e-4),
+        "bnb_solve_launch": (None, 1),
+        "bnb_solve_poll": (None, None),
+        "bnb_solve_finish": (None,) * 6,
+        "bnb_root_heuristic": (None, None, None),
+        "bnb_profile_round": (None, None, None, 15),
+        "bnb_get_histograms": (None, None, 0, None, 0),
+        "bnb_get_stats": (None, None),
+        "bnb_dual_bound_static": (None, None, 10, 20, 0.1, 0.01, 1.0, 4, None, None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(raw, name)(*args) == lib.BNB_EINVAL, name
+    X, y = np.ones((4, 3)), np.ones(4)
+    o = lib.bnb_options_default(M=1.0)
+    import ctypes
+    h = ctypes.c_void_p()
+    for n, p in [(0, 3), (4, 0), (-2, 3)]:
+        rc = raw.bnb_create(lib._ptr(X), lib._ptr(y), n, p, 0.1, 0.1, ctypes.byref(o), ctypes.byref(h))
+        assert rc == lib.BNB_EINVAL
+        assert b"positive" in raw.bnb_last_error(None)
+    assert raw.bnb_create(None, lib._ptr(y), 4, 3, 0.1, 0.1, ctypes.byref(o), ctypes.byref(h)) \
+        == lib.BNB_EINVAL
+    assert raw.bnb_create_device(None, None, 4, 3, 0.1, 0.1, ctypes.byref(o), ctypes.byref(h)) \
+        == lib.BNB_EINVAL
+    assert raw.bnb_stream(None) is None
+    raw.bnb_destroy(None)
