@@ -129,6 +129,22 @@ MUTANTS = [
      CF, "test_nu_is_conjugate_of_psi", (0.05, 0.01, 3.0)),
     ("z-F1-not-one", relax, "z_of_beta", "z = np.where(fix == F1, 1.0, zf)", "z = zf", 1,
      CF, "test_z_recovery_is_argmin", (0.05, 0.01, 3.0)),
+    ("branch-least-fractional", bnb, "branch_index", "j = int(np.argmax(frac))", "j = int(np.argmin(frac))", 1,
+     SV, "test_branch_index_hand_cases", ()),
+    ("branch-fixed-indices-eligible", bnb, "branch_index", "free = np.nonzero(fix == relax.FREE)[0]",
+     "free = np.arange(len(fix))", 1, SV, "test_branch_index_hand_cases", ()),
+    ("branch-integral-fallback-lowest", bnb, "branch_index", "return int(free[int(np.argmax(np.abs(g[free])))])",
+     "return int(free[0])", 1, SV, "test_branch_index_hand_cases", ()),
+    ("branch-fallback-signed-g", bnb, "branch_index", "np.argmax(np.abs(g[free]))", "np.argmax(g[free])", 1,
+     SV, "test_branch_index_hand_cases", ()),
+    ("mp-selected-not-masked", mp, "matching_pursuit", "d = np.where(in_s, np.inf, d)", "d = d", 1,
+     MP, "test_matching_pursuit_orthonormal_design", ()),
+    ("mp-forward-argmax", mp, "matching_pursuit", "j = int(np.argmin(d))", "j = int(np.argmax(d))", 1,
+     MP, "test_matching_pursuit_orthonormal_design", ()),
+    ("mp-residual-not-updated", mp, "matching_pursuit", "r = r - X[:, j] * b[j]", "r = r", 1,
+     MP, "test_matching_pursuit_ends_at_a_single_move_optimum", ((80, 30, 0.3, 4, 5.0, 5, 0.05),)),
+    ("mp-backward-never-taken", mp, "matching_pursuit", "if db[j] < 0.0:", "if False:", 1,
+     MP, "test_matching_pursuit_ends_at_a_single_move_optimum", ((60, 25, 0.7, 5, 3.0, 934, 0.1),)),
     ("mp-forward-curvature-doubled", mp, "forward_deltas", "+ 0.5 * D * b * b + lam0", "+ D * b * b + lam0", 1,
      MP, "test_forward_delta_is_objective_change", (1.5,)),
     ("mp-forward-step-unclipped", mp, "forward_deltas", "np.clip(c / D, -M, M)", "(c / D)", 1,

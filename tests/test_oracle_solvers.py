@@ -238,6 +238,24 @@ def test_bnb_exact_with_loose_node_solves():
     assert checked >= 1
 
 
+def test_branch_index_hand_cases():
+    """The branching rule on hand-made inputs: the most fractional free z_i
+    (min(z, 1 - z) largest), the lowest index on ties, fixed indices never chosen, and
+    with every free z integral the free index of largest |X_i^T r|; -1 at a leaf."""
+    FR, Z, O = relax.FREE, relax.F0, relax.F1
+    g = np.array([0.1, -3.0, 2.0, 0.5, -0.2])
+    fix = np.array([FR, FR, FR, FR, FR], dtype=np.int8)
+    assert bnb.branch_index(np.array([0.2, 0.9, 0.45, 0.1, 0.0]), fix, g) == 2
+    assert bnb.branch_index(np.array([0.25, 0.75, 0.0, 0.25, 1.0]), fix, g) == 0  # three-way tie
+    fix2 = np.array([Z, FR, O, FR, FR], dtype=np.int8)
+    assert bnb.branch_index(np.array([0.0, 0.8, 0.5, 0.4, 0.1]), fix2, g) == 3
+    g2 = np.array([0.1, 0.2, 2.0, -0.5, -0.9])
+    assert bnb.branch_index(np.array([0.0, 1.0, 1.0, 0.0, 0.0]), fix2, g2) == 4  # |g| = 0.9
+    assert bnb.branch_index(np.array([0.0, 0.0, 1.0, 1.0, 0.0]),
+                            np.array([Z, Z, O, FR, FR], dtype=np.int8), g) == 3
+    assert bnb.branch_index(np.zeros(5), np.array([Z, O, O, Z, Z], dtype=np.int8), g) == -1
+
+
 def test_orthonormal_design_closed_form():
     """X^T X = I: the problem separates per coordinate (a textbook case)."""
     rng = np.random.default_rng(10)
