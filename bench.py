@@ -97,6 +97,16 @@ def parse():
     return ap.parse_args()
 
 
+METRIC = "certified BnB nodes/s"        # both arms report this metric on the same config
+
+
+def line_config(cfg, args):
+    """The `config` object of both arms' JSON lines: the workload, its batch width and
+    target gap, and how the GPU arm keeps inputs out of L2 between timed steps."""
+    return dict(cfg, K=args.K, gap=1e-4, parallelism="replicas",
+                l2="GPU arm: a 256 MiB write flushes L2 before every timed step")
+
+
 def workload(name, inst_id, lam0_frac):
     c = datagen.CONFIGS[name]
     inst = datagen.config_instance(name, inst_id)
@@ -409,10 +419,11 @@ def reference_arm(args):
         secs += dt
     wall = time.perf_counter() - t0
     v = nodes / secs
-    line = {"impl": "reference", "metric": "certified BnB nodes/s", "value": v, "unit": "nodes/s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nodes/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": line_config(cfg, args),
             "cpu_baseline": {"value": v, "unit": "nodes/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": oracle_sample_text(cfg, nodes, secs)},
             "e2e": {"value": v, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -734,13 +745,14 @@ def main():
         cpu = None if args.no_cpu else run_oracle(args, args.cpu_seconds)
         value = nodes / (ms / 1e3)
         line = {
-            "metric": "certified BnB nodes/s (mixed-precision ADMM, FP64 certificates)",
+            "metric": METRIC,
             "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": dict(out["cfg"], K=args.K, check_every=args.check_every, gap=1e-4,
-                           precision=args.precision, rho=args.rho, relax_alpha=args.alpha,
-                           l2="flushed (256 MiB write) before every step", parallelism="replicas"),
+            "config": line_config(out["cfg"], args),
+            "solver": {"arithmetic": "mixed-precision ADMM, FP64 certificates and polish",
+                       "precision": args.precision, "check_every": args.check_every,
+                       "rho": args.rho, "relax_alpha": args.alpha},
             "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
             "roofline": roofline(out, args, pk),
             "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]

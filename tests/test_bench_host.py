@@ -79,3 +79,32 @@ def test_traffic_dropped_when_the_kernel_source_changes(bench, tmp_path, monkeyp
     (csrc / f).write_text(text[:i] + start + " /* edited */" + text[i + len(start):])
     r = bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1390.1})
     assert r["traffic"] is None
+
+
+def test_reference_arm_line(bench, monkeypatch, capsys):
+    """The reference arm (the oracle on the host cores) prints one contract line with the
+    GPU arm's metric, unit and config; ranks other than 0 print nothing."""
+    import json
+    calls = []
+    monkeypatch.setattr(bench, "oracle_setup", lambda *a, **k: "state")
+    monkeypatch.setattr(bench, "oracle_nodes", lambda st, sec: calls.append(sec) or (3, 0.5))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"])
+    args = bench.parse()
+    monkeypatch.setenv("RANK", "1")
+    bench.reference_arm(args)
+    assert capsys.readouterr().out == "" and not calls
+    monkeypatch.setenv("RANK", "0")
+    bench.reference_arm(args)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert len(calls) == 5
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "nodes/s" and line["higher_is_better"] is True
+    assert line["value"] == pytest.approx(3 * 2 / (0.5 * 2))
+    _, _, _, _, cfg = bench.workload(args.workload, 0, args.lam0_frac)
+    assert line["config"] == bench.line_config(cfg, args)
+    assert line["config"]["workload"] == "c2" and line["config"]["K"] == 512
+    for key in ("n_gpus", "steps", "warmup", "ms_per_step", "scaling", "vs_baseline", "dtype", "data"):
+        assert key in line
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "nodes/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
