@@ -717,6 +717,33 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def mine_line(args, out, world, ms, nodes, pk, cpu):
+    """The GPU arm's JSON line from run_mine's record, the max-over-ranks time `ms` of the
+    timed rounds and the nodes all ranks certified in them."""
+    return {
+        "metric": METRIC,
+        "value": nodes / (ms / 1e3), "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": line_config(out["cfg"], args),
+        "solver": {"arithmetic": "mixed-precision ADMM, FP64 certificates and polish",
+                   "precision": args.precision, "check_every": args.check_every,
+                   "rho": args.rho, "relax_alpha": args.alpha},
+        "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
+        "roofline": roofline(out, args, pk),
+        "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]
+                          / max(1e-12, out["fp64"]["value"])),
+        "prime": out["prime"],
+        "autotune": out["tune"],
+        "cpu_baseline": cpu,
+        "solve_progress": {"nodes": out["after"]["nodes"], "ub": out["after"]["ub"],
+                           "lb": out["after"]["lb"], "open_nodes": out["after"]["open_nodes"],
+                           "done": out["after"]["done"]},
+        "stages_ms": {k: v[0] for k, v in out["prof"].items()},
+        "kernel_shapes": out["shapes"],
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -741,31 +768,8 @@ def main():
     out = run_mine(args, rank, world)
     ms, nodes = combine_ranks(out["ms"], out["nodes"], world)
     if rank == 0:
-        pk = peaks()
         cpu = None if args.no_cpu else run_oracle(args, args.cpu_seconds)
-        value = nodes / (ms / 1e3)
-        line = {
-            "metric": METRIC,
-            "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": line_config(out["cfg"], args),
-            "solver": {"arithmetic": "mixed-precision ADMM, FP64 certificates and polish",
-                       "precision": args.precision, "check_every": args.check_every,
-                       "rho": args.rho, "relax_alpha": args.alpha},
-            "e2e": out["e2e"], "gpu_launches": out["kernels"], "clocks": out["clocks"],
-            "roofline": roofline(out, args, pk),
-            "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]
-                              / max(1e-12, out["fp64"]["value"])),
-            "prime": out["prime"],
-            "autotune": out["tune"],
-            "cpu_baseline": cpu,
-            "solve_progress": {"nodes": out["after"]["nodes"], "ub": out["after"]["ub"],
-                               "lb": out["after"]["lb"], "open_nodes": out["after"]["open_nodes"],
-                               "done": out["after"]["done"]},
-            "stages_ms": {k: v[0] for k, v in out["prof"].items()},
-            "kernel_shapes": out["shapes"],
-        }
+        line = mine_line(args, out, world, ms, nodes, peaks(), cpu)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

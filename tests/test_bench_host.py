@@ -108,3 +108,43 @@ def test_reference_arm_line(bench, monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "nodes/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_gpu_arm_line_has_the_contract_keys(bench, monkeypatch):
+    """The GPU arm's line, built from a record shaped like the one the timed run returns:
+    every contract key, the same metric and config as the reference arm, value = nodes
+    certified over the timed seconds."""
+    import json
+    key = next(iter(bench.TRAFFIC))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--steps", "80", "--warmup", "3"])
+    args = bench.parse()
+    args.rho, args.alpha = 0.2, 1.6                  # as the autotuner sets them
+    _, _, _, _, cfg = bench.workload(args.workload, 0, args.lam0_frac)
+    out = _out((key[0], args.workload, args.K, args.precision) + key[4:])
+    out["cfg"] = cfg
+    out.update(
+        kernels=40 * 80, tune={"rho": 0.2, "relax_alpha": 1.6},
+        clocks={"sm_mhz": 2032, "sm_max_mhz": 2032, "reasons": [], "samples": 50},
+        e2e={"value": 28000.0, "unit": "nodes/s", "h2d_bytes_per_step": 23 << 20,
+             "d2h_bytes_per_step": 20 << 20, "call": "bnb_relax_batch (host buffers)"},
+        fp64={"value": 300.0, "unit": "nodes/s", "mixed_same_batch": {"nodes_per_s": 36000.0},
+              "fp64": {"nodes_per_s": 300.0}, "bound_error": {"max_rel": 3e-5}},
+        prime={"rounds": 200, "seconds": 2.0, "active_slots": 500, "open_nodes": 9000},
+        after={"nodes": 50000, "ub": 1.0, "lb": 0.99, "open_nodes": 20000, "done": 0},
+        shapes={"fused_tile_width": key[4], "fused_clusters": 0, "fused_pairs": 74,
+                "fused_transposed": 0, "xw_tile_width": 128, "xw_cluster": 4, "u_split": 0})
+    cpu = {"value": 3.0, "unit": "nodes/s", "cores": 16, "kind": "oracle", "sample": "s"}
+    line = json.loads(json.dumps(bench.mine_line(args, out, 1, 64.0, 2688, {"bf16_tflops_sustained": 1390.1},
+                                                 cpu)))
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "clocks",
+              "roofline", "cpu_baseline"):
+        assert k in line, k
+    assert line["metric"] == bench.METRIC and line["unit"] == "nodes/s"
+    assert line["config"] == bench.line_config(cfg, args)
+    assert line["value"] == pytest.approx(2688 / 0.064)
+    assert line["ms_per_step"] == pytest.approx(64.0 / 80)
+    assert set(line["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert line["fp64_path"]["ratio_same_batch"] == pytest.approx(120.0)
+    assert line["solver"]["rho"] == 0.2
