@@ -19,11 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-def main():
-    import torch
-    import datagen
-    import paper_2602_04551_b300 as bnb
-
+def parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c4")
     ap.add_argument("--lam0-frac", type=float, default=0.02)
@@ -36,7 +32,15 @@ def main():
     ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-graphs", action="store_true")
-    a = ap.parse_args()
+    return ap
+
+
+def main():
+    import torch
+    import datagen
+    import paper_2602_04551_b300 as bnb
+
+    a = parser().parse_args()
     c = datagen.CONFIGS[a.workload]
     inst = datagen.config_instance(a.workload, 0)
     M = datagen.big_m(inst.X, inst.y, inst.support_true, c["lam2"])
