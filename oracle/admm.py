@@ -9,6 +9,12 @@ The dual candidate is r = y - X b (text after Proposition 1).  D is formed
 directly (no Woodbury) so that the oracle does not share the CUDA path's
 rewrite of the b-update.
 
+Over-relaxation (not in the paper; an option of the engine, from Boyd, Parikh,
+Chu, Peleato and Eckstein, "Distributed Optimization and Statistical Learning
+via the Alternating Direction Method of Multipliers", 2011, Section 3.4.3): with
+alpha != 1 the beta- and v-updates use bh = alpha b + (1 - alpha) beta_prev in
+place of b.  alpha = 1 is the paper's iteration.
+
 Node stop rule (Section 5.1 "BnB Settings"): relative primal-dual gap
 (P(beta) - D(r)) / max(1, |P(beta)|) <= tol, P from Eq. relaxnode2 at the
 feasible beta and D from Eq. dual (the best D seen so far is kept: every r
@@ -49,18 +55,19 @@ class AdmmData:
         self.D = np.linalg.inv(self.X.T @ self.X + self.rho * np.eye(p))
 
 
-def admm_iteration(data: AdmmData, beta, v, fix, lam0, lam2, M):
-    """One pass of Eq. admm-update; returns (b, beta_new, v_new)."""
+def admm_iteration(data: AdmmData, beta, v, fix, lam0, lam2, M, alpha=1.0):
+    """One pass of Eq. admm-update (over-relaxed when alpha != 1); returns (b, beta_new, v_new)."""
     rho = data.rho
     b = data.D @ (data.c + rho * beta - v)
-    bt = b + v / rho
+    bh = b if alpha == 1.0 else alpha * b + (1.0 - alpha) * beta
+    bt = bh + v / rho
     beta_new = relax.prox(bt, fix, lam0, lam2, M, rho)
-    v_new = v + rho * (b - beta_new)
+    v_new = v + rho * (bh - beta_new)
     return b, beta_new, v_new
 
 
 def solve_node(data: AdmmData, fix, lam0, lam2, M, beta0=None, v0=None,
-               tol=1e-10, max_iter=20000, check_every=10) -> AdmmResult:
+               tol=1e-10, max_iter=20000, check_every=10, alpha=1.0) -> AdmmResult:
     X, y = data.X, data.y
     p = X.shape[1]
     fix = np.asarray(fix)
@@ -72,7 +79,7 @@ def solve_node(data: AdmmData, fix, lam0, lam2, M, beta0=None, v0=None,
     best_r = y.copy()
     it = 0
     while it < max_iter:
-        b, beta, v = admm_iteration(data, beta, v, fix, lam0, lam2, M)
+        b, beta, v = admm_iteration(data, beta, v, fix, lam0, lam2, M, alpha)
         it += 1
         if it % check_every == 0 or it == max_iter:
             r = y - X @ b

@@ -76,17 +76,20 @@ MUTANTS = [
     ("primal-psi-dropped", relax, "primal_value",
      " + float(np.sum(psi(beta, fix, lam0, lam2, M)))", "", 1,
      SV, "test_admm_matches_second_solver_and_strong_duality", (1.5, 1.0, 1)),
-    ("admm-dual-update-sign", admm, "admm_iteration", "v + rho * (b - beta_new)",
-     "v - rho * (b - beta_new)", 1, SV, "test_admm_matches_second_solver_and_strong_duality",
+    ("admm-dual-update-sign", admm, "admm_iteration", "v + rho * (bh - beta_new)",
+     "v - rho * (bh - beta_new)", 1, SV, "test_admm_matches_second_solver_and_strong_duality",
      (1.5, 1.0, 1)),
     ("admm-b-update-without-v", admm, "admm_iteration", "data.c + rho * beta - v",
      "data.c + rho * beta", 1, SV, "test_admm_matches_second_solver_and_strong_duality",
      (1.5, 1.0, 1)),
-    ("admm-scaled-dual-unscaled", admm, "admm_iteration", "bt = b + v / rho", "bt = b + v", 1,
+    ("admm-scaled-dual-unscaled", admm, "admm_iteration", "bt = bh + v / rho", "bt = bh + v", 1,
      SV, "test_admm_matches_second_solver_and_strong_duality", (1.5, 0.35, 1)),
     ("admm-D-without-rho", admm.AdmmData, "__init__", "self.X.T @ self.X + self.rho * np.eye(p)",
      "self.X.T @ self.X + np.eye(p)", 1, SV, "test_admm_matches_second_solver_and_strong_duality",
      (1.5, 0.35, 1)),
+    ("admm-over-relaxation-weights-swapped", admm, "admm_iteration",
+     "alpha * b + (1.0 - alpha) * beta", "alpha * beta + (1.0 - alpha) * b", 1,
+     SV, "test_over_relaxed_admm_reaches_the_same_optimum", (1.5, 1)),
     ("pgd-prox-at-unit-step", pgd, "solve_node", "relax.prox(yk - g / L, fix, lam0, lam2, M, L)",
      "relax.prox(yk - g / L, fix, lam0, lam2, M, 1.0)", 1,
      SV, "test_admm_matches_second_solver_and_strong_duality", (1.5, 1.0, 1)),

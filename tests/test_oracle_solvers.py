@@ -60,6 +60,29 @@ def test_admm_matches_second_solver_and_strong_duality(mfac, rho, ysign):
         assert a.dual <= fb + 1e-10
 
 
+@pytest.mark.parametrize("mfac,ysign", [(1.5, 1), (0.3, -1)])
+def test_over_relaxed_admm_reaches_the_same_optimum(mfac, ysign):
+    """Over-relaxation (alpha = 1.6) changes the iterates, not the fixed point: strong
+    duality at convergence and agreement with the independent second solver; and one
+    over-relaxed step differs from the plain one (the option is not a no-op)."""
+    inst = _small(2)
+    lam0, lam2, M = _params(inst, mfac=mfac)
+    y = ysign * inst.y
+    rng = np.random.default_rng(14)
+    data = admm.AdmmData(inst.X, y, 0.35)
+    for _ in range(3):
+        fix = datagen.random_fixings(inst.p, 1, rng, 4)[0]
+        a = admm.solve_node(data, fix, lam0, lam2, M, tol=1e-12, max_iter=200000, alpha=1.6)
+        _, fb = pgd.solve_node(inst.X, y, fix, lam0, lam2, M)
+        assert a.primal - a.dual <= 1e-9 * max(1.0, abs(a.primal))
+        assert a.primal == pytest.approx(fb, rel=1e-9, abs=1e-10)
+    beta0 = rng.uniform(-M, M, inst.p) * (fix != relax.F0)
+    v0 = rng.normal(size=inst.p)
+    _, b1, v1 = admm.admm_iteration(data, beta0, v0, fix, lam0, lam2, M)
+    _, b2, v2 = admm.admm_iteration(data, beta0, v0, fix, lam0, lam2, M, alpha=1.6)
+    assert np.max(np.abs(v1 - v2)) > 1e-6
+
+
 def test_woodbury_reading():
     """b-update inverse: (1/rho)(I - X^T (X X^T + rho I)^{-1} X) is the inverse of
     X^T X + rho I; the printed coefficient 1/rho^2 on the second term is not."""
