@@ -1,4 +1,4 @@
-"""Profiling driver: a solve primed to steady state, then a few rounds, for ncu.
+"""Profiling harness: a solve primed to steady state, then a few rounds, for ncu.
 
     python -m paper_2602_04551_b300.profile_case --workload c4 --rounds 3
 
