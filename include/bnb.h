@@ -210,7 +210,9 @@ int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, double* ub, do
  * continuous slot refill, best-first selection, branching on the most
  * fractional z_i, pruning when LB >= UB (1 - rel_gap)).
  *   beta_out   p FP64 incumbent (host, may be NULL)
- *   ub, lb     final global bounds
+ *   ub, lb     final global bounds: lb is the smallest certified bound over the open
+ *              nodes, never above ub (the incumbent is feasible), and equals ub once
+ *              the tree is closed
  *   nodes      nodes solved
  *   status     BNB_STATUS_*
  */
