@@ -9,8 +9,9 @@ constant-correlation one):
   * rows of X are iid N(0, Sigma) with Sigma_ij = rho^|i-j|, drawn exactly as an
     AR(1) recursion along the feature index:
         x_0 = e_0,  x_j = rho * x_{j-1} + sqrt(1 - rho^2) * e_j ;
-  * every column is scaled to unit l2 norm, then X is rounded to FP32 once;
-    that FP32-representable X (held in float64 arrays) is the problem data;
+  * the draws are staged in float32, every column is scaled to unit l2 norm
+    (norms taken from the float64 draws) and the scaled matrix is rounded to
+    FP32; that FP32-representable X (held in float64 arrays) is the problem data;
   * beta_true has k entries equal to 1.0 at indices floor(j * p / k);
   * y = X beta_true + eps, eps ~ N(0, sigma^2 I), sigma^2 = Var(X beta_true)/SNR
     (sample variance of the noiseless response);

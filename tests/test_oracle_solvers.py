@@ -350,3 +350,21 @@ def test_datagen_toeplitz_recipe():
     for lag in range(1, 4):
         assert np.mean(np.diag(C, lag)) == pytest.approx(0.6 ** lag, abs=0.04)
     assert list(datagen.true_support(50, 5)) == [0, 10, 20, 30, 40]
+
+
+def test_datagen_noise_and_seeds():
+    """y = X beta_true + eps with sigma^2 = Var(X beta_true) / SNR (sample variance of the
+    noiseless response, Section 5.1), beta_true ones on the evenly spaced support, and the
+    seed rule 1000 * config + instance."""
+    inst = datagen.make_instance(4000, 20, 0.3, 4, 5.0, 77)
+    mu = inst.X @ inst.beta_true
+    assert list(np.nonzero(inst.beta_true)[0]) == [0, 5, 10, 15]
+    assert np.all(inst.beta_true[inst.support_true] == 1.0)
+    assert inst.sigma2 == pytest.approx(np.var(mu) / 5.0, rel=1e-12)
+    assert np.var(inst.y - mu) / inst.sigma2 == pytest.approx(1.0, abs=0.1)
+    assert abs(np.mean(inst.y - mu)) < 4 * np.sqrt(inst.sigma2 / 4000)
+    again = datagen.make_instance(4000, 20, 0.3, 4, 5.0, 77)
+    np.testing.assert_array_equal(inst.X, again.X)
+    np.testing.assert_array_equal(inst.y, again.y)
+    assert datagen.config_instance("c1", 3).seed == 1003
+    assert datagen.config_instance("c2_small", 0).seed == 2000
