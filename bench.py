@@ -256,6 +256,7 @@ def run_mine(args, rank, world):
                                           "fused_clusters", "fused_pairs", "fused_transposed",
                                           "u_split")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
+               setup_seconds=stats.get("setup_seconds"),
                kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
                       "active_slots": before["active_slots"], "open_nodes": before["open_nodes"]})
@@ -571,6 +572,7 @@ def run_solves(args):
             st = bnb.bnb_get_stats(h)
             dh, sh = bnb.bnb_get_histograms(h, args.max_depth + 1, 202)
         rec = {"lambda0_frac": frac, "seed": seed, "lambda0": lam0, "seconds": dt,
+               "setup_seconds": st.get("setup_seconds"),
                "status": res["status"], "nodes": res["nodes"],
                "nnz": int(np.count_nonzero(res["beta"])), "ub": res["ub"], "lb": res["lb"],
                "gap": (res["ub"] - res["lb"]) / res["ub"], "nodes_per_s": res["nodes"] / dt,
@@ -734,6 +736,7 @@ def mine_line(args, out, world, ms, nodes, pk, cpu):
         "fp64_path": dict(out["fp64"], ratio_same_batch=out["fp64"]["mixed_same_batch"]["nodes_per_s"]
                           / max(1e-12, out["fp64"]["value"])),
         "prime": out["prime"],
+        "setup_seconds": out.get("setup_seconds"),    # per-tree setup (R0), outside the timed rounds
         "autotune": out["tune"],
         "cpu_baseline": cpu,
         "solve_progress": {"nodes": out["after"]["nodes"], "ub": out["after"]["ub"],

@@ -148,3 +148,6 @@ def test_gpu_arm_line_has_the_contract_keys(bench, monkeypatch):
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert line["fp64_path"]["ratio_same_batch"] == pytest.approx(120.0)
     assert line["solver"]["rho"] == 0.2
+    assert line["setup_seconds"] is None             # absent from the fake record
+    out["setup_seconds"] = 0.9
+    assert bench.mine_line(args, out, 1, 64.0, 2688, {}, cpu)["setup_seconds"] == 0.9
