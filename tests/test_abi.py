@@ -161,3 +161,38 @@ def test_null_handle_and_bad_sizes_rejected_without_a_device(lib):
         == lib.BNB_EINVAL
     assert raw.bnb_stream(None) is None
     raw.bnb_destroy(None)
+
+
+def test_plain_c_program_links_and_calls_the_library(lib, tmp_path):
+    """The boundary is a C ABI: a C program that includes only bnb.h links against
+    libbnb.so and calls the entry points that need no device."""
+    src = r'''
+#include <stdio.h>
+#include <string.h>
+#include "bnb.h"
+int main(void) {
+  bnb_options o;
+  if (bnb_options_default(&o) != 0) return 1;
+  size_t bytes = 0;
+  if (bnb_footprint(1000, 5000, &o, &bytes) != 0 || bytes == 0) return 2;
+  if (bnb_footprint(0, 5000, &o, &bytes) != BNB_EINVAL) return 3;
+  double X[6] = {1, 2, 3, 4, 5, 6}, y[3] = {1, 2, 3};
+  bnb_handle* h = NULL;
+  if (bnb_create(X, y, 0, 2, 0.1, 0.1, &o, &h) != BNB_EINVAL || h != NULL) return 4;
+  if (strstr(bnb_last_error(NULL), "positive") == NULL) return 5;
+  if (bnb_solve_launch(NULL, 1) != BNB_EINVAL) return 6;
+  bnb_destroy(NULL);
+  printf("ok %zu\n", bytes);
+  return 0;
+}
+'''
+    c = tmp_path / "abi.c"
+    c.write_text(src)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib.LIB_PATH)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c),
+                    "-L", libdir, "-lbnb", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.startswith("ok ")
