@@ -105,7 +105,9 @@ def test_reference_arm_line(bench, monkeypatch, capsys):
     assert line["config"]["workload"] == "c2" and line["config"]["K"] == 512
     for key in ("n_gpus", "steps", "warmup", "ms_per_step", "scaling", "vs_baseline", "dtype", "data"):
         assert key in line
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert 1 <= line["cpu_baseline"]["cores"] <= os.cpu_count()
+    assert line["cpu_baseline"]["cores"] == bench.oracle_threads()
     assert line["e2e"] == {"value": line["value"], "unit": "nodes/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
