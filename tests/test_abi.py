@@ -196,3 +196,34 @@ int main(void) {
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
     assert out.stdout.startswith("ok ")
+
+
+def _header_defines():
+    txt = open(os.path.join(ROOT, "include", "bnb.h")).read()
+    return {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"^#define (BNB_[A-Z0-9_]+) \(?(-?\d+)\)?", txt, flags=re.M)}
+
+
+def test_constants_match_header(lib):
+    """Error codes and precisions have the header's values in the binding; every status
+    code the header defines has a name (BNB_STATUS_X -> "x")."""
+    defs = _header_defines()
+    assert len(defs) == 18        # OK, six error codes, five precisions, six statuses
+    for name, value in defs.items():
+        if name.startswith("BNB_STATUS_"):
+            assert lib.STATUS_NAMES[value] == name[len("BNB_STATUS_"):].lower(), name
+        else:
+            assert getattr(lib, name) == value, name
+
+
+def test_documented_defaults(lib):
+    """bnb_options_default sets the defaults the header documents."""
+    o = lib.bnb_options_default()
+    want = dict(M=0.0, rho=1.0, node_tol=1e-4, max_admm_iter=400, check_every=10, batch_K=512,
+                precision=lib.BNB_PREC_TC3, use_graphs=1, time_limit_s=3600.0, max_nodes=10**9,
+                queue_capacity=1 << 20, warm_capacity=0, support_max=200, ub_max_iter=200, device=0,
+                stream=None, relax_alpha=1.0, root_heuristic=1, max_depth=256, lockstep=0,
+                mv_crossover=-1, fused_shape=0, u_shape=0)
+    assert {k for k, _ in o._fields_} == set(want)
+    for k, v in want.items():
+        assert getattr(o, k) == v, k
