@@ -1,7 +1,8 @@
 """The profile summaries stay reproducible: each gives the command that made it, the
 command runs committed files with arguments their current parsers accept, the ncu
 capture re-runs exactly the plain command that exited 0 before it, and every ncu call
-leaves the clocks alone (--clock-control none)."""
+leaves the clocks alone (--clock-control none).  The README's example commands parse
+the same way."""
 import glob
 import importlib.util
 import os
@@ -53,3 +54,30 @@ def test_profile_command_is_reproducible(path, monkeypatch):
             assert os.path.exists(os.path.join(ROOT, tok[1]))
             a = _bench_parse(tok[2:], monkeypatch)
         assert a.workload in datagen.CONFIGS
+
+
+def test_readme_commands_parse(monkeypatch):
+    """The commands the README shows run committed entry points with accepted arguments."""
+    lines = []
+    cont = ""
+    for raw in open(os.path.join(ROOT, "README.md")):
+        line = raw.split("#")[0].rstrip()
+        if cont:
+            line = cont + " " + line.strip()
+            cont = ""
+        if line.endswith("\\"):
+            cont = line[:-1].strip()
+            continue
+        if line.strip().startswith("python "):
+            lines.append(line.strip())
+    assert any("bench.py" in l for l in lines)
+    for cmd in lines:
+        tok = shlex.split(cmd)
+        if tok[:2] == ["python", "bench.py"]:
+            _bench_parse(tok[2:], monkeypatch)
+        elif tok[:3] == ["python", "-m", "pytest"]:
+            assert os.path.isdir(os.path.join(ROOT, tok[3]))
+        else:
+            assert tok[:2] == ["python", "-m"], tok
+            mod = tok[2].replace(".", os.sep)
+            assert os.path.exists(os.path.join(ROOT, mod + ".py")), tok[2]
