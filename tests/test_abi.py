@@ -227,3 +227,39 @@ def test_documented_defaults(lib):
     assert {k for k, _ in o._fields_} == set(want)
     for k, v in want.items():
         assert getattr(o, k) == v, k
+
+
+def test_option_validation_on_the_host(lib):
+    """Every option rule of bnb_create is checked on the host before any device work:
+    each bad value returns BNB_EINVAL with its message, and a valid set reaches the
+    device check (BNB_ENODEV here).  The data pointers are placeholders that the library
+    never dereferences before that check, so the test runs only without a device."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("device present: the placeholder pointers would reach the device")
+    raw = lib.load_library()
+    ph = ctypes.c_void_p(4096)          # placeholder device pointers, never dereferenced
+    h = ctypes.c_void_p()
+
+    def create(lam0=0.1, lam2=0.01, **kw):
+        o = lib.bnb_options_default(**dict(dict(M=1.0), **kw))
+        rc = raw.bnb_create_device(ph, ph, 100, 50, lam0, lam2, ctypes.byref(o), ctypes.byref(h))
+        return rc, raw.bnb_last_error(None).decode()
+
+    assert create()[0] == lib.BNB_ENODEV
+    bad = [
+        (dict(lam0=-1.0), "lambda0"), (dict(lam2=0.0), "lambda2"), (dict(M=0.0), "options.M"),
+        (dict(rho=0.0), "rho"), (dict(batch_K=0), "batch_K"), (dict(batch_K=70000), "batch_K"),
+        (dict(support_max=0), "support_max"), (dict(support_max=300), "support_max"),
+        (dict(check_every=0), "check_every"), (dict(max_depth=4), "max_depth"),
+        (dict(max_depth=5000), "max_depth"), (dict(mv_crossover=-2), "mv_crossover"),
+        (dict(mv_crossover=33), "mv_crossover"), (dict(fused_shape=5), "fused_shape"),
+        (dict(u_shape=3), "u_shape"), (dict(relax_alpha=0.5), "relax_alpha"),
+        (dict(relax_alpha=2.0), "relax_alpha"), (dict(queue_capacity=10), "queue_capacity"),
+        (dict(queue_capacity=(1 << 30) + 1), "queue_capacity"), (dict(precision=7), "precision"),
+    ]
+    for kw, word in bad:
+        rc, msg = create(**kw)
+        assert rc == lib.BNB_EINVAL and word in msg, (kw, rc, msg)
+        assert h.value is None
