@@ -263,3 +263,26 @@ def test_option_validation_on_the_host(lib):
         rc, msg = create(**kw)
         assert rc == lib.BNB_EINVAL and word in msg, (kw, rc, msg)
         assert h.value is None
+
+
+def test_static_dual_bound_argument_checks_on_the_host(lib):
+    """bnb_dual_bound_static rejects bad sizes, parameters and requests beyond its fixed
+    scratch before any device work (placeholder pointers, never dereferenced)."""
+    import ctypes
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("device present: covered by the GPU no-allocation tests")
+    raw = lib.load_library()
+    ph = ctypes.c_void_p(4096)
+    f = raw.bnb_dual_bound_static
+    ok = dict(n=100, p=50, lam0=0.1, lam2=0.01, M=1.0, K=4)
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        return f(ph, ph, a["n"], a["p"], a["lam0"], a["lam2"], a["M"], a["K"], ph, ph, ph, None)
+
+    for kw in (dict(n=0), dict(p=-1), dict(K=0), dict(lam0=-0.1), dict(lam2=0.0), dict(M=0.0),
+               dict(K=70000), dict(p=50000, K=6000)):  # grid limit; 6000 x 198 doubles > 2^20
+        assert call(**kw) == lib.BNB_EINVAL, kw
+    assert f(None, ph, 100, 50, 0.1, 0.01, 1.0, 4, ph, ph, ph, None) == lib.BNB_EINVAL
+    assert call(p=50000, K=5000) == lib.BNB_ENODEV   # 5000 x 198 doubles fit: reaches the device
