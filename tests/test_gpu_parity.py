@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import datagen
-from oracle import relax, admm, pgd, ub as oub, bnb as obnb, brute
+from oracle import relax, admm, pgd, ub as oub, brute
 
 pytestmark = pytest.mark.gpu
 
