@@ -3,7 +3,6 @@ whose mean certified bound is weaker than the best by more than the tolerance ar
 chosen for speed, the fastest of the rest is, the narrow-form crossover is the largest
 width at which it wins, and results are cached per (n, p) bucket and grid."""
 import numpy as np
-import pytest
 
 from paper_2602_04551_b300 import autotune
 
