@@ -56,6 +56,9 @@ extern "C" {
 #define BNB_STATUS_NODE_LIMIT 4
 #define BNB_STATUS_DEPTH_LIMIT 5  /* a node deeper than options.max_depth was needed; its
                                      bound stays in LB, so LB remains valid */
+#define BNB_STATUS_SUPPORT_LIMIT 6 /* a leaf (no free index) whose support has more than
+                                      options.support_max elements could not be evaluated;
+                                      its bound stays in LB, so LB remains valid */
 
 typedef struct bnb_handle bnb_handle;
 
@@ -105,6 +108,10 @@ typedef struct {
                             chunks whose partial products a second kernel adds in order
                             (BNB_PREC_TC3 and BNB_PREC_BF16 only; needs at least two chunks
                             per tile to fill the GPU).  Otherwise as fused_shape. */
+  int ub_polish;         /* bnb_upper_batch: 1 (default) re-solves each support exactly in FP64
+                            after the projected-gradient method; 0 returns the projected-
+                            gradient solution itself (ADMM precision, upcast) with its FP64
+                            objective.  bnb_solve always polishes its candidate incumbents. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */
@@ -183,11 +190,14 @@ int bnb_dual_bound(bnb_handle* h, int K, const int8_t* fix, const double* r, dou
  * Scratch: a fixed 8 MiB device array inside the library (every GPU that loads the
  * library keeps it until the process exits); a call needs K * (ceil(p/256) + 2)
  * doubles of it and returns BNB_EINVAL beyond 2^20 doubles (or K > 65535).
- * The first call on a device looks up the array's device address once (with that
- * device current); make that first call before any stream capture.  All calls on
- * a device share the array: calls whose kernels overlap on the GPU race on it, so
- * order them (one stream, or events).  No cudaMalloc, cudaFree or other
- * allocating call is made.
+ * The first call on a device (and in each further context a caller makes current
+ * on it) looks up the array's device address once, with that device current; make
+ * that first call before any stream capture.  The CUDA runtime loads the array's
+ * module lazily, so that first call is also when the 8 MiB are reserved on the
+ * device: it can synchronise the device and can fail with BNB_ECUDA when no memory
+ * is left; later calls only launch two kernels.  All calls on a device share the
+ * array: calls whose kernels overlap on the GPU race on it, so order them (one
+ * stream, or events).  No cudaMalloc, cudaFree or other allocating call is made.
  */
 int bnb_dual_bound_static(const double* dX, const double* dy, int n, int p, double lambda0,
                           double lambda2, double M, int K, const int8_t* dfix, const double* dr,
@@ -196,9 +206,10 @@ int bnb_dual_bound_static(const double* dX, const double* dy, int n, int p, doub
 /*
  * Batched upper bound (Sections 3.3-3.4, Eq. upperboundbeta): for each of K
  * supports (K x p uint8 mask, host), projected gradient with t/(t+3)
- * extrapolation and Armijo backtracking in the ADMM precision, then an FP64
- * re-solve of the box ridge on the support (exact active set).  Returns
- *   ub[k]        FP64 objective of Eq. original at the FP64 solution (lambda0
+ * extrapolation and Armijo backtracking in the ADMM precision, then (unless
+ * options.ub_polish is 0) an FP64 re-solve of the box ridge on the support
+ * (exact active set).  Returns
+ *   ub[k]        FP64 objective of Eq. original at the returned solution (lambda0
  *                counted once per nonzero)
  *   beta_out     K x p FP64 solutions (or NULL)
  * Supports larger than opt.support_max return ub = +inf.
@@ -272,41 +283,6 @@ void* bnb_stream(const bnb_handle* h);
  * its FP32 screen and its exact FP64 part (15 stages).
  */
 int bnb_profile_round(bnb_handle* h, double* stage_ms, int* stage_launches, int nstages);
-
-/*
- * Diagnostics: the tcgen05 tensor-core contraction on its own.  C = A B^T with
- * A (M x Kd) and B (N x Kd) given K-major in FP64 device memory (element (m, k)
- * at A[k + m*Kd]), split into BF16 operands (nsplit 1: hi; 2: A hi, B a hi/lo pair,
- * two products; 3: hi/lo pairs, three products), tile width bn (128 or 256), `splits`
- * split-K chunks summed
- * in order; C is M x N column-major FP32 (device).  *err_out (host) receives the
- * kernel's pipeline error word (0 when every bounded wait completed).
- */
-int bnb_tc_gemm_check(const double* dA, const double* dB, int M, int N, int Kd, int nsplit, int bn,
-                      int splits, float* dC, int* err_out);
-
-/* Diagnostics: the same product through the cluster-reduced tcgen05 kernel that the
- * ADMM iteration uses for X W'^T and G^-1 T (128 x 256 tiles; the K range split over
- * `cluster` CTAs of one thread-block cluster, 1 <= cluster <= 8, whose partial tiles
- * are summed in rank order through distributed shared memory).  Arguments as for
- * bnb_tc_gemm_check; C (device, M x N column-major FP32) is written directly.
- * Returns BNB_EINVAL for bad sizes or a cluster size the device cannot co-schedule.
- * The paper has no counterpart: this checks a B300-specific kernel in isolation. */
-int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
-                              int nsplit, int cluster, float* dC, int* err_out);
-
-/* Diagnostics: the same product through the CTA-pair tcgen05 kernel (cta_group::2) that
- * the ADMM iteration can use for X^T U' with the roles exchanged: 256 x bn tiles
- * (bn = 128, 144 or 256), each computed by two CTAs on two SMs, the first holding rows
- * [0, 128) of the tile and B rows [0, bn/2), the second the rest.  nsplit: 1 (BF16),
- * 2 (A as a hi/lo pair, B one BF16 term: the iterate is A in that use) or 3 (both
- * pairs).  Arguments otherwise as for bnb_tc_gemm_check; C (device, M x N column-major
- * FP32) is written directly; M <= 16384.  Returns BNB_EINVAL for bad sizes or when the
- * device cannot co-schedule a pair; err_out receives the kernel's error word (0 when
- * every bounded wait completed and both CTAs of each pair held the same tensor-memory
- * columns).  The paper has no counterpart: this checks a B300-specific kernel alone. */
-int bnb_tc_gemm_check_pair(const double* dA, const double* dB, int M, int N, int Kd, int nsplit,
-                           int bn, float* dC, int* err_out);
 
 typedef struct {
   long long nodes;          /* nodes solved (retired with an FP64 certificate) */

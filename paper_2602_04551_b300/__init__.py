@@ -22,15 +22,19 @@ BNB_OK = 0
 BNB_EINVAL, BNB_ENOMEM, BNB_ECUDA, BNB_ETIMEOUT, BNB_EQUEUE, BNB_ENODEV = -1, -2, -3, -4, -5, -6
 BNB_PREC_FP64, BNB_PREC_FP32, BNB_PREC_BF16, BNB_PREC_TC3, BNB_PREC_BF16X2 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "optimal", 1: "gap", 2: "time_limit", 3: "queue_full", 4: "node_limit",
-                5: "depth_limit"}
+                5: "depth_limit", 6: "support_limit"}
 
 # exported symbols (kept in step with include/bnb.h)
 SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_device", "bnb_relax_batch",
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
-           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_tc_gemm_check_pair", "bnb_dual_bound_static",
+           "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_dual_bound_static",
            "bnb_get_stats", "bnb_get_histograms",
            "bnb_last_error", "bnb_destroy")
+# exported by libbnb_diag.so (kept in step with include/bnb_diag.h)
+DIAG_SYMBOLS = ("bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_tc_gemm_check_pair",
+                "bnb_diag_wait_expiry")
+DIAG_LIB_PATH = os.path.join(_HERE, "libbnb_diag.so")
 STAGES = ("select_refill", "gemm_xw", "reduce_t_or_make_w", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status",
           "cert_screen", "cert_exact")
@@ -47,7 +51,8 @@ class bnb_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("relax_alpha", ctypes.c_double),
                 ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int),
-                ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int)]
+                ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int),
+                ("ub_polish", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):
@@ -105,9 +110,6 @@ def load_library(path: str = LIB_PATH):
         "bnb_stream": ([P], P),
         "bnb_root_heuristic": ([P, P, P], I),
         "bnb_profile_round": ([P, P, P, I], I),
-        "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
-        "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
-        "bnb_tc_gemm_check_pair": ([P, P, I, I, I, I, I, P, P], I),
         "bnb_get_histograms": ([P, P, I, P, I], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
@@ -119,6 +121,33 @@ def load_library(path: str = LIB_PATH):
         f.argtypes = args
         f.restype = res
     _lib = lib
+    return lib
+
+
+_diag = None
+
+
+def load_diag_library(path: str = DIAG_LIB_PATH):
+    """Load libbnb_diag.so, the diagnostics of include/bnb_diag.h (raises if missing)."""
+    global _diag
+    if _diag is not None:
+        return _diag
+    load_library()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run python -m paper_2602_04551_b300.build")
+    lib = ctypes.CDLL(path)
+    P, D, I, LL = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_longlong
+    sig = {
+        "bnb_tc_gemm_check": ([P, P, I, I, I, I, I, I, P, P], I),
+        "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
+        "bnb_tc_gemm_check_pair": ([P, P, I, I, I, I, I, P, P], I),
+        "bnb_diag_wait_expiry": ([LL, D, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _diag = lib
     return lib
 
 
@@ -240,9 +269,38 @@ def bnb_dual_bound(h: Handle, fix, r):
     return lb
 
 
+def _check_device_tensor(name, t, dtype, numel, device):
+    if not hasattr(t, "is_cuda") or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+
+
 def bnb_dual_bound_static(dX, dy, n, p, lambda0, lambda2, M, dfix, dr, dlb, stream=0):
-    """Allocation-free dual bound on device tensors (see include/bnb.h)."""
+    """Allocation-free dual bound on device tensors (see include/bnb.h).
+
+    dX (n*p float64, column-major), dy (n float64), dfix (K x p int8), dr (K x n float64)
+    and dlb (K float64) must be contiguous CUDA tensors on one device; a size, dtype or
+    device mismatch raises ValueError before the library is called, so no kernel ever
+    reads or writes past a caller's buffer.  Sizes beyond the library's fixed scratch
+    come back as BnbError(BNB_EINVAL)."""
+    import torch
+    n, p = int(n), int(p)
+    if dfix.dim() != 2:
+        raise ValueError("dfix must be a K x p tensor")
     K = int(dfix.shape[0])
+    dev = dX.device if hasattr(dX, "device") else None
+    _check_device_tensor("dX", dX, torch.float64, n * p, dev)
+    _check_device_tensor("dy", dy, torch.float64, n, dev)
+    _check_device_tensor("dfix", dfix, torch.int8, K * p, dev)
+    _check_device_tensor("dr", dr, torch.float64, K * n, dev)
+    _check_device_tensor("dlb", dlb, torch.float64, K, dev)
     _check(load_library().bnb_dual_bound_static(_ptr(dX), _ptr(dy), int(n), int(p), float(lambda0),
                                                 float(lambda2), float(M), K, _ptr(dfix), _ptr(dr),
                                                 _ptr(dlb), ctypes.c_void_p(stream or 0)))
@@ -307,7 +365,7 @@ def bnb_profile_round(h: Handle) -> dict:
 def bnb_tc_gemm_check(dA, dB, M, N, Kd, nsplit=1, bn=128, splits=1, dC=None):
     """Tensor-core contraction C = A B^T on torch CUDA tensors (FP64 in, FP32 out)."""
     err = ctypes.c_int(0)
-    _check(load_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
+    _check(load_diag_library().bnb_tc_gemm_check(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn, splits,
                                             _ptr(dC), ctypes.byref(err)))
     return err.value
 
@@ -323,7 +381,7 @@ def bnb_get_histograms(h: Handle, ndepth: int = 257, nsupport: int = 258):
 def bnb_tc_gemm_check_pair(dA, dB, M, N, Kd, nsplit=3, bn=144, dC=None):
     """C = A B^T through the CTA-pair tensor-core kernel (FP64 in, FP32 out)."""
     err = ctypes.c_int(0)
-    _check(load_library().bnb_tc_gemm_check_pair(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn,
+    _check(load_diag_library().bnb_tc_gemm_check_pair(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, bn,
                                                  _ptr(dC), ctypes.byref(err)))
     return err.value
 
@@ -331,9 +389,19 @@ def bnb_tc_gemm_check_pair(dA, dB, M, N, Kd, nsplit=3, bn=144, dC=None):
 def bnb_tc_gemm_check_cluster(dA, dB, M, N, Kd, nsplit=3, cluster=8, dC=None):
     """C = A B^T through the cluster-reduced tensor-core kernel (FP64 in, FP32 out)."""
     err = ctypes.c_int(0)
-    _check(load_library().bnb_tc_gemm_check_cluster(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, cluster,
+    _check(load_diag_library().bnb_tc_gemm_check_cluster(_ptr(dA), _ptr(dB), M, N, Kd, nsplit, cluster,
                                                     _ptr(dC), ctypes.byref(err)))
     return err.value
+
+
+def bnb_diag_wait_expiry(max_polls: int, max_seconds: float):
+    """The kernels' bounded mbarrier wait on a barrier nothing arrives on, with short limits
+    (include/bnb_diag.h); returns (error word, seconds spent waiting)."""
+    err = ctypes.c_int(-1)
+    sec = ctypes.c_double(-1.0)
+    _check(load_diag_library().bnb_diag_wait_expiry(int(max_polls), float(max_seconds),
+                                                    ctypes.byref(err), ctypes.byref(sec)))
+    return err.value, sec.value
 
 
 def bnb_root_heuristic(h: Handle):

@@ -1,8 +1,10 @@
-"""Builds libbnb.so (the C-ABI library) in-tree for sm_103a with nvcc.
+"""Builds libbnb.so (the C-ABI library, include/bnb.h) and libbnb_diag.so (its
+diagnostics, include/bnb_diag.h) in-tree for sm_103a with nvcc.
 
     python -m paper_2602_04551_b300.build [--verbose]
 
-The library has no torch dependency; it links only the CUDA runtime.
+The libraries have no torch dependency; they link only the CUDA runtime, and the
+diagnostics library links libbnb.so for the operand helpers it shares.
 """
 import glob
 import os
@@ -12,6 +14,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libbnb.so")
+DIAG_LIB = os.path.join(HERE, "libbnb_diag.so")
+DIAG_SOURCES = ("diag.cu",)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -25,9 +29,9 @@ def headers():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(DIAG_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(DIAG_LIB))
     return all(os.path.getmtime(f) <= t for f in sources() + headers())
 
 
@@ -54,8 +58,11 @@ def build(verbose=False, force=False):
             sys.stdout.write(out.decode())
         if pr.returncode:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    link = [nvcc] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"]
-    subprocess.check_call(link)
+    main = [o for o, src in zip(objs, sources()) if os.path.basename(src) not in DIAG_SOURCES]
+    diag = [o for o, src in zip(objs, sources()) if os.path.basename(src) in DIAG_SOURCES]
+    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", LIB] + main + ["-lcudart"])
+    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", DIAG_LIB] + diag +
+                          ["-L", HERE, "-lbnb", "-Xlinker", "-rpath=$ORIGIN", "-lcudart"])
     return LIB
 
 

@@ -418,6 +418,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->mv_crossover = -1;
   o->fused_shape = 0;
   o->u_shape = 0;
+  o->ub_polish = 1;
   return BNB_OK;
 }
 
@@ -523,6 +524,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
+  if (o.ub_polish != 0 && o.ub_polish != 1) return fail(BNB_EINVAL, "ub_polish must be 0 or 1");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
@@ -811,7 +813,7 @@ extern "C" int bnb_upper_batch(bnb_handle* h, int K, const uint8_t* support, dou
     if (int rc = ub_from_masks(e, e.cflag, K)) return rc;
     double inf = INFINITY;
     BNB_CUDA_OK(cudaMemcpyAsync(e.inc_ub, &inf, sizeof(double), cudaMemcpyHostToDevice, e.st));
-    if (int rc = upper_bound(e, true)) return rc;
+    if (int rc = upper_bound(e, h->opt.ub_polish ? 1 : -1)) return rc;
     BNB_CUDA_OK(cudaMemcpyAsync(ub, e.ub_val, sizeof(double) * K, cudaMemcpyDeviceToHost, e.st));
     if (beta_out) {
       k_scatter_ub<<<K, 256, 0, e.st>>>(K, e.p, e.smax, e.sup, e.sup_cnt, e.ubb64, h->d_ubbeta);
@@ -856,7 +858,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     if (int rc = branch_support(e, false, true)) return rc;
     prof_end(pf, e.st, PK_BRANCH);
     prof_begin(pf, e.st);
-    if (int rc = upper_bound(e, false)) return rc;
+    if (int rc = upper_bound(e, 0)) return rc;
     prof_end(pf, e.st, PK_UB);
   } else {
     k_copy_scalar<<<1, 32, 0, e.st>>>(e.inc_ub, e.inc_snap);
@@ -866,7 +868,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     cudaStream_t main_st = e.st;
     e.st = e.st_aux;
     int rc = branch_support(e, false, true, true);
-    if (!rc) rc = upper_bound(e, false);
+    if (!rc) rc = upper_bound(e, 0);
     e.st = main_st;
     const cudaError_t ce = cudaEventRecord(e.ev_join, e.st_aux);
     if (rc) return rc;
@@ -996,7 +998,8 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
     if (s.active_slots == 0 && s.pool_count == 0) {
       S.done = true;
       S.status = (s.error & 2) ? BNB_STATUS_QUEUE_FULL
-                 : (s.error & 1) ? BNB_STATUS_DEPTH_LIMIT : BNB_STATUS_OPTIMAL;
+                 : (s.error & 1) ? BNB_STATUS_DEPTH_LIMIT
+                 : (s.error & 4) ? BNB_STATUS_SUPPORT_LIMIT : BNB_STATUS_OPTIMAL;
       if (s.error && std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub))
         S.status = BNB_STATUS_GAP;
     } else if (std::isfinite(s.ub) && (s.ub - s.lb) <= S.gap * std::fabs(s.ub)) {
@@ -1005,6 +1008,9 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
     } else if (s.error & 2) {
       S.done = true;
       S.status = BNB_STATUS_QUEUE_FULL;
+    } else if (s.error & 4) {
+      S.done = true;
+      S.status = BNB_STATUS_SUPPORT_LIMIT;
     } else if (el > o.time_limit_s) {
       S.done = true;
       S.status = BNB_STATUS_TIME_LIMIT;

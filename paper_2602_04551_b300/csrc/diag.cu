@@ -1,4 +1,5 @@
-// diag.cu -- diagnostics entry points: the tcgen05 contractions on their own.
+// diag.cu -- diagnostics entry points (libbnb_diag.so, declared in include/bnb_diag.h):
+// the tcgen05 contractions on their own, and the bounded mbarrier wait on its own.
 //
 // bnb_tc_gemm_check runs C = A B^T for FP64 inputs split into BF16 operands
 // (1 term: hi only; 3 terms: hi/lo pairs), K-major A (M x Kred) and B (N x Kred),
@@ -7,6 +8,7 @@
 // a plain product before it is used inside the ADMM iteration.
 #include <cuda_bf16.h>
 #include "bnb.h"
+#include "bnb_diag.h"
 #include "tc_host.cuh"
 
 namespace bnb {
@@ -97,7 +99,56 @@ static int make_operands(cudaStream_t st, const double* dA, const double* dB, in
   return rc;
 }
 
+// One CTA waits on an mbarrier that nothing arrives on (phase 0 of a fresh barrier with an
+// arrival count of 1), with the kernels' wait loop and short limits; no TMA copy and no
+// MMA is issued, so nothing is in flight when the wait gives up.  Every thread waits;
+// err receives the wait's code (1) from each expired wait and 2 if any wait reported
+// success; elapsed receives the time thread 0 spent in the wait.
+__global__ void k_wait_expiry(long long max_polls, unsigned long long max_ns, int* err,
+                              unsigned long long* elapsed) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const unsigned long long t0 = tc::global_ns();
+  const bool ok = tc::mbar_wait_bounded<false>(&bar, 0, err, 1, max_polls, max_ns);
+  if (ok) atomicOr(err, 2);
+  if (threadIdx.x == 0) *elapsed = tc::global_ns() - t0;
+  __syncthreads();
+}
+
 }  // namespace bnb
+
+extern "C" int bnb_diag_wait_expiry(long long max_polls, double max_seconds, int* err_out,
+                                    double* seconds_out) {
+  using namespace bnb;
+  if (max_polls < 1 || max_polls > (1ll << 30) || !(max_seconds > 0.0) || max_seconds > 1.0 ||
+      !err_out || !seconds_out)
+    return BNB_EINVAL;
+  int* err = nullptr;
+  unsigned long long* el = nullptr;
+  cudaError_t ce = cudaMalloc(&err, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMalloc(&el, sizeof(unsigned long long));
+  if (ce == cudaSuccess) ce = cudaMemset(err, 0, sizeof(int));
+  if (ce == cudaSuccess) {
+    k_wait_expiry<<<1, 128>>>(max_polls, (unsigned long long)(max_seconds * 1e9), err, el);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  unsigned long long ns = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(&ns, el, sizeof(ns), cudaMemcpyDeviceToHost);
+  *seconds_out = ns * 1e-9;
+  cudaFree(err);
+  cudaFree(el);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return BNB_ECUDA;
+  }
+  return BNB_OK;
+}
 
 extern "C" int bnb_tc_gemm_check_cluster(const double* dA, const double* dB, int M, int N, int Kd,
                                          int nsplit, int cluster, float* dC, int* err_out) {

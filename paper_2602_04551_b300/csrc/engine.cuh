@@ -29,7 +29,8 @@ struct Status {                 // copied to the host after every round
   int polished;
   int free_top;                 // free pool entries
   int warm_free;
-  int error;                    // 1: depth limit reached (node kept as lost bound)
+  int error;                    // bits (the node is kept as a lost bound): 1 depth limit,
+                                // 2 pool full, 4 a leaf support above support_max
   int max_depth;
   double lost_lb;
   long long nodes_total;        // nodes certified since the solve started
@@ -207,7 +208,7 @@ template <class R> int certify_exact(Engine<R>& e, bool use_threshold, const dou
 template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false,
                                       bool defer_fallback = false);
 template <class R> int branch_fallback(Engine<R>& e);
-template <class R> int upper_bound(Engine<R>& e, bool force_polish);
+template <class R> int upper_bound(Engine<R>& e, int force_polish);
 template <class R> int queue_push(Engine<R>& e);
 template <class R> int queue_select_refill(Engine<R>& e);
 template <class R> int queue_init(Engine<R>& e);

@@ -196,7 +196,7 @@ int root_heuristic(Engine<R>& e, int max_moves) {
   }
   k_mp_support<<<1, 32, 0, st>>>(in, p, e.smax, e.sup, e.sup_cnt, e.ret_count);
   BNB_CUDA_OK(cudaGetLastError());
-  if (int rc = upper_bound(e, true)) return rc;
+  if (int rc = upper_bound(e, 1)) return rc;
   BNB_CUDA_OK(cudaFreeAsync(mbeta, st));
   BNB_CUDA_OK(cudaFreeAsync(mr, st));
   BNB_CUDA_OK(cudaFreeAsync(mc, st));

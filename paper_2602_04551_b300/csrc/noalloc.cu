@@ -3,11 +3,18 @@
 // bnb_dual_bound_static computes the same Proposition 1 bound as bnb_dual_bound
 // for caller-supplied residuals, but it needs no handle and allocates nothing:
 // its per-(node, column block) partial sums live in a fixed, file-scope device
-// array that the library reserves once on every GPU that loads it.  It is meant
-// for callers that must not allocate device memory: for example code running
-// under another framework that already owns the GPU's memory budget through its
-// own allocator, or a latency-critical loop that cannot afford cudaMalloc's
-// implicit synchronisation or the risk of an allocation failure mid-run.
+// array.  It is meant for callers that must not allocate device memory: for
+// example code running under another framework that already owns the GPU's
+// memory budget through its own allocator, or a latency-critical loop that
+// cannot afford cudaMalloc's implicit synchronisation or the risk of an
+// allocation failure mid-run.
+//
+// When the array comes into being: the CUDA runtime loads this file's module
+// lazily (the default since CUDA 12.2), so the array is reserved on a device the
+// first time this entry point runs there -- the address lookup below triggers
+// the load.  That first call can therefore synchronise the device and can fail
+// (BNB_ECUDA) when the device has no 8 MiB left; later calls only launch.  Once
+// reserved, the array stays until the process exits.
 //
 // Limits and sharing: the array holds SCRATCH_DOUBLES doubles (8 MiB); a call
 // needs K * (ceil(p / 256) + 2) of them and is rejected with BNB_EINVAL beyond
@@ -23,7 +30,7 @@ namespace bnb {
 
 constexpr long long SCRATCH_DOUBLES = 1ll << 20;   // 8 MiB
 constexpr int COLS_PER_BLOCK = 256;                 // columns of X per block (8 warps x 32)
-constexpr int MAX_DEVICES = 64;
+constexpr int MAX_CONTEXTS = 64;       // cached (device, context) lookups
 
 static __device__ __align__(256) double g_cert_scratch[SCRATCH_DOUBLES];
 
@@ -78,24 +85,64 @@ __global__ void k_cert_static_final(int K, int nb, const double* __restrict__ sc
   lb[k] = -0.5 * s[0] + s[1] - nu;
 }
 
-// Device address of g_cert_scratch for each device, looked up once per device
-// (with that device current) on the first call made on it.
-static double* scratch_ptr[MAX_DEVICES];
+// Device address of g_cert_scratch, looked up once per (device, context) with that
+// device current: a device address is valid only in the context it came from, so a
+// caller that makes its own (non-primary) context current gets its own lookup.  The
+// driver's cuCtxGetCurrent is reached through the runtime's entry-point query, so the
+// library still links only the CUDA runtime.
+struct ScratchEntry {
+  int dev;
+  void* ctx;
+  double* ptr;
+};
+static ScratchEntry scratch_tab[MAX_CONTEXTS];
+static int scratch_used = 0;
 static std::mutex scratch_mu;
+
+typedef int (*CtxGetCurrentFn)(void** ctx);
+
+static int current_context(void** ctx) {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {   // called under scratch_mu
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)f;
+    else
+      cudaGetLastError();
+  }
+  *ctx = nullptr;
+  if (!fn || fn(ctx) != 0) return BNB_ECUDA;
+  return 0;
+}
 
 static int scratch_for_current_device(double** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return BNB_ENODEV;
-  std::lock_guard<std::mutex> lock(scratch_mu);
-  if (!scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_cert_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return BNB_ECUDA;
-    }
-    scratch_ptr[dev] = (double*)p;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
+    cudaGetLastError();
+    return BNB_ENODEV;
   }
-  *out = scratch_ptr[dev];
+  // with no context current yet (a thread's first CUDA call), the symbol lookup below
+  // makes the device's primary context current; the context is read again after it
+  std::lock_guard<std::mutex> lock(scratch_mu);
+  void* ctx = nullptr;
+  if (current_context(&ctx)) return BNB_ECUDA;
+  for (int i = 0; ctx && i < scratch_used; ++i)
+    if (scratch_tab[i].dev == dev && scratch_tab[i].ctx == ctx) {
+      *out = scratch_tab[i].ptr;
+      return 0;
+    }
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_cert_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return BNB_ECUDA;
+  }
+  if (!ctx && current_context(&ctx)) return BNB_ECUDA;
+  if (ctx && scratch_used < MAX_CONTEXTS) scratch_tab[scratch_used++] = ScratchEntry{dev, ctx, (double*)p};
+  *out = (double*)p;
   return 0;
 }
 

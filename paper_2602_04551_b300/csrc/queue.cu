@@ -84,8 +84,18 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
     atomicAdd(&hist_sup[(sc < 0 || sc > smax) ? smax + 1 : sc], 1);
     const double thr = inc_ub[0] * (1.0 - params[0]);
     decision = 0;
-    if (lbu >= thr || j < 0) {
+    if (lbu >= thr) {
       atomicAdd(&sel_state[SS_PRUNED], 1);
+    } else if (j < 0) {
+      // a leaf is closed by its support's upper bound (taken this round, or earlier when
+      // sup_cnt is -2); a leaf support larger than smax had none taken: keep its bound as
+      // a lost bound and stop the solve rather than drop its objective
+      if (sup_cnt[q] == -1) {
+        atomicOr(&sel_state[SS_ERROR], 4);
+        atomicMin(lost_key, dkey(lbu));
+      } else {
+        atomicAdd(&sel_state[SS_PRUNED], 1);
+      }
     } else if (d + 1 > dmax) {
       atomicOr(&sel_state[SS_ERROR], 1);
       atomicMin(lost_key, dkey(lbu));

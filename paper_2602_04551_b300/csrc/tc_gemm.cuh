@@ -47,7 +47,8 @@ constexpr int BM = 128;
 constexpr int BK = 64;             // 64 BF16 = 128 bytes: one swizzle row
 constexpr int EPI_WARPS = 8;       // default epilogue warps: two per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr long long WAIT_LIMIT = 1ll << 24;
+constexpr long long WAIT_LIMIT = 1ll << 24;   // polls of one bounded mbarrier wait
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // and at most 2 s of it
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -69,24 +70,42 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// bounded wait on the phase with parity `ph` (at most WAIT_LIMIT polls and 2 s);
-// false (and *err set) on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph, int* err, int code) {
+// bounded wait on the phase with parity `ph`: at most max_polls polls and max_ns of
+// %globaltimer; false (and *err |= code) on expiry.  CLUSTER selects the cluster-scope
+// acquire form (arrivals from the other CTA of a pair).  The kernels use the limits of
+// mbar_wait / mbar_wait_cluster; a diagnostics kernel runs the same loop with short
+// limits on a barrier nobody arrives on, to show that an expired wait returns.
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t ph, int* err, int code,
+                                                  long long max_polls, uint64_t max_ns) {
   const uint32_t a = smem_u32(bar);
   const uint64_t t0 = global_ns();
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+  for (long long i = 0; i < max_polls; ++i) {
     uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(ph)
-        : "memory");
+    if constexpr (CLUSTER)
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+          " selp.b32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(ph)
+          : "memory");
+    else
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+          " selp.b32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(ph)
+          : "memory");
     if (ok) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
+    if ((i & 255) == 255 && global_ns() - t0 > max_ns) break;
   }
   atomicOr(err, code);
   return false;
+}
+
+// the kernels' bound: WAIT_LIMIT polls and WAIT_NS (2 s)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t ph, int* err, int code) {
+  return mbar_wait_bounded<false>(bar, ph, err, code, WAIT_LIMIT, WAIT_NS);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -942,21 +961,7 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
 
 // bounded wait with cluster-scope acquire (arrivals from the other CTA of the pair)
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t ph, int* err, int code) {
-  const uint32_t a = smem_u32(bar);
-  const uint64_t t0 = global_ns();
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(ph)
-        : "memory");
-    if (ok) return true;
-    if ((i & 255) == 255 && global_ns() - t0 > 2000000000ull) break;
-  }
-  atomicOr(err, code);
-  return false;
+  return mbar_wait_bounded<true>(bar, ph, err, code, WAIT_LIMIT, WAIT_NS);
 }
 
 template <int BN, int NSPLIT>

@@ -323,7 +323,7 @@ __global__ void k_ub_fista(const R* __restrict__ Qg, const R* __restrict__ qv, i
 // FP64 value of Eq. original at the candidate (one block per node)
 template <class R>
 __global__ void k_ub_eval(const double* __restrict__ X64, const double* __restrict__ y64, int n,
-                          int smax, double lam0, double lam2, const int* __restrict__ sup,
+                          int smax, double lam0, double lam2, double M, const int* __restrict__ sup,
                           const int* __restrict__ sup_cnt, const int* __restrict__ ret_count,
                           const R* __restrict__ ubb, double* __restrict__ ubb64,
                           double* __restrict__ ub_val, int* __restrict__ pol_flag,
@@ -341,7 +341,10 @@ __global__ void k_ub_eval(const double* __restrict__ X64, const double* __restri
   }
   const int* S = sup + (long long)q * smax;
   double* b64 = ubb64 + (long long)q * 2 * smax;
-  for (int a = threadIdx.x; a < s; a += blockDim.x) b64[a] = (double)ubb[(long long)q * smax + a];
+  // the point clipped to the FP64 box: the ADMM-precision clip uses M rounded to that
+  // precision, which may lie just outside the box, and the value must be a feasible one
+  for (int a = threadIdx.x; a < s; a += blockDim.x)
+    b64[a] = fmin(M, fmax(-M, (double)ubb[(long long)q * smax + a]));
   __syncthreads();
   double rr = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -360,7 +363,8 @@ __global__ void k_ub_eval(const double* __restrict__ X64, const double* __restri
   if (threadIdx.x == 0) {
     const double v = 0.5 * rr + lam0 * nz + lam2 * bb;
     ub_val[q] = v;
-    pol_flag[q] = (s > 0) && (force || v < inc_ub[0] * (1.0 + 1e-6));
+    // force: 1 polish every candidate, -1 none, 0 those within 1e-6 of the incumbent
+    pol_flag[q] = (s > 0) && force >= 0 && (force || v < inc_ub[0] * (1.0 + 1e-6));
   }
 }
 
@@ -620,8 +624,10 @@ int branch_support(Engine<R>& e, bool write_z, bool memo, bool defer_fallback) {
   return 0;
 }
 
+// force_polish: 1 polish every candidate in FP64, -1 none (the projected-gradient
+// solutions are kept), 0 those within 1e-6 of the incumbent (a solve)
 template <class R>
-int upper_bound(Engine<R>& e, bool force_polish) {
+int upper_bound(Engine<R>& e, int force_polish) {
   cudaStream_t st = e.st;
   const int K = e.K;
   k_ub_gram<R><<<dim3(K, 16), 256, 0, st>>>(e.XR, e.yR, e.n, e.smax, e.P.lam2, e.sup, e.sup_cnt,
@@ -629,9 +635,9 @@ int upper_bound(Engine<R>& e, bool force_polish) {
   const size_t sm = sizeof(R) * 4 * e.smax;
   k_ub_fista<R><<<K, 256, sm, st>>>(e.Qg, e.qv, e.smax, e.P.M, e.sup_cnt, e.ret_count,
                                     e.ub_iters, sizeof(R) == 4 ? 1e-7 : 1e-13, e.ubb);
-  k_ub_eval<R><<<K, 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2, e.sup,
+  k_ub_eval<R><<<K, 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2, e.P.M, e.sup,
                                   e.sup_cnt, e.ret_count, e.ubb, e.ubb64, e.ub_val, e.pol_flag,
-                                  e.inc_ub, force_polish ? 1 : 0);
+                                  e.inc_ub, force_polish);
   k_ub_polish<<<K, 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2, e.P.M, e.sup,
                                  e.sup_cnt, e.ret_count, e.pol_flag, e.Q64, e.L64, e.ubb64,
                                  e.ub_val, e.sel_state + 8);
@@ -659,8 +665,8 @@ template int branch_support<float>(Engine<float>&, bool, bool, bool);
 template int branch_support<double>(Engine<double>&, bool, bool, bool);
 template int branch_fallback<float>(Engine<float>&);
 template int branch_fallback<double>(Engine<double>&);
-template int upper_bound<float>(Engine<float>&, bool);
-template int upper_bound<double>(Engine<double>&, bool);
+template int upper_bound<float>(Engine<float>&, int);
+template int upper_bound<double>(Engine<double>&, int);
 template int ub_from_masks<float>(Engine<float>&, const uint8_t*, int);
 template int ub_from_masks<double>(Engine<double>&, const uint8_t*, int);
 

@@ -18,19 +18,40 @@ def lib():
     return b
 
 
-def _declared():
-    txt = open(os.path.join(ROOT, "include", "bnb.h")).read()
+def _declared(header="bnb.h"):
+    txt = open(os.path.join(ROOT, "include", header)).read()
     return set(re.findall(r"\b(bnb_[a-z_0-9]+)\s*\(", txt)) - {"bnb_handle"}
 
 
-def test_header_symbols_exported(lib):
-    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
+def _exported(path):
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r" T (bnb_[a-z_0-9]+)", out))
+    return set(re.findall(r" T (bnb_[a-z_0-9]+)", out))
+
+
+def test_header_symbols_exported(lib):
+    exported = _exported(lib.LIB_PATH)
     declared = _declared()
     assert declared, "no declarations found"
     assert declared <= exported, declared - exported
     assert set(lib.SYMBOLS) == declared
+
+
+def test_diagnostics_library_exports_its_header_and_the_product_does_not(lib):
+    """The diagnostics (include/bnb_diag.h) live in libbnb_diag.so: it exports every call
+    the header declares, the product library exports none of them, and the diagnostics
+    library loads with its prototypes (their argument counts match the header)."""
+    declared = _declared("bnb_diag.h")
+    assert declared == set(lib.DIAG_SYMBOLS)
+    assert declared <= _exported(lib.DIAG_LIB_PATH)
+    assert not (declared & _exported(lib.LIB_PATH))
+    raw = lib.load_diag_library()
+    arity = _header_arity("bnb_diag.h")
+    assert set(arity) == declared
+    for name, count in arity.items():
+        assert len(getattr(raw, name).argtypes) == count, name
+    if raw.bnb_diag_wait_expiry(0, 0.001, None, None) != lib.BNB_EINVAL:
+        raise AssertionError("bad limits must be rejected before any device work")
 
 
 def test_options_default_and_errors(lib):
@@ -104,9 +125,9 @@ def test_footprint_host_arithmetic(lib):
         assert ei.value.code == lib.BNB_EINVAL
 
 
-def _header_arity():
+def _header_arity(header="bnb.h"):
     """Parameter count of every function the header declares."""
-    txt = open(os.path.join(ROOT, "include", "bnb.h")).read()
+    txt = open(os.path.join(ROOT, "include", header)).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     out = {}
     for name, params in re.findall(r"\b(bnb_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
@@ -208,7 +229,7 @@ def test_constants_match_header(lib):
     """Error codes and precisions have the header's values in the binding; every status
     code the header defines has a name (BNB_STATUS_X -> "x")."""
     defs = _header_defines()
-    assert len(defs) == 18        # OK, six error codes, five precisions, six statuses
+    assert len(defs) == 19        # OK, six error codes, five precisions, seven statuses
     for name, value in defs.items():
         if name.startswith("BNB_STATUS_"):
             assert lib.STATUS_NAMES[value] == name[len("BNB_STATUS_"):].lower(), name
@@ -223,7 +244,7 @@ def test_documented_defaults(lib):
                 precision=lib.BNB_PREC_TC3, use_graphs=1, time_limit_s=3600.0, max_nodes=10**9,
                 queue_capacity=1 << 20, warm_capacity=0, support_max=200, ub_max_iter=200, device=0,
                 stream=None, relax_alpha=1.0, root_heuristic=1, max_depth=256, lockstep=0,
-                mv_crossover=-1, fused_shape=0, u_shape=0)
+                mv_crossover=-1, fused_shape=0, u_shape=0, ub_polish=1)
     assert {k for k, _ in o._fields_} == set(want)
     for k, v in want.items():
         assert getattr(o, k) == v, k
@@ -258,6 +279,7 @@ def test_option_validation_on_the_host(lib):
         (dict(u_shape=3), "u_shape"), (dict(relax_alpha=0.5), "relax_alpha"),
         (dict(relax_alpha=2.0), "relax_alpha"), (dict(queue_capacity=10), "queue_capacity"),
         (dict(queue_capacity=(1 << 30) + 1), "queue_capacity"), (dict(precision=7), "precision"),
+        (dict(ub_polish=2), "ub_polish"),
     ]
     for kw, word in bad:
         rc, msg = create(**kw)

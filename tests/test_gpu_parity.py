@@ -85,20 +85,26 @@ def test_dual_bound_full_size_sampled(prec):
 # ------------------------------------------------------------------ ADMM iteration
 
 
-def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed, tol=None, **kw):
+def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed, tol=None, rho=1.0,
+                         alpha=1.0, **kw):
+    """One ADMM iteration (penalty rho, over-relaxation alpha) through the C ABI against the
+    oracle's direct-D iteration, element by element.  The b-update's operator
+    D = (X^T X + rho I)^-1 has norm 1/rho on the null space of X (p > n), so the error of the
+    low-precision products in b grows as 1/rho: the tolerance is ITER_TOL / min(1, rho)."""
     rng = np.random.default_rng(seed)
     fix = datagen.random_fixings(inst.p, K, rng, 20)
     wb = (rng.uniform(-M, M, (K, inst.p)) * (rng.random((K, inst.p)) < 0.05)).astype(np.float32)
     wb[fix == 0] = 0.0
     wv = rng.normal(0, 0.05, (K, inst.p)).astype(np.float32)
-    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1, **kw) as h:
+    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1, rho=rho, relax_alpha=alpha,
+                 **kw) as h:
         out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
     assert np.all(out["iters"] == 1)
-    data = admm.AdmmData(inst.X, inst.y, 1.0)
-    tol = ITER_TOL[prec] if tol is None else tol
+    data = admm.AdmmData(inst.X, inst.y, rho)
+    tol = (ITER_TOL[prec] if tol is None else tol) / min(1.0, rho)
     for k in rows:
         b, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
-                                         fix[k], lam0, lam2, M)
+                                         fix[k], lam0, lam2, M, alpha=alpha)
         sb = max(1.0, np.max(np.abs(beta)))
         sv = max(1.0, np.max(np.abs(v)))
         np.testing.assert_allclose(out["beta"][k], beta, atol=tol * sb)
@@ -118,6 +124,108 @@ def test_one_admm_iteration_full_size_sampled(prec):
     """C2 shape at the bench width K=512; four sampled nodes against the oracle."""
     inst, lam0, lam2, M = _inst("c2", 0)
     _one_iteration_check(inst, lam0, lam2, M, prec, K=512, Kopt=512, rows=[0, 131, 300, 511], seed=4)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_one_admm_iteration_benchmarked_rho_alpha(prec):
+    """The penalty and over-relaxation the benchmark's autotuner picks (rho = 0.3,
+    alpha = 1.6), element by element against the oracle's over-relaxed iteration: the
+    rho-scaled terms of the fused update (v / rho, rho beta - V, the shifted W') and
+    the alpha-mix of b and beta are exercised with rho != 1."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=64, rows=range(45), seed=13,
+                         rho=0.3, alpha=1.6)
+
+
+@pytest.mark.parametrize("prec", [3, 1])
+def test_one_admm_iteration_benchmarked_rho_alpha_full_size(prec):
+    """The same at the benchmark's c2 shape and launch width (K = 512), sampled rows."""
+    inst, lam0, lam2, M = _inst("c2", 0, frac=0.02)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=512, Kopt=512, rows=[0, 77, 256, 511],
+                         seed=14, rho=0.3, alpha=1.6)
+
+
+@pytest.mark.parametrize("prec", [3, 2])
+def test_one_admm_iteration_narrow_batch_benchmarked_rho_alpha(prec):
+    """Narrow batches (matrix-vector form) at rho = 0.3, alpha = 1.6."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=12, Kopt=64, rows=range(12), seed=15,
+                         tol=ITER_TOL[1], rho=0.3, alpha=1.6)
+
+
+def _threshold_targets(lam0, lam2, M, rho, fix, rng):
+    """Per coordinate, a target for beta~ = b + v / rho on a breakpoint of the prox of
+    Eq. minbetalower: free coordinates cycle over +-a, +-tau (the ridge switch) and
+    +-(a + M) (the box) in the perspective regime, or +-a_lin and +-(a_lin + M) in the
+    linear regime (sqrt(lam0/lam2) > M); F1 coordinates sit where the ridge value reaches
+    the box, +-M (rho + 2 lam2) / rho; F0 coordinates get arbitrary values."""
+    s0 = np.sqrt(lam0 / lam2)
+    if s0 > M:
+        a = (lam0 / M + lam2 * M) / rho
+        pts = [a, a + M]
+    else:
+        a = 2.0 * np.sqrt(lam0 * lam2) / rho
+        pts = [a, a + s0, a + M] if a + s0 < a + M else [a, a + M]
+    p = len(fix)
+    t = np.empty(p)
+    for i in range(p):
+        sg = 1.0 if i % 2 == 0 else -1.0
+        if fix[i] == 1:
+            t[i] = sg * M * (rho + 2.0 * lam2) / rho
+        elif fix[i] == 0:
+            t[i] = rng.normal(0, 0.5)
+        else:
+            t[i] = sg * pts[(i // 2) % len(pts)]
+    return t
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("frac", [pytest.param(0.01, id="perspective"),
+                                  pytest.param(0.1, id="linear")])
+def test_one_iteration_at_prox_breakpoints(prec, frac):
+    """A warm start crafted so that beta~ lands on the prox's breakpoints (within the FP32
+    rounding of the warm start) for F0, F1 and free coordinates, in both psi regimes; the
+    GPU's beta and v after one iteration match the oracle's element by element.  With
+    n > p (the c1 shape) I/rho - D is invertible, so v can be solved for any target:
+    beta~ = D (c + rho beta) + (I/rho - D) v."""
+    inst, lam0, lam2, M = _inst("c1", 0, frac=frac)
+    rho = 0.7
+    assert (np.sqrt(lam0 / lam2) > M) == (frac == 0.1)
+    rng = np.random.default_rng(17)
+    K, p = 6, inst.p
+    fix = np.full((K, p), -1, np.int8)
+    for k in range(1, K):
+        idx = rng.permutation(p)
+        fix[k, idx[: 4 * k]] = 0
+        fix[k, idx[4 * k: 6 * k]] = 1
+    data = admm.AdmmData(inst.X, inst.y, rho)
+    A = np.eye(p) / rho - data.D
+    wb = np.zeros((K, p), np.float32)
+    wv = np.zeros((K, p), np.float32)
+    for k in range(K):
+        tgt = _threshold_targets(lam0, lam2, M, rho, fix[k], rng)
+        b0 = rng.uniform(-M, M, p) * (rng.random(p) < 0.3)
+        b0[fix[k] == 0] = 0.0
+        wb[k] = b0.astype(np.float32)
+        v = np.linalg.solve(A, tgt - data.D @ (data.c + rho * wb[k].astype(np.float64)))
+        wv[k] = v.astype(np.float32)
+        # the crafted start reaches its targets up to the FP32 rounding of v
+        b = data.D @ (data.c + rho * wb[k].astype(np.float64) - wv[k].astype(np.float64))
+        bt = b + wv[k].astype(np.float64) / rho
+        assert np.max(np.abs(bt - tgt)) <= 1e-5 * max(1.0, np.max(np.abs(tgt)))
+    with _handle(inst, lam0, lam2, M, prec, K=8, check_every=1, rho=rho) as h:
+        out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
+    tol = ITER_TOL[prec] / min(1.0, rho)
+    for k in range(K):
+        _, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
+                                         fix[k], lam0, lam2, M)
+        # the crafted v is a few times larger than the iterates it produces (v_new = v +
+        # rho (b - beta) cancels), so the rounding of the products scales with |v|
+        sc = max(1.0, float(np.max(np.abs(wv[k]))))
+        np.testing.assert_allclose(out["beta"][k], beta, atol=tol * sc)
+        np.testing.assert_allclose(out["v"][k], v, atol=tol * sc)
+        assert np.all(out["beta"][k][fix[k] == 0] == 0.0)
+        assert np.all(np.abs(out["beta"][k]) <= M * (1 + 1e-7))
 
 
 @pytest.mark.parametrize("prec", [3, 2])
@@ -358,6 +466,50 @@ def test_upper_batch_matches_oracle(prec, mfac):
         obj, bref = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
         assert ubv[k] == pytest.approx(obj, rel=1e-10), k
         np.testing.assert_allclose(beta[k], bref, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", [1, 3, 0])
+@pytest.mark.parametrize("mfac", [1.5, 0.3])
+def test_projected_gradient_upper_bound_matches_oracle(prec, mfac):
+    """The projected-gradient upper bound on its own (options.ub_polish = 0: no FP64
+    re-solve), the value that decides inside a solve which supports get polished.  Against
+    the oracle: the returned point is feasible (box, support) and its reported value is its
+    exact objective; the value is within the method's stopping accuracy of the exact box
+    ridge optimum and of the oracle's own run of Eqs. fpg_extrapolate..fpg_armijo with the
+    same stopping rule (relative decrease below 1e-7, or 1e-13 on the FP64 path, within
+    200 iterations).  Tolerance: an objective gap delta leaves beta within
+    sqrt(2 delta / lambda_min(Q)) of the minimiser; delta <= 1e-5 relative here."""
+    inst, lam0, lam2, M = _inst("c2_small", 2, mfac=mfac)
+    rng = np.random.default_rng(16)
+    K = 21
+    sup = np.zeros((K, inst.p), np.uint8)
+    for k in range(1, K):
+        sup[k, rng.choice(inst.p, size=int(rng.integers(1, 15)), replace=False)] = 1
+    sup[K - 1, inst.support_true] = 1
+    with _handle(inst, lam0, lam2, M, prec, K=32, ub_polish=0) as h:
+        ubv, beta = bnb.bnb_upper_batch(h, sup)
+    rtol = 1e-7 if prec else 1e-13
+    for k in range(K):
+        S = np.nonzero(sup[k])[0]
+        assert np.all(beta[k][sup[k] == 0] == 0.0)
+        assert np.all(np.abs(beta[k]) <= M)
+        assert ubv[k] == pytest.approx(relax.mip_objective(inst.X, inst.y, beta[k], lam0, lam2),
+                                       rel=1e-12)
+        obj, bref = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
+        if k == 0:
+            assert ubv[k] == pytest.approx(obj, rel=1e-12)       # empty support
+            continue
+        assert ubv[k] >= obj * (1 - 1e-12)
+        assert ubv[k] <= obj * (1 + 1e-5), (k, ubv[k], obj)
+        bf = oub.fista_backtracking(inst.X, inst.y, S, lam2, M, tol=rtol, max_iter=200)
+        full = np.zeros(inst.p)
+        full[S] = bf
+        ofista = relax.mip_objective(inst.X, inst.y, full, lam0, lam2)
+        assert abs(ubv[k] - ofista) <= 1e-5 * abs(obj), (k, ubv[k], ofista)
+        Q = inst.X[:, S].T @ inst.X[:, S] + 2 * lam2 * np.eye(len(S))
+        lmin = float(np.linalg.eigvalsh(Q)[0])
+        dev = np.sqrt(2 * max(ubv[k] - obj, 0.0) / lmin) + 1e-6
+        assert np.max(np.abs(beta[k][S] - bref[S])) <= dev * 1.01 + 1e-6, k
 
 
 def test_solve_after_upper_batch_reports_its_own_incumbent():

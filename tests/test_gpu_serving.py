@@ -1,11 +1,15 @@
 """Serving: independent solves of different (n, p, lambda) arriving over time are
 admitted under an HBM budget and interleaved on the GPU; each result equals the
 result of the same request solved alone (same support, objective within 1e-8
-relative, both certified to the requested gap)."""
+relative, both certified to the requested gap), and agrees with the FP64 oracle:
+the p = 16 request is the brute-force optimum, every other one is within the
+certified gap of the oracle's own branch-and-bound and is the exact objective of
+the support it returns."""
 import numpy as np
 import pytest
 
 import datagen
+from oracle import bnb as obnb, brute, ub as oub
 
 pytestmark = pytest.mark.gpu
 bnb = pytest.importorskip("paper_2602_04551_b300")
@@ -50,3 +54,20 @@ def test_each_result_same_alone_and_in_the_mix():
         assert res.lb <= res.ub * (1 + 1e-12)
     s = latency_summary(mixed)
     assert s["solves"] == len(reqs) and s["p99_s"] >= s["p50_s"] > 0
+    # against the oracle
+    by_id = {res.rid: res for res in mixed}
+    for r in reqs:
+        res = by_id[r.rid]
+        S = np.nonzero(res.beta)[0]
+        obj, _ = oub.support_objective(r.X, r.y, S, r.lambda0, r.lambda2, r.M)
+        assert res.ub == pytest.approx(obj, rel=1e-9)          # the support's exact value
+        if r.X.shape[1] <= 16:
+            br = brute.solve(r.X, r.y, r.lambda0, r.lambda2, r.M)
+            assert tuple(S) == br.support
+            assert res.ub == pytest.approx(br.objective, rel=1e-8)
+        else:
+            ref = obnb.solve(r.X, r.y, r.lambda0, r.lambda2, r.M, gap=r.gap)
+            assert ref.status in ("optimal", "gap")
+            # both certified to the gap: each is within it of the optimum, hence of the other
+            assert abs(res.ub - ref.ub) <= 2 * r.gap * abs(ref.ub)
+            assert res.lb <= ref.ub * (1 + 1e-12) and ref.lb <= res.ub * (1 + 1e-12)
