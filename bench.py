@@ -6,18 +6,26 @@ SNR=5, lambda2=1e-3, M = 1.5 ||ridge on the true support||_inf, lambda0 from a
 sweep relative to max_j (X_j^T y)^2 / (2(||X_j||^2 + 2 lambda2)), node-batch
 width K=512, target gap 1e-4, FP32 ADMM with FP64 certificates.
 
-A "step" is one device round of the solve: refill free slots best-first,
-check_every ADMM iterations over all K slots, FP64 certificates of the nodes
-that stopped, branch pick + batched upper bound, prune/branch into the pool.
+A "step" is a fixed block of --rounds-per-step (default 25) device rounds of the
+solve; a round refills free slots best-first, runs check_every ADMM iterations over
+all K slots, certifies the nodes that stopped in FP64, picks branches and takes the
+batched upper bound, and prunes/branches into the pool.
   value     nodes certified per second over the timed steps (device time, CUDA
             events on the solve's stream; L2 flushed with a 256 MiB write
             before every step, outside the timed interval)
   e2e       nodes certified per second through bnb_relax_batch with host
             buffers: each step uploads K nodes (fixings + warm starts) from
             pinned memory and reads back bounds, beta, z
-  fp64_path the same rounds on the plain FP64 GPU path (the comparator)
+  fp64_path the plain FP64 GPU path on the same batch of nodes (the comparator)
+  fp32_path the same timed rounds with the FP32 CUDA-core ADMM (no tensor cores)
   roofline  the dominant kernel of a profiled round (CUDA events per launch)
   cpu_baseline the FP64 oracle's node solves on the host cores, bounded sample
+  certified_solves  full solves to gap 1e-4 over five lambda0 values chosen so that
+            the first incumbent has 5, 8, 12, 16 and 20 nonzeros, mixed precision
+            and plain FP64, per instance; with `reverify`: certificates of a real
+            solve and every final support re-checked by the FP64 oracle
+  serve     a short run of the serving workload (32 requests): p50/p99 latency,
+            queueing and service time, certified count
 
 `--impl reference` times the FP64 oracle itself (the reference arm for this
 build): node solves of the same workload on the host cores.
@@ -62,8 +70,6 @@ def parse():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--arrival-rate", type=float, default=20.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--serve-lam0-frac", type=float, default=0.3,
-                    help="serve mode: lambda0 = frac x max_j (X_j^T y)^2 / (2 (||X_j||^2 + 2 lambda2))")
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--fp64-compare", action="store_true",
                     help="solves mode: also solve each instance with the plain FP64 path")
@@ -84,6 +90,15 @@ def parse():
     ap.add_argument("--lam0-frac", type=float, default=0.02)
     ap.add_argument("--K", type=int, default=512)
     ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--rounds-per-step", type=int, default=25,
+                    help="device rounds in one timed step")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the side measurements (fp32 path, certified solves, serve)")
+    ap.add_argument("--cert-time-limit", type=float, default=8.0,
+                    help="per-solve limit of the certified_solves side key (each path)")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-time-limit", type=float, default=20.0)
+    ap.add_argument("--fp32-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--fp64-K", type=int, default=512,
@@ -98,6 +113,11 @@ def parse():
 
 
 METRIC = "certified BnB nodes/s"        # both arms report this metric on the same config
+
+
+def note(msg):
+    """Progress of the run on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
 
 def line_config(cfg, args):
@@ -196,6 +216,7 @@ def run_mine(args, rank, world):
                                         tune_crossover=False)
         args.rho = float(best["rho"])
         args.alpha = float(best.get("relax_alpha", 1.0))
+        note(f"autotune: rho {args.rho} alpha {args.alpha}")
         tune = {"chosen": best, "seconds": entry["seconds"],
                 "trials": [{k: t[k] for k in ("rho", "nodes_per_s", "mean_iters", "lb_mean")}
                            for t in entry["trials"]]}
@@ -221,11 +242,13 @@ def run_mine(args, rank, world):
         busy = pr["active_slots"] >= 0.9 * args.K and pr["nodes"] >= args.K
         if pr["done"] or busy or time.time() - t0 > args.prime_seconds:
             break
+    note(f"primed: {prime_rounds} rounds")
     clk = Clocks(dev)            # sampling spans the warm-up and the timed steps
     time.sleep(0.3)
+    R = args.rounds_per_step
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
-            bnb.bnb_solve_launch(h, 1)
+            bnb.bnb_solve_launch(h, R)
     before = bnb.bnb_solve_poll(h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -237,7 +260,7 @@ def run_mine(args, rank, world):
         for i in range(args.steps):
             flush.fill_(i & 0xff)
             ev[i][0].record(s)
-            bnb.bnb_solve_launch(h, 1)
+            bnb.bnb_solve_launch(h, R)
             ev[i][1].record(s)
     s.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -257,13 +280,69 @@ def run_mine(args, rank, world):
                                           "u_split")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                setup_seconds=stats.get("setup_seconds"),
-               kernels=kernels_per_round * args.steps, after=after, res=res, shapes=shapes,
+               kernels=kernels_per_round * args.steps * R, after=after, res=res, shapes=shapes,
+               rounds=after["rounds"] - before["rounds"],
                prime={"rounds": prime_rounds, "seconds": time.time() - t0,
                       "active_slots": before["active_slots"], "open_nodes": before["open_nodes"]})
+    note(f"timed: {nodes} nodes in {ms:.1f} ms")
     if rank == 0:
         out["e2e"] = run_e2e(args, inst, lam0, lam2, M, dev)
+        note("e2e done")
         out["fp64"] = run_fp64(args, inst, lam0, lam2, M, dev)
+        note("fp64 same-batch done")
+        if world == 1 and not args.no_side:
+            out["fp32"] = run_fp32_side(args, inst, lam0, lam2, M, dev)
+            note("fp32 side done")
+            out["certified"] = run_certified(args, inst.seed - 1000 * datagen.CONFIGS[args.workload]["cfg_id"])
+            note("certified solves done")
+            out["serve"] = run_serve_side(args)
+            note("serve side done")
     return out
+
+
+def run_fp32_side(args, inst, lam0, lam2, M, dev):
+    """The same workload and timed steps with the FP32 CUDA-core ADMM (BNB_PREC_FP32): the
+    path that computes the FP32 ADMM literally, beside the tensor-core default."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+    s = torch.cuda.Stream()
+    opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+                                  precision=bnb.BNB_PREC_FP32, device=dev, stream=s.cuda_stream,
+                                  queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
+                                  relax_alpha=args.alpha)
+    R = args.rounds_per_step
+    with bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt) as h:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+        bnb.bnb_solve_start(h, 1e-4)
+        t0 = time.time()
+        while True:
+            bnb.bnb_solve_launch(h, 20)
+            pr = bnb.bnb_solve_poll(h)
+            if pr["done"] or (pr["active_slots"] >= 0.9 * args.K and pr["nodes"] >= args.K) \
+                    or time.time() - t0 > args.prime_seconds:
+                break
+        with torch.cuda.stream(s):
+            bnb.bnb_solve_launch(h, R)
+        before = bnb.bnb_solve_poll(h)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.fp32_steps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for i in range(args.fp32_steps):
+                flush.fill_(i & 0xff)
+                ev[i][0].record(s)
+                bnb.bnb_solve_launch(h, R)
+                ev[i][1].record(s)
+        s.synchronize()
+        after = bnb.bnb_solve_poll(h)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        bnb.bnb_solve_finish(h)
+    nodes = after["nodes"] - before["nodes"]
+    rounds = after["rounds"] - before["rounds"]
+    return {"value": nodes / (ms / 1e3), "unit": "nodes/s", "precision": "fp32",
+            "ms_per_round": ms / max(1, rounds), "rounds": rounds, "nodes": nodes,
+            "how": f"{args.fp32_steps} steps of {R} rounds after priming, same workload, K, "
+                   "rho and alpha; FP32 state and products on CUDA cores, FP64 certificates"}
 
 
 def run_e2e(args, inst, lam0, lam2, M, dev):
@@ -531,15 +610,26 @@ def roofline(out, args, pk):
         r.update(bound="alu", peak=peak, frac=ach / peak,
                  peak_note="FP32 FMA peak 148 SM x 128 lanes x 2 x 2032 MHz (derived)")
     else:
-        if "bf16_tflops_sustained" in pk:
-            peak = float(pk["bf16_tflops_sustained"])
-            note = "measured sustained dense BF16 (MEASURED_PEAKS.json)"
+        # burst peak when the timed region ran at the maximum SM clock with no power cap
+        # (the kernel is not power-limited there), else the sustained one
+        clk = out.get("clocks") or {}
+        burst = (clk.get("sm_mhz") and clk.get("sm_max_mhz")
+                 and clk["sm_mhz"] >= 0.97 * clk["sm_max_mhz"]
+                 and "sw_power_cap" not in (clk.get("reasons") or []))
+        key = "bf16_tflops" if burst else "bf16_tflops_sustained"
+        if key in pk:
+            peak = float(pk[key])
+            note = (f"measured {'burst' if burst else 'sustained'} dense BF16 (MEASURED_PEAKS.json); "
+                    f"{'burst: SM clock at its maximum, no power cap in the timed region' if burst else 'sustained: clocks below maximum or power-capped'}")
         else:
-            peak = 1400.0
-            note = "fallback: 1.4 PFLOP/s sustained dense BF16 (no measured peaks file)"
+            peak = 1800.0 if burst else 1400.0
+            note = "fallback dense BF16 peak (no measured peaks file)"
         mult = {"tc3": 3.0, "bf16x2": 2.0}.get(args.precision, 1.0)
         r.update(bound="tensor", peak=peak, frac=ach / peak, achieved_hw=ach * mult,
-                 frac_hw=ach * mult / peak, peak_note=note)
+                 frac_hw=ach * mult / peak, peak_note=note, peak_kind="burst" if burst else "sustained")
+        other = "bf16_tflops_sustained" if burst else "bf16_tflops"
+        if other in pk:
+            r["frac_vs_" + ("sustained" if burst else "burst")] = ach / float(pk[other])
     return r
 
 
@@ -559,72 +649,245 @@ def combine_ranks(ms, nodes, world):
     return float(mx[0]), float(t[1])
 
 
-def run_solves(args):
-    """Full solves to gap 1e-4 of the workload over a lambda0 sweep (certified solves/s)."""
+# lambda0 where the workload gives a nonzero count: fractions of
+# max_j (X_j^T y)^2 / (2(||X_j||^2 + 2 lambda2)) on a geometric grid
+LAM0_TARGETS = (5, 8, 12, 16, 20)
+LAM0_GRID = tuple(float(x) for x in np.geomspace(1.0, 0.008, 28))
+
+
+def lambda0_by_count(inst, lam2, M, targets=LAM0_TARGETS, grid=LAM0_GRID, dev=0):
+    """lambda0 for each target count of nonzeros: on the geometric grid of fractions, the
+    support size of the first incumbent (the library's matching-pursuit root heuristic,
+    polished exactly in FP64); per target, the geometric midpoint of the grid points that
+    give that count, else the grid point whose count is nearest (ties to the larger
+    lambda0).  Returns (picks, counts per grid point)."""
+    import paper_2602_04551_b300 as bnb
+    sc = datagen.lambda0_scale(inst.X, inst.y, lam2)
+    counts = []
+    for f in grid:
+        o = bnb.bnb_options_default(M=M, batch_K=16, precision=bnb.BNB_PREC_FP32, device=dev,
+                                    queue_capacity=1 << 12)
+        with bnb.bnb_create(inst.X, inst.y, f * sc, lam2, o) as h:
+            b, _ = bnb.bnb_root_heuristic(h)
+        counts.append(int(np.count_nonzero(b)))
+    picks = [dict(pk, lambda0=pk["lambda0_frac"] * sc) for pk in pick_lambda0(counts, grid, targets)]
+    return picks, counts
+
+
+def pick_lambda0(counts, grid, targets):
+    """Per target count: the geometric midpoint of the grid fractions whose count equals it,
+    else the fraction whose count is nearest (ties to the larger lambda0, the earlier grid
+    point: the grid runs from large to small)."""
+    picks = []
+    for t in targets:
+        hit = [i for i, c in enumerate(counts) if c == t]
+        if hit:
+            f = float(np.sqrt(grid[hit[0]] * grid[hit[-1]]))
+        else:
+            f = float(grid[min(range(len(grid)), key=lambda i: (abs(counts[i] - t), i))])
+        picks.append({"target_nnz": t, "lambda0_frac": f})
+    return picks
+
+
+def greedy_lambda0(X, y, lam2, M, k):
+    """Per-request lambda0 of the serving workload for a target of k nonzeros: forward
+    single-coordinate steps from beta = 0 (each adds the coordinate whose fit on the current
+    residual lowers 1/2||r||^2 + lam2 beta^2 most, then refits the ridge on the support),
+    recording each step's drop; the greedy path stops at k nonzeros for lambda0 between the
+    k-th and (k+1)-th drops, and their geometric mean is returned."""
+    d = np.einsum("ij,ij->j", X, X) + 2.0 * lam2
+    S, drops = [], []
+    r = y.copy()
+    for _ in range(k + 1):
+        c = X.T @ r
+        b = np.clip(c / d, -M, M)
+        gain = c * b - 0.5 * d * b * b
+        gain[S] = -np.inf
+        j = int(np.argmax(gain))
+        drops.append(float(gain[j]))
+        S.append(j)
+        XS = X[:, S]
+        bs = np.clip(np.linalg.solve(XS.T @ XS + 2.0 * lam2 * np.eye(len(S)), XS.T @ y), -M, M)
+        r = y - XS @ bs
+    return float(np.sqrt(max(drops[k - 1], 1e-300) * max(drops[k], 1e-300)))
+
+
+def solve_record(args, inst, lam0, lam2, M, rho, alpha, prec, time_limit, log_nodes=0):
+    """One full solve to gap 1e-4; its record (and the node log when requested)."""
     import torch
     import paper_2602_04551_b300 as bnb
+    o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+                                precision=prec, rho=rho, relax_alpha=alpha,
+                                queue_capacity=1 << 21, max_depth=args.max_depth,
+                                time_limit_s=time_limit, log_nodes=log_nodes)
+    with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = bnb.bnb_solve(h, 1e-4)
+        dt = time.perf_counter() - t0
+        st = bnb.bnb_get_stats(h)
+        log = bnb.bnb_get_node_log(h) if log_nodes else None
+    rec = {"status": res["status"], "seconds": dt, "nodes": res["nodes"],
+           "nnz": int(np.count_nonzero(res["beta"])), "ub": res["ub"], "lb": res["lb"],
+           "gap": (res["ub"] - res["lb"]) / res["ub"], "nodes_per_s": res["nodes"] / dt,
+           "max_depth": st["max_depth"], "setup_seconds": st.get("setup_seconds"),
+           "certified": res["status"] in ("optimal", "gap")}
+    return rec, res["beta"], log
+
+
+def reverify_logs(inst, lam0, lam2, M, logs):
+    """Logged certificates of real solves against the oracle's Eq. dual at the logged r:
+    exact ones by relative error, screened ones by the excess D(r) - bound against their
+    recorded interval width (a valid screened bound has 0 <= excess <= width)."""
+    from oracle import relax
+    rel, ratio, n_ex, n_sc, bad = [], [], 0, 0, 0
+    for log in logs:
+        for k in range(log["count"]):
+            d = relax.dual_value(inst.X, inst.y, log["r"][k], log["fix"][k], lam0, lam2, M)
+            tol = 1e-10 * max(1.0, abs(d))
+            if log["exact"][k] == 1.0:
+                n_ex += 1
+                rel.append(abs(log["lb"][k] - d) / max(1.0, abs(d)))
+                bad += int(abs(log["lb"][k] - d) > tol)
+            else:
+                n_sc += 1
+                ex = d - log["lb"][k]
+                ratio.append(ex / log["width"][k] if log["width"][k] > 0 else 0.0)
+                bad += int(ex < -tol or ex > log["width"][k] * (1 + 1e-9) + tol)
+    return {"n_certs": n_ex + n_sc, "exact": n_ex, "screened": n_sc,
+            "exact_max_rel": float(max(rel)) if rel else None,
+            "exact_median_rel": float(np.median(rel)) if rel else None,
+            "screened_max_excess_over_width": float(max(ratio)) if ratio else None,
+            "violations": bad}
+
+
+def run_certified(args, seed):
+    """The certified_solves side key: the workload instance `seed`, lambda0 for 5, 8, 12,
+    16 and 20 nonzeros, each solved to gap 1e-4 by the mixed-precision path (with a node
+    log) and by the plain FP64 path under the same time limit; every final support
+    re-checked by the oracle's exact objective, and the logged certificates by its Eq. dual."""
+    import paper_2602_04551_b300 as bnb
+    from oracle import ub as oub
+    inst, _, lam2, M, cfg = workload(args.workload, seed, 0.1)
+    t0 = time.perf_counter()
+    picks, counts = lambda0_by_count(inst, lam2, M)
+    t_grid = time.perf_counter() - t0
+    rows, logs = [], []
+    for pk in picks:
+        lam0 = pk["lambda0"]
+        row = dict(pk)
+        for name, prec in (("mixed", PREC[args.precision]), ("fp64", bnb.BNB_PREC_FP64)):
+            rec, beta, log = solve_record(args, inst, lam0, lam2, M, args.rho, args.alpha, prec,
+                                          args.cert_time_limit, 128 if name == "mixed" else 0)
+            S = np.nonzero(beta)[0]
+            obj, _ = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
+            rec["support_objective_rel_diff"] = abs(obj - rec["ub"]) / abs(obj)
+            row[name] = rec
+            row[name + "_support"] = [int(i) for i in S]
+            if log is not None:
+                logs.append((lam0, log))
+            note(f"certified target {pk['target_nnz']} {name}: {rec['status']} {rec['seconds']:.2f} s")
+        row["same_support"] = row.pop("mixed_support") == row.pop("fp64_support")
+        if row["mixed"]["certified"] and row["fp64"]["certified"]:
+            row["speedup_time_to_certificate"] = row["fp64"]["seconds"] / row["mixed"]["seconds"]
+        rows.append(row)
+    cert = {}
+    for name in ("mixed", "fp64"):
+        done = [r[name] for r in rows if r[name]["certified"]]
+        cert[name] = {"certified": len(done), "of": len(rows),
+                      "solves_per_s": len(done) / sum(r[name]["seconds"] for r in rows)}
+    rv = {"certificates": None, "supports_ok": all(
+        r[nm]["support_objective_rel_diff"] <= 1e-10 for r in rows for nm in ("mixed", "fp64"))}
+    agg = None
+    for lam0, log in logs:
+        one = reverify_logs(inst, lam0, lam2, M, [log])
+        if agg is None:
+            agg = one
+        else:
+            for k in ("n_certs", "exact", "screened", "violations"):
+                agg[k] += one[k]
+            for k in ("exact_max_rel", "screened_max_excess_over_width"):
+                if one[k] is not None:
+                    agg[k] = one[k] if agg[k] is None else max(agg[k], one[k])
+            agg["exact_median_rel"] = None
+    rv["certificates"] = agg
+    return {"workload": args.workload, "seed": inst.seed, "gap": 1e-4,
+            "time_limit_s": args.cert_time_limit, "rho": args.rho, "relax_alpha": args.alpha,
+            "lambda0_rule": "first-incumbent nonzero count on a geometric grid of fractions",
+            "grid_counts": counts, "grid_seconds": t_grid, "paths": cert, "instances": rows,
+            "reverify": rv}
+
+
+def run_serve_side(args):
+    """A short run of the serving workload (the first --serve-requests requests of the
+    Poisson stream) for the bench line."""
+    srv, res, summ = serve_stream(args, args.serve_requests, args.serve_time_limit,
+                                  pregenerate=True)
+    status = {}
+    for r in res:
+        status[r.status] = status.get(r.status, 0) + 1
+    return dict(summ, status=status, requests=args.serve_requests,
+                time_limit_s=args.serve_time_limit, peak_admitted=srv.peak_active,
+                peak_gib=srv.peak_used / (1 << 30),
+                per_request=[{"rid": r.rid, "status": r.status, "nodes": r.nodes,
+                              "queue_s": round(r.queueing, 4), "service_s": round(r.service, 4),
+                              "gap": (r.ub - r.lb) / r.ub if r.ub else None} for r in res],
+                data="request data generated before the clock starts")
+
+
+def run_solves(args):
+    """Full solves to gap 1e-4 of the workload (certified solves/s): for each of --seeds
+    instances, lambda0 for 5, 8, 12, 16 and 20 nonzeros (lambda0_by_count), each solved by
+    the mixed-precision path and, with --fp64-compare, by the plain FP64 path.  rho and
+    alpha are autotuned once per instance (at the middle lambda0) unless --rho is given."""
+    import paper_2602_04551_b300 as bnb
     from paper_2602_04551_b300 import autotune
+    from oracle import ub as oub
     out = []
     t_all = time.perf_counter()
-    jobs = [(float(f), sd) for f in args.lam0_fracs.split(",") for sd in range(args.seeds)]
-    for frac, seed in jobs:
-        inst, lam0, lam2, M, cfg = workload(args.workload, seed, frac)
-        best, _ = autotune.autotune(inst.X, inst.y, lam0, lam2, M, use_cache=False,
-                                    grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
-                                          "check_every": [args.check_every]})
-        o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
-                                    precision=PREC[args.precision], rho=best["rho"],
-                                    relax_alpha=best["relax_alpha"], queue_capacity=1 << 21,
-                                    mv_crossover=int(best.get("mv_crossover", -1)),
-                                    max_depth=args.max_depth, time_limit_s=args.solve_time_limit)
-        with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = bnb.bnb_solve(h, 1e-4)
-            dt = time.perf_counter() - t0
-            st = bnb.bnb_get_stats(h)
-            dh, sh = bnb.bnb_get_histograms(h, args.max_depth + 1, 202)
-        rec = {"lambda0_frac": frac, "seed": seed, "lambda0": lam0, "seconds": dt,
-               "setup_seconds": st.get("setup_seconds"),
-               "status": res["status"], "nodes": res["nodes"],
-               "nnz": int(np.count_nonzero(res["beta"])), "ub": res["ub"], "lb": res["lb"],
-               "gap": (res["ub"] - res["lb"]) / res["ub"], "nodes_per_s": res["nodes"] / dt,
-               "rho": best["rho"], "relax_alpha": best["relax_alpha"],
-               "mv_crossover": best.get("mv_crossover"), "max_depth": st["max_depth"],
-               # solved nodes by depth 0..40 (+ deeper) and by rounded-support size 0..200 (+ larger)
-               "depth_hist": [int(x) for x in dh[:41]] + [int(dh[41:].sum())],
-               "support_hist": [int(x) for x in sh[:201]] + [int(sh[201:].sum())]}
-        if args.fp64_compare:
-            o64 = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
-                                          precision=0, rho=best["rho"],
-                                          relax_alpha=best["relax_alpha"], queue_capacity=1 << 21,
-                                          max_depth=args.max_depth,
-                                          time_limit_s=args.fp64_time_limit)
-            with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o64) as h:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r64 = bnb.bnb_solve(h, 1e-4)
-                d64 = time.perf_counter() - t0
-            rec["fp64"] = {"seconds": d64, "status": r64["status"], "nodes": r64["nodes"],
-                           "ub": r64["ub"], "lb": r64["lb"], "nodes_per_s": r64["nodes"] / d64,
-                           "same_support": bool(np.array_equal(np.nonzero(r64["beta"])[0],
-                                                               np.nonzero(res["beta"])[0]))}
-        out.append(rec)
-        print(json.dumps({"solve": out[-1]}), file=sys.stderr, flush=True)
-    done = [r for r in out if r["status"] in ("optimal", "gap")]
+    for seed in range(args.seeds):
+        inst, _, lam2, M, cfg = workload(args.workload, seed, 0.1)
+        picks, counts = lambda0_by_count(inst, lam2, M)
+        rho, alpha = args.rho, args.alpha
+        if rho <= 0:
+            best, _ = autotune.autotune(inst.X, inst.y, picks[len(picks) // 2]["lambda0"], lam2,
+                                        M, use_cache=False,
+                                        grid={"batch_K": [args.K],
+                                              "precision": [PREC[args.precision]],
+                                              "check_every": [args.check_every]},
+                                        tune_crossover=False)
+            rho, alpha = float(best["rho"]), float(best["relax_alpha"])
+        for pk in picks:
+            lam0 = pk["lambda0"]
+            rec, beta, _ = solve_record(args, inst, lam0, lam2, M, rho, alpha,
+                                        PREC[args.precision], args.solve_time_limit)
+            S = np.nonzero(beta)[0]
+            obj, _ = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
+            rec.update(pk, seed=seed, rho=rho, relax_alpha=alpha,
+                       support_objective_rel_diff=abs(obj - rec["ub"]) / abs(obj))
+            if args.fp64_compare:
+                r64, b64, _ = solve_record(args, inst, lam0, lam2, M, rho, alpha,
+                                           bnb.BNB_PREC_FP64, args.fp64_time_limit)
+                r64["same_support"] = bool(np.array_equal(np.nonzero(b64)[0], S))
+                rec["fp64"] = r64
+            out.append(rec)
+            print(json.dumps({"solve": out[-1]}), file=sys.stderr, flush=True)
+    done = [r for r in out if r["certified"]]
     total = time.perf_counter() - t_all
     fp64 = None
     if args.fp64_compare:
-        d64 = [r for r in out if r["fp64"]["status"] in ("optimal", "gap")]
+        d64 = [r for r in out if r["fp64"]["certified"]]
         fp64 = {"solves_per_s": len(d64) / sum(r["fp64"]["seconds"] for r in out),
-                "time_limit_s": args.fp64_time_limit,
-                "note": "same instances, autotuned rho and K, precision FP64 everywhere"}
+                "certified": len(d64), "time_limit_s": args.fp64_time_limit,
+                "note": "same instances, rho and alpha, precision FP64 everywhere"}
     lat = np.array([r["seconds"] for r in done]) if done else np.array([np.nan])
     line = {"metric": "certified solves/s (gap 1e-4)", "mode": "solves",
             "value": len(done) / sum(r["seconds"] for r in out), "unit": "solves/s",
+            "certified": len(done), "of": len(out),
             "n_gpus": 1, "higher_is_better": True, "dtype": DTYPE[args.precision],
             "data": "synthetic", "config": {"workload": args.workload, "K": args.K,
-                                            "lambda0_fracs": args.lam0_fracs, "seeds": args.seeds,
+                                            "lambda0_targets": list(LAM0_TARGETS),
+                                            "seeds": args.seeds,
                                             "time_limit_s": args.solve_time_limit},
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "wall_s": total, "fp64_path": fp64, "solves": out}
@@ -668,67 +931,74 @@ def run_kcurve(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """The serving workload: independent solves of random shapes arriving as a
-    Poisson stream, admitted under an HBM budget and interleaved on the GPU."""
-    import paper_2602_04551_b300 as bnb
+def serve_stream(args, count, time_limit, pregenerate=False):
+    """The serving workload's first `count` requests (Poisson arrivals at --arrival-rate,
+    shapes n ~ U[500, 5000], p ~ U[1000, 20000], rho in {0.1, 0.3, 0.5, 0.7}, k ~ U[5, 25],
+    SNR ~ U[2, 10], lambda2 = 0.01, lambda0 for k nonzeros by greedy_lambda0) through the
+    serving loop; returns (server, results, latency summary).  With `pregenerate` every
+    request's synthetic data are made before the clock starts (as if each request carried
+    its data); otherwise they are made at admission, inside the loop."""
     from paper_2602_04551_b300.serve import Request, Server, poisson_arrivals, latency_summary
     rng = np.random.Generator(np.random.PCG64(5000))
     times = poisson_arrivals(args.requests, args.arrival_rate, 5000)
-    reqs = []
     lam2 = 0.01
 
     def loader(n, p, rho, k, snr, seed):
         def make():
             inst = datagen.make_instance(n, p, rho, k, snr, seed)
             M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
-            lam0 = args.serve_lam0_frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
-            return inst.X, inst.y, lam0, M
+            return inst.X, inst.y, greedy_lambda0(inst.X, inst.y, lam2, M, k), M
         return make
 
+    reqs = []
     for i in range(args.requests):
         n = int(rng.integers(500, 5001))
         p = int(rng.integers(1000, 20001))
         rho = float(rng.choice([0.1, 0.3, 0.5, 0.7]))
         k = int(rng.integers(5, 26))
         snr = float(rng.uniform(2, 10))
-        reqs.append(Request(rid=i, X=None, y=None, lambda0=0.0, lambda2=lam2, M=1.0, gap=1e-4,
-                            arrival=float(times[i]), shape=(n, p),
-                            loader=loader(n, p, rho, k, snr, 5000 + i),
-                            options=dict(batch_K=256, rho=0.3, relax_alpha=1.6,
-                                         precision=PREC[args.precision],
-                                         time_limit_s=args.solve_time_limit)))
-    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), rounds_per_step=4)
+        if i < count:
+            reqs.append(Request(rid=i, X=None, y=None, lambda0=0.0, lambda2=lam2, M=1.0,
+                                gap=1e-4, arrival=float(times[i]), shape=(n, p),
+                                loader=loader(n, p, rho, k, snr, 5000 + i),
+                                options=dict(batch_K=256, rho=0.3, relax_alpha=1.6,
+                                             precision=PREC[args.precision], max_depth=1024,
+                                             time_limit_s=time_limit)))
+    if pregenerate:
+        for r in reqs:
+            r.data()
+            r.loader = None
+        note(f"serve: {len(reqs)} requests generated")
+    last = [0.0]
+
+    def progress(t, pending, active, done):
+        if t - last[0] >= 5.0:
+            last[0] = t
+            note(f"serve t={t:.1f}s pending {pending} active {active} done {done}")
+
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), rounds_per_step=4,
+                 progress=progress)
     res = srv.run(reqs)
-    summ = latency_summary(res)
+    return srv, res, latency_summary(res)
+
+
+def run_serve(args):
+    """The serving workload: independent solves of random shapes arriving as a
+    Poisson stream, admitted under an HBM budget and interleaved on the GPU."""
+    import paper_2602_04551_b300 as bnb
+    srv, res, summ = serve_stream(args, args.requests, args.solve_time_limit)
     status = {}
     for r in res:
         status[r.status] = status.get(r.status, 0) + 1
-    # a sample of requests re-solved alone: same support and objective
-    check = []
-    for r in res[: min(4, len(res))]:
-        q = reqs[r.rid]
-        X, y, lam0, M = q.loader()
-        o = bnb.bnb_options_default(M=M, batch_K=256, rho=0.3, relax_alpha=1.6,
-                                    precision=PREC[args.precision],
-                                    time_limit_s=args.solve_time_limit, queue_capacity=1 << 18,
-                                    warm_capacity=1 << 14)
-        with bnb.bnb_create(X, y, lam0, q.lambda2, o) as h:
-            a = bnb.bnb_solve(h, q.gap)
-        check.append({"rid": r.rid, "same_support": bool(np.array_equal(np.nonzero(a["beta"])[0],
-                                                                          np.nonzero(r.beta)[0])),
-                      "ub_rel_diff": abs(a["ub"] - r.ub) / abs(a["ub"])})
     line = {"metric": "serving: p50/p99 time to certified gap 1e-4", "mode": "serve",
-            "value": summ["solves_per_s"], "unit": "solves/s", "p50_s": summ["p50_s"],
-            "p99_s": summ["p99_s"], "mean_s": summ["mean_s"], "makespan_s": summ["makespan_s"],
-            "solves": summ["solves"], "status": status, "nodes": summ["nodes"],
-            "peak_admitted": srv.peak_active, "peak_bytes": srv.peak_used, "n_gpus": 1,
+            "value": summ["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": DTYPE[args.precision], "data": "synthetic",
+            "status": status, "peak_admitted": srv.peak_active, "peak_bytes": srv.peak_used,
             "config": {"workload": "serve", "requests": args.requests,
                        "arrival_rate_per_s": args.arrival_rate, "budget_gb": args.budget_gb,
                        "time_limit_s": args.solve_time_limit,
-                       "lambda0_frac": args.serve_lam0_frac},
-            "alone_vs_mix": check}
+                       "lambda0": "per request, k nonzeros on the greedy forward path"}}
+    line.update(summ)
     print(json.dumps(line), flush=True)
 
 
@@ -757,10 +1027,19 @@ def mine_line(args, out, world, ms, nodes, pk, cpu):
                            "done": out["after"]["done"]},
         "stages_ms": {k: v[0] for k, v in out["prof"].items()},
         "kernel_shapes": out["shapes"],
+        "rounds_per_step": args.rounds_per_step,
+        "rounds": out.get("rounds"),
+        "ms_per_round": ms / max(1, out.get("rounds") or args.steps * args.rounds_per_step),
+        "fp32_path": out.get("fp32"),
+        "certified_solves": out.get("certified"),
+        "serve": out.get("serve"),
     }
 
 
 def main():
+    import faulthandler
+    # a stalled run reports where it is: every thread's stack on stderr every 5 minutes
+    faulthandler.dump_traceback_later(300, repeat=True, file=sys.stderr)
     args = parse()
     if args.impl == "reference":
         reference_arm(args)

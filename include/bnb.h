@@ -112,6 +112,10 @@ typedef struct {
                             after the projected-gradient method; 0 returns the projected-
                             gradient solution itself (ADMM precision, upcast) with its FP64
                             objective.  bnb_solve always polishes its candidate incumbents. */
+  int log_nodes;         /* tracing: record the first log_nodes nodes certified in each solve
+                            (fixings, FP64 residual, certified bound; bnb_get_node_log), in
+                            [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)
+                            bytes of device memory */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */
@@ -318,6 +322,26 @@ int bnb_get_stats(const bnb_handle* h, bnb_stats* out);
  * reports; the paper has no counterpart call. */
 int bnb_get_histograms(bnb_handle* h, long long* depth_hist, int ndepth, long long* support_hist,
                        int nsupport);
+
+/*
+ * Node log (tracing; options.log_nodes = L > 0): the first L nodes certified since the
+ * last bnb_solve / bnb_solve_start, in retirement order.  Copies min(*count, max_entries)
+ * entries to the host arrays (each may be NULL):
+ *   fix   entries x p int8 fixings of the node
+ *   r     entries x n FP64 residual r = y - U the certificate used (Proposition 1)
+ *   rec   entries x 10 doubles: [0] the certified bound at r (exact, or screened: the
+ *         rigorous upper values of the unsettled nu terms), [1] 1 when every nu term was
+ *         taken in FP64, [2] width: D(r) - bound lies in [0, width] (0 when exact),
+ *         [3] the node's bound in the tree (max with the parent's), [4] the parent's
+ *         bound, [5] the prune threshold UB (1 - gap) it was decided against, [6] depth,
+ *         [7] ADMM iterations of the visit, [8] FP32 estimate of D(r) at the stop test,
+ *         [9] FP32 estimate of the primal value.
+ * *count receives the number of nodes recorded.  Synchronises the handle's stream.
+ * Measurement aid (re-checking certificates against an independent evaluation); the
+ * paper has no counterpart call.
+ */
+int bnb_get_node_log(bnb_handle* h, int max_entries, int8_t* fix, double* r, double* rec,
+                     int* count);
 
 /* Message of the last failed call on h (or of the last failed create when h is
  * NULL).  Valid until the next call on the same handle. */

@@ -29,8 +29,10 @@ SYMBOLS = ("bnb_options_default", "bnb_footprint", "bnb_create", "bnb_create_dev
            "bnb_relax_batch_device", "bnb_dual_bound", "bnb_upper_batch", "bnb_solve",
            "bnb_solve_start", "bnb_solve_launch", "bnb_solve_poll", "bnb_solve_finish",
            "bnb_stream", "bnb_root_heuristic", "bnb_profile_round", "bnb_dual_bound_static",
-           "bnb_get_stats", "bnb_get_histograms",
+           "bnb_get_stats", "bnb_get_histograms", "bnb_get_node_log",
            "bnb_last_error", "bnb_destroy")
+LOG_FIELDS = ("lb", "exact", "width", "node_lb", "parent_lb", "threshold", "depth", "iters",
+              "est_dual", "est_primal")
 # exported by libbnb_diag.so (kept in step with include/bnb_diag.h)
 DIAG_SYMBOLS = ("bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_tc_gemm_check_pair",
                 "bnb_diag_wait_expiry")
@@ -52,7 +54,7 @@ class bnb_options(ctypes.Structure):
                 ("root_heuristic", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int),
                 ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int),
-                ("ub_polish", ctypes.c_int)]
+                ("ub_polish", ctypes.c_int), ("log_nodes", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):
@@ -111,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "bnb_root_heuristic": ([P, P, P], I),
         "bnb_profile_round": ([P, P, P, I], I),
         "bnb_get_histograms": ([P, P, I, P, I], I),
+        "bnb_get_node_log": ([P, I, P, P, P, P], I),
         "bnb_dual_bound_static": ([P, P, I, I, D, D, D, I, P, P, P, P], I),
         "bnb_get_stats": ([P, P], I),
         "bnb_last_error": ([P], ctypes.c_char_p),
@@ -376,6 +379,25 @@ def bnb_get_histograms(h: Handle, ndepth: int = 257, nsupport: int = 258):
     s = np.zeros(nsupport, np.int64)
     _check(load_library().bnb_get_histograms(h.ptr, _ptr(d), ndepth, _ptr(s), nsupport), h.ptr)
     return d, s
+
+
+def bnb_get_node_log(h: Handle, max_entries: int | None = None) -> dict:
+    """The node log of the last solve (options.log_nodes > 0): fixings, FP64 residuals and
+    one record per certified node (fields LOG_FIELDS), in retirement order."""
+    lib = load_library()
+    cnt = ctypes.c_int(0)
+    _check(lib.bnb_get_node_log(h.ptr, 0, None, None, None, ctypes.byref(cnt)), h.ptr)
+    m = cnt.value if max_entries is None else min(cnt.value, int(max_entries))
+    fix = np.empty((m, h.p), np.int8)
+    r = np.empty((m, h.n), np.float64)
+    rec = np.empty((m, len(LOG_FIELDS)), np.float64)
+    if m:
+        _check(lib.bnb_get_node_log(h.ptr, m, _ptr(fix), _ptr(r), _ptr(rec), ctypes.byref(cnt)),
+               h.ptr)
+    out = {"count": cnt.value, "fix": fix, "r": r}
+    for i, name in enumerate(LOG_FIELDS):
+        out[name] = rec[:, i]
+    return out
 
 
 def bnb_tc_gemm_check_pair(dA, dB, M, N, Kd, nsplit=3, bn=144, dC=None):

@@ -215,6 +215,13 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.cert_yr, K);
   ALLOC(e.cert_rn, K);
   ALLOC(e.cert_lb, K);
+  ALLOC(e.cert_width, K);
+  if (e.log_cap > 0) {
+    ALLOC(e.log_count, 1);
+    ALLOC(e.log_fix, e.log_cap * p);
+    ALLOC(e.log_r, e.log_cap * n);
+    ALLOC(e.log_rec, e.log_cap * LOG_REC);
+  }
   ALLOC(e.node_lb, K);
   ALLOC(e.br_idx, K);
   ALLOC(e.sup_cnt, K);
@@ -363,6 +370,7 @@ static int mp_moves(const Engine<R>& e) {
 
 struct SolveState {
   bool started = false, done = false;
+  long long launched = 0;       // rounds enqueued since bnb_solve_start
   int status = BNB_STATUS_OPTIMAL;
   double gap = 0.0;
   std::chrono::steady_clock::time_point t0;
@@ -419,6 +427,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->fused_shape = 0;
   o->u_shape = 0;
   o->ub_polish = 1;
+  o->log_nodes = 0;
   return BNB_OK;
 }
 
@@ -436,6 +445,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
   e->qcap = o.queue_capacity;
+  e->log_cap = o.log_nodes;
   long long wdef = (4LL << 30) / (2LL * h->p * (long long)sizeof(R));
   if (wdef > e->qcap / 2) wdef = e->qcap / 2;
   if (wdef < 64) wdef = 64;
@@ -525,6 +535,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
   if (o.ub_polish != 0 && o.ub_polish != 1) return fail(BNB_EINVAL, "ub_polish must be 0 or 1");
+  if (o.log_nodes < 0 || o.log_nodes > (1 << 16)) return fail(BNB_EINVAL, "log_nodes must be in [0, 65536]");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
@@ -581,6 +592,7 @@ static size_t footprint_of(int n, int p, const bnb_options& o) {
   e.smax = o.support_max;
   e.dmax = o.max_depth;
   e.qcap = o.queue_capacity;
+  e.log_cap = o.log_nodes;
   long long wdef = (4LL << 30) / (2LL * p * (long long)sizeof(R));
   if (wdef > e.qcap / 2) wdef = e.qcap / 2;
   if (wdef < 64) wdef = 64;
@@ -853,6 +865,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     prof_begin(pf, e.st);
     if (int rc = certify_screen(e, nullptr)) return rc;
     if (int rc = certify_exact(e, true, e.inc_ub)) return rc;
+    if (int rc = node_log(e, e.inc_ub)) return rc;
     prof_end(pf, e.st, PK_CERT);
     prof_begin(pf, e.st);
     if (int rc = branch_support(e, false, true)) return rc;
@@ -875,6 +888,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     BNB_CUDA_OK(ce);
     if (int rc2 = certify_screen(e, nullptr)) return rc2;
     if (int rc2 = certify_exact(e, true, e.inc_snap)) return rc2;
+    if (int rc2 = node_log(e, e.inc_snap)) return rc2;
     BNB_CUDA_OK(cudaStreamWaitEvent(e.st, e.ev_join, 0));
     if (int rc2 = branch_fallback(e)) return rc2;
   }
@@ -933,6 +947,7 @@ static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
   double params[4] = {gap, 0, 0, 0};
   BNB_CUDA_OK(cudaMemcpyAsync(e.params_d, params, sizeof(params), cudaMemcpyHostToDevice, e.st));
   if (int rc = queue_init(e)) return rc;
+  if (e.log_count) BNB_CUDA_OK(cudaMemsetAsync(e.log_count, 0, sizeof(int), e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.inc_beta, 0, sizeof(double) * e.p, e.st));
   if (o.root_heuristic) {
     if (int rc = root_heuristic(e, mp_moves(e))) return rc;
@@ -940,6 +955,18 @@ static int solve_start(bnb_handle* h, Engine<R>& e, SolveState& S, double gap) {
   BNB_CUDA_OK(cudaStreamSynchronize(e.st));
   e.nodes = e.rounds = e.admm_iters = e.pruned = e.polished = e.pool_peak = 0;
   e.max_depth = 0;
+  {   // the status before the first round: the root alone in the pool, the incumbent of
+      // the root heuristic (or none); a poll before any round reads this, never a stale word
+    double ub0 = INFINITY;
+    BNB_CUDA_OK(cudaMemcpy(&ub0, e.inc_ub, sizeof(double), cudaMemcpyDeviceToHost));
+    Status s0{};
+    s0.ub = ub0;
+    s0.lb = -INFINITY;
+    s0.pool_count = 1;
+    s0.free_top = (int)(e.qcap - 1);
+    s0.lost_lb = INFINITY;
+    *e.status_h = s0;
+  }
   if (o.use_graphs) {
     cudaGraph_t g;
     BNB_CUDA_OK(cudaStreamBeginCapture(e.st, cudaStreamCaptureModeThreadLocal));
@@ -978,6 +1005,7 @@ static int solve_launch(bnb_handle* h, Engine<R>& e, SolveState& S, int rounds) 
     } else if (int rc = round_body(h, e)) {
       return rc;
     }
+    ++S.launched;
   }
   return 0;
 }
@@ -994,7 +1022,7 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
   if (s.pool_count > e.pool_peak) e.pool_peak = s.pool_count;
   e.max_depth = s.max_depth;
   const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
-  if (!S.done) {
+  if (!S.done && S.launched > 0) {   // no round has run yet: nothing can have ended
     if (s.active_slots == 0 && s.pool_count == 0) {
       S.done = true;
       S.status = (s.error & 2) ? BNB_STATUS_QUEUE_FULL
@@ -1024,7 +1052,7 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
   }
   if (out) {
     out->ub = s.ub;
-    out->lb = (s.active_slots == 0 && s.pool_count == 0 && !s.error) ? s.ub : s.lb;
+    out->lb = (S.done && s.active_slots == 0 && s.pool_count == 0 && !s.error) ? s.ub : s.lb;
     out->nodes = s.nodes_total;
     out->open_nodes = s.pool_count + s.active_slots;
     out->active_slots = s.active_slots;
@@ -1159,6 +1187,32 @@ extern "C" int bnb_get_histograms(bnb_handle* h, long long* depth_hist, int ndep
   int rc = h->ef ? read_histograms(*h->ef, depth_hist, ndepth, support_hist, nsupport)
                  : read_histograms(*h->ed, depth_hist, ndepth, support_hist, nsupport);
   return set_err(h, rc);
+}
+
+template <class R>
+static int read_node_log(Engine<R>& e, int max_entries, int8_t* fix, double* r, double* rec,
+                         int* count) {
+  int c = 0;
+  if (e.log_count) {
+    BNB_CUDA_OK(cudaMemcpyAsync(&c, e.log_count, sizeof(int), cudaMemcpyDeviceToHost, e.st));
+    BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  }
+  *count = c;
+  const long long m = c < max_entries ? c : max_entries;
+  if (m <= 0) return BNB_OK;
+  if (fix) BNB_CUDA_OK(cudaMemcpyAsync(fix, e.log_fix, (size_t)m * e.p, cudaMemcpyDeviceToHost, e.st));
+  if (r) BNB_CUDA_OK(cudaMemcpyAsync(r, e.log_r, sizeof(double) * m * e.n, cudaMemcpyDeviceToHost, e.st));
+  if (rec)
+    BNB_CUDA_OK(cudaMemcpyAsync(rec, e.log_rec, sizeof(double) * m * LOG_REC,
+                                cudaMemcpyDeviceToHost, e.st));
+  BNB_CUDA_OK(cudaStreamSynchronize(e.st));
+  return BNB_OK;
+}
+
+extern "C" int bnb_get_node_log(bnb_handle* h, int max_entries, int8_t* fix, double* r,
+                                double* rec, int* count) {
+  if (!h || !count || max_entries < 0) return fail(BNB_EINVAL, "bad node-log arguments");
+  return dispatch(h, [&](auto& e) -> int { return read_node_log(e, max_entries, fix, r, rec, count); });
 }
 
 extern "C" int bnb_get_stats(const bnb_handle* h, bnb_stats* out) {

@@ -324,7 +324,8 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
                               const double* __restrict__ slot_lbp, const double* __restrict__ inc_ub,
                               const double* __restrict__ params, int use_threshold,
                               double* __restrict__ base_out, uint8_t* __restrict__ need,
-                              double* __restrict__ cert_lb, double* __restrict__ node_lb) {
+                              double* __restrict__ cert_lb, double* __restrict__ node_lb,
+                              double* __restrict__ width) {
   const int q = blockIdx.x, lane = threadIdx.x;
   if (q >= *ret_count) return;
   double su = 0.0, ss = 0.0;
@@ -345,6 +346,7 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
   base_out[q] = base;
   need[q] = exact ? 1 : 0;
   cert_lb[q] = lb;                    // final unless the exact terms follow
+  width[q] = exact ? 0.0 : ss;
   const double lp = slot_lbp[ret_slot[q]];
   node_lb[q] = lb > lp ? lb : lp;
 }
@@ -415,7 +417,7 @@ int certify_exact(Engine<R>& e, bool use_threshold, const double* inc) {
   const dim3 gx(K, CX_G);
   k_cert_decide<<<K, 32, 0, st>>>(e.cpart, nbm, K, e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr,
                                   e.slot_lbp, inc, e.params_d, use_threshold ? 1 : 0,
-                                  e.cx_base, e.cx_need, e.cert_lb, e.node_lb);
+                                  e.cx_base, e.cx_need, e.cert_lb, e.node_lb, e.cert_width);
   k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
                                    e.ret_count, 1, e.cx_need, e.cx_part);
   k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
@@ -429,6 +431,65 @@ int certify_exact(Engine<R>& e, bool use_threshold, const double* inc) {
   return 0;
 }
 
+// Node log: the retired nodes of this round, in retirement order, fill the next free
+// records (up to log_cap); k_node_log_advance then moves the count.
+template <class R>
+__global__ void k_node_log(int n, int p, long long cap, const int* __restrict__ log_count,
+                           const int* __restrict__ ret_slot, const int* __restrict__ ret_count,
+                           const int8_t* __restrict__ fix, const double* __restrict__ r64,
+                           const double* __restrict__ cert_lb, const uint8_t* __restrict__ need,
+                           const double* __restrict__ width, const double* __restrict__ node_lb,
+                           const double* __restrict__ slot_lbp, const double* __restrict__ inc,
+                           const double* __restrict__ params, const int* __restrict__ slot_depth,
+                           const int* __restrict__ slot_iters, const double* __restrict__ slot_dual,
+                           const double* __restrict__ slot_primal, int8_t* __restrict__ log_fix,
+                           double* __restrict__ log_r, double* __restrict__ log_rec) {
+  const int q = blockIdx.x;
+  if (q >= *ret_count) return;
+  const long long idx = (long long)*log_count + q;
+  if (idx >= cap) return;
+  const int slot = ret_slot[q];
+  for (int i = threadIdx.x; i < p; i += blockDim.x)
+    log_fix[idx * p + i] = fix[(long long)slot * p + i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) log_r[idx * n + i] = r64[(long long)q * n + i];
+  if (threadIdx.x == 0) {
+    double* rec = log_rec + idx * LOG_REC;
+    rec[LOG_LB] = cert_lb[q];
+    rec[LOG_EXACT] = need[q] ? 1.0 : 0.0;
+    rec[LOG_WIDTH] = width[q];
+    rec[LOG_NODE_LB] = node_lb[q];
+    rec[LOG_PARENT_LB] = slot_lbp[slot];
+    rec[LOG_THRESHOLD] = inc ? inc[0] * (1.0 - params[0]) : INFINITY;
+    rec[LOG_DEPTH] = slot_depth[slot];
+    rec[LOG_ITERS] = slot_iters[slot];
+    rec[LOG_EST_DUAL] = slot_dual[slot];
+    rec[LOG_EST_PRIMAL] = slot_primal[slot];
+  }
+}
+
+__global__ void k_node_log_advance(long long cap, int* __restrict__ log_count,
+                                   const int* __restrict__ ret_count) {
+  if (threadIdx.x == 0) {
+    const long long c = (long long)*log_count + *ret_count;
+    *log_count = (int)(c < cap ? c : cap);
+  }
+}
+
+template <class R>
+int node_log(Engine<R>& e, const double* inc) {
+  if (e.log_cap <= 0) return 0;
+  k_node_log<R><<<e.K, 256, 0, e.st>>>(e.n, e.p, e.log_cap, e.log_count, e.ret_slot, e.ret_count,
+                                       e.fix, e.r64, e.cert_lb, e.cx_need, e.cert_width,
+                                       e.node_lb, e.slot_lbp, inc, e.params_d, e.slot_depth,
+                                       e.slot_iters, e.slot_dual, e.slot_primal, e.log_fix,
+                                       e.log_r, e.log_rec);
+  k_node_log_advance<<<1, 32, 0, e.st>>>(e.log_cap, e.log_count, e.ret_count);
+  BNB_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template int node_log<float>(Engine<float>&, const double*);
+template int node_log<double>(Engine<double>&, const double*);
 template int certify<float>(Engine<float>&, const double*, bool);
 template int certify<double>(Engine<double>&, const double*, bool);
 template int certify_screen<float>(Engine<float>&, const double*);

@@ -65,6 +65,21 @@ inline void prof_end(Profiler* pf, cudaStream_t st, int kind) {
   pf->open.pop_back();
 }
 
+// fields of a node-log record (doubles), see bnb_get_node_log
+enum LogField {
+  LOG_LB = 0,        // certified bound of Proposition 1 at the node's r (exact or screened)
+  LOG_EXACT,         // 1: every nu term in FP64; 0: screened (rigorous upper values)
+  LOG_WIDTH,         // D(r) - LOG_LB lies in [0, LOG_WIDTH]
+  LOG_NODE_LB,       // max(LOG_LB, parent bound): the node's bound in the tree
+  LOG_PARENT_LB,
+  LOG_THRESHOLD,     // prune threshold UB (1 - gap) the certificate decided against
+  LOG_DEPTH,
+  LOG_ITERS,         // ADMM iterations of this visit
+  LOG_EST_DUAL,      // FP32 estimate of D(r) at the stop test
+  LOG_EST_PRIMAL,    // FP32 estimate of the primal value P(beta)
+  LOG_REC
+};
+
 template <class R>
 struct Engine {
   Prob P{};
@@ -191,6 +206,15 @@ struct Engine {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int mv_body_kernels = 0, tc_body_kernels = 0;
 
+  // node log (tracing, options.log_nodes): the first log_cap nodes certified in a solve,
+  // each with its fixings, its FP64 residual r = y - U and a record of LOG_REC doubles
+  long long log_cap = 0;
+  int* log_count = nullptr;     // nodes recorded so far (device scalar, <= log_cap)
+  int8_t* log_fix = nullptr;    // log_cap x p
+  double* log_r = nullptr;      // log_cap x n
+  double* log_rec = nullptr;    // log_cap x LOG_REC (fields: LogField)
+  double* cert_width = nullptr; // [K] D(r) - certified bound is in [0, width] (0: exact)
+
   // counters (host)
   long long nodes = 0, rounds = 0, admm_iters = 0, pruned = 0, polished = 0, pool_peak = 0;
   long long slot_iters_sum = 0;
@@ -205,6 +229,7 @@ template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or n
                                bool use_threshold);
 template <class R> int certify_screen(Engine<R>& e, const double* r_given);
 template <class R> int certify_exact(Engine<R>& e, bool use_threshold, const double* inc);
+template <class R> int node_log(Engine<R>& e, const double* inc);
 template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false,
                                       bool defer_fallback = false);
 template <class R> int branch_fallback(Engine<R>& e);

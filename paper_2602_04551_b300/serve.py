@@ -2,13 +2,15 @@
 
 Each admitted request owns one handle (its X, G^-1 and node pool stay resident on
 the device) and one CUDA stream.  The loop
-  1. admits arrived requests in arrival order while their device footprint
-     (bnb_footprint) fits in the HBM budget;
-  2. enqueues `rounds_per_step` branch-and-bound rounds on every admitted solve
+  1. enqueues `rounds_per_step` branch-and-bound rounds on every admitted solve
      (asynchronous graph launches on their own streams, so the node batches of
      different solves overlap on the GPU);
+  2. while those rounds run, admits arrived requests in arrival order while their
+     device footprint (bnb_footprint) fits in the HBM budget (a request's data are
+     generated and its per-tree setup is enqueued at admission);
   3. polls every solve; finished ones release their memory and record the
-     time from arrival to a certified gap.
+     time from arrival to a certified gap, split into the wait for admission
+     (queueing) and the time from admission to the end (service).
 The device work is all in the library's kernels; this module only schedules.
 The backend is injectable so the scheduling logic is testable without a GPU.
 """
@@ -61,6 +63,14 @@ class Result:
     def latency(self) -> float:
         return self.finished - self.arrival
 
+    @property
+    def queueing(self) -> float:
+        return self.admitted - self.arrival
+
+    @property
+    def service(self) -> float:
+        return self.finished - self.admitted
+
 
 class LibraryBackend:
     """The C-ABI library (one handle and one stream per solve)."""
@@ -101,7 +111,8 @@ class LibraryBackend:
 
 class Server:
     def __init__(self, backend=None, budget_bytes: int = 150 << 30, rounds_per_step: int = 4,
-                 clock: Callable[[], float] = time.perf_counter, sleep=time.sleep):
+                 clock: Callable[[], float] = time.perf_counter, sleep=time.sleep,
+                 progress: Callable[[float, int, int, int], None] = None):
         self.backend = backend if backend is not None else LibraryBackend()
         self.budget = int(budget_bytes)
         self.rounds = int(rounds_per_step)
@@ -110,6 +121,7 @@ class Server:
         self.peak_used = 0
         self.peak_active = 0
         self.admission_log = []       # (time, rid, footprint, used_after)
+        self.progress = progress      # called once per loop pass: (time, pending, active, done)
 
     def run(self, requests: list[Request]) -> list[Result]:
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
@@ -121,6 +133,9 @@ class Server:
             if self.backend.footprint(r) > self.budget:
                 raise ValueError(f"request {r.rid} alone exceeds the HBM budget")
         while pending or active:
+            # rounds first, so that admission work on the host overlaps them on the GPU
+            for r, h, fp, _ in active.values():
+                self.backend.launch(h, self.rounds)
             now = self.clock() - t0
             # admission: arrival order, while the footprint fits
             while pending and pending[0].arrival <= now:
@@ -139,8 +154,6 @@ class Server:
                 if pending:
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
-            for r, h, fp, _ in active.values():
-                self.backend.launch(h, self.rounds)
             done = []
             for rid, (r, h, fp, adm) in active.items():
                 pr = self.backend.poll(h)
@@ -153,6 +166,8 @@ class Server:
                     used -= fp
             for rid in done:
                 del active[rid]
+            if self.progress is not None:
+                self.progress(self.clock() - t0, len(pending), len(active), len(results))
         return sorted(results, key=lambda x: x.rid)
 
 
@@ -163,9 +178,19 @@ def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
 
 
 def latency_summary(results: list[Result]) -> dict:
+    """Latency from arrival to the end of each solve (p50/p99), split into queueing (arrival
+    to admission) and service (admission to the end); solves/s over the whole stream; and
+    how many solves ended certified (optimal or at the gap)."""
     lat = np.array([r.latency for r in results])
+    que = np.array([r.queueing for r in results])
+    ser = np.array([r.service for r in results])
     span = max(r.finished for r in results) - min(r.arrival for r in results)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "solves_per_s": len(results) / span,
+    cert = [r for r in results if r.status in ("optimal", "gap")]
+    pct = lambda a, q: float(np.percentile(a, q))
+    return {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
+            "queue_p50_s": pct(que, 50), "queue_p99_s": pct(que, 99),
+            "service_p50_s": pct(ser, 50), "service_p99_s": pct(ser, 99),
+            "solves_per_s": len(results) / span, "certified": len(cert),
+            "certified_per_s": len(cert) / span,
             "makespan_s": span, "solves": len(results),
             "nodes": int(sum(r.nodes for r in results))}

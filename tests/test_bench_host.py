@@ -153,3 +153,48 @@ def test_gpu_arm_line_has_the_contract_keys(bench, monkeypatch):
     assert line["setup_seconds"] is None             # absent from the fake record
     out["setup_seconds"] = 0.9
     assert bench.mine_line(args, out, 1, 64.0, 2688, {}, cpu)["setup_seconds"] == 0.9
+
+
+def test_burst_peak_when_the_timed_region_ran_at_full_clock(bench):
+    """At the maximum SM clock with no power cap the kernel is compared with the burst
+    peak; otherwise with the sustained one; the other fraction is reported beside it."""
+    key = next(iter(bench.TRAFFIC))
+    pk = {"bf16_tflops": 1790.8, "bf16_tflops_sustained": 1386.4}
+    out = _out(key)
+    out["clocks"] = {"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": []}
+    r = bench.roofline(out, _args(key), pk)
+    assert r["peak"] == 1790.8 and r["peak_kind"] == "burst"
+    assert r["frac_vs_sustained"] == pytest.approx(r["achieved"] / 1386.4)
+    out["clocks"] = {"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"]}
+    r = bench.roofline(out, _args(key), pk)
+    assert r["peak"] == 1386.4 and r["peak_kind"] == "sustained"
+    out["clocks"] = {"sm_mhz": 1600.0, "sm_max_mhz": 2032.0, "reasons": []}
+    assert bench.roofline(out, _args(key), pk)["peak_kind"] == "sustained"
+
+
+def test_lambda0_pick_rule(bench):
+    grid = [1.0, 0.5, 0.25, 0.125, 0.0625]
+    counts = [3, 5, 5, 8, 13]
+    picks = bench.pick_lambda0(counts, grid, (5, 8, 12, 20, 1))
+    fr = [p["lambda0_frac"] for p in picks]
+    assert fr[0] == pytest.approx((0.5 * 0.25) ** 0.5)     # midpoint of the points giving 5
+    assert fr[1] == 0.125                                   # the one point giving 8
+    assert fr[2] == 0.0625                                  # nearest count to 12 is 13
+    assert fr[3] == 0.0625
+    assert fr[4] == 1.0                                     # nearest to 1 is 3 (largest lambda0)
+
+
+def test_greedy_lambda0_orthonormal_design(bench):
+    """Orthonormal columns: each forward step's drop is c_j^2 / (2 (1 + 2 lam2)) of the
+    untouched coefficient (box loose), so the returned lambda0 lies strictly between the
+    k-th and (k+1)-th largest of them."""
+    import numpy as np
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 12)))
+    beta = np.array([3.0, -2.6, 2.2, 1.9, -1.5, 1.2, 0.9, 0.7, 0.5, 0.3, 0.2, 0.1])
+    y = Q @ beta
+    lam2, M = 0.01, 10.0
+    drops = np.sort((Q.T @ y) ** 2 / (2 * (1 + 2 * lam2)))[::-1]
+    for k in (1, 4, 7):
+        lam0 = bench.greedy_lambda0(Q, y, lam2, M, k)
+        assert drops[k] < lam0 < drops[k - 1]

@@ -101,3 +101,25 @@ def test_bounded_mbarrier_wait_expires_sets_error_and_returns(polls, seconds):
     # the context is still usable
     x = torch.arange(1000, device="cuda", dtype=torch.float64)
     assert float(x.sum().item()) == 499500.0
+
+
+def test_poll_before_the_first_round_does_not_end_the_solve():
+    """bnb_solve_poll right after bnb_solve_start (no round launched yet) reports the root
+    alone and an open solve -- it must not read a stale status as a closed tree -- and the
+    solve then reaches the brute-force optimum as usual."""
+    inst, lam0, lam2, M = _p16(1, 0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    o = bnb.bnb_options_default(M=M, node_tol=1e-7, max_admm_iter=5000, batch_K=8,
+                                queue_capacity=1 << 12)
+    with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
+        for _ in range(2):                    # a second solve on the same handle as well
+            bnb.bnb_solve_start(h, 1e-9)
+            pr = bnb.bnb_solve_poll(h)
+            assert not pr["done"] and pr["nodes"] == 0 and pr["open_nodes"] == 1
+            assert pr["lb"] == -np.inf
+            while not pr["done"]:
+                bnb.bnb_solve_launch(h, 1)
+                pr = bnb.bnb_solve_poll(h)
+            res = bnb.bnb_solve_finish(h)
+            assert tuple(np.nonzero(res["beta"])[0]) == br.support
+            assert res["ub"] == pytest.approx(br.objective, rel=1e-8)

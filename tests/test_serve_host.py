@@ -90,3 +90,16 @@ def test_poisson_arrivals_and_summary():
     res = srv.run([_req(i, 3, 3, float(t[i]), 3) for i in range(20)])
     s = latency_summary(res)
     assert s["solves"] == 20 and s["p99_s"] >= s["p50_s"] > 0
+
+
+def test_latency_summary_splits_queueing_and_service():
+    from paper_2602_04551_b300.serve import Result
+    res = [Result(rid=i, status="gap" if i % 2 == 0 else "time_limit", ub=1.0, lb=0.9, nodes=10,
+                  beta=np.zeros(1), arrival=float(i), admitted=float(i) + 0.5 * i,
+                  finished=float(i) + 0.5 * i + 2.0) for i in range(5)]
+    s = latency_summary(res)
+    assert s["queue_p50_s"] == pytest.approx(1.0)          # 0, .5, 1, 1.5, 2
+    assert s["service_p50_s"] == pytest.approx(2.0) and s["service_p99_s"] == pytest.approx(2.0)
+    assert s["p50_s"] == pytest.approx(3.0)
+    assert s["certified"] == 3 and s["solves"] == 5
+    assert s["makespan_s"] == pytest.approx(4 + 2.0 + 2.0)
