@@ -112,6 +112,12 @@ typedef struct {
                             after the projected-gradient method; 0 returns the projected-
                             gradient solution itself (ADMM precision, upcast) with its FP64
                             objective.  bnb_solve always polishes its candidate incumbents. */
+  int fused_width;       /* tensor-core precisions, the fused X^T U' product: 0 (default) =
+                            the tile width measured fastest at creation; otherwise only
+                            shapes of this width compete (with fused_shape: the pair forms
+                            offer 128 and 144 transposed, 80, 96, 128 and 176 untransposed;
+                            one CTA per tile 64, 80, 96, 128).  A width no shape offers
+                            fails bnb_create with BNB_EINVAL. */
   int log_nodes;         /* tracing: record the first log_nodes nodes certified in each solve
                             (fixings, FP64 residual, certified bound; bnb_get_node_log), in
                             [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)

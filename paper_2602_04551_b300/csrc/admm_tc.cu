@@ -796,9 +796,24 @@ static int pair_clusters_bn() {
 template <int NS>
 static int fused_xtu(Engine<float>& e, const TcOperand& XC, const TcOperand& Uop, bool last) {
   if (e.tc_pair3 > 0 && e.tc_pairnt) {
-    if constexpr (NS != 2)
-      return last ? fused_pairnt_bn<NS, 176, true>(e, XC, Uop)
-                  : fused_pairnt_bn<NS, 176, false>(e, XC, Uop);
+    if constexpr (NS != 2) {
+      // widths up to 128 hold two accumulators per pair (the update of one tile overlaps
+      // the MMAs of the next); 176 holds one
+      switch (e.tc_bn3) {
+        case 80:
+          return last ? fused_pairnt_bn<NS, 80, true>(e, XC, Uop)
+                      : fused_pairnt_bn<NS, 80, false>(e, XC, Uop);
+        case 96:
+          return last ? fused_pairnt_bn<NS, 96, true>(e, XC, Uop)
+                      : fused_pairnt_bn<NS, 96, false>(e, XC, Uop);
+        case 128:
+          return last ? fused_pairnt_bn<NS, 128, true>(e, XC, Uop)
+                      : fused_pairnt_bn<NS, 128, false>(e, XC, Uop);
+        default:
+          return last ? fused_pairnt_bn<NS, 176, true>(e, XC, Uop)
+                      : fused_pairnt_bn<NS, 176, false>(e, XC, Uop);
+      }
+    }
     return BNB_EINVAL;
   }
   if (e.tc_pair3 > 0) {
@@ -1036,18 +1051,27 @@ static int pick_fused_shape(Engine<float>& e) {
       if (cl >= 1) cands.push_back({w, 0, cl, 0});
     }
   }
-  // CTA pairs untransposed: 256 features x 176 slots per pair tile (3 and 1 terms)
+  // CTA pairs untransposed: 256 features x 80, 96, 128 or 176 slots per pair tile (3 and 1
+  // terms); the narrower ones put about two tiles on each pair with two accumulators
   if constexpr (NS != 2) {
-    int cl = pairnt_clusters_bn<NS, 176>();
-    if (cl > e.sms / 2) cl = e.sms / 2;
-    if (cl >= 1) cands.push_back({176, 0, cl, 1});
+    for (int w : {80, 96, 128, 176}) {
+      if (w < 176 && e.K <= w && e.fused_width != w) continue;   // one slot tile: the widest covers it
+      int cl = w == 80    ? pairnt_clusters_bn<NS, 80>()
+               : w == 96  ? pairnt_clusters_bn<NS, 96>()
+               : w == 128 ? pairnt_clusters_bn<NS, 128>()
+                          : pairnt_clusters_bn<NS, 176>();
+      if (cl > e.sms / 2) cl = e.sms / 2;
+      if (cl >= 1) cands.push_back({w, 0, cl, 1});
+    }
   }
-  if (e.fused_kind > 0) {   // a requested kind: only its widths compete
+  if (e.fused_kind > 0 || e.fused_width > 0) {   // a requested kind and/or width
     std::vector<Shape> keep;
-    for (const Shape& c : cands)
-      if ((e.fused_kind == 1 && !c.mc && !c.pair) || (e.fused_kind == 2 && c.mc) ||
-          (e.fused_kind == 3 && c.pair && !c.nt) || (e.fused_kind == 4 && c.pair && c.nt))
-        keep.push_back(c);
+    for (const Shape& c : cands) {
+      const bool kind_ok = e.fused_kind == 0 || (e.fused_kind == 1 && !c.mc && !c.pair) ||
+                           (e.fused_kind == 2 && c.mc) || (e.fused_kind == 3 && c.pair && !c.nt) ||
+                           (e.fused_kind == 4 && c.pair && c.nt);
+      if (kind_ok && (e.fused_width == 0 || c.w == e.fused_width)) keep.push_back(c);
+    }
     cands.swap(keep);
   }
   if (cands.empty()) return BNB_EINVAL;

@@ -428,6 +428,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->u_shape = 0;
   o->ub_polish = 1;
   o->log_nodes = 0;
+  o->fused_width = 0;
   return BNB_OK;
 }
 
@@ -441,6 +442,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   e->dmax = o.max_depth;
   e->lockstep = o.lockstep ? 1 : 0;
   e->fused_kind = o.fused_shape;
+  e->fused_width = o.fused_width;
   e->u_kind = o.u_shape;
   e->smax = o.support_max;
   e->ub_iters = o.ub_max_iter;
@@ -487,8 +489,9 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
   if constexpr (sizeof(R) == 4) {
     if (e->tc_mode) {
       if (int rc = setup_tc(*e))
-        return rc == BNB_EINVAL ? fail(BNB_EINVAL, "fused_shape %d / u_shape %d: no such shape "
-                                                    "runs here", o.fused_shape, o.u_shape)
+        return rc == BNB_EINVAL ? fail(BNB_EINVAL, "fused_shape %d / fused_width %d / u_shape %d: "
+                                                    "no such shape runs here", o.fused_shape,
+                                       o.fused_width, o.u_shape)
                                 : rc;
       e->mv_cross = o.mv_crossover < 0 ? 16 : (o.mv_crossover > MV_MAX ? MV_MAX : o.mv_crossover);
       if (int rc = mv_setup(*e)) return rc;
@@ -536,6 +539,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
   if (o.ub_polish != 0 && o.ub_polish != 1) return fail(BNB_EINVAL, "ub_polish must be 0 or 1");
   if (o.log_nodes < 0 || o.log_nodes > (1 << 16)) return fail(BNB_EINVAL, "log_nodes must be in [0, 65536]");
+  if (o.fused_width < 0 || o.fused_width > 256) return fail(BNB_EINVAL, "fused_width must be in [0, 256]");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;

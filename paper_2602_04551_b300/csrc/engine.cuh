@@ -191,6 +191,7 @@ struct Engine {
   float* upart = nullptr;       // [usplit_max][K][n] partial products of U'
   int fused_kind = 0;           // requested shape: 0 measured, 1 single, 2 clusters of two,
                                 // 3 pairs transposed, 4 pairs untransposed
+  int fused_width = 0;          // requested tile width of that product (0: measured)
   float* tc_stat = nullptr;     // [3][nbt][K] per-tile column sums: ||y-U||^2, y^T(y-U), ||y-X beta||^2
   int nbt = 0;                  // row tiles of the n x K products
   int sms = 148;                // multiprocessors of the device (persistent grids)

@@ -313,6 +313,45 @@ def test_one_admm_iteration_cta_pairs_full_size(shape):
                          rows=[0, 127, 128, 255, 256, 511], seed=14, fused_shape=shape)
 
 
+PAIR_WIDTHS = [80, 96, 128, 176]
+
+
+@pytest.mark.parametrize("width", PAIR_WIDTHS)
+@pytest.mark.parametrize("prec", [3, 2])
+def test_one_admm_iteration_untransposed_pair_widths(width, prec):
+    """The untransposed CTA-pair product at every tile width it offers (80, 96 and 128 hold
+    two accumulators and put several tiles on a pair; 176 one), forced with fused_width:
+    at c2_small (K = 45 of 128 slots: ragged slot tiles) and at c2 (K = 512) with slots in
+    every slot tile and the ragged last feature tile compared."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=128, rows=range(45), seed=13,
+                         fused_shape=4, fused_width=width)
+    if prec == 3:
+        inst, lam0, lam2, M = _inst("c2", 0)
+        rows = sorted({0, width - 1, width, 2 * width + 3, 300, 511})
+        _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512, rows=rows, seed=14,
+                             fused_shape=4, fused_width=width)
+
+
+@pytest.mark.parametrize("width", PAIR_WIDTHS)
+def test_converged_bounds_untransposed_pair_widths(width):
+    """Converged bounds (both instantiations of the fused update: the round's last
+    iteration with the stop-test sums, the others without) at each pair width: valid and
+    within 20 node tolerances of the second solver's optimum."""
+    inst, lam0, lam2, M = _inst("c2_small", 2)
+    rng = np.random.default_rng(22)
+    fix = datagen.random_fixings(inst.p, 40, rng, 10)
+    with _handle(inst, lam0, lam2, M, 3, K=128, node_tol=1e-5, max_admm_iter=20000,
+                 mv_crossover=0, fused_shape=4, fused_width=width) as h:
+        out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
+        st = bnb.bnb_get_stats(h)
+    assert st["fused_pairs"] > 0 and not st["fused_transposed"] and st["fused_tile_width"] == width
+    for k in range(40):
+        _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
+        assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
+        assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_converged_bounds_and_solve_every_fused_shape(shape):
     """Converged node bounds (the stop-test sums of the fused epilogue decide when a node
