@@ -80,6 +80,10 @@ def parse():
                     help="fused X^T U' shape: 0 measured at setup, 1 one CTA per tile, "
                          "2 clusters of two sharing X, 3 transposed on CTA pairs, "
                          "4 untransposed on CTA pairs")
+    ap.add_argument("--fused-width", type=int, default=0,
+                    help="tile width of the fused X^T U' product (0: measured at setup)")
+    ap.add_argument("--fused-select", type=int, default=1, choices=[0, 1],
+                    help="selection and refill as one cooperative launch (1) or separate launches")
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2],
                     help="U' = H W'^T: 0 measured at setup, 1 cluster-reduced, 2 CTA pairs split-K")
     ap.add_argument("--mv-crossover", type=int, default=-1,
@@ -225,7 +229,8 @@ def run_mine(args, rank, world):
                                   precision=PREC[args.precision], device=dev, stream=s.cuda_stream,
                                   queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
                                   relax_alpha=args.alpha, mv_crossover=args.mv_crossover,
-                                  fused_shape=args.fused_shape, u_shape=args.u_shape)
+                                  fused_shape=args.fused_shape, u_shape=args.u_shape,
+                                  fused_width=args.fused_width, fused_select=args.fused_select)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4

@@ -118,6 +118,10 @@ typedef struct {
                             offer 128 and 144 transposed, 80, 96, 128 and 176 untransposed;
                             one CTA per tile 64, 80, 96, 128).  A width no shape offers
                             fails bnb_create with BNB_EINVAL. */
+  int fused_select;      /* 1 (default): a round's best-first selection and slot refill run as
+                            one cooperative launch whose blocks meet at (bounded) grid
+                            barriers, where the device supports it; 0: as eight separate
+                            launches.  Same selection either way. */
   int log_nodes;         /* tracing: record the first log_nodes nodes certified in each solve
                             (fixings, FP64 residual, certified bound; bnb_get_node_log), in
                             [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)

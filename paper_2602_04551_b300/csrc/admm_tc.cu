@@ -443,6 +443,10 @@ struct TcEpiAdmm {
   __device__ __forceinline__ void finish(int t, int nthr, int m0, int n0, int M, int N,
                                          float* sm) const {
     if constexpr (!STATS) return;
+    // a CTA whose 128 rows all lie past the last feature (the second CTA of a 256-row pair
+    // tile when p is small) has no row block of its own: the stop-test sums hold
+    // ceil(p / 128) row blocks per slot
+    if (m0 >= M || m0 / tc::BM >= nbm) return;
     for (int col = t; col < BN; col += nthr) {
       const int n = n0 + col;
       if (n >= N) continue;

@@ -429,6 +429,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->ub_polish = 1;
   o->log_nodes = 0;
   o->fused_width = 0;
+  o->fused_select = 1;
   return BNB_OK;
 }
 
@@ -481,6 +482,7 @@ static int engine_create(bnb_handle* h, Engine<R>*& e, const double* dX, const d
     if (o.precision == BNB_PREC_BF16X2) e->tc_mode = 2;
     if (o.precision == BNB_PREC_TC3) e->tc_mode = 3;
   }
+  e->sel_blocks = o.fused_select ? queue_fused_select_blocks<R>() : 0;
   if (int rc = allocate(*e)) return rc;
   if (int rc = setup_data(*e, dX, dy)) return rc;
   BNB_CUDA_OK(cudaStreamCreateWithFlags(&e->st_aux, cudaStreamNonBlocking));
@@ -540,6 +542,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.ub_polish != 0 && o.ub_polish != 1) return fail(BNB_EINVAL, "ub_polish must be 0 or 1");
   if (o.log_nodes < 0 || o.log_nodes > (1 << 16)) return fail(BNB_EINVAL, "log_nodes must be in [0, 65536]");
   if (o.fused_width < 0 || o.fused_width > 256) return fail(BNB_EINVAL, "fused_width must be in [0, 256]");
+  if (o.fused_select != 0 && o.fused_select != 1) return fail(BNB_EINVAL, "fused_select must be 0 or 1");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
@@ -1026,6 +1029,11 @@ static int solve_poll(bnb_handle* h, Engine<R>& e, SolveState& S, bnb_progress* 
   if (s.pool_count > e.pool_peak) e.pool_peak = s.pool_count;
   e.max_depth = s.max_depth;
   const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - S.t0).count();
+  if (s.error & 8) {
+    S.done = true;
+    return fail(BNB_ECUDA, "a grid barrier of the fused selection timed out (device blocks "
+                           "not co-resident)");
+  }
   if (!S.done && S.launched > 0) {   // no round has run yet: nothing can have ended
     if (s.active_slots == 0 && s.pool_count == 0) {
       S.done = true;

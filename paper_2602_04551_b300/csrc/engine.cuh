@@ -113,6 +113,7 @@ struct Engine {
   int *slot_active = nullptr, *slot_iters = nullptr, *slot_depth = nullptr, *slot_nfix = nullptr;
   int dmax = 256;               // deepest node (fixings kept per open node)
   int lockstep = 0;             // 1: refill only when every slot is free (Algorithm 1 batches)
+  int sel_blocks = 0;           // > 0: selection + refill as one cooperative launch of this many blocks
   unsigned long long* ub_seen = nullptr;  // [UB_SEEN] keys of evaluated supports (0: empty)
   int* sup_size = nullptr;      // [K] rounded-support size of each retired node (-1: > smax)
   int* hist_depth = nullptr;    // [dmax + 1] solved nodes by depth (last bin: deeper)
@@ -237,6 +238,7 @@ template <class R> int branch_fallback(Engine<R>& e);
 template <class R> int upper_bound(Engine<R>& e, int force_polish);
 template <class R> int queue_push(Engine<R>& e);
 template <class R> int queue_select_refill(Engine<R>& e);
+template <class R> int queue_fused_select_blocks();
 template <class R> int queue_init(Engine<R>& e);
 template <class R> int queue_status(Engine<R>& e);
 template <class R> int ub_from_masks(Engine<R>& e, const uint8_t* dmask, int K);

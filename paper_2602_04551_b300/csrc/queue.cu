@@ -25,6 +25,7 @@ namespace bnb {
 enum {
   SS_TAKE_ALL = 0, SS_F = 1, SS_PREFIX = 2, SS_NEED = 3, SS_LESS = 4, SS_TAU = 5, SS_EQ = 6,
   SS_OUT = 7, SS_POLISHED = 8, SS_PRUNED = 9, SS_COUNT = 10, SS_ERROR = 11, SS_MAXDEPTH = 12,
+  SS_BARCNT = 13, SS_BARGEN = 14,   // grid barrier of the fused selection (arrivals, phase)
   SS_WORDS = 16
 };
 
@@ -160,7 +161,8 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
   }
 }
 
-__global__ void k_sel_reset(unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+__device__ __forceinline__ void sel_reset_body(unsigned* hist, int* sel_state,
+                                               unsigned long long* poolmin) {
   for (int t = threadIdx.x; t < 3 * SEL_BINS; t += blockDim.x) hist[t] = 0;
   if (threadIdx.x == 0) {
     sel_state[SS_TAKE_ALL] = 0;
@@ -175,22 +177,30 @@ __global__ void k_sel_reset(unsigned* hist, int* sel_state, unsigned long long* 
   }
 }
 
-// pass 1: drop prunable entries, count, min LB, histogram of the top 11 key bits
-__global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid,
-                            const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
-                            const int* __restrict__ pool_warm, int* free_stack, int* free_top,
-                            int* warm_ref, int* warm_stack, int* warm_top,
-                            const double* __restrict__ inc_ub, const double* __restrict__ params,
-                            unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+__global__ void k_sel_reset(unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+  sel_reset_body(hist, sel_state, poolmin);
+}
+
+// pass 1: drop prunable entries, count, min LB, histogram of the top 11 key bits (block
+// `blk` of `nblk` in a grid-stride loop over the pool)
+__device__ __forceinline__ void sel_pass1_body(int blk, int nblk, const int* __restrict__ pool_hw,
+                                               uint8_t* pool_valid,
+                                               const double* __restrict__ pool_lb,
+                                               const unsigned* __restrict__ pool_key,
+                                               const int* __restrict__ pool_warm, int* free_stack,
+                                               int* free_top, int* warm_ref, int* warm_stack,
+                                               int* warm_top, const double* __restrict__ inc_ub,
+                                               const double* __restrict__ params, unsigned* hist,
+                                               int* sel_state, unsigned long long* poolmin) {
   __shared__ unsigned sh[SEL_BINS];
   const int hw = *pool_hw;
-  if (blockIdx.x * blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
+  if (blk * (int)blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
   const double thr = inc_ub[0] * (1.0 - params[0]);
   int cnt = 0;
   unsigned long long mn = ~0ull;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
     if (!pool_valid[i]) continue;
     const double lb = pool_lb[i];
     if (lb >= thr) {
@@ -212,11 +222,24 @@ __global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid
   if (mn != ~0ull) atomicMin(poolmin, mn);
 }
 
+__global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid,
+                            const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
+                            const int* __restrict__ pool_warm, int* free_stack, int* free_top,
+                            int* warm_ref, int* warm_stack, int* warm_top,
+                            const double* __restrict__ inc_ub, const double* __restrict__ params,
+                            unsigned* hist, int* sel_state, unsigned long long* poolmin) {
+  sel_pass1_body(blockIdx.x, gridDim.x, pool_hw, pool_valid, pool_lb, pool_key, pool_warm,
+                 free_stack, free_top, warm_ref, warm_stack, warm_top, inc_ub, params, hist,
+                 sel_state, poolmin);
+}
+
 // level-L scan (single block).  Level 1 also lists the free slots in order.
 // With `lockstep` (Algorithm 1's batches) nothing is selected until every slot is free;
 // SS_TAKE_ALL = 2 then means "take none" for the later levels and the collection.
-__global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* sel_state, int K,
-                           const int* __restrict__ slot_active, int* free_slots, int lockstep) {
+__device__ __forceinline__ void sel_scan_body(int level, const unsigned* __restrict__ hist,
+                                              int* sel_state, int K,
+                                              const int* __restrict__ slot_active,
+                                              int* free_slots, int lockstep) {
   __shared__ int wcnt[32];
   __shared__ int base;
   if (level == 1) {
@@ -309,19 +332,25 @@ __global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* se
   }
 }
 
+__global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* sel_state, int K,
+                           const int* __restrict__ slot_active, int* free_slots, int lockstep) {
+  sel_scan_body(level, hist, sel_state, K, slot_active, free_slots, lockstep);
+}
+
 // levels 2 and 3: histogram of the next key bits among entries matching the prefix
-__global__ void k_sel_pass(int level, const int* __restrict__ pool_hw,
-                           const uint8_t* __restrict__ pool_valid,
-                           const unsigned* __restrict__ pool_key, unsigned* hist,
-                           const int* __restrict__ sel_state) {
+__device__ __forceinline__ void sel_pass_body(int blk, int nblk, int level,
+                                              const int* __restrict__ pool_hw,
+                                              const uint8_t* __restrict__ pool_valid,
+                                              const unsigned* __restrict__ pool_key,
+                                              unsigned* hist, const int* __restrict__ sel_state) {
   if (sel_state[SS_TAKE_ALL]) return;
   __shared__ unsigned sh[SEL_BINS];
   const int hw = *pool_hw;
-  if (blockIdx.x * blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
+  if (blk * (int)blockDim.x >= hw) return;   // no pool entry for this block (grid-stride)
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
   const unsigned pre = (unsigned)sel_state[SS_PREFIX];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
     if (!pool_valid[i]) continue;
     const unsigned k = pool_key[i];
     if (level == 2) {
@@ -336,15 +365,24 @@ __global__ void k_sel_pass(int level, const int* __restrict__ pool_hw,
     if (sh[t]) atomicAdd(&h[t], sh[t]);
 }
 
-__global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_valid,
-                              const unsigned* __restrict__ pool_key, int* free_stack, int* free_top,
-                              int* sel_state, int* popped) {
+__global__ void k_sel_pass(int level, const int* __restrict__ pool_hw,
+                           const uint8_t* __restrict__ pool_valid,
+                           const unsigned* __restrict__ pool_key, unsigned* hist,
+                           const int* __restrict__ sel_state) {
+  sel_pass_body(blockIdx.x, gridDim.x, level, pool_hw, pool_valid, pool_key, hist, sel_state);
+}
+
+__device__ __forceinline__ void sel_collect_body(int blk, int nblk, const int* __restrict__ pool_hw,
+                                                 uint8_t* pool_valid,
+                                                 const unsigned* __restrict__ pool_key,
+                                                 int* free_stack, int* free_top, int* sel_state,
+                                                 int* popped) {
   const int hw = *pool_hw;
   const int all = sel_state[SS_TAKE_ALL];
   if (all == 2) return;                     // lockstep: slots still busy
   const unsigned tau = (unsigned)sel_state[SS_TAU];
   const int need_eq = sel_state[SS_NEED];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < hw; i += gridDim.x * blockDim.x) {
+  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
     if (!pool_valid[i]) continue;
     const unsigned k = pool_key[i];
     bool take = all == 1 || k < tau;
@@ -356,18 +394,27 @@ __global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_val
   }
 }
 
-// load popped nodes into free slots (one block per popped node)
+__global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_valid,
+                              const unsigned* __restrict__ pool_key, int* free_stack, int* free_top,
+                              int* sel_state, int* popped) {
+  sel_collect_body(blockIdx.x, gridDim.x, pool_hw, pool_valid, pool_key, free_stack, free_top,
+                   sel_state, popped);
+}
+
+// load popped node t into its free slot (one block)
 template <class R>
-__global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, const int* __restrict__ popped,
-                         const int* __restrict__ free_slots, const double* __restrict__ pool_lb,
-                         const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
-                         const int* __restrict__ pool_fix, const R* __restrict__ warm_beta,
-                         const R* __restrict__ warm_V, int* warm_ref, int* warm_stack,
-                         int* warm_top, int8_t* fix, R* beta, R* V, int* slot_active,
-                         int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
-                         int* slot_fixl) {
-  const int t = blockIdx.x;
-  if (t >= sel_state[SS_OUT]) return;
+__device__ __forceinline__ void refill_body(int t, int p, int dmax, const int* __restrict__ popped,
+                                            const int* __restrict__ free_slots,
+                                            const double* __restrict__ pool_lb,
+                                            const int* __restrict__ pool_depth,
+                                            const int* __restrict__ pool_warm,
+                                            const int* __restrict__ pool_fix,
+                                            const R* __restrict__ warm_beta,
+                                            const R* __restrict__ warm_V, int* warm_ref,
+                                            int* warm_stack, int* warm_top, int8_t* fix, R* beta,
+                                            R* V, int* slot_active, int* slot_iters,
+                                            double* slot_lbp, int* slot_depth, int* slot_nfix,
+                                            int* slot_fixl) {
   const int slot = free_slots[t];
   const int idx = popped[t];
   const int d = pool_depth[idx];
@@ -394,6 +441,115 @@ __global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, con
     slot_nfix[slot] = d;
     warm_release(w, warm_ref, warm_stack, warm_top);
   }
+}
+
+// load popped nodes into free slots (one block per popped node)
+template <class R>
+__global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, const int* __restrict__ popped,
+                         const int* __restrict__ free_slots, const double* __restrict__ pool_lb,
+                         const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
+                         const int* __restrict__ pool_fix, const R* __restrict__ warm_beta,
+                         const R* __restrict__ warm_V, int* warm_ref, int* warm_stack,
+                         int* warm_top, int8_t* fix, R* beta, R* V, int* slot_active,
+                         int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
+                         int* slot_fixl) {
+  const int t = blockIdx.x;
+  if (t >= sel_state[SS_OUT]) return;
+  refill_body<R>(t, p, dmax, popped, free_slots, pool_lb, pool_depth, pool_warm, pool_fix,
+                 warm_beta, warm_V, warm_ref, warm_stack, warm_top, fix, beta, V, slot_active,
+                 slot_iters, slot_lbp, slot_depth, slot_nfix, slot_fixl);
+}
+
+// ---- the selection and refill of a round in one cooperative launch ----
+// The steps above (reset, pass 1, three scans, two passes, collection, refill) are
+// dependent, and as separate launches most of their time is launch and ramp latency; here
+// the blocks of one cooperative launch (all co-resident) meet at grid barriers between
+// the steps.  Every barrier wait is bounded (2^24 polls and 1 s): a block that gives up
+// sets bit 8 of the error word and leaves, and the solve then ends with an error.
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// arrival count and phase generation live in sel_state; the last block to arrive resets
+// the count and advances the generation, the others wait for the generation to change
+__device__ bool coop_grid_sync(int* sel_state) {
+  __shared__ int ok_s;
+  unsigned* cnt = reinterpret_cast<unsigned*>(&sel_state[SS_BARCNT]);
+  unsigned* gen = reinterpret_cast<unsigned*>(&sel_state[SS_BARGEN]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g0 = ld_acquire_gpu(gen);
+    __threadfence();                             // this block's writes before its arrival
+    if (atomicAdd(cnt, 1u) + 1u == gridDim.x) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);                        // release the next phase
+    } else {
+      const unsigned long long t0 = global_timer_ns();
+      for (long long i = 0;; ++i) {
+        if (ld_acquire_gpu(gen) != g0) break;
+        if (i >= (1ll << 24) || ((i & 255) == 255 && global_timer_ns() - t0 > 1000000000ull)) {
+          atomicOr(&sel_state[SS_ERROR], 8);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+constexpr int SELC_THREADS = 1024;   // the scans' block width
+constexpr int SELC_BLOCKS = 64;      // co-resident blocks of the fused selection
+
+template <class R>
+__global__ void __launch_bounds__(SELC_THREADS) k_select_refill_coop(
+    int K, int p, int dmax, int lockstep, const int* __restrict__ pool_hw, uint8_t* pool_valid,
+    const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
+    const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
+    const int* __restrict__ pool_fix, int* free_stack, int* free_top,
+    const R* __restrict__ warm_beta, const R* __restrict__ warm_V, int* warm_ref,
+    int* warm_stack, int* warm_top, const double* __restrict__ inc_ub,
+    const double* __restrict__ params, unsigned* hist, int* sel_state,
+    unsigned long long* poolmin, int* free_slots, int* popped, int8_t* fix, R* beta, R* V,
+    int* slot_active, int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
+    int* slot_fixl) {
+  const int blk = blockIdx.x, nblk = gridDim.x;
+  if (blk == 0) sel_reset_body(hist, sel_state, poolmin);
+  if (!coop_grid_sync(sel_state)) return;
+  sel_pass1_body(blk, nblk, pool_hw, pool_valid, pool_lb, pool_key, pool_warm, free_stack,
+                 free_top, warm_ref, warm_stack, warm_top, inc_ub, params, hist, sel_state,
+                 poolmin);
+  if (!coop_grid_sync(sel_state)) return;
+  for (int level = 1; level <= 3; ++level) {
+    if (level > 1) {
+      sel_pass_body(blk, nblk, level, pool_hw, pool_valid, pool_key, hist, sel_state);
+      if (!coop_grid_sync(sel_state)) return;
+    }
+    if (blk == 0) sel_scan_body(level, hist, sel_state, K, slot_active, free_slots, lockstep);
+    if (!coop_grid_sync(sel_state)) return;
+  }
+  sel_collect_body(blk, nblk, pool_hw, pool_valid, pool_key, free_stack, free_top, sel_state,
+                   popped);
+  if (!coop_grid_sync(sel_state)) return;
+  const int out = sel_state[SS_OUT];
+  for (int t = blk; t < out; t += nblk)
+    refill_body<R>(t, p, dmax, popped, free_slots, pool_lb, pool_depth, pool_warm, pool_fix,
+                   warm_beta, warm_V, warm_ref, warm_stack, warm_top, fix, beta, V, slot_active,
+                   slot_iters, slot_lbp, slot_depth, slot_nfix, slot_fixl);
 }
 
 __global__ void k_status(int K, const int* __restrict__ slot_active,
@@ -487,9 +643,45 @@ int queue_push(Engine<R>& e) {
   return 0;
 }
 
+// blocks of the fused selection this engine launches (0: the separate launches), from the
+// device's cooperative-launch support and the kernel's occupancy
+template <class R>
+int queue_fused_select_blocks() {
+  int dev = 0, coop = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_select_refill_coop<R>, SELC_THREADS,
+                                                    0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (coop && per * sms >= SELC_BLOCKS) ? SELC_BLOCKS : 0;
+}
+
 template <class R>
 int queue_select_refill(Engine<R>& e) {
   cudaStream_t st = e.st;
+  if (e.sel_blocks > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(e.sel_blocks);
+    cfg.blockDim = dim3(SELC_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    BNB_CUDA_OK(cudaLaunchKernelEx(
+        &cfg, k_select_refill_coop<R>, e.K, e.p, e.dmax, e.lockstep, (const int*)e.pool_hw,
+        e.pool_valid, (const double*)e.pool_lb, (const unsigned*)e.pool_key,
+        (const int*)e.pool_depth, (const int*)e.pool_warm, (const int*)e.pool_fix, e.free_stack,
+        e.free_top, (const R*)e.warm_beta, (const R*)e.warm_V, e.warm_ref, e.warm_stack,
+        e.warm_top, (const double*)e.inc_ub, (const double*)e.params_d, e.sel, e.sel_state,
+        e.poolmin, e.free_slots, e.popped, e.fix, e.beta, e.V, e.slot_active, e.slot_iters,
+        e.slot_lbp, e.slot_depth, e.slot_nfix, e.slot_fixl));
+    return 0;
+  }
   const int g = pool_grid(e.qcap);
   k_sel_reset<<<1, 256, 0, st>>>(e.sel, e.sel_state, e.poolmin);
   k_sel_pass1<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_lb, e.pool_key, e.pool_warm,
@@ -525,6 +717,7 @@ int queue_status(Engine<R>& e) {
 }
 
 #define INST(R)                                      \
+  template int queue_fused_select_blocks<R>();       \
   template int queue_init<R>(Engine<R>&);            \
   template int queue_push<R>(Engine<R>&);            \
   template int queue_select_refill<R>(Engine<R>&);   \

@@ -731,3 +731,20 @@ def test_node_log_certificates_match_oracle_full_size():
         log = bnb.bnb_get_node_log(h)
     assert log["count"] == 128
     _reverify(inst, lam0, lam2, M, log)
+
+
+@pytest.mark.parametrize("lockstep", [0, 1])
+@pytest.mark.parametrize("K", [1, 8, 64])
+def test_fused_selection_same_answer_as_separate_launches(K, lockstep):
+    """The round's selection and refill as one cooperative launch (options.fused_select = 1,
+    the default) and as separate launches: both reach the brute-force optimum at p = 16,
+    with continuous refill and with Algorithm 1's lockstep batches."""
+    inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    for fused in (1, 0):
+        with _handle(inst, lam0, lam2, M, 3, K=K, node_tol=1e-7, max_admm_iter=5000,
+                     lockstep=lockstep, fused_select=fused) as h:
+            res = bnb.bnb_solve(h, 1e-9)
+        assert tuple(np.nonzero(res["beta"])[0]) == br.support, fused
+        assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+        assert res["lb"] <= br.objective * (1 + 1e-9)
