@@ -555,13 +555,9 @@ TRAFFIC = {
     # (stage, workload, K, precision, fused tile width, clusters of two sharing X, CTA pairs,
     #  transposed)
     ("gemm_xtu_prox", "c2", 512, "tc3", 176, False, True, False): {
-        "blocks": _PAIR_NT, "sources": "cbfa68214a12d6bb", "bytes": 45.185024e6 + 0.526592e6,
+        "blocks": _PAIR_NT, "sources": "50944af0a1ee1eec", "bytes": 45.185152e6 + 0.581760e6,
         "note": _NOTE.format(k="tc_gemm_pair_kernel<176, 3, TcEpiAdmmPair<176, 0>, 12>",
                              f="fused_pair_untransposed_c2_K512_tc3.md")},
-    ("gemm_xtu_prox", "c2", 512, "tc3", 64, False, False, False): {
-        "blocks": _PERSIST, "sources": "445fd8171ad98c9b", "bytes": 45.183232e6 + 0.606976e6,
-        "note": _NOTE.format(k="tc_gemm_persist_kernel<64, 3, TcEpiAdmm<64, 0>, 12>",
-                             f="fused_xtu_prox_shapes_c2_K512_tc3.md")},
 }
 
 

@@ -29,6 +29,7 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--mv-crossover", type=int, default=-1)
     ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--fused-width", type=int, default=0)
     ap.add_argument("--no-graphs", action="store_true")
     return ap
 
@@ -46,7 +47,8 @@ def main():
     o = bnb.bnb_options_default(M=M, batch_K=a.K, rho=a.rho, precision=a.precision,
                                 queue_capacity=1 << 20, time_limit_s=1e9,
                                 mv_crossover=a.mv_crossover, use_graphs=0 if a.no_graphs else 1,
-                                fused_shape=a.fused_shape, u_shape=a.u_shape)
+                                fused_shape=a.fused_shape, u_shape=a.u_shape,
+                                fused_width=a.fused_width)
     with bnb.bnb_create(inst.X, inst.y, lam0, c["lam2"], o) as h:
         bnb.bnb_solve_start(h, 1e-4)
         t0 = time.time()
