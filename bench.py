@@ -82,8 +82,8 @@ def parse():
                          "4 untransposed on CTA pairs")
     ap.add_argument("--fused-width", type=int, default=0,
                     help="tile width of the fused X^T U' product (0: measured at setup)")
-    ap.add_argument("--fused-select", type=int, default=1, choices=[0, 1],
-                    help="selection and refill as one cooperative launch (1) or separate launches")
+    ap.add_argument("--fused-select", type=int, default=0, choices=[0, 1],
+                    help="the selection as one cooperative launch (1) or separate launches (0)")
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2],
                     help="U' = H W'^T: 0 measured at setup, 1 cluster-reduced, 2 CTA pairs split-K")
     ap.add_argument("--mv-crossover", type=int, default=-1,

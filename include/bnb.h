@@ -118,10 +118,11 @@ typedef struct {
                             offer 128 and 144 transposed, 80, 96, 128 and 176 untransposed;
                             one CTA per tile 64, 80, 96, 128).  A width no shape offers
                             fails bnb_create with BNB_EINVAL. */
-  int fused_select;      /* 1 (default): a round's best-first selection and slot refill run as
-                            one cooperative launch whose blocks meet at (bounded) grid
-                            barriers, where the device supports it; 0: as eight separate
-                            launches.  Same selection either way. */
+  int fused_select;      /* 1: a round's best-first selection runs as one cooperative launch
+                            whose blocks meet at (bounded) grid barriers, where the device
+                            supports it; 0 (default): as seven separate launches.  The same
+                            selection either way; the slot refill follows in a launch of its
+                            own. */
   int log_nodes;         /* tracing: record the first log_nodes nodes certified in each solve
                             (fixings, FP64 residual, certified bound; bnb_get_node_log), in
                             [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)

@@ -429,7 +429,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->ub_polish = 1;
   o->log_nodes = 0;
   o->fused_width = 0;
-  o->fused_select = 1;
+  o->fused_select = 0;
   return BNB_OK;
 }
 

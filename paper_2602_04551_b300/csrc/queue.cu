@@ -460,11 +460,12 @@ __global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, con
                  slot_iters, slot_lbp, slot_depth, slot_nfix, slot_fixl);
 }
 
-// ---- the selection and refill of a round in one cooperative launch ----
-// The steps above (reset, pass 1, three scans, two passes, collection, refill) are
-// dependent, and as separate launches most of their time is launch and ramp latency; here
-// the blocks of one cooperative launch (all co-resident) meet at grid barriers between
-// the steps.  Every barrier wait is bounded (2^24 polls and 1 s): a block that gives up
+// ---- the selection of a round in one cooperative launch ----
+// The steps above (reset, pass 1, three scans, two passes, collection) are dependent, and
+// as separate launches much of their time is launch and ramp latency; here the blocks of
+// one cooperative launch (all co-resident) meet at grid barriers between the steps.  The
+// refill (one block per popped node, copying its warm start) stays a launch of its own:
+// with wide batches it moves K rows of p values and wants the whole GPU.  Every barrier wait is bounded (2^24 polls and 1 s): a block that gives up
 // sets bit 8 of the error word and leaves, and the solve then ends with an error.
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a) {
@@ -516,7 +517,7 @@ constexpr int SELC_THREADS = 1024;   // the scans' block width
 constexpr int SELC_BLOCKS = 64;      // co-resident blocks of the fused selection
 
 template <class R>
-__global__ void __launch_bounds__(SELC_THREADS) k_select_refill_coop(
+__global__ void __launch_bounds__(SELC_THREADS) k_select_coop(
     int K, int p, int dmax, int lockstep, const int* __restrict__ pool_hw, uint8_t* pool_valid,
     const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
     const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
@@ -544,12 +545,6 @@ __global__ void __launch_bounds__(SELC_THREADS) k_select_refill_coop(
   }
   sel_collect_body(blk, nblk, pool_hw, pool_valid, pool_key, free_stack, free_top, sel_state,
                    popped);
-  if (!coop_grid_sync(sel_state)) return;
-  const int out = sel_state[SS_OUT];
-  for (int t = blk; t < out; t += nblk)
-    refill_body<R>(t, p, dmax, popped, free_slots, pool_lb, pool_depth, pool_warm, pool_fix,
-                   warm_beta, warm_V, warm_ref, warm_stack, warm_top, fix, beta, V, slot_active,
-                   slot_iters, slot_lbp, slot_depth, slot_nfix, slot_fixl);
 }
 
 __global__ void k_status(int K, const int* __restrict__ slot_active,
@@ -651,7 +646,7 @@ int queue_fused_select_blocks() {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_select_refill_coop<R>, SELC_THREADS,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_select_coop<R>, SELC_THREADS,
                                                     0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -673,13 +668,19 @@ int queue_select_refill(Engine<R>& e) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     BNB_CUDA_OK(cudaLaunchKernelEx(
-        &cfg, k_select_refill_coop<R>, e.K, e.p, e.dmax, e.lockstep, (const int*)e.pool_hw,
+        &cfg, k_select_coop<R>, e.K, e.p, e.dmax, e.lockstep, (const int*)e.pool_hw,
         e.pool_valid, (const double*)e.pool_lb, (const unsigned*)e.pool_key,
         (const int*)e.pool_depth, (const int*)e.pool_warm, (const int*)e.pool_fix, e.free_stack,
         e.free_top, (const R*)e.warm_beta, (const R*)e.warm_V, e.warm_ref, e.warm_stack,
         e.warm_top, (const double*)e.inc_ub, (const double*)e.params_d, e.sel, e.sel_state,
         e.poolmin, e.free_slots, e.popped, e.fix, e.beta, e.V, e.slot_active, e.slot_iters,
         e.slot_lbp, e.slot_depth, e.slot_nfix, e.slot_fixl));
+    k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb,
+                                     e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
+                                     e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.fix,
+                                     e.beta, e.V, e.slot_active, e.slot_iters, e.slot_lbp,
+                                     e.slot_depth, e.slot_nfix, e.slot_fixl);
+    BNB_CUDA_OK(cudaGetLastError());
     return 0;
   }
   const int g = pool_grid(e.qcap);

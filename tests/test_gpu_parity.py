@@ -736,9 +736,9 @@ def test_node_log_certificates_match_oracle_full_size():
 @pytest.mark.parametrize("lockstep", [0, 1])
 @pytest.mark.parametrize("K", [1, 8, 64])
 def test_fused_selection_same_answer_as_separate_launches(K, lockstep):
-    """The round's selection and refill as one cooperative launch (options.fused_select = 1,
-    the default) and as separate launches: both reach the brute-force optimum at p = 16,
-    with continuous refill and with Algorithm 1's lockstep batches."""
+    """The round's selection as one cooperative launch (options.fused_select = 1, the
+    default) and as separate launches: both reach the brute-force optimum at p = 16, with
+    continuous refill and with Algorithm 1's lockstep batches."""
     inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
     br = brute.solve(inst.X, inst.y, lam0, lam2, M)
     for fused in (1, 0):
