@@ -20,6 +20,8 @@ batched upper bound, and prunes/branches into the pool.
   fp32_path the same timed rounds with the FP32 CUDA-core ADMM (no tensor cores)
   roofline  the dominant kernel of a profiled round (CUDA events per launch)
   cpu_baseline the FP64 oracle's node solves on the host cores, bounded sample
+  reverify  the certificates of a short logged solve of the same workload re-checked by
+            the FP64 oracle at the logged residuals
   certified_solves  full solves to gap 1e-4 over five lambda0 values chosen so that
             the first incumbent has 5, 8, 12, 16 and 20 nonzeros, mixed precision
             and plain FP64, per instance; with `reverify`: certificates of a real
@@ -103,6 +105,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-time-limit", type=float, default=20.0)
     ap.add_argument("--fp32-steps", type=int, default=4)
+    ap.add_argument("--reverify-nodes", type=int, default=128,
+                    help="certificates of a short logged solve re-checked by the oracle (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--fp64-K", type=int, default=512,
@@ -295,6 +299,9 @@ def run_mine(args, rank, world):
         note("e2e done")
         out["fp64"] = run_fp64(args, inst, lam0, lam2, M, dev)
         note("fp64 same-batch done")
+        if world == 1 and args.reverify_nodes > 0:
+            out["reverify"] = run_reverify(args, inst, lam0, lam2, M, dev)
+            note("reverify done")
         if world == 1 and not args.no_side:
             out["fp32"] = run_fp32_side(args, inst, lam0, lam2, M, dev)
             note("fp32 side done")
@@ -741,7 +748,7 @@ def reverify_logs(inst, lam0, lam2, M, logs):
     exact ones by relative error, screened ones by the excess D(r) - bound against their
     recorded interval width (a valid screened bound has 0 <= excess <= width)."""
     from oracle import relax
-    rel, ratio, n_ex, n_sc, bad = [], [], 0, 0, 0
+    rel, ratio, loose, n_ex, n_sc, bad = [], [], [], 0, 0, 0
     for log in logs:
         for k in range(log["count"]):
             d = relax.dual_value(inst.X, inst.y, log["r"][k], log["fix"][k], lam0, lam2, M)
@@ -754,12 +761,40 @@ def reverify_logs(inst, lam0, lam2, M, logs):
                 n_sc += 1
                 ex = d - log["lb"][k]
                 ratio.append(ex / log["width"][k] if log["width"][k] > 0 else 0.0)
+                loose.append(ex / max(1.0, abs(d)))
                 bad += int(ex < -tol or ex > log["width"][k] * (1 + 1e-9) + tol)
     return {"n_certs": n_ex + n_sc, "exact": n_ex, "screened": n_sc,
             "exact_max_rel": float(max(rel)) if rel else None,
             "exact_median_rel": float(np.median(rel)) if rel else None,
             "screened_max_excess_over_width": float(max(ratio)) if ratio else None,
+            # how far a screened bound sits below the exact FP64 D(r) at the same r
+            "screened_max_rel_below_exact": float(max(loose)) if loose else None,
+            "screened_median_rel_below_exact": float(np.median(loose)) if loose else None,
             "violations": bad}
+
+
+def run_reverify(args, inst, lam0, lam2, M, dev):
+    """A short solve of the timed workload that logs its first --reverify-nodes certified
+    nodes; each logged certificate is re-checked by the FP64 oracle's Eq. dual at the
+    logged residual (reverify_logs)."""
+    import paper_2602_04551_b300 as bnb
+    o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every, device=dev,
+                                precision=PREC[args.precision], rho=args.rho,
+                                relax_alpha=args.alpha, queue_capacity=1 << 20,
+                                time_limit_s=60.0, log_nodes=args.reverify_nodes)
+    with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
+        bnb.bnb_solve_start(h, 1e-4)
+        while True:
+            bnb.bnb_solve_launch(h, 5)
+            pr = bnb.bnb_solve_poll(h)
+            if pr["done"] or pr["nodes"] >= args.reverify_nodes:
+                break
+        log = bnb.bnb_get_node_log(h)
+        bnb.bnb_solve_finish(h)
+    t0 = time.perf_counter()
+    out = reverify_logs(inst, lam0, lam2, M, [log])
+    out["oracle_seconds"] = time.perf_counter() - t0
+    return out
 
 
 def run_certified(args, seed):
@@ -1031,6 +1066,7 @@ def mine_line(args, out, world, ms, nodes, pk, cpu):
         "rounds_per_step": args.rounds_per_step,
         "rounds": out.get("rounds"),
         "ms_per_round": ms / max(1, out.get("rounds") or args.steps * args.rounds_per_step),
+        "reverify": out.get("reverify"),
         "fp32_path": out.get("fp32"),
         "certified_solves": out.get("certified"),
         "serve": out.get("serve"),

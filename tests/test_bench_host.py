@@ -198,3 +198,26 @@ def test_greedy_lambda0_orthonormal_design(bench):
     for k in (1, 4, 7):
         lam0 = bench.greedy_lambda0(Q, y, lam2, M, k)
         assert drops[k] < lam0 < drops[k - 1]
+
+
+def test_reverify_logs_counts_and_flags(bench):
+    """reverify_logs against the oracle on a fabricated log: an exact bound equal to D(r),
+    a screened bound inside its interval, and one claiming more than D(r) (a violation)."""
+    import numpy as np
+    import datagen
+    from oracle import relax
+    inst = datagen.config_instance("c1", 0)
+    lam2 = 0.01
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = 0.05 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    rng = np.random.default_rng(2)
+    fix = datagen.random_fixings(inst.p, 3, rng, 5)
+    r = inst.y[None, :] * 0.9 + rng.normal(0, 0.05, (3, inst.n))
+    d = np.array([relax.dual_value(inst.X, inst.y, r[k], fix[k], lam0, lam2, M) for k in range(3)])
+    log = {"count": 3, "fix": fix, "r": r, "lb": np.array([d[0], d[1] - 0.01, d[2] + 0.01]),
+           "exact": np.array([1.0, 0.0, 0.0]), "width": np.array([0.0, 0.02, 0.02])}
+    out = bench.reverify_logs(inst, lam0, lam2, M, [log])
+    assert out["n_certs"] == 3 and out["exact"] == 1 and out["screened"] == 2
+    assert out["violations"] == 1
+    assert out["exact_max_rel"] <= 1e-15
+    assert out["screened_max_rel_below_exact"] == pytest.approx(0.01 / max(1.0, abs(d[1])))
