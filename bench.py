@@ -84,6 +84,9 @@ def parse():
                          "4 untransposed on CTA pairs")
     ap.add_argument("--fused-width", type=int, default=0,
                     help="tile width of the fused X^T U' product (0: measured at setup)")
+    ap.add_argument("--exact-bounds", type=int, default=0, choices=[0, 1],
+                    help="exact FP64 certificate terms for every branched node (1) or only "
+                         "where they can change the prune decision (0)")
     ap.add_argument("--fused-select", type=int, default=0, choices=[0, 1],
                     help="the selection as one cooperative launch (1) or separate launches (0)")
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2],
@@ -234,7 +237,8 @@ def run_mine(args, rank, world):
                                   queue_capacity=1 << 21, time_limit_s=1e9, rho=args.rho,
                                   relax_alpha=args.alpha, mv_crossover=args.mv_crossover,
                                   fused_shape=args.fused_shape, u_shape=args.u_shape,
-                                  fused_width=args.fused_width, fused_select=args.fused_select)
+                                  fused_width=args.fused_width, fused_select=args.fused_select,
+                                  exact_bounds=args.exact_bounds)
     h = bnb.bnb_create(inst.X, inst.y, lam0, lam2, opt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
@@ -781,7 +785,8 @@ def run_reverify(args, inst, lam0, lam2, M, dev):
     o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every, device=dev,
                                 precision=PREC[args.precision], rho=args.rho,
                                 relax_alpha=args.alpha, queue_capacity=1 << 20,
-                                time_limit_s=60.0, log_nodes=args.reverify_nodes)
+                                time_limit_s=60.0, log_nodes=args.reverify_nodes,
+                                exact_bounds=args.exact_bounds)
     with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
         bnb.bnb_solve_start(h, 1e-4)
         while True:

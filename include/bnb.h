@@ -123,6 +123,13 @@ typedef struct {
                             supports it; 0 (default): as seven separate launches.  The same
                             selection either way; the slot refill follows in a launch of its
                             own. */
+  int exact_bounds;      /* bnb_solve's certificates: 0 (default) takes the exact FP64 nu terms
+                            only where they can change the prune decision, so a branched
+                            node keeps the cheaper screened bound (certified, but lower than
+                            the exact value at r); 1 takes them for every node it does not
+                            prune, so the bound passed to the children and to the global
+                            lower bound is the exact value of Proposition 1 at r.  Pruning
+                            is the same either way. */
   int log_nodes;         /* tracing: record the first log_nodes nodes certified in each solve
                             (fixings, FP64 residual, certified bound; bnb_get_node_log), in
                             [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)

@@ -55,7 +55,8 @@ class bnb_options(ctypes.Structure):
                 ("lockstep", ctypes.c_int), ("mv_crossover", ctypes.c_int),
                 ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int),
                 ("ub_polish", ctypes.c_int), ("fused_width", ctypes.c_int),
-                ("fused_select", ctypes.c_int), ("log_nodes", ctypes.c_int)]
+                ("fused_select", ctypes.c_int), ("exact_bounds", ctypes.c_int),
+                ("log_nodes", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):

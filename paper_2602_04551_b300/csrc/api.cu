@@ -430,6 +430,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->log_nodes = 0;
   o->fused_width = 0;
   o->fused_select = 0;
+  o->exact_bounds = 0;
   return BNB_OK;
 }
 
@@ -543,6 +544,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.log_nodes < 0 || o.log_nodes > (1 << 16)) return fail(BNB_EINVAL, "log_nodes must be in [0, 65536]");
   if (o.fused_width < 0 || o.fused_width > 256) return fail(BNB_EINVAL, "fused_width must be in [0, 256]");
   if (o.fused_select != 0 && o.fused_select != 1) return fail(BNB_EINVAL, "fused_select must be 0 or 1");
+  if (o.exact_bounds != 0 && o.exact_bounds != 1) return fail(BNB_EINVAL, "exact_bounds must be 0 or 1");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
@@ -871,7 +873,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   if (pf) {
     prof_begin(pf, e.st);
     if (int rc = certify_screen(e, nullptr)) return rc;
-    if (int rc = certify_exact(e, true, e.inc_ub)) return rc;
+    if (int rc = certify_exact(e, o.exact_bounds ? 2 : 1, e.inc_ub)) return rc;
     if (int rc = node_log(e, e.inc_ub)) return rc;
     prof_end(pf, e.st, PK_CERT);
     prof_begin(pf, e.st);
@@ -894,7 +896,7 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
     if (rc) return rc;
     BNB_CUDA_OK(ce);
     if (int rc2 = certify_screen(e, nullptr)) return rc2;
-    if (int rc2 = certify_exact(e, true, e.inc_snap)) return rc2;
+    if (int rc2 = certify_exact(e, o.exact_bounds ? 2 : 1, e.inc_snap)) return rc2;
     if (int rc2 = node_log(e, e.inc_snap)) return rc2;
     BNB_CUDA_OK(cudaStreamWaitEvent(e.st, e.ev_join, 0));
     if (int rc2 = branch_fallback(e)) return rc2;

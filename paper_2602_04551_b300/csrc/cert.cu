@@ -340,8 +340,11 @@ __global__ void k_cert_decide(const double* __restrict__ cpart, int nbm, int K,
   const double lb = base - su;
   bool exact = true;
   if (use_threshold) {
+    // 1: the exact terms only where they can change the prune decision; 2: also for every
+    // node that will be branched (its bound is then the exact value at r for its children
+    // and the global bound), skipped only for nodes the cheap bound already prunes
     const double thr = inc_ub[0] * (1.0 - params[0]);
-    if (lb >= thr || lb + ss < thr) exact = false;
+    if (lb >= thr || (use_threshold == 1 && lb + ss < thr)) exact = false;
   }
   base_out[q] = base;
   need[q] = exact ? 1 : 0;
@@ -370,7 +373,7 @@ __global__ void k_cert_final(const int* __restrict__ ret_slot, const int* __rest
 template <class R>
 int certify(Engine<R>& e, const double* r_given, bool use_threshold) {
   if (int rc = certify_screen(e, r_given)) return rc;
-  return certify_exact(e, use_threshold, e.inc_ub);
+  return certify_exact(e, use_threshold ? 1 : 0, e.inc_ub);
 }
 
 // r = y - U (or the given r) in FP64 and FP32, then the FP32 screen of X^T r with its
@@ -408,7 +411,7 @@ int certify_screen(Engine<R>& e, const double* r_given) {
 // the decision per node (against the incumbent *inc), the exact FP64 terms it needs and
 // the certified bound
 template <class R>
-int certify_exact(Engine<R>& e, bool use_threshold, const double* inc) {
+int certify_exact(Engine<R>& e, int use_threshold, const double* inc) {
   using C = TileCfg<R>;
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
@@ -416,7 +419,7 @@ int certify_exact(Engine<R>& e, bool use_threshold, const double* inc) {
   prof_begin(e.prof, st);
   const dim3 gx(K, CX_G);
   k_cert_decide<<<K, 32, 0, st>>>(e.cpart, nbm, K, e.ret_slot, e.ret_count, e.cert_rr, e.cert_yr,
-                                  e.slot_lbp, inc, e.params_d, use_threshold ? 1 : 0,
+                                  e.slot_lbp, inc, e.params_d, use_threshold,
                                   e.cx_base, e.cx_need, e.cert_lb, e.node_lb, e.cert_width);
   k_cert_terms<<<gx, 256, 0, st>>>(e.X64, e.r64, e.fix, e.cflag, n, p, e.P, e.ret_slot,
                                    e.ret_count, 1, e.cx_need, e.cx_part);
@@ -494,7 +497,7 @@ template int certify<float>(Engine<float>&, const double*, bool);
 template int certify<double>(Engine<double>&, const double*, bool);
 template int certify_screen<float>(Engine<float>&, const double*);
 template int certify_screen<double>(Engine<double>&, const double*);
-template int certify_exact<float>(Engine<float>&, bool, const double*);
-template int certify_exact<double>(Engine<double>&, bool, const double*);
+template int certify_exact<float>(Engine<float>&, int, const double*);
+template int certify_exact<double>(Engine<double>&, int, const double*);
 
 }  // namespace bnb

@@ -230,7 +230,7 @@ template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double 
 template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */,
                                bool use_threshold);
 template <class R> int certify_screen(Engine<R>& e, const double* r_given);
-template <class R> int certify_exact(Engine<R>& e, bool use_threshold, const double* inc);
+template <class R> int certify_exact(Engine<R>& e, int use_threshold, const double* inc);
 template <class R> int node_log(Engine<R>& e, const double* inc);
 template <class R> int branch_support(Engine<R>& e, bool write_z, bool memo = false,
                                       bool defer_fallback = false);

@@ -748,3 +748,20 @@ def test_fused_selection_same_answer_as_separate_launches(K, lockstep):
         assert tuple(np.nonzero(res["beta"])[0]) == br.support, fused
         assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
         assert res["lb"] <= br.objective * (1 + 1e-9)
+
+
+def test_exact_bounds_option_same_answer_and_exact_certificates():
+    """options.exact_bounds = 1: a branched node's certificate is the exact FP64 value at its
+    residual (the node log shows every logged bound exact and equal to the oracle's Eq. dual),
+    and the solve returns the brute-force optimum as with the default."""
+    inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, 3, K=8, node_tol=1e-7, max_admm_iter=5000,
+                 exact_bounds=1, log_nodes=64) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+        log = bnb.bnb_get_node_log(h)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+    thr_pruned = log["lb"] >= log["threshold"]
+    assert np.all(log["exact"][~thr_pruned] == 1.0)
+    _reverify(inst, lam0, lam2, M, log)
