@@ -7,12 +7,14 @@
 //
 // B300 has little FP64 throughput, so the p products X_i^T r are not all taken
 // in FP64.  A screening product a_i = fl32(X32_i^T r32) runs on CUDA cores in
-// FP32 (one rounding per fused multiply-add, K-chunked in order), and
-//   |a_i - X_i^T r| <= e_i = (gamma_n (1+u)^2 + 2u(1+u)) ||X_i|| ||r|| (1 + 1e-3),
-//   u = 2^-24, gamma_n = n u / (1 - n u)
-// (standard bound for a sum of n products, Higham, "Accuracy and Stability of
-// Numerical Algorithms", Sec. 3.1, plus the rounding of X and r to FP32, and
-// Cauchy-Schwarz).  For a free coordinate nu_i(x) = 0 exactly when x <= x0
+// FP32 (one rounding per fused multiply-add, blocked summation), and
+//   |a_i - X_i^T r| <= e_i = (gamma_d (1+u)^2 + 2u(1+u)) ||X_i|| ||r|| (1 + 1e-3),
+//   u = 2^-24, gamma_d = d u / (1 - d u)
+// (standard bound for a sum of products in which no product meets more than d
+// roundings, Higham, "Accuracy and Stability of Numerical Algorithms", Secs. 3.1 and
+// 4.2, plus the rounding of X and r to FP32, and Cauchy-Schwarz; d is the depth of the
+// blocked sum plus two, screen_depth(n) + 2, about 37 + n / 128).  For a free
+// coordinate nu_i(x) = 0 exactly when x <= x0
 // (x0 = 2 sqrt(l0 l2), or l0/M + l2 M in the linear regime), so |a_i| + e_i <= x0
 // proves the term is zero.  An F1 coordinate (nu_i = h) and a free coordinate the
 // screen cannot settle have |X_i^T r| in [|a_i| - e_i, |a_i| + e_i]; both nu_i are
@@ -21,7 +23,7 @@
 // whenever the exact FP64 terms could not change the prune decision (k_cert_decide);
 // otherwise, and always for bnb_relax_batch and bnb_dual_bound, those coordinates get
 // their X_i^T r in FP64.  F0 terms are zero.  The FP64 path (R = double) screens in
-// FP64 with u = 2^-53.
+// FP64 with u = 2^-53 and d = n + 2.
 #include <cfloat>
 #include "engine.cuh"
 #include "gemm_simt.cuh"
@@ -118,22 +120,55 @@ struct EpiScreen {
 // Screening product of the FP32 engine, a[q][m] = fl32(X32_m^T r32_q) for the retired
 // columns q < R, followed by the EpiScreen bookkeeping.  The shape is tall and skinny
 // (p features x a few dozen retired nodes, contraction n), so the tiles are 32 x 32
-// (about two tiles per SM at R <= 64) and the contraction is split over the four
-// 64-thread groups of a CTA (4 x 4 outputs per thread, register-prefetched 32-wide k
-// steps); the four partial sums are added in a fixed order, so the result does not
-// depend on scheduling.  The rounding bound holds for any summation order; the host
-// adds the SC_G - 1 extra additions to n in gamma.
-constexpr int SC_BM = 32, SC_BN = 32, SC_BK = 32, SC_G = 4, SC_LD = SC_BK + 4;
+// (about one tile per SM at R <= 32) and the contraction is split over the four 64-thread
+// groups of a CTA (4 x 4 outputs per thread, 32-wide k steps); the four partial sums are
+// added in a fixed order, so the result does not depend on scheduling.  The operand tiles
+// stream through SC_NS shared-memory stages by cp.async (16-byte copies when n is a
+// multiple of 4, else 4-byte ones), so SC_NS - 1 k steps are in flight while one is
+// multiplied: with one CTA per SM a single step in flight left the kernel waiting on memory.
+//
+// The summation is blocked (Higham, Sec. 4.2): each 32-wide k step is accumulated from
+// zero (SC_BK fused multiply-adds) and then added to the thread's running total, so a
+// product passes through at most SC_BK + (k steps of its group) + SC_G - 1 roundings
+// instead of n + SC_G - 1, and the bound of Sec. 3.1 holds with gamma of that depth
+// (screen_depth); at n = 1000 that is 43 instead of 1003.
+constexpr int SC_BM = 32, SC_BN = 32, SC_BK = 32, SC_G = 4, SC_LD = SC_BK + 4, SC_NS = 3;
+constexpr int SC_STAGE_FLOATS = 2 * SC_G * SC_BM * SC_LD;
+constexpr int SC_SMEM = SC_NS * SC_STAGE_FLOATS * (int)sizeof(float);
 
+// the most roundings a product meets in k_screen32 at contraction length n
+inline int screen_depth(int n) {
+  const int nk = (n + SC_BK - 1) / SC_BK, per = (nk + SC_G - 1) / SC_G;
+  return SC_BK + per + SC_G - 1;
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X32, int n, int p,
                                                      const float* __restrict__ rS,
                                                      const int* __restrict__ ret_count,
                                                      EpiScreen<float> epi) {
-  // operand tiles; after the k loop the same bytes hold the four partial tiles
-  __shared__ __align__(16) float sm[2 * SC_G * SC_BM * SC_LD];
-  static_assert(SC_G * SC_BM * (SC_BN + 1) <= 2 * SC_G * SC_BM * SC_LD, "partial tiles fit");
-  auto As = reinterpret_cast<float(*)[SC_BM][SC_LD]>(sm);
-  auto Bs = reinterpret_cast<float(*)[SC_BN][SC_LD]>(sm + SC_G * SC_BM * SC_LD);
+  // SC_NS stages of operand tiles [stage][A|B][group][row][k]; after the k loop the first
+  // bytes hold the four partial tiles
+  extern __shared__ __align__(16) float sm[];
+  static_assert(SC_G * SC_BM * (SC_BN + 1) <= SC_STAGE_FLOATS, "partial tiles fit");
+  auto As = [&](int st, int g, int r) { return sm + st * SC_STAGE_FLOATS + (g * SC_BM + r) * SC_LD; };
+  auto Bs = [&](int st, int g, int r) {
+    return sm + st * SC_STAGE_FLOATS + ((SC_G + g) * SC_BM + r) * SC_LD;
+  };
   auto red = reinterpret_cast<float(*)[SC_BM][SC_BN + 1]>(sm);
   const int R = *ret_count;
   const int q0 = blockIdx.y * SC_BN, m0 = blockIdx.x * SC_BM;
@@ -143,16 +178,28 @@ __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X
   const int nk = (n + SC_BK - 1) / SC_BK;
   const int per = (nk + SC_G - 1) / SC_G;
   const int kb0 = g * per;
-  float ra[16], rb[16];
-  auto load = [&](int kb) {
+  // copies of k step kb of this group into stage st (zero-filled outside the operands)
+  auto issue = [&](int kb, int st) {
     const int k0 = kb * SC_BK;
     const bool live = kb < nk;
+    if constexpr (VEC) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int e = t + 64 * i, kk = e & 31, rr = e >> 5;
-      const int k = k0 + kk, m = m0 + rr, q = q0 + rr;
-      ra[i] = (live && k < n && m < p) ? X32[(long long)m * n + k] : 0.f;
-      rb[i] = (live && k < n && q < R) ? rS[(long long)q * n + k] : 0.f;
+      for (int i = 0; i < 4; ++i) {
+        const int e = t + 64 * i, rr = e >> 3, kk = (e & 7) * 4;
+        const int k = k0 + kk, m = m0 + rr, q = q0 + rr;
+        const bool va = live && k < n && m < p, vb = live && k < n && q < R;
+        cp_async16(As(st, g, rr) + kk, va ? X32 + (long long)m * n + k : X32, va);
+        cp_async16(Bs(st, g, rr) + kk, vb ? rS + (long long)q * n + k : rS, vb);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int e = t + 64 * i, kk = e & 31, rr = e >> 5;
+        const int k = k0 + kk, m = m0 + rr, q = q0 + rr;
+        const bool va = live && k < n && m < p, vb = live && k < n && q < R;
+        cp_async4(As(st, g, rr) + kk, va ? X32 + (long long)m * n + k : X32, va);
+        cp_async4(Bs(st, g, rr) + kk, vb ? rS + (long long)q * n + k : rS, vb);
+      }
     }
   };
   float acc[4][4];
@@ -160,35 +207,48 @@ __global__ void __launch_bounds__(256, 2) k_screen32(const float* __restrict__ X
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  load(kb0);
-  for (int it = 0; it < per; ++it) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int e = t + 64 * i, kk = e & 31, rr = e >> 5;
-      As[g][rr][kk] = ra[i];
-      Bs[g][rr][kk] = rb[i];
-    }
+  for (int st = 0; st < SC_NS - 1; ++st) {
+    if (st < per) issue(kb0 + st, st);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int it = 0; it < per; ++it) {
+    // this thread's copies of step `it` are done; the barrier makes everyone's visible and
+    // retires step it - 1, whose stage the next copies overwrite
+    asm volatile("cp.async.wait_group %0;" ::"n"(SC_NS - 2) : "memory");
     __syncthreads();
-    if (it + 1 < per) load(kb0 + it + 1);
+    if (it + SC_NS - 1 < per) issue(kb0 + it + SC_NS - 1, (it + SC_NS - 1) % SC_NS);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int st = it % SC_NS;
+    float c[4][4];                                // this k step, from zero
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
 #pragma unroll
     for (int k4 = 0; k4 < SC_BK; k4 += 4) {
       float4 a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = *(const float4*)&As[g][tx + 8 * i][k4];
+      for (int i = 0; i < 4; ++i) a[i] = *(const float4*)(As(st, g, tx + 8 * i) + k4);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = *(const float4*)&Bs[g][ty + 8 * j][k4];
+      for (int j = 0; j < 4; ++j) b[j] = *(const float4*)(Bs(st, g, ty + 8 * j) + k4);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          acc[i][j] = fmaf(a[i].x, b[j].x, acc[i][j]);
-          acc[i][j] = fmaf(a[i].y, b[j].y, acc[i][j]);
-          acc[i][j] = fmaf(a[i].z, b[j].z, acc[i][j]);
-          acc[i][j] = fmaf(a[i].w, b[j].w, acc[i][j]);
+          c[i][j] = fmaf(a[i].x, b[j].x, c[i][j]);
+          c[i][j] = fmaf(a[i].y, b[j].y, c[i][j]);
+          c[i][j] = fmaf(a[i].z, b[j].z, c[i][j]);
+          c[i][j] = fmaf(a[i].w, b[j].w, c[i][j]);
         }
     }
-    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] += c[i][j];
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();                                // every stage read before red overwrites it
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -387,7 +447,7 @@ int certify_screen(Engine<R>& e, const double* r_given) {
                                     e.cert_rr, e.cert_yr, e.cert_rn);
   BNB_CUDA_OK(cudaGetLastError());
   const double u = (sizeof(R) == 4) ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
-  const double nu_ = (double)(n + 2 + (sizeof(R) == 4 ? SC_G : 0)) * u;
+  const double nu_ = (double)((sizeof(R) == 4 ? screen_depth(n) : n) + 2) * u;
   const double gam = nu_ / (1.0 - nu_);
   const double errc = (sizeof(R) == 4 ? (gam * (1 + u) * (1 + u) + 2 * u * (1 + u))
                                       : (gam * (1 + u) * (1 + u) + 2 * u)) * (1.0 + 1e-3);
@@ -397,8 +457,12 @@ int certify_screen(Engine<R>& e, const double* r_given) {
                          e.cpart, e.P, errc, x0, p, nbm, K};
   prof_begin(e.prof, st);
   if constexpr (sizeof(R) == 4) {
-    k_screen32<<<dim3(nbm, (K + SC_BN - 1) / SC_BN), 256, 0, st>>>((const float*)e.X32, n, p,
-                                                                 (const float*)e.rS, e.ret_count, epi);
+    // 16-byte copies need every row of X32 and rS to start on a 16-byte boundary
+    const bool vec = n % 4 == 0 && ((uintptr_t)e.X32 & 15) == 0 && ((uintptr_t)e.rS & 15) == 0;
+    auto kern = vec ? k_screen32<true> : k_screen32<false>;
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_SMEM));
+    kern<<<dim3(nbm, (K + SC_BN - 1) / SC_BN), 256, SC_SMEM, st>>>(
+        (const float*)e.X32, n, p, (const float*)e.rS, e.ret_count, epi);
     BNB_CUDA_OK(cudaGetLastError());
   } else {
     BNB_CUDA_OK((gemm_simt<R, true, false>(st, (const R*)e.X64, n, p, K, n, 1, e.ret_active,

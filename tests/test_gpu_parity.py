@@ -721,6 +721,18 @@ def test_node_log_certificates_match_oracle(prec):
     _reverify(inst, lam0, lam2, M, log)
 
 
+def test_node_log_certificates_match_oracle_odd_sizes():
+    """The node log of a solve on the n = 101, p = 503 instance: the certificate screen
+    takes its 4-byte-copy form there (n not a multiple of 4), and every logged bound is
+    still the oracle's Eq. dual at the logged residual, or below it within the width."""
+    inst, lam0, lam2, M = _inst_odd()
+    with _handle(inst, lam0, lam2, M, 3, K=64, log_nodes=150, time_limit_s=5.0) as h:
+        res = bnb.bnb_solve(h, 1e-4)
+        log = bnb.bnb_get_node_log(h)
+    assert log["count"] == min(150, res["nodes"]) > 0
+    _reverify(inst, lam0, lam2, M, log)
+
+
 def test_node_log_certificates_match_oracle_full_size():
     """The same at the benchmark's c2 shape and width (K = 512, TC3): 128 certificates of a
     real solve re-checked by the oracle."""
@@ -736,8 +748,8 @@ def test_node_log_certificates_match_oracle_full_size():
 @pytest.mark.parametrize("lockstep", [0, 1])
 @pytest.mark.parametrize("K", [1, 8, 64])
 def test_fused_selection_same_answer_as_separate_launches(K, lockstep):
-    """The round's selection as one cooperative launch (options.fused_select = 1, the
-    default) and as separate launches: both reach the brute-force optimum at p = 16, with
+    """The round's selection as one cooperative launch (options.fused_select = 1) and as
+    separate launches (the default): both reach the brute-force optimum at p = 16, with
     continuous refill and with Algorithm 1's lockstep batches."""
     inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
     br = brute.solve(inst.X, inst.y, lam0, lam2, M)
