@@ -143,7 +143,9 @@ __global__ void k_finalize_u(const R* __restrict__ Upart, int S, R* __restrict__
   }
 }
 
-// Node stop rule per slot (one block per slot)
+// Node stop rule per slot, one warp per slot (8 slots per 256-thread block): the slot's
+// partial sums are read lane-strided and added by butterfly shuffles, so no block barrier
+// separates the seven sums.
 template <class R>
 __global__ void k_stop(const R* __restrict__ XBpart, int S, const R* __restrict__ y, int n, int K,
                        const R* __restrict__ g3part, int nbm, const R* __restrict__ rstat,
@@ -153,43 +155,43 @@ __global__ void k_stop(const R* __restrict__ XBpart, int S, const R* __restrict_
                        int max_iter, double node_tol, const double* __restrict__ inc_ub,
                        const double* __restrict__ params, int use_inc,
                        const float* __restrict__ tstat, int nbt) {
-  __shared__ R sh[32];
-  const int s = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (s >= K) return;
   if (!slot_active[s]) {
-    if (threadIdx.x == 0) slot_retire[s] = 0;
+    if (lane == 0) slot_retire[s] = 0;
     return;
   }
   R xr = 0;
   R rs[2] = {0, 0};
   if (tstat) {
-    // per-tile column sums of the cluster-reduced products, added in tile order
+    // per-tile column sums of the cluster-reduced products
     R a[3] = {0, 0, 0};
-    for (int b = threadIdx.x; b < nbt; b += blockDim.x)
+    for (int b = lane; b < nbt; b += 32)
 #pragma unroll
       for (int t = 0; t < 3; ++t) a[t] += (R)tstat[((long long)t * nbt + b) * K + s];
-    rs[0] = block_sum(a[0], sh);
-    rs[1] = block_sum(a[1], sh);
-    xr = block_sum(a[2], sh);
+    rs[0] = warp_sum(a[0]);
+    rs[1] = warp_sum(a[1]);
+    xr = warp_sum(a[2]);
   } else {
     const long long zs = (long long)n * K, base = (long long)s * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = lane; i < n; i += 32) {
       R xb = XBpart[base + i];
       for (int z = 1; z < S; ++z) xb += XBpart[z * zs + base + i];
       R r = y[i] - xb;
       xr += r * r;
     }
-    xr = block_sum(xr, sh);
+    xr = warp_sum(xr);
     rs[0] = rstat[s];
     rs[1] = rstat[K + s];
   }
-  R q[4];
+  R q[4] = {0, 0, 0, 0};
+  for (int b = lane; b < nbm; b += 32)
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    R a = 0;
-    for (int b = threadIdx.x; b < nbm; b += blockDim.x) a += g3part[((long long)t * nbm + b) * K + s];
-    q[t] = block_sum(a, sh);
-  }
-  if (threadIdx.x == 0) {
+    for (int t = 0; t < 4; ++t) q[t] += g3part[((long long)t * nbm + b) * K + s];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) q[t] = warp_sum(q[t]);
+  if (lane == 0) {
     const double primal = 0.5 * (double)xr + (double)q[0];
     const double dual = -0.5 * (double)rs[0] + (double)rs[1] - (double)q[1];
     const double gap = (primal - dual) / fmax(1.0, fabs(primal));
@@ -313,7 +315,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   }
   e.admm_iters += iters;
   prof_begin(e.prof, st);
-  k_stop<R><<<K, 256, 0, st>>>(e.XBpart, S_check, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
+  k_stop<R><<<(K + 7) / 8, 256, 0, st>>>(e.XBpart, S_check, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
                                e.slot_active, e.slot_iters, e.slot_retire, e.slot_gap, e.slot_dual,
                                e.slot_primal, iters, max_iter, node_tol, e.inc_ub, e.params_d,
                                use_inc ? 1 : 0, e.tc_c1 > 0 ? e.tc_stat : nullptr, e.nbt);

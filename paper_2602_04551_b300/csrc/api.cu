@@ -235,6 +235,9 @@ static int allocate(Engine<R>& e) {
   ALLOC(e.ubb64, K * 2 * sm);
   ALLOC(e.ub_val, K);
   ALLOC(e.pol_flag, K);
+  ALLOC(e.ue_part, K * UE_NB);
+  ALLOC(e.ue_cnt, K);
+  ALLOC(e.push_w, K);
   ALLOC(e.inc_beta, p);
   ALLOC(e.inc_ub, 1);
   ALLOC(e.inc_snap, 1);
@@ -272,6 +275,7 @@ static int allocate(Engine<R>& e) {
   BNB_CUDA_OK(cudaMemsetAsync(e.fix, 0xff, K * p, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * K, e.st));
   BNB_CUDA_OK(cudaMemsetAsync(e.sel_state, 0, sizeof(int) * 16, e.st));
+  BNB_CUDA_OK(cudaMemsetAsync(e.ue_cnt, 0, sizeof(int) * K, e.st));
   return 0;
 }
 

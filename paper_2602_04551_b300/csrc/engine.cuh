@@ -19,6 +19,9 @@ constexpr int UB_SEEN = 1 << 16;  // supports remembered per solve (upper bound 
 constexpr int MV_MAX = 32;      // most active slots the matrix-vector round form handles
 constexpr int MV_ZMAX = 96;     // most contraction chunks of its partial products
 constexpr int SEL_BINS = 2048;  // radix-select histogram width
+constexpr int UE_NB = 8;        // blocks per node of the FP64 upper-bound evaluation
+constexpr int PUSH_NB = 8;      // blocks per branched node of the warm-start copy
+constexpr int REFILL_NB = 8;    // blocks per refilled slot
 
 struct Status {                 // copied to the host after every round
   double ub, lb;
@@ -140,6 +143,9 @@ struct Engine {
   R *Qg = nullptr, *qv = nullptr, *ubb = nullptr;   // K x smax^2, K x smax, K x smax
   double *Q64 = nullptr, *L64 = nullptr, *ubb64 = nullptr, *ub_val = nullptr;
   int* pol_flag = nullptr;
+  double* ue_part = nullptr;   // k_ub_eval: per-node partial residual sums [K][UE_NB]
+  int* ue_cnt = nullptr;       // k_ub_eval: blocks of a node done (zero between launches)
+  int* push_w = nullptr;       // k_push: warm-store row of each retired node's children, or -1
   double* inc_beta = nullptr;   // p, FP64 incumbent
   double* inc_ub = nullptr;     // scalar
   double* inc_snap = nullptr;   // the incumbent when the round's certificate decides (scalar)

@@ -70,7 +70,7 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
                        R* warm_beta, R* warm_V, int* warm_ref, int* warm_stack, int* warm_top,
                        int* sel_state, unsigned long long* poolmin, unsigned long long* lost_key,
                        const int* __restrict__ sup_cnt, int smax, int* hist_depth,
-                       int* hist_sup) {
+                       int* hist_sup, int* __restrict__ push_w) {
   __shared__ int c0, c1, wslot, decision;
   const int q = blockIdx.x;
   if (q >= *ret_count) return;
@@ -137,6 +137,7 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
   decided:;
   }
   __syncthreads();
+  if (threadIdx.x == 0) push_w[q] = decision ? wslot : -1;
   if (!decision) return;
   for (int t = threadIdx.x; t < d; t += blockDim.x) {
     const int e = slot_fixl[(long long)slot * dmax + t];
@@ -147,17 +148,30 @@ __global__ void k_push(int p, int dmax, const int* __restrict__ ret_slot, const 
     pool_fix[(long long)c0 * dmax + d] = (j << 1) | 0;
     pool_fix[(long long)c1 * dmax + d] = (j << 1) | 1;
   }
-  if (wslot >= 0) {
-    const long long so = (long long)slot * p, wo = (long long)wslot * p;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      warm_beta[wo + i] = beta[so + i];
-      warm_V[wo + i] = V[so + i];
-    }
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     pool_valid[c0] = 1;
     pool_valid[c1] = 1;
+  }
+}
+
+// the parent's (beta, v) rows into the warm store slot k_push gave its children (grid
+// K x PUSH_NB: block z copies the z-th slice of the p values).  The rows are read next by
+// the refill of a later launch, so stream order is all the synchronisation needed.
+template <class R>
+__global__ void k_push_copy(int p, const int* __restrict__ ret_slot,
+                            const int* __restrict__ ret_count, const int* __restrict__ push_w,
+                            const R* __restrict__ beta, const R* __restrict__ V,
+                            R* __restrict__ warm_beta, R* __restrict__ warm_V) {
+  const int q = blockIdx.x;
+  if (q >= *ret_count) return;
+  const int w = push_w[q];
+  if (w < 0) return;
+  const int chunk = (p + gridDim.y - 1) / gridDim.y;
+  const int i0 = blockIdx.y * chunk, i1 = min(p, i0 + chunk);
+  const long long so = (long long)ret_slot[q] * p, wo = (long long)w * p;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    warm_beta[wo + i] = beta[so + i];
+    warm_V[wo + i] = V[so + i];
   }
 }
 
@@ -401,49 +415,11 @@ __global__ void k_sel_collect(const int* __restrict__ pool_hw, uint8_t* pool_val
                    sel_state, popped);
 }
 
-// load popped node t into its free slot (one block)
-template <class R>
-__device__ __forceinline__ void refill_body(int t, int p, int dmax, const int* __restrict__ popped,
-                                            const int* __restrict__ free_slots,
-                                            const double* __restrict__ pool_lb,
-                                            const int* __restrict__ pool_depth,
-                                            const int* __restrict__ pool_warm,
-                                            const int* __restrict__ pool_fix,
-                                            const R* __restrict__ warm_beta,
-                                            const R* __restrict__ warm_V, int* warm_ref,
-                                            int* warm_stack, int* warm_top, int8_t* fix, R* beta,
-                                            R* V, int* slot_active, int* slot_iters,
-                                            double* slot_lbp, int* slot_depth, int* slot_nfix,
-                                            int* slot_fixl) {
-  const int slot = free_slots[t];
-  const int idx = popped[t];
-  const int d = pool_depth[idx];
-  const int w = pool_warm[idx];
-  const long long so = (long long)slot * p;
-  for (int i = threadIdx.x; i < p; i += blockDim.x) {
-    fix[so + i] = -1;
-    beta[so + i] = w >= 0 ? warm_beta[(long long)w * p + i] : R(0);
-    V[so + i] = w >= 0 ? warm_V[(long long)w * p + i] : R(0);
-  }
-  __syncthreads();
-  for (int u = threadIdx.x; u < d; u += blockDim.x) {
-    const int e = pool_fix[(long long)idx * dmax + u];
-    slot_fixl[(long long)slot * dmax + u] = e;
-    fix[so + (e >> 1)] = (int8_t)(e & 1);
-    if ((e & 1) == 0) beta[so + (e >> 1)] = R(0);  // the new F0 coordinate starts at zero
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    slot_active[slot] = 1;
-    slot_iters[slot] = 0;
-    slot_lbp[slot] = pool_lb[idx];
-    slot_depth[slot] = d;
-    slot_nfix[slot] = d;
-    warm_release(w, warm_ref, warm_stack, warm_top);
-  }
-}
-
-// load popped nodes into free slots (one block per popped node)
+// load popped node t into its free slot: grid K x REFILL_NB, block z writing the z-th
+// slice of the slot's p values (cleared fixings, warm or zero beta and v, then the node's
+// fixings that fall in the slice); block 0 also copies the fixing list and the slot's
+// bookkeeping and releases the warm row (whose slot only a later k_push can reuse, so the
+// other blocks of this launch still read it safely)
 template <class R>
 __global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, const int* __restrict__ popped,
                          const int* __restrict__ free_slots, const double* __restrict__ pool_lb,
@@ -453,11 +429,37 @@ __global__ void k_refill(int p, int dmax, const int* __restrict__ sel_state, con
                          int* warm_top, int8_t* fix, R* beta, R* V, int* slot_active,
                          int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
                          int* slot_fixl) {
-  const int t = blockIdx.x;
+  const int t = blockIdx.x, z = blockIdx.y;
   if (t >= sel_state[SS_OUT]) return;
-  refill_body<R>(t, p, dmax, popped, free_slots, pool_lb, pool_depth, pool_warm, pool_fix,
-                 warm_beta, warm_V, warm_ref, warm_stack, warm_top, fix, beta, V, slot_active,
-                 slot_iters, slot_lbp, slot_depth, slot_nfix, slot_fixl);
+  const int slot = free_slots[t];
+  const int idx = popped[t];
+  const int d = pool_depth[idx];
+  const int w = pool_warm[idx];
+  const int chunk = (p + gridDim.y - 1) / gridDim.y;
+  const int i0 = z * chunk, i1 = min(p, i0 + chunk);
+  const long long so = (long long)slot * p;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    fix[so + i] = -1;
+    beta[so + i] = w >= 0 ? warm_beta[(long long)w * p + i] : R(0);
+    V[so + i] = w >= 0 ? warm_V[(long long)w * p + i] : R(0);
+  }
+  __syncthreads();
+  for (int u = threadIdx.x; u < d; u += blockDim.x) {
+    const int e = pool_fix[(long long)idx * dmax + u];
+    if (z == 0) slot_fixl[(long long)slot * dmax + u] = e;
+    const int i = e >> 1;
+    if (i < i0 || i >= i1) continue;
+    fix[so + i] = (int8_t)(e & 1);
+    if ((e & 1) == 0) beta[so + i] = R(0);  // the new F0 coordinate starts at zero
+  }
+  if (z == 0 && threadIdx.x == 0) {
+    slot_active[slot] = 1;
+    slot_iters[slot] = 0;
+    slot_lbp[slot] = pool_lb[idx];
+    slot_depth[slot] = d;
+    slot_nfix[slot] = d;
+    warm_release(w, warm_ref, warm_stack, warm_top);
+  }
 }
 
 // ---- the selection of a round in one cooperative launch ----
@@ -516,18 +518,13 @@ __device__ bool coop_grid_sync(int* sel_state) {
 constexpr int SELC_THREADS = 1024;   // the scans' block width
 constexpr int SELC_BLOCKS = 64;      // co-resident blocks of the fused selection
 
-template <class R>
 __global__ void __launch_bounds__(SELC_THREADS) k_select_coop(
-    int K, int p, int dmax, int lockstep, const int* __restrict__ pool_hw, uint8_t* pool_valid,
+    int K, int lockstep, const int* __restrict__ pool_hw, uint8_t* pool_valid,
     const double* __restrict__ pool_lb, const unsigned* __restrict__ pool_key,
-    const int* __restrict__ pool_depth, const int* __restrict__ pool_warm,
-    const int* __restrict__ pool_fix, int* free_stack, int* free_top,
-    const R* __restrict__ warm_beta, const R* __restrict__ warm_V, int* warm_ref,
+    const int* __restrict__ pool_warm, int* free_stack, int* free_top, int* warm_ref,
     int* warm_stack, int* warm_top, const double* __restrict__ inc_ub,
     const double* __restrict__ params, unsigned* hist, int* sel_state,
-    unsigned long long* poolmin, int* free_slots, int* popped, int8_t* fix, R* beta, R* V,
-    int* slot_active, int* slot_iters, double* slot_lbp, int* slot_depth, int* slot_nfix,
-    int* slot_fixl) {
+    unsigned long long* poolmin, int* free_slots, int* popped, const int* __restrict__ slot_active) {
   const int blk = blockIdx.x, nblk = gridDim.x;
   if (blk == 0) sel_reset_body(hist, sel_state, poolmin);
   if (!coop_grid_sync(sel_state)) return;
@@ -633,7 +630,9 @@ int queue_push(Engine<R>& e) {
                                    e.pool_key, e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
                                    e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.sel_state,
                                    e.poolmin, e.poolmin + 1, e.sup_size, e.smax, e.hist_depth,
-                                   e.hist_sup);
+                                   e.hist_sup, e.push_w);
+  k_push_copy<R><<<dim3(e.K, PUSH_NB), 256, 0, e.st>>>(e.p, e.ret_slot, e.ret_count, e.push_w,
+                                                       e.beta, e.V, e.warm_beta, e.warm_V);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }
@@ -646,7 +645,7 @@ int queue_fused_select_blocks() {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_select_coop<R>, SELC_THREADS,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_select_coop, SELC_THREADS,
                                                     0) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -668,18 +667,15 @@ int queue_select_refill(Engine<R>& e) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     BNB_CUDA_OK(cudaLaunchKernelEx(
-        &cfg, k_select_coop<R>, e.K, e.p, e.dmax, e.lockstep, (const int*)e.pool_hw,
-        e.pool_valid, (const double*)e.pool_lb, (const unsigned*)e.pool_key,
-        (const int*)e.pool_depth, (const int*)e.pool_warm, (const int*)e.pool_fix, e.free_stack,
-        e.free_top, (const R*)e.warm_beta, (const R*)e.warm_V, e.warm_ref, e.warm_stack,
-        e.warm_top, (const double*)e.inc_ub, (const double*)e.params_d, e.sel, e.sel_state,
-        e.poolmin, e.free_slots, e.popped, e.fix, e.beta, e.V, e.slot_active, e.slot_iters,
-        e.slot_lbp, e.slot_depth, e.slot_nfix, e.slot_fixl));
-    k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb,
-                                     e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta,
-                                     e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.fix,
-                                     e.beta, e.V, e.slot_active, e.slot_iters, e.slot_lbp,
-                                     e.slot_depth, e.slot_nfix, e.slot_fixl);
+        &cfg, k_select_coop, e.K, e.lockstep, (const int*)e.pool_hw, e.pool_valid,
+        (const double*)e.pool_lb, (const unsigned*)e.pool_key, (const int*)e.pool_warm,
+        e.free_stack, e.free_top, e.warm_ref, e.warm_stack, e.warm_top, (const double*)e.inc_ub,
+        (const double*)e.params_d, e.sel, e.sel_state, e.poolmin, e.free_slots, e.popped,
+        (const int*)e.slot_active));
+    k_refill<R><<<dim3(e.K, REFILL_NB), 256, 0, st>>>(
+        e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb, e.pool_depth, e.pool_warm,
+        e.pool_fix, e.warm_beta, e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.fix, e.beta,
+        e.V, e.slot_active, e.slot_iters, e.slot_lbp, e.slot_depth, e.slot_nfix, e.slot_fixl);
     BNB_CUDA_OK(cudaGetLastError());
     return 0;
   }
@@ -698,11 +694,10 @@ int queue_select_refill(Engine<R>& e) {
                                  e.lockstep);
   k_sel_collect<<<g, 256, 0, st>>>(e.pool_hw, e.pool_valid, e.pool_key, e.free_stack, e.free_top,
                                    e.sel_state, e.popped);
-  k_refill<R><<<e.K, 256, 0, st>>>(e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb,
-                                   e.pool_depth, e.pool_warm, e.pool_fix, e.warm_beta, e.warm_V,
-                                   e.warm_ref, e.warm_stack, e.warm_top, e.fix, e.beta, e.V,
-                                   e.slot_active, e.slot_iters, e.slot_lbp, e.slot_depth,
-                                   e.slot_nfix, e.slot_fixl);
+  k_refill<R><<<dim3(e.K, REFILL_NB), 256, 0, st>>>(
+      e.p, e.dmax, e.sel_state, e.popped, e.free_slots, e.pool_lb, e.pool_depth, e.pool_warm,
+      e.pool_fix, e.warm_beta, e.warm_V, e.warm_ref, e.warm_stack, e.warm_top, e.fix, e.beta,
+      e.V, e.slot_active, e.slot_iters, e.slot_lbp, e.slot_depth, e.slot_nfix, e.slot_fixl);
   BNB_CUDA_OK(cudaGetLastError());
   return 0;
 }

@@ -83,7 +83,7 @@ __device__ bool support_seen(unsigned long long* table, int mask, unsigned long 
   return false;
 }
 
-// one block (256 threads) per retired node.  Without gscr (the screened X^T r) a node whose
+// one block (1024 threads) per retired node.  Without gscr (the screened X^T r) a node whose
 // free z are all integral gets br_idx = BR_DEFERRED, decided later by k_branch_fallback.
 constexpr int BR_DEFERRED = -3;
 
@@ -97,23 +97,30 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
                                  int seen_mask, int* __restrict__ sup_size) {
   __shared__ unsigned long long shk[32];
   __shared__ int wcnt[32];
-  __shared__ int base;
   __shared__ double shd[32];
   const int q = blockIdx.x;
   if (q >= *ret_count) return;
   const long long slot = ret_slot[q];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // warp w takes the contiguous range [i_beg, i_end) of the p indices, so the support list
+  // (increasing index) is the warps' lists in warp order: one pass counts, a barrier and a
+  // prefix over the 32 counts give each warp its offset, and a second pass writes
+  const int C = ((p + nw - 1) / nw + 31) & ~31;
+  const int i_beg = min(p, w * C), i_end = min(p, i_beg + C);
+  auto in_support = [&](int i, float& z, int& f) {
+    f = fix[slot * p + i];
+    z = (float)z_coord<R>(beta[slot * p + i], f, P);
+    return f == -1 ? z >= 0.5f : f == 1;
+  };
   unsigned long long kf = 0, kg = 0, hsum = 0;
-  int nf = 0;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  for (int i0 = 0; i0 < p; i0 += blockDim.x) {
-    const int i = i0 + threadIdx.x;
+  int nf = 0, cnt = 0;
+  for (int i0 = i_beg; i0 < i_end; i0 += 32) {
+    const int i = i0 + lane;
     int insup = 0;
-    if (i < p) {
-      const int f = fix[slot * p + i];
-      const R b = beta[slot * p + i];
-      const float z = (float)z_coord<R>(b, f, P);
+    if (i < i_end) {
+      float z;
+      int f;
+      insup = in_support(i, z, f);
       if (zbuf) zbuf[slot * p + i] = z;
       if (f == -1) {
         ++nf;
@@ -127,26 +134,27 @@ __global__ void k_branch_support(const R* __restrict__ beta, const int8_t* __res
               ((unsigned long long)__float_as_uint(g) << 32) | (unsigned)(0x7fffffff - i);
           kg = umax64(kg, kg2);
         }
-        insup = z >= 0.5f;
-      } else {
-        insup = (f == 1);
       }
     }
     if (insup) hsum += support_mix(i);
+    cnt += __popc(__ballot_sync(0xffffffffu, insup));
+  }
+  if (lane == 0) wcnt[w] = cnt;
+  __syncthreads();
+  int off = 0, base = 0;
+  for (int t = 0; t < nw; ++t) {
+    off += t < w ? wcnt[t] : 0;
+    base += wcnt[t];
+  }
+  for (int i0 = i_beg; i0 < i_end && off < smax; i0 += 32) {
+    const int i = i0 + lane;
+    float z;
+    int f;
+    const int insup = i < i_end ? in_support(i, z, f) : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, insup);
-    if (lane == 0) wcnt[w] = __popc(bal);
-    __syncthreads();
-    int off = base;
-    for (int t = 0; t < w; ++t) off += wcnt[t];
     const int pos = off + __popc(bal & ((1u << lane) - 1u));
     if (insup && pos < smax) sup[(long long)q * smax + pos] = i;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int tot = 0;
-      for (int t = 0; t < nw; ++t) tot += wcnt[t];
-      base += tot;
-    }
-    __syncthreads();
+    off += __popc(bal);
   }
   kf = block_max_u64(kf, shk);
   kg = block_max_u64(kg, shk);
@@ -219,6 +227,7 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
       const R* xa = XR + (long long)S[a] * n;
       const R* xb = XR + (long long)S[b] * n;
       R d = 0;
+#pragma unroll 8
       for (int k = lane; k < n; k += 32) d = fma(xa[k], xb[k], d);
       d = warp_sum(d);
       if (lane == 0) {
@@ -230,6 +239,7 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
       const int a = t - npair;
       const R* xa = XR + (long long)S[a] * n;
       R d = 0;
+#pragma unroll 8
       for (int k = lane; k < n; k += 32) d = fma(xa[k], yR[k], d);
       d = warp_sum(d);
       if (lane == 0) qv[(long long)q * smax + a] = d;
@@ -237,8 +247,71 @@ __global__ void k_ub_gram(const R* __restrict__ XR, const R* __restrict__ yR, in
   }
 }
 
+// The projected-gradient iteration of k_ub_fista for a support of at most 32 on one warp:
+// lane a holds coordinate a and row a of Q in registers, Q x takes x_b from lane b by
+// shuffle (the same products in the same order b = 0, 1, ... as the block form), and the
+// sums are butterfly shuffles, which leave the identical value in every lane, so every
+// branch below is uniform over the warp.  No block barrier is involved.
+template <class R>
+__device__ void fista_warp(const R* __restrict__ Q, const R* __restrict__ qq, int s, R M,
+                           int max_iter, double rtol, R* __restrict__ out) {
+  const int a = threadIdx.x & 31;
+  const bool own = a < s;
+  R qrow[32];
+#pragma unroll
+  for (int b = 0; b < 32; ++b) qrow[b] = (own && b < s) ? Q[a * s + b] : R(0);
+  const R qa = own ? qq[a] : R(0);
+  auto matvec = [&](R x) {
+    R v = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) v = fma(qrow[b], __shfl_sync(0xffffffffu, x, b), v);
+    return v;
+  };
+  R ext = own ? R(1) : R(0);
+  R lam = R(1);
+  for (int it = 0; it < 12; ++it) {
+    const R v = matvec(ext);
+    const R nrm2 = warp_sum<R>(v * v);
+    const R dot = warp_sum<R>(v * ext);
+    const R e2 = warp_sum<R>(ext * ext);
+    lam = dot / e2;
+    const R inv = R(1) / sqrt(nrm2 > R(0) ? nrm2 : R(1));
+    ext = own ? v * inv : R(0);
+  }
+  R alpha = R(1) / lam;
+  R cur = R(0), prev = R(0), fcur = R(0);
+  for (int t = 0; t < max_iter; ++t) {
+    const R mom = (R)t / (R)(t + 3);
+    const R e = own ? cur + mom * (cur - prev) : R(0);
+    const R Qe = matvec(e);
+    const R g = own ? Qe - qa : R(0);
+    const R fext = warp_sum<R>(own ? e * (R(0.5) * Qe - qa) : R(0));
+    R fnew = 0, x = 0;
+    for (int bt = 0; bt < 40; ++bt) {
+      x = own ? e - alpha * g : R(0);
+      x = x > M ? M : (x < -M ? -M : x);
+      const R Qn = matvec(x);
+      const R d = x - e;
+      fnew = warp_sum<R>(own ? x * (R(0.5) * Qn - qa) : R(0));
+      const R gd = warp_sum<R>(g * d);
+      const R dd = warp_sum<R>(d * d);
+      const R slack = R(8) * (R)(sizeof(R) == 4 ? 1.2e-7 : 2.3e-16) * (fabs(fext) + R(1));
+      if (fnew <= fext + gd + dd / (R(2) * alpha) + slack) break;
+      alpha *= R(0.5);
+    }
+    prev = cur;
+    cur = x;
+    const bool done = t > 0 && fabs(fcur - fnew) <= (R)rtol * (fabs(fnew) + R(1));
+    fcur = fnew;
+    if (done) break;
+  }
+  if (own) out[a] = cur;
+}
+
 // Batched projected gradient with t/(t+3) extrapolation and Armijo backtracking.
-// One block per node, one thread per support coordinate (s <= blockDim.x).
+// One block per node: a support of at most 32 runs on the block's first warp
+// (fista_warp), a larger one on the whole block, one thread per support coordinate
+// (s <= blockDim.x).
 template <class R>
 __global__ void k_ub_fista(const R* __restrict__ Qg, const R* __restrict__ qv, int smax, double M_,
                            const int* __restrict__ sup_cnt, const int* __restrict__ ret_count,
@@ -250,6 +323,12 @@ __global__ void k_ub_fista(const R* __restrict__ Qg, const R* __restrict__ qv, i
   if (q >= *ret_count) return;
   const int s = sup_cnt[q];
   if (s <= 0) return;
+  if (s <= 32) {
+    if (threadIdx.x < 32)
+      fista_warp<R>(Qg + (long long)q * smax * smax, qv + (long long)q * smax, s, (R)M_,
+                    max_iter, rtol, ubb + (long long)q * smax);
+    return;
+  }
   R* cur = sm;
   R* prev = sm + smax;
   R* ext = sm + 2 * smax;
@@ -320,20 +399,27 @@ __global__ void k_ub_fista(const R* __restrict__ Qg, const R* __restrict__ qv, i
   if (own) ubb[(long long)q * smax + a] = cur[a];
 }
 
-// FP64 value of Eq. original at the candidate (one block per node)
+// FP64 value of Eq. original at the candidate.  UE_NB blocks per node (grid K x UE_NB),
+// block z taking the samples of its slice of n; each writes its partial ||y - X_S b||^2
+// and the last of a node's blocks to finish (counted in ue_cnt, which it resets) adds the
+// UE_NB partials in slice order, so the value does not depend on which block ends last.
 template <class R>
 __global__ void k_ub_eval(const double* __restrict__ X64, const double* __restrict__ y64, int n,
                           int smax, double lam0, double lam2, double M, const int* __restrict__ sup,
                           const int* __restrict__ sup_cnt, const int* __restrict__ ret_count,
                           const R* __restrict__ ubb, double* __restrict__ ubb64,
                           double* __restrict__ ub_val, int* __restrict__ pol_flag,
-                          const double* __restrict__ inc_ub, int force) {
+                          const double* __restrict__ inc_ub, int force, double* __restrict__ part,
+                          int* __restrict__ cnt) {
   __shared__ double sh[32];
-  const int q = blockIdx.x;
+  __shared__ double bs[256];
+  __shared__ int sS[256];
+  __shared__ int last;
+  const int q = blockIdx.x, z = blockIdx.y, nz = gridDim.y;
   if (q >= *ret_count) return;
   const int s = sup_cnt[q];
   if (s < 0) {
-    if (threadIdx.x == 0) {
+    if (z == 0 && threadIdx.x == 0) {
       ub_val[q] = INFINITY;
       pol_flag[q] = 0;
     }
@@ -343,25 +429,43 @@ __global__ void k_ub_eval(const double* __restrict__ X64, const double* __restri
   double* b64 = ubb64 + (long long)q * 2 * smax;
   // the point clipped to the FP64 box: the ADMM-precision clip uses M rounded to that
   // precision, which may lie just outside the box, and the value must be a feasible one
-  for (int a = threadIdx.x; a < s; a += blockDim.x)
-    b64[a] = fmin(M, fmax(-M, (double)ubb[(long long)q * smax + a]));
+  for (int a = threadIdx.x; a < s; a += blockDim.x) {
+    bs[a] = fmin(M, fmax(-M, (double)ubb[(long long)q * smax + a]));
+    sS[a] = S[a];
+    if (z == 0) b64[a] = bs[a];
+  }
   __syncthreads();
+  // the support indices come from shared memory, so the s column loads of a sample do not
+  // wait on one another; only the FMA chain on r is sequential
+  const int chunk = (n + nz - 1) / nz, i0 = z * chunk, i1 = min(n, i0 + chunk);
   double rr = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     double r = y64[i];
-    for (int a = 0; a < s; ++a) r = fma(-X64[(long long)S[a] * n + i], b64[a], r);
+#pragma unroll 8
+    for (int a = 0; a < s; ++a) r = fma(-X64[(long long)sS[a] * n + i], bs[a], r);
     rr = fma(r, r, rr);
   }
   rr = block_sum(rr, sh);
-  double bb = 0.0, nz = 0.0;
+  if (threadIdx.x == 0) {
+    part[(long long)q * nz + z] = rr;
+    __threadfence();
+    last = atomicAdd(&cnt[q], 1) == nz - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double bb = 0.0, nzc = 0.0;
   for (int a = threadIdx.x; a < s; a += blockDim.x) {
-    bb = fma(b64[a], b64[a], bb);
-    nz += b64[a] != 0.0 ? 1.0 : 0.0;
+    bb = fma(bs[a], bs[a], bb);
+    nzc += bs[a] != 0.0 ? 1.0 : 0.0;
   }
   bb = block_sum(bb, sh);
-  nz = block_sum(nz, sh);
+  nzc = block_sum(nzc, sh);
   if (threadIdx.x == 0) {
-    const double v = 0.5 * rr + lam0 * nz + lam2 * bb;
+    double tot = 0.0;
+    for (int t = 0; t < nz; ++t) tot += __ldcg(&part[(long long)q * nz + t]);
+    cnt[q] = 0;
+    const double v = 0.5 * tot + lam0 * nzc + lam2 * bb;
     ub_val[q] = v;
     // force: 1 polish every candidate, -1 none, 0 those within 1e-6 of the incumbent
     pol_flag[q] = (s > 0) && force >= 0 && (force || v < inc_ub[0] * (1.0 + 1e-6));
@@ -563,13 +667,33 @@ __global__ void k_ub_update(int p, int smax, const int* __restrict__ sup,
                             double* __restrict__ inc_ub, double* __restrict__ inc_beta) {
   __shared__ int best_q;
   __shared__ double best_v;
-  if (threadIdx.x == 0) {
-    best_q = -1;
-    best_v = inc_ub[0];
+  if (threadIdx.x < 32) {
+    // the smallest value below the incumbent, the lowest q among equal ones: each lane
+    // scans q = lane, lane + 32, ... (keeping its first strict minimum), then a butterfly
+    // over (value, q) pairs; only supports evaluated in this call count (empty or skipped
+    // ones left ub_val untouched)
     const int R = *ret_count;
-    for (int q = 0; q < R; ++q)
-      // only supports evaluated in this call (empty or skipped ones left ub_val untouched)
-      if (sup_cnt[q] > 0 && ub_val[q] < best_v) { best_v = ub_val[q]; best_q = q; }
+    double v = inc_ub[0];
+    int bq = -1;
+    for (int q = threadIdx.x; q < R; q += 32)
+      if (sup_cnt[q] > 0 && ub_val[q] < v) {
+        v = ub_val[q];
+        bq = q;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+      const bool take = oq >= 0 && (bq < 0 || ov < v || (ov == v && oq < bq));
+      if (take) {
+        v = ov;
+        bq = oq;
+      }
+    }
+    if (threadIdx.x == 0) {
+      best_q = bq;
+      best_v = v;
+    }
   }
   __syncthreads();
   const int q = best_q;
@@ -635,9 +759,10 @@ int upper_bound(Engine<R>& e, int force_polish) {
   const size_t sm = sizeof(R) * 4 * e.smax;
   k_ub_fista<R><<<K, 256, sm, st>>>(e.Qg, e.qv, e.smax, e.P.M, e.sup_cnt, e.ret_count,
                                     e.ub_iters, sizeof(R) == 4 ? 1e-7 : 1e-13, e.ubb);
-  k_ub_eval<R><<<K, 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2, e.P.M, e.sup,
-                                  e.sup_cnt, e.ret_count, e.ubb, e.ubb64, e.ub_val, e.pol_flag,
-                                  e.inc_ub, force_polish);
+  k_ub_eval<R><<<dim3(K, UE_NB), 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2,
+                                               e.P.M, e.sup, e.sup_cnt, e.ret_count, e.ubb,
+                                               e.ubb64, e.ub_val, e.pol_flag, e.inc_ub,
+                                               force_polish, e.ue_part, e.ue_cnt);
   k_ub_polish<<<K, 256, 0, st>>>(e.X64, e.y64, e.n, e.smax, e.P.lam0, e.P.lam2, e.P.M, e.sup,
                                  e.sup_cnt, e.ret_count, e.pol_flag, e.Q64, e.L64, e.ubb64,
                                  e.ub_val, e.sel_state + 8);
