@@ -98,7 +98,9 @@ def parse():
                     help="kcurve mode: batch widths; each solve runs --solve-time-limit seconds")
     ap.add_argument("--lam0-frac", type=float, default=0.02)
     ap.add_argument("--K", type=int, default=512)
-    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="ADMM iterations between stop tests (0: chosen by the autotuner among "
+                         "10, 20 and 30 on search measurements, 10 when --rho is given)")
     ap.add_argument("--rounds-per-step", type=int, default=25,
                     help="device rounds in one timed step")
     ap.add_argument("--no-side", action="store_true",
@@ -120,7 +122,12 @@ def parse():
     ap.add_argument("--precision", default="tc3", choices=["fp32", "tc3", "bf16", "bf16x2"])
     ap.add_argument("--rho", type=float, default=0.0, help="0: chosen by the autotuner")
     ap.add_argument("--alpha", type=float, default=1.0, help="ADMM over-relaxation (autotuned with rho)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    # the interval is tuned only with rho (timed-rounds mode); elsewhere it defaults to 10
+    args.check_every_auto = args.check_every <= 0 and args.rho <= 0 and args.mode == "rounds"
+    if args.check_every <= 0:
+        args.check_every = 10
+    return args
 
 
 METRIC = "certified BnB nodes/s"        # both arms report this metric on the same config
@@ -224,12 +231,16 @@ def run_mine(args, rank, world):
         best, entry = autotune.autotune(inst.X, inst.y, lam0, lam2, M, device=dev, use_cache=False,
                                         grid={"batch_K": [args.K], "precision": [PREC[args.precision]],
                                               "check_every": [args.check_every]},
-                                        tune_crossover=False)
+                                        tune_crossover=False,
+                                        check_every_values=(10, 20, 30) if args.check_every_auto
+                                        else None)
         args.rho = float(best["rho"])
         args.alpha = float(best.get("relax_alpha", 1.0))
+        args.check_every = int(best["check_every"])
         note(f"autotune: rho {args.rho} alpha {args.alpha}")
-        tune = {"chosen": best, "seconds": entry["seconds"],
-                "trials": [{k: t[k] for k in ("rho", "nodes_per_s", "mean_iters", "lb_mean")}
+        tune = {"chosen": best, "seconds": entry["seconds"], "check_every": entry["check_every"],
+                "trials": [{k: t[k] for k in ("rho", "relax_alpha", "nodes_per_s", "mean_iters",
+                                              "lb_mean", "search_nodes_per_s") if k in t}
                            for t in entry["trials"]]}
     s = torch.cuda.Stream()
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,

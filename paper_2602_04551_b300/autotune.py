@@ -7,6 +7,14 @@ depth, the shape of the nodes the tree produces) through bnb_relax_batch_device,
 timed with CUDA events on the handle's stream.  The score is certified nodes per
 second; the mean FP64 bound of the batch is recorded so that a mode whose bounds
 are markedly weaker (e.g. plain BF16) is not chosen for speed alone.
+The few best candidates of that batch measurement (search_top) are then timed on the
+tree search itself (search_trial): a solve of the problem with the candidate options is
+run until its node slots are busy, and the certified nodes of the next rounds per second
+decide.  The batch measurement alone ranks candidates of close score unreliably: its
+random children are not the nodes the search produces, and its time is set by the
+slowest node of the batch, where the search refills each slot as its node finishes.
+With check_every_values the stop-test interval is then chosen the same way, by search
+measurements of the chosen configuration at each interval.
 A second, short measurement picks the crossover below which a round runs the
 narrow matrix-vector form instead of tensor-core tiles (mv_crossover): batches of 4 to
 32 children are timed with the narrow form forced on and off, and the crossover is the
@@ -81,6 +89,51 @@ def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0, nodes=None):
                 "lb_mean": float(dlb.mean())}
 
 
+def search_trial(X, y, lam0, lam2, M, opts: dict, device=0, rounds=300, prime_rounds=400,
+                 warm_rounds=125, gap=1e-4):
+    """Certified nodes per second of the tree search with the candidate options: a solve
+    primed until 90 % of its slots are busy and a batch's worth of nodes is certified (at
+    most prime_rounds rounds), `warm_rounds` more rounds, then `rounds` rounds timed with
+    CUDA events on the handle's stream.  The rate changes as the tree grows (a setting
+    that retires nodes faster in the first rounds can be the slower one a few hundred
+    rounds later), so the timed rounds start where a long solve's steady state does.  None
+    when the solve ends before the timed rounds."""
+    import torch
+    import paper_2602_04551_b300 as bnb
+    K = int(opts["batch_K"])
+    s = torch.cuda.Stream(device=device)
+    o = bnb.bnb_options_default(M=M, device=device, stream=s.cuda_stream, time_limit_s=1e9,
+                                **opts)
+    with bnb.bnb_create(X, y, lam0, lam2, o) as h:
+        bnb.bnb_solve_start(h, gap)
+        primed = 0
+        while primed < prime_rounds:
+            bnb.bnb_solve_launch(h, 20)
+            primed += 20
+            pr = bnb.bnb_solve_poll(h)
+            if pr["done"]:
+                return None
+            if pr["active_slots"] >= 0.9 * K and pr["nodes"] >= K:
+                break
+        if warm_rounds > 0:
+            bnb.bnb_solve_launch(h, warm_rounds)
+            pr = bnb.bnb_solve_poll(h)
+            if pr["done"]:
+                return None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.synchronize()
+        e0.record(s)
+        bnb.bnb_solve_launch(h, rounds)
+        e1.record(s)
+        s.synchronize()
+        after = bnb.bnb_solve_poll(h)
+        ms = e0.elapsed_time(e1)
+        bnb.bnb_solve_finish(h)
+    nodes = after["nodes"] - pr["nodes"]
+    return {"search_nodes_per_s": nodes / (ms / 1e3), "search_ms": ms, "search_nodes": nodes,
+            "search_rounds": rounds, "prime_rounds": primed + warm_rounds}
+
+
 def crossover(X, y, lam0, lam2, M, opts: dict, device=0, widths=(4, 8, 16, 32)):
     """Largest batch width (<= 32) at which the narrow matrix-vector form beats the
     tensor-core form on `widths`-node batches; 0 when it never does."""
@@ -96,10 +149,10 @@ def crossover(X, y, lam0, lam2, M, opts: dict, device=0, widths=(4, 8, 16, 32)):
 
 
 def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol=1e-3,
-             tune_crossover=True):
+             tune_crossover=True, search_top=4, check_every_values=None):
     grid = dict(DEFAULT_GRID, **(grid or {}))
     n, p = X.shape
-    key = _key(n, p, grid)
+    key = _key(n, p, grid) + f"|search_top={search_top}|ce={check_every_values}"
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -118,13 +171,41 @@ def autotune(X, y, lam0, lam2, M, grid=None, device=0, use_cache=True, bound_tol
         results.append((opts, r))
     best_lb = max(r["lb_mean"] for _, r in results)
     ok = [(o, r) for o, r in results if r["lb_mean"] >= best_lb - bound_tol * max(1.0, abs(best_lb))]
-    best, br = max(ok, key=lambda t: t[1]["nodes_per_s"])
+    ok.sort(key=lambda t: -t[1]["nodes_per_s"])
+    best, br = ok[0]
+    searched = []
+    if search_top > 0:
+        for o, r in ok[:search_top]:
+            st = search_trial(X, y, lam0, lam2, M, o, device=device)
+            if st is not None:
+                r.update(st)
+                searched.append((o, r))
+        if searched:
+            best, br = max(searched, key=lambda t: t[1]["search_nodes_per_s"])
     best = dict(best)
+    ce_rows = []
+    if check_every_values and "search_nodes_per_s" in br:
+        # the stop-test interval, on the search alone: the batch measurement cannot see it
+        # (a longer interval spreads each round's fixed work -- certificate, branching,
+        # upper bound, selection -- over more iterations, but a converged node waits longer
+        # for its test)
+        ce_rows.append({"check_every": best.get("check_every"),
+                        "search_nodes_per_s": br["search_nodes_per_s"]})
+        for ce in check_every_values:
+            if ce == best.get("check_every"):
+                continue
+            st = search_trial(X, y, lam0, lam2, M, dict(best, check_every=ce), device=device)
+            if st is not None:
+                ce_rows.append({"check_every": ce, "search_nodes_per_s": st["search_nodes_per_s"]})
+        top = max(ce_rows, key=lambda r: r["search_nodes_per_s"])
+        if top["check_every"] != best.get("check_every"):
+            best["check_every"] = top["check_every"]
+            br = dict(br, search_nodes_per_s=top["search_nodes_per_s"])
     cross_rows = []
     if tune_crossover and best.get("precision", 3) in (2, 3, 4):
         best["mv_crossover"], cross_rows = crossover(X, y, lam0, lam2, M, best, device=device)
     entry = {"best": best, "score": br, "trials": [dict(o, **r) for o, r in results],
-             "crossover": cross_rows, "seconds": time.time() - t0}
+             "check_every": ce_rows, "crossover": cross_rows, "seconds": time.time() - t0}
     if use_cache:
         cache[key] = entry
         os.makedirs(os.path.dirname(path), exist_ok=True)

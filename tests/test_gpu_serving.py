@@ -71,3 +71,27 @@ def test_each_result_same_alone_and_in_the_mix():
             # both certified to the gap: each is within it of the optimum, hence of the other
             assert abs(res.ub - ref.ub) <= 2 * r.gap * abs(ref.ub)
             assert res.lb <= ref.ub * (1 + 1e-12) and ref.lb <= res.ub * (1 + 1e-12)
+
+
+def test_autotune_search_trial_times_the_tree_search():
+    """The autotuner's search measurement on a real solve: a primed solve of the c2_small
+    instance, timed rounds, a positive node rate; and autotune with search_top picks one of
+    the searched candidates."""
+    from paper_2602_04551_b300 import autotune
+    inst = datagen.config_instance("c2_small", 0)
+    lam2 = datagen.CONFIGS["c2_small"]["lam2"]
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = 0.02 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    opts = dict(rho=0.3, relax_alpha=1.6, batch_K=64, check_every=10, precision=3)
+    st = autotune.search_trial(inst.X, inst.y, lam0, lam2, M, opts, rounds=50, warm_rounds=20)
+    if st is not None:                             # None only when the solve ends while priming
+        assert st["search_nodes"] > 0 and st["search_nodes_per_s"] > 0
+        assert st["search_rounds"] == 50 and st["prime_rounds"] <= 420
+    grid = {"rho": [0.2, 0.3], "relax_alpha": [1.6], "batch_K": [64], "check_every": [10],
+            "precision": [3]}
+    best, entry = autotune.autotune(inst.X, inst.y, lam0, lam2, M, grid=grid, use_cache=False,
+                                    tune_crossover=False, search_top=2)
+    searched = [t for t in entry["trials"] if "search_nodes_per_s" in t]
+    if searched:
+        top = max(searched, key=lambda t: t["search_nodes_per_s"])
+        assert best["rho"] == top["rho"]
