@@ -254,17 +254,18 @@ def run_mine(args, rank, world):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
     gap = 1e-4
     bnb.bnb_solve_start(h, gap)
-    # priming (untimed): grow the tree until the slots are busy and a batch's worth of
-    # nodes has been certified, so that the timed rounds measure the steady state of the
-    # solve (slots retiring and refilling) rather than its first nodes
+    # priming (untimed): grow the tree until a batch's worth of nodes has been certified
+    # and the pool holds a batch of open nodes beside the slots, so that the timed rounds
+    # measure the steady state of the solve (slots retiring and refilling) rather than its
+    # first nodes, and not a pool grown to its capacity
+    from paper_2602_04551_b300 import autotune
     t0 = time.time()
     prime_rounds = 0
     while True:
         bnb.bnb_solve_launch(h, 20)
         prime_rounds += 20
         pr = bnb.bnb_solve_poll(h)
-        busy = pr["active_slots"] >= 0.9 * args.K and pr["nodes"] >= args.K
-        if pr["done"] or busy or time.time() - t0 > args.prime_seconds:
+        if pr["done"] or autotune.steady(pr, args.K) or time.time() - t0 > args.prime_seconds:
             break
     note(f"primed: {prime_rounds} rounds")
     clk = Clocks(dev)            # sampling spans the warm-up and the timed steps
@@ -332,6 +333,7 @@ def run_fp32_side(args, inst, lam0, lam2, M, dev):
     path that computes the FP32 ADMM literally, beside the tensor-core default."""
     import torch
     import paper_2602_04551_b300 as bnb
+    from paper_2602_04551_b300 import autotune
     s = torch.cuda.Stream()
     opt = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
                                   precision=bnb.BNB_PREC_FP32, device=dev, stream=s.cuda_stream,
@@ -345,8 +347,7 @@ def run_fp32_side(args, inst, lam0, lam2, M, dev):
         while True:
             bnb.bnb_solve_launch(h, 20)
             pr = bnb.bnb_solve_poll(h)
-            if pr["done"] or (pr["active_slots"] >= 0.9 * args.K and pr["nodes"] >= args.K) \
-                    or time.time() - t0 > args.prime_seconds:
+            if pr["done"] or autotune.steady(pr, args.K) or time.time() - t0 > args.prime_seconds:
                 break
         with torch.cuda.stream(s):
             bnb.bnb_solve_launch(h, R)

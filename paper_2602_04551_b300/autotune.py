@@ -89,6 +89,15 @@ def trial(X, y, lam0, lam2, M, opts: dict, device=0, seed=0, nodes=None):
                 "lb_mean": float(dlb.mean())}
 
 
+def steady(pr: dict, K: int) -> bool:
+    """A solve is in its steady state once a batch's worth of nodes has been certified
+    and the pool holds at least K open nodes besides the active slots, so that every
+    refill fills each free slot.  (The active-slot count itself is read after the round's
+    stop test has retired its converged slots, so with a long stop-test interval it sits
+    well below K even when the slots are all busy.)"""
+    return pr["nodes"] >= K and pr["open_nodes"] - pr["active_slots"] >= K
+
+
 def search_trial(X, y, lam0, lam2, M, opts: dict, device=0, rounds=300, prime_rounds=400,
                  warm_rounds=125, gap=1e-4):
     """Certified nodes per second of the tree search with the candidate options: a solve
@@ -113,7 +122,7 @@ def search_trial(X, y, lam0, lam2, M, opts: dict, device=0, rounds=300, prime_ro
             pr = bnb.bnb_solve_poll(h)
             if pr["done"]:
                 return None
-            if pr["active_slots"] >= 0.9 * K and pr["nodes"] >= K:
+            if steady(pr, K):
                 break
         if warm_rounds > 0:
             bnb.bnb_solve_launch(h, warm_rounds)

@@ -195,8 +195,29 @@ __global__ void k_sel_reset(unsigned* hist, int* sel_state, unsigned long long* 
   sel_reset_body(hist, sel_state, poolmin);
 }
 
+// One histogram increment per distinct bin among a warp's lanes (bin ~0u: none).  The
+// keys of a deep tree's open nodes sit in a few bins of the upper levels (children carry
+// their parent's bound), so per-lane shared atomics would serialise on those bins.
+__device__ __forceinline__ void warp_hist_add(unsigned* sh, unsigned bin) {
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  if (bin != ~0u && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&sh[bin], __popc(peers));
+}
+
+// Slots in a shared array for the lanes whose flag is set: one atomicAdd per warp on the
+// counter, each flagged lane gets base + its rank among the flagged lanes (-1 if unflagged).
+__device__ __forceinline__ int warp_claim(int* counter, bool flag) {
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (m && lane == __ffs(m) - 1) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, __ffs(m ? m : 1u) - 1);
+  return flag ? base + __popc(m & ((1u << lane) - 1u)) : -1;
+}
+
 // pass 1: drop prunable entries, count, min LB, histogram of the top 11 key bits (block
-// `blk` of `nblk` in a grid-stride loop over the pool)
+// `blk` of `nblk` in a grid-stride loop over the pool).  The loop runs over whole warps
+// (entries i0 + lane, i0 a multiple of 32) so that every lane takes part in the warp-wide
+// aggregation of the histogram and of the free-stack pushes.
 __device__ __forceinline__ void sel_pass1_body(int blk, int nblk, const int* __restrict__ pool_hw,
                                                uint8_t* pool_valid,
                                                const double* __restrict__ pool_lb,
@@ -212,28 +233,44 @@ __device__ __forceinline__ void sel_pass1_body(int blk, int nblk, const int* __r
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
   const double thr = inc_ub[0] * (1.0 - params[0]);
-  int cnt = 0;
+  const int lane = threadIdx.x & 31;
+  int cnt = 0, npruned = 0;
   unsigned long long mn = ~0ull;
-  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
-    if (!pool_valid[i]) continue;
-    const double lb = pool_lb[i];
-    if (lb >= thr) {
+  for (int i0 = blk * blockDim.x + (threadIdx.x & ~31); i0 < hw; i0 += nblk * blockDim.x) {
+    const int i = i0 + lane;
+    const bool live = i < hw && pool_valid[i];
+    const double lb = live ? pool_lb[i] : 0.0;
+    const bool prune = live && lb >= thr;
+    const int slot = warp_claim(free_top, prune);
+    unsigned bin = ~0u;
+    if (prune) {
       pool_valid[i] = 0;
-      free_stack[atomicAdd(free_top, 1)] = i;
+      free_stack[slot] = i;
       warm_release(pool_warm[i], warm_ref, warm_stack, warm_top);
-      atomicAdd(&sel_state[SS_PRUNED], 1);
-      continue;
+      ++npruned;
+    } else if (live) {
+      ++cnt;
+      const unsigned long long k = dkey(lb);
+      mn = k < mn ? k : mn;
+      bin = pool_key[i] >> 21;
     }
-    ++cnt;
-    const unsigned long long k = dkey(lb);
-    mn = k < mn ? k : mn;
-    atomicAdd(&sh[pool_key[i] >> 21], 1u);
+    warp_hist_add(sh, bin);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x)
     if (sh[t]) atomicAdd(&hist[t], sh[t]);
-  if (cnt) atomicAdd(&sel_state[SS_COUNT], cnt);
-  if (mn != ~0ull) atomicMin(poolmin, mn);
+  cnt = warp_sum(cnt);
+  npruned = warp_sum(npruned);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mn, o);
+    mn = y < mn ? y : mn;
+  }
+  if (lane == 0) {
+    if (cnt) atomicAdd(&sel_state[SS_COUNT], cnt);
+    if (npruned) atomicAdd(&sel_state[SS_PRUNED], npruned);
+    if (mn != ~0ull) atomicMin(poolmin, mn);
+  }
 }
 
 __global__ void k_sel_pass1(const int* __restrict__ pool_hw, uint8_t* pool_valid,
@@ -352,6 +389,7 @@ __global__ void k_sel_scan(int level, const unsigned* __restrict__ hist, int* se
 }
 
 // levels 2 and 3: histogram of the next key bits among entries matching the prefix
+// (whole-warp loop and warp-aggregated increments, as in pass 1)
 __device__ __forceinline__ void sel_pass_body(int blk, int nblk, int level,
                                               const int* __restrict__ pool_hw,
                                               const uint8_t* __restrict__ pool_valid,
@@ -364,14 +402,19 @@ __device__ __forceinline__ void sel_pass_body(int blk, int nblk, int level,
   for (int t = threadIdx.x; t < SEL_BINS; t += blockDim.x) sh[t] = 0;
   __syncthreads();
   const unsigned pre = (unsigned)sel_state[SS_PREFIX];
-  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
-    if (!pool_valid[i]) continue;
-    const unsigned k = pool_key[i];
-    if (level == 2) {
-      if ((k >> 21) == pre) atomicAdd(&sh[(k >> 10) & 2047u], 1u);
-    } else {
-      if ((k >> 10) == pre) atomicAdd(&sh[k & 1023u], 1u);
+  const int lane = threadIdx.x & 31;
+  for (int i0 = blk * blockDim.x + (threadIdx.x & ~31); i0 < hw; i0 += nblk * blockDim.x) {
+    const int i = i0 + lane;
+    unsigned bin = ~0u;
+    if (i < hw && pool_valid[i]) {
+      const unsigned k = pool_key[i];
+      if (level == 2) {
+        if ((k >> 21) == pre) bin = (k >> 10) & 2047u;
+      } else {
+        if ((k >> 10) == pre) bin = k & 1023u;
+      }
     }
+    warp_hist_add(sh, bin);
   }
   __syncthreads();
   unsigned* h = hist + (level - 1) * SEL_BINS;
@@ -396,15 +439,22 @@ __device__ __forceinline__ void sel_collect_body(int blk, int nblk, const int* _
   if (all == 2) return;                     // lockstep: slots still busy
   const unsigned tau = (unsigned)sel_state[SS_TAU];
   const int need_eq = sel_state[SS_NEED];
-  for (int i = blk * blockDim.x + threadIdx.x; i < hw; i += nblk * blockDim.x) {
-    if (!pool_valid[i]) continue;
-    const unsigned k = pool_key[i];
-    bool take = all == 1 || k < tau;
-    if (!take && k == tau) take = atomicAdd(&sel_state[SS_EQ], 1) < need_eq;
-    if (!take) continue;
-    popped[atomicAdd(&sel_state[SS_OUT], 1)] = i;
-    pool_valid[i] = 0;
-    free_stack[atomicAdd(free_top, 1)] = i;
+  const int lane = threadIdx.x & 31;
+  for (int i0 = blk * blockDim.x + (threadIdx.x & ~31); i0 < hw; i0 += nblk * blockDim.x) {
+    const int i = i0 + lane;
+    const bool live = i < hw && pool_valid[i];
+    const unsigned k = live ? pool_key[i] : 0u;
+    bool take = live && (all == 1 || k < tau);
+    // entries at the threshold key: the first need_eq claims (in any order) are taken
+    const int eq = warp_claim(&sel_state[SS_EQ], live && !take && k == tau);
+    if (eq >= 0 && eq < need_eq) take = true;
+    const int out = warp_claim(&sel_state[SS_OUT], take);
+    const int fs = warp_claim(free_top, take);
+    if (take) {
+      popped[out] = i;
+      pool_valid[i] = 0;
+      free_stack[fs] = i;
+    }
   }
 }
 

@@ -38,6 +38,7 @@ def main():
     import torch
     import datagen
     import paper_2602_04551_b300 as bnb
+    from paper_2602_04551_b300 import autotune
 
     a = parser().parse_args()
     c = datagen.CONFIGS[a.workload]
@@ -55,7 +56,7 @@ def main():
         while True:
             bnb.bnb_solve_launch(h, 10)
             pr = bnb.bnb_solve_poll(h)
-            if pr["done"] or pr["active_slots"] >= 0.9 * a.K or time.time() - t0 > a.prime_seconds:
+            if pr["done"] or autotune.steady(pr, a.K) or time.time() - t0 > a.prime_seconds:
                 break
         torch.cuda.nvtx.range_push("profiled_rounds")
         bnb.bnb_solve_launch(h, a.rounds)
