@@ -66,6 +66,25 @@ int bnb_tc_gemm_check_pair(const double* dA, const double* dB, int M, int N, int
 int bnb_diag_wait_expiry(long long max_polls, double max_seconds, int* err_out,
                          double* seconds_out);
 
+/*
+ * Diagnostics: the TMA operand ring of the tensor-core kernels on its own, to measure
+ * how fast operand tiles reach the SMs.  `ctas` CTAs (1 <= ctas <= the SM count; one per
+ * SM) each stream `reps` passes (1..64) of 16 K steps; a K step is one ring stage holding
+ * the four tiles one CTA of the fused product's CTA pair loads: A hi and lo (128 rows) and
+ * B hi and lo (b_rows rows, a multiple of 8 up to 256), each 64 BF16 = 128 bytes wide with
+ * the 128-byte swizzle, through a ring of `stages` stages (2..8, within 227 KB of shared
+ * memory).  There is no MMA: a consumer thread frees each stage as soon as it has landed.
+ * The four source tensors (1024 BF16 wide, zeroed, together 21 MB at b_rows = 88) are
+ * allocated here and stay L2-resident.  *us_out: the shortest of `launches` (1..50)
+ * launches after two warm-ups, in microseconds (CUDA events); *bytes_out: the bytes one
+ * launch delivers (ctas x reps x 16 x stage bytes); *err_out: the kernel's error word (0
+ * when every bounded wait completed).  Returns BNB_EINVAL for out-of-range arguments.
+ * The paper has no counterpart: this measures the ceiling the operand-streaming main
+ * loops of the two ADMM products run against.
+ */
+int bnb_diag_tma_stream(int ctas, int stages, int b_rows, int reps, int launches, double* us_out,
+                        double* bytes_out, int* err_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,7 @@ LOG_FIELDS = ("lb", "exact", "width", "node_lb", "parent_lb", "threshold", "dept
               "est_dual", "est_primal")
 # exported by libbnb_diag.so (kept in step with include/bnb_diag.h)
 DIAG_SYMBOLS = ("bnb_tc_gemm_check", "bnb_tc_gemm_check_cluster", "bnb_tc_gemm_check_pair",
-                "bnb_diag_wait_expiry")
+                "bnb_diag_wait_expiry", "bnb_diag_tma_stream")
 DIAG_LIB_PATH = os.path.join(_HERE, "libbnb_diag.so")
 STAGES = ("select_refill", "gemm_xw", "reduce_t_or_make_w", "gemm_ginv_t", "finalize_u", "gemm_xtu_prox",
           "check_xbeta", "stop_test", "certificate", "branch", "upper_bound", "push", "status",
@@ -147,6 +147,7 @@ def load_diag_library(path: str = DIAG_LIB_PATH):
         "bnb_tc_gemm_check_cluster": ([P, P, I, I, I, I, I, P, P], I),
         "bnb_tc_gemm_check_pair": ([P, P, I, I, I, I, I, P, P], I),
         "bnb_diag_wait_expiry": ([LL, D, P, P], I),
+        "bnb_diag_tma_stream": ([I, I, I, I, I, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -426,6 +427,21 @@ def bnb_diag_wait_expiry(max_polls: int, max_seconds: float):
     _check(load_diag_library().bnb_diag_wait_expiry(int(max_polls), float(max_seconds),
                                                     ctypes.byref(err), ctypes.byref(sec)))
     return err.value, sec.value
+
+
+def bnb_diag_tma_stream(ctas: int, stages: int = 3, b_rows: int = 88, reps: int = 8,
+                        launches: int = 5):
+    """The TMA operand ring alone (include/bnb_diag.h): dict with the best launch time
+    (us), the bytes one launch delivers, GB/s per CTA (one CTA per SM) and in total, and
+    the kernel's error word."""
+    us, nbytes, err = ctypes.c_double(-1.0), ctypes.c_double(-1.0), ctypes.c_int(-1)
+    _check(load_diag_library().bnb_diag_tma_stream(int(ctas), int(stages), int(b_rows), int(reps),
+                                                   int(launches), ctypes.byref(us),
+                                                   ctypes.byref(nbytes), ctypes.byref(err)))
+    t = us.value * 1e-6
+    return {"us": us.value, "bytes": nbytes.value, "err": err.value,
+            "gbs_per_sm": nbytes.value / ctas / t / 1e9 if t > 0 else 0.0,
+            "tbs_total": nbytes.value / t / 1e12 if t > 0 else 0.0}
 
 
 def bnb_root_heuristic(h: Handle):

@@ -1,5 +1,6 @@
 // diag.cu -- diagnostics entry points (libbnb_diag.so, declared in include/bnb_diag.h):
-// the tcgen05 contractions on their own, and the bounded mbarrier wait on its own.
+// the tcgen05 contractions on their own, the bounded mbarrier wait on its own, and the
+// TMA operand ring on its own (how fast operand tiles reach an SM).
 //
 // bnb_tc_gemm_check runs C = A B^T for FP64 inputs split into BF16 operands
 // (1 term: hi only; 3 terms: hi/lo pairs), K-major A (M x Kred) and B (N x Kred),
@@ -119,6 +120,121 @@ __global__ void k_wait_expiry(long long max_polls, unsigned long long max_ns, in
   __syncthreads();
 }
 
+// The operand ring on its own: a producer thread streams `reps` passes of 16 K steps of
+// one stage (A hi, B hi, A lo, B lo: the tiles a CTA of the fused product's pair loads,
+// 128-byte swizzle) through an S-stage ring; a consumer thread frees each stage once its
+// bytes have landed (no MMA).  CTA c reads A rows 128 (c % 40) .. and B rows
+// b_rows (c / 40) ..; every wait is bounded and the consumer sees every stage land, so
+// no copy is in flight when the CTA exits.
+constexpr int TMA_STREAM_MAX_STAGES = 8;
+__global__ void __launch_bounds__(64, 1)
+k_tma_stream(const __grid_constant__ CUtensorMap ah, const __grid_constant__ CUtensorMap bh,
+             const __grid_constant__ CUtensorMap al, const __grid_constant__ CUtensorMap bl,
+             int S, int b_rows, int reps, int* err) {
+  extern __shared__ uint8_t raw[];
+  __shared__ __align__(8) uint64_t full[TMA_STREAM_MAX_STAGES], empty[TMA_STREAM_MAX_STAGES];
+  uint8_t* base = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  const int A_B = tc::BM * tc::BK * 2, B_B = b_rows * tc::BK * 2, STAGE = 2 * A_B + 2 * B_B;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int arow = tc::BM * (blockIdx.x % 40), brow = b_rows * (blockIdx.x / 40);
+  const long long total = 16ll * reps;
+  if (threadIdx.x == 0) {
+    for (long long g = 0; g < total; ++g) {
+      const int s = (int)(g % S);
+      if (g >= S && !tc::mbar_wait(&empty[s], (uint32_t)(((g / S) & 1) ^ 1), err, 1)) break;
+      tc::mbar_expect_tx(&full[s], STAGE);
+      const int k = (int)(g % 16) * tc::BK;
+      uint8_t* st = base + s * STAGE;
+      tc::tma_load_2d(st, &ah, &full[s], k, arow);
+      tc::tma_load_2d(st + A_B, &bh, &full[s], k, brow);
+      tc::tma_load_2d(st + A_B + B_B, &al, &full[s], k, arow);
+      tc::tma_load_2d(st + 2 * A_B + B_B, &bl, &full[s], k, brow);
+    }
+  } else if (threadIdx.x == 32) {
+    for (long long g = 0; g < total; ++g) {
+      const int s = (int)(g % S);
+      if (!tc::mbar_wait(&full[s], (uint32_t)((g / S) & 1), err, 2)) break;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s]))
+                   : "memory");
+    }
+  }
+}
+
+}  // namespace bnb
+
+extern "C" int bnb_diag_tma_stream(int ctas, int stages, int b_rows, int reps, int launches,
+                                   double* us_out, double* bytes_out, int* err_out) {
+  using namespace bnb;
+  const long long stage = 2ll * tc::BM * tc::BK * 2 + 2ll * b_rows * tc::BK * 2;
+  const long long smem = stages * stage + 1024;
+  if (ctas < 1 || ctas > 160 || stages < 2 || stages > TMA_STREAM_MAX_STAGES || b_rows < 8 ||
+      b_rows > 256 || b_rows % 8 || reps < 1 || reps > 64 || launches < 1 || launches > 50 ||
+      smem > 227 * 1024 || !us_out || !bytes_out || !err_out)
+    return BNB_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BNB_ENODEV;
+  }
+  if (ctas > sms) return BNB_EINVAL;
+  const long long inner = 16 * tc::BK, arows = 40 * tc::BM, brows = 4ll * b_rows;
+  __nv_bfloat16* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  const long long elems[4] = {inner * arows, inner * brows, inner * arows, inner * brows};
+  int* err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaSuccess;
+  for (int i = 0; i < 4 && ce == cudaSuccess; ++i) {
+    ce = cudaMalloc(&buf[i], elems[i] * 2);
+    if (ce == cudaSuccess) ce = cudaMemset(buf[i], 0, elems[i] * 2);
+  }
+  if (ce == cudaSuccess) ce = cudaMalloc(&err, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaMemset(err, 0, sizeof(int));
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  int rc = ce == cudaSuccess ? BNB_OK : BNB_ENOMEM;
+  CUtensorMap m[4];
+  for (int i = 0; i < 4 && rc == BNB_OK; ++i)
+    rc = make_map_bf16(&m[i], buf[i], inner, (i % 2) ? brows : arows, inner,
+                       (i % 2) ? b_rows : tc::BM);
+  if (rc == BNB_OK &&
+      cudaFuncSetAttribute(k_tma_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    rc = BNB_ECUDA;
+  float best = -1.f;
+  for (int it = 0; it < launches + 2 && rc == BNB_OK; ++it) {
+    cudaEventRecord(e0);
+    k_tma_stream<<<ctas, 64, (size_t)smem>>>(m[0], m[1], m[2], m[3], stages, b_rows, reps, err);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = BNB_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (it >= 2 && (best < 0.f || ms < best)) best = ms;
+  }
+  if (rc == BNB_OK && cudaGetLastError() != cudaSuccess) rc = BNB_ECUDA;
+  if (rc == BNB_OK && cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = BNB_ECUDA;
+  *us_out = best * 1e3;
+  *bytes_out = (double)ctas * reps * 16 * (double)stage;
+  for (int i = 0; i < 4; ++i) cudaFree(buf[i]);
+  cudaFree(err);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  return rc;
+}
+
+namespace bnb {
 }  // namespace bnb
 
 extern "C" int bnb_diag_wait_expiry(long long max_polls, double max_seconds, int* err_out,

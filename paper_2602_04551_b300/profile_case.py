@@ -31,7 +31,23 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--fused-width", type=int, default=0)
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--tma-stream", action="store_true",
+                    help="time the TMA operand ring alone (bnb_diag_tma_stream) over CTA "
+                         "counts and pass counts, one JSON line per case, and exit")
     return ap
+
+
+def tma_stream_table() -> None:
+    """The operand ring of the fused product's pair tile alone (A hi/lo 128 rows, B hi/lo
+    88 rows per CTA, three stages): one pass of 16 K steps (the c2 main loop: 864 KB per
+    CTA) and eight passes (the steady rate), on 30 to 148 SMs."""
+    import json
+    import paper_2602_04551_b300 as bnb
+    for ctas, stages, b_rows, reps in [(120, 3, 88, 1), (120, 3, 88, 8), (148, 3, 88, 8),
+                                       (60, 3, 88, 8), (30, 3, 88, 8), (120, 4, 64, 8)]:
+        r = bnb.bnb_diag_tma_stream(ctas, stages, b_rows, reps, launches=5)
+        print(json.dumps(dict(ctas=ctas, stages=stages, b_rows=b_rows, reps=reps,
+                              kb_per_cta=r["bytes"] / ctas / 1024, **r)), flush=True)
 
 
 def main():
@@ -41,6 +57,9 @@ def main():
     from paper_2602_04551_b300 import autotune
 
     a = parser().parse_args()
+    if a.tma_stream:
+        tma_stream_table()
+        return
     c = datagen.CONFIGS[a.workload]
     inst = datagen.config_instance(a.workload, 0)
     M = datagen.big_m(inst.X, inst.y, inst.support_true, c["lam2"])

@@ -52,6 +52,12 @@ def test_diagnostics_library_exports_its_header_and_the_product_does_not(lib):
         assert len(getattr(raw, name).argtypes) == count, name
     if raw.bnb_diag_wait_expiry(0, 0.001, None, None) != lib.BNB_EINVAL:
         raise AssertionError("bad limits must be rejected before any device work")
+    import ctypes
+    us, nb, err = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    for bad in [(0, 3, 88, 8, 5), (120, 1, 88, 8, 5), (120, 3, 90, 8, 5), (120, 3, 88, 0, 5),
+                (120, 3, 88, 8, 0), (120, 8, 256, 8, 5)]:   # the last needs 513 KB of ring
+        rc = raw.bnb_diag_tma_stream(*bad, ctypes.byref(us), ctypes.byref(nb), ctypes.byref(err))
+        assert rc == lib.BNB_EINVAL, (bad, rc)
 
 
 def test_options_default_and_errors(lib):

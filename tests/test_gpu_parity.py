@@ -87,25 +87,32 @@ def test_dual_bound_full_size_sampled(prec):
 
 
 def _one_iteration_check(inst, lam0, lam2, M, prec, K, Kopt, rows, seed, tol=None, rho=1.0,
-                         alpha=1.0, **kw):
-    """One ADMM iteration (penalty rho, over-relaxation alpha) through the C ABI against the
-    oracle's direct-D iteration, element by element.  The b-update's operator
-    D = (X^T X + rho I)^-1 has norm 1/rho on the null space of X (p > n), so the error of the
-    low-precision products in b grows as 1/rho: the tolerance is ITER_TOL / min(1, rho)."""
+                         alpha=1.0, iters=1, stats=None, **kw):
+    """`iters` ADMM iterations (penalty rho, over-relaxation alpha; one round of that many
+    iterations, so all but the last take the fused update without the stop-test sums)
+    through the C ABI against the oracle's direct-D iterations, element by element.  The
+    b-update's operator D = (X^T X + rho I)^-1 has norm 1/rho on the null space of X (p > n),
+    so the error of the low-precision products in b grows as 1/rho, and the iterations add
+    their errors: the tolerance is iters * ITER_TOL / min(1, rho).  `stats`: entries the
+    handle's bnb_get_stats must show."""
     rng = np.random.default_rng(seed)
     fix = datagen.random_fixings(inst.p, K, rng, 20)
     wb = (rng.uniform(-M, M, (K, inst.p)) * (rng.random((K, inst.p)) < 0.05)).astype(np.float32)
     wb[fix == 0] = 0.0
     wv = rng.normal(0, 0.05, (K, inst.p)).astype(np.float32)
-    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=1, rho=rho, relax_alpha=alpha,
-                 **kw) as h:
-        out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=1, want_v=True)
-    assert np.all(out["iters"] == 1)
+    with _handle(inst, lam0, lam2, M, prec, K=Kopt, check_every=iters, rho=rho,
+                 relax_alpha=alpha, **kw) as h:
+        out = bnb.bnb_relax_batch(h, fix, wb, wv, max_iter=iters, want_v=True)
+        st = bnb.bnb_get_stats(h)
+    for key, want in (stats or {}).items():
+        assert st[key] == want, (key, st[key], want)
+    assert np.all(out["iters"] == iters)
     data = admm.AdmmData(inst.X, inst.y, rho)
-    tol = (ITER_TOL[prec] if tol is None else tol) / min(1.0, rho)
+    tol = iters * (ITER_TOL[prec] if tol is None else tol) / min(1.0, rho)
     for k in rows:
-        b, beta, v = admm.admm_iteration(data, wb[k].astype(np.float64), wv[k].astype(np.float64),
-                                         fix[k], lam0, lam2, M, alpha=alpha)
+        beta, v = wb[k].astype(np.float64), wv[k].astype(np.float64)
+        for _ in range(iters):
+            b, beta, v = admm.admm_iteration(data, beta, v, fix[k], lam0, lam2, M, alpha=alpha)
         sb = max(1.0, np.max(np.abs(beta)))
         sv = max(1.0, np.max(np.abs(v)))
         np.testing.assert_allclose(out["beta"][k], beta, atol=tol * sb)
@@ -331,6 +338,25 @@ def test_one_admm_iteration_untransposed_pair_widths(width, prec):
         rows = sorted({0, width - 1, width, 2 * width + 3, 300, 511})
         _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512, rows=rows, seed=14,
                              fused_shape=4, fused_width=width)
+
+
+@pytest.mark.parametrize("rho,alpha", [(1.0, 1.0), (0.2, 1.6)])
+def test_admm_iterations_one_round_untransposed_pairs(rho, alpha):
+    """Three iterations in one round on the 256 x 176 pair tile (TC3): the first two take
+    the fused update without the stop-test sums, the third the one with them; at c2_small
+    (K = 45 of 128 slots: inactive and past-K slots, ragged feature tile) and at the
+    benchmark's c2 shape (K = 512: the second CTA of every pair, every slot tile, the last
+    feature tile), element by element against the oracle's three iterations, at rho = 1
+    and at the benchmarked rho = 0.2, alpha = 1.6."""
+    inst, lam0, lam2, M = _inst("c2_small", 1)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=45, Kopt=128, rows=range(45), seed=31,
+                         rho=rho, alpha=alpha, iters=3, fused_shape=4, fused_width=176,
+                         mv_crossover=0, stats={"fused_tile_width": 176, "fused_transposed": 0})
+    inst, lam0, lam2, M = _inst("c2", 0, frac=0.02)
+    rows = [0, 15, 16, 175, 176, 191, 352, 500, 511]
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512, rows=rows, seed=32,
+                         rho=rho, alpha=alpha, iters=3, fused_shape=4, fused_width=176,
+                         mv_crossover=0, stats={"fused_tile_width": 176, "fused_transposed": 0})
 
 
 @pytest.mark.parametrize("width", PAIR_WIDTHS)

@@ -139,3 +139,15 @@ def _compare(A, B, C, nsplit):
         scale = (A.abs() @ B.abs().T).numpy()
         tol = 4e-5
     assert np.all(np.abs(C - ref) <= tol * scale + 1e-6), np.max(np.abs(C - ref) / (scale + 1e-30))
+
+
+@pytest.mark.parametrize("ctas,stages,b_rows", [(120, 3, 88), (148, 3, 88), (30, 4, 64)])
+def test_tma_operand_ring_streams_every_stage(ctas, stages, b_rows):
+    """The TMA operand ring alone (the fused product's stage: A hi/lo 128 rows, B hi/lo
+    b_rows rows) on up to every SM: every bounded wait completes, the bytes delivered are
+    the stage bytes of every pass, and the rate per SM is a plausible figure."""
+    r = bnb.bnb_diag_tma_stream(ctas, stages, b_rows, reps=4, launches=3)
+    assert r["err"] == 0, r
+    stage = 2 * 128 * 64 * 2 + 2 * b_rows * 64 * 2
+    assert r["bytes"] == ctas * 4 * 16 * stage
+    assert 5.0 < r["gbs_per_sm"] < 2000.0, r
