@@ -89,8 +89,8 @@ def parse():
                          "where they can change the prune decision (0)")
     ap.add_argument("--fused-select", type=int, default=0, choices=[0, 1],
                     help="the selection as one cooperative launch (1) or separate launches (0)")
-    ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2],
-                    help="U' = H W'^T: 0 measured at setup, 1 cluster-reduced, 2 CTA pairs split-K")
+    ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="U' = H W'^T: 0 measured at setup, 1 cluster-reduced, 2 CTA pairs split-K, 3 CTA pairs in split-K clusters")
     ap.add_argument("--mv-crossover", type=int, default=-1,
                     help="narrow-form crossover (-1 default; 0 = tensor-core form only: graphs "
                          "without conditional nodes, which ncu can profile kernel by kernel)")
@@ -302,7 +302,7 @@ def run_mine(args, rank, world):
     h.close()
     shapes = {k: stats.get(k) for k in ("xw_tile_width", "xw_cluster", "fused_tile_width",
                                           "fused_clusters", "fused_pairs", "fused_transposed",
-                                          "u_split")}
+                                          "u_split", "u_cluster_pairs")}
     out = dict(ms=ms, nodes=nodes, prof=prof, prog=prog, clocks=clocks, cfg=cfg, tune=tune,
                setup_seconds=stats.get("setup_seconds"),
                kernels=kernels_per_round * args.steps * R, after=after, res=res, shapes=shapes,

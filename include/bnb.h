@@ -102,12 +102,15 @@ typedef struct {
                             the device or the problem cannot run fails bnb_create with
                             BNB_EINVAL. */
   int u_shape;           /* tensor-core precisions, the product U' = H W'^T: 0 (default) =
-                            the faster of the two forms measured at creation; 1 = K split
+                            the fastest of the forms measured at creation; 1 = K split
                             over the CTAs of a thread-block cluster, reduced in distributed
                             shared memory; 2 = 256 x 256 tiles on CTA pairs with K split into
                             chunks whose partial products a second kernel adds in order
                             (BNB_PREC_TC3 and BNB_PREC_BF16 only; needs at least two chunks
-                            per tile to fill the GPU).  Otherwise as fused_shape. */
+                            per tile to fill the GPU); 3 = 256 x 128 tiles, each on a
+                            cluster of 4 (else 2) CTA pairs that split K and add their
+                            partial tiles in distributed shared memory (BNB_PREC_TC3 and
+                            BNB_PREC_BF16 only).  Otherwise as fused_shape. */
   int ub_polish;         /* bnb_upper_batch: 1 (default) re-solves each support exactly in FP64
                             after the projected-gradient method; 0 returns the projected-
                             gradient solution itself (ADMM precision, upcast) with its FP64
@@ -327,6 +330,8 @@ typedef struct {
      slots) */
   int xw_tile_width, xw_cluster, fused_tile_width, fused_clusters, fused_pairs, fused_transposed;
   int u_split;              /* K chunks of U' = H W'^T on CTA pairs (0: the cluster-reduced form) */
+  int u_cluster_pairs;      /* CTA pairs per cluster of U' = H W'^T in its pair-in-cluster form
+                               (u_shape 3; 0: another form) */
 } bnb_stats;
 
 int bnb_get_stats(const bnb_handle* h, bnb_stats* out);

@@ -69,7 +69,8 @@ class bnb_stats(ctypes.Structure):
                 ("round_kernels", ctypes.c_int), ("xw_tile_width", ctypes.c_int),
                 ("xw_cluster", ctypes.c_int), ("fused_tile_width", ctypes.c_int),
                 ("fused_clusters", ctypes.c_int), ("fused_pairs", ctypes.c_int),
-                ("fused_transposed", ctypes.c_int), ("u_split", ctypes.c_int)]
+                ("fused_transposed", ctypes.c_int), ("u_split", ctypes.c_int),
+                ("u_cluster_pairs", ctypes.c_int)]
 
 
 class bnb_progress(ctypes.Structure):

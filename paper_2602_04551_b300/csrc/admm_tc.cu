@@ -851,6 +851,11 @@ template <int NS>
 static int u_product(Engine<float>& e, const TcOperand& HT, const TcOperand& Wop, bool last) {
   const int n = e.n, p = e.p, K = e.K;
   if constexpr (NS != 2) {
+    if (e.tc_ucs > 0)
+      return tc_gemm_cpair<128, NS, TcEpiU>(
+          e.st, HT, Wop, n, K, p, e.tc_ucs, e.slot_active, e.tc_err,
+          TcEpiU{e.u_hi, NS >= 2 ? e.u_lo : nullptr, e.ldn, e.slot_active, (float*)e.U,
+                 (const float*)e.ucR, (const float*)e.yR, e.tc_stat, e.nbt, K, last ? 1 : 0});
     if (e.tc_usplit > 0) {
       const int kc = u_chunk(e);
       const int nz = (p + kc - 1) / kc;
@@ -872,28 +877,49 @@ static int u_product(Engine<float>& e, const TcOperand& HT, const TcOperand& Wop
                          last ? 1 : 0});
 }
 
-// Times the two forms of U' = H W'^T (cluster-reduced; CTA pairs with the K range split
-// into chunks reduced by k_u_reduce) and keeps the faster, or the one u_product asks for.
+// Times the forms of U' = H W'^T (cluster-reduced; CTA pairs with the K range split into
+// chunks reduced by k_u_reduce; CTA pairs in clusters that split the K range, reduced in
+// distributed shared memory) and keeps the fastest, or the one u_product is asked for.
 template <int NS>
 static int pick_u_shape(Engine<float>& e) {
   e.tc_usplit = 0;
+  e.tc_ucs = 0;
   if constexpr (NS == 2) {
-    return e.u_kind == 2 ? BNB_EINVAL : 0;   // the pair kernel's 2-term form pairs H, not W'
+    return e.u_kind >= 2 ? BNB_EINVAL : 0;   // the pair kernels' 2-term form pairs H, not W'
   } else {
+  const int steps = (e.p + tc::BK - 1) / tc::BK;
+  // pair split-K with partial sums in global memory
   const int tiles = ((e.n + 255) / 256) * ((e.K + 255) / 256);
   int pairs = tc_pair_clusters<256, NS, TcEpiPartial, 8>();
   if (pairs > e.sms / 2) pairs = e.sms / 2;
-  const int steps = (e.p + tc::BK - 1) / tc::BK;
   int nz = tiles > 0 ? pairs / tiles : 0;
   if (nz > e.usplit_max) nz = e.usplit_max;
   if (nz > steps) nz = steps;
-  if (nz < 2) return e.u_kind == 2 ? BNB_EINVAL : 0;   // the pair form would not fill the GPU
+  if (nz < 2) nz = 0;                        // the pair form would not fill the GPU
+  // pairs in clusters: 4 or 2 pairs per cluster, each K chunk at least two K steps
+  std::vector<int> cpair;
+  for (int cs : {4, 2})
+    if (steps >= 2 * cs && tc_cpair_active_clusters<128, NS, TcEpiU>(cs) >= 1) cpair.push_back(cs);
   if (e.u_kind == 1) return 0;
-  e.tc_upairs = pairs;
   if (e.u_kind == 2) {
+    if (!nz) return BNB_EINVAL;
+    e.tc_upairs = pairs;
     e.tc_usplit = nz;
     return 0;
   }
+  if (e.u_kind == 3) {
+    if (cpair.empty()) return BNB_EINVAL;
+    e.tc_ucs = cpair[0];
+    return 0;
+  }
+  struct Cand {
+    int usplit, ucs;
+  };
+  std::vector<Cand> cands = {{0, 0}};
+  if (nz) cands.push_back({nz, 0});
+  for (int cs : cpair) cands.push_back({0, cs});
+  if (cands.size() == 1) return 0;
+  e.tc_upairs = pairs;
   cudaStream_t st = e.st;
   const TcOperand HT{e.ht_hi, e.ht_lo, e.n, e.p, e.ldp};
   const TcOperand Wop{e.w_hi, e.w_lo, e.K, e.p, e.ldp};
@@ -901,11 +927,12 @@ static int pick_u_shape(Engine<float>& e) {
   cudaEvent_t ev[2];
   BNB_CUDA_OK(cudaEventCreate(&ev[0]));
   BNB_CUDA_OK(cudaEventCreate(&ev[1]));
-  float tbest[2] = {-1.f, -1.f};
+  std::vector<float> tbest(cands.size(), -1.f);
   int rc = 0;
   for (int sweep = 0; sweep < 2 && !rc; ++sweep)
-    for (int c = 0; c < 2 && !rc; ++c) {
-      e.tc_usplit = c ? nz : 0;
+    for (size_t c = 0; c < cands.size() && !rc; ++c) {
+      e.tc_usplit = cands[c].usplit;
+      e.tc_ucs = cands[c].ucs;
       if ((rc = u_product<NS>(e, HT, Wop, false))) break;                    // warm-up
       cudaEventRecord(ev[0], st);
       for (int r = 0; r < 5 && !rc; ++r) rc = u_product<NS>(e, HT, Wop, false);
@@ -918,7 +945,11 @@ static int pick_u_shape(Engine<float>& e) {
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (rc) return rc;
-  e.tc_usplit = (tbest[1] >= 0 && tbest[1] < tbest[0]) ? nz : 0;
+  size_t best = 0;
+  for (size_t c = 1; c < cands.size(); ++c)
+    if (tbest[c] >= 0 && tbest[c] < tbest[best]) best = c;
+  e.tc_usplit = cands[best].usplit;
+  e.tc_ucs = cands[best].ucs;
   BNB_CUDA_OK(cudaMemsetAsync(e.slot_active, 0, sizeof(int) * e.K, st));
   BNB_CUDA_OK(cudaMemsetAsync(e.u_hi, 0, 2 * (size_t)e.K * e.ldn, st));
   if (e.u_lo) BNB_CUDA_OK(cudaMemsetAsync(e.u_lo, 0, 2 * (size_t)e.K * e.ldn, st));

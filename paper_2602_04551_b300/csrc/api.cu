@@ -540,7 +540,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.max_depth < 8 || o.max_depth > 4096) return fail(BNB_EINVAL, "max_depth must be in [8, 4096]");
   if (o.mv_crossover < -1 || o.mv_crossover > 32) return fail(BNB_EINVAL, "mv_crossover must be in [-1, 32]");
   if (o.fused_shape < 0 || o.fused_shape > 4) return fail(BNB_EINVAL, "fused_shape must be in [0, 4]");
-  if (o.u_shape < 0 || o.u_shape > 2) return fail(BNB_EINVAL, "u_shape must be in [0, 2]");
+  if (o.u_shape < 0 || o.u_shape > 3) return fail(BNB_EINVAL, "u_shape must be in [0, 3]");
   if (!(o.relax_alpha >= 1.0 && o.relax_alpha <= 1.9)) return fail(BNB_EINVAL, "relax_alpha must be in [1, 1.9]");
   if (o.queue_capacity < 4LL * o.batch_K + 8 || o.queue_capacity > (1LL << 30))
     return fail(BNB_EINVAL, "queue_capacity must be in [4 K + 8, 2^30]");
@@ -591,6 +591,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
     h->stats.fused_pairs = h->ef->tc_pair3;
     h->stats.fused_transposed = h->ef->tc_pair3 > 0 && !h->ef->tc_pairnt ? 1 : 0;
     h->stats.u_split = h->ef->tc_usplit;
+    h->stats.u_cluster_pairs = h->ef->tc_ucs;
   }
   *out = h;
   return BNB_OK;

@@ -194,6 +194,8 @@ struct Engine {
   int u_kind = 0;               // U' = H W'^T: 0 measured, 1 cluster-reduced, 2 pairs split-K
   int tc_usplit = 0;            // > 0: U' on CTA pairs in this many K chunks (k_u_reduce)
   int tc_upairs = 0;            // CTA pairs the split form runs on
+  int tc_ucs = 0;               // > 0: U' on 256 x 128 tiles, clusters of this many CTA pairs
+                                // splitting K (tc_gemm_cpair_kernel)
   int usplit_max = 0;           // most K chunks the partial buffer holds
   float* upart = nullptr;       // [usplit_max][K][n] partial products of U'
   int fused_kind = 0;           // requested shape: 0 measured, 1 single, 2 clusters of two,

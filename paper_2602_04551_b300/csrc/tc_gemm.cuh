@@ -1217,5 +1217,224 @@ tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap ma_hi,
   }
 }
 
+// ---- CTA pairs inside a split-K cluster: one 256 x BN tile per cluster
+//
+// A cluster of 2 cs CTAs computes one 256 x BN output tile: CTA rank r is half h = r & 1
+// of pair z = r >> 1, and pair z accumulates the K chunk [z kchunk, (z + 1) kchunk) with
+// cta_group::2 MMAs issued by its even CTA (rows [0, 128) of the tile in the even CTA's
+// tensor memory, [128, 256) in the odd one's; B rows [BN/2 h, BN/2 (h + 1)) loaded by
+// half h).  Against the cluster-reduced kernel (128 x BN tiles, one CTA per K chunk), each
+// CTA loads half the B rows per output, so the operand bytes each SM receives drop by a
+// quarter at BN = 128.  The partial tiles are then summed through distributed shared
+// memory: the cs CTAs of half h each own BN / cs columns, add the pairs' partials in
+// pair order (deterministic) and hand each 4-row group to the epilogue (put4 / col as
+// for tc_gemm_cred_kernel, col's row tile = 2 mt + h in 128-row tiles).
+template <int BN, int NSPLIT>
+struct CPairGeo {
+  static constexpr int A_BYTES = BM * BK * 2;              // this CTA's 128 rows of A
+  static constexpr int B_BYTES = (BN / 2) * BK * 2;        // this CTA's BN/2 rows of B
+  static constexpr int STAGE_BYTES =
+      A_BYTES * (NSPLIT >= 2 ? 2 : 1) + B_BYTES * (NSPLIT == 3 ? 2 : 1);
+  static constexpr int STAGES =
+      (196 * 1024) / STAGE_BYTES > 8 ? 8 : (196 * 1024) / STAGE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  static_assert(STAGES >= 2, "at least two stages");
+  static_assert(STAGES * STAGE_BYTES >= BN * BM * 4, "the partial tile reuses the operand ring");
+};
+
+// the leader's commit arrives on the mbarrier at this offset in both CTAs of its pair
+// (cluster ranks `first` and first + 1)
+__device__ __forceinline__ void mma_commit_pair_at(uint64_t* bar, uint32_t first) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)), "h"((uint16_t)(3u << first))
+      : "memory");
+}
+
+template <int BN, int NSPLIT, class Epi>
+__global__ void __launch_bounds__(64 + 32 * EPI_WARPS, 1)
+tc_gemm_cpair_kernel(const __grid_constant__ CUtensorMap ma_hi,
+                     const __grid_constant__ CUtensorMap ma_lo,
+                     const __grid_constant__ CUtensorMap mb_hi,
+                     const __grid_constant__ CUtensorMap mb_lo, int M, int N, int Kred,
+                     int kchunk, const int* __restrict__ active, int* err, Epi epi) {
+  using G = CPairGeo<BN, NSPLIT>;
+  constexpr int S = G::STAGES;
+  static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "pair MMA N: a multiple of 16 up to 256");
+  extern __shared__ uint8_t dsm_raw[];
+  __shared__ __align__(8) uint64_t full_bar[S];
+  __shared__ __align__(8) uint64_t empty_bar[S];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  uint8_t* base = (uint8_t*)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank(), cs2 = cluster_size();
+  const uint32_t h = rank & 1u, z = rank >> 1, first = rank & ~1u;
+  const bool leader = h == 0;
+  const int tile = (int)(blockIdx.x / cs2);
+  const int mtiles = (M + 255) / 256;
+  const int mt = tile % mtiles, nt = tile / mtiles;
+  const int m0 = mt * 256 + 128 * (int)h;                  // this CTA's first output row
+  const int nb = nt * BN;                                  // the tile's first column
+  if (active != nullptr) {
+    int any = 0;
+    for (int j = threadIdx.x; j < BN; j += blockDim.x)
+      if (nb + j < N && active[nb + j]) any = 1;
+    if (!__syncthreads_or(any)) return;     // the whole cluster shares this tile
+  }
+  const int kbeg = (int)z * kchunk;
+  const int kend = min(Kred, kbeg + kchunk);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  cluster_sync_all();                            // every CTA's barriers and TMEM exist
+  const uint32_t tmem = tmem_slot;
+  uint32_t peer_tmem;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];"
+               : "=r"(peer_tmem)
+               : "r"(mapa_u32(smem_u32(&tmem_slot), rank ^ 1u))
+               : "memory");
+  const bool pair_ok = peer_tmem == tmem;
+  if (!pair_ok && threadIdx.x == 0) atomicOr(err, 32);
+  const uint32_t full_l = mapa_u32(smem_u32(&full_bar[0]), first);   // the pair leader's
+  float* part = reinterpret_cast<float*>(base);   // [BN][BM] after the main loop
+
+  if (pair_ok && warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs of the pair): this CTA's halves of each stage
+    const int brow = nb + (BN / 2) * (int)h;
+    long long g = 0;
+    for (int kb = 0; kb < nk; ++kb, ++g) {
+      const int s = kb % S;
+      if (kb >= S && !mbar_wait(&empty_bar[s], (uint32_t)(((kb / S) & 1) ^ 1), err, 1)) break;
+      if (leader) mbar_expect_tx(&full_bar[s], 2 * G::STAGE_BYTES);
+      const int k = kbeg + kb * BK;
+      const uint32_t fb = full_l + 8u * (uint32_t)s;
+      uint8_t* st0 = base + s * G::STAGE_BYTES;
+      tma_load_2d_pair(st0, &ma_hi, fb, k, m0);
+      tma_load_2d_pair(st0 + G::A_BYTES, &mb_hi, fb, k, brow);
+      if (NSPLIT >= 2) tma_load_2d_pair(st0 + G::A_BYTES + G::B_BYTES, &ma_lo, fb, k, m0);
+      if (NSPLIT == 3) tma_load_2d_pair(st0 + 2 * G::A_BYTES + G::B_BYTES, &mb_lo, fb, k, brow);
+    }
+    // the leader's last stages count both CTAs' copies: they have all landed before the
+    // ring is reused for the partial tile
+    if (leader)
+      for (long long j = g - S < 0 ? 0 : g - S; j < g; ++j)
+        mbar_wait(&full_bar[(int)(j % S)], (uint32_t)((j / S) & 1), err, 16);
+  } else if (pair_ok && warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (the pair's even CTA)
+    constexpr uint32_t idesc = idesc_bf16_pair(BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % S;
+      if (!mbar_wait(&full_bar[s], (uint32_t)((kb / S) & 1), err, 2)) break;
+      fence_after();
+      uint8_t* st0 = base + s * G::STAGE_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t ah = smem_desc_sw128(st0 + kk * 32);
+        const uint64_t bh = smem_desc_sw128(st0 + G::A_BYTES + kk * 32);
+        mma_bf16_pair(tmem, ah, bh, idesc, acc);
+        if (NSPLIT >= 2)
+          mma_bf16_pair(tmem, smem_desc_sw128(st0 + G::A_BYTES + G::B_BYTES + kk * 32), bh, idesc,
+                        1u);
+        if (NSPLIT == 3)
+          mma_bf16_pair(tmem, ah, smem_desc_sw128(st0 + 2 * G::A_BYTES + G::B_BYTES + kk * 32),
+                        idesc, 1u);
+      }
+      mma_commit_pair_at(&empty_bar[s], first);   // stage s free in both CTAs of the pair
+    }
+    mma_commit_pair_at(&done_bar, first);         // after every MMA issued above
+  } else if (pair_ok && warp >= 2) {
+    // ---------------- accumulator -> own partial tile (warp w: TMEM lanes 32 (w % 4) ..)
+    const int q = warp & 3, g = (warp - 2) >> 2;
+    const bool ok = mbar_wait_cluster(&done_bar, 0, err, 4);
+    fence_after();
+    const int row = 32 * q + lane;
+#pragma unroll 1
+    for (int c = 16 * g; c < BN; c += 16 * (EPI_WARPS / 4)) {
+      float v[16];
+      if (ok && nk > 0) {
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[(c + j) * BM + row] = v[j];
+    }
+  }
+  cluster_sync_all();
+  if (pair_ok && warp >= 2) {
+    // ---------------- this CTA's columns of its half: the pairs' partials added in order
+    const int cs = (int)(cs2 >> 1);
+    const int w = warp - 2;
+    const int per = (BN + cs - 1) / cs;
+    const int c0 = (int)z * per, c1 = min(BN, c0 + per);
+    const uint32_t lbase = smem_u32(part);
+#pragma unroll 1
+    for (int c = c0 + w; c < c1; c += EPI_WARPS) {
+      const int n = nb + c;
+      if (n >= N) break;                         // warp-uniform; later columns are out too
+      const uint32_t off = lbase + (uint32_t)(c * BM + 4 * lane) * 4u;
+      float4 pr[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (r < cs) pr[r] = ld_dsmem_f4(off, 2u * (uint32_t)r + h);
+      float4 a = pr[0];
+#pragma unroll
+      for (int r = 1; r < 4; ++r)
+        if (r < cs) {
+          a.x += pr[r].x;
+          a.y += pr[r].y;
+          a.z += pr[r].z;
+          a.w += pr[r].w;
+        }
+      float st[Epi::NSTAT > 0 ? Epi::NSTAT : 1];
+#pragma unroll
+      for (int k = 0; k < (Epi::NSTAT > 0 ? Epi::NSTAT : 1); ++k) st[k] = 0.f;
+      epi.put4(m0 + 4 * lane, n, a, M, N, st);
+      if constexpr (Epi::NSTAT > 0) {
+        if (epi.stats && m0 < M) {
+#pragma unroll
+          for (int k = 0; k < Epi::NSTAT; ++k) st[k] = warp_sum(st[k]);
+          if (lane == 0) epi.col(2 * mt + (int)h, n, st);
+        }
+      }
+    }
+  }
+  // teardown: every MMA of the pair has completed, no CTA leaves while its tile is read,
+  // then the pair frees its columns
+  if (pair_ok && warp == 1) {
+    if (lane == 0) mbar_wait_cluster(&done_bar, 0, err, 64);
+    __syncwarp();
+  }
+  cluster_sync_all();
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 }  // namespace tc
 }  // namespace bnb

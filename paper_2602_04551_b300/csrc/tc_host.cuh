@@ -348,6 +348,84 @@ int tc_gemm_pair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M,
   return 0;
 }
 
+// Co-resident clusters of 2 cs CTAs (cs pairs) of the pair-in-cluster kernel (0: none);
+// cached per instantiation and cs.
+template <int BN, int NSPLIT, class Epi>
+int tc_cpair_active_clusters(int cs) {
+  using G = tc::CPairGeo<BN, NSPLIT>;
+  static int cached[5] = {-1, -1, -1, -1, -1};
+  if (cs < 1 || cs > 4) return 0;
+  if (cached[cs] < 0) {
+    cached[cs] = 0;
+    auto kern = tc::tc_gemm_cpair_kernel<BN, NSPLIT, Epi>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * cs);
+    cfg.blockDim = dim3(64 + 32 * tc::EPI_WARPS);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2 * cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      nc = 0;
+    }
+    cached[cs] = nc;
+  }
+  return cached[cs];
+}
+
+// C = A B^T with 256 x BN tiles, each on a cluster of cs CTA pairs that split the K range
+// (tc_gemm_cpair_kernel); A: M rows (boxes of 128 rows), B: N rows (boxes of BN/2 rows).
+template <int BN, int NSPLIT, class Epi>
+int tc_gemm_cpair(cudaStream_t st, const TcOperand& A, const TcOperand& B, int M, int N, int Kred,
+                  int cs, const int* active, int* err, Epi epi) {
+  using G = tc::CPairGeo<BN, NSPLIT>;
+  if (M <= 0 || N <= 0 || Kred <= 0) return 0;
+  if (cs < 1 || cs > 4) return BNB_EINVAL;
+  CUtensorMap ah, al, bh, bl;
+  if (int rc = make_map_bf16(&ah, A.hi, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (int rc = make_map_bf16(&bh, B.hi, B.kdim, B.rows, B.ld, BN / 2)) return rc;
+  al = ah;
+  bl = bh;
+  if (NSPLIT >= 2)
+    if (int rc = make_map_bf16(&al, A.lo, A.kdim, A.rows, A.ld, tc::BM)) return rc;
+  if (NSPLIT == 3)
+    if (int rc = make_map_bf16(&bl, B.lo, B.kdim, B.rows, B.ld, BN / 2)) return rc;
+  auto kern = tc::tc_gemm_cpair_kernel<BN, NSPLIT, Epi>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    BNB_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM));
+    attr_set = true;
+  }
+  const int steps = (Kred + tc::BK - 1) / tc::BK;
+  const int kchunk = (steps + cs - 1) / cs * tc::BK;
+  const long long tiles = (long long)((M + 255) / 256) * ((N + BN - 1) / BN);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * cs * tiles));
+  cfg.blockDim = dim3(64 + 32 * tc::EPI_WARPS);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2 * cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  BNB_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, M, N, Kred, kchunk, active, err, epi));
+  return 0;
+}
+
 // Split-K partial store: C + z * zstride [m + n * ldc] = acc
 struct TcEpiStore {
   static constexpr int SMEM_FLOATS = 0;

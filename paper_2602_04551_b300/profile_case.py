@@ -28,7 +28,7 @@ def parser() -> argparse.ArgumentParser:
     ap.add_argument("--prime-seconds", type=float, default=30.0)
     ap.add_argument("--mv-crossover", type=int, default=-1)
     ap.add_argument("--fused-shape", type=int, default=0, choices=[0, 1, 2, 3, 4])
-    ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--u-shape", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--fused-width", type=int, default=0)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--tma-stream", action="store_true",

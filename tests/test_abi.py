@@ -283,7 +283,7 @@ def test_option_validation_on_the_host(lib):
         (dict(check_every=0), "check_every"), (dict(max_depth=4), "max_depth"),
         (dict(max_depth=5000), "max_depth"), (dict(mv_crossover=-2), "mv_crossover"),
         (dict(mv_crossover=33), "mv_crossover"), (dict(fused_shape=5), "fused_shape"),
-        (dict(u_shape=3), "u_shape"), (dict(relax_alpha=0.5), "relax_alpha"),
+        (dict(u_shape=4), "u_shape"), (dict(relax_alpha=0.5), "relax_alpha"),
         (dict(relax_alpha=2.0), "relax_alpha"), (dict(queue_capacity=10), "queue_capacity"),
         (dict(queue_capacity=(1 << 30) + 1), "queue_capacity"), (dict(precision=7), "precision"),
         (dict(ub_polish=2), "ub_polish"), (dict(log_nodes=-1), "log_nodes"),

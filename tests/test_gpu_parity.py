@@ -447,14 +447,15 @@ def test_converged_bounds_odd_sizes():
             assert out["lb"][k] >= opt - 20 * 1e-5 * max(1.0, abs(opt))
 
 
-U_SHAPES = [pytest.param(1, id="cluster_reduced"), pytest.param(2, id="pairs_split_k")]
+U_SHAPES = [pytest.param(1, id="cluster_reduced"), pytest.param(2, id="pairs_split_k"),
+            pytest.param(3, id="pairs_in_clusters")]
 
 
 @pytest.mark.parametrize("ushape", U_SHAPES)
 @pytest.mark.parametrize("prec", [3, 2])
 def test_one_admm_iteration_every_u_shape(ushape, prec):
-    """Both forms of U' = H W'^T (K split over a cluster; K chunks on CTA pairs added by
-    a second kernel) give the oracle's iteration."""
+    """Every form of U' = H W'^T (K split over a cluster; K chunks on CTA pairs added by
+    a second kernel; CTA pairs in clusters that split K) gives the oracle's iteration."""
     inst, lam0, lam2, M = _inst("c2_small", 1)
     _one_iteration_check(inst, lam0, lam2, M, prec, K=45, Kopt=128, rows=range(45), seed=41,
                          u_shape=ushape, mv_crossover=0)
@@ -468,6 +469,20 @@ def test_one_admm_iteration_pairs_split_k_full_size():
                          rows=[0, 127, 128, 255, 256, 511], seed=42, u_shape=2, mv_crossover=0)
 
 
+@pytest.mark.parametrize("rho,alpha", [(1.0, 1.0), (0.2, 1.6)])
+def test_admm_iterations_pairs_in_clusters_full_size(rho, alpha):
+    """c2 at K = 512 with U' on 256 x 128 tiles, each on a cluster of CTA pairs splitting
+    the K range (samples of both CTAs of a pair: rows 0-127 and 128-255 of each tile lie in
+    different CTAs, every pair's partial tile summed in distributed shared memory), over a
+    round of three iterations (the last one also forms U and the stop-test sums), against
+    the oracle's iterations."""
+    inst, lam0, lam2, M = _inst("c2", 0, frac=0.02)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=512, Kopt=512,
+                         rows=[0, 63, 64, 127, 128, 255, 256, 383, 511], seed=44, rho=rho,
+                         alpha=alpha, iters=3, u_shape=3, mv_crossover=0,
+                         stats={"u_cluster_pairs": 4})
+
+
 @pytest.mark.parametrize("ushape", U_SHAPES)
 def test_converged_bounds_every_u_shape(ushape):
     """Converged node bounds (the stop-test sums of U come from either form of U') stay
@@ -478,7 +493,9 @@ def test_converged_bounds_every_u_shape(ushape):
     with _handle(inst, lam0, lam2, M, 3, K=128, node_tol=1e-5, max_admm_iter=20000,
                  mv_crossover=0, u_shape=ushape) as h:
         out = bnb.bnb_relax_batch(h, fix, max_iter=20000)
-        assert (bnb.bnb_get_stats(h)["u_split"] > 0) == (ushape == 2)
+        st = bnb.bnb_get_stats(h)
+        assert (st["u_split"] > 0) == (ushape == 2)
+        assert (st["u_cluster_pairs"] > 0) == (ushape == 3)
     for k in range(20):
         _, opt = pgd.solve_node(inst.X, inst.y, fix[k], lam0, lam2, M)
         assert out["lb"][k] <= opt + 1e-9 * max(1.0, abs(opt))
