@@ -24,7 +24,8 @@ batched upper bound, and prunes/branches into the pool.
             the FP64 oracle at the logged residuals
   certified_solves  full solves to gap 1e-4 over five lambda0 values chosen so that
             the first incumbent has 5, 8, 12, 16 and 20 nonzeros, mixed precision
-            and plain FP64, per instance; with `reverify`: certificates of a real
+            and plain FP64, per instance, and where the mixed path certified, again
+            with the early-branch node stop; with `reverify`: certificates of a real
             solve and every final support re-checked by the FP64 oracle
   serve     a short run of the serving workload (32 requests): p50/p99 latency,
             queueing and service time, certified count
@@ -84,6 +85,9 @@ def parse():
                          "4 untransposed on CTA pairs")
     ap.add_argument("--fused-width", type=int, default=0,
                     help="tile width of the fused X^T U' product (0: measured at setup)")
+    ap.add_argument("--early-branch", type=int, default=0, choices=[0, 1],
+                    help="solves: retire a node whose primal estimate is already below the "
+                         "prune threshold (bnb_options.early_branch)")
     ap.add_argument("--exact-bounds", type=int, default=0, choices=[0, 1],
                     help="exact FP64 certificate terms for every branched node (1) or only "
                          "where they can change the prune decision (0)")
@@ -736,14 +740,19 @@ def greedy_lambda0(X, y, lam2, M, k):
     return float(np.sqrt(max(drops[k - 1], 1e-300) * max(drops[k], 1e-300)))
 
 
-def solve_record(args, inst, lam0, lam2, M, rho, alpha, prec, time_limit, log_nodes=0):
-    """One full solve to gap 1e-4; its record (and the node log when requested)."""
+def solve_record(args, inst, lam0, lam2, M, rho, alpha, prec, time_limit, log_nodes=0,
+                 early_branch=None, check_every=None):
+    """One full solve to gap 1e-4; its record (and the node log when requested).  The node
+    stop settings default to the command line's."""
     import torch
     import paper_2602_04551_b300 as bnb
-    o = bnb.bnb_options_default(M=M, batch_K=args.K, check_every=args.check_every,
+    o = bnb.bnb_options_default(M=M, batch_K=args.K,
+                                check_every=args.check_every if check_every is None else check_every,
                                 precision=prec, rho=rho, relax_alpha=alpha,
                                 queue_capacity=1 << 21, max_depth=args.max_depth,
-                                time_limit_s=time_limit, log_nodes=log_nodes)
+                                time_limit_s=time_limit, log_nodes=log_nodes,
+                                early_branch=args.early_branch if early_branch is None
+                                else early_branch)
     with bnb.bnb_create(inst.X, inst.y, lam0, lam2, o) as h:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -837,20 +846,48 @@ def run_certified(args, seed):
             rec["support_objective_rel_diff"] = abs(obj - rec["ub"]) / abs(obj)
             row[name] = rec
             row[name + "_support"] = [int(i) for i in S]
+            if name == "mixed":
+                row["mixed_support_list"] = [int(i) for i in S]
             if log is not None:
                 logs.append((lam0, log))
             note(f"certified target {pk['target_nnz']} {name}: {rec['status']} {rec['seconds']:.2f} s")
         row["same_support"] = row.pop("mixed_support") == row.pop("fp64_support")
         if row["mixed"]["certified"] and row["fp64"]["certified"]:
             row["speedup_time_to_certificate"] = row["fp64"]["seconds"] / row["mixed"]["seconds"]
+        if row["mixed"]["certified"]:
+            # the same instance with the early-branch node stop (a node whose primal estimate
+            # is below the prune threshold is branched at once) and a stop test every 10
+            # iterations: run where the default path certified, to time the same certificate
+            rec, beta, _ = solve_record(args, inst, lam0, lam2, M, args.rho, args.alpha,
+                                        PREC[args.precision], args.cert_time_limit,
+                                        early_branch=1, check_every=10)
+            S = np.nonzero(beta)[0]
+            obj, _ = oub.support_objective(inst.X, inst.y, S, lam0, lam2, M)
+            rec["support_objective_rel_diff"] = abs(obj - rec["ub"]) / abs(obj)
+            rec["same_support_as_mixed"] = [int(i) for i in S] == row["mixed_support_list"]
+            if rec["certified"]:
+                rec["speedup_vs_mixed"] = row["mixed"]["seconds"] / rec["seconds"]
+                if row["fp64"]["certified"]:
+                    rec["speedup_vs_fp64"] = row["fp64"]["seconds"] / rec["seconds"]
+            row["mixed_early_branch"] = rec
+            note(f"certified target {pk['target_nnz']} mixed_early_branch: {rec['status']} "
+                 f"{rec['seconds']:.3f} s")
+        row.pop("mixed_support_list", None)
         rows.append(row)
     cert = {}
     for name in ("mixed", "fp64"):
         done = [r[name] for r in rows if r[name]["certified"]]
         cert[name] = {"certified": len(done), "of": len(rows),
                       "solves_per_s": len(done) / sum(r[name]["seconds"] for r in rows)}
+    eb = [r["mixed_early_branch"] for r in rows if "mixed_early_branch" in r]
+    cert["mixed_early_branch"] = {
+        "certified": sum(1 for r in eb if r["certified"]), "of": len(eb),
+        "note": "run on the instances the mixed path certified; early_branch = 1, a stop "
+                "test every 10 iterations",
+        "seconds": [r["seconds"] for r in eb]}
     rv = {"certificates": None, "supports_ok": all(
-        r[nm]["support_objective_rel_diff"] <= 1e-10 for r in rows for nm in ("mixed", "fp64"))}
+        r[nm]["support_objective_rel_diff"] <= 1e-10 for r in rows for nm in ("mixed", "fp64"))
+        and all(r["support_objective_rel_diff"] <= 1e-10 for r in eb)}
     agg = None
     for lam0, log in logs:
         one = reverify_logs(inst, lam0, lam2, M, [log])

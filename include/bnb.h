@@ -137,6 +137,14 @@ typedef struct {
                             (fixings, FP64 residual, certified bound; bnb_get_node_log), in
                             [0, 65536], default 0 (off); takes log_nodes x (p + 8 n + 80)
                             bytes of device memory */
+  int early_branch;      /* bnb_solve's node stop: 1 also retires a node at a stop test where
+                            its estimated relaxation objective P(beta) (an upper bound on the
+                            node's relaxation value, beta being feasible) lies below the
+                            prune threshold UB (1 - gap) by more than 10 node_tol: no
+                            accuracy could then prune it, so it is certified (a valid, looser
+                            FP64 bound) and branched at once; 0 (default) iterates every
+                            node to the node gap, as the paper does (Section 5.1).  Exactness
+                            is the same either way. */
 } bnb_options;
 
 /* Fill *opt with defaults (M is set to 0: the caller must set it). */

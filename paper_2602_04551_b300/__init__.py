@@ -56,7 +56,7 @@ class bnb_options(ctypes.Structure):
                 ("fused_shape", ctypes.c_int), ("u_shape", ctypes.c_int),
                 ("ub_polish", ctypes.c_int), ("fused_width", ctypes.c_int),
                 ("fused_select", ctypes.c_int), ("exact_bounds", ctypes.c_int),
-                ("log_nodes", ctypes.c_int)]
+                ("log_nodes", ctypes.c_int), ("early_branch", ctypes.c_int)]
 
 
 class bnb_stats(ctypes.Structure):

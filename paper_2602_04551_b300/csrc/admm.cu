@@ -204,6 +204,10 @@ __global__ void k_stop(const R* __restrict__ XBpart, int S, const R* __restrict_
     if (use_inc) {
       const double thr = inc_ub[0] * (1.0 - params[0]);
       if (dual > thr + 1e-12 * fabs(thr)) ret = 1;
+      // P(beta) >= the node's relaxation value (beta is feasible for it): a primal estimate
+      // clearly below the threshold means no accuracy can prune the node
+      if (use_inc == 2 && isfinite(thr) && primal < thr - 10.0 * node_tol * fmax(1.0, fabs(thr)))
+        ret = 1;
     }
     slot_retire[s] = ret;
   }
@@ -246,7 +250,7 @@ __global__ void k_retired_list(int K, int* __restrict__ slot_retire, int* __rest
 }
 
 template <class R>
-int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_inc) {
+int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, int use_inc) {
   using C = TileCfg<R>;
   const int n = e.n, p = e.p, K = e.K;
   cudaStream_t st = e.st;
@@ -318,7 +322,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   k_stop<R><<<(K + 7) / 8, 256, 0, st>>>(e.XBpart, S_check, e.yR, n, K, e.g3part, e.nbm3, e.rstat,
                                e.slot_active, e.slot_iters, e.slot_retire, e.slot_gap, e.slot_dual,
                                e.slot_primal, iters, max_iter, node_tol, e.inc_ub, e.params_d,
-                               use_inc ? 1 : 0, e.tc_c1 > 0 ? e.tc_stat : nullptr, e.nbt);
+                               use_inc, e.tc_c1 > 0 ? e.tc_stat : nullptr, e.nbt);
   k_retired_list<<<1, 1024, 0, st>>>(K, e.slot_retire, e.slot_active, e.ret_slot, e.ret_active,
                                      e.ret_count);
   prof_end(e.prof, st, PK_STOP);
@@ -327,7 +331,7 @@ int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol, bool use_
   return 0;
 }
 
-template int admm_round<float>(Engine<float>&, int, int, double, bool);
-template int admm_round<double>(Engine<double>&, int, int, double, bool);
+template int admm_round<float>(Engine<float>&, int, int, double, int);
+template int admm_round<double>(Engine<double>&, int, int, double, int);
 
 }  // namespace bnb

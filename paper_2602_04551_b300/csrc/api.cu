@@ -435,6 +435,7 @@ extern "C" int bnb_options_default(bnb_options* o) {
   o->fused_width = 0;
   o->fused_select = 0;
   o->exact_bounds = 0;
+  o->early_branch = 0;
   return BNB_OK;
 }
 
@@ -549,6 +550,7 @@ static int create_common(const double* dX, const double* dy, int n, int p, doubl
   if (o.fused_width < 0 || o.fused_width > 256) return fail(BNB_EINVAL, "fused_width must be in [0, 256]");
   if (o.fused_select != 0 && o.fused_select != 1) return fail(BNB_EINVAL, "fused_select must be 0 or 1");
   if (o.exact_bounds != 0 && o.exact_bounds != 1) return fail(BNB_EINVAL, "exact_bounds must be 0 or 1");
+  if (o.early_branch != 0 && o.early_branch != 1) return fail(BNB_EINVAL, "early_branch must be 0 or 1");
   if (o.precision < BNB_PREC_FP64 || o.precision > BNB_PREC_BF16X2)
     return fail(BNB_EINVAL, "unknown precision %d", o.precision);
   if (int rc = check_device(o.device)) return rc;
@@ -710,7 +712,7 @@ static int relax_impl(bnb_handle* h, Engine<R>& e, int K, const int8_t* dfix, co
   const int max_rounds = (max_iter + o.check_every - 1) / o.check_every + 1;
   e.mv_hint = K;                      // active slots, known exactly on the host here
   while (true) {
-    if (int rc = admm_round(e, o.check_every, max_iter, o.node_tol, false)) return rc;
+    if (int rc = admm_round(e, o.check_every, max_iter, o.node_tol, 0)) return rc;
     if (int rc = certify(e, nullptr, false)) return rc;
     if (int rc = branch_support(e, true)) return rc;
     k_scatter_relax<<<(e.K + 255) / 256, 256, 0, st>>>(e.ret_slot, e.ret_count, e.cert_lb,
@@ -874,7 +876,8 @@ static int round_body(bnb_handle* h, Engine<R>& e) {
   prof_begin(pf, e.st);
   if (int rc = queue_select_refill(e)) return rc;
   prof_end(pf, e.st, PK_SELECT);
-  if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, true)) return rc;
+  if (int rc = admm_round(e, o.check_every, o.max_admm_iter, o.node_tol, o.early_branch ? 2 : 1))
+    return rc;
   if (pf) {
     prof_begin(pf, e.st);
     if (int rc = certify_screen(e, nullptr)) return rc;

@@ -233,8 +233,11 @@ struct Engine {
 
 // ---- stage launchers (all asynchronous on e.st) ----
 template <class R> int setup_data(Engine<R>& e, const double* dX, const double* dy);
+// use_incumbent: 0 none; 1 a node whose dual estimate passes the prune threshold stops
+// early; 2 also a node whose primal estimate lies below it (it is branched whatever the
+// accuracy)
 template <class R> int admm_round(Engine<R>& e, int iters, int max_iter, double node_tol,
-                                  bool use_incumbent);
+                                  int use_incumbent);
 template <class R> int certify(Engine<R>& e, const double* r_given /* K x n or null */,
                                bool use_threshold);
 template <class R> int certify_screen(Engine<R>& e, const double* r_given);

@@ -251,7 +251,8 @@ def test_documented_defaults(lib):
                 precision=lib.BNB_PREC_TC3, use_graphs=1, time_limit_s=3600.0, max_nodes=10**9,
                 queue_capacity=1 << 20, warm_capacity=0, support_max=200, ub_max_iter=200, device=0,
                 stream=None, relax_alpha=1.0, root_heuristic=1, max_depth=256, lockstep=0,
-                mv_crossover=-1, fused_shape=0, u_shape=0, ub_polish=1, fused_width=0, fused_select=0, exact_bounds=0, log_nodes=0)
+                mv_crossover=-1, fused_shape=0, u_shape=0, ub_polish=1, fused_width=0, fused_select=0, exact_bounds=0, log_nodes=0,
+                early_branch=0)
     assert {k for k, _ in o._fields_} == set(want)
     for k, v in want.items():
         assert getattr(o, k) == v, k
@@ -289,7 +290,7 @@ def test_option_validation_on_the_host(lib):
         (dict(ub_polish=2), "ub_polish"), (dict(log_nodes=-1), "log_nodes"),
         (dict(log_nodes=70000), "log_nodes"), (dict(fused_width=-1), "fused_width"),
         (dict(fused_width=300), "fused_width"), (dict(fused_select=2), "fused_select"),
-        (dict(exact_bounds=2), "exact_bounds"),
+        (dict(exact_bounds=2), "exact_bounds"), (dict(early_branch=2), "early_branch"),
     ]
     for kw, word in bad:
         rc, msg = create(**kw)

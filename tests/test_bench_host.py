@@ -221,3 +221,42 @@ def test_reverify_logs_counts_and_flags(bench):
     assert out["violations"] == 1
     assert out["exact_max_rel"] <= 1e-15
     assert out["screened_max_rel_below_exact"] == pytest.approx(0.01 / max(1.0, abs(d[1])))
+
+
+def test_certified_side_times_the_early_branch_stop_where_the_mixed_path_certified(bench, monkeypatch):
+    """run_certified (the bench line's certified_solves): every target lambda0 is solved by
+    the mixed and the FP64 paths; where the mixed path certified, once more with the
+    early-branch node stop and a stop test every 10 iterations, with its speed-ups; the
+    instances the mixed path did not certify get no third solve."""
+    import numpy as np
+    from oracle import ub as oub
+    calls = []
+    picks = [{"target_nnz": 5, "lambda0": 0.5}, {"target_nnz": 12, "lambda0": 0.05}]
+    monkeypatch.setattr(bench, "lambda0_by_count", lambda inst, lam2, M: (picks, [5, 12]))
+
+    def fake_solve(args, inst, lam0, lam2, M, rho, alpha, prec, tl, log_nodes=0,
+                   early_branch=None, check_every=None):
+        calls.append((lam0, prec, early_branch, check_every))
+        beta = np.zeros(inst.p)
+        beta[[0, 3]] = 0.5
+        obj, _ = oub.support_objective(inst.X, inst.y, np.array([0, 3]), lam0, lam2, M)
+        cert = lam0 > 0.1
+        secs = {None: 2.0 if prec == 0 else 0.04, 1: 0.02}[early_branch]
+        rec = {"status": "optimal" if cert else "time_limit", "seconds": secs, "nodes": 100,
+               "nnz": 2, "ub": obj, "lb": obj, "gap": 0.0, "certified": cert}
+        return rec, beta, None
+
+    monkeypatch.setattr(bench, "solve_record", fake_solve)
+    args = types.SimpleNamespace(workload="c1_p16", rho=0.3, alpha=1.6, precision="tc3",
+                                 cert_time_limit=1.0)
+    out = bench.run_certified(args, 0)
+    rows = out["instances"]
+    assert [c[2:] for c in calls] == [(None, None), (None, None), (1, 10), (None, None),
+                                      (None, None)]
+    eb = rows[0]["mixed_early_branch"]
+    assert eb["same_support_as_mixed"] and eb["speedup_vs_mixed"] == pytest.approx(2.0)
+    assert eb["speedup_vs_fp64"] == pytest.approx(100.0)
+    assert "mixed_early_branch" not in rows[1] and "mixed_support_list" not in rows[0]
+    assert out["paths"]["mixed_early_branch"]["certified"] == 1
+    assert out["paths"]["mixed_early_branch"]["of"] == 1
+    assert out["reverify"]["supports_ok"]

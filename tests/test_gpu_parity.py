@@ -644,6 +644,31 @@ def test_solve_matches_brute_force_p16(prec, frac):
     assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
 
 
+@pytest.mark.parametrize("prec", [3, 1, 0])
+@pytest.mark.parametrize("frac", [0.2, 0.03])
+def test_early_branch_reaches_the_brute_force_optimum(prec, frac):
+    """early_branch = 1 (a node whose primal estimate is already below the prune threshold
+    is certified and branched at once): the same brute-force optimum, a final lower bound
+    that is valid, and a C1 golden solve unchanged."""
+    inst, lam0, lam2, M = _inst("c1_p16", 0, frac=frac)
+    br = brute.solve(inst.X, inst.y, lam0, lam2, M)
+    with _handle(inst, lam0, lam2, M, prec, K=8, node_tol=1e-7, max_admm_iter=5000,
+                 early_branch=1) as h:
+        res = bnb.bnb_solve(h, 1e-9)
+    assert tuple(np.nonzero(res["beta"])[0]) == br.support
+    assert res["ub"] == pytest.approx(br.objective, rel=1e-8)
+    assert res["lb"] <= br.objective * (1 + 1e-9)
+    case = json.load(open(GOLD))["cases"][0]
+    inst = datagen.config_instance("c1", case["instance"])
+    o = bnb.bnb_options_default(M=case["M"], precision=prec, batch_K=64, node_tol=1e-7,
+                                max_admm_iter=5000, queue_capacity=1 << 16, time_limit_s=60.0,
+                                early_branch=1)
+    with bnb.bnb_create(inst.X, inst.y, case["lambda0"], case["lambda2"], o) as h:
+        res = bnb.bnb_solve(h, case["gap"])
+    assert [int(i) for i in np.nonzero(res["beta"])[0]] == case["support"]
+    assert res["ub"] == pytest.approx(case["objective"], rel=1e-8)
+
+
 def test_histograms_count_every_solved_node_and_depth_limit_is_reported():
     inst, lam0, lam2, M = _inst("c1_p16", 1, frac=0.03)
     br = brute.solve(inst.X, inst.y, lam0, lam2, M)
