@@ -16,7 +16,7 @@ bnb = pytest.importorskip("paper_2602_04551_b300")
 from paper_2602_04551_b300.serve import Request, Server, LibraryBackend, latency_summary  # noqa: E402
 
 
-def _requests():
+def _requests(early_branch=0):
     specs = [(120, 16, 0.1, 3, 0.05), (200, 40, 0.3, 4, 0.03), (150, 60, 0.5, 5, 0.05),
              (300, 30, 0.7, 3, 0.1), (200, 50, 0.1, 5, 0.04), (100, 24, 0.3, 3, 0.02)]
     reqs = []
@@ -26,18 +26,23 @@ def _requests():
         M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
         lam0 = frac * datagen.lambda0_scale(inst.X, inst.y, lam2)
         reqs.append(Request(rid=i, X=inst.X, y=inst.y, lambda0=lam0, lambda2=lam2, M=M, gap=1e-6,
-                            arrival=0.02 * i,
+                            # (the early-branch stop solves these small trees in a few
+                            # milliseconds: closer arrivals keep the solves overlapping)
+                            arrival=(0.002 if early_branch else 0.02) * i,
                             options=dict(batch_K=64, node_tol=1e-7, max_admm_iter=5000,
-                                         time_limit_s=60.0)))
+                                         time_limit_s=60.0, early_branch=early_branch)))
     return reqs
 
 
-def test_each_result_same_alone_and_in_the_mix():
-    reqs = _requests()
+@pytest.mark.parametrize("early_branch", [0, 1])
+def test_each_result_same_alone_and_in_the_mix(early_branch):
+    """With the paper's node stop and with the early-branch one the serving loop uses."""
+    reqs = _requests(early_branch)
     alone = {}
     for r in reqs:
         o = bnb.bnb_options_default(M=r.M, batch_K=64, node_tol=1e-7, max_admm_iter=5000,
-                                    queue_capacity=1 << 16, time_limit_s=60.0)
+                                    queue_capacity=1 << 16, time_limit_s=60.0,
+                                    early_branch=early_branch)
         with bnb.bnb_create(r.X, r.y, r.lambda0, r.lambda2, o) as h:
             alone[r.rid] = bnb.bnb_solve(h, r.gap)
     # a budget that holds only part of the stream at once forces admission waits
