@@ -870,6 +870,17 @@ def run_certified(args, seed):
                 if row["fp64"]["certified"]:
                     rec["speedup_vs_fp64"] = row["fp64"]["seconds"] / rec["seconds"]
             row["mixed_early_branch"] = rec
+            # the plain FP64 path with the same node stop (same algorithm, FP64 everywhere)
+            r64, b64, _ = solve_record(args, inst, lam0, lam2, M, args.rho, args.alpha,
+                                       bnb.BNB_PREC_FP64, args.cert_time_limit,
+                                       early_branch=1, check_every=10)
+            r64["same_support_as_mixed"] = [int(i) for i in np.nonzero(b64)[0]] == \
+                row["mixed_support_list"]
+            if rec["certified"] and r64["certified"]:
+                rec["speedup_vs_fp64_early_branch"] = r64["seconds"] / rec["seconds"]
+            row["fp64_early_branch"] = r64
+            note(f"certified target {pk['target_nnz']} fp64_early_branch: {r64['status']} "
+                 f"{r64['seconds']:.3f} s")
             note(f"certified target {pk['target_nnz']} mixed_early_branch: {rec['status']} "
                  f"{rec['seconds']:.3f} s")
         row.pop("mixed_support_list", None)
@@ -885,6 +896,11 @@ def run_certified(args, seed):
         "note": "run on the instances the mixed path certified; early_branch = 1, a stop "
                 "test every 10 iterations",
         "seconds": [r["seconds"] for r in eb]}
+    eb64 = [r["fp64_early_branch"] for r in rows if "fp64_early_branch" in r]
+    cert["fp64_early_branch"] = {
+        "certified": sum(1 for r in eb64 if r["certified"]), "of": len(eb64),
+        "note": "the same instances and node stop, FP64 everywhere",
+        "seconds": [r["seconds"] for r in eb64]}
     rv = {"certificates": None, "supports_ok": all(
         r[nm]["support_objective_rel_diff"] <= 1e-10 for r in rows for nm in ("mixed", "fp64"))
         and all(r["support_objective_rel_diff"] <= 1e-10 for r in eb)}

@@ -251,11 +251,14 @@ def test_certified_side_times_the_early_branch_stop_where_the_mixed_path_certifi
                                  cert_time_limit=1.0)
     out = bench.run_certified(args, 0)
     rows = out["instances"]
-    assert [c[2:] for c in calls] == [(None, None), (None, None), (1, 10), (None, None),
-                                      (None, None)]
+    assert [c[1:] for c in calls] == [(3, None, None), (0, None, None), (3, 1, 10),
+                                      (0, 1, 10), (3, None, None), (0, None, None)]
     eb = rows[0]["mixed_early_branch"]
     assert eb["same_support_as_mixed"] and eb["speedup_vs_mixed"] == pytest.approx(2.0)
     assert eb["speedup_vs_fp64"] == pytest.approx(100.0)
+    assert eb["speedup_vs_fp64_early_branch"] == pytest.approx(1.0)
+    assert rows[0]["fp64_early_branch"]["same_support_as_mixed"]
+    assert out["paths"]["fp64_early_branch"]["of"] == 1
     assert "mixed_early_branch" not in rows[1] and "mixed_support_list" not in rows[0]
     assert out["paths"]["mixed_early_branch"]["certified"] == 1
     assert out["paths"]["mixed_early_branch"]["of"] == 1
