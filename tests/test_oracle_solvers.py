@@ -261,6 +261,39 @@ def test_bnb_exact_with_loose_node_solves():
     assert checked >= 1
 
 
+@pytest.mark.parametrize("mfac", [1.5, 0.3])   # both regimes of Eq. psi
+def test_primal_at_feasible_points_bounds_the_node_value_from_above(mfac):
+    """The premise of the early-branch node stop: the relaxation objective at any point
+    feasible for the node (|beta_i| <= M, beta = 0 on F0) -- in particular every ADMM iterate
+    after its prox step -- is at least the node's relaxation value (from the independent
+    second solver), so a primal value below the prune threshold proves the node cannot be
+    pruned.  A point outside the box is infeasible and has no such bound (psi = inf)."""
+    inst = _small(4)
+    lam0, lam2, M = _params(inst, frac=0.03, mfac=mfac)
+    X, y = inst.X, inst.y
+    rng = np.random.default_rng(7)
+    data = admm.AdmmData(X, y, 0.5)
+    for trial in range(6):
+        fix = np.full(inst.p, relax.FREE, dtype=np.int8)
+        idx = rng.choice(inst.p, size=4, replace=False)
+        fix[idx[:2]] = relax.F0
+        fix[idx[2:3]] = relax.F1
+        _, opt = pgd.solve_node(X, y, fix, lam0, lam2, M)
+        for _ in range(20):
+            b = rng.uniform(-M, M, inst.p) * (rng.random(inst.p) < 0.5)
+            b[fix == relax.F0] = 0.0
+            assert relax.primal_value(X, y, b, fix, lam0, lam2, M) >= opt - 1e-12 * max(1.0, abs(opt))
+        beta = np.zeros(inst.p)
+        v = np.zeros(inst.p)
+        for _ in range(15):
+            _, beta, v = admm.admm_iteration(data, beta, v, fix, lam0, lam2, M)
+            assert np.all(np.abs(beta) <= M * (1 + 1e-15)) and np.all(beta[fix == relax.F0] == 0)
+            assert relax.primal_value(X, y, beta, fix, lam0, lam2, M) >= opt - 1e-12 * max(1.0, abs(opt))
+    out = np.zeros(inst.p)
+    out[0] = 2 * M
+    assert relax.primal_value(X, y, out, np.full(inst.p, relax.FREE, np.int8), lam0, lam2, M) == np.inf
+
+
 def test_branch_index_hand_cases():
     """The branching rule on hand-made inputs: the most fractional free z_i
     (min(z, 1 - z) largest), the lowest index on ties, fixed indices never chosen, and
