@@ -483,6 +483,19 @@ def test_admm_iterations_pairs_in_clusters_full_size(rho, alpha):
                          stats={"u_cluster_pairs": 4})
 
 
+def test_admm_iterations_pairs_in_clusters_of_two():
+    """U' on CTA pairs in split-K clusters with two pairs per cluster (the form the setup
+    picks at C3): p = 300 gives 5 K steps, too few for four pairs, so the forced form takes
+    two; three iterations in one round against the oracle's."""
+    inst = datagen.make_instance(100, 300, 0.3, 5, 5.0, 2601)
+    lam2 = 1e-3
+    M = datagen.big_m(inst.X, inst.y, inst.support_true, lam2)
+    lam0 = 0.05 * datagen.lambda0_scale(inst.X, inst.y, lam2)
+    _one_iteration_check(inst, lam0, lam2, M, 3, K=200, Kopt=256, rows=range(0, 200, 7),
+                         seed=45, rho=0.3, alpha=1.6, iters=3, u_shape=3, mv_crossover=0,
+                         stats={"u_cluster_pairs": 2})
+
+
 @pytest.mark.parametrize("ushape", U_SHAPES)
 def test_converged_bounds_every_u_shape(ushape):
     """Converged node bounds (the stop-test sums of U come from either form of U') stay
