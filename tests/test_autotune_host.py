@@ -132,3 +132,17 @@ def test_check_every_chosen_by_search(monkeypatch):
     assert calls[2:] == [(0.3, 20), (0.3, 30), (0.3, 40)]
     assert [r["check_every"] for r in entry["check_every"]] == [10, 20, 30]
     assert entry["score"]["search_nodes_per_s"] == 260.0
+
+
+def test_steady_state_needs_a_certified_batch_and_a_batch_of_waiting_nodes():
+    """autotune.steady, the priming rule of the bench and of the tree-search trial: a batch's
+    worth of certified nodes and K open nodes besides the active slots; the active-slot
+    count alone (read after a round's stop test has retired its converged slots) does not
+    decide it."""
+    K = 512
+    pr = lambda nodes, open_nodes, active: {"nodes": nodes, "open_nodes": open_nodes,
+                                             "active_slots": active}
+    assert autotune.steady(pr(600, 1100, 437), K)          # slots refill from 663 waiting
+    assert not autotune.steady(pr(400, 5000, 512), K)      # too few nodes certified yet
+    assert not autotune.steady(pr(600, 900, 500), K)       # only 400 waiting: a refill runs short
+    assert autotune.steady(pr(10**6, 2 * 10**6, 0), K)     # every slot retired at once (C3)
