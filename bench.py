@@ -658,6 +658,20 @@ def roofline(out, args, pk):
         other = "bf16_tflops_sustained" if burst else "bf16_tflops"
         if other in pk:
             r["frac_vs_" + ("sustained" if burst else "burst")] = ach / float(pk[other])
+    if name == "gemm_xtu_prox" and "hbm_gbs" in pk:
+        # the same launch against the copy bandwidth: its compulsory bytes are the data
+        # operand (X as the precision stores it), U' and the node state the update reads
+        # and writes (beta, V read and written, the fixing codes read, W' written: 21 bytes
+        # per element in the tensor-core forms, 25 in FP32); most of it stays in L2
+        ex = {"tc3": 4, "bf16x2": 2, "bf16": 2}.get(args.precision, 4)
+        state = 21 if args.precision != "fp32" else 25
+        nbytes = float(ex * n * p + ex * n * active + state * p * active)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        r["hbm_view"] = {"algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+                         "peak_gbs": float(pk["hbm_gbs"]), "frac": gbs / float(pk["hbm_gbs"]),
+                         "note": "compulsory bytes of the launch over its time, against the "
+                                 "measured copy bandwidth (the launch is not DRAM-bound: "
+                                 "its working set stays largely in L2)"}
     return r
 
 

@@ -53,6 +53,20 @@ def test_roofline_figures(bench):
     assert r["traffic"] == bench.TRAFFIC[key]["bytes"]
 
 
+def test_roofline_hbm_view_of_the_fused_product(bench):
+    """The fused product's compulsory bytes (X and U' as BF16 pairs, 21 bytes of node state
+    per active element) over its launch time, against the measured copy bandwidth."""
+    key = next(iter(bench.TRAFFIC))
+    r = bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1390.1, "hbm_gbs": 6480.8})
+    n, p, a = 1000, 5000, 491
+    nbytes = 4.0 * n * p + 4.0 * n * a + 21.0 * p * a
+    hv = r["hbm_view"]
+    assert hv["algorithmic_bytes"] == nbytes
+    assert hv["achieved_gbs"] == pytest.approx(nbytes / 0.036e-3 / 1e9)
+    assert hv["frac"] == pytest.approx(hv["achieved_gbs"] / 6480.8)
+    assert "hbm_view" not in bench.roofline(_out(key), _args(key), {"bf16_tflops_sustained": 1.0})
+
+
 def test_fallback_peak_is_labelled(bench):
     key = next(iter(bench.TRAFFIC))
     r = bench.roofline(_out(key), _args(key), {})
