@@ -140,7 +140,8 @@ typedef struct {
   int early_branch;      /* bnb_solve's node stop: 1 also retires a node at a stop test where
                             its estimated relaxation objective P(beta) (an upper bound on the
                             node's relaxation value, beta being feasible) lies below the
-                            prune threshold UB (1 - gap) by more than 10 node_tol: no
+                            prune threshold t = UB (1 - gap) by more than
+                            10 node_tol max(1, |t|) (with an incumbent): no
                             accuracy could then prune it, so it is certified (a valid, looser
                             FP64 bound) and branched at once; 0 (default) iterates every
                             node to the node gap, as the paper does (Section 5.1).  Exactness
